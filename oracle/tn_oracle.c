@@ -1,0 +1,665 @@
+/*
+ * tn_oracle.c -- plain, slow, CPU-only oracle for the independent-set (IS)
+ * tensor network contraction of arXiv:2501.00227.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this file.  It shares no
+ * code, header, table or helper with the GPU library under
+ * paper_2501_00227_gb300/csrc, and the GPU library never calls it.
+ *
+ * What it computes (all exact, all integer valued):
+ *   - the tensors of the IS network: one edge tensor B per edge (Eq. 6) and
+ *     one vertex tensor W per vertex (Eq. 7); leaves are numbered edges first,
+ *     then vertices, as in the flattened einsum of Sec. 3.2;
+ *   - a pairwise (binary-tree) contraction along a given SSA order, Sec. 4.1:
+ *     each step contracts two live tensors into a new one whose labels are
+ *     the labels of the pair still used by some other live tensor (the output
+ *     of the whole network is a scalar, Sec. 3.2);
+ *   - element types (Table 1, Sec. 5.2, Sec. 5.3):
+ *       tropical  (max,+), zero = -inf, one = 0                   -> MIS size
+ *       counting  (max,+) paired with a count                      -> #MIS
+ *       mod-p     ordinary (+,*) reduced modulo a prime p          -> #IS mod p
+ *   - the complexity measures tc / sc / rwc of a binary order (Sec. 4.1);
+ *   - the greedy order of Sec. 4.2.1 (cost Eq. 9 with alpha = 0);
+ *   - brute force over all 2^n vertex subsets (definition of an independent
+ *     set, Sec. 2.1.1) as an independent second check.
+ *
+ * Representation: a tensor of rank r over labels L[0..r-1] (vertex ids) is a
+ * dense array of 2^r entries; entry x holds the value for the assignment in
+ * which label L[j] takes the value of bit j of x (L[0] is the least
+ * significant bit).
+ *
+ * Tropical values are int64 with OR_NEG_INF = INT64_MIN standing for -inf.
+ * Counting values are (int64 max, unsigned __int128 count); counts saturate
+ * at 2^128-1 (never reached by the tests).  Mod-p values are uint64 < p and
+ * every operation is a plain `%`.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_NEG_INF INT64_MIN
+#define OR_MAX_RANK 128
+
+enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2, OR_ETOOBIG = -3 };
+enum { OR_TROPICAL = 1, OR_COUNTING = 2, OR_MODP = 3 };
+
+typedef unsigned __int128 u128;
+
+/* ------------------------------------------------------------------ */
+/* element types                                                       */
+/* ------------------------------------------------------------------ */
+
+/* tropical (Sec. 5.2): a (+) b = max(a, b); a (x) b = a + b; -inf absorbs */
+static int64_t trop_mul(int64_t a, int64_t b) {
+    if (a == OR_NEG_INF || b == OR_NEG_INF) return OR_NEG_INF;
+    return a + b;
+}
+static int64_t trop_add(int64_t a, int64_t b) { return a > b ? a : b; }
+
+/* counting tropical (Sec. 5.3, CountingMax): (n, c).
+ * (a, c) (x) (b, d) = (a + b, c * d)
+ * (a, c) (+) (b, d) = the pair with the larger first component; on a tie the
+ *                      counts add.  zero = (-inf, 0), one = (0, 1).          */
+typedef struct { int64_t n; u128 c; } cnt_t;
+
+static const u128 U128_MAX = ~(u128)0;
+
+static u128 sat_mul128(u128 a, u128 b) {
+    if (a == 0 || b == 0) return 0;
+    if (a > U128_MAX / b) return U128_MAX;
+    return a * b;
+}
+static u128 sat_add128(u128 a, u128 b) {
+    u128 s = a + b;
+    return s < a ? U128_MAX : s;
+}
+static cnt_t cnt_mul(cnt_t x, cnt_t y) {
+    cnt_t r;
+    if (x.n == OR_NEG_INF || y.n == OR_NEG_INF) { r.n = OR_NEG_INF; r.c = 0; return r; }
+    r.n = x.n + y.n;
+    r.c = sat_mul128(x.c, y.c);
+    return r;
+}
+static cnt_t cnt_add(cnt_t x, cnt_t y) {
+    if (x.n > y.n) return x;
+    if (y.n > x.n) return y;
+    cnt_t r; r.n = x.n; r.c = sat_add128(x.c, y.c);
+    return r;
+}
+
+/* ------------------------------------------------------------------ */
+/* the network: leaves and SSA order                                   */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int rank;
+    int32_t labels[OR_MAX_RANK];
+    void *data;      /* 2^rank entries of the element type */
+} tensor_t;
+
+static size_t elem_size(int kind, int nprimes) {
+    if (kind == OR_TROPICAL) return sizeof(int64_t);
+    if (kind == OR_COUNTING) return sizeof(cnt_t);
+    return sizeof(uint64_t) * (size_t)nprimes;   /* one residue per prime */
+}
+
+/* Checks that the graph is simple (0 <= u,v < n, u != v, no repeated edge). */
+static int check_graph(int n, const int32_t *edges, int m) {
+    if (n < 1 || m < 0) return OR_EINVAL;
+    for (int e = 0; e < m; e++) {
+        int u = edges[2 * e], v = edges[2 * e + 1];
+        if (u < 0 || v < 0 || u >= n || v >= n || u == v) return OR_EINVAL;
+        for (int f = 0; f < e; f++) {
+            int a = edges[2 * f], b = edges[2 * f + 1];
+            if ((a == u && b == v) || (a == v && b == u)) return OR_EINVAL;
+        }
+    }
+    return OR_OK;
+}
+
+/* Checks an SSA order: T = m + n leaves; step s consumes two distinct ids that
+ * exist (< T + s) and were not consumed before; it creates id T + s.  A
+ * complete order has T - 1 steps. */
+static int check_order(int T, const int32_t *order, int nsteps) {
+    if (nsteps != T - 1) return OR_EINVAL;
+    char *used = calloc((size_t)(2 * T), 1);
+    if (!used) return OR_ENOMEM;
+    int rc = OR_OK;
+    for (int s = 0; s < nsteps && rc == OR_OK; s++) {
+        int i = order[2 * s], j = order[2 * s + 1];
+        if (i < 0 || j < 0 || i >= T + s || j >= T + s || i == j || used[i] || used[j]) rc = OR_EINVAL;
+        else used[i] = used[j] = 1;
+    }
+    free(used);
+    return rc;
+}
+
+/* Leaf tensors of the IS network, Eqs. (5)-(7) with unit weights:
+ *   B(n_u, n_v) = [[one, one], [one, zero]]      (edge)
+ *   W(n_v)      = [one, x]  with x = e^{beta w}:  tropical 1, counting (1,1),
+ *                                                 counting all IS (beta = 0): 1. */
+static int make_leaf(tensor_t *t, int kind, const uint32_t *primes, int nprimes, int is_edge,
+                     int32_t u, int32_t v) {
+    t->rank = is_edge ? 2 : 1;
+    t->labels[0] = u;
+    if (is_edge) t->labels[1] = v;
+    size_t ne = (size_t)1 << t->rank;
+    t->data = malloc(ne * elem_size(kind, nprimes));
+    if (!t->data) return OR_ENOMEM;
+    for (size_t x = 0; x < ne; x++) {
+        int both = is_edge && x == 3;          /* n_u = n_v = 1 */
+        int occupied = !is_edge && x == 1;     /* n_v = 1       */
+        if (kind == OR_TROPICAL) {
+            int64_t *d = t->data;
+            d[x] = both ? OR_NEG_INF : (occupied ? 1 : 0);
+        } else if (kind == OR_COUNTING) {
+            cnt_t *d = t->data;
+            if (both) { d[x].n = OR_NEG_INF; d[x].c = 0; }
+            else { d[x].n = occupied ? 1 : 0; d[x].c = 1; }
+        } else {
+            uint64_t *d = t->data;
+            for (int q = 0; q < nprimes; q++) d[x * nprimes + q] = both ? 0 : 1 % primes[q];
+        }
+    }
+    return OR_OK;
+}
+
+/* position of label l in L[0..r-1], or -1 */
+static int find_label(const int32_t *L, int r, int32_t l) {
+    for (int j = 0; j < r; j++) if (L[j] == l) return j;
+    return -1;
+}
+
+/* ------------------------------------------------------------------ */
+/* one pairwise contraction (Sec. 4.1):                                */
+/*   C[c] = (+)_{s} A[a(c, s)] (x) B[b(c, s)]                          */
+/* where c ranges over assignments of the output labels LC and s over  */
+/* assignments of the summed labels S = (LA u LB) \ LC.                */
+/* ------------------------------------------------------------------ */
+static int contract_pair(int kind, const uint32_t *primes, int nprimes,
+                         const tensor_t *A, const tensor_t *B, tensor_t *C) {
+    int32_t S[2 * OR_MAX_RANK];
+    int ns = 0;
+    for (int j = 0; j < A->rank; j++)
+        if (find_label(C->labels, C->rank, A->labels[j]) < 0) S[ns++] = A->labels[j];
+    for (int j = 0; j < B->rank; j++)
+        if (find_label(C->labels, C->rank, B->labels[j]) < 0 &&
+            find_label(A->labels, A->rank, B->labels[j]) < 0) S[ns++] = B->labels[j];
+    if (ns > 40 || C->rank > 34 || A->rank > 34 || B->rank > 34) return OR_ETOOBIG;
+
+    /* offset of each summed-label assignment s into A and into B */
+    size_t nsum = (size_t)1 << ns;
+    uint64_t *sa = malloc(nsum * sizeof(uint64_t)), *sb = malloc(nsum * sizeof(uint64_t));
+    if (!sa || !sb) { free(sa); free(sb); return OR_ENOMEM; }
+    for (size_t s = 0; s < nsum; s++) {
+        uint64_t oa = 0, ob = 0;
+        for (int j = 0; j < ns; j++) {
+            if (!((s >> j) & 1)) continue;
+            int pa = find_label(A->labels, A->rank, S[j]);
+            int pb = find_label(B->labels, B->rank, S[j]);
+            if (pa >= 0) oa |= (uint64_t)1 << pa;
+            if (pb >= 0) ob |= (uint64_t)1 << pb;
+        }
+        sa[s] = oa; sb[s] = ob;
+    }
+    /* position of each output label in A and in B (-1 if absent) */
+    int ca[OR_MAX_RANK], cb[OR_MAX_RANK];
+    for (int j = 0; j < C->rank; j++) {
+        ca[j] = find_label(A->labels, A->rank, C->labels[j]);
+        cb[j] = find_label(B->labels, B->rank, C->labels[j]);
+    }
+
+    size_t nc = (size_t)1 << C->rank;
+    C->data = malloc(nc * elem_size(kind, nprimes));
+    if (!C->data) { free(sa); free(sb); return OR_ENOMEM; }
+
+#pragma omp parallel for schedule(static)
+    for (long long ci = 0; ci < (long long)nc; ci++) {
+        uint64_t c = (uint64_t)ci, ba = 0, bb = 0;
+        for (int j = 0; j < C->rank; j++) {
+            if (!((c >> j) & 1)) continue;
+            if (ca[j] >= 0) ba |= (uint64_t)1 << ca[j];
+            if (cb[j] >= 0) bb |= (uint64_t)1 << cb[j];
+        }
+        if (kind == OR_TROPICAL) {
+            const int64_t *a = A->data, *b = B->data;
+            int64_t acc = OR_NEG_INF;                      /* zero */
+            for (size_t s = 0; s < nsum; s++)
+                acc = trop_add(acc, trop_mul(a[ba | sa[s]], b[bb | sb[s]]));
+            ((int64_t *)C->data)[c] = acc;
+        } else if (kind == OR_COUNTING) {
+            const cnt_t *a = A->data, *b = B->data;
+            cnt_t acc; acc.n = OR_NEG_INF; acc.c = 0;     /* zero */
+            for (size_t s = 0; s < nsum; s++)
+                acc = cnt_add(acc, cnt_mul(a[ba | sa[s]], b[bb | sb[s]]));
+            ((cnt_t *)C->data)[c] = acc;
+        } else {
+            const uint64_t *a = A->data, *b = B->data;
+            uint64_t *out = (uint64_t *)C->data + c * nprimes;
+            for (int q = 0; q < nprimes; q++) {
+                uint64_t p = primes[q], acc = 0;
+                for (size_t s = 0; s < nsum; s++) {
+                    uint64_t prod = (a[(ba | sa[s]) * nprimes + q] * b[(bb | sb[s]) * nprimes + q]) % p;
+                    acc = (acc + prod) % p;
+                }
+                out[q] = acc;
+            }
+        }
+    }
+    free(sa); free(sb);
+    return OR_OK;
+}
+
+/* Output labels of contracting live tensors i and j: the labels of the pair
+ * still used by some other live tensor (the network output is a scalar). */
+static void output_labels(const tensor_t *ti, const tensor_t *tj, const int *users, tensor_t *out) {
+    out->rank = 0;
+    for (int k = 0; k < ti->rank; k++) {
+        int32_t l = ti->labels[k];
+        int others = users[l] - 1 - (find_label(tj->labels, tj->rank, l) >= 0);
+        if (others > 0) out->labels[out->rank++] = l;
+    }
+    for (int k = 0; k < tj->rank; k++) {
+        int32_t l = tj->labels[k];
+        if (find_label(ti->labels, ti->rank, l) >= 0) continue;
+        if (users[l] - 1 > 0) out->labels[out->rank++] = l;
+    }
+}
+
+/* Contract the whole network along an SSA order and write the scalar into
+ * *result (element type `kind`).  With a single leaf (n = 1, m = 0) the scalar
+ * is the (+)-sum of that leaf's entries. */
+static int contract_network(int kind, const uint32_t *primes, int nprimes, int n, const int32_t *edges,
+                            int m, const int32_t *order, int nsteps, void *result) {
+    int rc = check_graph(n, edges, m);
+    if (rc) return rc;
+    int T = m + n;
+    rc = check_order(T, order, nsteps);
+    if (rc) return rc;
+    if (kind == OR_MODP) {
+        if (nprimes < 1) return OR_EINVAL;
+        for (int q = 0; q < nprimes; q++) if (primes[q] < 2 || primes[q] >= (1u << 31)) return OR_EINVAL;
+    }
+    tensor_t *t = calloc((size_t)(2 * T), sizeof(tensor_t));
+    int *users = calloc((size_t)n, sizeof(int));
+    if (!t || !users) { free(t); free(users); return OR_ENOMEM; }
+    for (int e = 0; e < m && !rc; e++) rc = make_leaf(&t[e], kind, primes, nprimes, 1, edges[2 * e], edges[2 * e + 1]);
+    for (int v = 0; v < n && !rc; v++) rc = make_leaf(&t[m + v], kind, primes, nprimes, 0, v, 0);
+    for (int i = 0; i < T && !rc; i++) for (int k = 0; k < t[i].rank; k++) users[t[i].labels[k]]++;
+
+    int root = 0;
+    for (int s = 0; s < nsteps && !rc; s++) {
+        int i = order[2 * s], j = order[2 * s + 1], c = T + s;
+        output_labels(&t[i], &t[j], users, &t[c]);
+        rc = contract_pair(kind, primes, nprimes, &t[i], &t[j], &t[c]);
+        if (rc) break;
+        for (int k = 0; k < t[i].rank; k++) users[t[i].labels[k]]--;
+        for (int k = 0; k < t[j].rank; k++) users[t[j].labels[k]]--;
+        for (int k = 0; k < t[c].rank; k++) users[t[c].labels[k]]++;
+        free(t[i].data); t[i].data = NULL;
+        free(t[j].data); t[j].data = NULL;
+        root = c;
+    }
+    if (!rc) {
+        tensor_t *r = &t[root];
+        size_t ne = (size_t)1 << r->rank;          /* rank 0 unless T == 1 */
+        if (kind == OR_TROPICAL) {
+            int64_t acc = OR_NEG_INF;
+            for (size_t x = 0; x < ne; x++) acc = trop_add(acc, ((int64_t *)r->data)[x]);
+            *(int64_t *)result = acc;
+        } else if (kind == OR_COUNTING) {
+            cnt_t acc; acc.n = OR_NEG_INF; acc.c = 0;
+            for (size_t x = 0; x < ne; x++) acc = cnt_add(acc, ((cnt_t *)r->data)[x]);
+            *(cnt_t *)result = acc;
+        } else {
+            for (int q = 0; q < nprimes; q++) {
+                uint64_t acc = 0;
+                for (size_t x = 0; x < ne; x++) acc = (acc + ((uint64_t *)r->data)[x * nprimes + q]) % primes[q];
+                ((uint64_t *)result)[q] = acc;
+            }
+        }
+    }
+    for (int i = 0; i < 2 * T; i++) free(t[i].data);
+    free(t); free(users);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* exported entry points (ctypes)                                      */
+/* ------------------------------------------------------------------ */
+
+int or_set_threads(int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
+int or_check_order(int n, const int32_t *edges, int m, const int32_t *order, int nsteps) {
+    int rc = check_graph(n, edges, m);
+    return rc ? rc : check_order(m + n, order, nsteps);
+}
+
+/* MIS size: *max_out = tropical scalar (INT64_MIN if -inf). */
+int or_contract_tropical(int n, const int32_t *edges, int m, const int32_t *order, int nsteps,
+                         int64_t *max_out) {
+    return contract_network(OR_TROPICAL, NULL, 0, n, edges, m, order, nsteps, max_out);
+}
+
+/* (MIS size, number of maximum independent sets); the count is returned as
+ * two 64-bit halves of the 128-bit value. */
+int or_contract_counting(int n, const int32_t *edges, int m, const int32_t *order, int nsteps,
+                         int64_t *max_out, uint64_t *count_lo, uint64_t *count_hi) {
+    cnt_t r;
+    int rc = contract_network(OR_COUNTING, NULL, 0, n, edges, m, order, nsteps, &r);
+    if (!rc) { *max_out = r.n; *count_lo = (uint64_t)r.c; *count_hi = (uint64_t)(r.c >> 64); }
+    return rc;
+}
+
+/* Number of independent sets modulo each prime (Z at beta = 0, Sec. 5.1). */
+int or_contract_modp(int n, const int32_t *edges, int m, const int32_t *order, int nsteps,
+                     const uint32_t *primes, int nprimes, uint64_t *residues) {
+    return contract_network(OR_MODP, primes, nprimes, n, edges, m, order, nsteps, residues);
+}
+
+/* One pairwise contraction on caller tensors (labels as above, LC given). */
+static int pair_common(int kind, const uint32_t *primes, int nprimes,
+                       const void *a, const int32_t *la, int ra,
+                       const void *b, const int32_t *lb, int rb,
+                       const int32_t *lc, int rc_, void *c) {
+    if (ra < 0 || rb < 0 || rc_ < 0 || ra > 30 || rb > 30 || rc_ > 30) return OR_EINVAL;
+    tensor_t A = {0}, B = {0}, C = {0};
+    A.rank = ra; B.rank = rb; C.rank = rc_;
+    memcpy(A.labels, la, sizeof(int32_t) * (size_t)ra);
+    memcpy(B.labels, lb, sizeof(int32_t) * (size_t)rb);
+    memcpy(C.labels, lc, sizeof(int32_t) * (size_t)rc_);
+    for (int j = 0; j < rc_; j++)
+        if (find_label(la, ra, lc[j]) < 0 && find_label(lb, rb, lc[j]) < 0) return OR_EINVAL;
+    A.data = (void *)a; B.data = (void *)b;
+    int rc = contract_pair(kind, primes, nprimes, &A, &B, &C);
+    if (rc) return rc;
+    memcpy(c, C.data, ((size_t)1 << rc_) * elem_size(kind, nprimes));
+    free(C.data);
+    return OR_OK;
+}
+
+int or_pair_tropical(const int64_t *a, const int32_t *la, int ra, const int64_t *b, const int32_t *lb, int rb,
+                     const int32_t *lc, int rc, int64_t *c) {
+    return pair_common(OR_TROPICAL, NULL, 0, a, la, ra, b, lb, rb, lc, rc, c);
+}
+
+/* counting pair: values n[], counts as 64-bit inputs; output counts as 128-bit (lo, hi) */
+int or_pair_counting(const int64_t *an, const uint64_t *ac, const int32_t *la, int ra,
+                     const int64_t *bn, const uint64_t *bc, const int32_t *lb, int rb,
+                     const int32_t *lc, int rc, int64_t *cn, uint64_t *c_lo, uint64_t *c_hi) {
+    size_t na = (size_t)1 << ra, nb = (size_t)1 << rb, ncc = (size_t)1 << rc;
+    cnt_t *A = malloc(na * sizeof(cnt_t)), *B = malloc(nb * sizeof(cnt_t)), *C = malloc(ncc * sizeof(cnt_t));
+    int r = OR_ENOMEM;
+    if (A && B && C) {
+        for (size_t x = 0; x < na; x++) { A[x].n = an[x]; A[x].c = ac[x]; }
+        for (size_t x = 0; x < nb; x++) { B[x].n = bn[x]; B[x].c = bc[x]; }
+        r = pair_common(OR_COUNTING, NULL, 0, A, la, ra, B, lb, rb, lc, rc, C);
+        if (!r) for (size_t x = 0; x < ncc; x++) { cn[x] = C[x].n; c_lo[x] = (uint64_t)C[x].c; c_hi[x] = (uint64_t)(C[x].c >> 64); }
+    }
+    free(A); free(B); free(C);
+    return r;
+}
+
+/* mod-p pair, one prime, residues as uint64 */
+int or_pair_modp(const uint64_t *a, const int32_t *la, int ra, const uint64_t *b, const int32_t *lb, int rb,
+                 const int32_t *lc, int rc, uint32_t p, uint64_t *c) {
+    if (p < 2 || p >= (1u << 31)) return OR_EINVAL;
+    return pair_common(OR_MODP, &p, 1, a, la, ra, b, lb, rb, lc, rc, c);
+}
+
+/* ------------------------------------------------------------------ */
+/* complexity of an order (Sec. 4.1)                                   */
+/*   tc  = sum over steps of 2^{|LA u LB|}   (operations)              */
+/*   sc  = max over steps of 2^{|LC|}        (largest intermediate)    */
+/*   rwc = sum over steps of 2^|LA| + 2^|LB| + 2^|LC|                  */
+/* returned as doubles (exact below 2^53).                             */
+/* ------------------------------------------------------------------ */
+int or_complexity(int n, const int32_t *edges, int m, const int32_t *order, int nsteps,
+                  double *tc, double *sc, double *rwc) {
+    int rc = or_check_order(n, edges, m, order, nsteps);
+    if (rc) return rc;
+    int T = m + n;
+    tensor_t *t = calloc((size_t)(2 * T), sizeof(tensor_t));
+    int *users = calloc((size_t)n, sizeof(int));
+    if (!t || !users) { free(t); free(users); return OR_ENOMEM; }
+    for (int e = 0; e < m; e++) { t[e].rank = 2; t[e].labels[0] = edges[2 * e]; t[e].labels[1] = edges[2 * e + 1]; }
+    for (int v = 0; v < n; v++) { t[m + v].rank = 1; t[m + v].labels[0] = v; }
+    for (int i = 0; i < T; i++) for (int k = 0; k < t[i].rank; k++) users[t[i].labels[k]]++;
+    double TC = 0, SC = 0, RW = 0;
+    for (int s = 0; s < nsteps; s++) {
+        int i = order[2 * s], j = order[2 * s + 1], c = T + s;
+        output_labels(&t[i], &t[j], users, &t[c]);
+        int uni = t[i].rank;
+        for (int k = 0; k < t[j].rank; k++) if (find_label(t[i].labels, t[i].rank, t[j].labels[k]) < 0) uni++;
+        TC += (double)((uint64_t)1 << uni);
+        double sz = (double)((uint64_t)1 << t[c].rank);
+        if (sz > SC) SC = sz;
+        RW += (double)((uint64_t)1 << t[i].rank) + (double)((uint64_t)1 << t[j].rank) + sz;
+        for (int k = 0; k < t[i].rank; k++) users[t[i].labels[k]]--;
+        for (int k = 0; k < t[j].rank; k++) users[t[j].labels[k]]--;
+        for (int k = 0; k < t[c].rank; k++) users[t[c].labels[k]]++;
+    }
+    if (nsteps == 0) SC = (double)((uint64_t)1 << t[0].rank);
+    *tc = TC; *sc = SC; *rwc = RW;
+    free(t); free(users);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* greedy order (Sec. 4.2.1, Eq. 9 with alpha = 0, temperature 0)      */
+/* At each step every pair of live tensors that shares a label is a    */
+/* candidate; its cost is the size 2^{|LC|} of the tensor it would     */
+/* produce.  The cheapest pair is contracted (ties broken uniformly at */
+/* random).  If no pair shares a label, the two lowest-rank tensors    */
+/* are contracted (an outer product).  The whole run is repeated       */
+/* nrepeat times and the order with the smallest (sc, tc) is kept.     */
+/* ------------------------------------------------------------------ */
+static uint64_t sm64(uint64_t *s) {           /* splitmix64 (Steele et al. 2014) */
+    uint64_t z = (*s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static int greedy_once(int n, const int32_t *edges, int m, uint64_t *rng, int32_t *order,
+                       double *tc_out, int *sc_out) {
+    int T = m + n;
+    tensor_t *t = calloc((size_t)(2 * T), sizeof(tensor_t));
+    int *users = calloc((size_t)n, sizeof(int));
+    char *live = calloc((size_t)(2 * T), 1);
+    int cap = 1 << 16;
+    int32_t *cand = malloc(sizeof(int32_t) * 2 * (size_t)cap);
+    if (!t || !users || !live || !cand) { free(t); free(users); free(live); free(cand); return OR_ENOMEM; }
+    for (int e = 0; e < m; e++) { t[e].rank = 2; t[e].labels[0] = edges[2 * e]; t[e].labels[1] = edges[2 * e + 1]; }
+    for (int v = 0; v < n; v++) { t[m + v].rank = 1; t[m + v].labels[0] = v; }
+    for (int i = 0; i < T; i++) { live[i] = 1; for (int k = 0; k < t[i].rank; k++) users[t[i].labels[k]]++; }
+    double TC = 0; int SC = 0;
+    int rc = OR_OK;
+    /* per-step lists of the live tensors that hold each label */
+    int *ucount = calloc((size_t)n, sizeof(int));
+    int *ustart = calloc((size_t)n + 1, sizeof(int));
+    int *ulist = malloc(sizeof(int) * (size_t)(2 * T) * OR_MAX_RANK);
+    if (!ucount || !ustart || !ulist) { free(ucount); free(ustart); free(ulist); rc = OR_ENOMEM; goto done; }
+    for (int s = 0; s < T - 1; s++) {
+        int best = 1 << 30, ncand = 0;
+        int ntot = T + s;
+        memset(ucount, 0, sizeof(int) * (size_t)n);
+        for (int i = 0; i < ntot; i++)
+            if (live[i]) for (int k = 0; k < t[i].rank; k++) ucount[t[i].labels[k]]++;
+        ustart[0] = 0;
+        for (int l = 0; l < n; l++) ustart[l + 1] = ustart[l] + ucount[l];
+        memset(ucount, 0, sizeof(int) * (size_t)n);
+        for (int i = 0; i < ntot; i++)
+            if (live[i]) for (int k = 0; k < t[i].rank; k++) {
+                int l = t[i].labels[k];
+                ulist[ustart[l] + ucount[l]++] = i;
+            }
+        /* every pair sharing a label, visited once: at its smallest shared label */
+        for (int l = 0; l < n; l++) {
+            for (int x = ustart[l]; x < ustart[l + 1]; x++) {
+                for (int y = x + 1; y < ustart[l + 1]; y++) {
+                    int i = ulist[x], j = ulist[y];
+                    if (i > j) { int tmp = i; i = j; j = tmp; }
+                    int smaller_shared = 0;
+                    for (int k = 0; k < t[i].rank && !smaller_shared; k++)
+                        smaller_shared = t[i].labels[k] < l && find_label(t[j].labels, t[j].rank, t[i].labels[k]) >= 0;
+                    if (smaller_shared) continue;
+                    tensor_t o;
+                    output_labels(&t[i], &t[j], users, &o);
+                    if (o.rank < best) { best = o.rank; ncand = 0; }
+                    if (o.rank == best) {
+                        if (ncand == cap) {
+                            cap *= 2;
+                            int32_t *nc = realloc(cand, sizeof(int32_t) * 2 * (size_t)cap);
+                            if (!nc) { free(ucount); free(ustart); free(ulist); rc = OR_ENOMEM; goto done; }
+                            cand = nc;
+                        }
+                        cand[2 * ncand] = i; cand[2 * ncand + 1] = j; ncand++;
+                    }
+                }
+            }
+        }
+        int pi, pj;
+        if (ncand > 0) {
+            uint64_t r = sm64(rng) % (uint64_t)ncand;
+            pi = cand[2 * r]; pj = cand[2 * r + 1];
+        } else {
+            /* disconnected: outer product of the two lowest-rank live tensors */
+            pi = pj = -1;
+            for (int i = 0; i < ntot; i++) {
+                if (!live[i]) continue;
+                if (pi < 0 || t[i].rank < t[pi].rank) { pj = pi; pi = i; }
+                else if (pj < 0 || t[i].rank < t[pj].rank) pj = i;
+            }
+        }
+        int c = T + s;
+        output_labels(&t[pi], &t[pj], users, &t[c]);
+        if (t[c].rank > 62) { rc = OR_ETOOBIG; goto done; }
+        int uni = t[pi].rank;
+        for (int k = 0; k < t[pj].rank; k++) if (find_label(t[pi].labels, t[pi].rank, t[pj].labels[k]) < 0) uni++;
+        TC += (double)((uint64_t)1 << (uni > 62 ? 62 : uni));
+        if (t[c].rank > SC) SC = t[c].rank;
+        for (int k = 0; k < t[pi].rank; k++) users[t[pi].labels[k]]--;
+        for (int k = 0; k < t[pj].rank; k++) users[t[pj].labels[k]]--;
+        for (int k = 0; k < t[c].rank; k++) users[t[c].labels[k]]++;
+        live[pi] = live[pj] = 0; live[c] = 1;
+        order[2 * s] = pi; order[2 * s + 1] = pj;
+    }
+    free(ucount); free(ustart); free(ulist);
+    *tc_out = TC; *sc_out = SC;
+done:
+    free(t); free(users); free(live); free(cand);
+    return rc;
+}
+
+int or_greedy_order(int n, const int32_t *edges, int m, int nrepeat, uint64_t seed, int32_t *order_out) {
+    int rc = check_graph(n, edges, m);
+    if (rc) return rc;
+    int T = m + n;
+    if (T < 2) return OR_OK;                   /* nothing to contract */
+    if (nrepeat < 1) nrepeat = 1;
+    int32_t *tmp = malloc(sizeof(int32_t) * 2 * (size_t)(T - 1));
+    if (!tmp) return OR_ENOMEM;
+    uint64_t rng = seed;
+    double best_tc = 0; int best_sc = -1;
+    for (int r = 0; r < nrepeat; r++) {
+        double tc; int sc;
+        rc = greedy_once(n, edges, m, &rng, tmp, &tc, &sc);
+        if (rc) break;
+        if (best_sc < 0 || sc < best_sc || (sc == best_sc && tc < best_tc)) {
+            best_sc = sc; best_tc = tc;
+            memcpy(order_out, tmp, sizeof(int32_t) * 2 * (size_t)(T - 1));
+        }
+    }
+    free(tmp);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* brute force (definition of an independent set, Sec. 2.1.1):        */
+/* poly[k] = number of vertex subsets of size k with no edge inside.   */
+/* ------------------------------------------------------------------ */
+int or_bruteforce_poly(int n, const int32_t *edges, int m, uint64_t *poly) {
+    int rc = check_graph(n, edges, m);
+    if (rc) return rc;
+    if (n > 30) return OR_ETOOBIG;
+    uint32_t adj[32] = {0};
+    for (int e = 0; e < m; e++) {
+        adj[edges[2 * e]] |= 1u << edges[2 * e + 1];
+        adj[edges[2 * e + 1]] |= 1u << edges[2 * e];
+    }
+    for (int k = 0; k <= n; k++) poly[k] = 0;
+    uint64_t total = (uint64_t)1 << n;
+    for (uint64_t S = 0; S < total; S++) {
+        int ok = 1;
+        for (int v = 0; v < n && ok; v++)
+            if (((S >> v) & 1) && (adj[v] & (uint32_t)S)) ok = 0;
+        if (ok) poly[__builtin_popcountll(S)]++;
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* flat contraction (Eq. 8 for any graph): the network's scalar as one */
+/* (+)-sum over all 2^n assignments of the (x)-product of every edge   */
+/* tensor and every vertex tensor entry, built from make_leaf's        */
+/* tensors.  No contraction order is involved.  n <= 26.               */
+/* ------------------------------------------------------------------ */
+int or_flat_contract(int kind, int n, const int32_t *edges, int m, const uint32_t *primes, int nprimes,
+                     int64_t *val_out, uint64_t *count_lo, uint64_t *count_hi, uint64_t *residues) {
+    int rc = check_graph(n, edges, m);
+    if (rc) return rc;
+    if (n > 26) return OR_ETOOBIG;
+    if (kind == OR_MODP) {
+        if (nprimes < 1) return OR_EINVAL;
+        for (int q = 0; q < nprimes; q++) if (primes[q] < 2 || primes[q] >= (1u << 31)) return OR_EINVAL;
+    }
+    int np_ = kind == OR_MODP ? nprimes : 0;
+    int T = m + n;
+    tensor_t *t = calloc((size_t)T, sizeof(tensor_t));
+    if (!t) return OR_ENOMEM;
+    for (int e = 0; e < m && !rc; e++) rc = make_leaf(&t[e], kind, primes, np_, 1, edges[2 * e], edges[2 * e + 1]);
+    for (int v = 0; v < n && !rc; v++) rc = make_leaf(&t[m + v], kind, primes, np_, 0, v, 0);
+    if (!rc) {
+        int64_t tacc = OR_NEG_INF;
+        cnt_t cacc; cacc.n = OR_NEG_INF; cacc.c = 0;
+        uint64_t macc[64] = {0};
+        if (np_ > 64) rc = OR_EINVAL;
+        for (uint64_t x = 0; !rc && x < ((uint64_t)1 << n); x++) {
+            int64_t tp = 0;                            /* one */
+            cnt_t cp; cp.n = 0; cp.c = 1;
+            uint64_t mp[64];
+            for (int q = 0; q < np_; q++) mp[q] = 1 % primes[q];
+            for (int i = 0; i < T; i++) {
+                size_t idx = 0;                        /* entry of tensor i at assignment x */
+                for (int j = 0; j < t[i].rank; j++) idx |= (size_t)((x >> t[i].labels[j]) & 1) << j;
+                if (kind == OR_TROPICAL) tp = trop_mul(tp, ((int64_t *)t[i].data)[idx]);
+                else if (kind == OR_COUNTING) cp = cnt_mul(cp, ((cnt_t *)t[i].data)[idx]);
+                else for (int q = 0; q < np_; q++) mp[q] = (mp[q] * ((uint64_t *)t[i].data)[idx * np_ + q]) % primes[q];
+            }
+            if (kind == OR_TROPICAL) tacc = trop_add(tacc, tp);
+            else if (kind == OR_COUNTING) cacc = cnt_add(cacc, cp);
+            else for (int q = 0; q < np_; q++) macc[q] = (macc[q] + mp[q]) % primes[q];
+        }
+        if (!rc) {
+            if (kind == OR_TROPICAL) *val_out = tacc;
+            else if (kind == OR_COUNTING) { *val_out = cacc.n; *count_lo = (uint64_t)cacc.c; *count_hi = (uint64_t)(cacc.c >> 64); }
+            else for (int q = 0; q < np_; q++) residues[q] = macc[q];
+        }
+    }
+    for (int i = 0; i < T; i++) free(t[i].data);
+    free(t);
+    return rc;
+}
