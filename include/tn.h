@@ -1,0 +1,191 @@
+/*
+ * tn.h -- C ABI of libtn, a GB300 (sm_103a) library that contracts the
+ * independent-set (IS) tensor network of arXiv:2501.00227 along a pairwise
+ * contraction order, in one of several semirings.
+ *
+ * The method (paper references are to arXiv:2501.00227):
+ *   - Sec. 3.2, Eqs. (4)-(8): a graph G = (V, E) becomes a tensor network with
+ *     one rank-2 tensor B per edge, B(n_u, n_v) = [[1, 1], [1, 0]] (semiring
+ *     one and zero), and one rank-1 tensor W per vertex, W(n_v) = [1, x];
+ *     contracting all of them to a scalar gives the partition function.
+ *     Leaves are numbered edges first (in the caller's edge order), then
+ *     vertices, as in the flattened einsum printed in Sec. 3.2.
+ *   - Sec. 4.1: the contraction is a binary tree; each pairwise step
+ *     contracts two tensors (a matricised, GEMM-like product).  tc, sc and
+ *     rwc measure an order.
+ *   - Sec. 4.2.1, Eq. (9): the greedy order.
+ *   - Sec. 5.1 (Table 1), Sec. 5.2, Sec. 5.3: the element type selects the
+ *     property: tropical (max,+) -> MIS size (SizeMax); counting tropical ->
+ *     number of maximum independent sets (CountingMax); ordinary (+,*) at
+ *     x = 1 -> number of all independent sets (CountingAll, PartitionFunction
+ *     at beta = 0), computed here exactly as residues modulo 31-bit primes
+ *     recombined by the Chinese remainder theorem (the finite-field approach
+ *     named in Sec. 6.2).
+ *
+ * Conventions shared by every call:
+ *   - All functions return TN_OK (0) or a negative TN_E* code and never abort.
+ *   - Graphs are simple and undirected: edges[2*e], edges[2*e+1] are 0-based
+ *     vertex ids, u != v, no repeated edge.  Weights are unit weights.
+ *   - A contraction order is an SSA list: with T = m + n leaves, step s
+ *     (0 <= s < T-1) contracts ids order[2s] and order[2s+1] (both < T+s, each
+ *     id consumed once) into the new id T+s.  The labels kept by a step are
+ *     the labels of the pair still used by some other live tensor; the last
+ *     step yields the scalar.
+ *   - A tensor of rank r over labels L[0..r-1] is a dense array of 2^r
+ *     entries; entry x is the value at the assignment where label L[j] takes
+ *     bit j of x (L[0] is the least significant bit).
+ *   - Device buffers and streams belong to the caller.  Plans and servers are
+ *     library-owned; a plan is immutable after tn_plan and may be shared by
+ *     threads.
+ */
+#ifndef TN_H
+#define TN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define TN_OK         0
+#define TN_EINVAL    (-1)   /* malformed graph, order, semiring or argument      */
+#define TN_ENOMEM    (-2)   /* host allocation failed or workspace too small      */
+#define TN_EOVERFLOW (-3)   /* a uint64 count reached 2^64-1 (saturated)          */
+#define TN_ETIMEOUT  (-4)   /* a bounded device wait gave up                      */
+#define TN_EAGAIN    (-5)   /* tn_poll: the ticket has not finished yet           */
+#define TN_ECUDA     (-6)   /* a CUDA runtime call failed                         */
+
+/* Element types (Table 1 of the paper).  Device layouts of a tensor with E
+ * entries:
+ *   TN_TROPICAL_F32       float[E]; -inf is IEEE -inf.  Exact for integer
+ *                         values below 2^24.
+ *   TN_TROPICAL_I32       int32[E]; "-inf" is any value < TN_I32_NEG_INF / 2
+ *                         (kernels start every (max,+) accumulation at
+ *                         TN_I32_NEG_INF, so values never go below it).
+ *   TN_COUNTING_TROPICAL  int32 max[E] (as TN_TROPICAL_I32), then, starting
+ *                         at byte offset 8 * ceil(E / 2), uint64 count[E].
+ *                         Counts saturate at UINT64_MAX (= overflow).
+ *   TN_COUNT_MODP         uint32 residue[nprimes][E] (prime-major); each
+ *                         residue is in [0, p). */
+typedef enum {
+    TN_TROPICAL_F32 = 1,
+    TN_TROPICAL_I32 = 2,
+    TN_COUNTING_TROPICAL = 3,
+    TN_COUNT_MODP = 4
+} tn_semiring_t;
+
+#define TN_I32_NEG_INF (-(1 << 30))
+#define TN_MAX_PRIMES 16
+
+typedef struct tn_plan_s *tn_plan_t;
+typedef struct tn_server_s *tn_server_t;
+
+/* Complexity of a plan (Sec. 4.1) and the workspace it needs.
+ *   tc       = sum over steps of 2^{|LA u LB|}  (semiring multiply-adds)
+ *   sc_elems = largest intermediate tensor, in entries
+ *   rwc      = sum over steps of 2^|LA| + 2^|LB| + 2^|LC|  (entries)
+ *   peak_bytes[k] = device workspace tn_contract needs for semiring k+1
+ *                   (for TN_COUNT_MODP: with the nprimes given to
+ *                   tn_plan_info). */
+typedef struct {
+    double log2_tc, log2_sc, log2_rwc;
+    uint64_t tc, sc_elems, rwc;
+    uint64_t peak_bytes[4];
+    int32_t nsteps;
+    int32_t nlaunch_steps;   /* steps executed by the wide (multi-CTA) kernels */
+} tn_plan_info_t;
+
+/* Result of one contraction.
+ *   status   TN_OK, or TN_EOVERFLOW when the count saturated.
+ *   max_i32  MIS size (tropical and counting); INT32_MIN for -inf.
+ *   max_f32  MIS size as float (TN_TROPICAL_F32).
+ *   count    number of maximum independent sets (TN_COUNTING_TROPICAL).
+ *   residues number of independent sets modulo primes[i] (TN_COUNT_MODP);
+ *   crt_limbs the unique value in [0, prod primes) congruent to every
+ *            residue, little-endian 32-bit limbs (crt_nlimbs of them). */
+typedef struct {
+    int32_t status;
+    int32_t max_i32;
+    float max_f32;
+    uint64_t count;
+    int32_t nprimes;
+    uint32_t primes[TN_MAX_PRIMES];
+    uint32_t residues[TN_MAX_PRIMES];
+    int32_t crt_nlimbs;
+    uint32_t crt_limbs[32];
+} tn_result_t;
+
+/* Build a plan from a graph and a complete SSA order (order_len = number of
+ * steps = n + m - 1).  Host only; validates graph and order (TN_EINVAL).
+ * The plan holds the per-step label classes, the kernel chosen for each
+ * step and the offsets of every intermediate in the workspace. */
+int tn_plan(int32_t n_vertices, const int32_t *edges, int32_t m,
+            const int32_t *order, int32_t order_len, tn_plan_t *out);
+
+/* Greedy order of Sec. 4.2.1: at every step contract the label-sharing pair
+ * with the smallest cost 2^|LC| - alpha * (2^|LA| + 2^|LB|) (Eq. 9), ties
+ * broken at random from `seed`; nrepeat runs, keep the one with the smallest
+ * (sc, tc).  Disconnected pieces are joined by outer products of the two
+ * lowest-rank tensors.  order_out: caller-owned, 2 * (n + m - 1) int32. */
+int tn_order_greedy(int32_t n, const int32_t *edges, int32_t m, double alpha,
+                    int32_t nrepeat, uint64_t seed, int32_t *order_out);
+
+/* Complexity and workspace sizes of a plan; nprimes sizes the mod-p entry. */
+int tn_plan_info(tn_plan_t plan, tn_semiring_t semiring, int32_t nprimes, tn_plan_info_t *out);
+
+/* Contract the whole network on the GPU and return the decoded scalar.
+ * primes/nprimes: only for TN_COUNT_MODP (1..TN_MAX_PRIMES pairwise coprime
+ * moduli in [2, 2^31)).  d_workspace: caller-owned device memory of at least
+ * peak_bytes[semiring-1] bytes, 256-byte aligned.  cuda_stream: a
+ * cudaStream_t (NULL = legacy default stream).  Enqueues every kernel on the
+ * stream, then waits for that stream to finish (one 64-byte device-to-host
+ * copy).  Errors: TN_EINVAL (arguments), TN_ENOMEM (workspace too small),
+ * TN_ECUDA (launch failure), TN_ETIMEOUT (a device wait gave up); out->status
+ * is TN_EOVERFLOW when a count saturated. */
+int tn_contract(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *primes, int32_t nprimes,
+                void *d_workspace, size_t ws_bytes, void *cuda_stream, tn_result_t *out);
+
+/* As tn_contract, without waiting: enqueues the contraction and a copy of
+ * the raw scalar into d_raw (TN_RAW_BYTES bytes of caller device memory).
+ * Decode it later (after the stream is done and the bytes are on the host)
+ * with tn_result_decode. */
+#define TN_RAW_BYTES 128
+int tn_contract_async(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *primes, int32_t nprimes,
+                      void *d_workspace, size_t ws_bytes, void *cuda_stream, void *d_raw);
+int tn_result_decode(tn_semiring_t semiring, const uint32_t *primes, int32_t nprimes,
+                     const void *h_raw, tn_result_t *out);
+
+/* One pairwise contraction (Sec. 4.1) on caller device tensors, with the
+ * layout conventions above:
+ *   C[c] = (+)_{s} A[a(c, s)] (x) B[b(c, s)]
+ * where c runs over assignments of the labels LC (every label of LC must be
+ * in LA or LB) and s over assignments of the labels of LA u LB not in LC.
+ * Ranks ra, rb, rc <= 30.  For TN_COUNT_MODP every prime is processed (the
+ * buffers hold nprimes prime-major blocks).  A, B and C must not overlap.
+ * Enqueued on cuda_stream; does not wait.  Uses no workspace. */
+int tn_contract_pair(tn_semiring_t semiring, const uint32_t *primes, int32_t nprimes,
+                     const void *d_a, const int32_t *la, int32_t ra,
+                     const void *d_b, const int32_t *lb, int32_t rb,
+                     const int32_t *lc, int32_t rc, void *d_c, void *cuda_stream);
+
+/* Serving (continuous batching).  A server owns a worker thread, a CUDA
+ * stream pool and an HBM budget; tn_submit admits a request once the peak
+ * workspace of its plan fits in the free part of the budget and fewer than
+ * max_inflight requests run, and returns a ticket at once.  tn_poll returns
+ * TN_EAGAIN until the ticket's result is ready, then TN_OK (the result is
+ * handed out once).  The plan must outlive its request. */
+int tn_server_create(size_t hbm_budget_bytes, int32_t max_inflight, tn_server_t *out);
+int tn_submit(tn_server_t server, tn_plan_t plan, tn_semiring_t semiring, const uint32_t *primes,
+              int32_t nprimes, uint64_t *ticket);
+int tn_poll(tn_server_t server, uint64_t ticket, tn_result_t *out);
+
+void tn_plan_destroy(tn_plan_t plan);
+void tn_server_destroy(tn_server_t server);
+const char *tn_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TN_H */

@@ -1,0 +1,192 @@
+// semiring.cuh -- device element types of libtn (Table 1, Secs. 5.2-5.3 of
+// arXiv:2501.00227) and operand access for the step kernels.
+//
+//   SrF32  tropical (max,+) in float; zero = -inf, one = 0 (Sec. 5.2)
+//   SrI32  tropical (max,+) in int32; "-inf" is kNegInf = -2^30 and every
+//          accumulation starts there, so sums of two stored values stay
+//          >= -2^31 and never wrap
+//   SrCnt  counting tropical (CountingMax, Sec. 5.3): (max in int32, count in
+//          uint64); (a,c)(x)(b,d) = (a+b, c*d); (+) keeps the larger max and
+//          adds counts on a tie; counts saturate at 2^64-1
+//   SrMod  ordinary (+,*) modulo a prime p < 2^31 (the count of all
+//          independent sets, Z at beta = 0, one residue per prime)
+#pragma once
+
+#include <cstdint>
+
+#include "tn_internal.h"
+
+namespace tn {
+namespace dev {
+
+constexpr int32_t kNegInf = TN_I32_NEG_INF;
+
+// One operand of a step: an array in device memory or a leaf generated on
+// the fly (its entry index is the only input).
+struct Operand {
+  int32_t kind;          // OperandKind
+  int32_t pad_;
+  const void* p0;        // float / int32 values, or residues of prime 0
+  const void* p1;        // uint64 counts (counting semiring)
+  int64_t prime_stride;  // entries between consecutive prime blocks
+};
+
+struct Output {
+  void* p0;
+  void* p1;
+  int64_t prime_stride;
+};
+
+// Constants of one modulus p (2 <= p < 2^31):
+//   r32 = 2^32 mod p   (folds the high word of a 64-bit accumulator)
+//   mu  = floor((2^64 - 1) / p)   (Barrett 1986 reciprocal)
+struct ModParams {
+  uint32_t p, r32;
+  uint64_t mu;
+};
+
+struct ModTable {
+  ModParams q[TN_MAX_PRIMES];
+};
+
+// ---------------------------------------------------------------- float
+struct SrF32 {
+  using Val = float;
+  using Acc = float;
+  static __device__ __forceinline__ Acc zero(const ModParams&) { return -__int_as_float(0x7f800000); }
+  static __device__ __forceinline__ Val leaf(int32_t kind, int64_t e) {
+    if (kind == kOpEdge) return e == 3 ? -__int_as_float(0x7f800000) : 0.0f;
+    if (kind == kOpVertex) return e == 1 ? 1.0f : 0.0f;
+    return 0.0f;
+  }
+  static __device__ __forceinline__ Val load(const Operand& o, int64_t e, int) {
+    if (o.kind != kOpArena) return leaf(o.kind, e);
+    return static_cast<const float*>(o.p0)[e];
+  }
+  static __device__ __forceinline__ void mac(Acc& acc, Val a, Val b, const ModParams&) {
+    acc = fmaxf(acc, a + b);
+  }
+  static __device__ __forceinline__ void merge(Acc& acc, const Acc& o, const ModParams&) {
+    acc = fmaxf(acc, o);
+  }
+  static __device__ __forceinline__ void store(const Output& o, int64_t e, int, const Acc& acc,
+                                               const ModParams&) {
+    static_cast<float*>(o.p0)[e] = acc;
+  }
+};
+
+// ---------------------------------------------------------------- int32
+struct SrI32 {
+  using Val = int32_t;
+  using Acc = int32_t;
+  static __device__ __forceinline__ Acc zero(const ModParams&) { return kNegInf; }
+  static __device__ __forceinline__ Val leaf(int32_t kind, int64_t e) {
+    if (kind == kOpEdge) return e == 3 ? kNegInf : 0;
+    if (kind == kOpVertex) return e == 1 ? 1 : 0;
+    return 0;
+  }
+  static __device__ __forceinline__ Val load(const Operand& o, int64_t e, int) {
+    if (o.kind != kOpArena) return leaf(o.kind, e);
+    return static_cast<const int32_t*>(o.p0)[e];
+  }
+  static __device__ __forceinline__ void mac(Acc& acc, Val a, Val b, const ModParams&) {
+    acc = __viaddmax_s32(a, b, acc);  // max(a + b, acc)
+  }
+  static __device__ __forceinline__ void merge(Acc& acc, const Acc& o, const ModParams&) {
+    acc = max(acc, o);
+  }
+  static __device__ __forceinline__ void store(const Output& o, int64_t e, int, const Acc& acc,
+                                               const ModParams&) {
+    static_cast<int32_t*>(o.p0)[e] = acc;
+  }
+};
+
+// ---------------------------------------------------------------- counting
+__device__ __forceinline__ uint64_t sat_mul_u64(uint64_t a, uint64_t b) {
+  return __umul64hi(a, b) ? ~0ull : a * b;
+}
+__device__ __forceinline__ uint64_t sat_add_u64(uint64_t a, uint64_t b) {
+  uint64_t s = a + b;
+  return s < a ? ~0ull : s;
+}
+
+struct CntVal {
+  int32_t v;
+  uint64_t c;
+};
+
+struct SrCnt {
+  using Val = CntVal;
+  using Acc = CntVal;
+  static __device__ __forceinline__ Acc zero(const ModParams&) { return CntVal{kNegInf, 0ull}; }
+  static __device__ __forceinline__ Val leaf(int32_t kind, int64_t e) {
+    if (kind == kOpEdge) return e == 3 ? CntVal{kNegInf, 0ull} : CntVal{0, 1ull};
+    if (kind == kOpVertex) return e == 1 ? CntVal{1, 1ull} : CntVal{0, 1ull};
+    return CntVal{0, 1ull};
+  }
+  static __device__ __forceinline__ Val load(const Operand& o, int64_t e, int) {
+    if (o.kind != kOpArena) return leaf(o.kind, e);
+    return CntVal{static_cast<const int32_t*>(o.p0)[e], static_cast<const uint64_t*>(o.p1)[e]};
+  }
+  static __device__ __forceinline__ void mac(Acc& acc, const Val& a, const Val& b, const ModParams&) {
+    int32_t s = a.v + b.v;
+    if (s > acc.v) {
+      acc.v = s;
+      acc.c = sat_mul_u64(a.c, b.c);
+    } else if (s == acc.v) {
+      acc.c = sat_add_u64(acc.c, sat_mul_u64(a.c, b.c));
+    }
+  }
+  static __device__ __forceinline__ void merge(Acc& acc, const Acc& o, const ModParams&) {
+    if (o.v > acc.v) acc = o;
+    else if (o.v == acc.v) acc.c = sat_add_u64(acc.c, o.c);
+  }
+  static __device__ __forceinline__ void store(const Output& o, int64_t e, int, const Acc& acc,
+                                               const ModParams&) {
+    static_cast<int32_t*>(o.p0)[e] = acc.v;
+    static_cast<uint64_t*>(o.p1)[e] = acc.c;
+  }
+};
+
+// ---------------------------------------------------------------- mod p
+// Accumulation: acc (64-bit) += a*b with a, b < p < 2^31, so a*b < 2^62.
+// After every product the high word is folded back, acc <- hi * r32 + lo
+// (2^32 = r32 mod p); this keeps acc < 2^63 + 2^32 and the sum below 2^64.
+// The final residue is a Barrett reduction (Barrett 1986) of the 64-bit acc.
+__device__ __forceinline__ uint64_t fold32(uint64_t x, uint32_t r32) {
+  return static_cast<uint64_t>(static_cast<uint32_t>(x >> 32)) * r32 + static_cast<uint32_t>(x);
+}
+__device__ __forceinline__ uint32_t barrett64(uint64_t x, const ModParams& mp) {
+  // q = floor(x * mu / 2^64) is floor(x / p) or one less.
+  uint64_t q = __umul64hi(x, mp.mu);
+  uint64_t r = x - q * mp.p;
+  return static_cast<uint32_t>(r >= mp.p ? r - mp.p : r);
+}
+
+struct SrMod {
+  using Val = uint32_t;
+  using Acc = uint64_t;
+  static __device__ __forceinline__ Acc zero(const ModParams&) { return 0ull; }
+  static __device__ __forceinline__ Val leaf(int32_t kind, int64_t e) {
+    // beta = 0: every allowed configuration weighs 1, a forbidden one 0
+    if (kind == kOpEdge) return e == 3 ? 0u : 1u;
+    return 1u;
+  }
+  static __device__ __forceinline__ Val load(const Operand& o, int64_t e, int q) {
+    if (o.kind != kOpArena) return leaf(o.kind, e);
+    return static_cast<const uint32_t*>(o.p0)[q * o.prime_stride + e];
+  }
+  static __device__ __forceinline__ void mac(Acc& acc, Val a, Val b, const ModParams& mp) {
+    acc = fold32(acc + static_cast<uint64_t>(a) * b, mp.r32);
+  }
+  static __device__ __forceinline__ void merge(Acc& acc, const Acc& o, const ModParams& mp) {
+    acc = static_cast<uint64_t>(barrett64(acc, mp)) + barrett64(o, mp);  // < 2p
+  }
+  static __device__ __forceinline__ void store(const Output& o, int64_t e, int q, const Acc& acc,
+                                               const ModParams& mp) {
+    static_cast<uint32_t*>(o.p0)[q * o.prime_stride + e] = barrett64(acc, mp);
+  }
+};
+
+}  // namespace dev
+}  // namespace tn

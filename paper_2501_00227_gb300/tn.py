@@ -1,0 +1,290 @@
+"""Python binding of libtn (include/tn.h): argument marshalling only.
+
+Every function named ``tn_*`` here calls the C entry point of the same name.
+All arithmetic of a contraction runs in libtn's CUDA kernels; this module
+only converts NumPy / PyTorch objects into pointers and sizes.  PyTorch is
+used for device memory (workspaces) and streams.
+
+If ``_build/libtn.so`` is missing the first call raises ``TNError``: there is
+no fallback path.  Run ``paper_2501_00227_gb300.build.build()`` (or
+``__graft_entry__.build()``) first.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+TN_OK, TN_EINVAL, TN_ENOMEM, TN_EOVERFLOW, TN_ETIMEOUT, TN_EAGAIN, TN_ECUDA = 0, -1, -2, -3, -4, -5, -6
+TN_TROPICAL_F32, TN_TROPICAL_I32, TN_COUNTING_TROPICAL, TN_COUNT_MODP = 1, 2, 3, 4
+TN_I32_NEG_INF = -(1 << 30)
+TN_MAX_PRIMES = 16
+TN_RAW_BYTES = 128
+
+SEMIRINGS = {"tropical_f32": TN_TROPICAL_F32, "tropical_i32": TN_TROPICAL_I32,
+             "counting": TN_COUNTING_TROPICAL, "modp": TN_COUNT_MODP}
+
+#: the eight largest primes below 2^31
+PRIMES31 = (2147483647, 2147483629, 2147483587, 2147483579,
+            2147483563, 2147483549, 2147483543, 2147483497)
+
+
+class tn_plan_info_t(ctypes.Structure):
+    _fields_ = [("log2_tc", ctypes.c_double), ("log2_sc", ctypes.c_double), ("log2_rwc", ctypes.c_double),
+                ("tc", ctypes.c_uint64), ("sc_elems", ctypes.c_uint64), ("rwc", ctypes.c_uint64),
+                ("peak_bytes", ctypes.c_uint64 * 4), ("nsteps", ctypes.c_int32),
+                ("nlaunch_steps", ctypes.c_int32)]
+
+
+class tn_result_t(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("max_i32", ctypes.c_int32), ("max_f32", ctypes.c_float),
+                ("count", ctypes.c_uint64), ("nprimes", ctypes.c_int32),
+                ("primes", ctypes.c_uint32 * TN_MAX_PRIMES), ("residues", ctypes.c_uint32 * TN_MAX_PRIMES),
+                ("crt_nlimbs", ctypes.c_int32), ("crt_limbs", ctypes.c_uint32 * 32)]
+
+
+class TNError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {tn_strerror(code)} ({code})" if what else f"{code}")
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libtn.so (built in-tree); raise if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise TNError(TN_EINVAL, f"libtn.so not built at {path}; run paper_2501_00227_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        vp, i32, u32, u64, i32p, u32p = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64,
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint32))
+        L.tn_plan.argtypes = [i32, i32p, i32, i32p, i32, ctypes.POINTER(vp)]
+        L.tn_order_greedy.argtypes = [i32, i32p, i32, ctypes.c_double, i32, u64, i32p]
+        L.tn_plan_info.argtypes = [vp, ctypes.c_int, i32, ctypes.POINTER(tn_plan_info_t)]
+        L.tn_contract.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.c_size_t, vp, ctypes.POINTER(tn_result_t)]
+        L.tn_contract_async.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.c_size_t, vp, vp]
+        L.tn_result_decode.argtypes = [ctypes.c_int, u32p, i32, vp, ctypes.POINTER(tn_result_t)]
+        L.tn_contract_pair.argtypes = [ctypes.c_int, u32p, i32, vp, i32p, i32, vp, i32p, i32, i32p, i32, vp, vp]
+        L.tn_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
+        L.tn_submit.argtypes = [vp, vp, ctypes.c_int, u32p, i32, ctypes.POINTER(u64)]
+        L.tn_poll.argtypes = [vp, u64, ctypes.POINTER(tn_result_t)]
+        L.tn_plan_destroy.argtypes = [vp]
+        L.tn_server_destroy.argtypes = [vp]
+        L.tn_strerror.argtypes = [ctypes.c_int]
+        L.tn_strerror.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def declared_symbols() -> list[str]:
+    """Names of every function include/tn.h declares."""
+    hdr = os.path.join(_build.INCLUDE, "tn.h")
+    with open(hdr) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tn_[a-z_]+)\s*\(", text)))
+
+
+# --------------------------------------------------------------------- helpers
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _p32(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _primes(primes):
+    if primes is None:
+        return None, 0
+    pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint32))
+    return pr, int(pr.size)
+
+
+def _u32p(pr):
+    return None if pr is None else pr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+
+
+def _check(rc, what):
+    if rc != TN_OK:
+        raise TNError(rc, what)
+
+
+def _sr(semiring):
+    return SEMIRINGS[semiring] if isinstance(semiring, str) else int(semiring)
+
+
+def result_dict(r: tn_result_t, semiring) -> dict:
+    s = _sr(semiring)
+    out = {"status": int(r.status)}
+    if s in (TN_TROPICAL_F32, TN_TROPICAL_I32, TN_COUNTING_TROPICAL):
+        out["max"] = None if r.max_i32 == -(2 ** 31) else int(r.max_i32)
+        out["max_f32"] = float(r.max_f32)
+    if s == TN_COUNTING_TROPICAL:
+        out["count"] = int(r.count)
+    if s == TN_COUNT_MODP:
+        k = int(r.nprimes)
+        out["primes"] = [int(x) for x in r.primes[:k]]
+        out["residues"] = [int(x) for x in r.residues[:k]]
+        x = 0
+        for i in range(int(r.crt_nlimbs)):
+            x |= int(r.crt_limbs[i]) << (32 * i)
+        M = 1
+        for p in out["primes"]:
+            M *= p
+        out["crt"], out["modulus"] = x, M
+    return out
+
+
+# --------------------------------------------------------------------- C ABI
+
+def tn_strerror(code: int) -> str:
+    return lib().tn_strerror(int(code)).decode()
+
+
+def tn_order_greedy(n, edges, alpha: float = 0.0, nrepeat: int = 10, seed: int = 0) -> np.ndarray:
+    e = _i32(edges).reshape(-1, 2)
+    m = e.shape[0]
+    out = np.zeros((max(n + m - 1, 0), 2), dtype=np.int32)
+    _check(lib().tn_order_greedy(int(n), _p32(e), m, float(alpha), int(nrepeat), int(seed) & (2 ** 64 - 1),
+                                 _p32(out)), "tn_order_greedy")
+    return out
+
+
+def tn_plan(n, edges, order) -> int:
+    e = _i32(edges).reshape(-1, 2)
+    o = _i32(order).reshape(-1, 2)
+    h = ctypes.c_void_p()
+    _check(lib().tn_plan(int(n), _p32(e), e.shape[0], _p32(o), o.shape[0], ctypes.byref(h)), "tn_plan")
+    return h.value
+
+
+def tn_plan_info(plan, semiring=TN_TROPICAL_I32, nprimes: int = 1) -> dict:
+    info = tn_plan_info_t()
+    _check(lib().tn_plan_info(plan, _sr(semiring), int(nprimes), ctypes.byref(info)), "tn_plan_info")
+    return {"log2_tc": info.log2_tc, "log2_sc": info.log2_sc, "log2_rwc": info.log2_rwc,
+            "tc": int(info.tc), "sc": int(info.sc_elems), "rwc": int(info.rwc),
+            "peak_bytes": [int(x) for x in info.peak_bytes], "nsteps": int(info.nsteps),
+            "nlaunch_steps": int(info.nlaunch_steps)}
+
+
+def tn_plan_destroy(plan):
+    if plan:
+        lib().tn_plan_destroy(plan)
+
+
+def tn_contract(plan, semiring, primes, ws_ptr: int, ws_bytes: int, stream: int) -> dict:
+    pr, k = _primes(primes)
+    r = tn_result_t()
+    _check(lib().tn_contract(plan, _sr(semiring), _u32p(pr), k, ctypes.c_void_p(ws_ptr), ws_bytes,
+                             ctypes.c_void_p(stream), ctypes.byref(r)), "tn_contract")
+    return result_dict(r, semiring)
+
+
+def tn_contract_async(plan, semiring, primes, ws_ptr: int, ws_bytes: int, stream: int, raw_ptr: int):
+    pr, k = _primes(primes)
+    _check(lib().tn_contract_async(plan, _sr(semiring), _u32p(pr), k, ctypes.c_void_p(ws_ptr), ws_bytes,
+                                   ctypes.c_void_p(stream), ctypes.c_void_p(raw_ptr)), "tn_contract_async")
+
+
+def tn_result_decode(semiring, primes, raw: bytes) -> dict:
+    pr, k = _primes(primes)
+    buf = ctypes.create_string_buffer(bytes(raw), TN_RAW_BYTES)
+    r = tn_result_t()
+    _check(lib().tn_result_decode(_sr(semiring), _u32p(pr), k, ctypes.cast(buf, ctypes.c_void_p),
+                                  ctypes.byref(r)), "tn_result_decode")
+    return result_dict(r, semiring)
+
+
+def tn_contract_pair(semiring, primes, a_ptr, la, b_ptr, lb, lc, c_ptr, stream: int):
+    pr, k = _primes(primes)
+    la, lb, lc = _i32(la).reshape(-1), _i32(lb).reshape(-1), _i32(lc).reshape(-1)
+    _check(lib().tn_contract_pair(_sr(semiring), _u32p(pr), k, ctypes.c_void_p(a_ptr), _p32(la), la.size,
+                                  ctypes.c_void_p(b_ptr), _p32(lb), lb.size, _p32(lc), lc.size,
+                                  ctypes.c_void_p(c_ptr), ctypes.c_void_p(stream)), "tn_contract_pair")
+
+
+def tn_server_create(hbm_budget_bytes: int, max_inflight: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().tn_server_create(int(hbm_budget_bytes), int(max_inflight), ctypes.byref(h)), "tn_server_create")
+    return h.value
+
+
+def tn_submit(server, plan, semiring, primes=None) -> int:
+    pr, k = _primes(primes)
+    t = ctypes.c_uint64()
+    _check(lib().tn_submit(server, plan, _sr(semiring), _u32p(pr), k, ctypes.byref(t)), "tn_submit")
+    return int(t.value)
+
+
+def tn_poll(server, ticket: int, semiring):
+    """Result dict once ready, None while TN_EAGAIN."""
+    r = tn_result_t()
+    rc = lib().tn_poll(server, int(ticket), ctypes.byref(r))
+    if rc == TN_EAGAIN:
+        return None
+    _check(rc, "tn_poll")
+    return result_dict(r, semiring)
+
+
+def tn_server_destroy(server):
+    if server:
+        lib().tn_server_destroy(server)
+
+
+# --------------------------------------------------------------------- objects
+
+class Plan:
+    """A contraction plan (graph + order) owning its libtn handle."""
+
+    def __init__(self, n, edges, order=None, *, nrepeat: int = 10, seed: int = 0, alpha: float = 0.0):
+        self.n = int(n)
+        self.edges = _i32(edges).reshape(-1, 2)
+        self.order = (tn_order_greedy(n, self.edges, alpha, nrepeat, seed) if order is None
+                      else _i32(order).reshape(-1, 2))
+        self.handle = tn_plan(self.n, self.edges, self.order)
+
+    def info(self, semiring=TN_TROPICAL_I32, nprimes: int = 1) -> dict:
+        return tn_plan_info(self.handle, semiring, nprimes)
+
+    def workspace_bytes(self, semiring, nprimes: int = 1) -> int:
+        return self.info(semiring, nprimes)["peak_bytes"][_sr(semiring) - 1]
+
+    def contract(self, semiring, primes=None, workspace=None, stream=None) -> dict:
+        """Contract on the current CUDA device; allocates a torch workspace if none is given."""
+        import torch
+        nprimes = 0 if primes is None else len(primes)
+        need = self.workspace_bytes(semiring, max(nprimes, 1))
+        if workspace is None:
+            workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        return tn_contract(self.handle, semiring, primes, workspace.data_ptr(), workspace.numel(),
+                           st.cuda_stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tn_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
