@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark: semiring contraction of the independent-set tensor network.
+
+Workload (one "step"): random 3-regular graphs n = 100 and n = 140 (seeds
+1, 2, 3 each; configuration model), each contracted along its greedy order in
+three element types -- tropical int32 (MIS size), counting tropical (MIS
+size and count) and ordinary (+,*) modulo three 31-bit primes (the count of
+all independent sets, recombined by CRT).  Orders and plans are built on the
+host before timing (reported separately as plan_ms).
+
+Metric: semiring-contraction Gop/s = sum over contractions of tc (Sec. 4.1:
+2^{|LA u LB|} multiply-adds per pairwise step; once per prime for mod p)
+divided by device time.  L2 is flushed (a 256 MiB write) before every timed
+step, outside the timed events.
+
+--impl reference times the CPU oracle (plain C loops, all host cores) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import graphgen  # noqa: E402
+
+PRIMES3 = (2147483647, 2147483629, 2147483587)
+GRAPHS = [("reg3", 100, s) for s in (1, 2, 3)] + [("reg3", 140, s) for s in (1, 2, 3)]
+SEMIRINGS = [("tropical_i32", None), ("counting", None), ("modp", PRIMES3)]
+METRIC = "semiring-contraction Gop/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["tn", "reference"], default="tn")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# Instruction-issue peaks of the 152-SM GB300 used as roofline denominators
+# (see the kernel table in the design notes): one (max,+) multiply-add is one
+# VIADDMNMX, issued at 64 per clock per SM (measured by a register-only
+# microbenchmark of __viaddmax_s32: 19.9 Tops/s at 2.07 GHz).
+SMS = 152
+MAXPLUS_PER_CLK_SM = 64
+
+
+def cpu_reference(sample_graphs, threads: int):
+    """Times the CPU oracle on the given graphs in every element type."""
+    import oracle
+    oracle.build()
+    used = oracle.set_threads(threads)
+    ops, secs = 0, 0.0
+    for kind, n, seed in sample_graphs:
+        nn, e = graphgen.random_regular3(n, seed)
+        order = oracle.greedy_order(nn, e, nrepeat=4, seed=1)
+        tc = oracle.complexity(nn, e, order)[0]
+        t = time.perf_counter()
+        oracle.mis_size(nn, e, order)
+        oracle.mis_count(nn, e, order)
+        oracle.count_modp(nn, e, order, PRIMES3)
+        secs += time.perf_counter() - t
+        ops += tc * (2 + len(PRIMES3))
+    return ops, secs, used
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    sample = [("reg3", 140, 1)]
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        cpu_reference(sample, threads)
+    ops = secs = 0.0
+    used = threads
+    for _ in range(args.steps):
+        o, s, used = cpu_reference(sample, threads)
+        ops += o
+        secs += s
+    val = ops / secs / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gop/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": "random 3-regular n=140 seed 1 (bounded sample of the n=100/140 workload)",
+                       "semirings": ["tropical", "counting", "mod 3 primes"], "order": "oracle greedy"},
+            "cpu_baseline": {"value": val, "unit": "Gop/s", "cores": used, "kind": "oracle",
+                             "sample": "reg3 n=140 seed 1, tropical + counting + 3 primes, per step"},
+            "e2e": {"value": val, "unit": "Gop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_tn(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2501_00227_gb300 import build as B
+    from paper_2501_00227_gb300 import tn
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+
+    # ---- plans (host; not timed in the metric)
+    t0 = time.perf_counter()
+    plans = []
+    for kind, n, seed in GRAPHS:
+        nn, e = graphgen.random_regular3(n, seed)
+        plans.append(tn.Plan(nn, e, nrepeat=10, seed=1))
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    jobs = []          # (plan, semiring, primes, ops)
+    for p in plans:
+        info = p.info(tn.TN_COUNT_MODP, len(PRIMES3))
+        for sr, pr in SEMIRINGS:
+            jobs.append((p, sr, pr, info["tc"] * (len(pr) if pr else 1), info["nsteps"]))
+    ops_per_step = sum(j[3] for j in jobs)
+    ws_bytes = max(p.workspace_bytes(sr, len(pr) if pr else 1) for p, sr, pr, _, _ in jobs)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    raw = torch.zeros(len(jobs) * tn.TN_RAW_BYTES, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+
+    def one_step():
+        for i, (p, sr, pr, _, _) in enumerate(jobs):
+            tn.tn_contract_async(p.handle, sr, pr, ws.data_ptr(), ws_bytes, sptr,
+                                 raw.data_ptr() + i * tn.TN_RAW_BYTES)
+
+    def check(raw_host, ref=None):
+        out = []
+        for i, (p, sr, pr, _, _) in enumerate(jobs):
+            r = tn.tn_result_decode(sr, pr, bytes(raw_host[i * tn.TN_RAW_BYTES:(i + 1) * tn.TN_RAW_BYTES]))
+            out.append(json.dumps(r, sort_keys=True))
+        if ref is not None and out != ref:
+            raise RuntimeError("results changed between steps")
+        return out
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        one_step()
+    torch.cuda.synchronize()
+    ref = check(raw.cpu().numpy())
+
+    # ---- timed region: K steps, device time between events, L2 flushed before each
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            one_step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    check(raw.cpu().numpy(), ref)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * ops_per_step * args.steps / (total_ms * 1e-3) / 1e9
+
+    # ---- end to end through the public API: synchronous tn_contract calls
+    # (plan from host edge list + order, launch, result read back to the host)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        for p, sr, pr, _, _ in jobs:
+            h = tn.tn_plan(p.n, p.edges, p.order)
+            tn.tn_contract(h, sr, pr, ws.data_ptr(), ws_bytes, sptr)
+            tn.tn_plan_destroy(h)
+    e2e_s = time.perf_counter() - t
+    e2e_val = ops_per_step * e2e_steps / e2e_s / 1e9
+    launch_bytes = sum(nsteps * 400 for _, _, _, _, nsteps in jobs)   # step descriptors as launch parameters
+
+    # ---- per-kernel attribution (CUDA events around every step's kernels)
+    per = {}
+    for p, sr, pr, _, nsteps in jobs:
+        r, ms, kern, ops = tn.tn_contract_timed(p.handle, sr, pr, ws.data_ptr(), ws_bytes, sptr, nsteps)
+        mult = len(pr) if pr else 1
+        for k_id, t_ms, o in zip(kern, ms, ops):
+            key = (sr, int(k_id))
+            a = per.setdefault(key, [0.0, 0, 0])
+            a[0] += float(t_ms)
+            a[1] += int(o) * mult
+            a[2] += 1
+    dom = max(per.items(), key=lambda kv: kv[1][0])
+    (dom_sr, dom_k), (dom_ms, dom_ops, dom_n) = dom
+    kname = {0: "k_step_naive", 1: "k_step_tiled"}[dom_k]
+    csum = clk.summary()
+    clock_mhz = csum["sm_max_mhz"] or 2070.0
+    peak_ops = SMS * MAXPLUS_PER_CLK_SM * clock_mhz * 1e6 / 1e12   # Tops/s
+    achieved = dom_ops / (dom_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": f"{kname}<{dom_sr}>", "achieved": achieved, "peak": peak_ops,
+                "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": None,
+                "peak_basis": f"{SMS} SMs x {MAXPLUS_PER_CLK_SM} (max,+)/clk/SM x {clock_mhz:.0f} MHz",
+                "time_share": dom_ms / sum(v[0] for v in per.values()), "launches": dom_n}
+
+    line = {"metric": METRIC, "value": value, "unit": "Gop/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32/uint64", "data": "synthetic",
+            "config": {"workload": "random 3-regular n=100 and n=140, seeds 1-3, greedy order (nrepeat 10)",
+                       "semirings": ["tropical_i32", "counting(int32,uint64)", "modp x3 (31-bit) + CRT"],
+                       "ops_per_step": ops_per_step, "contractions_per_step": len(jobs),
+                       "l2": "flushed (256 MiB write) before each timed step", "plan_ms": plan_ms},
+            "e2e": {"value": e2e_val, "unit": "Gop/s", "h2d_bytes_per_step": launch_bytes,
+                    "d2h_bytes_per_step": tn.TN_RAW_BYTES * len(jobs)},
+            "gpu_launches": None, "roofline": roofline, "clocks": csum}
+    # kernel launches per step: every step of every job is one launch, plus a finalize
+    line["gpu_launches"] = args.steps * sum(nsteps + 1 for _, _, _, _, nsteps in jobs)
+    if rank == 0 and not args.no_cpu_baseline:
+        ops, secs, used = cpu_reference([("reg3", 140, 1), ("reg3", 140, 2)], os.cpu_count() or 1)
+        line["cpu_baseline"] = {"value": ops / secs / 1e9, "unit": "Gop/s", "cores": used, "kind": "oracle",
+                                "sample": "reg3 n=140 seeds 1-2 (oracle greedy order), tropical + counting + "
+                                          f"3 primes, {secs:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line))
+    for p in plans:
+        p.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_tn(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -157,6 +157,16 @@ int tn_contract_async(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *pr
 int tn_result_decode(tn_semiring_t semiring, const uint32_t *primes, int32_t nprimes,
                      const void *h_raw, tn_result_t *out);
 
+/* As tn_contract, and also times every step: a CUDA event pair is recorded
+ * on the stream around each step's kernels; after the contraction the call
+ * waits and writes, for step i, step_ms[i] (milliseconds) and step_kernel[i]
+ * (0 = general kernel, 1 = tiled kernel) and step_ops[i] (= 2^{|LA u LB|},
+ * semiring multiply-adds per prime).  Arrays hold tn_plan_info().nsteps
+ * entries; any of them may be NULL. */
+int tn_contract_timed(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *primes, int32_t nprimes,
+                      void *d_workspace, size_t ws_bytes, void *cuda_stream, tn_result_t *out,
+                      float *step_ms, int32_t *step_kernel, uint64_t *step_ops);
+
 /* One pairwise contraction (Sec. 4.1) on caller device tensors, with the
  * layout conventions above:
  *   C[c] = (+)_{s} A[a(c, s)] (x) B[b(c, s)]

@@ -91,19 +91,28 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? TN_OK : TN_ECUDA; }
 }  // namespace
 
 int contract_enqueue(const tn_plan_s* p, tn_semiring_t s, const ModTable& mods, int32_t nprimes,
-                     void* ws, cudaStream_t st, void* d_raw) {
+                     void* ws, cudaStream_t st, void* d_raw, cudaEvent_t* step_events) {
   Regions rg = regions(p, s, ws);
   uint32_t* d_status = static_cast<uint32_t*>(ws);
   int rc = cuda_rc(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st));
   if (rc) return rc;
   const int np = s == TN_COUNT_MODP ? nprimes : 1;
-  for (const Step& step : p->steps) {
+  for (size_t i = 0; i < p->steps.size(); ++i) {
+    const Step& step = p->steps[i];
+    if (step_events) {
+      rc = cuda_rc(cudaEventRecord(step_events[2 * i], st));
+      if (rc) return rc;
+    }
     Operand A = operand_of(p, rg, step.a_id);
     Operand B = operand_of(p, rg, step.b_id);
     Operand Cin = operand_of(p, rg, step.c_id);
     Output C{const_cast<void*>(Cin.p0), const_cast<void*>(Cin.p1), Cin.prime_stride};
     rc = dev::launch_step_naive(s, step.g, A, B, C, mods, np, st);
     if (rc) return rc;
+    if (step_events) {
+      rc = cuda_rc(cudaEventRecord(step_events[2 * i + 1], st));
+      if (rc) return rc;
+    }
   }
   return dev::launch_finalize(s, operand_of(p, rg, p->root), np, d_status, d_raw, st);
 }
@@ -207,7 +216,7 @@ int tn_contract_async(tn_plan_t plan, tn_semiring_t semiring, const uint32_t* pr
   if (rc) return rc;
   if (ws_bytes < workspace_bytes(plan, semiring, nprimes)) return TN_ENOMEM;
   return contract_enqueue(plan, semiring, mods, nprimes, d_workspace,
-                          static_cast<cudaStream_t>(cuda_stream), d_raw);
+                          static_cast<cudaStream_t>(cuda_stream), d_raw, nullptr);
 }
 
 int tn_result_decode(tn_semiring_t semiring, const uint32_t* primes, int32_t nprimes,
@@ -233,6 +242,38 @@ int tn_contract(tn_plan_t plan, tn_semiring_t semiring, const uint32_t* primes, 
   rc = cuda_rc(cudaStreamSynchronize(st));
   if (rc) return rc;
   return tn_result_decode(semiring, primes, nprimes, raw, out);
+}
+
+int tn_contract_timed(tn_plan_t plan, tn_semiring_t semiring, const uint32_t* primes,
+                      int32_t nprimes, void* d_workspace, size_t ws_bytes, void* cuda_stream,
+                      tn_result_t* out, float* step_ms, int32_t* step_kernel, uint64_t* step_ops) {
+  if (!plan || !out || !semiring_ok(semiring) || !d_workspace) return TN_EINVAL;
+  if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0) return TN_EINVAL;
+  ModTable mods;
+  int rc = make_mods(semiring, primes, nprimes, &mods);
+  if (rc) return rc;
+  if (ws_bytes < workspace_bytes(plan, semiring, nprimes)) return TN_ENOMEM;
+  const size_t ns = plan->steps.size();
+  std::vector<cudaEvent_t> ev(2 * ns, nullptr);
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) { rc = TN_ECUDA; break; }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  void* d_raw = static_cast<char*>(d_workspace) + 64;
+  unsigned char raw[TN_RAW_BYTES];
+  if (!rc) rc = contract_enqueue(plan, semiring, mods, nprimes, d_workspace, st, d_raw, ev.data());
+  if (!rc) rc = cuda_rc(cudaMemcpyAsync(raw, d_raw, TN_RAW_BYTES, cudaMemcpyDeviceToHost, st));
+  if (!rc) rc = cuda_rc(cudaStreamSynchronize(st));
+  for (size_t i = 0; i < ns && !rc; ++i) {
+    float ms = 0.f;
+    if (step_ms) rc = cuda_rc(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+    if (step_ms) step_ms[i] = ms;
+    if (step_kernel) step_kernel[i] = plan->steps[i].kernel;
+    if (step_ops) step_ops[i] = plan->steps[i].ops;
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (rc) return rc;
+  return decode_raw(semiring, mods, nprimes, raw, out);
 }
 
 int tn_contract_pair(tn_semiring_t semiring, const uint32_t* primes, int32_t nprimes,

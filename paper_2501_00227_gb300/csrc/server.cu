@@ -27,7 +27,8 @@
 
 namespace tn {
 int contract_enqueue(const tn_plan_s* p, tn_semiring_t s, const dev::ModTable& mods,
-                     int32_t nprimes, void* ws, cudaStream_t st, void* d_raw);
+                     int32_t nprimes, void* ws, cudaStream_t st, void* d_raw,
+                     cudaEvent_t* step_events);
 int decode_raw(tn_semiring_t s, const dev::ModTable& mods, int32_t nprimes,
                const unsigned char* raw, tn_result_t* out);
 }  // namespace tn
@@ -106,7 +107,7 @@ void worker_loop(tn_server_s* S) {
       int rc = cudaMallocAsync(&ws, r.bytes, sl.stream) == cudaSuccess ? TN_OK : TN_ENOMEM;
       if (rc == TN_OK)
         rc = tn::contract_enqueue(r.plan, r.semiring, mods, static_cast<int32_t>(r.primes.size()),
-                                  ws, sl.stream, static_cast<char*>(ws) + 64);
+                                  ws, sl.stream, static_cast<char*>(ws) + 64, nullptr);
       if (rc == TN_OK)
         rc = cudaMemcpyAsync(sl.h_raw, static_cast<char*>(ws) + 64, TN_RAW_BYTES,
                              cudaMemcpyDeviceToHost, sl.stream) == cudaSuccess ? TN_OK : TN_ECUDA;

@@ -79,6 +79,9 @@ def lib():
         L.tn_plan_info.argtypes = [vp, ctypes.c_int, i32, ctypes.POINTER(tn_plan_info_t)]
         L.tn_contract.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.c_size_t, vp, ctypes.POINTER(tn_result_t)]
         L.tn_contract_async.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.c_size_t, vp, vp]
+        L.tn_contract_timed.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.c_size_t, vp,
+                                        ctypes.POINTER(tn_result_t), ctypes.POINTER(ctypes.c_float),
+                                        i32p, ctypes.POINTER(ctypes.c_uint64)]
         L.tn_result_decode.argtypes = [ctypes.c_int, u32p, i32, vp, ctypes.POINTER(tn_result_t)]
         L.tn_contract_pair.argtypes = [ctypes.c_int, u32p, i32, vp, i32p, i32, vp, i32p, i32, i32p, i32, vp, vp]
         L.tn_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
@@ -196,6 +199,20 @@ def tn_contract(plan, semiring, primes, ws_ptr: int, ws_bytes: int, stream: int)
     _check(lib().tn_contract(plan, _sr(semiring), _u32p(pr), k, ctypes.c_void_p(ws_ptr), ws_bytes,
                              ctypes.c_void_p(stream), ctypes.byref(r)), "tn_contract")
     return result_dict(r, semiring)
+
+
+def tn_contract_timed(plan, semiring, primes, ws_ptr: int, ws_bytes: int, stream: int, nsteps: int):
+    """(result dict, per-step ms, per-step kernel id, per-step ops)."""
+    pr, k = _primes(primes)
+    r = tn_result_t()
+    ms = np.zeros(nsteps, dtype=np.float32)
+    kern = np.zeros(nsteps, dtype=np.int32)
+    ops = np.zeros(nsteps, dtype=np.uint64)
+    _check(lib().tn_contract_timed(plan, _sr(semiring), _u32p(pr), k, ctypes.c_void_p(ws_ptr), ws_bytes,
+                                   ctypes.c_void_p(stream), ctypes.byref(r),
+                                   ms.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _p32(kern),
+                                   ops.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))), "tn_contract_timed")
+    return result_dict(r, semiring), ms, kern, ops
 
 
 def tn_contract_async(plan, semiring, primes, ws_ptr: int, ws_bytes: int, stream: int, raw_ptr: int):
