@@ -107,7 +107,7 @@ int contract_enqueue(const tn_plan_s* p, tn_semiring_t s, const ModTable& mods, 
     Operand B = operand_of(p, rg, step.b_id);
     Operand Cin = operand_of(p, rg, step.c_id);
     Output C{const_cast<void*>(Cin.p0), const_cast<void*>(Cin.p1), Cin.prime_stride};
-    rc = dev::launch_step_naive(s, step.g, A, B, C, mods, np, st);
+    rc = dev::launch_step(s, step.g, A, B, C, mods, np, st, nullptr);
     if (rc) return rc;
     if (step_events) {
       rc = cuda_rc(cudaEventRecord(step_events[2 * i + 1], st));
@@ -201,7 +201,11 @@ int tn_plan_info(tn_plan_t plan, tn_semiring_t semiring, int32_t nprimes, tn_pla
   for (int k = 0; k < 4; ++k)
     out->peak_bytes[k] = workspace_bytes(plan, static_cast<tn_semiring_t>(k + 1), nprimes);
   int wide = 0;
-  for (const auto& s : plan->steps) wide += s.kernel != kKernNaive;
+  for (const auto& s : plan->steps) {
+    int k, t, sp;
+    dev::pick_launch(s.g, semiring, nprimes, &k, &t, &sp);
+    wide += k != kKernNaive;
+  }
   out->nlaunch_steps = wide;
   return TN_OK;
 }
@@ -267,7 +271,11 @@ int tn_contract_timed(tn_plan_t plan, tn_semiring_t semiring, const uint32_t* pr
     float ms = 0.f;
     if (step_ms) rc = cuda_rc(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
     if (step_ms) step_ms[i] = ms;
-    if (step_kernel) step_kernel[i] = plan->steps[i].kernel;
+    if (step_kernel) {
+      int k, t, sp;
+      dev::pick_launch(plan->steps[i].g, semiring, nprimes, &k, &t, &sp);
+      step_kernel[i] = k;
+    }
     if (step_ops) step_ops[i] = plan->steps[i].ops;
   }
   for (auto& e : ev)
@@ -313,8 +321,8 @@ int tn_contract_pair(tn_semiring_t semiring, const uint32_t* primes, int32_t npr
   Operand B{kOpArena, 0, d_b, counts_at(d_b, rb), int64_t(1) << rb};
   Output C{d_c, const_cast<void*>(counts_at(d_c, rc)), int64_t(1) << rc};
   const int np = semiring == TN_COUNT_MODP ? nprimes : 1;
-  return dev::launch_step_naive(semiring, g, A, B, C, mods, np,
-                                static_cast<cudaStream_t>(cuda_stream));
+  return dev::launch_step(semiring, g, A, B, C, mods, np, static_cast<cudaStream_t>(cuda_stream),
+                         nullptr);
 }
 
 void tn_plan_destroy(tn_plan_t plan) { delete plan; }

@@ -13,6 +13,22 @@ namespace dev {
 int launch_step_naive(tn_semiring_t s, const StepGeom& g, const Operand& A, const Operand& B,
                       const Output& C, const ModTable& mods, int nprimes, cudaStream_t st);
 
+// Register-blocked semiring GEMM (kernels_tiled.cu).  tile: 0 = 128 x 128
+// output tile (tropical only), 1 = 64 x 64; split: CTAs of a cluster that
+// share one output tile (split-K, power of two <= 8).
+int launch_step_tiled(tn_semiring_t s, const StepGeom& g, const Operand& A, const Operand& B,
+                      const Output& C, const ModTable& mods, int nprimes, int tile, int split,
+                      cudaStream_t st);
+int tiled_tile_bm(int tile);
+int tiled_tile_bn(int tile);
+int tiled_tile_bk(int tile);
+
+// Kernel choice for one step: fills kernel (kKernNaive / kKernTiled), tile
+// and split from the step geometry, the semiring and the number of primes.
+void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, int* tile, int* split);
+int launch_step(tn_semiring_t s, const StepGeom& g, const Operand& A, const Operand& B,
+                const Output& C, const ModTable& mods, int nprimes, cudaStream_t st, int* kernel_used);
+
 // Copies the root scalar and the status word into a TN_RAW_BYTES block.
 int launch_finalize(tn_semiring_t s, const Operand& root, int nprimes, const uint32_t* d_status,
                     void* d_raw, cudaStream_t st);

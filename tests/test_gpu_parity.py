@@ -267,3 +267,71 @@ def test_workspace_too_small_rejected():
         assert ei.value.code == tn.TN_ENOMEM
     finally:
         p.close()
+
+
+# ------------------------------------------------------------------ GEMM-shaped steps, both kernels
+
+def _gemm_labels(rng, nb, nm, nn, nk):
+    pool = [int(x) for x in rng.permutation(200)[: nb + nm + nn + nk]]
+    bt, M, N, K = pool[:nb], pool[nb:nb + nm], pool[nb + nm:nb + nm + nn], pool[nb + nm + nn:]
+    LA = bt + M + K; LB = bt + K + N; LC = bt + M + N
+    rng.shuffle(LA); rng.shuffle(LB); rng.shuffle(LC)
+    return LA, LB, LC
+
+
+GEMM_SHAPES = [(0, 7, 8, 11), (2, 8, 9, 6), (1, 9, 3, 7), (0, 3, 3, 14), (4, 4, 4, 4), (0, 8, 8, 2),
+               (0, 1, 9, 9), (3, 6, 7, 5), (0, 10, 10, 3), (5, 2, 2, 2)]
+
+
+@pytest.mark.parametrize("mode", ["auto", "tiled", "naive"])
+@pytest.mark.parametrize("shape", GEMM_SHAPES)
+def test_gemm_steps_all_semirings(shape, mode, monkeypatch):
+    monkeypatch.setenv("TN_KERNEL", mode)
+    rng = np.random.default_rng(hash(shape) % 2 ** 32)
+    LA, LB, LC = _gemm_labels(rng, *shape)
+    ea, eb, E = 1 << len(LA), 1 << len(LB), 1 << len(LC)
+    # tropical int32
+    a = rng.integers(0, 40, size=ea); a[rng.random(ea) < 0.1] = -1
+    b = rng.integers(0, 40, size=eb); b[rng.random(eb) < 0.1] = -1
+    ref = O.pair_tropical(np.where(a < 0, O.OR_NEG_INF, a), LA, np.where(b < 0, O.OR_NEG_INF, b), LB, LC)
+    got = _gpu_pair(tn.TN_TROPICAL_I32, None, _to_dev_i32(np.where(a < 0, NEG, a)), LA,
+                    _to_dev_i32(np.where(b < 0, NEG, b)), LB, LC, 4 * E).view(np.int32).astype(np.int64)
+    assert np.array_equal(np.where(got < NEG // 2, O.OR_NEG_INF, got), ref)
+    # counting (small counts: no overflow)
+    ac = rng.integers(1, 2 ** 10, size=ea, dtype=np.uint64); ac[a < 0] = 0
+    bc = rng.integers(1, 2 ** 10, size=eb, dtype=np.uint64); bc[b < 0] = 0
+    av = rng.integers(0, 4, size=ea); av[a < 0] = -1
+    bv = rng.integers(0, 4, size=eb); bv[b < 0] = -1
+    rn, rcnt = O.pair_counting(np.where(av < 0, O.OR_NEG_INF, av), ac, LA, np.where(bv < 0, O.OR_NEG_INF, bv), bc, LB, LC)
+    A, _ = _counting_buffer(np.where(av < 0, NEG, av), ac)
+    B, _ = _counting_buffer(np.where(bv < 0, NEG, bv), bc)
+    off = 8 * ((E + 1) // 2)
+    out = _gpu_pair(tn.TN_COUNTING_TROPICAL, None, A, LA, B, LB, LC, off + 8 * E)
+    gv = out[: 4 * E].view(np.int32).astype(np.int64)
+    gc = out[off: off + 8 * E].view(np.uint64)
+    fin = rn != O.OR_NEG_INF
+    assert np.array_equal(gv[fin], rn[fin]) and (gv[~fin] < NEG // 2).all()
+    assert [int(x) for x in gc[fin]] == [min(c, U64MAX) for c, f in zip(rcnt, fin) if f]
+    # mod p, two primes
+    primes = [tn.PRIMES31[1], tn.PRIMES31[5]]
+    Am = np.stack([rng.integers(0, p, size=ea, dtype=np.uint64) for p in primes])
+    Bm = np.stack([rng.integers(0, p, size=eb, dtype=np.uint64) for p in primes])
+    out = _gpu_pair(tn.TN_COUNT_MODP, primes, torch.from_numpy(Am.astype(np.uint32).reshape(-1).view(np.int32)).cuda(),
+                    LA, torch.from_numpy(Bm.astype(np.uint32).reshape(-1).view(np.int32)).cuda(), LB, LC,
+                    4 * E * len(primes)).view(np.uint32)
+    for q, p in enumerate(primes):
+        assert np.array_equal(out[q * E:(q + 1) * E].astype(np.uint64), O.pair_modp(Am[q], LA, Bm[q], LB, LC, p))
+
+
+@pytest.mark.parametrize("mode", ["tiled", "naive"])
+def test_networks_both_kernels(mode, monkeypatch):
+    """Whole contractions with every step forced onto one kernel."""
+    monkeypatch.setenv("TN_KERNEL", mode)
+    for spec in ["reg3:20:1", "ksg:5:0.8:4", "er:16:0.25:1"]:
+        n, e = g.by_name(spec)
+        poly = O.bruteforce_poly(n, e)
+        alpha = max(k for k, c in enumerate(poly) if c)
+        r = _gpu_all(n, e, tn.tn_order_greedy(n, e, 0.0, 3, 7))
+        assert r["i32"] == alpha and r["f32"] == alpha
+        assert r["cnt"] == (alpha, poly[alpha], tn.TN_OK)
+        assert r["mod"][1] == sum(poly)
