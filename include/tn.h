@@ -94,7 +94,10 @@ typedef struct {
     uint64_t tc, sc_elems, rwc;
     uint64_t peak_bytes[4];
     int32_t nsteps;
-    int32_t nlaunch_steps;   /* steps executed by the wide (multi-CTA) kernels */
+    int32_t nlaunch_steps;   /* steps executed by the tiled (GEMM) kernels */
+    uint64_t exec_table_bytes;  /* step/task tables uploaded once per plan and device */
+    int32_t exec_tasks;         /* tasks of one executor launch (this semiring) */
+    int32_t exec_levels;        /* dependency levels of the steps */
 } tn_plan_info_t;
 
 /* Result of one contraction.

@@ -9,11 +9,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <numeric>
 #include <vector>
 
+#include "exec.h"
 #include "kernels.h"
 #include "tn_internal.h"
 
@@ -90,8 +92,24 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? TN_OK : TN_ECUDA; }
 
 }  // namespace
 
+// Workspace a contraction needs: the larger of the per-step layout and the
+// executor layout (so one buffer serves both paths).
+size_t required_bytes(tn_plan_s* p, tn_semiring_t s, int32_t nprimes) {
+  int rc;
+  ExecPlan* X = exec_plan_get(p, s, nprimes < 1 ? 1 : nprimes, &rc);
+  size_t a = workspace_bytes(p, s, nprimes);
+  return X ? std::max(a, X->total_bytes) : ~size_t(0);
+}
+
+bool executor_enabled() {
+  const char* e = getenv("TN_EXEC");
+  return !(e && e[0] == '0');
+}
+
 int contract_enqueue(const tn_plan_s* p, tn_semiring_t s, const ModTable& mods, int32_t nprimes,
                      void* ws, cudaStream_t st, void* d_raw, cudaEvent_t* step_events) {
+  if (!step_events && executor_enabled())
+    return exec_enqueue(const_cast<tn_plan_s*>(p), s, &mods, nprimes, ws, ~size_t(0), st, d_raw);
   Regions rg = regions(p, s, ws);
   uint32_t* d_status = static_cast<uint32_t*>(ws);
   int rc = cuda_rc(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st));
@@ -198,8 +216,13 @@ int tn_plan_info(tn_plan_t plan, tn_semiring_t semiring, int32_t nprimes, tn_pla
   out->log2_sc = std::log2(static_cast<double>(plan->sc));
   out->log2_rwc = std::log2(static_cast<double>(plan->rwc));
   out->nsteps = static_cast<int32_t>(plan->steps.size());
-  for (int k = 0; k < 4; ++k)
-    out->peak_bytes[k] = workspace_bytes(plan, static_cast<tn_semiring_t>(k + 1), nprimes);
+  for (int k = 0; k < 4; ++k) {
+    int rc;
+    tn_semiring_t sk = static_cast<tn_semiring_t>(k + 1);
+    ExecPlan* X = exec_plan_get(plan, sk, nprimes < 1 ? 1 : nprimes, &rc);
+    if (!X) return rc;
+    out->peak_bytes[k] = std::max(workspace_bytes(plan, sk, nprimes), X->total_bytes);
+  }
   int wide = 0;
   for (const auto& s : plan->steps) {
     int k, t, sp;
@@ -207,6 +230,12 @@ int tn_plan_info(tn_plan_t plan, tn_semiring_t semiring, int32_t nprimes, tn_pla
     wide += k != kKernNaive;
   }
   out->nlaunch_steps = wide;
+  int rc;
+  ExecPlan* X = exec_plan_get(plan, semiring, nprimes < 1 ? 1 : nprimes, &rc);
+  if (!X) return rc;
+  out->exec_table_bytes = X->table_bytes;
+  out->exec_tasks = static_cast<int32_t>(X->tasks.size());
+  out->exec_levels = X->nlevels;
   return TN_OK;
 }
 
@@ -218,7 +247,7 @@ int tn_contract_async(tn_plan_t plan, tn_semiring_t semiring, const uint32_t* pr
   ModTable mods;
   int rc = make_mods(semiring, primes, nprimes, &mods);
   if (rc) return rc;
-  if (ws_bytes < workspace_bytes(plan, semiring, nprimes)) return TN_ENOMEM;
+  if (ws_bytes < required_bytes(plan, semiring, nprimes)) return TN_ENOMEM;
   return contract_enqueue(plan, semiring, mods, nprimes, d_workspace,
                           static_cast<cudaStream_t>(cuda_stream), d_raw, nullptr);
 }
@@ -256,7 +285,7 @@ int tn_contract_timed(tn_plan_t plan, tn_semiring_t semiring, const uint32_t* pr
   ModTable mods;
   int rc = make_mods(semiring, primes, nprimes, &mods);
   if (rc) return rc;
-  if (ws_bytes < workspace_bytes(plan, semiring, nprimes)) return TN_ENOMEM;
+  if (ws_bytes < required_bytes(plan, semiring, nprimes)) return TN_ENOMEM;
   const size_t ns = plan->steps.size();
   std::vector<cudaEvent_t> ev(2 * ns, nullptr);
   for (auto& e : ev)
@@ -325,7 +354,11 @@ int tn_contract_pair(tn_semiring_t semiring, const uint32_t* primes, int32_t npr
                          nullptr);
 }
 
-void tn_plan_destroy(tn_plan_t plan) { delete plan; }
+void tn_plan_destroy(tn_plan_t plan) {
+  if (!plan) return;
+  exec_plans_free(plan);
+  delete plan;
+}
 
 const char* tn_strerror(int code) {
   switch (code) {

@@ -1,0 +1,387 @@
+// exec.cu -- the persistent plan executor kernel (see exec.h).
+//
+// One launch contracts a whole network.  Each CTA loops: claim the next task
+// (atomic counter), copy its step record to shared memory, wait (warp 0,
+// acquire loads, bounded by a timeout) until every step it depends on has
+// published all of its tasks, run the task, publish (release).  Wide steps
+// run as register-blocked GEMM tiles; their split-K partial tiles go to a
+// scratch area and the last CTA of a tile to arrive merges them.  Tensors
+// written during the launch are read through L2 only (ld.global.cg).
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <type_traits>
+
+#include "exec.h"
+#include "kernels.h"
+#include "semiring.cuh"
+#include "step_device.cuh"
+#include "tile_device.cuh"
+
+namespace tn {
+
+namespace dev {
+
+struct ExecArgs {
+  const ExecStep* steps;
+  const int32_t* deps;
+  const ExecTask* tasks;
+  int32_t ntasks_total;
+  int32_t nprimes;
+  int32_t* done;        // per exec step: finished tasks
+  int32_t* arrive;      // split-K arrival counters
+  int32_t* task_ctr;    // next task to claim
+  uint32_t* status;     // bit 0: a wait timed out
+  char* r0;             // arena: values / residues
+  char* r1;             // arena: counts
+  int64_t prime_stride; // entries between prime blocks
+  char* scratch;
+  unsigned char* raw;   // result block (TN_RAW_BYTES)
+  ModTable mods;
+  int32_t semiring;
+  int32_t pad_;
+  unsigned long long timeout_ns;
+};
+
+constexpr uint32_t kStatusTimeout = 1u;
+
+__device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ Operand exec_operand(const ExecArgs& a, int32_t kind, int64_t off) {
+  Operand o;
+  o.kind = kind;
+  o.pad_ = 0;
+  o.p0 = a.r0 + 4 * off;
+  o.p1 = a.r1 ? a.r1 + 8 * off : nullptr;
+  o.prime_stride = a.prime_stride;
+  return o;
+}
+
+template <class SR>
+struct ExecTile {
+  // tropical steps may use 8 x 8 micro-tiles; counting and mod p use 4 x 4
+  static constexpr bool kBig = std::is_same<SR, SrI32>::value || std::is_same<SR, SrF32>::value;
+};
+
+template <class SR, int TM, int TN, int FOLD>
+__device__ __forceinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
+                                               unsigned char* smem, int* s_last) {
+  constexpr int BK = 16, BM = 16 * TM, BN = 16 * TN;
+  using Acc = typename SR::Acc;
+  auto& sm = *reinterpret_cast<TileSmem<SR, TM, TN, BK>*>(smem);
+  const StepGeom& g = st.g;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int split = st.split;
+  const int rank = task.local % split;
+  const int64_t tile = task.local / split;
+  const int64_t per_b = int64_t(st.tiles_m) * st.tiles_n;
+  const int64_t b = tile / per_b;
+  const int64_t tm = (tile % per_b) / st.tiles_n, tn_ = tile % st.tiles_n;
+  const int q = task.prime;
+  const ModParams mp = a.mods.q[q];
+  const int64_t M = int64_t(1) << g.nm, N = int64_t(1) << g.nn, K = int64_t(1) << g.nk;
+  const int64_t kspan = K >= split ? K / split : K;
+  const int64_t kbeg = int64_t(rank) * kspan;
+  const Operand A = exec_operand(a, g.a_kind, st.a_off);
+  const Operand B = exec_operand(a, g.b_kind, st.b_off);
+  Output C{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride};
+
+  Acc acc[TM][TN];
+  tile_mainloop<SR, TM, TN, BK, FOLD, true>(g, A, B, mp, q, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
+
+  const int64_t m0 = tm * BM, n0 = tn_ * BN;
+  const int64_t cbase = b << (g.nn + g.nm);
+  if (split > 1) {
+    // publish this partial tile, then let the last CTA of the tile merge
+    Acc* part = reinterpret_cast<Acc*>(a.scratch + st.scratch_off) +
+                ((int64_t(q) * (per_b << g.nb) + tile) * split) * (BM * BN);
+    Acc* mine = part + int64_t(rank) * BM * BN;
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) mine[(ty * TM + i) * BN + tx * TN + j] = acc[i][j];
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      int32_t* ctr = a.arrive + st.arrive_off + int64_t(q) * (per_b << g.nb) + tile;
+      *s_last = atomicAdd(ctr, 1) == split - 1;
+      __threadfence();
+    }
+    __syncthreads();
+    if (!*s_last) return;
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j)
+        for (int r = 0; r < split; ++r) {
+          if (r == rank) continue;
+          const Acc* other = part + int64_t(r) * BM * BN;
+          Acc v;
+          const int e = (ty * TM + i) * BN + tx * TN + j;
+          if constexpr (std::is_same<Acc, CntVal>::value) {
+            v.v = __ldcg(&other[e].v);
+            v.c = __ldcg(&other[e].c);
+          } else {
+            v = __ldcg(&other[e]);
+          }
+          SR::merge(acc[i][j], v, mp);
+        }
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int64_t m = m0 + ty * TM + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int64_t n = n0 + tx * TN + j;
+      if (n < N) SR::store(C, cbase + (m << g.nn) + n, q, acc[i][j], mp);
+    }
+  }
+}
+
+template <class SR>
+__device__ __forceinline__ void exec_naive_task(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
+                                                unsigned char* smem) {
+  auto& sm = *reinterpret_cast<NaiveSmem<SR>*>(smem);
+  const StepGeom& g = st.g;
+  naive_tables<SR>(g, sm);
+  const int q = task.prime;
+  const ModParams mp = a.mods.q[q];
+  const Operand A = exec_operand(a, g.a_kind, st.a_off);
+  const Operand B = exec_operand(a, g.b_kind, st.b_off);
+  Output C{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride};
+  const int64_t E = int64_t(1) << g.rc;
+  const int64_t c0 = int64_t(task.local) * st.chunk;
+  const int64_t c1 = c0 + st.chunk < E ? c0 + st.chunk : E;
+  auto la = [&](int64_t e) { return SR::template load<true>(A, e, q); };
+  auto lb = [&](int64_t e) { return SR::template load<true>(B, e, q); };
+  naive_chunk<SR>(g, la, lb, C, mp, q, c0, c1, st.R, sm);
+}
+
+__device__ __forceinline__ void exec_final(const ExecArgs& a, const ExecStep& st) {
+  if (threadIdx.x != 0) return;
+  const char* r0 = a.r0 + 4 * st.c_off;
+  if (a.semiring == TN_TROPICAL_F32 || a.semiring == TN_TROPICAL_I32) {
+    *reinterpret_cast<int32_t*>(a.raw) = __ldcg(reinterpret_cast<const int32_t*>(r0));
+  } else if (a.semiring == TN_COUNTING_TROPICAL) {
+    *reinterpret_cast<int32_t*>(a.raw) = __ldcg(reinterpret_cast<const int32_t*>(r0));
+    *reinterpret_cast<uint64_t*>(a.raw + 8) =
+        __ldcg(reinterpret_cast<const uint64_t*>(a.r1 + 8 * st.c_off));
+  } else {
+    for (int q = 0; q < a.nprimes; ++q)
+      reinterpret_cast<uint32_t*>(a.raw + 16)[q] =
+          __ldcg(reinterpret_cast<const uint32_t*>(r0) + q * a.prime_stride);
+  }
+  *reinterpret_cast<uint32_t*>(a.raw + 96) = ld_relaxed_u32(a.status);
+}
+
+template <class SR, int FOLD>
+__global__ void __launch_bounds__(kBlock) k_exec(const __grid_constant__ ExecArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ ExecStep s_step;
+  __shared__ ExecTask s_task;
+  __shared__ int s_t, s_abort, s_last;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) {
+      s_abort = ld_relaxed_u32(a.status) != 0;
+      s_t = s_abort ? a.ntasks_total : atomicAdd(a.task_ctr, 1);
+    }
+    __syncthreads();
+    const int t = s_t;
+    if (t >= a.ntasks_total) break;
+    if (tid == 0) s_task = a.tasks[t];
+    __syncthreads();
+    {
+      const int32_t* src = reinterpret_cast<const int32_t*>(a.steps + s_task.step);
+      int32_t* dst = reinterpret_cast<int32_t*>(&s_step);
+      for (int i = tid; i < static_cast<int>(sizeof(ExecStep) / 4); i += kBlock) dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    // wait for the steps this one depends on (warp 0, one dependency per lane)
+    if (tid < 32) {
+      const bool final_task = s_task.kind == kTaskFinal;
+      const int nd = final_task ? 1 : s_step.dep_count;
+      bool timed_out = false;
+      for (int d0 = 0; d0 < nd; d0 += 32) {
+        const int d = d0 + tid;
+        if (d < nd) {
+          const int dep = final_task ? s_task.step : a.deps[s_step.dep_begin + d];
+          const int32_t target = a.steps[dep].ntasks * a.nprimes;
+          const unsigned long long t0 = global_ns();
+          unsigned ns = 32;
+          while (ld_acquire(a.done + dep) < target) {
+            if (global_ns() - t0 > a.timeout_ns || ld_relaxed_u32(a.status) != 0) {
+              timed_out = true;
+              break;
+            }
+            __nanosleep(ns);
+            if (ns < 1024) ns *= 2;
+          }
+        }
+      }
+      timed_out = __any_sync(0xffffffffu, timed_out);
+      if (tid == 0 && timed_out) {
+        atomicOr(a.status, kStatusTimeout);
+        atomicOr(reinterpret_cast<unsigned int*>(a.raw + 96), kStatusTimeout);
+        s_abort = 1;
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    if (s_task.kind == kTaskFinal) {
+      exec_final(a, s_step);
+    } else if (s_task.kind == kTaskNaive) {
+      exec_naive_task<SR>(a, s_step, s_task, smem);
+    } else {
+      if constexpr (ExecTile<SR>::kBig) {
+        if (s_step.tile == 0) exec_tile_task<SR, 8, 8, FOLD>(a, s_step, s_task, smem, &s_last);
+        else exec_tile_task<SR, 4, 4, FOLD>(a, s_step, s_task, smem, &s_last);
+      } else {
+        exec_tile_task<SR, 4, 4, FOLD>(a, s_step, s_task, smem, &s_last);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(a.done + s_task.step, 1);
+    }
+  }
+}
+
+template <class SR, int FOLD>
+static size_t smem_for() {
+  size_t t = ExecTile<SR>::kBig ? sizeof(TileSmem<SR, 8, 8, 16>) : sizeof(TileSmem<SR, 4, 4, 16>);
+  size_t n = sizeof(NaiveSmem<SR>);
+  return t > n ? t : n;
+}
+
+// Resident CTAs of one executor instantiation on the current device
+// (computed once per instantiation; one GPU per process).
+template <class SR, int FOLD>
+static int exec_resident(size_t* smem_out) {
+  static int resident = 0;
+  static size_t smem = 0;
+  if (resident == 0) {
+    auto kern = k_exec<SR, FOLD>;
+    smem = smem_for<SR, FOLD>();
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+        cudaSuccess)
+      return -1;
+    int dev, sms, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem) != cudaSuccess)
+      return -1;
+    resident = sms * (per_sm < 1 ? 1 : per_sm);
+  }
+  *smem_out = smem;
+  return resident;
+}
+
+template <class SR, int FOLD>
+static int exec_launch_t(ExecPlan* X, const ExecArgs& args, cudaStream_t st) {
+  size_t smem;
+  const int resident = exec_resident<SR, FOLD>(&smem);
+  if (resident < 0) return TN_ECUDA;
+  const int grid = resident < args.ntasks_total ? resident : args.ntasks_total;
+  X->grid = grid;
+  X->smem = smem;
+  k_exec<SR, FOLD><<<grid, kBlock, smem, st>>>(args);
+  return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ECUDA;
+}
+
+}  // namespace dev
+
+size_t exec_acc_bytes(tn_semiring_t s) {
+  switch (s) {
+    case TN_TROPICAL_F32: return sizeof(float);
+    case TN_TROPICAL_I32: return sizeof(int32_t);
+    case TN_COUNTING_TROPICAL: return sizeof(dev::CntVal);
+    case TN_COUNT_MODP: return sizeof(uint64_t);
+  }
+  return 0;
+}
+
+int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods_v, int32_t nprimes, void* ws,
+                 size_t ws_bytes, void* stream, void* d_raw) {
+  const dev::ModTable& mods = *static_cast<const dev::ModTable*>(mods_v);
+  int rc;
+  ExecPlan* X = exec_plan_get(p, s, nprimes, &rc);
+  if (!X) return rc;
+  if (ws_bytes < X->total_bytes) return TN_ENOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {
+    // one-time upload of the step / dependency / task tables to this device
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TN_ECUDA;
+    if (!X->d_tables || X->device != dev) {
+      if (X->d_tables) cudaFree(X->d_tables);
+      X->d_tables = nullptr;
+      std::vector<unsigned char> img(X->table_bytes, 0);
+      std::memcpy(img.data() + X->off_steps, X->steps.data(), sizeof(ExecStep) * X->steps.size());
+      std::memcpy(img.data() + X->off_deps, X->deps.data(), sizeof(int32_t) * X->deps.size());
+      std::memcpy(img.data() + X->off_tasks, X->tasks.data(), sizeof(ExecTask) * X->tasks.size());
+      if (cudaMalloc(&X->d_tables, X->table_bytes) != cudaSuccess) return TN_ENOMEM;
+      if (cudaMemcpy(X->d_tables, img.data(), X->table_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+        return TN_ECUDA;
+      X->device = dev;
+      X->grid = 0;
+    }
+  }
+  char* w = static_cast<char*>(ws);
+  if (cudaMemsetAsync(w, 0, X->ctr_off + X->ctr_bytes, st) != cudaSuccess) return TN_ECUDA;
+  dev::ExecArgs a;
+  std::memset(&a, 0, sizeof(a));
+  const int ns = static_cast<int>(X->steps.size());
+  char* tables = static_cast<char*>(X->d_tables);
+  a.steps = reinterpret_cast<const ExecStep*>(tables + X->off_steps);
+  a.deps = reinterpret_cast<const int32_t*>(tables + X->off_deps);
+  a.tasks = reinterpret_cast<const ExecTask*>(tables + X->off_tasks);
+  a.ntasks_total = static_cast<int32_t>(X->tasks.size());
+  a.nprimes = X->nprimes;
+  int32_t* ctr = reinterpret_cast<int32_t*>(w + X->ctr_off);
+  a.done = ctr;
+  a.arrive = ctr + ns;
+  a.task_ctr = ctr + ns + X->n_arrive;
+  a.status = reinterpret_cast<uint32_t*>(w);
+  const size_t e = static_cast<size_t>(X->arena_entries);
+  const size_t b4 = (4 * e + 255) / 256 * 256;
+  a.r0 = w + X->arena_base;
+  a.r1 = s == TN_COUNTING_TROPICAL ? a.r0 + b4 : nullptr;
+  a.prime_stride = static_cast<int64_t>(b4 / 4);
+  a.scratch = w + X->scratch_base;
+  a.raw = static_cast<unsigned char*>(d_raw);
+  a.mods = mods;
+  a.semiring = s;
+  a.timeout_ns = 2000000000ull;  // 2 s per wait
+  switch (s) {
+    case TN_TROPICAL_F32: return dev::exec_launch_t<dev::SrF32, 1>(X, a, st);
+    case TN_TROPICAL_I32: return dev::exec_launch_t<dev::SrI32, 1>(X, a, st);
+    case TN_COUNTING_TROPICAL: return dev::exec_launch_t<dev::SrCnt, 1>(X, a, st);
+    case TN_COUNT_MODP: {
+      bool small_r = true;
+      for (int i = 0; i < X->nprimes; ++i) small_r = small_r && mods.q[i].r32 < (1u << 20);
+      return small_r ? dev::exec_launch_t<dev::SrMod, 3>(X, a, st) : dev::exec_launch_t<dev::SrMod, 1>(X, a, st);
+    }
+  }
+  return TN_EINVAL;
+}
+
+}  // namespace tn

@@ -1,0 +1,85 @@
+// exec.h -- the persistent plan executor of libtn: data shared by the host
+// exec planner (exec_plan.cpp) and the executor kernel (exec.cu).
+//
+// A contraction runs as ONE kernel launch.  The host turns the plan's
+// pairwise steps (Sec. 4.1 of arXiv:2501.00227) into a flat list of tasks in
+// a topological order (by dependency level): a task is a chunk of output
+// entries of a general step, one output tile (and split-K slice) of a wide
+// step, or the final copy of the scalar.  Persistent CTAs claim tasks with an
+// atomic counter; a task first waits until the steps it depends on have
+// completed (per-step done counters, acquire loads), runs, then publishes its
+// completion (release).  Because a task only waits on tasks earlier in the
+// list, and those were claimed by CTAs that are already running, the
+// schedule cannot deadlock; every wait is still bounded by a timeout that
+// aborts the whole launch with TN_ETIMEOUT.
+#pragma once
+
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "tn_internal.h"
+
+namespace tn {
+
+struct ExecStep {
+  StepGeom g;
+  int64_t a_off, b_off, c_off;   // arena entry offsets (intermediates)
+  int64_t scratch_off;           // byte offset of the split-K partial tiles
+  int64_t chunk;                 // naive: output entries per task
+  int32_t kernel;                // kKernNaive / kKernTiled
+  int32_t tile, split, tiles_m, tiles_n;
+  int32_t R;                     // naive: threads per output entry
+  int32_t ntasks;                // tasks per prime
+  int32_t dep_begin, dep_count;  // into the dependency array (exec-step indices)
+  int32_t arrive_off;            // first split-K arrival counter of this step
+  int32_t pad_;
+};
+
+enum ExecTaskKind : int32_t { kTaskNaive = 0, kTaskTile = 1, kTaskFinal = 2 };
+
+struct ExecTask {
+  int32_t step;   // exec-step index
+  int32_t local;  // naive: chunk index; tile: tile * split + rank
+  int32_t prime;  // prime index (mod p), else 0
+  int32_t kind;
+};
+
+// Host-side executor plan for one (plan, semiring, nprimes).
+struct ExecPlan {
+  tn_semiring_t semiring;
+  int32_t nprimes;
+  std::vector<ExecStep> steps;     // execution (level) order
+  std::vector<int32_t> deps;
+  std::vector<ExecTask> tasks;
+  int64_t arena_entries = 0;
+  int64_t root_off = 0;
+  int32_t root_step = -1;
+  int32_t n_arrive = 0;
+  int32_t nlevels = 0;
+  size_t scratch_bytes = 0;
+  // workspace layout (bytes from the start of the workspace)
+  size_t ctr_off = 0, ctr_bytes = 0, scratch_base = 0, arena_base = 0, total_bytes = 0;
+  // device copy of steps / deps / tasks (library-owned, uploaded once)
+  void* d_tables = nullptr;
+  int device = -1;
+  size_t off_steps = 0, off_deps = 0, off_tasks = 0, table_bytes = 0;
+  // executor launch shape
+  int grid = 0;
+  size_t smem = 0;
+};
+
+// Builds (or returns the cached) executor plan; thread-safe.
+ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc);
+void exec_plans_free(tn_plan_s* p);
+
+// Enqueues one contraction through the executor (exec.cu).
+int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods, int32_t nprimes, void* ws,
+                 size_t ws_bytes, void* stream, void* d_raw);
+
+// Bytes per accumulator / per staged value of the tiled tasks, and the
+// dynamic shared memory the executor needs (exec.cu).
+size_t exec_acc_bytes(tn_semiring_t s);
+size_t exec_smem_bytes(tn_semiring_t s);
+
+}  // namespace tn

@@ -1,0 +1,294 @@
+// exec_plan.cu -- host side of the persistent executor: turns a plan's
+// pairwise steps into a level-ordered task list with dependencies, lays out
+// the workspace (counters, split-K scratch, arena) and caches the result per
+// (semiring, number of primes) inside the plan.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+
+#include "exec.h"
+#include "kernels.h"
+#include "step_device.cuh"
+
+namespace tn {
+
+namespace {
+
+struct Cache {
+  std::mutex mu;
+  std::vector<std::unique_ptr<ExecPlan>> plans;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// First-fit arena whose free blocks remember which steps released them: a
+// step that takes memory another step released must run after that step
+// (write-after-read), so the releasers become dependencies.
+class LevelArena {
+ public:
+  int64_t alloc(int64_t size, std::vector<int32_t>* war) {
+    size = static_cast<int64_t>(align_up(static_cast<size_t>(size), kArenaAlign));
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second.len >= size) {
+        int64_t off = it->first;
+        Block blk = it->second;
+        free_.erase(it);
+        war->insert(war->end(), blk.rel.begin(), blk.rel.end());
+        if (blk.len > size) free_[off + size] = Block{blk.len - size, blk.rel};
+        return off;
+      }
+    }
+    int64_t off = top_;
+    top_ += size;
+    return off;
+  }
+  void release(int64_t off, int64_t size, int32_t releaser) {
+    size = static_cast<int64_t>(align_up(static_cast<size_t>(size), kArenaAlign));
+    auto it = free_.emplace(off, Block{size, {releaser}}).first;
+    auto next = std::next(it);
+    if (next != free_.end() && it->first + it->second.len == next->first) {
+      merge(&it->second, next->second);
+      free_.erase(next);
+    }
+    if (it != free_.begin()) {
+      auto prev = std::prev(it);
+      if (prev->first + prev->second.len == it->first) {
+        merge(&prev->second, it->second);
+        free_.erase(it);
+      }
+    }
+  }
+  int64_t top() const { return top_; }
+
+ private:
+  struct Block {
+    int64_t len;
+    std::vector<int32_t> rel;
+  };
+  static void merge(Block* a, const Block& b) {
+    a->len += b.len;
+    a->rel.insert(a->rel.end(), b.rel.begin(), b.rel.end());
+    std::sort(a->rel.begin(), a->rel.end());
+    a->rel.erase(std::unique(a->rel.begin(), a->rel.end()), a->rel.end());
+  }
+  std::map<int64_t, Block> free_;
+  int64_t top_ = 0;
+};
+
+int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X) {
+  const int ns = static_cast<int>(p->steps.size());
+  const int np = s == TN_COUNT_MODP ? nprimes : 1;
+  X->semiring = s;
+  X->nprimes = np;
+
+  // dependency levels (leaves at -1)
+  std::vector<int32_t> level(ns);
+  auto prod = [&](int32_t id) { return p->tensors[id].producer; };
+  for (int i = 0; i < ns; ++i) {
+    int la = prod(p->steps[i].a_id), lb = prod(p->steps[i].b_id);
+    level[i] = 1 + std::max(la >= 0 ? level[la] : -1, lb >= 0 ? level[lb] : -1);
+  }
+  std::vector<int32_t> order(ns);
+  for (int i = 0; i < ns; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return level[a] < level[b]; });
+  std::vector<int32_t> pos(ns);
+  for (int i = 0; i < ns; ++i) pos[order[i]] = i;
+  X->nlevels = ns ? level[order[ns - 1]] + 1 : 0;
+
+  // memory: a level's outputs may only reuse memory released by earlier
+  // levels; the releasing steps become (write-after-read) dependencies
+  std::vector<std::vector<int32_t>> dep(ns);  // in plan-step indices
+  std::vector<int64_t> c_off(ns, 0);
+  LevelArena arena;
+  for (int i = 0; i < ns;) {
+    int j = i;
+    while (j < ns && level[order[j]] == level[order[i]]) ++j;
+    for (int x = i; x < j; ++x) {
+      const int st = order[x];
+      const Step& S = p->steps[st];
+      std::vector<int32_t> war;
+      c_off[st] = arena.alloc(int64_t(1) << S.g.rc, &war);
+      dep[st] = war;
+      for (int32_t id : {S.a_id, S.b_id})
+        if (prod(id) >= 0) dep[st].push_back(prod(id));
+    }
+    for (int x = i; x < j; ++x) {
+      const int st = order[x];
+      const Step& S = p->steps[st];
+      for (int32_t id : {S.a_id, S.b_id}) {
+        int pr = prod(id);
+        if (pr >= 0) arena.release(c_off[pr], int64_t(1) << p->steps[pr].g.rc, st);
+      }
+    }
+    i = j;
+  }
+  X->arena_entries = std::max<int64_t>(arena.top(), kArenaAlign);
+
+  // transitive reduction of the dependencies (ancestor bitsets, exec order)
+  const int words = (ns + 63) / 64;
+  std::vector<uint64_t> anc(static_cast<size_t>(ns) * words, 0);
+  std::vector<std::vector<int32_t>> red(ns);
+  for (int x = 0; x < ns; ++x) {
+    const int st = order[x];
+    auto& d = dep[st];
+    std::sort(d.begin(), d.end());
+    d.erase(std::unique(d.begin(), d.end()), d.end());
+    uint64_t* a = &anc[static_cast<size_t>(x) * words];
+    for (int32_t u : d) {
+      const int pu = pos[u];
+      const uint64_t* au = &anc[static_cast<size_t>(pu) * words];
+      for (int w = 0; w < words; ++w) a[w] |= au[w];
+      a[pu / 64] |= 1ull << (pu % 64);
+    }
+    for (int32_t u : d) {
+      const int pu = pos[u];
+      bool implied = false;
+      for (int32_t v : d) {
+        if (v == u) continue;
+        const uint64_t* av = &anc[static_cast<size_t>(pos[v]) * words];
+        if ((av[pu / 64] >> (pu % 64)) & 1) { implied = true; break; }
+      }
+      if (!implied) red[st].push_back(pu);
+    }
+  }
+
+  // steps, tasks, split-K scratch and arrival counters
+  const size_t acc_bytes = exec_acc_bytes(s);
+  X->steps.assign(ns, ExecStep());
+  X->deps.clear();
+  X->tasks.clear();
+  size_t scratch = 0;
+  int32_t arrive = 0;
+  for (int x = 0; x < ns; ++x) {
+    const int st = order[x];
+    const Step& S = p->steps[st];
+    ExecStep& E = X->steps[x];
+    std::memset(&E, 0, sizeof(E));
+    E.g = S.g;
+    auto off = [&](int32_t id) -> int64_t { return prod(id) >= 0 ? c_off[prod(id)] : 0; };
+    E.a_off = off(S.a_id);
+    E.b_off = off(S.b_id);
+    E.c_off = c_off[st];
+    E.dep_begin = static_cast<int32_t>(X->deps.size());
+    E.dep_count = static_cast<int32_t>(red[st].size());
+    X->deps.insert(X->deps.end(), red[st].begin(), red[st].end());
+    int kernel, tile, split;
+    dev::pick_launch(S.g, s, np, &kernel, &tile, &split);
+    if (kernel == kKernTiled && S.g.c_identity) {
+      const int64_t bm = dev::tiled_tile_bm(tile), bn = dev::tiled_tile_bn(tile);
+      E.kernel = kKernTiled;
+      E.tile = tile;
+      E.split = split;
+      E.tiles_m = static_cast<int32_t>(((int64_t(1) << S.g.nm) + bm - 1) / bm);
+      E.tiles_n = static_cast<int32_t>(((int64_t(1) << S.g.nn) + bn - 1) / bn);
+      const int64_t ntiles = int64_t(E.tiles_m) * E.tiles_n << S.g.nb;
+      E.ntasks = static_cast<int32_t>(ntiles * split);
+      if (split > 1) {
+        E.arrive_off = arrive;
+        arrive += static_cast<int32_t>(ntiles * np);
+        E.scratch_off = static_cast<int64_t>(scratch);
+        scratch += align_up(static_cast<size_t>(ntiles * np * split * bm * bn) * acc_bytes, 256);
+      }
+    } else {
+      const dev::NaiveShape sh = dev::naive_shape(S.g.rc, S.g.nk);
+      E.kernel = kKernNaive;
+      E.R = sh.R;
+      E.chunk = sh.chunk;
+      E.ntasks = static_cast<int32_t>(sh.ntasks);
+    }
+    for (int q = 0; q < np; ++q)
+      for (int t = 0; t < E.ntasks; ++t)
+        X->tasks.push_back(ExecTask{x, t, q, E.kernel == kKernTiled ? kTaskTile : kTaskNaive});
+  }
+  X->root_step = pos[ns - 1];
+  X->root_off = c_off[ns - 1];
+
+  // Self-check (TN_EXEC_CHECK=1): the schedule is safe if (1) every step
+  // depends only on steps earlier in the execution order and (2) whenever
+  // the output of a step y overlaps the memory of an earlier tensor x, every
+  // reader of x (its consumer) is an ancestor of y, so y cannot overwrite x
+  // while it is still being read.
+  const char* chk = getenv("TN_EXEC_CHECK");
+  if (chk && chk[0] == '1') {
+    for (int x = 0; x < ns; ++x)
+      for (int d = 0; d < X->steps[x].dep_count; ++d)
+        if (X->deps[X->steps[x].dep_begin + d] >= x) return TN_EINVAL;
+    auto is_anc = [&](int a_pos, int of_pos) {
+      const uint64_t* av = &anc[static_cast<size_t>(of_pos) * words];
+      return ((av[a_pos / 64] >> (a_pos % 64)) & 1) != 0;
+    };
+    for (int y = 0; y < ns; ++y) {
+      const int sy = order[y];
+      const int64_t y0 = c_off[sy], y1 = y0 + (int64_t(1) << p->steps[sy].g.rc);
+      for (int x = 0; x < y; ++x) {
+        const int sx = order[x];
+        const int64_t x0 = c_off[sx], x1 = x0 + (int64_t(1) << p->steps[sx].g.rc);
+        if (x1 <= y0 || y1 <= x0) continue;
+        const int cons = p->tensors[p->steps[sx].c_id].consumer;
+        if (cons < 0 || !is_anc(pos[cons], y)) return TN_EINVAL;
+      }
+    }
+  }
+  X->tasks.push_back(ExecTask{X->root_step, 0, 0, kTaskFinal});
+  X->n_arrive = arrive;
+  X->scratch_bytes = scratch;
+
+  // workspace layout: header | counters | scratch | arena regions
+  X->ctr_off = kHeaderBytes;
+  X->ctr_bytes = align_up(sizeof(int32_t) * (static_cast<size_t>(ns) + arrive + 8), 256);
+  X->scratch_base = X->ctr_off + X->ctr_bytes;
+  X->arena_base = X->scratch_base + align_up(scratch, 256);
+  const size_t e = static_cast<size_t>(X->arena_entries);
+  size_t regions = 0;
+  switch (s) {
+    case TN_TROPICAL_F32:
+    case TN_TROPICAL_I32: regions = align_up(4 * e, 256); break;
+    case TN_COUNTING_TROPICAL: regions = align_up(4 * e, 256) + align_up(8 * e, 256); break;
+    case TN_COUNT_MODP: regions = static_cast<size_t>(np) * align_up(4 * e, 256); break;
+  }
+  X->total_bytes = X->arena_base + regions;
+
+  // device table image: steps | deps | tasks
+  X->off_steps = 0;
+  X->off_deps = align_up(sizeof(ExecStep) * X->steps.size(), 256);
+  X->off_tasks = X->off_deps + align_up(sizeof(int32_t) * (X->deps.size() + 1), 256);
+  X->table_bytes = X->off_tasks + sizeof(ExecTask) * X->tasks.size();
+  return TN_OK;
+}
+
+}  // namespace
+
+ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc) {
+  if (!p->exec_cache) {
+    static std::mutex init_mu;
+    std::lock_guard<std::mutex> lk(init_mu);
+    if (!p->exec_cache) p->exec_cache = new Cache();
+  }
+  Cache* c = static_cast<Cache*>(p->exec_cache);
+  const int np = s == TN_COUNT_MODP ? nprimes : 1;
+  std::lock_guard<std::mutex> lk(c->mu);
+  for (auto& x : c->plans)
+    if (x->semiring == s && x->nprimes == np) {
+      *rc = TN_OK;
+      return x.get();
+    }
+  std::unique_ptr<ExecPlan> X(new ExecPlan());
+  *rc = build_exec(p, s, nprimes, X.get());
+  if (*rc != TN_OK) return nullptr;
+  c->plans.push_back(std::move(X));
+  return c->plans.back().get();
+}
+
+void exec_plans_free(tn_plan_s* p) {
+  Cache* c = static_cast<Cache*>(p->exec_cache);
+  if (!c) return;
+  for (auto& x : c->plans)
+    if (x->d_tables) cudaFree(x->d_tables);
+  delete c;
+  p->exec_cache = nullptr;
+}
+
+}  // namespace tn

@@ -1,7 +1,8 @@
-// kernels_naive.cu -- the general pairwise-step kernel of libtn: one thread
-// per output entry, operands read through bit-position maps.  It handles any
-// step (any label classes, leaves generated on the fly, broadcast labels)
-// and is the path for the many small steps of a contraction; wide steps go
+// kernels_naive.cu -- the general pairwise-step kernel of libtn: R threads
+// per output entry (K-parallel, merged with the semiring (+)), operands read
+// through bit-position maps.  It handles any step (any label classes, leaves
+// generated on the fly, broadcast labels) and is the path for the many small
+// steps of a contraction and for reductions with few outputs; wide steps go
 // to the tiled kernels in kernels_tiled.cu.
 //
 // A step (Sec. 4.1 of arXiv:2501.00227) computes
@@ -11,67 +12,33 @@
 
 #include "kernels.h"
 #include "semiring.cuh"
+#include "step_device.cuh"
 
 namespace tn {
 namespace dev {
 
-// Scatter the bits of x into the positions pos[first .. first+count).
-__device__ __forceinline__ int64_t deposit(int64_t x, const int8_t* pos, int first, int count) {
-  int64_t r = 0;
-  for (int j = 0; j < count; ++j)
-    if ((x >> j) & 1) {
-      int p = pos[first + j];
-      if (p >= 0) r |= int64_t(1) << p;
-    }
-  return r;
-}
-
-constexpr int kNaiveKLoBits = 9;
-
 template <class SR>
-__global__ void __launch_bounds__(256) k_step_naive(const __grid_constant__ StepGeom g, Operand A,
-                                                    Operand B, Output C,
-                                                    ModTable mods) {
-  __shared__ int64_t s_ka[1 << kNaiveKLoBits];
-  __shared__ int64_t s_kb[1 << kNaiveKLoBits];
-  const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
-  const int64_t nklo = int64_t(1) << kl;
-  const int64_t nkhi = int64_t(1) << (g.nk - kl);
-  const int a_k0 = g.nb + g.nm;  // first k bit in a_pos
-  const int b_k0 = g.nb;         // first k bit in b_pos
-  for (int64_t i = threadIdx.x; i < nklo; i += blockDim.x) {
-    s_ka[i] = deposit(i, g.a_pos, a_k0, kl);
-    s_kb[i] = deposit(i, g.b_pos, b_k0, kl);
-  }
-  __syncthreads();
+__global__ void __launch_bounds__(kBlock) k_step_naive(const __grid_constant__ StepGeom g, Operand A,
+                                                       Operand B, Output C, ModTable mods, int R,
+                                                       int64_t chunk) {
+  __shared__ NaiveSmem<SR> sm;
+  naive_tables<SR>(g, sm);
   const int q = blockIdx.y;
   const ModParams mp = mods.q[q];
-  const int64_t nc = int64_t(1) << g.rc;
-  const int64_t mask_n = (int64_t(1) << g.nn) - 1, mask_m = (int64_t(1) << g.nm) - 1;
-  for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < nc;
-       c += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t n = c & mask_n, m = (c >> g.nn) & mask_m, b = c >> (g.nn + g.nm);
-    const int64_t base_a = deposit(b, g.a_pos, 0, g.nb) | deposit(m, g.a_pos, g.nb, g.nm);
-    const int64_t base_b = deposit(b, g.b_pos, 0, g.nb) | deposit(n, g.b_pos, g.nb + g.nk, g.nn);
-    typename SR::Acc acc = SR::zero(mp);
-    for (int64_t kh = 0; kh < nkhi; ++kh) {
-      const int64_t oa = base_a | deposit(kh, g.a_pos, a_k0 + kl, g.nk - kl);
-      const int64_t ob = base_b | deposit(kh, g.b_pos, b_k0 + kl, g.nk - kl);
-      for (int64_t k = 0; k < nklo; ++k)
-        SR::mac(acc, SR::load(A, oa | s_ka[k], q), SR::load(B, ob | s_kb[k], q), mp);
-    }
-    SR::store(C, g.c_identity ? c : deposit(c, g.c_pos, 0, g.rc), q, acc, mp);
-  }
+  const int64_t E = int64_t(1) << g.rc;
+  const int64_t c0 = int64_t(blockIdx.x) * chunk;
+  const int64_t c1 = c0 + chunk < E ? c0 + chunk : E;
+  auto la = [&](int64_t e) { return SR::load(A, e, q); };
+  auto lb = [&](int64_t e) { return SR::load(B, e, q); };
+  naive_chunk<SR>(g, la, lb, C, mp, q, c0, c1, R, sm);
 }
 
 template <class SR>
 static int launch_naive_t(const StepGeom& g, const Operand& A, const Operand& B, const Output& C,
                           const ModTable& mods, int nprimes, cudaStream_t st) {
-  const int64_t nc = int64_t(1) << g.rc;
-  int64_t blocks = (nc + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
-  dim3 grid(static_cast<unsigned>(blocks), static_cast<unsigned>(nprimes));
-  k_step_naive<SR><<<grid, 256, 0, st>>>(g, A, B, C, mods);
+  const NaiveShape sh = naive_shape(g.rc, g.nk);
+  dim3 grid(static_cast<unsigned>(sh.ntasks), static_cast<unsigned>(nprimes));
+  k_step_naive<SR><<<grid, kBlock, 0, st>>>(g, A, B, C, mods, sh.R, sh.chunk);
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ECUDA;
 }
 

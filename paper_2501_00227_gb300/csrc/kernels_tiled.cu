@@ -22,48 +22,12 @@
 
 #include "kernels.h"
 #include "semiring.cuh"
+#include "tile_device.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace tn {
 namespace dev {
-
-namespace {
-
-__device__ __forceinline__ int64_t dep_bits(int64_t x, const int8_t* pos, int first, int count) {
-  int64_t r = 0;
-  for (int j = 0; j < count; ++j)
-    if ((x >> j) & 1) {
-      int p = pos[first + j];
-      if (p >= 0) r |= int64_t(1) << p;
-    }
-  return r;
-}
-
-// Per-semiring hooks of the tiled kernel on top of semiring.cuh.
-template <class SR>
-struct Tiled {
-  // multiply-add without the periodic fold (mod p folds every FOLD steps)
-  static __device__ __forceinline__ void mac(typename SR::Acc& acc, const typename SR::Val& a,
-                                             const typename SR::Val& b, const ModParams& mp) {
-    SR::mac(acc, a, b, mp);
-  }
-  static __device__ __forceinline__ void fold(typename SR::Acc&, const ModParams&) {}
-  static __device__ __forceinline__ typename SR::Val zero_val() { return SR::leaf(kOpEdge, 3); }
-};
-
-template <>
-struct Tiled<SrMod> {
-  static __device__ __forceinline__ void mac(uint64_t& acc, uint32_t a, uint32_t b, const ModParams&) {
-    acc += static_cast<uint64_t>(a) * b;
-  }
-  static __device__ __forceinline__ void fold(uint64_t& acc, const ModParams& mp) {
-    acc = fold32(acc, mp.r32);
-  }
-  static __device__ __forceinline__ uint32_t zero_val() { return 0u; }
-};
-
-}  // namespace
 
 struct TiledArgs {
   StepGeom g;
@@ -74,113 +38,30 @@ struct TiledArgs {
   int32_t tiles_m, tiles_n;
 };
 
-// FOLD: products accumulated between two folds of a mod-p accumulator
-// (1 is safe for every p < 2^31; 3 needs 2^32 mod p < 2^20).
 template <class SR, int TM, int TN, int BK, int FOLD>
-__global__ void __launch_bounds__(256) k_step_tiled(const __grid_constant__ TiledArgs args) {
+__global__ void __launch_bounds__(kBlock) k_step_tiled(const __grid_constant__ TiledArgs args) {
   constexpr int BM = 16 * TM, BN = 16 * TN;
-  using Val = typename SR::Val;
   using Acc = typename SR::Acc;
-  using T = Tiled<SR>;
   extern __shared__ __align__(16) unsigned char smem[];
-  Val* As = reinterpret_cast<Val*>(smem);                 // [BK][BM]
-  Val* Bs = As + BK * BM;                                 // [BK][BN]
-  int64_t* offAm = reinterpret_cast<int64_t*>(Bs + BK * BN);
-  int64_t* offAk = offAm + BM;
-  int64_t* offBk = offAk + BK;
-  int64_t* offBn = offBk + BK;
-
+  auto& sm = *reinterpret_cast<TileSmem<SR, TM, TN, BK>*>(smem);
   const StepGeom& g = args.g;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int split = args.split;
   const int rank = static_cast<int>(blockIdx.x) % split;
   const int tile = static_cast<int>(blockIdx.x) / split;
-  const int tm = tile / args.tiles_n, tn_ = tile % args.tiles_n;
+  const int64_t tm = tile / args.tiles_n, tn_ = tile % args.tiles_n;
   const int64_t b = blockIdx.y;
   const int q = blockIdx.z;
   const ModParams mp = args.mods.q[q];
-
   const int64_t M = int64_t(1) << g.nm, N = int64_t(1) << g.nn, K = int64_t(1) << g.nk;
-  const int64_t m0 = int64_t(tm) * BM, n0 = int64_t(tn_) * BN;
-  const int a_k0 = g.nb + g.nm, b_k0 = g.nb, b_n0 = g.nb + g.nk;
-
-  // offset tables for the low (in-tile) coordinate bits
-  const int lbm = 31 - __clz(BM), lbn = 31 - __clz(BN), lbk = 31 - __clz(BK);
-  for (int i = tid; i < BM; i += 256) offAm[i] = dep_bits(i, g.a_pos, g.nb, min(lbm, g.nm));
-  for (int i = tid; i < BN; i += 256) offBn[i] = dep_bits(i, g.b_pos, b_n0, min(lbn, g.nn));
-  for (int i = tid; i < BK; i += 256) {
-    offAk[i] = dep_bits(i, g.a_pos, a_k0, min(lbk, g.nk));
-    offBk[i] = dep_bits(i, g.b_pos, b_k0, min(lbk, g.nk));
-  }
-  // tile bases: batch bits and the high coordinate bits
-  const int64_t baseA = dep_bits(b, g.a_pos, 0, g.nb) +
-                        (g.nm > lbm ? dep_bits(m0 >> lbm, g.a_pos, g.nb + lbm, g.nm - lbm) : 0);
-  const int64_t baseB = dep_bits(b, g.b_pos, 0, g.nb) +
-                        (g.nn > lbn ? dep_bits(n0 >> lbn, g.b_pos, b_n0 + lbn, g.nn - lbn) : 0);
-
-  // k range of this split
   const int64_t kspan = K >= split ? K / split : K;
   const int64_t kbeg = int64_t(rank) * kspan;
-  const int64_t kend = kbeg + kspan;
-  __syncthreads();
 
   Acc acc[TM][TN];
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = SR::zero(mp);
+  tile_mainloop<SR, TM, TN, BK, FOLD, false>(g, args.A, args.B, mp, q, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
 
-  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
-    const int64_t kbaseA = g.nk > lbk ? dep_bits(k0 >> lbk, g.a_pos, a_k0 + lbk, g.nk - lbk) : 0;
-    const int64_t kbaseB = g.nk > lbk ? dep_bits(k0 >> lbk, g.b_pos, b_k0 + lbk, g.nk - lbk) : 0;
-    // stage A[k0 .. k0+BK)[m0 .. m0+BM) and B[k0 ..)[n0 ..) (m / n fastest)
-#pragma unroll 4
-    for (int e = tid; e < BK * BM; e += 256) {
-      const int kk = e / BM, mm = e % BM;
-      Val v = T::zero_val();
-      if (m0 + mm < M && k0 + kk < K) {
-        const int64_t off = baseA + offAm[mm] + kbaseA + offAk[kk];
-        v = SR::load(args.A, off, q);
-      }
-      As[kk * BM + mm] = v;
-    }
-#pragma unroll 4
-    for (int e = tid; e < BK * BN; e += 256) {
-      const int kk = e / BN, nn = e % BN;
-      Val v = T::zero_val();
-      if (n0 + nn < N && k0 + kk < K) {
-        const int64_t off = baseB + offBn[nn] + kbaseB + offBk[kk];
-        v = SR::load(args.B, off, q);
-      }
-      Bs[kk * BN + nn] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      Val a[TM], bv[TN];
-#pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk * BM + ty * TM + i];
-#pragma unroll
-      for (int j = 0; j < TN; ++j) bv[j] = Bs[kk * BN + tx * TN + j];
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) T::mac(acc[i][j], a[i], bv[j], mp);
-      if ((kk + 1) % FOLD == 0 || kk == BK - 1) {
-#pragma unroll
-        for (int i = 0; i < TM; ++i)
-#pragma unroll
-          for (int j = 0; j < TN; ++j) T::fold(acc[i][j], mp);
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < TM; ++i)
-#pragma unroll
-    for (int j = 0; j < TN; ++j) T::fold(acc[i][j], mp);
-
+  const int64_t m0 = tm * BM, n0 = tn_ * BN;
   const int64_t cbase = b << (g.nn + g.nm);
   if (split == 1) {
 #pragma unroll
@@ -205,7 +86,7 @@ __global__ void __launch_bounds__(256) k_step_tiled(const __grid_constant__ Tile
     for (int j = 0; j < TN; ++j) red[(ty * TM + i) * BN + tx * TN + j] = acc[i][j];
   cluster.sync();
   const int per = BM * BN / split;
-  for (int e = rank * per + tid; e < (rank + 1) * per; e += 256) {
+  for (int e = rank * per + tid; e < (rank + 1) * per; e += kBlock) {
     Acc v = red[e];
     for (int r = 0; r < split; ++r) {
       if (r == rank) continue;
@@ -224,9 +105,8 @@ __global__ void __launch_bounds__(256) k_step_tiled(const __grid_constant__ Tile
 template <class SR, int TM, int TN, int BK, int FOLD>
 static int launch_tiled_t(const TiledArgs& a, int nprimes, cudaStream_t st) {
   constexpr int BM = 16 * TM, BN = 16 * TN;
-  using Val = typename SR::Val;
   using Acc = typename SR::Acc;
-  size_t stage = sizeof(Val) * BK * (BM + BN) + sizeof(int64_t) * (BM + BN + 2 * BK);
+  size_t stage = sizeof(TileSmem<SR, TM, TN, BK>);
   size_t red = a.split > 1 ? sizeof(Acc) * BM * BN : 0;
   size_t smem = stage > red ? stage : red;
   auto kern = k_step_tiled<SR, TM, TN, BK, FOLD>;

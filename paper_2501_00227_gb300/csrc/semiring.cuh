@@ -49,6 +49,14 @@ struct ModTable {
   ModParams q[TN_MAX_PRIMES];
 };
 
+// Global loads; CG = true reads through L2 only (ld.global.cg), which the
+// persistent executor uses for tensors other CTAs wrote during the launch.
+template <bool CG, class T>
+__device__ __forceinline__ T ldg_t(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
 // ---------------------------------------------------------------- float
 struct SrF32 {
   using Val = float;
@@ -59,9 +67,10 @@ struct SrF32 {
     if (kind == kOpVertex) return e == 1 ? 1.0f : 0.0f;
     return 0.0f;
   }
+  template <bool CG = false>
   static __device__ __forceinline__ Val load(const Operand& o, int64_t e, int) {
     if (o.kind != kOpArena) return leaf(o.kind, e);
-    return static_cast<const float*>(o.p0)[e];
+    return ldg_t<CG>(static_cast<const float*>(o.p0) + e);
   }
   static __device__ __forceinline__ void mac(Acc& acc, Val a, Val b, const ModParams&) {
     acc = fmaxf(acc, a + b);
@@ -85,9 +94,10 @@ struct SrI32 {
     if (kind == kOpVertex) return e == 1 ? 1 : 0;
     return 0;
   }
+  template <bool CG = false>
   static __device__ __forceinline__ Val load(const Operand& o, int64_t e, int) {
     if (o.kind != kOpArena) return leaf(o.kind, e);
-    return static_cast<const int32_t*>(o.p0)[e];
+    return ldg_t<CG>(static_cast<const int32_t*>(o.p0) + e);
   }
   static __device__ __forceinline__ void mac(Acc& acc, Val a, Val b, const ModParams&) {
     acc = __viaddmax_s32(a, b, acc);  // max(a + b, acc)
@@ -124,9 +134,11 @@ struct SrCnt {
     if (kind == kOpVertex) return e == 1 ? CntVal{1, 1ull} : CntVal{0, 1ull};
     return CntVal{0, 1ull};
   }
+  template <bool CG = false>
   static __device__ __forceinline__ Val load(const Operand& o, int64_t e, int) {
     if (o.kind != kOpArena) return leaf(o.kind, e);
-    return CntVal{static_cast<const int32_t*>(o.p0)[e], static_cast<const uint64_t*>(o.p1)[e]};
+    return CntVal{ldg_t<CG>(static_cast<const int32_t*>(o.p0) + e),
+                  ldg_t<CG>(static_cast<const uint64_t*>(o.p1) + e)};
   }
   static __device__ __forceinline__ void mac(Acc& acc, const Val& a, const Val& b, const ModParams&) {
     int32_t s = a.v + b.v;
@@ -172,9 +184,10 @@ struct SrMod {
     if (kind == kOpEdge) return e == 3 ? 0u : 1u;
     return 1u;
   }
+  template <bool CG = false>
   static __device__ __forceinline__ Val load(const Operand& o, int64_t e, int q) {
     if (o.kind != kOpArena) return leaf(o.kind, e);
-    return static_cast<const uint32_t*>(o.p0)[q * o.prime_stride + e];
+    return ldg_t<CG>(static_cast<const uint32_t*>(o.p0) + q * o.prime_stride + e);
   }
   static __device__ __forceinline__ void mac(Acc& acc, Val a, Val b, const ModParams& mp) {
     acc = fold32(acc + static_cast<uint64_t>(a) * b, mp.r32);

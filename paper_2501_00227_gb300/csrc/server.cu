@@ -31,6 +31,7 @@ int contract_enqueue(const tn_plan_s* p, tn_semiring_t s, const dev::ModTable& m
                      cudaEvent_t* step_events);
 int decode_raw(tn_semiring_t s, const dev::ModTable& mods, int32_t nprimes,
                const unsigned char* raw, tn_result_t* out);
+size_t required_bytes(tn_plan_s* p, tn_semiring_t s, int32_t nprimes);
 }  // namespace tn
 
 namespace {
@@ -212,7 +213,7 @@ int tn_submit(tn_server_t S, tn_plan_t plan, tn_semiring_t semiring, const uint3
     if (rc != TN_OK) return rc;
     r.primes.assign(primes, primes + nprimes);
   }
-  r.bytes = tn::workspace_bytes(plan, semiring, nprimes);
+  r.bytes = tn::required_bytes(plan, semiring, nprimes);
   if (r.bytes > S->budget) return TN_ENOMEM;
   {
     std::lock_guard<std::mutex> lk(S->mu);

@@ -1,0 +1,140 @@
+// step_device.cuh -- device building blocks shared by the per-step kernels
+// and the persistent plan executor: bit-position maps and the general
+// ("naive chunk") step body with K-parallel reduction.
+//
+// A step (Sec. 4.1 of arXiv:2501.00227) computes
+//   C[b, m, n] = (+)_k A[b, m, k] (x) B[b, k, n],
+// C stored contiguously as c = n | m << nn | b << (nn + nm) (or scattered
+// through c_pos when the caller fixes the output label order).
+#pragma once
+
+#include <cstdint>
+
+#include "semiring.cuh"
+
+namespace tn {
+namespace dev {
+
+// Scatter the bits of x into the positions pos[first .. first+count).
+__device__ __forceinline__ int64_t deposit(int64_t x, const int8_t* pos, int first, int count) {
+  int64_t r = 0;
+  for (int j = 0; j < count; ++j)
+    if ((x >> j) & 1) {
+      int p = pos[first + j];
+      if (p >= 0) r |= int64_t(1) << p;
+    }
+  return r;
+}
+
+constexpr int kNaiveKLoBits = 9;    // k offsets of the low 9 bits come from a table
+constexpr int kBlock = 256;         // threads per CTA of every libtn kernel
+
+// Shared-memory scratch of one naive chunk.
+template <class SR>
+struct NaiveSmem {
+  int64_t ka[1 << kNaiveKLoBits];
+  int64_t kb[1 << kNaiveKLoBits];
+  typename SR::Acc red[kBlock / 32];
+};
+
+template <class T>
+__device__ __forceinline__ T shfl_xor_val(T v, int off) {
+  return __shfl_xor_sync(0xffffffffu, v, off);
+}
+__device__ __forceinline__ CntVal shfl_xor_val(CntVal v, int off) {
+  CntVal r;
+  r.v = __shfl_xor_sync(0xffffffffu, v.v, off);
+  r.c = __shfl_xor_sync(0xffffffffu, v.c, off);
+  return r;
+}
+
+// Fills the k-offset tables of a step (all threads of the CTA; ends with a
+// barrier).
+template <class SR>
+__device__ __forceinline__ void naive_tables(const StepGeom& g, NaiveSmem<SR>& sm) {
+  const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
+  const int a_k0 = g.nb + g.nm, b_k0 = g.nb;
+  for (int i = threadIdx.x; i < (1 << kl); i += kBlock) {
+    sm.ka[i] = deposit(i, g.a_pos, a_k0, kl);
+    sm.kb[i] = deposit(i, g.b_pos, b_k0, kl);
+  }
+  __syncthreads();
+}
+
+// Computes output entries [c_begin, c_end) of a step for prime index q.
+// R threads (a power of two, 1..256, R <= 2^nk) share each output entry:
+// each takes every R-th k, then the R partial results are merged with the
+// semiring (+) by warp shuffles (R <= 32) or through shared memory.
+// Every thread of the CTA must call this (it uses barriers when R > 32).
+template <class SR, class LoadA, class LoadB>
+__device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, LoadB loadB, const Output& C,
+                                            const ModParams& mp, int q, int64_t c_begin, int64_t c_end,
+                                            int R, NaiveSmem<SR>& sm) {
+  using Acc = typename SR::Acc;
+  const int tid = threadIdx.x;
+  const int slot = tid / R, lane = tid % R;
+  const int per_pass = kBlock / R;
+  const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
+  const int64_t nklo = int64_t(1) << kl;
+  const int64_t nkhi = int64_t(1) << (g.nk - kl);
+  const int a_k0 = g.nb + g.nm, b_k0 = g.nb;
+  const int64_t mask_n = (int64_t(1) << g.nn) - 1, mask_m = (int64_t(1) << g.nm) - 1;
+  for (int64_t cb = c_begin; cb < c_end; cb += per_pass) {
+    const int64_t c = cb + slot;
+    const bool valid = c < c_end;
+    Acc acc = SR::zero(mp);
+    if (valid) {
+      const int64_t n = c & mask_n, m = (c >> g.nn) & mask_m, b = c >> (g.nn + g.nm);
+      const int64_t base_a = deposit(b, g.a_pos, 0, g.nb) | deposit(m, g.a_pos, g.nb, g.nm);
+      const int64_t base_b = deposit(b, g.b_pos, 0, g.nb) | deposit(n, g.b_pos, g.nb + g.nk, g.nn);
+      for (int64_t kh = 0; kh < nkhi; ++kh) {
+        const int64_t oa = base_a | deposit(kh, g.a_pos, a_k0 + kl, g.nk - kl);
+        const int64_t ob = base_b | deposit(kh, g.b_pos, b_k0 + kl, g.nk - kl);
+        for (int64_t k = lane; k < nklo; k += R) SR::mac(acc, loadA(oa | sm.ka[k]), loadB(ob | sm.kb[k]), mp);
+      }
+    }
+    // merge the R partial accumulators of each output entry
+    const int rw = R < 32 ? R : 32;
+    for (int off = rw / 2; off >= 1; off >>= 1) {
+      Acc o = shfl_xor_val(acc, off);
+      SR::merge(acc, o, mp);
+    }
+    if (R > 32) {
+      if ((tid & 31) == 0) sm.red[tid >> 5] = acc;
+      __syncthreads();
+      if (lane == 0) {
+        for (int w = 1; w < R / 32; ++w) SR::merge(acc, sm.red[(tid >> 5) + w], mp);
+      }
+      __syncthreads();
+    }
+    if (valid && lane == 0) SR::store(C, g.c_identity ? c : deposit(c, g.c_pos, 0, g.rc), q, acc, mp);
+  }
+}
+
+// Host-side choice of R (threads per output entry) and of the number of
+// output entries per CTA for a naive-chunk step with E outputs and K terms.
+struct NaiveShape {
+  int R;
+  int64_t chunk;   // output entries per CTA (multiple of 256 / R)
+  int64_t ntasks;  // CTAs
+};
+
+inline NaiveShape naive_shape(int rc, int nk) {
+  NaiveShape s;
+  const int64_t E = int64_t(1) << rc, K = int64_t(1) << nk;
+  int R = 1;
+  // give each thread at least ~16 terms, but keep at least ~2^17 threads busy
+  while (R < 256 && R * 2 <= K && K / (R * 2) >= 16 && E * R < (int64_t(1) << 17)) R *= 2;
+  s.R = R;
+  const int64_t per_pass = kBlock / R;
+  // at most ~8 passes per CTA and at most 4096 CTAs
+  int64_t chunk = per_pass;
+  while (chunk * 2 <= per_pass * 8 && (E + chunk - 1) / chunk > 4096) chunk *= 2;
+  while ((E + chunk - 1) / chunk > 4096) chunk *= 2;
+  s.chunk = chunk;
+  s.ntasks = (E + chunk - 1) / chunk;
+  return s;
+}
+
+}  // namespace dev
+}  // namespace tn

@@ -86,6 +86,7 @@ struct tn_plan_s {
   int64_t arena_entries = 0;             // arena length in entries (aligned)
   uint64_t tc = 0, rwc = 0, sc = 0;
   int32_t root = -1;                     // id of the scalar result
+  void* exec_cache = nullptr;            // executor plans (exec_plan.cu)
 };
 
 namespace tn {

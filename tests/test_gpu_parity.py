@@ -197,12 +197,15 @@ def test_config1_reg20_fp32_and_counting_vs_bruteforce():
         p.close()
 
 
+@pytest.mark.parametrize("execu", ["1", "0"])
 @pytest.mark.parametrize("spec", ["reg3:100:1", "reg3:100:2", "reg3:100:3", "reg3:140:1", "reg3:140:2", "reg3:140:3"])
-def test_config2_regular_vs_oracle(spec):
+def test_config2_regular_vs_oracle(spec, execu, monkeypatch):
     """n = 100 and 140 random 3-regular graphs: tropical int32, counting
     tropical and the count mod three 31-bit primes (+ CRT).  The GPU runs the
     library's greedy order, the oracle its own order: exact semirings give the
-    same scalar for any order."""
+    same scalar for any order.  Run through the persistent executor and through
+    per-step launches."""
+    monkeypatch.setenv("TN_EXEC", execu)
     n, e = g.by_name(spec)
     primes = tn.PRIMES31[:3]
     oo = O.greedy_order(n, e, nrepeat=4, seed=1)
@@ -323,11 +326,14 @@ def test_gemm_steps_all_semirings(shape, mode, monkeypatch):
         assert np.array_equal(out[q * E:(q + 1) * E].astype(np.uint64), O.pair_modp(Am[q], LA, Bm[q], LB, LC, p))
 
 
-@pytest.mark.parametrize("mode", ["tiled", "naive"])
-def test_networks_both_kernels(mode, monkeypatch):
-    """Whole contractions with every step forced onto one kernel."""
+@pytest.mark.parametrize("execu", ["1", "0"])
+@pytest.mark.parametrize("mode", ["tiled", "naive", "auto"])
+def test_networks_both_kernels(mode, execu, monkeypatch):
+    """Whole contractions with every step forced onto one kernel, through the
+    persistent executor (one launch) and through per-step launches."""
     monkeypatch.setenv("TN_KERNEL", mode)
-    for spec in ["reg3:20:1", "ksg:5:0.8:4", "er:16:0.25:1"]:
+    monkeypatch.setenv("TN_EXEC", execu)
+    for spec in ["reg3:20:1", "ksg:5:0.8:4", "er:16:0.25:1", "empty:3", "er:20:0.12:9"]:
         n, e = g.by_name(spec)
         poly = O.bruteforce_poly(n, e)
         alpha = max(k for k, c in enumerate(poly) if c)
