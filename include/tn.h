@@ -170,6 +170,18 @@ int tn_contract_timed(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *pr
                       void *d_workspace, size_t ws_bytes, void *cuda_stream, tn_result_t *out,
                       float *step_ms, int32_t *step_kernel, uint64_t *step_ops);
 
+/* Tracing: as tn_contract through the persistent executor, and records for
+ * every executor task t, in d_trace[4t .. 4t+3] (caller device memory of
+ * 32 * tn_plan_info().exec_tasks bytes): the global timer (ns) when a CTA
+ * claimed it, when its dependencies were met, when it finished, and
+ * (SM id << 32 | CTA index).  task_step[t], task_kind[t] (0 general chunk,
+ * 1 GEMM tile, 2 final copy) and step_level[i] (dependency level of executor
+ * step i) describe the schedule; any of the three may be NULL.  Waits for the
+ * stream. */
+int tn_contract_trace(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *primes, int32_t nprimes,
+                      void *d_workspace, size_t ws_bytes, void *cuda_stream, void *d_trace,
+                      int32_t *task_step, int32_t *task_kind, int32_t *step_level, tn_result_t *out);
+
 /* One pairwise contraction (Sec. 4.1) on caller device tensors, with the
  * layout conventions above:
  *   C[c] = (+)_{s} A[a(c, s)] (x) B[b(c, s)]

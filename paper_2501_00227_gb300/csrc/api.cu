@@ -109,7 +109,7 @@ bool executor_enabled() {
 int contract_enqueue(const tn_plan_s* p, tn_semiring_t s, const ModTable& mods, int32_t nprimes,
                      void* ws, cudaStream_t st, void* d_raw, cudaEvent_t* step_events) {
   if (!step_events && executor_enabled())
-    return exec_enqueue(const_cast<tn_plan_s*>(p), s, &mods, nprimes, ws, ~size_t(0), st, d_raw);
+    return exec_enqueue(const_cast<tn_plan_s*>(p), s, &mods, nprimes, ws, ~size_t(0), st, d_raw, nullptr);
   Regions rg = regions(p, s, ws);
   uint32_t* d_status = static_cast<uint32_t*>(ws);
   int rc = cuda_rc(cudaMemsetAsync(d_status, 0, sizeof(uint32_t), st));
@@ -310,6 +310,35 @@ int tn_contract_timed(tn_plan_t plan, tn_semiring_t semiring, const uint32_t* pr
   for (auto& e : ev)
     if (e) cudaEventDestroy(e);
   if (rc) return rc;
+  return decode_raw(semiring, mods, nprimes, raw, out);
+}
+
+int tn_contract_trace(tn_plan_t plan, tn_semiring_t semiring, const uint32_t* primes,
+                      int32_t nprimes, void* d_workspace, size_t ws_bytes, void* cuda_stream,
+                      void* d_trace, int32_t* task_step, int32_t* task_kind, int32_t* step_level,
+                      tn_result_t* out) {
+  if (!plan || !out || !semiring_ok(semiring) || !d_workspace || !d_trace) return TN_EINVAL;
+  if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0) return TN_EINVAL;
+  ModTable mods;
+  int rc = make_mods(semiring, primes, nprimes, &mods);
+  if (rc) return rc;
+  if (ws_bytes < required_bytes(plan, semiring, nprimes)) return TN_ENOMEM;
+  ExecPlan* X = exec_plan_get(plan, semiring, nprimes, &rc);
+  if (!X) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  void* d_raw = static_cast<char*>(d_workspace) + 64;
+  rc = exec_enqueue(plan, semiring, &mods, nprimes, d_workspace, ws_bytes, st, d_raw, d_trace);
+  if (rc) return rc;
+  unsigned char raw[TN_RAW_BYTES];
+  rc = cuda_rc(cudaMemcpyAsync(raw, d_raw, TN_RAW_BYTES, cudaMemcpyDeviceToHost, st));
+  if (!rc) rc = cuda_rc(cudaStreamSynchronize(st));
+  if (rc) return rc;
+  for (size_t t = 0; t < X->tasks.size(); ++t) {
+    if (task_step) task_step[t] = X->tasks[t].step;
+    if (task_kind) task_kind[t] = X->tasks[t].kind;
+  }
+  if (step_level)
+    for (size_t i = 0; i < X->steps.size(); ++i) step_level[i] = X->step_level[i];
   return decode_raw(semiring, mods, nprimes, raw, out);
 }
 

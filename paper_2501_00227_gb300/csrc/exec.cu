@@ -41,6 +41,7 @@ struct ExecArgs {
   int32_t semiring;
   int32_t pad_;
   unsigned long long timeout_ns;
+  unsigned long long* trace;  // optional: 4 words per task (see tn_contract_trace)
 };
 
 constexpr uint32_t kStatusTimeout = 1u;
@@ -196,8 +197,10 @@ __global__ void __launch_bounds__(kBlock) k_exec(const __grid_constant__ ExecArg
   __shared__ ExecTask s_task;
   __shared__ int s_t, s_abort, s_last;
   const int tid = threadIdx.x;
+  unsigned long long t_claim = 0;
   for (;;) {
     if (tid == 0) {
+      if (a.trace) t_claim = global_ns();
       s_abort = ld_relaxed_u32(a.status) != 0;
       s_t = s_abort ? a.ntasks_total : atomicAdd(a.task_ctr, 1);
     }
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(kBlock) k_exec(const __grid_constant__ ExecArg
               break;
             }
             __nanosleep(ns);
-            if (ns < 1024) ns *= 2;
+            if (ns < 256) ns *= 2;
           }
         }
       }
@@ -243,6 +246,8 @@ __global__ void __launch_bounds__(kBlock) k_exec(const __grid_constant__ ExecArg
     }
     __syncthreads();
     if (s_abort) break;
+    unsigned long long t_ready = 0;
+    if (a.trace && tid == 0) t_ready = global_ns();
     if (s_task.kind == kTaskFinal) {
       exec_final(a, s_step);
     } else if (s_task.kind == kTaskNaive) {
@@ -259,6 +264,15 @@ __global__ void __launch_bounds__(kBlock) k_exec(const __grid_constant__ ExecArg
     if (tid == 0) {
       __threadfence();
       atomicAdd(a.done + s_task.step, 1);
+      if (a.trace) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        unsigned long long* tr = a.trace + 4 * static_cast<int64_t>(t);
+        tr[0] = t_claim;
+        tr[1] = t_ready;
+        tr[2] = global_ns();
+        tr[3] = (static_cast<unsigned long long>(smid) << 32) | blockIdx.x;
+      }
     }
   }
 }
@@ -318,7 +332,7 @@ size_t exec_acc_bytes(tn_semiring_t s) {
 }
 
 int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods_v, int32_t nprimes, void* ws,
-                 size_t ws_bytes, void* stream, void* d_raw) {
+                 size_t ws_bytes, void* stream, void* d_raw, void* d_trace) {
   const dev::ModTable& mods = *static_cast<const dev::ModTable*>(mods_v);
   int rc;
   ExecPlan* X = exec_plan_get(p, s, nprimes, &rc);
@@ -371,6 +385,7 @@ int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods_v, int32_t npri
   a.mods = mods;
   a.semiring = s;
   a.timeout_ns = 2000000000ull;  // 2 s per wait
+  a.trace = static_cast<unsigned long long*>(d_trace);
   switch (s) {
     case TN_TROPICAL_F32: return dev::exec_launch_t<dev::SrF32, 1>(X, a, st);
     case TN_TROPICAL_I32: return dev::exec_launch_t<dev::SrI32, 1>(X, a, st);

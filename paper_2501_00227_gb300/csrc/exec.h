@@ -52,6 +52,7 @@ struct ExecPlan {
   std::vector<ExecStep> steps;     // execution (level) order
   std::vector<int32_t> deps;
   std::vector<ExecTask> tasks;
+  std::vector<int32_t> step_level;   // dependency level of each exec step
   int64_t arena_entries = 0;
   int64_t root_off = 0;
   int32_t root_step = -1;
@@ -75,7 +76,7 @@ void exec_plans_free(tn_plan_s* p);
 
 // Enqueues one contraction through the executor (exec.cu).
 int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods, int32_t nprimes, void* ws,
-                 size_t ws_bytes, void* stream, void* d_raw);
+                 size_t ws_bytes, void* stream, void* d_raw, void* d_trace);
 
 // Bytes per accumulator / per staged value of the tiled tasks, and the
 // dynamic shared memory the executor needs (exec.cu).

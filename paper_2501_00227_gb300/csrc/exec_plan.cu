@@ -97,6 +97,8 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   std::vector<int32_t> pos(ns);
   for (int i = 0; i < ns; ++i) pos[order[i]] = i;
   X->nlevels = ns ? level[order[ns - 1]] + 1 : 0;
+  X->step_level.resize(ns);
+  for (int i = 0; i < ns; ++i) X->step_level[i] = level[order[i]];
 
   // memory: a level's outputs may only reuse memory released by earlier
   // levels; the releasing steps become (write-after-read) dependencies

@@ -83,6 +83,8 @@ def lib():
         L.tn_contract_timed.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.c_size_t, vp,
                                         ctypes.POINTER(tn_result_t), ctypes.POINTER(ctypes.c_float),
                                         i32p, ctypes.POINTER(ctypes.c_uint64)]
+        L.tn_contract_trace.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.c_size_t, vp, vp, i32p, i32p,
+                                        i32p, ctypes.POINTER(tn_result_t)]
         L.tn_result_decode.argtypes = [ctypes.c_int, u32p, i32, vp, ctypes.POINTER(tn_result_t)]
         L.tn_contract_pair.argtypes = [ctypes.c_int, u32p, i32, vp, i32p, i32, vp, i32p, i32, i32p, i32, vp, vp]
         L.tn_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
@@ -215,6 +217,21 @@ def tn_contract_timed(plan, semiring, primes, ws_ptr: int, ws_bytes: int, stream
                                    ms.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _p32(kern),
                                    ops.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))), "tn_contract_timed")
     return result_dict(r, semiring), ms, kern, ops
+
+
+def tn_contract_trace(plan, semiring, primes, ws_ptr: int, ws_bytes: int, stream: int, trace_ptr: int,
+                      ntasks: int, nsteps: int):
+    """(result dict, task_step, task_kind, step_level); the trace itself is in
+    the caller's device buffer at trace_ptr (4 uint64 per task)."""
+    pr, k = _primes(primes)
+    r = tn_result_t()
+    ts = np.zeros(ntasks, dtype=np.int32)
+    tk = np.zeros(ntasks, dtype=np.int32)
+    lv = np.zeros(nsteps, dtype=np.int32)
+    _check(lib().tn_contract_trace(plan, _sr(semiring), _u32p(pr), k, ctypes.c_void_p(ws_ptr), ws_bytes,
+                                   ctypes.c_void_p(stream), ctypes.c_void_p(trace_ptr), _p32(ts), _p32(tk),
+                                   _p32(lv), ctypes.byref(r)), "tn_contract_trace")
+    return result_dict(r, semiring), ts, tk, lv
 
 
 def tn_contract_async(plan, semiring, primes, ws_ptr: int, ws_bytes: int, stream: int, raw_ptr: int):
