@@ -78,70 +78,89 @@ struct ExecTile {
   static constexpr bool kBig = std::is_same<SR, SrI32>::value || std::is_same<SR, SrF32>::value;
 };
 
-template <class SR, int TM, int TN, int FOLD>
-__device__ __forceinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
+template <class T>
+__device__ __forceinline__ T ldcg_acc(const T* p) {
+  return __ldcg(p);
+}
+__device__ __forceinline__ CntVal ldcg_acc(const CntVal* p) {
+  CntVal v;
+  v.v = __ldcg(&p->v);
+  v.c = __ldcg(&p->c);
+  return v;
+}
+
+// Arrival on a split counter: returns (to every thread) whether this CTA is
+// the last of `split` to arrive; its writes before the call are visible to
+// that last CTA.
+__device__ __forceinline__ bool arrive_last(int32_t* ctr, int split, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    *s_flag = atomicAdd(ctr, 1) == split - 1;
+    __threadfence();
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+// Task bodies are separate (not inlined) functions so that each gets its own
+// register allocation under the kernel's 128-register bound.
+template <class SR, class Cfg, int FOLD>
+__device__ __noinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
                                                unsigned char* smem, int* s_last) {
-  constexpr int BK = 16, BM = 16 * TM, BN = 16 * TN;
+  constexpr int BM = Cfg::BM, BN = Cfg::BN, TM = Cfg::TM, TN = Cfg::TN;
   using Acc = typename SR::Acc;
-  auto& sm = *reinterpret_cast<TileSmem<SR, TM, TN, BK>*>(smem);
+  auto& sm = *reinterpret_cast<TileSmem<SR, Cfg>*>(smem);
   const StepGeom& g = st.g;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x;
+  const int grp = tid / Cfg::GT, gt = tid % Cfg::GT;
+  const int tx = gt % Cfg::WN, ty = gt / Cfg::WN;
   const int split = st.split;
   const int rank = task.local % split;
   const int64_t tile = task.local / split;
   const int64_t per_b = int64_t(st.tiles_m) * st.tiles_n;
+  const int64_t ntiles = per_b << g.nb;
   const int64_t b = tile / per_b;
   const int64_t tm = (tile % per_b) / st.tiles_n, tn_ = tile % st.tiles_n;
   const int q = task.prime;
   const ModParams mp = a.mods.q[q];
   const int64_t M = int64_t(1) << g.nm, N = int64_t(1) << g.nn, K = int64_t(1) << g.nk;
-  const int64_t kspan = K >= split ? K / split : K;
+  const int64_t kspan = split > 1 ? K / split : K;
   const int64_t kbeg = int64_t(rank) * kspan;
   const Operand A = exec_operand(a, g.a_kind, st.a_off);
   const Operand B = exec_operand(a, g.b_kind, st.b_off);
   Output C{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride};
 
   Acc acc[TM][TN];
-  tile_mainloop<SR, TM, TN, BK, FOLD, true>(g, A, B, mp, q, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
+  tile_mainloop<SR, Cfg, FOLD, true>(g, A, B, mp, q, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
+  tile_merge_groups<SR, Cfg>(acc, reinterpret_cast<Acc*>(smem), mp);
 
   const int64_t m0 = tm * BM, n0 = tn_ * BN;
   const int64_t cbase = b << (g.nn + g.nm);
   if (split > 1) {
     // publish this partial tile, then let the last CTA of the tile merge
-    Acc* part = reinterpret_cast<Acc*>(a.scratch + st.scratch_off) +
-                ((int64_t(q) * (per_b << g.nb) + tile) * split) * (BM * BN);
-    Acc* mine = part + int64_t(rank) * BM * BN;
+    Acc* part = reinterpret_cast<Acc*>(a.scratch + st.scratch_off) + ((int64_t(q) * ntiles + tile) * split) * (BM * BN);
+    if (grp == 0) {
+      Acc* mine = part + int64_t(rank) * BM * BN;
 #pragma unroll
-    for (int i = 0; i < TM; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < TN; ++j) mine[(ty * TM + i) * BN + tx * TN + j] = acc[i][j];
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      int32_t* ctr = a.arrive + st.arrive_off + int64_t(q) * (per_b << g.nb) + tile;
-      *s_last = atomicAdd(ctr, 1) == split - 1;
-      __threadfence();
+        for (int j = 0; j < TN; ++j) mine[(ty * TM + i) * BN + tx * TN + j] = acc[i][j];
     }
-    __syncthreads();
-    if (!*s_last) return;
+    if (!arrive_last(a.arrive + st.arrive_off + int64_t(q) * ntiles + tile, split, s_last)) return;
+    if (grp == 0) {
+      for (int r = 0; r < split; ++r) {
+        if (r == rank) continue;
+        const Acc* other = part + int64_t(r) * BM * BN;
 #pragma unroll
-    for (int i = 0; i < TM; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < TN; ++j)
-        for (int r = 0; r < split; ++r) {
-          if (r == rank) continue;
-          const Acc* other = part + int64_t(r) * BM * BN;
-          Acc v;
-          const int e = (ty * TM + i) * BN + tx * TN + j;
-          if constexpr (std::is_same<Acc, CntVal>::value) {
-            v.v = __ldcg(&other[e].v);
-            v.c = __ldcg(&other[e].c);
-          } else {
-            v = __ldcg(&other[e]);
-          }
-          SR::merge(acc[i][j], v, mp);
-        }
+          for (int j = 0; j < TN; ++j)
+            SR::merge(acc[i][j], ldcg_acc(other + (ty * TM + i) * BN + tx * TN + j), mp);
+      }
+    }
   }
+  if (grp != 0) return;
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int64_t m = m0 + ty * TM + i;
@@ -155,8 +174,9 @@ __device__ __forceinline__ void exec_tile_task(const ExecArgs& a, const ExecStep
 }
 
 template <class SR>
-__device__ __forceinline__ void exec_naive_task(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
-                                                unsigned char* smem) {
+__device__ __noinline__ void exec_naive_task(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
+                                                unsigned char* smem, int* s_last) {
+  using Acc = typename SR::Acc;
   auto& sm = *reinterpret_cast<NaiveSmem<SR>*>(smem);
   const StepGeom& g = st.g;
   naive_tables<SR>(g, sm);
@@ -166,11 +186,32 @@ __device__ __forceinline__ void exec_naive_task(const ExecArgs& a, const ExecSte
   const Operand B = exec_operand(a, g.b_kind, st.b_off);
   Output C{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride};
   const int64_t E = int64_t(1) << g.rc;
-  const int64_t c0 = int64_t(task.local) * st.chunk;
+  const int ks = st.ks;
+  const int64_t chunk_id = task.local / ks;
+  const int r = task.local % ks;
+  const int64_t c0 = chunk_id * st.chunk;
   const int64_t c1 = c0 + st.chunk < E ? c0 + st.chunk : E;
+  const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
+  const int64_t nkhi = int64_t(1) << (g.nk - kl);
+  const int64_t kh0 = nkhi / ks * r, kh1 = kh0 + nkhi / ks;
   auto la = [&](int64_t e) { return SR::template load<true>(A, e, q); };
   auto lb = [&](int64_t e) { return SR::template load<true>(B, e, q); };
-  naive_chunk<SR>(g, la, lb, C, mp, q, c0, c1, st.R, sm);
+  if (ks == 1) {
+    auto sink = [&](int64_t c, const Acc& v) { SR::store(C, c, q, v, mp); };
+    naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, kh0, kh1, st.R, sm);
+    return;
+  }
+  // k split: partial results to scratch; the last CTA of the chunk merges
+  Acc* part = reinterpret_cast<Acc*>(a.scratch + st.scratch_off) +
+              (int64_t(q) * st.nchunks + chunk_id) * ks * st.chunk;
+  auto sink = [&](int64_t c, const Acc& v) { part[int64_t(r) * st.chunk + (c - c0)] = v; };
+  naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, kh0, kh1, st.R, sm);
+  if (!arrive_last(a.arrive + st.arrive_off + int64_t(q) * st.nchunks + chunk_id, ks, s_last)) return;
+  for (int64_t c = c0 + threadIdx.x; c < c1; c += kBlock) {
+    Acc v = ldcg_acc(part + (c - c0));
+    for (int rr = 1; rr < ks; ++rr) SR::merge(v, ldcg_acc(part + int64_t(rr) * st.chunk + (c - c0)), mp);
+    SR::store(C, c, q, v, mp);
+  }
 }
 
 __device__ __forceinline__ void exec_final(const ExecArgs& a, const ExecStep& st) {
@@ -191,7 +232,7 @@ __device__ __forceinline__ void exec_final(const ExecArgs& a, const ExecStep& st
 }
 
 template <class SR, int FOLD>
-__global__ void __launch_bounds__(kBlock) k_exec(const __grid_constant__ ExecArgs a) {
+__global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ ExecArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ ExecStep s_step;
   __shared__ ExecTask s_task;
@@ -251,13 +292,16 @@ __global__ void __launch_bounds__(kBlock) k_exec(const __grid_constant__ ExecArg
     if (s_task.kind == kTaskFinal) {
       exec_final(a, s_step);
     } else if (s_task.kind == kTaskNaive) {
-      exec_naive_task<SR>(a, s_step, s_task, smem);
+      exec_naive_task<SR>(a, s_step, s_task, smem, &s_last);
     } else {
-      if constexpr (ExecTile<SR>::kBig) {
-        if (s_step.tile == 0) exec_tile_task<SR, 8, 8, FOLD>(a, s_step, s_task, smem, &s_last);
-        else exec_tile_task<SR, 4, 4, FOLD>(a, s_step, s_task, smem, &s_last);
-      } else {
-        exec_tile_task<SR, 4, 4, FOLD>(a, s_step, s_task, smem, &s_last);
+      switch (s_step.tile) {
+        case 0:
+          if constexpr (ExecTile<SR>::kBig) exec_tile_task<SR, TileC0, FOLD>(a, s_step, s_task, smem, &s_last);
+          break;
+        case 1: exec_tile_task<SR, TileC1, FOLD>(a, s_step, s_task, smem, &s_last); break;
+        case 2: exec_tile_task<SR, TileC2, FOLD>(a, s_step, s_task, smem, &s_last); break;
+        case 3: exec_tile_task<SR, TileC3, FOLD>(a, s_step, s_task, smem, &s_last); break;
+        default: exec_tile_task<SR, TileC4, FOLD>(a, s_step, s_task, smem, &s_last); break;
       }
     }
     __syncthreads();
@@ -279,9 +323,11 @@ __global__ void __launch_bounds__(kBlock) k_exec(const __grid_constant__ ExecArg
 
 template <class SR, int FOLD>
 static size_t smem_for() {
-  size_t t = ExecTile<SR>::kBig ? sizeof(TileSmem<SR, 8, 8, 16>) : sizeof(TileSmem<SR, 4, 4, 16>);
-  size_t n = sizeof(NaiveSmem<SR>);
-  return t > n ? t : n;
+  size_t t = tile_smem_bytes<SR, TileC1>();
+  const size_t cands[] = {ExecTile<SR>::kBig ? tile_smem_bytes<SR, TileC0>() : 0, tile_smem_bytes<SR, TileC2>(),
+                          tile_smem_bytes<SR, TileC3>(), tile_smem_bytes<SR, TileC4>(), sizeof(NaiveSmem<SR>)};
+  for (size_t c : cands) t = c > t ? c : t;
+  return t;
 }
 
 // Resident CTAs of one executor instantiation on the current device

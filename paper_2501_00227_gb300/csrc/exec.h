@@ -33,6 +33,8 @@ struct ExecStep {
   int32_t ntasks;                // tasks per prime
   int32_t dep_begin, dep_count;  // into the dependency array (exec-step indices)
   int32_t arrive_off;            // first split-K arrival counter of this step
+  int32_t ks;                    // naive: k splits per output chunk
+  int32_t nchunks;               // naive: output chunks
   int32_t pad_;
 };
 

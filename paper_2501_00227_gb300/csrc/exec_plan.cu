@@ -195,11 +195,19 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
         scratch += align_up(static_cast<size_t>(ntiles * np * split * bm * bn) * acc_bytes, 256);
       }
     } else {
-      const dev::NaiveShape sh = dev::naive_shape(S.g.rc, S.g.nk);
+      const dev::NaiveShape sh = dev::naive_shape(S.g.rc, S.g.nk, true);
       E.kernel = kKernNaive;
       E.R = sh.R;
       E.chunk = sh.chunk;
+      E.ks = sh.ks;
+      E.nchunks = static_cast<int32_t>(sh.nchunks);
       E.ntasks = static_cast<int32_t>(sh.ntasks);
+      if (sh.ks > 1) {
+        E.arrive_off = arrive;
+        arrive += static_cast<int32_t>(sh.nchunks * np);
+        E.scratch_off = static_cast<int64_t>(scratch);
+        scratch += align_up(static_cast<size_t>(sh.nchunks * np * sh.ks * sh.chunk) * acc_bytes, 256);
+      }
     }
     for (int q = 0; q < np; ++q)
       for (int t = 0; t < E.ntasks; ++t)

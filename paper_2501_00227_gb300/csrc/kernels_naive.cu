@@ -30,13 +30,17 @@ __global__ void __launch_bounds__(kBlock) k_step_naive(const __grid_constant__ S
   const int64_t c1 = c0 + chunk < E ? c0 + chunk : E;
   auto la = [&](int64_t e) { return SR::load(A, e, q); };
   auto lb = [&](int64_t e) { return SR::load(B, e, q); };
-  naive_chunk<SR>(g, la, lb, C, mp, q, c0, c1, R, sm);
+  auto sink = [&](int64_t c, const typename SR::Acc& acc) {
+    SR::store(C, g.c_identity ? c : deposit(c, g.c_pos, 0, g.rc), q, acc, mp);
+  };
+  const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
+  naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, 0, int64_t(1) << (g.nk - kl), R, sm);
 }
 
 template <class SR>
 static int launch_naive_t(const StepGeom& g, const Operand& A, const Operand& B, const Output& C,
                           const ModTable& mods, int nprimes, cudaStream_t st) {
-  const NaiveShape sh = naive_shape(g.rc, g.nk);
+  const NaiveShape sh = naive_shape(g.rc, g.nk, false);
   dim3 grid(static_cast<unsigned>(sh.ntasks), static_cast<unsigned>(nprimes));
   k_step_naive<SR><<<grid, kBlock, 0, st>>>(g, A, B, C, mods, sh.R, sh.chunk);
   return cudaGetLastError() == cudaSuccess ? TN_OK : TN_ECUDA;

@@ -1,24 +1,15 @@
-// kernels_tiled.cu -- register-blocked semiring GEMM for the wide pairwise
-// steps of a contraction (Sec. 4.1 of arXiv:2501.00227: a binary step is a
-// matricised product; here the product is over a semiring).
+// kernels_tiled.cu -- per-step launch of the register-blocked semiring GEMM
+// (tile_device.cuh) and the host-side choice of kernel, tile shape and
+// split-K for a step.
 //
-//   C[b, m, n] = (+)_k A[b, m, k] (x) B[b, k, n]
-//
-// * Operands are read in place through bit-position maps (no permute pass):
-//   the offset of A[b, m, k] is dep_b(b) + dep_m(m) + dep_k(k), each term a
-//   scatter of the coordinate's bits to the operand's label positions.  A CTA
-//   tile covers the low bits of m, n and k, so the per-tile offsets are small
-//   tables in shared memory plus one base per tile.
-// * A CTA computes a BM x BN output tile for one batch index; each of its 256
-//   threads owns a TM x TN micro-tile held in registers; k advances in chunks
-//   of BK staged through shared memory (A as [k][m], B as [k][n]).
-// * Split-K: S CTAs of one thread-block cluster share an output tile, each
-//   taking 1/S of the k range; the partial tiles are merged through
-//   distributed shared memory (DSMEM) with the semiring (+), and each CTA of
-//   the cluster writes 1/S of the tile.
+// Split-K in a per-step launch: S CTAs of one thread-block cluster share an
+// output tile, each taking 1/S of the k range; the partial tiles are merged
+// through distributed shared memory (DSMEM) with the semiring (+), and each
+// CTA of the cluster writes 1/S of the tile.
 #include <cooperative_groups.h>
-#include <cstdlib>
 #include <cuda_runtime.h>
+
+#include <cstdlib>
 
 #include "kernels.h"
 #include "semiring.cuh"
@@ -34,19 +25,20 @@ struct TiledArgs {
   Operand A, B;
   Output C;
   ModTable mods;
-  int32_t split;      // CTAs per output tile (cluster size along x)
+  int32_t split;  // CTAs per output tile (cluster size along x)
   int32_t tiles_m, tiles_n;
 };
 
-template <class SR, int TM, int TN, int BK, int FOLD>
-__global__ void __launch_bounds__(kBlock) k_step_tiled(const __grid_constant__ TiledArgs args) {
-  constexpr int BM = 16 * TM, BN = 16 * TN;
+template <class SR, class Cfg, int FOLD>
+__global__ void __launch_bounds__(kBlock, 2) k_step_tiled(const __grid_constant__ TiledArgs args) {
+  constexpr int BM = Cfg::BM, BN = Cfg::BN, TM = Cfg::TM, TN = Cfg::TN;
   using Acc = typename SR::Acc;
   extern __shared__ __align__(16) unsigned char smem[];
-  auto& sm = *reinterpret_cast<TileSmem<SR, TM, TN, BK>*>(smem);
+  auto& sm = *reinterpret_cast<TileSmem<SR, Cfg>*>(smem);
   const StepGeom& g = args.g;
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
+  const int grp = tid / Cfg::GT, gt = tid % Cfg::GT;
+  const int tx = gt % Cfg::WN, ty = gt / Cfg::WN;
   const int split = args.split;
   const int rank = static_cast<int>(blockIdx.x) % split;
   const int tile = static_cast<int>(blockIdx.x) / split;
@@ -55,15 +47,17 @@ __global__ void __launch_bounds__(kBlock) k_step_tiled(const __grid_constant__ T
   const int q = blockIdx.z;
   const ModParams mp = args.mods.q[q];
   const int64_t M = int64_t(1) << g.nm, N = int64_t(1) << g.nn, K = int64_t(1) << g.nk;
-  const int64_t kspan = K >= split ? K / split : K;
+  const int64_t kspan = split > 1 ? K / split : K;
   const int64_t kbeg = int64_t(rank) * kspan;
 
   Acc acc[TM][TN];
-  tile_mainloop<SR, TM, TN, BK, FOLD, false>(g, args.A, args.B, mp, q, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
+  tile_mainloop<SR, Cfg, FOLD, false>(g, args.A, args.B, mp, q, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
+  tile_merge_groups<SR, Cfg>(acc, reinterpret_cast<Acc*>(smem), mp);
 
   const int64_t m0 = tm * BM, n0 = tn_ * BN;
   const int64_t cbase = b << (g.nn + g.nm);
   if (split == 1) {
+    if (grp != 0) return;
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
       const int64_t m = m0 + ty * TM + i;
@@ -79,11 +73,13 @@ __global__ void __launch_bounds__(kBlock) k_step_tiled(const __grid_constant__ T
 
   // split-K: merge the partial tiles of the cluster through DSMEM
   cg::cluster_group cluster = cg::this_cluster();
-  Acc* red = reinterpret_cast<Acc*>(smem);  // [BM][BN], reuses the staging buffers
+  Acc* red = reinterpret_cast<Acc*>(smem);  // [BM][BN]
+  if (grp == 0) {
 #pragma unroll
-  for (int i = 0; i < TM; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) red[(ty * TM + i) * BN + tx * TN + j] = acc[i][j];
+      for (int j = 0; j < TN; ++j) red[(ty * TM + i) * BN + tx * TN + j] = acc[i][j];
+  }
   cluster.sync();
   const int per = BM * BN / split;
   for (int e = rank * per + tid; e < (rank + 1) * per; e += kBlock) {
@@ -99,17 +95,13 @@ __global__ void __launch_bounds__(kBlock) k_step_tiled(const __grid_constant__ T
   cluster.sync();
 }
 
-// --------------------------------------------------------------------------
-// host side
-// --------------------------------------------------------------------------
-template <class SR, int TM, int TN, int BK, int FOLD>
+template <class SR, class Cfg, int FOLD>
 static int launch_tiled_t(const TiledArgs& a, int nprimes, cudaStream_t st) {
-  constexpr int BM = 16 * TM, BN = 16 * TN;
   using Acc = typename SR::Acc;
-  size_t stage = sizeof(TileSmem<SR, TM, TN, BK>);
-  size_t red = a.split > 1 ? sizeof(Acc) * BM * BN : 0;
-  size_t smem = stage > red ? stage : red;
-  auto kern = k_step_tiled<SR, TM, TN, BK, FOLD>;
+  size_t smem = tile_smem_bytes<SR, Cfg>();
+  const size_t red = sizeof(Acc) * Cfg::BM * Cfg::BN;
+  if (a.split > 1 && red > smem) smem = red;
+  auto kern = k_step_tiled<SR, Cfg, FOLD>;
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
@@ -122,7 +114,7 @@ static int launch_tiled_t(const TiledArgs& a, int nprimes, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(a.tiles_m * a.tiles_n * a.split), static_cast<unsigned>(batch),
                      static_cast<unsigned>(nprimes));
-  cfg.blockDim = dim3(256, 1, 1);
+  cfg.blockDim = dim3(kBlock, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -136,11 +128,27 @@ static int launch_tiled_t(const TiledArgs& a, int nprimes, cudaStream_t st) {
   return e == cudaSuccess ? TN_OK : TN_ECUDA;
 }
 
-// Tile shapes (TM x TN micro-tiles on a 16 x 16 thread grid).
-//   id 0: 128 x 128 (8 x 8), id 1: 64 x 64 (4 x 4)
-int tiled_tile_bm(int tile) { return tile == 0 ? 128 : 64; }
-int tiled_tile_bn(int tile) { return tile == 0 ? 128 : 64; }
-int tiled_tile_bk(int) { return 16; }
+// Tile shapes: see TileC0..TileC4 in tile_device.cuh.
+static const int kTileBM[kNumTiles] = {TileC0::BM, TileC1::BM, TileC2::BM, TileC3::BM, TileC4::BM};
+static const int kTileBN[kNumTiles] = {TileC0::BN, TileC1::BN, TileC2::BN, TileC3::BN, TileC4::BN};
+static const int kTileBK[kNumTiles] = {TileC0::BK, TileC1::BK, TileC2::BK, TileC3::BK, TileC4::BK};
+// relative throughput of a fully used tile (register blocking, sliced-K merge)
+static const float kTileEff[kNumTiles] = {1.0f, 0.8f, 0.72f, 0.68f, 0.68f};
+
+int tiled_tile_bm(int tile) { return kTileBM[tile]; }
+int tiled_tile_bn(int tile) { return kTileBN[tile]; }
+int tiled_tile_bk(int tile) { return kTileBK[tile]; }
+
+template <class SR, int FOLD>
+static int launch_cfg(const TiledArgs& a, int tile, int nprimes, cudaStream_t st) {
+  switch (tile) {
+    case 1: return launch_tiled_t<SR, TileC1, FOLD>(a, nprimes, st);
+    case 2: return launch_tiled_t<SR, TileC2, FOLD>(a, nprimes, st);
+    case 3: return launch_tiled_t<SR, TileC3, FOLD>(a, nprimes, st);
+    case 4: return launch_tiled_t<SR, TileC4, FOLD>(a, nprimes, st);
+  }
+  return TN_EINVAL;
+}
 
 int launch_step_tiled(tn_semiring_t s, const StepGeom& g, const Operand& A, const Operand& B,
                       const Output& C, const ModTable& mods, int nprimes, int tile, int split,
@@ -158,28 +166,27 @@ int launch_step_tiled(tn_semiring_t s, const StepGeom& g, const Operand& A, cons
   a.tiles_n = static_cast<int32_t>((N + bn - 1) / bn);
   switch (s) {
     case TN_TROPICAL_F32:
-      return tile == 0 ? launch_tiled_t<SrF32, 8, 8, 16, 1>(a, 1, st)
-                       : launch_tiled_t<SrF32, 4, 4, 16, 1>(a, 1, st);
+      return tile == 0 ? launch_tiled_t<SrF32, TileC0, 1>(a, 1, st) : launch_cfg<SrF32, 1>(a, tile, 1, st);
     case TN_TROPICAL_I32:
-      return tile == 0 ? launch_tiled_t<SrI32, 8, 8, 16, 1>(a, 1, st)
-                       : launch_tiled_t<SrI32, 4, 4, 16, 1>(a, 1, st);
+      return tile == 0 ? launch_tiled_t<SrI32, TileC0, 1>(a, 1, st) : launch_cfg<SrI32, 1>(a, tile, 1, st);
     case TN_COUNTING_TROPICAL:
-      return launch_tiled_t<SrCnt, 4, 4, 16, 1>(a, 1, st);
+      return launch_cfg<SrCnt, 1>(a, tile, 1, st);
     case TN_COUNT_MODP: {
       bool small_r = true;
       for (int i = 0; i < nprimes; ++i) small_r = small_r && mods.q[i].r32 < (1u << 20);
-      return small_r ? launch_tiled_t<SrMod, 4, 4, 16, 3>(a, nprimes, st)
-                     : launch_tiled_t<SrMod, 4, 4, 16, 1>(a, nprimes, st);
+      return small_r ? launch_cfg<SrMod, 3>(a, tile, nprimes, st) : launch_cfg<SrMod, 1>(a, tile, nprimes, st);
     }
   }
   return TN_EINVAL;
 }
 
-// Heuristic kernel choice (see the step-kernel table in the design notes):
-// the tiled GEMM needs some reduction depth (nk >= 2), tiles that are not
-// mostly empty (nm, nn >= 3), a batch that fits gridDim.y and enough work to
-// beat the general kernel.  Split-K doubles until two waves of CTAs are
-// resident or the k range per CTA would drop below one BK chunk.
+// Heuristic kernel choice (the "step kernels" table of the design notes).
+// The tiled GEMM needs some reduction depth (K >= 8), an M x N extent that
+// fills at least a 16 x 64 tile, a batch that fits gridDim.y and enough work.
+// Among the tile shapes the one maximising (tile efficiency) x (useful
+// fraction of the tile) x (fraction of ~2 CTAs per SM it can occupy with
+// split-K) wins; split-K then doubles until two CTAs per SM have work, while
+// every split keeps at least 4 chunks of its k range.
 // TN_KERNEL=naive|tiled in the environment forces one path (tests).
 void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, int* tile, int* split) {
   const char* force = getenv("TN_KERNEL");
@@ -190,16 +197,31 @@ void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, i
   *split = 1;
   if (force_naive || g.nb > 15 || g.rc < 1) return;
   const int ops_bits = g.nb + g.nm + g.nn + g.nk;
-  if (!force_tiled && (ops_bits < 15 || g.nk < 2 || g.nm < 3 || g.nn < 3)) return;
+  if (!force_tiled && (ops_bits < 16 || g.nk < 3 || g.nm + g.nn < 10 || g.nm < 2 || g.nn < 2)) return;
   const bool tropical = (s == TN_TROPICAL_F32 || s == TN_TROPICAL_I32);
-  *tile = (tropical && g.nm >= 7 && g.nn >= 7) ? 0 : 1;
-  const int64_t bm = tiled_tile_bm(*tile), bn = tiled_tile_bn(*tile), bk = tiled_tile_bk(*tile);
-  const int64_t tiles = ((int64_t(1) << g.nm) + bm - 1) / bm * (((int64_t(1) << g.nn) + bn - 1) / bn) *
-                        (int64_t(1) << g.nb) * (s == TN_COUNT_MODP ? nprimes : 1);
-  const int64_t K = int64_t(1) << g.nk;
-  int sp = 1;
-  while (tiles * sp < 2 * 152 && sp < 8 && K / (2 * sp) >= bk) sp *= 2;
-  *split = sp;
+  const int64_t M = int64_t(1) << g.nm, N = int64_t(1) << g.nn, K = int64_t(1) << g.nk;
+  const int64_t batch = (int64_t(1) << g.nb) * (s == TN_COUNT_MODP ? nprimes : 1);
+  constexpr int64_t kFull = 2 * 152;
+  float best = -1.0f;
+  int best_tile = 1, best_split = 1;
+  for (int t = 0; t < kNumTiles; ++t) {
+    if (t == 0 && !tropical) continue;
+    const int64_t bm = kTileBM[t], bn = kTileBN[t], bk = kTileBK[t];
+    const int64_t tmn = (M + bm - 1) / bm, tnn = (N + bn - 1) / bn;
+    const float util = float(M) / float(tmn * bm) * float(N) / float(tnn * bn);
+    const int64_t tiles = tmn * tnn * batch;
+    int sp = 1;
+    while (tiles * sp < kFull && sp < 16 && K / (2 * sp) >= 4 * bk) sp *= 2;
+    const float par = tiles * sp >= kFull ? 1.0f : float(tiles * sp) / float(kFull);
+    const float score = kTileEff[t] * util * par;
+    if (score > best) {
+      best = score;
+      best_tile = t;
+      best_split = sp;
+    }
+  }
+  *tile = best_tile;
+  *split = best_split;
   *kernel = kKernTiled;
 }
 
@@ -207,6 +229,7 @@ int launch_step(tn_semiring_t s, const StepGeom& g, const Operand& A, const Oper
                 const Output& C, const ModTable& mods, int nprimes, cudaStream_t st, int* kernel_used) {
   int kernel, tile, split;
   pick_launch(g, s, nprimes, &kernel, &tile, &split);
+  if (split > 8) split = 8;  // portable cluster size for the per-step launch
   if (kernel_used) *kernel_used = kernel;
   if (kernel == kKernTiled && g.c_identity)
     return launch_step_tiled(s, g, A, B, C, mods, nprimes, tile, split, st);

@@ -61,22 +61,23 @@ __device__ __forceinline__ void naive_tables(const StepGeom& g, NaiveSmem<SR>& s
   __syncthreads();
 }
 
-// Computes output entries [c_begin, c_end) of a step for prime index q.
+// Computes output entries [c_begin, c_end) of a step for prime index q,
+// over the high-k blocks [kh_begin, kh_end) (each block is 2^min(nk, 9) k's).
 // R threads (a power of two, 1..256, R <= 2^nk) share each output entry:
 // each takes every R-th k, then the R partial results are merged with the
-// semiring (+) by warp shuffles (R <= 32) or through shared memory.
+// semiring (+) by warp shuffles (R <= 32) or through shared memory.  The
+// merged value of entry c goes to sink(c, acc) (called by one thread).
 // Every thread of the CTA must call this (it uses barriers when R > 32).
-template <class SR, class LoadA, class LoadB>
-__device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, LoadB loadB, const Output& C,
-                                            const ModParams& mp, int q, int64_t c_begin, int64_t c_end,
-                                            int R, NaiveSmem<SR>& sm) {
+template <class SR, class LoadA, class LoadB, class Sink>
+__device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, LoadB loadB, Sink sink,
+                                            const ModParams& mp, int64_t c_begin, int64_t c_end,
+                                            int64_t kh_begin, int64_t kh_end, int R, NaiveSmem<SR>& sm) {
   using Acc = typename SR::Acc;
   const int tid = threadIdx.x;
   const int slot = tid / R, lane = tid % R;
   const int per_pass = kBlock / R;
   const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
   const int64_t nklo = int64_t(1) << kl;
-  const int64_t nkhi = int64_t(1) << (g.nk - kl);
   const int a_k0 = g.nb + g.nm, b_k0 = g.nb;
   const int64_t mask_n = (int64_t(1) << g.nn) - 1, mask_m = (int64_t(1) << g.nm) - 1;
   for (int64_t cb = c_begin; cb < c_end; cb += per_pass) {
@@ -87,7 +88,7 @@ __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, Load
       const int64_t n = c & mask_n, m = (c >> g.nn) & mask_m, b = c >> (g.nn + g.nm);
       const int64_t base_a = deposit(b, g.a_pos, 0, g.nb) | deposit(m, g.a_pos, g.nb, g.nm);
       const int64_t base_b = deposit(b, g.b_pos, 0, g.nb) | deposit(n, g.b_pos, g.nb + g.nk, g.nn);
-      for (int64_t kh = 0; kh < nkhi; ++kh) {
+      for (int64_t kh = kh_begin; kh < kh_end; ++kh) {
         const int64_t oa = base_a | deposit(kh, g.a_pos, a_k0 + kl, g.nk - kl);
         const int64_t ob = base_b | deposit(kh, g.b_pos, b_k0 + kl, g.nk - kl);
         for (int64_t k = lane; k < nklo; k += R) SR::mac(acc, loadA(oa | sm.ka[k]), loadB(ob | sm.kb[k]), mp);
@@ -107,19 +108,23 @@ __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, Load
       }
       __syncthreads();
     }
-    if (valid && lane == 0) SR::store(C, g.c_identity ? c : deposit(c, g.c_pos, 0, g.rc), q, acc, mp);
+    if (valid && lane == 0) sink(c, acc);
   }
 }
 
-// Host-side choice of R (threads per output entry) and of the number of
-// output entries per CTA for a naive-chunk step with E outputs and K terms.
+// Host-side shape of a general ("naive") step with E = 2^rc outputs and
+// K = 2^nk terms: R threads per output entry, `chunk` outputs per task,
+// `ks` tasks sharing each chunk along k (their partial results are merged by
+// the last one to finish; ks > 1 only in the executor).
 struct NaiveShape {
   int R;
-  int64_t chunk;   // output entries per CTA (multiple of 256 / R)
-  int64_t ntasks;  // CTAs
+  int64_t chunk;    // output entries per task (multiple of 256 / R)
+  int64_t nchunks;  // output chunks
+  int ks;           // k splits per chunk
+  int64_t ntasks;   // nchunks * ks
 };
 
-inline NaiveShape naive_shape(int rc, int nk) {
+inline NaiveShape naive_shape(int rc, int nk, bool allow_ksplit) {
   NaiveShape s;
   const int64_t E = int64_t(1) << rc, K = int64_t(1) << nk;
   int R = 1;
@@ -127,12 +132,20 @@ inline NaiveShape naive_shape(int rc, int nk) {
   while (R < 256 && R * 2 <= K && K / (R * 2) >= 16 && E * R < (int64_t(1) << 17)) R *= 2;
   s.R = R;
   const int64_t per_pass = kBlock / R;
-  // at most ~8 passes per CTA and at most 4096 CTAs
+  // at most ~8 passes per task and at most 4096 chunks
   int64_t chunk = per_pass;
   while (chunk * 2 <= per_pass * 8 && (E + chunk - 1) / chunk > 4096) chunk *= 2;
   while ((E + chunk - 1) / chunk > 4096) chunk *= 2;
   s.chunk = chunk;
-  s.ntasks = (E + chunk - 1) / chunk;
+  s.nchunks = (E + chunk - 1) / chunk;
+  // split long reductions over several CTAs (whole high-k blocks each)
+  const int kl = nk < kNaiveKLoBits ? nk : kNaiveKLoBits;
+  const int64_t nkhi = int64_t(1) << (nk - kl);
+  int ks = 1;
+  while (allow_ksplit && s.nchunks * ks < 304 && ks * 2 <= nkhi && K / (int64_t(R) * ks * 2) >= 64 && ks < 256)
+    ks *= 2;
+  s.ks = ks;
+  s.ntasks = s.nchunks * ks;
   return s;
 }
 

@@ -3,13 +3,19 @@
 //
 //   C[b, m, n] = (+)_k A[b, m, k] (x) B[b, k, n]   (Sec. 4.1 of arXiv:2501.00227)
 //
-// A CTA computes a BM x BN output tile (BM = 16 TM, BN = 16 TN) for one batch
-// index; each of its 256 threads owns a TM x TN micro-tile in registers; k
-// advances in chunks of BK staged in shared memory (A as [k][m], B as
-// [k][n]).  Operands are read in place through bit-position maps: the offset
-// of A[b, m, k] is dep_b(b) + dep_m(m) + dep_k(k); the tile covers the low
-// bits of m, n and k, so in-tile offsets come from small shared tables and
-// each tile adds one base.
+// A CTA (256 threads) computes a BM x BN output tile of one batch index.  The
+// threads form KG groups of WM x WN threads; each thread owns a TM x TN
+// micro-tile in registers (BM = WM TM, BN = WN TN).  k advances in chunks of
+// BK = 16 KG staged in shared memory (A as [k][m], B as [k][n]); group g
+// consumes the k rows [16 g, 16 g + 16) of every chunk ("sliced K"), and the
+// KG partial tiles are merged with the semiring (+) at the end.  KG > 1 lets
+// small M x N tiles (32 x 32) keep 4 x 4 register blocking.
+//
+// Operands are read in place through bit-position maps: the offset of
+// A[b, m, k] is dep_b(b) + dep_m(m) + dep_k(k).  A tile covers the low bits of
+// m, n and k, so each thread's staging offsets are fixed for the whole tile
+// and only a per-chunk base (the high k bits) changes.  The next chunk is
+// prefetched into registers while the current one is computed.
 #pragma once
 
 #include "semiring.cuh"
@@ -41,38 +47,68 @@ struct Tiled<SrMod> {
   static __device__ __forceinline__ uint32_t zero_val() { return 0u; }
 };
 
-template <class SR, int TM, int TN, int BK>
-struct TileSmem {
-  static constexpr int BM = 16 * TM, BN = 16 * TN;
-  typename SR::Val As[BK * BM];
-  typename SR::Val Bs[BK * BN];
-  int64_t offAm[BM];
-  int64_t offBn[BN];
-  int64_t offAk[BK];
-  int64_t offBk[BK];
+template <int TM_, int TN_, int WM_, int WN_, int KG_, int BKG_>
+struct TileCfg {
+  static constexpr int TM = TM_, TN = TN_, WM = WM_, WN = WN_, KG = KG_;
+  static constexpr int BM = WM * TM, BN = WN * TN;
+  static constexpr int GT = WM * WN;  // threads per k group
+  static constexpr int BKG = BKG_;    // k rows per group per chunk
+  static constexpr int BK = BKG * KG; // k rows per staged chunk
+  static constexpr int EA = BK * BM / kBlock, EB = BK * BN / kBlock;  // staged elements per thread
+  static_assert(GT * KG == kBlock, "a tile uses all 256 threads");
+  static_assert(EA >= 1 && EB >= 1 && (BK * BM) % kBlock == 0 && (BK * BN) % kBlock == 0, "staging");
 };
 
-// Accumulates the tile (tm, tn) of batch b over k in [kbeg, kend) into acc.
-// FOLD: products accumulated between two folds of a mod-p accumulator
-// (1 is safe for every p < 2^31; 3 needs 2^32 mod p < 2^20).  All threads of
-// the CTA must call it.
-template <class SR, int TM, int TN, int BK, int FOLD, bool CG>
+// Tile shapes (index = ExecStep.tile / the tile argument of the launchers).
+// Every shape stages 4 A and 4 B elements per thread and chunk.
+using TileC0 = TileCfg<8, 8, 16, 16, 1, 8>;   // 128 x 128, BK 8, tropical only
+using TileC1 = TileCfg<4, 4, 16, 16, 1, 16>;  // 64 x 64, BK 16
+using TileC2 = TileCfg<4, 4, 8, 8, 4, 8>;     // 32 x 32, sliced K 4 x 8
+using TileC3 = TileCfg<4, 4, 4, 16, 4, 8>;    // 16 x 64, sliced K 4 x 8
+using TileC4 = TileCfg<4, 4, 16, 4, 4, 8>;    // 64 x 16, sliced K 4 x 8
+constexpr int kNumTiles = 5;
+
+template <class SR, class C>
+struct TileSmem {
+  typename SR::Val As[C::BK * C::BM];
+  typename SR::Val Bs[C::BK * C::BN];
+  int64_t offAm[C::BM];
+  int64_t offBn[C::BN];
+  int64_t offAk[C::BK];
+  int64_t offBk[C::BK];
+};
+
+template <int X>
+struct Log2 {
+  static constexpr int v = X <= 1 ? 0 : 1 + Log2<X / 2>::v;
+};
+template <>
+struct Log2<1> {
+  static constexpr int v = 0;
+};
+
+// Accumulates tile (tm, tn) of batch b over k in [kbeg, kend) into acc (of
+// the calling thread's group; the partial tiles of the KG groups are NOT yet
+// merged -- see tile_merge_groups).  FOLD: mod-p products accumulated between
+// two folds (1 is safe for every p < 2^31; 3 needs 2^32 mod p < 2^20).  All
+// threads of the CTA must call it.
+template <class SR, class C, int FOLD, bool CG>
 __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& A, const Operand& B,
                                               const ModParams& mp, int q, int64_t b, int64_t tm,
                                               int64_t tn_, int64_t kbeg, int64_t kend,
-                                              TileSmem<SR, TM, TN, BK>& sm,
-                                              typename SR::Acc (&acc)[TM][TN]) {
-  constexpr int BM = 16 * TM, BN = 16 * TN;
+                                              TileSmem<SR, C>& sm,
+                                              typename SR::Acc (&acc)[C::TM][C::TN]) {
   using Val = typename SR::Val;
   using T = Tiled<SR>;
+  constexpr int BM = C::BM, BN = C::BN, BK = C::BK, TM = C::TM, TN = C::TN;
+  constexpr int lbm = Log2<BM>::v, lbn = Log2<BN>::v, lbk = Log2<BK>::v;
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
+  const int grp = tid / C::GT, gt = tid % C::GT;
+  const int tx = gt % C::WN, ty = gt / C::WN;
   const int64_t M = int64_t(1) << g.nm, N = int64_t(1) << g.nn, K = int64_t(1) << g.nk;
   const int64_t m0 = tm * BM, n0 = tn_ * BN;
   const int a_k0 = g.nb + g.nm, b_k0 = g.nb, b_n0 = g.nb + g.nk;
-  constexpr int lbm = (BM >= 128) ? 7 : (BM >= 64 ? 6 : (BM >= 32 ? 5 : 4));
-  constexpr int lbn = (BN >= 128) ? 7 : (BN >= 64 ? 6 : (BN >= 32 ? 5 : 4));
-  constexpr int lbk = (BK >= 32) ? 5 : (BK >= 16 ? 4 : 3);
+
   for (int i = tid; i < BM; i += kBlock) sm.offAm[i] = deposit(i, g.a_pos, g.nb, min(lbm, g.nm));
   for (int i = tid; i < BN; i += kBlock) sm.offBn[i] = deposit(i, g.b_pos, b_n0, min(lbn, g.nn));
   for (int i = tid; i < BK; i += kBlock) {
@@ -85,49 +121,109 @@ __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& 
                         (g.nn > lbn ? deposit(n0 >> lbn, g.b_pos, b_n0 + lbn, g.nn - lbn) : 0);
   __syncthreads();
 
+  // this thread's staging slots: element e = tid + 256 j of the chunk; the
+  // entry offset inside the operand (< 2^30), or -1 for padding
+  int32_t offA[C::EA], offB[C::EB];
+  const int64_t kvalid = K < BK ? K : BK;  // k rows that exist inside a chunk
+#pragma unroll
+  for (int j = 0; j < C::EA; ++j) {
+    const int e = tid + kBlock * j, kk = e / BM, mm = e % BM;
+    const bool ok = (m0 + mm < M) && (kk < kvalid);
+    offA[j] = ok ? static_cast<int32_t>(baseA + sm.offAm[mm] + sm.offAk[kk]) : -1;
+  }
+#pragma unroll
+  for (int j = 0; j < C::EB; ++j) {
+    const int e = tid + kBlock * j, kk = e / BN, nn = e % BN;
+    const bool ok = (n0 + nn < N) && (kk < kvalid);
+    offB[j] = ok ? static_cast<int32_t>(baseB + sm.offBn[nn] + sm.offBk[kk]) : -1;
+  }
+
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = SR::zero(mp);
 
+  Val ra[C::EA], rb[C::EB];
+  auto fetch = [&](int64_t k0) {
+    const int64_t kA = g.nk > lbk ? deposit(k0 >> lbk, g.a_pos, a_k0 + lbk, g.nk - lbk) : 0;
+    const int64_t kB = g.nk > lbk ? deposit(k0 >> lbk, g.b_pos, b_k0 + lbk, g.nk - lbk) : 0;
+#pragma unroll
+    for (int j = 0; j < C::EA; ++j) ra[j] = offA[j] >= 0 ? SR::template load<CG>(A, offA[j] + kA, q) : T::zero_val();
+#pragma unroll
+    for (int j = 0; j < C::EB; ++j) rb[j] = offB[j] >= 0 ? SR::template load<CG>(B, offB[j] + kB, q) : T::zero_val();
+  };
+  if (kbeg < kend) fetch(kbeg);
   for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
-    const int64_t kbaseA = g.nk > lbk ? deposit(k0 >> lbk, g.a_pos, a_k0 + lbk, g.nk - lbk) : 0;
-    const int64_t kbaseB = g.nk > lbk ? deposit(k0 >> lbk, g.b_pos, b_k0 + lbk, g.nk - lbk) : 0;
-#pragma unroll 4
-    for (int e = tid; e < BK * BM; e += kBlock) {
-      const int kk = e / BM, mm = e % BM;
-      Val v = T::zero_val();
-      if (m0 + mm < M && k0 + kk < K) v = SR::template load<CG>(A, baseA + sm.offAm[mm] + kbaseA + sm.offAk[kk], q);
-      sm.As[kk * BM + mm] = v;
-    }
-#pragma unroll 4
-    for (int e = tid; e < BK * BN; e += kBlock) {
-      const int kk = e / BN, nn = e % BN;
-      Val v = T::zero_val();
-      if (n0 + nn < N && k0 + kk < K) v = SR::template load<CG>(B, baseB + sm.offBn[nn] + kbaseB + sm.offBk[kk], q);
-      sm.Bs[kk * BN + nn] = v;
-    }
+#pragma unroll
+    for (int j = 0; j < C::EA; ++j) sm.As[tid + kBlock * j] = ra[j];
+#pragma unroll
+    for (int j = 0; j < C::EB; ++j) sm.Bs[tid + kBlock * j] = rb[j];
     __syncthreads();
+    if (k0 + BK < kend) fetch(k0 + BK);  // loads in flight during the compute below
+    const Val* Ag = sm.As + grp * C::BKG * BM;
+    const Val* Bg = sm.Bs + grp * C::BKG * BN;
+    // the k rows of a chunk in groups of FOLD (mod p folds after each group)
+#pragma unroll 2
+    for (int k1 = 0; k1 < C::BKG; k1 += FOLD) {
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      Val a[TM], bv[TN];
+      for (int k2 = 0; k2 < FOLD; ++k2) {
+        const int kk = k1 + k2;
+        if (FOLD > 1 && kk >= C::BKG) break;
+        Val a[TM], bv[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = sm.As[kk * BM + ty * TM + i];
+        for (int i = 0; i < TM; ++i) a[i] = Ag[kk * BM + ty * TM + i];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) bv[j] = sm.Bs[kk * BN + tx * TN + j];
-#pragma unroll
-      for (int i = 0; i < TM; ++i)
-#pragma unroll
-        for (int j = 0; j < TN; ++j) T::mac(acc[i][j], a[i], bv[j], mp);
-      if ((kk + 1) % FOLD == 0 || kk == BK - 1) {
+        for (int j = 0; j < TN; ++j) bv[j] = Bg[kk * BN + tx * TN + j];
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
-          for (int j = 0; j < TN; ++j) T::fold(acc[i][j], mp);
+          for (int j = 0; j < TN; ++j) T::mac(acc[i][j], a[i], bv[j], mp);
       }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) T::fold(acc[i][j], mp);
     }
     __syncthreads();
   }
+}
+
+// Merges the KG partial tiles into group 0 (through shared memory `red`,
+// KG-1 tiles of BM x BN accumulators).  Afterwards the threads of group 0
+// hold the CTA's tile.  All threads must call it.
+template <class SR, class C>
+__device__ __forceinline__ void tile_merge_groups(typename SR::Acc (&acc)[C::TM][C::TN],
+                                                  typename SR::Acc* red, const ModParams& mp) {
+  if constexpr (C::KG > 1) {
+    const int tid = threadIdx.x;
+    const int grp = tid / C::GT, gt = tid % C::GT;
+    const int tx = gt % C::WN, ty = gt / C::WN;
+    if (grp > 0) {
+#pragma unroll
+      for (int i = 0; i < C::TM; ++i)
+#pragma unroll
+        for (int j = 0; j < C::TN; ++j)
+          red[(grp - 1) * C::BM * C::BN + (ty * C::TM + i) * C::BN + tx * C::TN + j] = acc[i][j];
+    }
+    __syncthreads();
+    if (grp == 0) {
+      for (int r = 0; r < C::KG - 1; ++r)
+#pragma unroll
+        for (int i = 0; i < C::TM; ++i)
+#pragma unroll
+          for (int j = 0; j < C::TN; ++j)
+            SR::merge(acc[i][j], red[r * C::BM * C::BN + (ty * C::TM + i) * C::BN + tx * C::TN + j], mp);
+    }
+    __syncthreads();
+  }
+}
+
+// Shared memory a tile needs: staging, or the group-merge buffer.
+template <class SR, class C>
+constexpr size_t tile_smem_bytes() {
+  return sizeof(TileSmem<SR, C>) > sizeof(typename SR::Acc) * (C::KG - 1) * C::BM * C::BN
+             ? sizeof(TileSmem<SR, C>)
+             : sizeof(typename SR::Acc) * (C::KG - 1) * C::BM * C::BN;
 }
 
 }  // namespace dev
