@@ -49,6 +49,21 @@ struct ModTable {
   ModParams q[TN_MAX_PRIMES];
 };
 
+// Asynchronous global -> shared copies (cp.async, 4 or 8 bytes).
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Global loads; CG = true reads through L2 only (ld.global.cg), which the
 // persistent executor uses for tensors other CTAs wrote during the launch.
 template <bool CG, class T>
@@ -71,6 +86,9 @@ struct SrF32 {
   static __device__ __forceinline__ Val load(const Operand& o, int64_t e, int) {
     if (o.kind != kOpArena) return leaf(o.kind, e);
     return ldg_t<CG>(static_cast<const float*>(o.p0) + e);
+  }
+  static __device__ __forceinline__ void copy_async(Val* dst, const Operand& o, int64_t e, int) {
+    cp_async4(dst, static_cast<const float*>(o.p0) + e);
   }
   static __device__ __forceinline__ void mac(Acc& acc, Val a, Val b, const ModParams&) {
     acc = fmaxf(acc, a + b);
@@ -99,6 +117,9 @@ struct SrI32 {
     if (o.kind != kOpArena) return leaf(o.kind, e);
     return ldg_t<CG>(static_cast<const int32_t*>(o.p0) + e);
   }
+  static __device__ __forceinline__ void copy_async(Val* dst, const Operand& o, int64_t e, int) {
+    cp_async4(dst, static_cast<const int32_t*>(o.p0) + e);
+  }
   static __device__ __forceinline__ void mac(Acc& acc, Val a, Val b, const ModParams&) {
     acc = __viaddmax_s32(a, b, acc);  // max(a + b, acc)
   }
@@ -120,7 +141,7 @@ __device__ __forceinline__ uint64_t sat_add_u64(uint64_t a, uint64_t b) {
   return s < a ? ~0ull : s;
 }
 
-struct CntVal {
+struct __align__(16) CntVal {
   int32_t v;
   uint64_t c;
 };
@@ -139,6 +160,10 @@ struct SrCnt {
     if (o.kind != kOpArena) return leaf(o.kind, e);
     return CntVal{ldg_t<CG>(static_cast<const int32_t*>(o.p0) + e),
                   ldg_t<CG>(static_cast<const uint64_t*>(o.p1) + e)};
+  }
+  static __device__ __forceinline__ void copy_async(Val* dst, const Operand& o, int64_t e, int) {
+    cp_async4(&dst->v, static_cast<const int32_t*>(o.p0) + e);
+    cp_async8(&dst->c, static_cast<const uint64_t*>(o.p1) + e);
   }
   static __device__ __forceinline__ void mac(Acc& acc, const Val& a, const Val& b, const ModParams&) {
     int32_t s = a.v + b.v;
@@ -188,6 +213,9 @@ struct SrMod {
   static __device__ __forceinline__ Val load(const Operand& o, int64_t e, int q) {
     if (o.kind != kOpArena) return leaf(o.kind, e);
     return ldg_t<CG>(static_cast<const uint32_t*>(o.p0) + q * o.prime_stride + e);
+  }
+  static __device__ __forceinline__ void copy_async(Val* dst, const Operand& o, int64_t e, int q) {
+    cp_async4(dst, static_cast<const uint32_t*>(o.p0) + q * o.prime_stride + e);
   }
   static __device__ __forceinline__ void mac(Acc& acc, Val a, Val b, const ModParams& mp) {
     acc = fold32(acc + static_cast<uint64_t>(a) * b, mp.r32);

@@ -91,7 +91,19 @@ __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, Load
       for (int64_t kh = kh_begin; kh < kh_end; ++kh) {
         const int64_t oa = base_a | deposit(kh, g.a_pos, a_k0 + kl, g.nk - kl);
         const int64_t ob = base_b | deposit(kh, g.b_pos, b_k0 + kl, g.nk - kl);
-        for (int64_t k = lane; k < nklo; k += R) SR::mac(acc, loadA(oa | sm.ka[k]), loadB(ob | sm.kb[k]), mp);
+        int64_t k = lane;
+        // four independent loads in flight per operand before the multiply-adds
+        for (; k + 3 * R < nklo; k += 4 * R) {
+          const auto a0 = loadA(oa | sm.ka[k]), a1 = loadA(oa | sm.ka[k + R]);
+          const auto a2 = loadA(oa | sm.ka[k + 2 * R]), a3 = loadA(oa | sm.ka[k + 3 * R]);
+          const auto b0 = loadB(ob | sm.kb[k]), b1 = loadB(ob | sm.kb[k + R]);
+          const auto b2 = loadB(ob | sm.kb[k + 2 * R]), b3 = loadB(ob | sm.kb[k + 3 * R]);
+          SR::mac(acc, a0, b0, mp);
+          SR::mac(acc, a1, b1, mp);
+          SR::mac(acc, a2, b2, mp);
+          SR::mac(acc, a3, b3, mp);
+        }
+        for (; k < nklo; k += R) SR::mac(acc, loadA(oa | sm.ka[k]), loadB(ob | sm.kb[k]), mp);
       }
     }
     // merge the R partial accumulators of each output entry
@@ -142,7 +154,7 @@ inline NaiveShape naive_shape(int rc, int nk, bool allow_ksplit) {
   const int kl = nk < kNaiveKLoBits ? nk : kNaiveKLoBits;
   const int64_t nkhi = int64_t(1) << (nk - kl);
   int ks = 1;
-  while (allow_ksplit && s.nchunks * ks < 304 && ks * 2 <= nkhi && K / (int64_t(R) * ks * 2) >= 64 && ks < 256)
+  while (allow_ksplit && s.nchunks * ks < 304 && ks * 2 <= nkhi && K / (int64_t(R) * ks * 2) >= 16 && ks < 256)
     ks *= 2;
   s.ks = ks;
   s.ntasks = s.nchunks * ks;

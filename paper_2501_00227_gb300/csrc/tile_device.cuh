@@ -6,16 +6,16 @@
 // A CTA (256 threads) computes a BM x BN output tile of one batch index.  The
 // threads form KG groups of WM x WN threads; each thread owns a TM x TN
 // micro-tile in registers (BM = WM TM, BN = WN TN).  k advances in chunks of
-// BK = 16 KG staged in shared memory (A as [k][m], B as [k][n]); group g
-// consumes the k rows [16 g, 16 g + 16) of every chunk ("sliced K"), and the
-// KG partial tiles are merged with the semiring (+) at the end.  KG > 1 lets
-// small M x N tiles (32 x 32) keep 4 x 4 register blocking.
+// BK = BKG KG staged in shared memory (A as [k][m], B as [k][n]) through a
+// three-stage cp.async pipeline; group g consumes the k rows [BKG g, BKG g +
+// BKG) of every chunk ("sliced K"), and the KG partial tiles are merged with
+// the semiring (+) at the end.  KG > 1 lets small M x N tiles (32 x 32) keep
+// 4 x 4 register blocking.
 //
 // Operands are read in place through bit-position maps: the offset of
 // A[b, m, k] is dep_b(b) + dep_m(m) + dep_k(k).  A tile covers the low bits of
 // m, n and k, so each thread's staging offsets are fixed for the whole tile
-// and only a per-chunk base (the high k bits) changes.  The next chunk is
-// prefetched into registers while the current one is computed.
+// and only a per-chunk base (the high k bits) changes.
 #pragma once
 
 #include "semiring.cuh"
@@ -68,15 +68,36 @@ using TileC3 = TileCfg<4, 4, 4, 16, 4, 8>;    // 16 x 64, sliced K 4 x 8
 using TileC4 = TileCfg<4, 4, 16, 4, 4, 8>;    // 64 x 16, sliced K 4 x 8
 constexpr int kNumTiles = 5;
 
+constexpr int kStages = 3;  // cp.async pipeline depth of the tile main loop
+
 template <class SR, class C>
 struct TileSmem {
-  typename SR::Val As[C::BK * C::BM];
-  typename SR::Val Bs[C::BK * C::BN];
+  typename SR::Val As[kStages][C::BK * C::BM];
+  typename SR::Val Bs[kStages][C::BK * C::BN];
   int64_t offAm[C::BM];
   int64_t offBn[C::BN];
   int64_t offAk[C::BK];
   int64_t offBk[C::BK];
 };
+
+// Fragment of T consecutive 4-byte values from shared memory (16-byte
+// vector loads when T is a multiple of 4; the address is 16-byte aligned).
+template <int T, class V>
+__device__ __forceinline__ void load_frag(const V* p, V (&out)[T]) {
+  if constexpr (sizeof(V) == 4 && T % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < T; i += 4) {
+      const uint4 w = *reinterpret_cast<const uint4*>(p + i);
+      out[i] = __builtin_bit_cast(V, w.x);
+      out[i + 1] = __builtin_bit_cast(V, w.y);
+      out[i + 2] = __builtin_bit_cast(V, w.z);
+      out[i + 3] = __builtin_bit_cast(V, w.w);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < T; ++i) out[i] = p[i];
+  }
+}
 
 template <int X>
 struct Log2 {
@@ -143,25 +164,54 @@ __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& 
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = SR::zero(mp);
 
-  Val ra[C::EA], rb[C::EB];
-  auto fetch = [&](int64_t k0) {
+  // padding slots (outside M / N / K) hold the semiring zero in every stage;
+  // the copies below never write them
+#pragma unroll
+  for (int j = 0; j < C::EA; ++j)
+    if (offA[j] < 0)
+      for (int st = 0; st < kStages; ++st) sm.As[st][tid + kBlock * j] = T::zero_val();
+#pragma unroll
+  for (int j = 0; j < C::EB; ++j)
+    if (offB[j] < 0)
+      for (int st = 0; st < kStages; ++st) sm.Bs[st][tid + kBlock * j] = T::zero_val();
+
+  // stage the chunk starting at k0 into buffer st: cp.async for stored
+  // operands, plain loads for leaves generated on the fly
+  const bool a_async = A.kind == kOpArena, b_async = B.kind == kOpArena;
+  auto issue = [&](int st, int64_t k0) {
     const int64_t kA = g.nk > lbk ? deposit(k0 >> lbk, g.a_pos, a_k0 + lbk, g.nk - lbk) : 0;
     const int64_t kB = g.nk > lbk ? deposit(k0 >> lbk, g.b_pos, b_k0 + lbk, g.nk - lbk) : 0;
 #pragma unroll
-    for (int j = 0; j < C::EA; ++j) ra[j] = offA[j] >= 0 ? SR::template load<CG>(A, offA[j] + kA, q) : T::zero_val();
+    for (int j = 0; j < C::EA; ++j)
+      if (offA[j] >= 0) {
+        if (a_async) SR::copy_async(&sm.As[st][tid + kBlock * j], A, offA[j] + kA, q);
+        else sm.As[st][tid + kBlock * j] = SR::template load<CG>(A, offA[j] + kA, q);
+      }
 #pragma unroll
-    for (int j = 0; j < C::EB; ++j) rb[j] = offB[j] >= 0 ? SR::template load<CG>(B, offB[j] + kB, q) : T::zero_val();
+    for (int j = 0; j < C::EB; ++j)
+      if (offB[j] >= 0) {
+        if (b_async) SR::copy_async(&sm.Bs[st][tid + kBlock * j], B, offB[j] + kB, q);
+        else sm.Bs[st][tid + kBlock * j] = SR::template load<CG>(B, offB[j] + kB, q);
+      }
   };
-  if (kbeg < kend) fetch(kbeg);
+#pragma unroll
+  for (int st = 0; st < kStages - 1; ++st) {
+    if (kbeg + st * BK < kend) issue(st, kbeg + st * BK);
+    cp_async_commit();
+  }
+  int cur = 0;
   for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
-#pragma unroll
-    for (int j = 0; j < C::EA; ++j) sm.As[tid + kBlock * j] = ra[j];
-#pragma unroll
-    for (int j = 0; j < C::EB; ++j) sm.Bs[tid + kBlock * j] = rb[j];
+    cp_async_wait<kStages - 2>();
     __syncthreads();
-    if (k0 + BK < kend) fetch(k0 + BK);  // loads in flight during the compute below
-    const Val* Ag = sm.As + grp * C::BKG * BM;
-    const Val* Bg = sm.Bs + grp * C::BKG * BN;
+    {
+      // refill the buffer computed on in the previous iteration
+      const int64_t kn = k0 + (kStages - 1) * BK;
+      const int nxt = (cur + kStages - 1) % kStages;
+      if (kn < kend) issue(nxt, kn);
+      cp_async_commit();
+    }
+    const Val* Ag = sm.As[cur] + grp * C::BKG * BM;
+    const Val* Bg = sm.Bs[cur] + grp * C::BKG * BN;
     // the k rows of a chunk in groups of FOLD (mod p folds after each group)
 #pragma unroll 2
     for (int k1 = 0; k1 < C::BKG; k1 += FOLD) {
@@ -170,10 +220,8 @@ __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& 
         const int kk = k1 + k2;
         if (FOLD > 1 && kk >= C::BKG) break;
         Val a[TM], bv[TN];
-#pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = Ag[kk * BM + ty * TM + i];
-#pragma unroll
-        for (int j = 0; j < TN; ++j) bv[j] = Bg[kk * BN + tx * TN + j];
+        load_frag<TM>(Ag + kk * BM + ty * TM, a);
+        load_frag<TN>(Bg + kk * BN + tx * TN, bv);
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -184,8 +232,10 @@ __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& 
 #pragma unroll
         for (int j = 0; j < TN; ++j) T::fold(acc[i][j], mp);
     }
-    __syncthreads();
+    cur = (cur + 1) % kStages;
   }
+  cp_async_wait<0>();
+  __syncthreads();
 }
 
 // Merges the KG partial tiles into group 0 (through shared memory `red`,
