@@ -98,6 +98,8 @@ typedef struct {
     uint64_t exec_table_bytes;  /* step/task tables uploaded once per plan and device */
     int32_t exec_tasks;         /* tasks of one executor launch (this semiring) */
     int32_t exec_levels;        /* dependency levels of the steps */
+    int32_t exec_grid;          /* CTAs of the last executor launch (0 before the first) */
+    int32_t exec_smem;          /* dynamic shared memory per CTA of that launch, bytes */
 } tn_plan_info_t;
 
 /* Result of one contraction.

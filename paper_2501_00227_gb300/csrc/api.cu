@@ -236,6 +236,8 @@ int tn_plan_info(tn_plan_t plan, tn_semiring_t semiring, int32_t nprimes, tn_pla
   out->exec_table_bytes = X->table_bytes;
   out->exec_tasks = static_cast<int32_t>(X->tasks.size());
   out->exec_levels = X->nlevels;
+  out->exec_grid = X->grid;
+  out->exec_smem = static_cast<int32_t>(X->smem);
   return TN_OK;
 }
 

@@ -68,12 +68,17 @@ using TileC3 = TileCfg<4, 4, 4, 16, 4, 8>;    // 16 x 64, sliced K 4 x 8
 using TileC4 = TileCfg<4, 4, 16, 4, 4, 8>;    // 64 x 16, sliced K 4 x 8
 constexpr int kNumTiles = 5;
 
-constexpr int kStages = 3;  // cp.async pipeline depth of the tile main loop
+// cp.async pipeline depth of the tile main loop: three stages for 4-byte
+// elements, two for the 16-byte (max, count) pairs
+template <class SR>
+struct Stages {
+  static constexpr int v = sizeof(typename SR::Val) <= 4 ? 3 : 2;
+};
 
 template <class SR, class C>
 struct TileSmem {
-  typename SR::Val As[kStages][C::BK * C::BM];
-  typename SR::Val Bs[kStages][C::BK * C::BN];
+  typename SR::Val As[Stages<SR>::v][C::BK * C::BM];
+  typename SR::Val Bs[Stages<SR>::v][C::BK * C::BN];
   int64_t offAm[C::BM];
   int64_t offBn[C::BN];
   int64_t offAk[C::BK];
@@ -121,6 +126,7 @@ __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& 
                                               typename SR::Acc (&acc)[C::TM][C::TN]) {
   using Val = typename SR::Val;
   using T = Tiled<SR>;
+  constexpr int kStages = Stages<SR>::v;
   constexpr int BM = C::BM, BN = C::BN, BK = C::BK, TM = C::TM, TN = C::TN;
   constexpr int lbm = Log2<BM>::v, lbn = Log2<BN>::v, lbk = Log2<BK>::v;
   const int tid = threadIdx.x;

@@ -39,7 +39,8 @@ class tn_plan_info_t(ctypes.Structure):
                 ("tc", ctypes.c_uint64), ("sc_elems", ctypes.c_uint64), ("rwc", ctypes.c_uint64),
                 ("peak_bytes", ctypes.c_uint64 * 4), ("nsteps", ctypes.c_int32),
                 ("nlaunch_steps", ctypes.c_int32), ("exec_table_bytes", ctypes.c_uint64),
-                ("exec_tasks", ctypes.c_int32), ("exec_levels", ctypes.c_int32)]
+                ("exec_tasks", ctypes.c_int32), ("exec_levels", ctypes.c_int32),
+                ("exec_grid", ctypes.c_int32), ("exec_smem", ctypes.c_int32)]
 
 
 class tn_result_t(ctypes.Structure):
@@ -189,7 +190,8 @@ def tn_plan_info(plan, semiring=TN_TROPICAL_I32, nprimes: int = 1) -> dict:
             "tc": int(info.tc), "sc": int(info.sc_elems), "rwc": int(info.rwc),
             "peak_bytes": [int(x) for x in info.peak_bytes], "nsteps": int(info.nsteps),
             "nlaunch_steps": int(info.nlaunch_steps), "exec_table_bytes": int(info.exec_table_bytes),
-            "exec_tasks": int(info.exec_tasks), "exec_levels": int(info.exec_levels)}
+            "exec_tasks": int(info.exec_tasks), "exec_levels": int(info.exec_levels),
+            "exec_grid": int(info.exec_grid), "exec_smem": int(info.exec_smem)}
 
 
 def tn_plan_destroy(plan):
