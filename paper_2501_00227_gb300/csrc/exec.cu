@@ -132,7 +132,10 @@ __device__ __noinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& s
   Output C{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride};
 
   Acc acc[TM][TN];
-  tile_mainloop<SR, Cfg, FOLD, true>(g, A, B, mp, q, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
+  if constexpr (std::is_same<SR, SrCnt>::value)
+    tile_mainloop_counting<Cfg, true>(g, A, B, mp, b, tm, tn_, kbeg, kbeg + kspan, smem, acc);
+  else
+    tile_mainloop<SR, Cfg, FOLD, true>(g, A, B, mp, q, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
   tile_merge_groups<SR, Cfg>(acc, reinterpret_cast<Acc*>(smem), mp);
 
   const int64_t m0 = tm * BM, n0 = tn_ * BN;

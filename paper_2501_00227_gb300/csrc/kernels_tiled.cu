@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdlib>
+#include <type_traits>
 
 #include "kernels.h"
 #include "semiring.cuh"
@@ -51,7 +52,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_step_tiled(const __grid_constant_
   const int64_t kbeg = int64_t(rank) * kspan;
 
   Acc acc[TM][TN];
-  tile_mainloop<SR, Cfg, FOLD, false>(g, args.A, args.B, mp, q, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
+  if constexpr (std::is_same<SR, SrCnt>::value)
+    tile_mainloop_counting<Cfg, false>(g, args.A, args.B, mp, b, tm, tn_, kbeg, kbeg + kspan, smem, acc);
+  else
+    tile_mainloop<SR, Cfg, FOLD, false>(g, args.A, args.B, mp, q, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
   tile_merge_groups<SR, Cfg>(acc, reinterpret_cast<Acc*>(smem), mp);
 
   const int64_t m0 = tm * BM, n0 = tn_ * BN;

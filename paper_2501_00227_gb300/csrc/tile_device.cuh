@@ -284,3 +284,183 @@ constexpr size_t tile_smem_bytes() {
 
 }  // namespace dev
 }  // namespace tn
+
+namespace tn {
+namespace dev {
+
+// ---------------------------------------------------------------------------
+// Counting tropical in two passes over a tile (same result as the single
+// pass with SrCnt::mac, far fewer instructions per multiply-add):
+//   pass 1: the (max,+) tile of the values alone (tile_mainloop on SrI32);
+//   pass 2: count = sum over k of a.c * b.c for the terms whose a.v + b.v
+//           equals the pass-1 maximum of that entry.
+// Pass 2 accumulates exactly in 96 bits (32 x 32 -> 64 products added with
+// carry into a 32-bit overflow word) whenever every count staged in the
+// chunk fits in 32 bits; otherwise the chunk uses saturating 64 x 64
+// products.  The result is then min(exact count, 2^64 - 1), as for SrCnt.
+// ---------------------------------------------------------------------------
+
+// c (96 bits: c2:c1:c0) += a * b when s == vmax
+__device__ __forceinline__ void cnt_fma32(uint32_t& c0, uint32_t& c1, uint32_t& c2, int32_t s, int32_t vmax,
+                                          uint32_t a, uint32_t b) {
+  asm("{\n\t.reg .pred p;\n\t"
+      "setp.eq.s32 p, %3, %4;\n\t"
+      "@p mad.lo.cc.u32 %0, %5, %6, %0;\n\t"
+      "@p madc.hi.cc.u32 %1, %5, %6, %1;\n\t"
+      "@p addc.u32 %2, %2, 0;\n\t}"
+      : "+r"(c0), "+r"(c1), "+r"(c2)
+      : "r"(s), "r"(vmax), "r"(a), "r"(b));
+}
+
+// c (96 bits) += p (64 bits)
+__device__ __forceinline__ void cnt_add64(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint64_t p) {
+  asm("{\n\t"
+      "add.cc.u32 %0, %0, %3;\n\t"
+      "addc.cc.u32 %1, %1, %4;\n\t"
+      "addc.u32 %2, %2, 0;\n\t}"
+      : "+r"(c0), "+r"(c1), "+r"(c2)
+      : "r"(static_cast<uint32_t>(p)), "r"(static_cast<uint32_t>(p >> 32)));
+}
+
+template <class C, bool CG>
+__device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const Operand& A, const Operand& B,
+                                                       const ModParams& mp, int64_t b, int64_t tm, int64_t tn_,
+                                                       int64_t kbeg, int64_t kend, unsigned char* smem_raw,
+                                                       CntVal (&acc)[C::TM][C::TN]) {
+  constexpr int BM = C::BM, BN = C::BN, BK = C::BK, TM = C::TM, TN = C::TN;
+  constexpr int kSt = Stages<SrCnt>::v;
+  constexpr int lbm = Log2<BM>::v, lbn = Log2<BN>::v, lbk = Log2<BK>::v;
+  // pass 1: maxima of the values
+  int32_t vmax[TM][TN];
+  tile_mainloop<SrI32, C, 1, CG>(g, A, B, mp, 0, b, tm, tn_, kbeg, kend,
+                                 *reinterpret_cast<TileSmem<SrI32, C>*>(smem_raw), vmax);
+  // pass 2: counts of the maximising terms
+  auto& sm = *reinterpret_cast<TileSmem<SrCnt, C>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int grp = tid / C::GT, gt = tid % C::GT;
+  const int tx = gt % C::WN, ty = gt / C::WN;
+  const int64_t M = int64_t(1) << g.nm, N = int64_t(1) << g.nn, K = int64_t(1) << g.nk;
+  const int64_t m0 = tm * BM, n0 = tn_ * BN;
+  const int a_k0 = g.nb + g.nm, b_k0 = g.nb, b_n0 = g.nb + g.nk;
+  for (int i = tid; i < BM; i += kBlock) sm.offAm[i] = deposit(i, g.a_pos, g.nb, min(lbm, g.nm));
+  for (int i = tid; i < BN; i += kBlock) sm.offBn[i] = deposit(i, g.b_pos, b_n0, min(lbn, g.nn));
+  for (int i = tid; i < BK; i += kBlock) {
+    sm.offAk[i] = deposit(i, g.a_pos, a_k0, min(lbk, g.nk));
+    sm.offBk[i] = deposit(i, g.b_pos, b_k0, min(lbk, g.nk));
+  }
+  const int64_t baseA = deposit(b, g.a_pos, 0, g.nb) +
+                        (g.nm > lbm ? deposit(m0 >> lbm, g.a_pos, g.nb + lbm, g.nm - lbm) : 0);
+  const int64_t baseB = deposit(b, g.b_pos, 0, g.nb) +
+                        (g.nn > lbn ? deposit(n0 >> lbn, g.b_pos, b_n0 + lbn, g.nn - lbn) : 0);
+  __syncthreads();
+  int32_t offA[C::EA], offB[C::EB];
+  const int64_t kvalid = K < BK ? K : BK;
+#pragma unroll
+  for (int j = 0; j < C::EA; ++j) {
+    const int e = tid + kBlock * j, kk = e / BM, mm = e % BM;
+    offA[j] = ((m0 + mm < M) && (kk < kvalid)) ? static_cast<int32_t>(baseA + sm.offAm[mm] + sm.offAk[kk]) : -1;
+  }
+#pragma unroll
+  for (int j = 0; j < C::EB; ++j) {
+    const int e = tid + kBlock * j, kk = e / BN, nn = e % BN;
+    offB[j] = ((n0 + nn < N) && (kk < kvalid)) ? static_cast<int32_t>(baseB + sm.offBn[nn] + sm.offBk[kk]) : -1;
+  }
+  const CntVal zero = SrCnt::leaf(kOpEdge, 3);
+#pragma unroll
+  for (int j = 0; j < C::EA; ++j)
+    if (offA[j] < 0)
+      for (int st = 0; st < kSt; ++st) sm.As[st][tid + kBlock * j] = zero;
+#pragma unroll
+  for (int j = 0; j < C::EB; ++j)
+    if (offB[j] < 0)
+      for (int st = 0; st < kSt; ++st) sm.Bs[st][tid + kBlock * j] = zero;
+
+  uint32_t c0[TM][TN], c1[TM][TN], c2[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) c0[i][j] = c1[i][j] = c2[i][j] = 0u;
+
+  const bool a_async = A.kind == kOpArena, b_async = B.kind == kOpArena;
+  auto issue = [&](int st, int64_t k0) {
+    const int64_t kA = g.nk > lbk ? deposit(k0 >> lbk, g.a_pos, a_k0 + lbk, g.nk - lbk) : 0;
+    const int64_t kB = g.nk > lbk ? deposit(k0 >> lbk, g.b_pos, b_k0 + lbk, g.nk - lbk) : 0;
+#pragma unroll
+    for (int j = 0; j < C::EA; ++j)
+      if (offA[j] >= 0) {
+        if (a_async) SrCnt::copy_async(&sm.As[st][tid + kBlock * j], A, offA[j] + kA, 0);
+        else sm.As[st][tid + kBlock * j] = SrCnt::template load<CG>(A, offA[j] + kA, 0);
+      }
+#pragma unroll
+    for (int j = 0; j < C::EB; ++j)
+      if (offB[j] >= 0) {
+        if (b_async) SrCnt::copy_async(&sm.Bs[st][tid + kBlock * j], B, offB[j] + kB, 0);
+        else sm.Bs[st][tid + kBlock * j] = SrCnt::template load<CG>(B, offB[j] + kB, 0);
+      }
+  };
+#pragma unroll
+  for (int st = 0; st < kSt - 1; ++st) {
+    if (kbeg + st * BK < kend) issue(st, kbeg + st * BK);
+    cp_async_commit();
+  }
+  int cur = 0;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+    cp_async_wait<kSt - 2>();
+    // this thread's own copies of the chunk are complete: do they all fit 32 bits?
+    uint32_t hi = 0;
+#pragma unroll
+    for (int j = 0; j < C::EA; ++j) hi |= static_cast<uint32_t>(sm.As[cur][tid + kBlock * j].c >> 32);
+#pragma unroll
+    for (int j = 0; j < C::EB; ++j) hi |= static_cast<uint32_t>(sm.Bs[cur][tid + kBlock * j].c >> 32);
+    const bool wide = __syncthreads_or(hi != 0) != 0;
+    {
+      const int64_t kn = k0 + (kSt - 1) * BK;
+      const int nxt = (cur + kSt - 1) % kSt;
+      if (kn < kend) issue(nxt, kn);
+      cp_async_commit();
+    }
+    const CntVal* Ag = sm.As[cur] + grp * C::BKG * BM;
+    const CntVal* Bg = sm.Bs[cur] + grp * C::BKG * BN;
+    if (!wide) {
+#pragma unroll 2
+      for (int kk = 0; kk < C::BKG; ++kk) {
+        CntVal a[TM], bv[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) a[i] = Ag[kk * BM + ty * TM + i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) bv[j] = Bg[kk * BN + tx * TN + j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j)
+            cnt_fma32(c0[i][j], c1[i][j], c2[i][j], a[i].v + bv[j].v, vmax[i][j], static_cast<uint32_t>(a[i].c),
+                      static_cast<uint32_t>(bv[j].c));
+      }
+    } else {
+      for (int kk = 0; kk < C::BKG; ++kk) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+          const CntVal a = Ag[kk * BM + ty * TM + i];
+#pragma unroll
+          for (int j = 0; j < TN; ++j) {
+            const CntVal bb = Bg[kk * BN + tx * TN + j];
+            if (a.v + bb.v == vmax[i][j]) cnt_add64(c0[i][j], c1[i][j], c2[i][j], sat_mul_u64(a.c, bb.c));
+          }
+        }
+      }
+    }
+    cur = (cur + 1) % kSt;
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      acc[i][j].v = vmax[i][j];
+      acc[i][j].c = c2[i][j] ? ~0ull : (static_cast<uint64_t>(c1[i][j]) << 32) | c0[i][j];
+    }
+}
+
+}  // namespace dev
+}  // namespace tn
