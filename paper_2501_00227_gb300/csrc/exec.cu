@@ -384,12 +384,10 @@ size_t exec_acc_bytes(tn_semiring_t s) {
 
 int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods_v, int32_t nprimes, void* ws,
                  size_t ws_bytes, void* stream, void* d_raw, void* d_trace) {
-  const dev::ModTable& mods = *static_cast<const dev::ModTable*>(mods_v);
   int rc;
   ExecPlan* X = exec_plan_get(p, s, nprimes, &rc);
   if (!X) return rc;
   if (ws_bytes < X->total_bytes) return TN_ENOMEM;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   {
     // one-time upload of the step / dependency / task tables to this device
     static std::mutex mu;
@@ -399,23 +397,26 @@ int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods_v, int32_t npri
     if (!X->d_tables || X->device != dev) {
       if (X->d_tables) cudaFree(X->d_tables);
       X->d_tables = nullptr;
-      std::vector<unsigned char> img(X->table_bytes, 0);
-      std::memcpy(img.data() + X->off_steps, X->steps.data(), sizeof(ExecStep) * X->steps.size());
-      std::memcpy(img.data() + X->off_deps, X->deps.data(), sizeof(int32_t) * X->deps.size());
-      std::memcpy(img.data() + X->off_tasks, X->tasks.data(), sizeof(ExecTask) * X->tasks.size());
       if (cudaMalloc(&X->d_tables, X->table_bytes) != cudaSuccess) return TN_ENOMEM;
-      if (cudaMemcpy(X->d_tables, img.data(), X->table_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+      if (cudaMemcpy(X->d_tables, X->table_image.data(), X->table_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
         return TN_ECUDA;
       X->device = dev;
       X->grid = 0;
     }
   }
+  return exec_launch_core(X, s, mods_v, ws, stream, d_raw, d_trace, X->d_tables);
+}
+
+int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods_v, void* ws, void* stream, void* d_raw,
+                     void* d_trace, const void* d_tables) {
+  const dev::ModTable& mods = *static_cast<const dev::ModTable*>(mods_v);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ws);
   if (cudaMemsetAsync(w, 0, X->ctr_off + X->ctr_bytes, st) != cudaSuccess) return TN_ECUDA;
   dev::ExecArgs a;
   std::memset(&a, 0, sizeof(a));
   const int ns = static_cast<int>(X->steps.size());
-  char* tables = static_cast<char*>(X->d_tables);
+  const char* tables = static_cast<const char*>(d_tables);
   a.steps = reinterpret_cast<const ExecStep*>(tables + X->off_steps);
   a.deps = reinterpret_cast<const int32_t*>(tables + X->off_deps);
   a.tasks = reinterpret_cast<const ExecTask*>(tables + X->off_tasks);

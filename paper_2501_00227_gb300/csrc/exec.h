@@ -63,7 +63,9 @@ struct ExecPlan {
   size_t scratch_bytes = 0;
   // workspace layout (bytes from the start of the workspace)
   size_t ctr_off = 0, ctr_bytes = 0, scratch_base = 0, arena_base = 0, total_bytes = 0;
-  // device copy of steps / deps / tasks (library-owned, uploaded once)
+  // host image of the step / dependency / task tables and its device copy
+  // (library-owned, uploaded once per device)
+  std::vector<unsigned char> table_image;
   void* d_tables = nullptr;
   int device = -1;
   size_t off_steps = 0, off_deps = 0, off_tasks = 0, table_bytes = 0;
@@ -79,6 +81,10 @@ void exec_plans_free(tn_plan_s* p);
 // Enqueues one contraction through the executor (exec.cu).
 int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods, int32_t nprimes, void* ws,
                  size_t ws_bytes, void* stream, void* d_raw, void* d_trace);
+
+// Launches the executor with the tables already on the device at d_tables.
+int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods, void* ws, void* stream, void* d_raw,
+                     void* d_trace, const void* d_tables);
 
 // Bytes per accumulator / per staged value of the tiled tasks, and the
 // dynamic shared memory the executor needs (exec.cu).

@@ -266,6 +266,10 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   X->off_deps = align_up(sizeof(ExecStep) * X->steps.size(), 256);
   X->off_tasks = X->off_deps + align_up(sizeof(int32_t) * (X->deps.size() + 1), 256);
   X->table_bytes = X->off_tasks + sizeof(ExecTask) * X->tasks.size();
+  X->table_image.assign(X->table_bytes, 0);
+  std::memcpy(X->table_image.data() + X->off_steps, X->steps.data(), sizeof(ExecStep) * X->steps.size());
+  std::memcpy(X->table_image.data() + X->off_deps, X->deps.data(), sizeof(int32_t) * X->deps.size());
+  std::memcpy(X->table_image.data() + X->off_tasks, X->tasks.data(), sizeof(ExecTask) * X->tasks.size());
   return TN_OK;
 }
 
