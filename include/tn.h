@@ -197,6 +197,32 @@ int tn_contract_pair(tn_semiring_t semiring, const uint32_t *primes, int32_t npr
                      const void *d_b, const int32_t *lb, int32_t rb,
                      const int32_t *lc, int32_t rc, void *d_c, void *cuda_stream);
 
+/* Contraction without any device allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (or have nothing to pass as a workspace) -- for
+ * example code running where another component owns device memory through
+ * its own pool, so a plain cudaMalloc could fail or fragment that pool, or
+ * latency-critical host loops that must not risk the implicit device-wide
+ * synchronisation that cudaMalloc / cudaFree can cause.
+ *
+ * It behaves like tn_contract, but its whole workspace (executor counters,
+ * split-K scratch, intermediate tensors and the plan's step/task tables) is
+ * one file-scope device array of TN_STATIC_WORKSPACE_BYTES (64 MiB) that
+ * every GPU loading libtn keeps until the process exits.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.  Plans whose needs
+ * (tn_plan_info peak_bytes for the semiring plus exec_table_bytes, each
+ * rounded up to 256 bytes) exceed the array are rejected with TN_ENOMEM.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the array, which keeps the
+ * previous call's contents; each call clears what must start at zero, and
+ * calls that overlap on the GPU (concurrent threads or streams) race on it.
+ * Enqueues on cuda_stream and waits for it. */
+#define TN_STATIC_WORKSPACE_BYTES (64 * 1024 * 1024)
+int tn_contract_static(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *primes, int32_t nprimes,
+                       void *cuda_stream, tn_result_t *out);
+
 /* Serving (continuous batching).  A server owns a worker thread, a CUDA
  * stream pool and an HBM budget; tn_submit admits a request once the peak
  * workspace of its plan fits in the free part of the budget and fewer than

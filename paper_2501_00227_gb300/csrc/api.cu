@@ -92,6 +92,19 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? TN_OK : TN_ECUDA; }
 
 }  // namespace
 
+// Checked modulus table and raw-result decoding for entry points that live
+// in other translation units (tn_contract_static).
+int make_mod_table_checked(tn_semiring_t s, const uint32_t* primes, int32_t nprimes, void* mods) {
+  if (!semiring_ok(s)) return TN_EINVAL;
+  return make_mods(s, primes, nprimes, static_cast<ModTable*>(mods));
+}
+int decode_raw(tn_semiring_t s, const ModTable& mods, int32_t nprimes, const unsigned char* raw,
+               tn_result_t* out);
+int decode_raw_any(tn_semiring_t s, const void* mods, int32_t nprimes, const unsigned char* raw,
+                   tn_result_t* out) {
+  return decode_raw(s, *static_cast<const ModTable*>(mods), nprimes, raw, out);
+}
+
 // Workspace a contraction needs: the larger of the per-step layout and the
 // executor layout (so one buffer serves both paths).
 size_t required_bytes(tn_plan_s* p, tn_semiring_t s, int32_t nprimes) {

@@ -86,6 +86,7 @@ def lib():
                                         i32p, ctypes.POINTER(ctypes.c_uint64)]
         L.tn_contract_trace.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.c_size_t, vp, vp, i32p, i32p,
                                         i32p, ctypes.POINTER(tn_result_t)]
+        L.tn_contract_static.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.POINTER(tn_result_t)]
         L.tn_result_decode.argtypes = [ctypes.c_int, u32p, i32, vp, ctypes.POINTER(tn_result_t)]
         L.tn_contract_pair.argtypes = [ctypes.c_int, u32p, i32, vp, i32p, i32, vp, i32p, i32, i32p, i32, vp, vp]
         L.tn_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
@@ -234,6 +235,19 @@ def tn_contract_trace(plan, semiring, primes, ws_ptr: int, ws_bytes: int, stream
                                    ctypes.c_void_p(stream), ctypes.c_void_p(trace_ptr), _p32(ts), _p32(tk),
                                    _p32(lv), ctypes.byref(r)), "tn_contract_trace")
     return result_dict(r, semiring), ts, tk, lv
+
+
+TN_STATIC_WORKSPACE_BYTES = 64 * 1024 * 1024
+
+
+def tn_contract_static(plan, semiring, primes, stream: int) -> dict:
+    """Contraction whose workspace is the library's static device array (no
+    device allocation; for callers that cannot call cudaMalloc)."""
+    pr, k = _primes(primes)
+    r = tn_result_t()
+    _check(lib().tn_contract_static(plan, _sr(semiring), _u32p(pr), k, ctypes.c_void_p(stream), ctypes.byref(r)),
+           "tn_contract_static")
+    return result_dict(r, semiring)
 
 
 def tn_contract_async(plan, semiring, primes, ws_ptr: int, ws_bytes: int, stream: int, raw_ptr: int):
