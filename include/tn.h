@@ -223,6 +223,34 @@ int tn_contract_pair(tn_semiring_t semiring, const uint32_t *primes, int32_t npr
 int tn_contract_static(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *primes, int32_t nprimes,
                        void *cuda_stream, tn_result_t *out);
 
+/* Batching: many independent networks contracted by ONE persistent
+ * executor launch (the tasks of all networks merged in dependency-level
+ * order, so small networks fill the GPU together), optionally replayed from
+ * a CUDA graph.  Paper: each network is an ordinary contraction (Sec. 4.1);
+ * grouping is a GB300 execution choice.
+ *   tn_batch_create    plans: `count` plans (all must outlive the batch);
+ *                      one semiring (and prime list) for all.
+ *   tn_batch_info      workspace bytes the batch needs, tasks, levels,
+ *                      bytes of its device tables.
+ *   tn_batch_contract  enqueues the batch on cuda_stream: d_workspace
+ *                      (caller device memory, 256-byte aligned), d_raw
+ *                      (count * TN_RAW_BYTES of caller device memory; slot i
+ *                      receives network i's raw result, decode each with
+ *                      tn_result_decode).  Does not wait.
+ *   tn_batch_contract_graph  the same, through a CUDA graph captured on the
+ *                      first call for this (workspace, raw, stream) and
+ *                      replayed on later calls.
+ * The device tables are uploaded on the first contraction (library-owned). */
+typedef struct tn_batch_s *tn_batch_t;
+int tn_batch_create(const tn_plan_t *plans, int32_t count, tn_semiring_t semiring, const uint32_t *primes,
+                    int32_t nprimes, tn_batch_t *out);
+int tn_batch_info(tn_batch_t batch, uint64_t *workspace_bytes, int32_t *tasks, int32_t *levels,
+                  uint64_t *table_bytes);
+int tn_batch_contract(tn_batch_t batch, void *d_workspace, size_t ws_bytes, void *cuda_stream, void *d_raw);
+int tn_batch_contract_graph(tn_batch_t batch, void *d_workspace, size_t ws_bytes, void *cuda_stream,
+                            void *d_raw);
+void tn_batch_destroy(tn_batch_t batch);
+
 /* Serving (continuous batching).  A server owns a worker thread, a CUDA
  * stream pool and an HBM budget; tn_submit admits a request once the peak
  * workspace of its plan fits in the free part of the budget and fewer than

@@ -42,6 +42,8 @@ struct ExecArgs {
   int32_t pad_;
   unsigned long long timeout_ns;
   unsigned long long* trace;  // optional: 4 words per task (see tn_contract_trace)
+  int32_t nraw;               // raw result slots (networks in the launch)
+  int32_t pad2_;
 };
 
 constexpr uint32_t kStatusTimeout = 1u;
@@ -217,21 +219,25 @@ __device__ __noinline__ void exec_naive_task(const ExecArgs& a, const ExecStep& 
   }
 }
 
-__device__ __forceinline__ void exec_final(const ExecArgs& a, const ExecStep& st) {
+// Copies the scalar of a network (the output of its last step) into raw
+// result slot `slot` (a single contraction uses slot 0; a batch one per
+// network).
+__device__ __forceinline__ void exec_final(const ExecArgs& a, const ExecStep& st, int slot) {
   if (threadIdx.x != 0) return;
+  unsigned char* raw = a.raw + static_cast<int64_t>(slot) * TN_RAW_BYTES;
   const char* r0 = a.r0 + 4 * st.c_off;
   if (a.semiring == TN_TROPICAL_F32 || a.semiring == TN_TROPICAL_I32) {
-    *reinterpret_cast<int32_t*>(a.raw) = __ldcg(reinterpret_cast<const int32_t*>(r0));
+    *reinterpret_cast<int32_t*>(raw) = __ldcg(reinterpret_cast<const int32_t*>(r0));
   } else if (a.semiring == TN_COUNTING_TROPICAL) {
-    *reinterpret_cast<int32_t*>(a.raw) = __ldcg(reinterpret_cast<const int32_t*>(r0));
-    *reinterpret_cast<uint64_t*>(a.raw + 8) =
+    *reinterpret_cast<int32_t*>(raw) = __ldcg(reinterpret_cast<const int32_t*>(r0));
+    *reinterpret_cast<uint64_t*>(raw + 8) =
         __ldcg(reinterpret_cast<const uint64_t*>(a.r1 + 8 * st.c_off));
   } else {
     for (int q = 0; q < a.nprimes; ++q)
-      reinterpret_cast<uint32_t*>(a.raw + 16)[q] =
+      reinterpret_cast<uint32_t*>(raw + 16)[q] =
           __ldcg(reinterpret_cast<const uint32_t*>(r0) + q * a.prime_stride);
   }
-  *reinterpret_cast<uint32_t*>(a.raw + 96) = ld_relaxed_u32(a.status);
+  *reinterpret_cast<uint32_t*>(raw + 96) = ld_relaxed_u32(a.status);
 }
 
 template <class SR, int FOLD>
@@ -284,7 +290,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
       timed_out = __any_sync(0xffffffffu, timed_out);
       if (tid == 0 && timed_out) {
         atomicOr(a.status, kStatusTimeout);
-        atomicOr(reinterpret_cast<unsigned int*>(a.raw + 96), kStatusTimeout);
+        for (int r = 0; r < a.nraw; ++r)
+          atomicOr(reinterpret_cast<unsigned int*>(a.raw + static_cast<int64_t>(r) * TN_RAW_BYTES + 96),
+                   kStatusTimeout);
         s_abort = 1;
       }
     }
@@ -293,7 +301,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
     unsigned long long t_ready = 0;
     if (a.trace && tid == 0) t_ready = global_ns();
     if (s_task.kind == kTaskFinal) {
-      exec_final(a, s_step);
+      exec_final(a, s_step, s_task.local);
     } else if (s_task.kind == kTaskNaive) {
       exec_naive_task<SR>(a, s_step, s_task, smem, &s_last);
     } else {
@@ -372,6 +380,25 @@ static int exec_launch_t(ExecPlan* X, const ExecArgs& args, cudaStream_t st) {
 
 }  // namespace dev
 
+int exec_prepare_launch(tn_semiring_t s, const void* mods_v) {
+  const dev::ModTable& mods = *static_cast<const dev::ModTable*>(mods_v);
+  size_t smem;
+  int r = 0;
+  switch (s) {
+    case TN_TROPICAL_F32: r = dev::exec_resident<dev::SrF32, 1>(&smem); break;
+    case TN_TROPICAL_I32: r = dev::exec_resident<dev::SrI32, 1>(&smem); break;
+    case TN_COUNTING_TROPICAL: r = dev::exec_resident<dev::SrCnt, 1>(&smem); break;
+    case TN_COUNT_MODP: {
+      bool small_r = true;
+      for (int i = 0; i < TN_MAX_PRIMES && mods.q[i].p; ++i) small_r = small_r && mods.q[i].r32 < (1u << 20);
+      r = small_r ? dev::exec_resident<dev::SrMod, 3>(&smem) : dev::exec_resident<dev::SrMod, 1>(&smem);
+      break;
+    }
+    default: return TN_EINVAL;
+  }
+  return r < 0 ? TN_ECUDA : TN_OK;
+}
+
 size_t exec_acc_bytes(tn_semiring_t s) {
   switch (s) {
     case TN_TROPICAL_F32: return sizeof(float);
@@ -438,6 +465,7 @@ int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods_v, void* ws,
   a.semiring = s;
   a.timeout_ns = 2000000000ull;  // 2 s per wait
   a.trace = static_cast<unsigned long long*>(d_trace);
+  a.nraw = X->nraw;
   switch (s) {
     case TN_TROPICAL_F32: return dev::exec_launch_t<dev::SrF32, 1>(X, a, st);
     case TN_TROPICAL_I32: return dev::exec_launch_t<dev::SrI32, 1>(X, a, st);

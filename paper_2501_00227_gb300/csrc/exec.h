@@ -60,6 +60,7 @@ struct ExecPlan {
   int32_t root_step = -1;
   int32_t n_arrive = 0;
   int32_t nlevels = 0;
+  int32_t nraw = 1;   // raw result slots (networks) of one launch
   size_t scratch_bytes = 0;
   // workspace layout (bytes from the start of the workspace)
   size_t ctr_off = 0, ctr_bytes = 0, scratch_base = 0, arena_base = 0, total_bytes = 0;
@@ -85,6 +86,10 @@ int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods, int32_t nprime
 // Launches the executor with the tables already on the device at d_tables.
 int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods, void* ws, void* stream, void* d_raw,
                      void* d_trace, const void* d_tables);
+
+// One-time kernel set-up of the executor instantiation a launch would use
+// (attributes, occupancy), so that a later launch can be graph-captured.
+int exec_prepare_launch(tn_semiring_t s, const void* mods);
 
 // Bytes per accumulator / per staged value of the tiled tasks, and the
 // dynamic shared memory the executor needs (exec.cu).

@@ -87,6 +87,11 @@ def lib():
         L.tn_contract_trace.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.c_size_t, vp, vp, i32p, i32p,
                                         i32p, ctypes.POINTER(tn_result_t)]
         L.tn_contract_static.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.POINTER(tn_result_t)]
+        L.tn_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_int, u32p, i32, ctypes.POINTER(vp)]
+        L.tn_batch_info.argtypes = [vp, ctypes.POINTER(u64), i32p, i32p, ctypes.POINTER(u64)]
+        L.tn_batch_contract.argtypes = [vp, vp, ctypes.c_size_t, vp, vp]
+        L.tn_batch_contract_graph.argtypes = [vp, vp, ctypes.c_size_t, vp, vp]
+        L.tn_batch_destroy.argtypes = [vp]
         L.tn_result_decode.argtypes = [ctypes.c_int, u32p, i32, vp, ctypes.POINTER(tn_result_t)]
         L.tn_contract_pair.argtypes = [ctypes.c_int, u32p, i32, vp, i32p, i32, vp, i32p, i32, i32p, i32, vp, vp]
         L.tn_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
@@ -301,6 +306,39 @@ def tn_server_destroy(server):
         lib().tn_server_destroy(server)
 
 
+def tn_batch_create(plans, semiring, primes=None) -> int:
+    handles = (ctypes.c_void_p * len(plans))(*[p.handle if hasattr(p, "handle") else p for p in plans])
+    pr, k = _primes(primes)
+    h = ctypes.c_void_p()
+    _check(lib().tn_batch_create(handles, len(plans), _sr(semiring), _u32p(pr), k, ctypes.byref(h)),
+           "tn_batch_create")
+    return h.value
+
+
+def tn_batch_info(batch) -> dict:
+    ws, tb = ctypes.c_uint64(), ctypes.c_uint64()
+    ta, lv = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().tn_batch_info(batch, ctypes.byref(ws), ctypes.byref(ta), ctypes.byref(lv), ctypes.byref(tb)),
+           "tn_batch_info")
+    return {"workspace_bytes": int(ws.value), "tasks": int(ta.value), "levels": int(lv.value),
+            "table_bytes": int(tb.value)}
+
+
+def tn_batch_contract(batch, ws_ptr: int, ws_bytes: int, stream: int, raw_ptr: int):
+    _check(lib().tn_batch_contract(batch, ctypes.c_void_p(ws_ptr), ws_bytes, ctypes.c_void_p(stream),
+                                   ctypes.c_void_p(raw_ptr)), "tn_batch_contract")
+
+
+def tn_batch_contract_graph(batch, ws_ptr: int, ws_bytes: int, stream: int, raw_ptr: int):
+    _check(lib().tn_batch_contract_graph(batch, ctypes.c_void_p(ws_ptr), ws_bytes, ctypes.c_void_p(stream),
+                                         ctypes.c_void_p(raw_ptr)), "tn_batch_contract_graph")
+
+
+def tn_batch_destroy(batch):
+    if batch:
+        lib().tn_batch_destroy(batch)
+
+
 # --------------------------------------------------------------------- objects
 
 class Plan:
@@ -333,6 +371,56 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             tn_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many plans contracted in one persistent launch (tn_batch_*)."""
+
+    def __init__(self, plans, semiring, primes=None):
+        self.plans = list(plans)
+        self.semiring = semiring
+        self.primes = primes
+        self.handle = tn_batch_create(self.plans, semiring, primes)
+        self.info = tn_batch_info(self.handle)
+        self.ws = None
+        self.raw = None
+
+    def buffers(self):
+        import torch
+        if self.ws is None:
+            self.ws = torch.empty(max(self.info["workspace_bytes"], 256), dtype=torch.uint8, device="cuda")
+            self.raw = torch.zeros(len(self.plans) * TN_RAW_BYTES, dtype=torch.uint8, device="cuda")
+        return self.ws, self.raw
+
+    def launch(self, graph: bool = False, stream=None):
+        """Enqueue the batch (no wait)."""
+        import torch
+        ws, raw = self.buffers()
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        f = tn_batch_contract_graph if graph else tn_batch_contract
+        f(self.handle, ws.data_ptr(), ws.numel(), st, raw.data_ptr())
+
+    def results(self):
+        import torch
+        torch.cuda.current_stream().synchronize()
+        host = self.raw.cpu().numpy().tobytes()
+        return [tn_result_decode(self.semiring, self.primes, host[i * TN_RAW_BYTES:(i + 1) * TN_RAW_BYTES])
+                for i in range(len(self.plans))]
+
+    def run(self, graph: bool = False):
+        self.launch(graph)
+        return self.results()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tn_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
