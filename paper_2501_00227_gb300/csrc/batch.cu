@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -32,6 +33,7 @@ struct tn_batch_s {
   tn_semiring_t semiring;
   int32_t nprimes = 1;
   int32_t count = 0;
+  int32_t group_h = 64;  // networks of a batch run their tiny subtrees whole
   alignas(16) unsigned char mods[512];
   tn::ExecPlan X;  // the merged plan
   std::mutex mu;
@@ -54,20 +56,22 @@ int build_batch(tn_batch_s* B, const tn_plan_t* plans, int32_t count) {
   std::vector<ExecPlan*> xs(count);
   for (int i = 0; i < count; ++i) {
     int rc;
-    xs[i] = exec_plan_get(plans[i], B->semiring, B->nprimes, &rc);
+    xs[i] = exec_plan_get_h(plans[i], B->semiring, B->nprimes, B->group_h, &rc);
     if (!xs[i]) return rc;
   }
   ExecPlan& M = B->X;
   M.semiring = B->semiring;
   M.nprimes = xs.empty() ? 1 : xs[0]->nprimes;
-  std::vector<int64_t> step_base(count), arena_base(count);
+  std::vector<int64_t> step_base(count), arena_base(count), group_base(count);
   std::vector<size_t> scratch_base(count);
   std::vector<int32_t> arrive_base(count);
-  int64_t nsteps = 0, arena = 0, arrive = 0;
+  int64_t nsteps = 0, arena = 0, arrive = 0, ngroups = 0;
   size_t scratch = 0;
   int maxlev = 0;
   for (int i = 0; i < count; ++i) {
     step_base[i] = nsteps;
+    group_base[i] = ngroups;
+    ngroups += xs[i]->ngroups;
     arena_base[i] = arena;
     scratch_base[i] = scratch;
     arrive_base[i] = static_cast<int32_t>(arrive);
@@ -82,6 +86,18 @@ int build_batch(tn_batch_s* B, const tn_plan_t* plans, int32_t count) {
   M.deps.clear();
   M.tasks.clear();
   M.step_level.clear();
+  M.group_begin.clear();
+  M.group_members.clear();
+  for (int i = 0; i < count; ++i) {
+    const ExecPlan& x = *xs[i];
+    for (int gi = 0; gi < x.ngroups; ++gi) {
+      M.group_begin.push_back(static_cast<int32_t>(M.group_members.size()));
+      for (int32_t k = x.group_begin[gi]; k < x.group_begin[gi + 1]; ++k)
+        M.group_members.push_back(x.group_members[k] + static_cast<int32_t>(step_base[i]));
+    }
+  }
+  M.ngroups = static_cast<int32_t>(M.group_begin.size());
+  M.group_begin.push_back(static_cast<int32_t>(M.group_members.size()));
   M.steps.reserve(static_cast<size_t>(nsteps));
   M.step_level.reserve(static_cast<size_t>(nsteps));
   for (int i = 0; i < count; ++i) {
@@ -112,6 +128,9 @@ int build_batch(tn_batch_s* B, const tn_plan_t* plans, int32_t count) {
       if (t.kind == kTaskFinal) {
         u.local = i;  // raw-result slot of this network
         lev = maxlev;
+      } else if (t.kind == kTaskGroup) {
+        u.local += static_cast<int32_t>(group_base[i]);
+        lev = x.step_level[t.step];
       } else {
         lev = x.step_level[t.step];
       }
@@ -143,8 +162,13 @@ int build_batch(tn_batch_s* B, const tn_plan_t* plans, int32_t count) {
   M.off_steps = 0;
   M.off_deps = align_up(sizeof(ExecStep) * M.steps.size(), 256);
   M.off_tasks = M.off_deps + align_up(sizeof(int32_t) * (M.deps.size() + 1), 256);
-  M.table_bytes = M.off_tasks + sizeof(ExecTask) * M.tasks.size();
+  M.off_groups = M.off_tasks + align_up(sizeof(ExecTask) * M.tasks.size(), 256);
+  M.off_members = M.off_groups + align_up(sizeof(int32_t) * M.group_begin.size(), 256);
+  M.table_bytes = M.off_members + sizeof(int32_t) * (M.group_members.size() + 1);
   M.table_image.assign(M.table_bytes, 0);
+  std::memcpy(M.table_image.data() + M.off_groups, M.group_begin.data(), sizeof(int32_t) * M.group_begin.size());
+  std::memcpy(M.table_image.data() + M.off_members, M.group_members.data(),
+              sizeof(int32_t) * M.group_members.size());
   std::memcpy(M.table_image.data() + M.off_steps, M.steps.data(), sizeof(ExecStep) * M.steps.size());
   std::memcpy(M.table_image.data() + M.off_deps, M.deps.data(), sizeof(int32_t) * M.deps.size());
   std::memcpy(M.table_image.data() + M.off_tasks, M.tasks.data(), sizeof(ExecTask) * M.tasks.size());
@@ -179,6 +203,10 @@ int tn_batch_create(const tn_plan_t* plans, int32_t count, tn_semiring_t semirin
   B->semiring = semiring;
   B->nprimes = semiring == TN_COUNT_MODP ? nprimes : 1;
   B->count = count;
+  {
+    const char* e = getenv("TN_GROUP_HEIGHT");
+    if (e && *e) B->group_h = atoi(e);
+  }
   static_assert(sizeof(tn::dev::ModTable) <= sizeof(B->mods), "modulus table");
   int rc = tn::make_mod_table_checked(semiring, primes, nprimes, B->mods);
   if (rc) return rc;

@@ -26,6 +26,8 @@ struct ExecArgs {
   const ExecStep* steps;
   const int32_t* deps;
   const ExecTask* tasks;
+  const int32_t* group_begin;    // group g: group_members[group_begin[g] .. group_begin[g+1])
+  const int32_t* group_members;  // exec-step indices
   int32_t ntasks_total;
   int32_t nprimes;
   int32_t* done;        // per exec step: finished tasks
@@ -222,6 +224,41 @@ __device__ __noinline__ void exec_naive_task(const ExecArgs& a, const ExecStep& 
 // Copies the scalar of a network (the output of its last step) into raw
 // result slot `slot` (a single contraction uses slot 0; a batch one per
 // network).
+// All outputs of one general step over its whole k range (a member of a
+// group of tiny steps).
+template <class SR>
+__device__ __forceinline__ void exec_naive_whole(const ExecArgs& a, const ExecStep& st, int q, unsigned char* smem) {
+  auto& sm = *reinterpret_cast<NaiveSmem<SR>*>(smem);
+  const StepGeom& g = st.g;
+  naive_tables<SR>(g, sm);
+  const ModParams mp = a.mods.q[q];
+  const Operand A = exec_operand(a, g.a_kind, st.a_off);
+  const Operand B = exec_operand(a, g.b_kind, st.b_off);
+  Output C{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride};
+  const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
+  auto la = [&](int64_t e) { return SR::template load<true>(A, e, q); };
+  auto lb = [&](int64_t e) { return SR::template load<true>(B, e, q); };
+  auto sink = [&](int64_t c, const typename SR::Acc& v) { SR::store(C, c, q, v, mp); };
+  naive_chunk<SR>(g, la, lb, sink, mp, 0, int64_t(1) << g.rc, 0, int64_t(1) << (g.nk - kl), st.R, sm);
+}
+
+// A group of tiny steps, run back to back by this CTA: barriers between the
+// steps make each step's outputs visible to the next.
+template <class SR>
+__device__ __noinline__ void exec_group_task(const ExecArgs& a, const ExecTask& task, ExecStep* s_step,
+                                             unsigned char* smem) {
+  const int b0 = a.group_begin[task.local], b1 = a.group_begin[task.local + 1];
+  for (int i = b0; i < b1; ++i) {
+    const int m = a.group_members[i];
+    __syncthreads();
+    const int32_t* src = reinterpret_cast<const int32_t*>(a.steps + m);
+    int32_t* dst = reinterpret_cast<int32_t*>(s_step);
+    for (int w = threadIdx.x; w < static_cast<int>(sizeof(ExecStep) / 4); w += kBlock) dst[w] = __ldg(src + w);
+    __syncthreads();
+    exec_naive_whole<SR>(a, *s_step, task.prime, smem);
+  }
+}
+
 __device__ __forceinline__ void exec_final(const ExecArgs& a, const ExecStep& st, int slot) {
   if (threadIdx.x != 0) return;
   unsigned char* raw = a.raw + static_cast<int64_t>(slot) * TN_RAW_BYTES;
@@ -304,6 +341,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
       exec_final(a, s_step, s_task.local);
     } else if (s_task.kind == kTaskNaive) {
       exec_naive_task<SR>(a, s_step, s_task, smem, &s_last);
+    } else if (s_task.kind == kTaskGroup) {
+      exec_group_task<SR>(a, s_task, &s_step, smem);
     } else {
       switch (s_step.tile) {
         case 0:
@@ -447,6 +486,8 @@ int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods_v, void* ws,
   a.steps = reinterpret_cast<const ExecStep*>(tables + X->off_steps);
   a.deps = reinterpret_cast<const int32_t*>(tables + X->off_deps);
   a.tasks = reinterpret_cast<const ExecTask*>(tables + X->off_tasks);
+  a.group_begin = reinterpret_cast<const int32_t*>(tables + X->off_groups);
+  a.group_members = reinterpret_cast<const int32_t*>(tables + X->off_members);
   a.ntasks_total = static_cast<int32_t>(X->tasks.size());
   a.nprimes = X->nprimes;
   int32_t* ctr = reinterpret_cast<int32_t*>(w + X->ctr_off);

@@ -38,7 +38,7 @@ struct ExecStep {
   int32_t pad_;
 };
 
-enum ExecTaskKind : int32_t { kTaskNaive = 0, kTaskTile = 1, kTaskFinal = 2 };
+enum ExecTaskKind : int32_t { kTaskNaive = 0, kTaskTile = 1, kTaskFinal = 2, kTaskGroup = 3 };
 
 struct ExecTask {
   int32_t step;   // exec-step index
@@ -55,6 +55,10 @@ struct ExecPlan {
   std::vector<int32_t> deps;
   std::vector<ExecTask> tasks;
   std::vector<int32_t> step_level;   // dependency level of each exec step
+  std::vector<int32_t> group_begin;  // group g's members: group_members[begin[g] .. begin[g+1])
+  std::vector<int32_t> group_members;  // exec-step indices, in execution order
+  int32_t ngroups = 0;
+  int32_t group_h = 4;               // group height limit the plan was built with
   int64_t arena_entries = 0;
   int64_t root_off = 0;
   int32_t root_step = -1;
@@ -69,7 +73,7 @@ struct ExecPlan {
   std::vector<unsigned char> table_image;
   void* d_tables = nullptr;
   int device = -1;
-  size_t off_steps = 0, off_deps = 0, off_tasks = 0, table_bytes = 0;
+  size_t off_steps = 0, off_deps = 0, off_tasks = 0, off_groups = 0, off_members = 0, table_bytes = 0;
   // executor launch shape
   int grid = 0;
   size_t smem = 0;
@@ -77,6 +81,11 @@ struct ExecPlan {
 
 // Builds (or returns the cached) executor plan; thread-safe.
 ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc);
+// The same with an explicit group height (largest tree of tiny steps one
+// CTA runs back to back; 1 disables grouping).
+ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int height, int* rc);
+// TN_GROUP_HEIGHT, else 4.
+int group_height();
 void exec_plans_free(tn_plan_s* p);
 
 // Enqueues one contraction through the executor (exec.cu).

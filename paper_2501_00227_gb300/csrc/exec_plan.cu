@@ -24,6 +24,18 @@ struct Cache {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+}  // namespace
+
+// Largest height of a group of tiny steps run by one CTA (TN_GROUP_HEIGHT,
+// default 4; 0 or 1 disables grouping).
+int group_height() {
+  const char* e = getenv("TN_GROUP_HEIGHT");
+  if (!e || !*e) return 4;
+  return atoi(e);
+}
+
+namespace {
+
 // First-fit arena whose free blocks remember which steps released them: a
 // step that takes memory another step released must run after that step
 // (write-after-read), so the releasers become dependencies.
@@ -80,6 +92,7 @@ class LevelArena {
 
 int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X) {
   const int ns = static_cast<int>(p->steps.size());
+  const int H = X->group_h;
   const int np = s == TN_COUNT_MODP ? nprimes : 1;
   X->semiring = s;
   X->nprimes = np;
@@ -100,8 +113,45 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   X->step_level.resize(ns);
   for (int i = 0; i < ns; ++i) X->step_level[i] = level[order[i]];
 
+  // ---- groups: trees of tiny steps (one output chunk, little work) of
+  // height <= H run back to back inside one CTA (one task, barriers between
+  // the steps) instead of one task per step.  Only a group's root output
+  // leaves the group; the other members' outputs ("internal" tensors) live in
+  // a region of their own that is never reused.
+  std::vector<int32_t> groot(ns, -1), gh(ns, 0);
+  std::vector<std::vector<int32_t>> gmem(ns);
+  auto tiny = [&](int st) {
+    const StepGeom& g = p->steps[st].g;
+    int kernel, tile, split;
+    dev::pick_launch(g, s, np, &kernel, &tile, &split);
+    return kernel == kKernNaive && g.rc <= 10 && g.rc + g.nk <= 13;
+  };
+  if (H > 1) {
+    for (int st = 0; st < ns; ++st) {  // plan order is topological
+      if (!tiny(st)) continue;
+      groot[st] = st;
+      gh[st] = 1;
+      gmem[st] = {st};
+      for (int32_t id : {p->steps[st].a_id, p->steps[st].b_id}) {
+        const int pr = prod(id);
+        if (pr < 0 || groot[pr] != pr || gh[pr] + 1 > H) continue;
+        for (int32_t m : gmem[pr]) groot[m] = st;
+        gmem[st].insert(gmem[st].end(), gmem[pr].begin(), gmem[pr].end());
+        gmem[pr].clear();
+        gh[st] = std::max(gh[st], gh[pr] + 1);
+      }
+    }
+  }
+  // a group of one step is an ordinary step
+  for (int st = 0; st < ns; ++st)
+    if (groot[st] == st && gmem[st].size() < 2) groot[st] = -1;
+  auto internal = [&](int st) { return groot[st] >= 0 && groot[st] != st; };
+  auto owner = [&](int st) { return internal(st) ? groot[st] : st; };  // step that runs st
+
   // memory: a level's outputs may only reuse memory released by earlier
-  // levels; the releasing steps become (write-after-read) dependencies
+  // levels; the releasing steps become (write-after-read) dependencies.
+  // Inputs consumed inside a group are released when the group's root level
+  // is reached, by the root.
   std::vector<std::vector<int32_t>> dep(ns);  // in plan-step indices
   std::vector<int64_t> c_off(ns, 0);
   LevelArena arena;
@@ -110,24 +160,36 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
     while (j < ns && level[order[j]] == level[order[i]]) ++j;
     for (int x = i; x < j; ++x) {
       const int st = order[x];
+      if (internal(st)) continue;
       const Step& S = p->steps[st];
       std::vector<int32_t> war;
       c_off[st] = arena.alloc(int64_t(1) << S.g.rc, &war);
       dep[st] = war;
-      for (int32_t id : {S.a_id, S.b_id})
-        if (prod(id) >= 0) dep[st].push_back(prod(id));
     }
     for (int x = i; x < j; ++x) {
       const int st = order[x];
-      const Step& S = p->steps[st];
-      for (int32_t id : {S.a_id, S.b_id}) {
-        int pr = prod(id);
-        if (pr >= 0) arena.release(c_off[pr], int64_t(1) << p->steps[pr].g.rc, st);
+      if (internal(st)) continue;
+      const std::vector<int32_t> runs = groot[st] == st ? gmem[st] : std::vector<int32_t>{st};
+      for (int32_t m : runs) {
+        const Step& S = p->steps[m];
+        for (int32_t id : {S.a_id, S.b_id}) {
+          const int pr = prod(id);
+          if (pr < 0 || owner(pr) == st) continue;  // a leaf, or internal to this group
+          dep[st].push_back(owner(pr));
+          arena.release(c_off[pr], int64_t(1) << p->steps[pr].g.rc, st);
+        }
       }
     }
     i = j;
   }
-  X->arena_entries = std::max<int64_t>(arena.top(), kArenaAlign);
+  // internal tensors after the shared arena
+  int64_t top = arena.top();
+  for (int st = 0; st < ns; ++st)
+    if (internal(st)) {
+      c_off[st] = top;
+      top += static_cast<int64_t>(align_up(size_t(1) << p->steps[st].g.rc, kArenaAlign));
+    }
+  X->arena_entries = std::max<int64_t>(top, kArenaAlign);
 
   // transitive reduction of the dependencies (ancestor bitsets, exec order)
   const int words = (ns + 63) / 64;
@@ -162,6 +224,8 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   X->steps.assign(ns, ExecStep());
   X->deps.clear();
   X->tasks.clear();
+  X->group_begin.clear();
+  X->group_members.clear();
   size_t scratch = 0;
   int32_t arrive = 0;
   for (int x = 0; x < ns; ++x) {
@@ -179,7 +243,25 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
     X->deps.insert(X->deps.end(), red[st].begin(), red[st].end());
     int kernel, tile, split;
     dev::pick_launch(S.g, s, np, &kernel, &tile, &split);
-    if (kernel == kKernTiled && S.g.c_identity) {
+    if (internal(st) || groot[st] == st) {
+      // group member: one whole-output chunk, no k split
+      const dev::NaiveShape sh = dev::naive_shape(S.g.rc, S.g.nk, false);
+      E.kernel = kKernNaive;
+      E.R = sh.R;
+      E.chunk = int64_t(1) << S.g.rc;
+      E.ks = 1;
+      E.nchunks = 1;
+      E.ntasks = internal(st) ? 0 : 1;
+      if (groot[st] == st) {
+        // members in execution order (level, then plan order)
+        std::vector<int32_t> mem = gmem[st];
+        std::sort(mem.begin(), mem.end(), [&](int a, int b) { return pos[a] < pos[b]; });
+        const int32_t gid = static_cast<int32_t>(X->group_begin.size());
+        X->group_begin.push_back(static_cast<int32_t>(X->group_members.size()));
+        for (int32_t m : mem) X->group_members.push_back(pos[m]);
+        for (int q = 0; q < np; ++q) X->tasks.push_back(ExecTask{x, gid, q, kTaskGroup});
+      }
+    } else if (kernel == kKernTiled && S.g.c_identity) {
       const int64_t bm = dev::tiled_tile_bm(tile), bn = dev::tiled_tile_bn(tile);
       E.kernel = kKernTiled;
       E.tile = tile;
@@ -209,10 +291,13 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
         scratch += align_up(static_cast<size_t>(sh.nchunks * np * sh.ks * sh.chunk) * acc_bytes, 256);
       }
     }
-    for (int q = 0; q < np; ++q)
-      for (int t = 0; t < E.ntasks; ++t)
-        X->tasks.push_back(ExecTask{x, t, q, E.kernel == kKernTiled ? kTaskTile : kTaskNaive});
+    if (groot[st] < 0)
+      for (int q = 0; q < np; ++q)
+        for (int t = 0; t < E.ntasks; ++t)
+          X->tasks.push_back(ExecTask{x, t, q, E.kernel == kKernTiled ? kTaskTile : kTaskNaive});
   }
+  X->ngroups = static_cast<int32_t>(X->group_begin.size());
+  X->group_begin.push_back(static_cast<int32_t>(X->group_members.size()));
   X->root_step = pos[ns - 1];
   X->root_off = c_off[ns - 1];
 
@@ -237,8 +322,9 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
         const int sx = order[x];
         const int64_t x0 = c_off[sx], x1 = x0 + (int64_t(1) << p->steps[sx].g.rc);
         if (x1 <= y0 || y1 <= x0) continue;
+        if (internal(sx) || internal(sy)) return TN_EINVAL;  // internal tensors are never shared
         const int cons = p->tensors[p->steps[sx].c_id].consumer;
-        if (cons < 0 || !is_anc(pos[cons], y)) return TN_EINVAL;
+        if (cons < 0 || !is_anc(pos[owner(cons)], y)) return TN_EINVAL;
       }
     }
   }
@@ -265,8 +351,13 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   X->off_steps = 0;
   X->off_deps = align_up(sizeof(ExecStep) * X->steps.size(), 256);
   X->off_tasks = X->off_deps + align_up(sizeof(int32_t) * (X->deps.size() + 1), 256);
-  X->table_bytes = X->off_tasks + sizeof(ExecTask) * X->tasks.size();
+  X->off_groups = X->off_tasks + align_up(sizeof(ExecTask) * X->tasks.size(), 256);
+  X->off_members = X->off_groups + align_up(sizeof(int32_t) * X->group_begin.size(), 256);
+  X->table_bytes = X->off_members + sizeof(int32_t) * (X->group_members.size() + 1);
   X->table_image.assign(X->table_bytes, 0);
+  std::memcpy(X->table_image.data() + X->off_groups, X->group_begin.data(), sizeof(int32_t) * X->group_begin.size());
+  std::memcpy(X->table_image.data() + X->off_members, X->group_members.data(),
+              sizeof(int32_t) * X->group_members.size());
   std::memcpy(X->table_image.data() + X->off_steps, X->steps.data(), sizeof(ExecStep) * X->steps.size());
   std::memcpy(X->table_image.data() + X->off_deps, X->deps.data(), sizeof(int32_t) * X->deps.size());
   std::memcpy(X->table_image.data() + X->off_tasks, X->tasks.data(), sizeof(ExecTask) * X->tasks.size());
@@ -276,6 +367,10 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
 }  // namespace
 
 ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc) {
+  return exec_plan_get_h(p, s, nprimes, group_height(), rc);
+}
+
+ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H, int* rc) {
   if (!p->exec_cache) {
     static std::mutex init_mu;
     std::lock_guard<std::mutex> lk(init_mu);
@@ -285,11 +380,12 @@ ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc)
   const int np = s == TN_COUNT_MODP ? nprimes : 1;
   std::lock_guard<std::mutex> lk(c->mu);
   for (auto& x : c->plans)
-    if (x->semiring == s && x->nprimes == np) {
+    if (x->semiring == s && x->nprimes == np && x->group_h == H) {
       *rc = TN_OK;
       return x.get();
     }
   std::unique_ptr<ExecPlan> X(new ExecPlan());
+  X->group_h = H;
   *rc = build_exec(p, s, nprimes, X.get());
   if (*rc != TN_OK) return nullptr;
   c->plans.push_back(std::move(X));

@@ -326,13 +326,16 @@ def test_gemm_steps_all_semirings(shape, mode, monkeypatch):
         assert np.array_equal(out[q * E:(q + 1) * E].astype(np.uint64), O.pair_modp(Am[q], LA, Bm[q], LB, LC, p))
 
 
+@pytest.mark.parametrize("height", ["1", "4", "64"])
 @pytest.mark.parametrize("execu", ["1", "0"])
 @pytest.mark.parametrize("mode", ["tiled", "naive", "auto"])
-def test_networks_both_kernels(mode, execu, monkeypatch):
+def test_networks_both_kernels(mode, execu, height, monkeypatch):
     """Whole contractions with every step forced onto one kernel, through the
-    persistent executor (one launch) and through per-step launches."""
+    persistent executor (one launch; tiny steps grouped up to `height` per
+    CTA task) and through per-step launches."""
     monkeypatch.setenv("TN_KERNEL", mode)
     monkeypatch.setenv("TN_EXEC", execu)
+    monkeypatch.setenv("TN_GROUP_HEIGHT", height)
     for spec in ["reg3:20:1", "ksg:5:0.8:4", "er:16:0.25:1", "empty:3", "er:20:0.12:9"]:
         n, e = g.by_name(spec)
         poly = O.bruteforce_poly(n, e)

@@ -159,18 +159,23 @@ def test_result_decode_crt_matches_oracle():
         tn.tn_result_decode(tn.TN_COUNT_MODP, [6, 9], bytes(raw))   # moduli not coprime
 
 
+@pytest.mark.parametrize("height", ["1", "4", "64"])
 @pytest.mark.parametrize("spec", ["reg3:140:1", "ksg:12:0.8:2", "er:40:0.08:1", "empty:7", "square:8"])
-def test_executor_schedule_self_check(spec, monkeypatch):
+def test_executor_schedule_self_check(spec, height, monkeypatch):
     """The executor's task order and workspace reuse pass the library's own
     schedule check (dependencies point backwards; a step never overwrites a
-    tensor some non-ancestor step still reads)."""
+    tensor some non-ancestor step still reads), with and without groups of
+    tiny steps run by one CTA."""
     monkeypatch.setenv("TN_EXEC_CHECK", "1")
+    monkeypatch.setenv("TN_GROUP_HEIGHT", height)
     n, e = g.by_name(spec)
     p = tn.tn_plan(n, e, tn.tn_order_greedy(n, e, 0.0, 2, 3))
     try:
         for sr in (tn.TN_TROPICAL_I32, tn.TN_COUNTING_TROPICAL, tn.TN_COUNT_MODP):
             info = tn.tn_plan_info(p, sr, 3)
-            assert info["exec_tasks"] >= info["nsteps"] + 1
+            assert info["exec_tasks"] >= 2
+            if height == "1":
+                assert info["exec_tasks"] >= info["nsteps"] + 1
             assert info["exec_levels"] >= 1
     finally:
         tn.tn_plan_destroy(p)
