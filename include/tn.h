@@ -251,12 +251,17 @@ int tn_batch_contract_graph(tn_batch_t batch, void *d_workspace, size_t ws_bytes
                             void *d_raw);
 void tn_batch_destroy(tn_batch_t batch);
 
-/* Serving (continuous batching).  A server owns a worker thread, a CUDA
- * stream pool and an HBM budget; tn_submit admits a request once the peak
- * workspace of its plan fits in the free part of the budget and fewer than
- * max_inflight requests run, and returns a ticket at once.  tn_poll returns
- * TN_EAGAIN until the ticket's result is ready, then TN_OK (the result is
- * handed out once).  The plan must outlive its request. */
+/* Serving (continuous batching).  A server owns a worker thread, up to
+ * max_inflight (1..64) concurrent grouped launches, each on a stream of its
+ * own, and an HBM budget.  tn_submit queues a request and returns a ticket at
+ * once (TN_ENOMEM if its plan alone exceeds the budget).  Whenever a launch
+ * slot is free, the worker takes the oldest pending request and, in arrival
+ * order, the other pending requests with the same semiring and primes whose
+ * predicted workspaces (tn_plan_info peak_bytes) still fit in the unused
+ * budget (up to 512), and runs them as one persistent executor launch, so
+ * requests that arrive while others run overlap with them on the device.
+ * tn_poll returns TN_EAGAIN until the ticket's result is ready, then TN_OK
+ * (the result is handed out once).  The plan must outlive its request. */
 int tn_server_create(size_t hbm_budget_bytes, int32_t max_inflight, tn_server_t *out);
 int tn_submit(tn_server_t server, tn_plan_t plan, tn_semiring_t semiring, const uint32_t *primes,
               int32_t nprimes, uint64_t *ticket);

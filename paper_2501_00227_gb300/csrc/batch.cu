@@ -51,16 +51,22 @@ namespace {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-int build_batch(tn_batch_s* B, const tn_plan_t* plans, int32_t count) {
-  using namespace tn;
+}  // namespace
+
+namespace tn {
+
+// Merges the executor plans of `count` networks into one plan M (see the
+// file comment).  nprimes: as given to the mod-p semiring (1 otherwise).
+int build_batch_plan(tn_plan_s* const* plans, int32_t count, tn_semiring_t semiring, int32_t nprimes,
+                     int group_h, ExecPlan* out) {
   std::vector<ExecPlan*> xs(count);
   for (int i = 0; i < count; ++i) {
     int rc;
-    xs[i] = exec_plan_get_h(plans[i], B->semiring, B->nprimes, B->group_h, &rc);
+    xs[i] = exec_plan_get_h(plans[i], semiring, nprimes, group_h, &rc);
     if (!xs[i]) return rc;
   }
-  ExecPlan& M = B->X;
-  M.semiring = B->semiring;
+  ExecPlan& M = *out;
+  M.semiring = semiring;
   M.nprimes = xs.empty() ? 1 : xs[0]->nprimes;
   std::vector<int64_t> step_base(count), arena_base(count), group_base(count);
   std::vector<size_t> scratch_base(count);
@@ -152,7 +158,7 @@ int build_batch(tn_batch_s* B, const tn_plan_t* plans, int32_t count) {
   M.arena_base = M.scratch_base + align_up(scratch, 256);
   const size_t e = static_cast<size_t>(M.arena_entries);
   size_t regions = 0;
-  switch (B->semiring) {
+  switch (semiring) {
     case TN_TROPICAL_F32:
     case TN_TROPICAL_I32: regions = align_up(4 * e, 256); break;
     case TN_COUNTING_TROPICAL: regions = align_up(4 * e, 256) + align_up(8 * e, 256); break;
@@ -211,7 +217,7 @@ int tn_batch_create(const tn_plan_t* plans, int32_t count, tn_semiring_t semirin
   int rc = tn::make_mod_table_checked(semiring, primes, nprimes, B->mods);
   if (rc) return rc;
   try {
-    rc = build_batch(B.get(), plans, count);
+    rc = tn::build_batch_plan(plans, count, semiring, B->nprimes, B->group_h, &B->X);
   } catch (const std::bad_alloc&) {
     rc = TN_ENOMEM;
   }

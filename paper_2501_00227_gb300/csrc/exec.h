@@ -58,7 +58,7 @@ struct ExecPlan {
   std::vector<int32_t> group_begin;  // group g's members: group_members[begin[g] .. begin[g+1])
   std::vector<int32_t> group_members;  // exec-step indices, in execution order
   int32_t ngroups = 0;
-  int32_t group_h = 4;               // group height limit the plan was built with
+  int32_t group_h = 1;               // group height limit the plan was built with
   int64_t arena_entries = 0;
   int64_t root_off = 0;
   int32_t root_step = -1;
@@ -84,7 +84,7 @@ ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc)
 // The same with an explicit group height (largest tree of tiny steps one
 // CTA runs back to back; 1 disables grouping).
 ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int height, int* rc);
-// TN_GROUP_HEIGHT, else 4.
+// TN_GROUP_HEIGHT, else 1.
 int group_height();
 void exec_plans_free(tn_plan_s* p);
 
@@ -95,6 +95,10 @@ int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods, int32_t nprime
 // Launches the executor with the tables already on the device at d_tables.
 int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods, void* ws, void* stream, void* d_raw,
                      void* d_trace, const void* d_tables);
+
+// Merges the executor plans of several networks into one launch (batch.cu).
+int build_batch_plan(tn_plan_s* const* plans, int32_t count, tn_semiring_t semiring, int32_t nprimes,
+                     int group_h, ExecPlan* out);
 
 // One-time kernel set-up of the executor instantiation a launch would use
 // (attributes, occupancy), so that a later launch can be graph-captured.

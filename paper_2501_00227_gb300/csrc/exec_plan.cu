@@ -26,11 +26,13 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
-// Largest height of a group of tiny steps run by one CTA (TN_GROUP_HEIGHT,
-// default 4; 0 or 1 disables grouping).
+// Largest height of a group of tiny steps run by one CTA for a single
+// contraction (TN_GROUP_HEIGHT, default 1 = no grouping: a lone contraction
+// is latency-bound and the dependency levels already run in parallel;
+// batches and the server group whole tiny subtrees, see batch.cu).
 int group_height() {
   const char* e = getenv("TN_GROUP_HEIGHT");
-  if (!e || !*e) return 4;
+  if (!e || !*e) return 1;
   return atoi(e);
 }
 

@@ -1,15 +1,19 @@
-// server.cpp -- serving entry points of libtn (tn_server_create, tn_submit,
+// server.cu -- serving entry points of libtn (tn_server_create, tn_submit,
 // tn_poll, tn_server_destroy): continuous batching of contraction requests.
 //
-// Requests of any size and semiring arrive at any time.  A worker thread
-// admits a pending request as soon as (a) the predicted peak workspace of its
-// plan (the space complexity of its order, Sec. 4.1 of arXiv:2501.00227,
-// times the bytes per entry) fits in the unused part of the HBM budget and
-// (b) fewer than max_inflight requests run.  Each admitted request gets a
-// stream from a pool and a stream-ordered workspace allocation; its kernels
-// overlap on the device with those of every other running request.  The
-// worker retires finished requests in completion order, decodes their result
-// on the host and frees their workspace, which admits more requests.
+// Requests of any size and semiring arrive at any time; tn_submit only
+// queues them.  A worker thread keeps up to max_inflight grouped launches on
+// the GPU, each on a stream of its own.  Whenever a launch slot is free it
+// takes the oldest pending request and, in arrival order, every other
+// pending request with the same semiring and primes, as long as the sum of
+// their predicted workspaces (the executor layout of each plan: its space
+// complexity, Sec. 4.1 of arXiv:2501.00227, times the bytes per entry, plus
+// scratch) fits in the unused part of the HBM budget; these go out as ONE
+// persistent executor launch (the batch machinery of batch.cu).  Requests
+// that arrive while launches run join the next free slot, so their work
+// overlaps on the device with the launches still running.  The worker
+// retires launches as they complete, decodes every request's scalar on the
+// host and frees the launch's memory, which admits more requests.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -17,43 +21,52 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
 #include <vector>
 
+#include "exec.h"
 #include "kernels.h"
 #include "tn_internal.h"
 
 namespace tn {
-int contract_enqueue(const tn_plan_s* p, tn_semiring_t s, const dev::ModTable& mods,
-                     int32_t nprimes, void* ws, cudaStream_t st, void* d_raw,
-                     cudaEvent_t* step_events);
-int decode_raw(tn_semiring_t s, const dev::ModTable& mods, int32_t nprimes,
-               const unsigned char* raw, tn_result_t* out);
+int decode_raw(tn_semiring_t s, const dev::ModTable& mods, int32_t nprimes, const unsigned char* raw,
+               tn_result_t* out);
 size_t required_bytes(tn_plan_s* p, tn_semiring_t s, int32_t nprimes);
+int make_mod_table_checked(tn_semiring_t s, const uint32_t* primes, int32_t nprimes, void* mods);
 }  // namespace tn
 
 namespace {
 
+constexpr int kMaxBatch = 512;  // requests per grouped launch
+
 struct Request {
   uint64_t ticket;
-  const tn_plan_s* plan;
+  tn_plan_s* plan;
   tn_semiring_t semiring;
   std::vector<uint32_t> primes;
   size_t bytes;
-  // while running
-  int slot = -1;
-  void* ws = nullptr;
 };
 
-struct Slot {
+struct Flight {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  unsigned char* h_raw = nullptr;  // pinned, TN_RAW_BYTES
+  unsigned char* h_raw = nullptr;  // pinned, kMaxBatch * TN_RAW_BYTES
   bool busy = false;
-  Request req;
+  std::vector<Request> reqs;
+  std::unique_ptr<tn::ExecPlan> plan;
+  tn::dev::ModTable mods;
+  void* ws = nullptr;
+  void* d_raw = nullptr;
+  void* d_tables = nullptr;
+  size_t bytes = 0;
 };
+
+bool same_key(const Request& a, const Request& b) {
+  return a.semiring == b.semiring && a.primes == b.primes;
+}
 
 }  // namespace
 
@@ -66,24 +79,67 @@ struct tn_server_s {
   std::deque<Request> pending;
   std::unordered_map<uint64_t, tn_result_t> done;
   std::unordered_map<uint64_t, int> state;  // 0 pending, 1 running, 2 done
-  std::vector<Slot> slots;
+  std::vector<Flight> flights;
   uint64_t next_ticket = 1;
   std::atomic<bool> stop{false};
   std::thread worker;
-  int fatal = TN_OK;
 };
 
 namespace {
 
-int make_mod_table(tn_semiring_t s, const std::vector<uint32_t>& pr, tn::dev::ModTable* mt) {
-  std::memset(mt, 0, sizeof(*mt));
-  mt->q[0].p = 2;
-  if (s != TN_COUNT_MODP) return TN_OK;
-  for (size_t i = 0; i < pr.size(); ++i) {
-    mt->q[i].p = pr[i];
-    mt->q[i].r32 = static_cast<uint32_t>((uint64_t(1) << 32) % pr[i]);
-    mt->q[i].mu = ~0ull / pr[i];
+void finish_with_status(tn_server_s* S, const std::vector<Request>& reqs, int status) {
+  for (const Request& r : reqs) {
+    tn_result_t res;
+    std::memset(&res, 0, sizeof(res));
+    res.status = status;
+    S->done[r.ticket] = res;
+    S->state[r.ticket] = 2;
   }
+}
+
+void release_flight(Flight& f) {
+  if (f.ws) cudaFreeAsync(f.ws, f.stream);
+  if (f.d_raw) cudaFreeAsync(f.d_raw, f.stream);
+  if (f.d_tables) cudaFreeAsync(f.d_tables, f.stream);
+  f.ws = f.d_raw = f.d_tables = nullptr;
+  f.plan.reset();
+  f.reqs.clear();
+  f.busy = false;
+}
+
+// Launches `reqs` as one grouped executor launch on flight f.
+int launch_flight(tn_server_s* S, Flight& f, std::vector<Request>&& reqs) {
+  f.reqs = std::move(reqs);
+  const Request& r0 = f.reqs.front();
+  const int32_t np = static_cast<int32_t>(r0.primes.size());
+  int rc = tn::make_mod_table_checked(r0.semiring, np ? r0.primes.data() : nullptr, np, &f.mods);
+  if (rc) return rc;
+  std::vector<tn_plan_s*> plans;
+  for (const Request& r : f.reqs) plans.push_back(r.plan);
+  f.plan.reset(new tn::ExecPlan());
+  try {
+    rc = tn::build_batch_plan(plans.data(), static_cast<int32_t>(plans.size()), r0.semiring, np < 1 ? 1 : np,
+                              64, f.plan.get());
+  } catch (const std::bad_alloc&) {
+    rc = TN_ENOMEM;
+  }
+  if (rc) return rc;
+  tn::ExecPlan& X = *f.plan;
+  const size_t raw_bytes = f.reqs.size() * TN_RAW_BYTES;
+  if (cudaMallocAsync(&f.ws, X.total_bytes, f.stream) != cudaSuccess ||
+      cudaMallocAsync(&f.d_raw, raw_bytes, f.stream) != cudaSuccess ||
+      cudaMallocAsync(&f.d_tables, X.table_bytes, f.stream) != cudaSuccess)
+    return TN_ENOMEM;
+  if (cudaMemcpyAsync(f.d_tables, X.table_image.data(), X.table_bytes, cudaMemcpyHostToDevice, f.stream) !=
+      cudaSuccess)
+    return TN_ECUDA;
+  rc = tn::exec_launch_core(&X, r0.semiring, &f.mods, f.ws, f.stream, f.d_raw, nullptr, f.d_tables);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(f.h_raw, f.d_raw, raw_bytes, cudaMemcpyDeviceToHost, f.stream) != cudaSuccess ||
+      cudaEventRecord(f.done, f.stream) != cudaSuccess)
+    return TN_ECUDA;
+  f.bytes = X.total_bytes;
+  f.busy = true;
   return TN_OK;
 }
 
@@ -92,77 +148,63 @@ void worker_loop(tn_server_s* S) {
   std::unique_lock<std::mutex> lk(S->mu);
   while (!S->stop.load()) {
     bool progressed = false;
-    // admit: first-come first-served among requests that fit
-    for (auto it = S->pending.begin(); it != S->pending.end();) {
-      int free_slot = -1;
-      for (size_t k = 0; k < S->slots.size(); ++k)
-        if (!S->slots[k].busy) { free_slot = static_cast<int>(k); break; }
-      if (free_slot < 0) break;
-      if (S->used + it->bytes > S->budget) { ++it; continue; }
-      Request r = *it;
-      it = S->pending.erase(it);
-      Slot& sl = S->slots[free_slot];
-      void* ws = nullptr;
-      tn::dev::ModTable mods;
-      make_mod_table(r.semiring, r.primes, &mods);
-      int rc = cudaMallocAsync(&ws, r.bytes, sl.stream) == cudaSuccess ? TN_OK : TN_ENOMEM;
-      if (rc == TN_OK)
-        rc = tn::contract_enqueue(r.plan, r.semiring, mods, static_cast<int32_t>(r.primes.size()),
-                                  ws, sl.stream, static_cast<char*>(ws) + 64, nullptr);
-      if (rc == TN_OK)
-        rc = cudaMemcpyAsync(sl.h_raw, static_cast<char*>(ws) + 64, TN_RAW_BYTES,
-                             cudaMemcpyDeviceToHost, sl.stream) == cudaSuccess ? TN_OK : TN_ECUDA;
-      if (rc == TN_OK)
-        rc = cudaEventRecord(sl.done, sl.stream) == cudaSuccess ? TN_OK : TN_ECUDA;
-      if (rc != TN_OK) {
-        if (ws) cudaFreeAsync(ws, sl.stream);
+    // retire finished launches
+    for (Flight& f : S->flights) {
+      if (!f.busy) continue;
+      cudaError_t q = cudaEventQuery(f.done);
+      if (q == cudaErrorNotReady) continue;
+      for (size_t i = 0; i < f.reqs.size(); ++i) {
         tn_result_t res;
         std::memset(&res, 0, sizeof(res));
-        res.status = rc;
-        S->done[r.ticket] = res;
-        S->state[r.ticket] = 2;
-        continue;
+        if (q != cudaSuccess) {
+          res.status = TN_ECUDA;
+        } else {
+          const int32_t np = static_cast<int32_t>(f.reqs[i].primes.size());
+          int rc = tn::decode_raw(f.reqs[i].semiring, f.mods, np, f.h_raw + i * TN_RAW_BYTES, &res);
+          if (rc != TN_OK) res.status = rc;
+        }
+        S->done[f.reqs[i].ticket] = res;
+        S->state[f.reqs[i].ticket] = 2;
       }
-      r.slot = free_slot;
-      r.ws = ws;
-      sl.req = r;
-      sl.busy = true;
-      S->used += r.bytes;
-      S->state[r.ticket] = 1;
+      S->used -= f.bytes;
+      release_flight(f);
       progressed = true;
     }
-    // retire finished requests
-    for (auto& sl : S->slots) {
-      if (!sl.busy) continue;
-      cudaError_t q = cudaEventQuery(sl.done);
-      if (q == cudaErrorNotReady) continue;
-      tn_result_t res;
-      std::memset(&res, 0, sizeof(res));
-      if (q != cudaSuccess) {
-        res.status = TN_ECUDA;
-      } else {
-        tn::dev::ModTable mods;
-        make_mod_table(sl.req.semiring, sl.req.primes, &mods);
-        int rc = tn::decode_raw(sl.req.semiring, mods, static_cast<int32_t>(sl.req.primes.size()),
-                                sl.h_raw, &res);
-        if (rc != TN_OK) res.status = rc;
+    // fill free launch slots
+    for (Flight& f : S->flights) {
+      if (f.busy || S->pending.empty()) continue;
+      std::vector<Request> take;
+      size_t bytes = 0;
+      const Request key = S->pending.front();
+      for (auto it = S->pending.begin(); it != S->pending.end() && take.size() < kMaxBatch;) {
+        if (same_key(*it, key) && S->used + bytes + it->bytes <= S->budget) {
+          bytes += it->bytes;
+          take.push_back(*it);
+          it = S->pending.erase(it);
+        } else {
+          ++it;
+        }
       }
-      cudaFreeAsync(sl.req.ws, sl.stream);
-      S->used -= sl.req.bytes;
-      S->done[sl.req.ticket] = res;
-      S->state[sl.req.ticket] = 2;
-      sl.busy = false;
+      if (take.empty()) break;  // the oldest request waits for memory
+      for (const Request& r : take) S->state[r.ticket] = 1;
+      int rc = launch_flight(S, f, std::move(take));
+      if (rc != TN_OK) {
+        finish_with_status(S, f.reqs, rc);
+        release_flight(f);
+        continue;
+      }
+      S->used += f.bytes;
       progressed = true;
     }
     bool any_busy = false;
-    for (auto& sl : S->slots) any_busy |= sl.busy;
+    for (const Flight& f : S->flights) any_busy |= f.busy;
     if (!progressed) {
       if (any_busy) {
         lk.unlock();
         std::this_thread::sleep_for(std::chrono::microseconds(20));
         lk.lock();
       } else {
-        S->cv.wait_for(lk, std::chrono::milliseconds(50));
+        S->cv.wait_for(lk, std::chrono::milliseconds(20));
       }
     }
   }
@@ -173,7 +215,7 @@ void worker_loop(tn_server_s* S) {
 extern "C" {
 
 int tn_server_create(size_t hbm_budget_bytes, int32_t max_inflight, tn_server_t* out) {
-  if (!out || max_inflight < 1 || max_inflight > 1024 || hbm_budget_bytes == 0) return TN_EINVAL;
+  if (!out || max_inflight < 1 || max_inflight > 64 || hbm_budget_bytes == 0) return TN_EINVAL;
   *out = nullptr;
   tn_server_s* S = new (std::nothrow) tn_server_s();
   if (!S) return TN_ENOMEM;
@@ -183,11 +225,11 @@ int tn_server_create(size_t hbm_budget_bytes, int32_t max_inflight, tn_server_t*
     delete S;
     return TN_ECUDA;
   }
-  S->slots.resize(static_cast<size_t>(max_inflight));
-  for (auto& sl : S->slots) {
-    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost(reinterpret_cast<void**>(&sl.h_raw), TN_RAW_BYTES) != cudaSuccess) {
+  S->flights.resize(static_cast<size_t>(max_inflight));
+  for (Flight& f : S->flights) {
+    if (cudaStreamCreateWithFlags(&f.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&f.h_raw), size_t(kMaxBatch) * TN_RAW_BYTES) != cudaSuccess) {
       tn_server_destroy(S);
       return TN_ECUDA;
     }
@@ -197,22 +239,16 @@ int tn_server_create(size_t hbm_budget_bytes, int32_t max_inflight, tn_server_t*
   return TN_OK;
 }
 
-int tn_submit(tn_server_t S, tn_plan_t plan, tn_semiring_t semiring, const uint32_t* primes,
-              int32_t nprimes, uint64_t* ticket) {
+int tn_submit(tn_server_t S, tn_plan_t plan, tn_semiring_t semiring, const uint32_t* primes, int32_t nprimes,
+              uint64_t* ticket) {
   if (!S || !plan || !ticket) return TN_EINVAL;
-  if (semiring < TN_TROPICAL_F32 || semiring > TN_COUNT_MODP) return TN_EINVAL;
   Request r;
   r.plan = plan;
   r.semiring = semiring;
-  if (semiring == TN_COUNT_MODP) {
-    if (!primes || nprimes < 1 || nprimes > TN_MAX_PRIMES) return TN_EINVAL;
-    tn_result_t scratch;
-    // validates the moduli the same way tn_contract does
-    unsigned char zero[TN_RAW_BYTES] = {0};
-    int rc = tn_result_decode(semiring, primes, nprimes, zero, &scratch);
-    if (rc != TN_OK) return rc;
-    r.primes.assign(primes, primes + nprimes);
-  }
+  tn::dev::ModTable mods;
+  int rc = tn::make_mod_table_checked(semiring, primes, nprimes, &mods);
+  if (rc) return rc;
+  if (semiring == TN_COUNT_MODP) r.primes.assign(primes, primes + nprimes);
   r.bytes = tn::required_bytes(plan, semiring, nprimes);
   if (r.bytes > S->budget) return TN_ENOMEM;
   {
@@ -243,12 +279,13 @@ void tn_server_destroy(tn_server_t S) {
   S->stop.store(true);
   S->cv.notify_all();
   if (S->worker.joinable()) S->worker.join();
-  for (auto& sl : S->slots) {
-    if (sl.stream) cudaStreamSynchronize(sl.stream);
-    if (sl.busy && sl.req.ws) cudaFree(sl.req.ws);
-    if (sl.h_raw) cudaFreeHost(sl.h_raw);
-    if (sl.done) cudaEventDestroy(sl.done);
-    if (sl.stream) cudaStreamDestroy(sl.stream);
+  for (Flight& f : S->flights) {
+    if (f.stream) cudaStreamSynchronize(f.stream);
+    if (f.busy) release_flight(f);
+    if (f.stream) cudaStreamSynchronize(f.stream);
+    if (f.h_raw) cudaFreeHost(f.h_raw);
+    if (f.done) cudaEventDestroy(f.done);
+    if (f.stream) cudaStreamDestroy(f.stream);
   }
   delete S;
 }
