@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["tn", "reference"], default="tn")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -175,6 +177,134 @@ def run_reference(args):
             "e2e": {"value": val, "unit": "Gop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def batching_bench(tn, torch, count: int = 4096):
+    """Grouped persistent launch of `count` random 3-regular graphs with n
+    uniform over the even numbers in [30, 60] (seed 0), MIS size and MIS count
+    per instance, replayed from a CUDA graph; compared with one executor
+    launch per instance (timed on the first 512 instances)."""
+    rng = np.random.default_rng(0)
+    ns = rng.integers(15, 31, size=count) * 2
+    t0 = time.perf_counter()
+    plans = [tn.Plan(*graphgen.random_regular3(int(n), 10000 + i), nrepeat=2, seed=1) for i, n in enumerate(ns)]
+    plan_s = time.perf_counter() - t0
+    out = {"workload": f"{count} random 3-regular graphs, n uniform even in [30,60], seed 0",
+           "plan_s": plan_s}
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for sr in ("tropical_i32", "counting"):
+        ops = sum(p.info(sr, 1)["tc"] for p in plans)
+        b = tn.Batch(plans, sr)
+        res = b.run(graph=True)
+        for _ in range(3):
+            b.launch(graph=True)
+        torch.cuda.synchronize()
+        reps = 10
+        e0.record(stream)
+        for _ in range(reps):
+            b.launch(graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        if b.results() != res:
+            raise RuntimeError("batched results changed between launches")
+        S = min(count, 512)
+        ws = torch.empty(max(p.workspace_bytes(sr) for p in plans[:S]), dtype=torch.uint8, device="cuda")
+        raw = torch.zeros(tn.TN_RAW_BYTES, dtype=torch.uint8, device="cuda")
+        for p in plans[:16]:
+            tn.tn_contract_async(p.handle, sr, None, ws.data_ptr(), ws.numel(), stream.cuda_stream, raw.data_ptr())
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for p in plans[:S]:
+            tn.tn_contract_async(p.handle, sr, None, ws.data_ptr(), ws.numel(), stream.cuda_stream, raw.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per_ms = e0.elapsed_time(e1) / S
+        out[sr] = {"ms_per_batch": ms, "inst_per_s": count / ms * 1e3, "gops": ops / ms / 1e6,
+                   "per_instance_launch_inst_per_s": 1e3 / per_ms,
+                   "speedup_vs_per_instance": (count / ms) / (1.0 / per_ms), "tasks": b.info["tasks"]}
+        b.close()
+    for p in plans:
+        p.close()
+    return out
+
+
+def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120):
+    """Poisson request stream mixing random 3-regular graphs (n even in
+    [40,160]) and King's subgraphs (L in [8,16], filling 0.8), each asking the
+    MIS size, the MIS count or the count of all independent sets mod 4 primes,
+    served with continuous batching under a 120 GB budget.  Plain baseline:
+    the same requests one at a time (synchronous tn_contract)."""
+    rng = np.random.default_rng(5)
+    pool = []
+    for i in range(96):
+        if i % 2 == 0:
+            n, e = graphgen.random_regular3(int(rng.integers(20, 81)) * 2, 20000 + i)
+        else:
+            n, e = graphgen.kings_subgraph(int(rng.integers(8, 17)), 0.8, 30000 + i)
+        pool.append(tn.Plan(n, e, nrepeat=2, seed=1))
+    kinds = [("tropical_i32", None), ("counting", None), ("modp", tuple(tn.PRIMES31[:4]))]
+    reqs = [(pool[int(rng.integers(0, len(pool)))], *kinds[int(rng.integers(0, 3))]) for _ in range(nreq)]
+    need = max(p.workspace_bytes(sr, len(pr) if pr else 1) for p, sr, pr in reqs)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    # plain: one request at a time
+    for p, sr, pr in reqs[:20]:
+        tn.tn_contract(p.handle, sr, pr, ws.data_ptr(), need, st)
+    lat = []
+    t0 = time.perf_counter()
+    ref = []
+    for p, sr, pr in reqs:
+        t = time.perf_counter()
+        ref.append(tn.tn_contract(p.handle, sr, pr, ws.data_ptr(), need, st))
+        lat.append(time.perf_counter() - t)
+    plain_s = time.perf_counter() - t0
+    plain = {"inst_per_s": nreq / plain_s, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+             "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+
+    def serve(rate):
+        server = tn.tn_server_create(budget_gb << 30, 4)
+        try:
+            arrive = np.cumsum(rng.exponential(1.0 / rate, size=nreq)) if rate else np.zeros(nreq)
+            tickets, done, outstanding = [], {}, []
+            t_start = time.perf_counter()
+            i = 0
+            while len(done) < nreq:
+                now = time.perf_counter() - t_start
+                while i < nreq and arrive[i] <= now:
+                    p, sr, pr = reqs[i]
+                    tk = (tn.tn_submit(server, p.handle, sr, pr), sr, arrive[i])
+                    tickets.append(tk)
+                    outstanding.append(tk)
+                    i += 1
+                still = []
+                for t, sr, a in outstanding:
+                    r = tn.tn_poll(server, t, sr)
+                    if r is None:
+                        still.append((t, sr, a))
+                    else:
+                        done[t] = (r, time.perf_counter() - t_start - a)
+                outstanding = still
+            total = time.perf_counter() - t_start
+        finally:
+            tn.tn_server_destroy(server)
+        res = [done[t][0] for t, _, _ in tickets]
+        if res != ref:
+            raise RuntimeError("served results differ from the same requests run alone")
+        lats = [done[t][1] for t, _, _ in tickets]
+        return {"offered_per_s": rate or None, "inst_per_s": nreq / total,
+                "p50_ms": 1e3 * float(np.percentile(lats, 50)), "p99_ms": 1e3 * float(np.percentile(lats, 99))}
+
+    sat = serve(0)  # every request offered at once
+    sweep = [serve(f * sat["inst_per_s"]) for f in (0.25, 0.5, 1.0)]
+    for p in pool:
+        p.close()
+    return {"workload": f"{nreq} requests, Poisson arrivals (seed 5), 50/50 3-regular n in [40,160] / "
+                        "King's subgraph L in [8,16] p=0.8, MIS size | MIS count | count mod 4 primes, "
+                        f"{budget_gb} GB budget, 4 launch slots",
+            "plain_one_at_a_time": plain, "served_saturated": sat, "served_rate_sweep": sweep,
+            "speedup_inst_per_s": sat["inst_per_s"] / plain["inst_per_s"]}
 
 
 def run_tn(args):
@@ -310,6 +440,10 @@ def run_tn(args):
             "gpu_launches": None, "roofline": roofline, "clocks": csum}
     # one executor launch per contraction
     line["gpu_launches"] = args.steps * len(jobs)
+    if rank == 0 and not args.no_batching:
+        line["batching"] = batching_bench(tn, torch)
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_bench(tn, torch)
     if rank == 0 and not args.no_cpu_baseline:
         ops, secs, used = cpu_reference([("reg3", 140, 1), ("reg3", 140, 2)], os.cpu_count() or 1)
         line["cpu_baseline"] = {"value": ops / secs / 1e9, "unit": "Gop/s", "cores": used, "kind": "oracle",
