@@ -243,7 +243,7 @@ def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120):
             n, e = graphgen.random_regular3(int(rng.integers(20, 81)) * 2, 20000 + i)
         else:
             n, e = graphgen.kings_subgraph(int(rng.integers(8, 17)), 0.8, 30000 + i)
-        pool.append(tn.Plan(n, e, nrepeat=2, seed=1))
+        pool.append(tn.Plan(n, e, nrepeat=10, seed=1))  # the paper's greedy default (Sec. 4.2.1)
     kinds = [("tropical_i32", None), ("counting", None), ("modp", tuple(tn.PRIMES31[:4]))]
     reqs = [(pool[int(rng.integers(0, len(pool)))], *kinds[int(rng.integers(0, 3))]) for _ in range(nreq)]
     need = max(p.workspace_bytes(sr, len(pr) if pr else 1) for p, sr, pr in reqs)

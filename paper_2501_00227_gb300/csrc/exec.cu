@@ -205,7 +205,10 @@ __device__ __noinline__ void exec_naive_task(const ExecArgs& a, const ExecStep& 
   auto lb = [&](int64_t e) { return SR::template load<true>(B, e, q); };
   if (ks == 1) {
     auto sink = [&](int64_t c, const Acc& v) { SR::store(C, c, q, v, mp); };
-    naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, kh0, kh1, st.R, sm);
+    if (st.R == 1 && st.chunk % (int64_t(kNaiveWideU) * kBlock) == 0)
+      naive_chunk_wide<SR, kNaiveWideU>(g, la, lb, sink, mp, c0, c1, sm);
+    else
+      naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, kh0, kh1, st.R, sm);
     return;
   }
   // k split: partial results to scratch; the last CTA of the chunk merges

@@ -19,6 +19,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <memory>
@@ -81,6 +82,7 @@ struct tn_server_s {
   std::unordered_map<uint64_t, int> state;  // 0 pending, 1 running, 2 done
   std::vector<Flight> flights;
   uint64_t next_ticket = 1;
+  int group_h = 4;  // height of the groups of tiny steps one CTA runs back to back
   std::atomic<bool> stop{false};
   std::thread worker;
 };
@@ -119,7 +121,7 @@ int launch_flight(tn_server_s* S, Flight& f, std::vector<Request>&& reqs) {
   f.plan.reset(new tn::ExecPlan());
   try {
     rc = tn::build_batch_plan(plans.data(), static_cast<int32_t>(plans.size()), r0.semiring, np < 1 ? 1 : np,
-                              64, f.plan.get());
+                              S->group_h, f.plan.get());
   } catch (const std::bad_alloc&) {
     rc = TN_ENOMEM;
   }
@@ -221,6 +223,7 @@ int tn_server_create(size_t hbm_budget_bytes, int32_t max_inflight, tn_server_t*
   if (!S) return TN_ENOMEM;
   S->budget = hbm_budget_bytes;
   S->max_inflight = max_inflight;
+  if (const char* e = getenv("TN_SERVE_GROUP_HEIGHT")) S->group_h = atoi(e) > 0 ? atoi(e) : 1;
   if (cudaGetDevice(&S->device) != cudaSuccess) {
     delete S;
     return TN_ECUDA;

@@ -28,6 +28,7 @@ __device__ __forceinline__ int64_t deposit(int64_t x, const int8_t* pos, int fir
 
 constexpr int kNaiveKLoBits = 9;    // k offsets of the low 9 bits come from a table
 constexpr int kBlock = 256;         // threads per CTA of every libtn kernel
+constexpr int kNaiveWideU = 4;      // entries per thread in naive_chunk_wide
 
 // Shared-memory scratch of one naive chunk.
 template <class SR>
@@ -124,6 +125,53 @@ __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, Load
   }
 }
 
+// R = 1 variant of naive_chunk: each thread computes U output entries at
+// once (entries cb + tid + 256 u), so U independent loads per operand are in
+// flight.  Used for wide steps with short reductions.
+template <class SR, int U, class LoadA, class LoadB, class Sink>
+__device__ __forceinline__ void naive_chunk_wide(const StepGeom& g, LoadA loadA, LoadB loadB, Sink sink,
+                                                 const ModParams& mp, int64_t c_begin, int64_t c_end,
+                                                 NaiveSmem<SR>& sm) {
+  using Acc = typename SR::Acc;
+  const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
+  const int64_t nklo = int64_t(1) << kl, nkhi = int64_t(1) << (g.nk - kl);
+  const int a_k0 = g.nb + g.nm, b_k0 = g.nb;
+  const int64_t mask_n = (int64_t(1) << g.nn) - 1, mask_m = (int64_t(1) << g.nm) - 1;
+  for (int64_t cb = c_begin; cb < c_end; cb += int64_t(U) * kBlock) {
+    int64_t base_a[U], base_b[U];
+    Acc acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = cb + threadIdx.x + int64_t(u) * kBlock;
+      const int64_t cc = c < c_end ? c : c_begin;  // out-of-range lanes recompute a valid entry
+      const int64_t n = cc & mask_n, m = (cc >> g.nn) & mask_m, b = cc >> (g.nn + g.nm);
+      base_a[u] = deposit(b, g.a_pos, 0, g.nb) | deposit(m, g.a_pos, g.nb, g.nm);
+      base_b[u] = deposit(b, g.b_pos, 0, g.nb) | deposit(n, g.b_pos, g.nb + g.nk, g.nn);
+      acc[u] = SR::zero(mp);
+    }
+    for (int64_t kh = 0; kh < nkhi; ++kh) {
+      const int64_t da = deposit(kh, g.a_pos, a_k0 + kl, g.nk - kl);
+      const int64_t db = deposit(kh, g.b_pos, b_k0 + kl, g.nk - kl);
+      for (int64_t k = 0; k < nklo; ++k) {
+        const int64_t ka = sm.ka[k] | da, kb = sm.kb[k] | db;
+        typename SR::Val va[U], vb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          va[u] = loadA(base_a[u] | ka);
+          vb[u] = loadB(base_b[u] | kb);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) SR::mac(acc[u], va[u], vb[u], mp);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t c = cb + threadIdx.x + int64_t(u) * kBlock;
+      if (c < c_end) sink(c, acc[u]);
+    }
+  }
+}
+
 // Host-side shape of a general ("naive") step with E = 2^rc outputs and
 // K = 2^nk terms: R threads per output entry, `chunk` outputs per task,
 // `ks` tasks sharing each chunk along k (their partial results are merged by
@@ -144,10 +192,16 @@ inline NaiveShape naive_shape(int rc, int nk, bool allow_ksplit) {
   while (R < 256 && R * 2 <= K && K / (R * 2) >= 16 && E * R < (int64_t(1) << 17)) R *= 2;
   s.R = R;
   const int64_t per_pass = kBlock / R;
-  // at most ~8 passes per task and at most 4096 chunks
   int64_t chunk = per_pass;
-  while (chunk * 2 <= per_pass * 8 && (E + chunk - 1) / chunk > 4096) chunk *= 2;
-  while ((E + chunk - 1) / chunk > 4096) chunk *= 2;
+  if (R == 1 && E >= int64_t(kNaiveWideU) * kBlock * 152) {
+    // wide and shallow: U entries per thread, about one wave of ~2 tasks per SM
+    chunk = int64_t(kNaiveWideU) * kBlock;
+    while ((E + chunk - 1) / chunk > 608) chunk *= 2;
+  } else {
+    // at most ~8 passes per task and at most 4096 chunks
+    while (chunk * 2 <= per_pass * 8 && (E + chunk - 1) / chunk > 4096) chunk *= 2;
+    while ((E + chunk - 1) / chunk > 4096) chunk *= 2;
+  }
   s.chunk = chunk;
   s.nchunks = (E + chunk - 1) / chunk;
   // split long reductions over several CTAs (whole high-k blocks each)
