@@ -181,13 +181,27 @@ __device__ __noinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& s
 }
 
 template <class SR>
+__device__ __forceinline__ void exec_naive_task_q(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
+                                                  int q, unsigned char* smem, int* s_last);
+
+template <class SR>
 __device__ __noinline__ void exec_naive_task(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
-                                                unsigned char* smem, int* s_last) {
+                                             unsigned char* smem, int* s_last) {
+  auto& sm = *reinterpret_cast<NaiveSmem<SR>*>(smem);
+  naive_tables<SR>(st.g, sm);
+  if (task.prime >= 0) {
+    exec_naive_task_q<SR>(a, st, task, task.prime, smem, s_last);
+  } else {
+    for (int q = 0; q < a.nprimes; ++q) exec_naive_task_q<SR>(a, st, task, q, smem, s_last);
+  }
+}
+
+template <class SR>
+__device__ __forceinline__ void exec_naive_task_q(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
+                                                  int q, unsigned char* smem, int* s_last) {
   using Acc = typename SR::Acc;
   auto& sm = *reinterpret_cast<NaiveSmem<SR>*>(smem);
   const StepGeom& g = st.g;
-  naive_tables<SR>(g, sm);
-  const int q = task.prime;
   const ModParams mp = a.mods.q[q];
   const Operand A = exec_operand(a, g.a_kind, st.a_off);
   const Operand B = exec_operand(a, g.b_kind, st.b_off);
@@ -258,7 +272,14 @@ __device__ __noinline__ void exec_group_task(const ExecArgs& a, const ExecTask& 
     int32_t* dst = reinterpret_cast<int32_t*>(s_step);
     for (int w = threadIdx.x; w < static_cast<int>(sizeof(ExecStep) / 4); w += kBlock) dst[w] = __ldg(src + w);
     __syncthreads();
-    exec_naive_whole<SR>(a, *s_step, task.prime, smem);
+    if (task.prime >= 0) {
+      exec_naive_whole<SR>(a, *s_step, task.prime, smem);
+    } else {
+      for (int q = 0; q < a.nprimes; ++q) {
+        __syncthreads();
+        exec_naive_whole<SR>(a, *s_step, q, smem);
+      }
+    }
   }
 }
 
@@ -314,7 +335,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
         const int d = d0 + tid;
         if (d < nd) {
           const int dep = final_task ? s_task.step : a.deps[s_step.dep_begin + d];
-          const int32_t target = a.steps[dep].ntasks * a.nprimes;
+          const int32_t target = a.steps[dep].done_target;
           const unsigned long long t0 = global_ns();
           unsigned ns = 32;
           while (ld_acquire(a.done + dep) < target) {

@@ -35,15 +35,15 @@ struct ExecStep {
   int32_t arrive_off;            // first split-K arrival counter of this step
   int32_t ks;                    // naive: k splits per output chunk
   int32_t nchunks;               // naive: output chunks
-  int32_t pad_;
+  int32_t done_target;           // tasks of this step (its done counter's final value)
 };
 
 enum ExecTaskKind : int32_t { kTaskNaive = 0, kTaskTile = 1, kTaskFinal = 2, kTaskGroup = 3 };
 
 struct ExecTask {
   int32_t step;   // exec-step index
-  int32_t local;  // naive: chunk index; tile: tile * split + rank
-  int32_t prime;  // prime index (mod p), else 0
+  int32_t local;  // naive: chunk index; tile: tile * split + rank; group: group index
+  int32_t prime;  // prime index (mod p), else 0; -1: every prime in turn
   int32_t kind;
 };
 

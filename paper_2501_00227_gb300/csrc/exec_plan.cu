@@ -261,7 +261,8 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
         const int32_t gid = static_cast<int32_t>(X->group_begin.size());
         X->group_begin.push_back(static_cast<int32_t>(X->group_members.size()));
         for (int32_t m : mem) X->group_members.push_back(pos[m]);
-        for (int q = 0; q < np; ++q) X->tasks.push_back(ExecTask{x, gid, q, kTaskGroup});
+        X->tasks.push_back(ExecTask{x, gid, np > 1 ? -1 : 0, kTaskGroup});  // all primes in one task
+        E.done_target = 1;
       }
     } else if (kernel == kKernTiled && S.g.c_identity) {
       const int64_t bm = dev::tiled_tile_bm(tile), bn = dev::tiled_tile_bn(tile);
@@ -293,10 +294,18 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
         scratch += align_up(static_cast<size_t>(sh.nchunks * np * sh.ks * sh.chunk) * acc_bytes, 256);
       }
     }
-    if (groot[st] < 0)
-      for (int q = 0; q < np; ++q)
-        for (int t = 0; t < E.ntasks; ++t)
-          X->tasks.push_back(ExecTask{x, t, q, E.kernel == kKernTiled ? kTaskTile : kTaskNaive});
+    if (groot[st] < 0) {
+      if (E.kernel == kKernNaive && E.ks == 1 && np > 1) {
+        // a general step without k split does every prime inside each task
+        for (int t = 0; t < E.ntasks; ++t) X->tasks.push_back(ExecTask{x, t, -1, kTaskNaive});
+        E.done_target = E.ntasks;
+      } else {
+        for (int q = 0; q < np; ++q)
+          for (int t = 0; t < E.ntasks; ++t)
+            X->tasks.push_back(ExecTask{x, t, q, E.kernel == kKernTiled ? kTaskTile : kTaskNaive});
+        E.done_target = E.ntasks * np;
+      }
+    }
   }
   X->ngroups = static_cast<int32_t>(X->group_begin.size());
   X->group_begin.push_back(static_cast<int32_t>(X->group_members.size()));

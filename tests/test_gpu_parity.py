@@ -344,3 +344,43 @@ def test_networks_both_kernels(mode, execu, height, monkeypatch):
         assert r["i32"] == alpha and r["f32"] == alpha
         assert r["cnt"] == (alpha, poly[alpha], tn.TN_OK)
         assert r["mod"][1] == sum(poly)
+
+
+@pytest.mark.slow
+def test_config4_kings_subgraph_20_vs_oracle():
+    """20 x 20 King's subgraph at filling 0.8 (seed 1, ~324 vertices): tropical
+    int32, counting tropical and the count modulo four 31-bit primes against
+    the oracle on its own greedy order; CRT of 4 residues is the count modulo
+    their product (the count itself needs 6 primes, see the design notes)."""
+    n, e = g.kings_subgraph(20, 0.8, 1)
+    primes = tn.PRIMES31[:4]
+    oo = O.greedy_order(n, e, nrepeat=3, seed=1)
+    ref_size = O.mis_size(n, e, oo)
+    ref_cnt = O.mis_count(n, e, oo)
+    ref_res = O.count_modp(n, e, oo, primes)
+    p = tn.Plan(n, e, nrepeat=10, seed=1)
+    try:
+        assert p.contract("tropical_i32")["max"] == ref_size
+        r = p.contract("counting")
+        assert (r["max"], r["count"]) == ref_cnt
+        r = p.contract("modp", primes)
+        assert r["residues"] == ref_res
+        assert r["crt"] == O.crt(ref_res, primes)[0]
+    finally:
+        p.close()
+
+
+def test_kings_subgraph_count_exact_with_six_primes():
+    """The all-independent-set count of a 12 x 12 King's subgraph, exact from
+    6 primes, equals the oracle's (and its float agrees with a 7-prime CRT)."""
+    n, e = g.kings_subgraph(12, 0.8, 2)
+    oo = O.greedy_order(n, e, nrepeat=2, seed=1)
+    res6 = O.count_modp(n, e, oo, tn.PRIMES31[:6])
+    p = tn.Plan(n, e, nrepeat=10, seed=1)
+    try:
+        r6 = p.contract("modp", tn.PRIMES31[:6])
+        r7 = p.contract("modp", tn.PRIMES31[:7])
+    finally:
+        p.close()
+    assert r6["residues"] == res6
+    assert r6["crt"] == r7["crt"]          # 6 primes already exceed the count
