@@ -312,6 +312,7 @@ def run_tn(args):
     import torch.distributed as dist
 
     from paper_2501_00227_gb300 import build as B
+    from paper_2501_00227_gb300 import shard
     from paper_2501_00227_gb300 import tn
 
     rank, world, local = dist_env()
@@ -385,11 +386,9 @@ def run_tn(args):
         dist.barrier()
     check(raw.cpu().numpy(), ref)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    # every rank contracts the same per-GPU workload (independent networks, no
+    # data-path collective); the job's time is the slowest rank's
+    total_ms = shard.max_over_ranks(sum(step_ms), dist if world > 1 else None, dev)
     value = world * ops_per_step * args.steps / (total_ms * 1e-3) / 1e9
 
     # ---- per-kernel attribution: one executor launch per contraction
