@@ -173,13 +173,17 @@ int tn_contract_timed(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *pr
                       float *step_ms, int32_t *step_kernel, uint64_t *step_ops);
 
 /* Tracing: as tn_contract through the persistent executor, and records for
- * every executor task t, in d_trace[4t .. 4t+3] (caller device memory of
- * 32 * tn_plan_info().exec_tasks bytes): the global timer (ns) when a CTA
- * claimed it, when its dependencies were met, when it finished, and
- * (SM id << 32 | CTA index).  task_step[t], task_kind[t] (0 general chunk,
- * 1 GEMM tile, 2 final copy) and step_level[i] (dependency level of executor
- * step i) describe the schedule; any of the three may be NULL.  Waits for the
- * stream. */
+ * every executor task t, in d_trace[8t .. 8t+7] (caller device memory of
+ * 64 * tn_plan_info().exec_tasks bytes): the global timer (ns) when a CTA
+ * claimed it [0], when the task and step records were in shared memory [1],
+ * when its dependencies were met [2], when its body ended [3] and when its
+ * completion was published [4]; then (SM id << 32 | CTA index) [5]; then two
+ * phase marks of the body [6], [7] (general chunk: offset tables built,
+ * reduction done; GEMM tile: main loop done, final merge or store started;
+ * 0 where the task kind has none).  task_step[t], task_kind[t] (0 general
+ * chunk, 1 GEMM tile, 2 final copy, 3 group of tiny steps) and step_level[i]
+ * (dependency level of executor step i) describe the schedule; any of the
+ * three may be NULL.  Waits for the stream. */
 int tn_contract_trace(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *primes, int32_t nprimes,
                       void *d_workspace, size_t ws_bytes, void *cuda_stream, void *d_trace,
                       int32_t *task_step, int32_t *task_kind, int32_t *step_level, tn_result_t *out);

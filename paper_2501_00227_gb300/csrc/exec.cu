@@ -43,12 +43,16 @@ struct ExecArgs {
   int32_t semiring;
   int32_t pad_;
   unsigned long long timeout_ns;
-  unsigned long long* trace;  // optional: 4 words per task (see tn_contract_trace)
+  unsigned long long* trace;  // optional: 8 words per task (see tn_contract_trace)
   int32_t nraw;               // raw result slots (networks in the launch)
   int32_t pad2_;
 };
 
 constexpr uint32_t kStatusTimeout = 1u;
+
+// Phase marks of the running task (global timer, ns), written only while
+// tracing: [0] end of the main computation, [1] start of the merge / store.
+__shared__ unsigned long long g_trace_mark[2];
 
 __device__ __forceinline__ int32_t ld_acquire(const int32_t* p) {
   int32_t v;
@@ -144,38 +148,64 @@ __device__ __noinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& s
 
   const int64_t m0 = tm * BM, n0 = tn_ * BN;
   const int64_t cbase = b << (g.nn + g.nm);
+  static_assert(TN % 4 == 0, "vector epilogue");
+  if (a.trace && tid == 0) g_trace_mark[0] = global_ns();
   if (split > 1) {
-    // publish this partial tile, then let the last CTA of the tile merge
+    // publish this partial tile ([BM][BN], 16-byte stores), then the last
+    // CTA of the tile to arrive merges all `split` partial tiles with every
+    // thread, four entries at a time
     Acc* part = reinterpret_cast<Acc*>(a.scratch + st.scratch_off) + ((int64_t(q) * ntiles + tile) * split) * (BM * BN);
     if (grp == 0) {
       Acc* mine = part + int64_t(rank) * BM * BN;
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) mine[(ty * TM + i) * BN + tx * TN + j] = acc[i][j];
+        for (int j = 0; j < TN; j += 4) {
+          const Acc v[4] = {acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]};
+          SR::st4(mine + (ty * TM + i) * BN + tx * TN + j, v);
+        }
     }
     if (!arrive_last(a.arrive + st.arrive_off + int64_t(q) * ntiles + tile, split, s_last)) return;
-    if (grp == 0) {
-      for (int r = 0; r < split; ++r) {
-        if (r == rank) continue;
-        const Acc* other = part + int64_t(r) * BM * BN;
+    if (a.trace && tid == 0) g_trace_mark[1] = global_ns();
+    for (int e = 4 * tid; e < BM * BN; e += 4 * kBlock) {
+      const int64_t m = m0 + e / BN, n = n0 + e % BN;
+      if (m >= M || n >= N) continue;
+      Acc v[4];
+      SR::ldcg4(part + e, v);
+#pragma unroll 4
+      for (int r = 1; r < split; ++r) {
+        Acc o[4];
+        SR::ldcg4(part + int64_t(r) * BM * BN + e, o);
 #pragma unroll
-        for (int i = 0; i < TM; ++i)
+        for (int u = 0; u < 4; ++u) SR::merge(v[u], o[u], mp);
+      }
+      if (g.nn >= 2) {
+        SR::store4(C, cbase + (m << g.nn) + n, q, v, mp);  // N >= 4: the 4 entries are in range, 16-byte aligned
+      } else {
 #pragma unroll
-          for (int j = 0; j < TN; ++j)
-            SR::merge(acc[i][j], ldcg_acc(other + (ty * TM + i) * BN + tx * TN + j), mp);
+        for (int u = 0; u < 4; ++u)
+          if (n + u < N) SR::store(C, cbase + (m << g.nn) + n + u, q, v[u], mp);
       }
     }
+    return;
   }
+  if (a.trace && tid == 0) g_trace_mark[1] = global_ns();
   if (grp != 0) return;
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int64_t m = m0 + ty * TM + i;
     if (m >= M) continue;
 #pragma unroll
-    for (int j = 0; j < TN; ++j) {
+    for (int j = 0; j < TN; j += 4) {
       const int64_t n = n0 + tx * TN + j;
-      if (n < N) SR::store(C, cbase + (m << g.nn) + n, q, acc[i][j], mp);
+      const Acc v[4] = {acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]};
+      if (g.nn >= 2) {
+        if (n < N) SR::store4(C, cbase + (m << g.nn) + n, q, v, mp);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (n + u < N) SR::store(C, cbase + (m << g.nn) + n + u, q, v[u], mp);
+      }
     }
   }
 }
@@ -184,11 +214,23 @@ template <class SR>
 __device__ __forceinline__ void exec_naive_task_q(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
                                                   int q, unsigned char* smem, int* s_last);
 
+// High-k block range [kh0, kh1) of a general-step task (k split `ks`).
+__device__ __forceinline__ void naive_task_kh(const ExecStep& st, const ExecTask& task, int64_t* kh0,
+                                              int64_t* kh1) {
+  const int kl = st.g.nk < kNaiveKLoBits ? st.g.nk : kNaiveKLoBits;
+  const int64_t nkhi = int64_t(1) << (st.g.nk - kl);
+  const int r = task.local % st.ks;
+  *kh0 = nkhi / st.ks * r;
+  *kh1 = *kh0 + nkhi / st.ks;
+}
+
 template <class SR>
 __device__ __noinline__ void exec_naive_task(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
                                              unsigned char* smem, int* s_last) {
   auto& sm = *reinterpret_cast<NaiveSmem<SR>*>(smem);
-  naive_tables<SR>(st.g, sm);
+  int64_t kh0, kh1;
+  naive_task_kh(st, task, &kh0, &kh1);
+  naive_tables<SR>(st.g, sm, kh0, kh1);
   if (task.prime >= 0) {
     exec_naive_task_q<SR>(a, st, task, task.prime, smem, s_last);
   } else {
@@ -212,17 +254,18 @@ __device__ __forceinline__ void exec_naive_task_q(const ExecArgs& a, const ExecS
   const int r = task.local % ks;
   const int64_t c0 = chunk_id * st.chunk;
   const int64_t c1 = c0 + st.chunk < E ? c0 + st.chunk : E;
-  const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
-  const int64_t nkhi = int64_t(1) << (g.nk - kl);
-  const int64_t kh0 = nkhi / ks * r, kh1 = kh0 + nkhi / ks;
+  int64_t kh0, kh1;
+  naive_task_kh(st, task, &kh0, &kh1);
   auto la = [&](int64_t e) { return SR::template load<true>(A, e, q); };
   auto lb = [&](int64_t e) { return SR::template load<true>(B, e, q); };
+  if (a.trace && threadIdx.x == 0) g_trace_mark[0] = global_ns();
   if (ks == 1) {
     auto sink = [&](int64_t c, const Acc& v) { SR::store(C, c, q, v, mp); };
     if (st.R == 1 && st.chunk % (int64_t(kNaiveWideU) * kBlock) == 0)
       naive_chunk_wide<SR, kNaiveWideU>(g, la, lb, sink, mp, c0, c1, sm);
     else
       naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, kh0, kh1, st.R, sm);
+    if (a.trace && threadIdx.x == 0) g_trace_mark[1] = global_ns();
     return;
   }
   // k split: partial results to scratch; the last CTA of the chunk merges
@@ -231,8 +274,23 @@ __device__ __forceinline__ void exec_naive_task_q(const ExecArgs& a, const ExecS
   auto sink = [&](int64_t c, const Acc& v) { part[int64_t(r) * st.chunk + (c - c0)] = v; };
   naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, kh0, kh1, st.R, sm);
   if (!arrive_last(a.arrive + st.arrive_off + int64_t(q) * st.nchunks + chunk_id, ks, s_last)) return;
+  if (a.trace && threadIdx.x == 0) g_trace_mark[1] = global_ns();
+  if (st.chunk * ks <= kBlock && ks <= 32) {
+    // one partial per thread, merged across the ks lanes of each entry
+    const int cl = threadIdx.x / ks, rr = threadIdx.x % ks;
+    const int64_t c = c0 + cl;
+    Acc v = SR::zero(mp);
+    if (cl < st.chunk && c < c1) v = ldcg_acc(part + int64_t(rr) * st.chunk + cl);
+    for (int off = ks / 2; off >= 1; off >>= 1) {
+      Acc o = shfl_xor_val(v, off);
+      SR::merge(v, o, mp);
+    }
+    if (rr == 0 && cl < st.chunk && c < c1) SR::store(C, c, q, v, mp);
+    return;
+  }
   for (int64_t c = c0 + threadIdx.x; c < c1; c += kBlock) {
     Acc v = ldcg_acc(part + (c - c0));
+#pragma unroll 4
     for (int rr = 1; rr < ks; ++rr) SR::merge(v, ldcg_acc(part + int64_t(rr) * st.chunk + (c - c0)), mp);
     SR::store(C, c, q, v, mp);
   }
@@ -247,16 +305,17 @@ template <class SR>
 __device__ __forceinline__ void exec_naive_whole(const ExecArgs& a, const ExecStep& st, int q, unsigned char* smem) {
   auto& sm = *reinterpret_cast<NaiveSmem<SR>*>(smem);
   const StepGeom& g = st.g;
-  naive_tables<SR>(g, sm);
+  const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
+  const int64_t nkhi = int64_t(1) << (g.nk - kl);
+  naive_tables<SR>(g, sm, 0, nkhi);
   const ModParams mp = a.mods.q[q];
   const Operand A = exec_operand(a, g.a_kind, st.a_off);
   const Operand B = exec_operand(a, g.b_kind, st.b_off);
   Output C{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride};
-  const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
   auto la = [&](int64_t e) { return SR::template load<true>(A, e, q); };
   auto lb = [&](int64_t e) { return SR::template load<true>(B, e, q); };
   auto sink = [&](int64_t c, const typename SR::Acc& v) { SR::store(C, c, q, v, mp); };
-  naive_chunk<SR>(g, la, lb, sink, mp, 0, int64_t(1) << g.rc, 0, int64_t(1) << (g.nk - kl), st.R, sm);
+  naive_chunk<SR>(g, la, lb, sink, mp, 0, int64_t(1) << g.rc, 0, nkhi, st.R, sm);
 }
 
 // A group of tiny steps, run back to back by this CTA: barriers between the
@@ -308,7 +367,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
   __shared__ ExecTask s_task;
   __shared__ int s_t, s_abort, s_last;
   const int tid = threadIdx.x;
-  unsigned long long t_claim = 0;
+  unsigned long long t_claim = 0, t_loaded = 0;
   for (;;) {
     if (tid == 0) {
       if (a.trace) t_claim = global_ns();
@@ -326,6 +385,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
       for (int i = tid; i < static_cast<int>(sizeof(ExecStep) / 4); i += kBlock) dst[i] = __ldg(src + i);
     }
     __syncthreads();
+    if (a.trace && tid == 0) t_loaded = global_ns();
     // wait for the steps this one depends on (warp 0, one dependency per lane)
     if (tid < 32) {
       const bool final_task = s_task.kind == kTaskFinal;
@@ -360,7 +420,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
     __syncthreads();
     if (s_abort) break;
     unsigned long long t_ready = 0;
-    if (a.trace && tid == 0) t_ready = global_ns();
+    if (a.trace && tid == 0) {
+      t_ready = global_ns();
+      g_trace_mark[0] = g_trace_mark[1] = 0;
+    }
     if (s_task.kind == kTaskFinal) {
       exec_final(a, s_step, s_task.local);
     } else if (s_task.kind == kTaskNaive) {
@@ -380,16 +443,21 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
     }
     __syncthreads();
     if (tid == 0) {
+      const unsigned long long t_body = a.trace ? global_ns() : 0;
       __threadfence();
       atomicAdd(a.done + s_task.step, 1);
       if (a.trace) {
         unsigned smid;
         asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-        unsigned long long* tr = a.trace + 4 * static_cast<int64_t>(t);
+        unsigned long long* tr = a.trace + 8 * static_cast<int64_t>(t);
         tr[0] = t_claim;
-        tr[1] = t_ready;
-        tr[2] = global_ns();
-        tr[3] = (static_cast<unsigned long long>(smid) << 32) | blockIdx.x;
+        tr[1] = t_loaded;
+        tr[2] = t_ready;
+        tr[3] = t_body;
+        tr[4] = global_ns();
+        tr[5] = (static_cast<unsigned long long>(smid) << 32) | blockIdx.x;
+        tr[6] = g_trace_mark[0];
+        tr[7] = g_trace_mark[1];
       }
     }
   }

@@ -22,7 +22,8 @@ __global__ void __launch_bounds__(kBlock) k_step_naive(const __grid_constant__ S
                                                        Operand B, Output C, ModTable mods, int R,
                                                        int64_t chunk) {
   __shared__ NaiveSmem<SR> sm;
-  naive_tables<SR>(g, sm);
+  const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
+  naive_tables<SR>(g, sm, 0, int64_t(1) << (g.nk - kl));
   const int q = blockIdx.y;
   const ModParams mp = mods.q[q];
   const int64_t E = int64_t(1) << g.rc;
@@ -33,7 +34,6 @@ __global__ void __launch_bounds__(kBlock) k_step_naive(const __grid_constant__ S
   auto sink = [&](int64_t c, const typename SR::Acc& acc) {
     SR::store(C, g.c_identity ? c : deposit(c, g.c_pos, 0, g.rc), q, acc, mp);
   };
-  const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
   naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, 0, int64_t(1) << (g.nk - kl), R, sm);
 }
 

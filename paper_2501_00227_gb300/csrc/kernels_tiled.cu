@@ -227,6 +227,16 @@ void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, i
   *tile = best_tile;
   *split = best_split;
   *kernel = kKernTiled;
+  // TN_TILE / TN_SPLIT in the environment force the tile shape / split-K of
+  // every tiled step (measurement and tests)
+  static const int force_tile = getenv("TN_TILE") ? atoi(getenv("TN_TILE")) : -1;
+  static const int force_split = getenv("TN_SPLIT") ? atoi(getenv("TN_SPLIT")) : -1;
+  if (force_tile >= 0 && force_tile < kNumTiles && (tropical || force_tile != 0)) *tile = force_tile;
+  if (force_split >= 1) {
+    int sp = 1;
+    while (sp * 2 <= force_split && K / (sp * 2) >= kTileBK[*tile]) sp *= 2;
+    *split = sp;
+  }
 }
 
 int launch_step(tn_semiring_t s, const StepGeom& g, const Operand& A, const Operand& B,

@@ -100,6 +100,21 @@ struct SrF32 {
                                                const ModParams&) {
     static_cast<float*>(o.p0)[e] = acc;
   }
+  // four consecutive entries e .. e+3 (e a multiple of 4, 16-byte aligned)
+  static __device__ __forceinline__ void store4(const Output& o, int64_t e, int, const Acc (&v)[4],
+                                                const ModParams&) {
+    *reinterpret_cast<float4*>(static_cast<float*>(o.p0) + e) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  static __device__ __forceinline__ void st4(Acc* p, const Acc (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  static __device__ __forceinline__ void ldcg4(const Acc* p, Acc (&v)[4]) {
+    const float4 w = __ldcg(reinterpret_cast<const float4*>(p));
+    v[0] = w.x;
+    v[1] = w.y;
+    v[2] = w.z;
+    v[3] = w.w;
+  }
 };
 
 // ---------------------------------------------------------------- int32
@@ -129,6 +144,20 @@ struct SrI32 {
   static __device__ __forceinline__ void store(const Output& o, int64_t e, int, const Acc& acc,
                                                const ModParams&) {
     static_cast<int32_t*>(o.p0)[e] = acc;
+  }
+  static __device__ __forceinline__ void store4(const Output& o, int64_t e, int, const Acc (&v)[4],
+                                                const ModParams&) {
+    *reinterpret_cast<int4*>(static_cast<int32_t*>(o.p0) + e) = make_int4(v[0], v[1], v[2], v[3]);
+  }
+  static __device__ __forceinline__ void st4(Acc* p, const Acc (&v)[4]) {
+    *reinterpret_cast<int4*>(p) = make_int4(v[0], v[1], v[2], v[3]);
+  }
+  static __device__ __forceinline__ void ldcg4(const Acc* p, Acc (&v)[4]) {
+    const int4 w = __ldcg(reinterpret_cast<const int4*>(p));
+    v[0] = w.x;
+    v[1] = w.y;
+    v[2] = w.z;
+    v[3] = w.w;
   }
 };
 
@@ -183,6 +212,27 @@ struct SrCnt {
     static_cast<int32_t*>(o.p0)[e] = acc.v;
     static_cast<uint64_t*>(o.p1)[e] = acc.c;
   }
+  static __device__ __forceinline__ void store4(const Output& o, int64_t e, int, const Acc (&v)[4],
+                                                const ModParams&) {
+    *reinterpret_cast<int4*>(static_cast<int32_t*>(o.p0) + e) = make_int4(v[0].v, v[1].v, v[2].v, v[3].v);
+    ulonglong2* c = reinterpret_cast<ulonglong2*>(static_cast<uint64_t*>(o.p1) + e);
+    c[0] = make_ulonglong2(v[0].c, v[1].c);
+    c[1] = make_ulonglong2(v[2].c, v[3].c);
+  }
+  static __device__ __forceinline__ void st4(Acc* p, const Acc (&v)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      *reinterpret_cast<int4*>(p + i) = make_int4(v[i].v, 0, static_cast<int32_t>(static_cast<uint32_t>(v[i].c)),
+                                                  static_cast<int32_t>(static_cast<uint32_t>(v[i].c >> 32)));
+  }
+  static __device__ __forceinline__ void ldcg4(const Acc* p, Acc (&v)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int4 w = __ldcg(reinterpret_cast<const int4*>(p + i));
+      v[i].v = w.x;
+      v[i].c = static_cast<uint64_t>(static_cast<uint32_t>(w.z)) | (static_cast<uint64_t>(static_cast<uint32_t>(w.w)) << 32);
+    }
+  }
 };
 
 // ---------------------------------------------------------------- mod p
@@ -226,6 +276,23 @@ struct SrMod {
   static __device__ __forceinline__ void store(const Output& o, int64_t e, int q, const Acc& acc,
                                                const ModParams& mp) {
     static_cast<uint32_t*>(o.p0)[q * o.prime_stride + e] = barrett64(acc, mp);
+  }
+  static __device__ __forceinline__ void store4(const Output& o, int64_t e, int q, const Acc (&v)[4],
+                                                const ModParams& mp) {
+    *reinterpret_cast<uint4*>(static_cast<uint32_t*>(o.p0) + q * o.prime_stride + e) =
+        make_uint4(barrett64(v[0], mp), barrett64(v[1], mp), barrett64(v[2], mp), barrett64(v[3], mp));
+  }
+  static __device__ __forceinline__ void st4(Acc* p, const Acc (&v)[4]) {
+    reinterpret_cast<ulonglong2*>(p)[0] = make_ulonglong2(v[0], v[1]);
+    reinterpret_cast<ulonglong2*>(p)[1] = make_ulonglong2(v[2], v[3]);
+  }
+  static __device__ __forceinline__ void ldcg4(const Acc* p, Acc (&v)[4]) {
+    const ulonglong2 w0 = __ldcg(reinterpret_cast<const ulonglong2*>(p));
+    const ulonglong2 w1 = __ldcg(reinterpret_cast<const ulonglong2*>(p) + 1);
+    v[0] = w0.x;
+    v[1] = w0.y;
+    v[2] = w1.x;
+    v[3] = w1.y;
   }
 };
 

@@ -27,15 +27,26 @@ __device__ __forceinline__ int64_t deposit(int64_t x, const int8_t* pos, int fir
 }
 
 constexpr int kNaiveKLoBits = 9;    // k offsets of the low 9 bits come from a table
+constexpr int kNaiveKHi = 256;      // high-k blocks per task whose offsets are tabulated
 constexpr int kBlock = 256;         // threads per CTA of every libtn kernel
 constexpr int kNaiveWideU = 4;      // entries per thread in naive_chunk_wide
 
-// Shared-memory scratch of one naive chunk.
+// Shared-memory scratch of one naive chunk: offsets of the low k bits
+// (ka / kb) and of the high-k blocks [kh_begin, kh_begin + kNaiveKHi) of
+// the task (kha / khb).
 template <class SR>
 struct NaiveSmem {
   int64_t ka[1 << kNaiveKLoBits];
   int64_t kb[1 << kNaiveKLoBits];
+  int64_t kha[kNaiveKHi];
+  int64_t khb[kNaiveKHi];
   typename SR::Acc red[kBlock / 32];
+};
+
+// Loads in flight per thread in the reduction loop of naive_chunk.
+template <class SR>
+struct NaiveUnroll {
+  static constexpr int v = sizeof(typename SR::Val) <= 4 ? 8 : 4;
 };
 
 template <class T>
@@ -49,38 +60,62 @@ __device__ __forceinline__ CntVal shfl_xor_val(CntVal v, int off) {
   return r;
 }
 
-// Fills the k-offset tables of a step (all threads of the CTA; ends with a
-// barrier).
+// Fills the k-offset tables of a step for the high-k blocks
+// [kh_begin, kh_end) (all threads of the CTA; ends with a barrier).
 template <class SR>
-__device__ __forceinline__ void naive_tables(const StepGeom& g, NaiveSmem<SR>& sm) {
+__device__ __forceinline__ void naive_tables(const StepGeom& g, NaiveSmem<SR>& sm, int64_t kh_begin,
+                                             int64_t kh_end) {
   const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
   const int a_k0 = g.nb + g.nm, b_k0 = g.nb;
   for (int i = threadIdx.x; i < (1 << kl); i += kBlock) {
     sm.ka[i] = deposit(i, g.a_pos, a_k0, kl);
     sm.kb[i] = deposit(i, g.b_pos, b_k0, kl);
   }
+  if (kh_end - kh_begin <= kNaiveKHi)
+    for (int i = threadIdx.x; i < kh_end - kh_begin; i += kBlock) {
+      sm.kha[i] = deposit(kh_begin + i, g.a_pos, a_k0 + kl, g.nk - kl);
+      sm.khb[i] = deposit(kh_begin + i, g.b_pos, b_k0 + kl, g.nk - kl);
+    }
   __syncthreads();
 }
 
 // Computes output entries [c_begin, c_end) of a step for prime index q,
-// over the high-k blocks [kh_begin, kh_end) (each block is 2^min(nk, 9) k's).
+// over the high-k blocks [kh_begin, kh_end) (each block is 2^min(nk, 9) k's;
+// naive_tables must have been called with the same block range).
 // R threads (a power of two, 1..256, R <= 2^nk) share each output entry:
-// each takes every R-th k, then the R partial results are merged with the
-// semiring (+) by warp shuffles (R <= 32) or through shared memory.  The
-// merged value of entry c goes to sink(c, acc) (called by one thread).
-// Every thread of the CTA must call this (it uses barriers when R > 32).
+// lane l takes the terms l, l + R, l + 2R, ... of the entry's flattened
+// (block, low k) range, NaiveUnroll loads per operand in flight (a batch
+// beyond the range is padded with the edge tensor's forbidden entry, the
+// semiring zero: (max,+) -inf, (max, count) (-inf, 0), mod p 0), then the R
+// partial results are merged with the semiring (+) by warp shuffles
+// (R <= 32) or through shared memory.  The merged value of entry c goes to
+// sink(c, acc) (called by one thread).  Every thread of the CTA must call
+// this (it uses barriers when R > 32).
 template <class SR, class LoadA, class LoadB, class Sink>
 __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, LoadB loadB, Sink sink,
                                             const ModParams& mp, int64_t c_begin, int64_t c_end,
                                             int64_t kh_begin, int64_t kh_end, int R, NaiveSmem<SR>& sm) {
   using Acc = typename SR::Acc;
+  using Val = typename SR::Val;
+  constexpr int U = NaiveUnroll<SR>::v;
   const int tid = threadIdx.x;
   const int slot = tid / R, lane = tid % R;
   const int per_pass = kBlock / R;
   const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
-  const int64_t nklo = int64_t(1) << kl;
+  const int64_t mlo = (int64_t(1) << kl) - 1;
   const int a_k0 = g.nb + g.nm, b_k0 = g.nb;
   const int64_t mask_n = (int64_t(1) << g.nn) - 1, mask_m = (int64_t(1) << g.nm) - 1;
+  const int64_t nterm = (kh_end - kh_begin) << kl;
+  const bool tab = kh_end - kh_begin <= kNaiveKHi;
+  // offsets of term j inside A and B (high block from the table or computed)
+  auto koffA = [&](int64_t j) -> int64_t {
+    const int64_t h = j >> kl;
+    return (tab ? sm.kha[h] : deposit(kh_begin + h, g.a_pos, a_k0 + kl, g.nk - kl)) | sm.ka[j & mlo];
+  };
+  auto koffB = [&](int64_t j) -> int64_t {
+    const int64_t h = j >> kl;
+    return (tab ? sm.khb[h] : deposit(kh_begin + h, g.b_pos, b_k0 + kl, g.nk - kl)) | sm.kb[j & mlo];
+  };
   for (int64_t cb = c_begin; cb < c_end; cb += per_pass) {
     const int64_t c = cb + slot;
     const bool valid = c < c_end;
@@ -89,22 +124,19 @@ __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, Load
       const int64_t n = c & mask_n, m = (c >> g.nn) & mask_m, b = c >> (g.nn + g.nm);
       const int64_t base_a = deposit(b, g.a_pos, 0, g.nb) | deposit(m, g.a_pos, g.nb, g.nm);
       const int64_t base_b = deposit(b, g.b_pos, 0, g.nb) | deposit(n, g.b_pos, g.nb + g.nk, g.nn);
-      for (int64_t kh = kh_begin; kh < kh_end; ++kh) {
-        const int64_t oa = base_a | deposit(kh, g.a_pos, a_k0 + kl, g.nk - kl);
-        const int64_t ob = base_b | deposit(kh, g.b_pos, b_k0 + kl, g.nk - kl);
-        int64_t k = lane;
-        // four independent loads in flight per operand before the multiply-adds
-        for (; k + 3 * R < nklo; k += 4 * R) {
-          const auto a0 = loadA(oa | sm.ka[k]), a1 = loadA(oa | sm.ka[k + R]);
-          const auto a2 = loadA(oa | sm.ka[k + 2 * R]), a3 = loadA(oa | sm.ka[k + 3 * R]);
-          const auto b0 = loadB(ob | sm.kb[k]), b1 = loadB(ob | sm.kb[k + R]);
-          const auto b2 = loadB(ob | sm.kb[k + 2 * R]), b3 = loadB(ob | sm.kb[k + 3 * R]);
-          SR::mac(acc, a0, b0, mp);
-          SR::mac(acc, a1, b1, mp);
-          SR::mac(acc, a2, b2, mp);
-          SR::mac(acc, a3, b3, mp);
+      // U terms per batch; the last batch pads with the semiring zero, so
+      // its loads are in flight together as well
+      for (int64_t j = lane; j < nterm; j += U * R) {
+        Val va[U], vb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t jj = j + u * R;
+          const bool in = jj < nterm;
+          va[u] = in ? loadA(base_a | koffA(jj)) : SR::leaf(kOpEdge, 3);
+          vb[u] = in ? loadB(base_b | koffB(jj)) : SR::leaf(kOpEdge, 3);
         }
-        for (; k < nklo; k += R) SR::mac(acc, loadA(oa | sm.ka[k]), loadB(ob | sm.kb[k]), mp);
+#pragma unroll
+        for (int u = 0; u < U; ++u) SR::mac(acc, va[u], vb[u], mp);
       }
     }
     // merge the R partial accumulators of each output entry
@@ -127,15 +159,17 @@ __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, Load
 
 // R = 1 variant of naive_chunk: each thread computes U output entries at
 // once (entries cb + tid + 256 u), so U independent loads per operand are in
-// flight.  Used for wide steps with short reductions.
+// flight (2U with the unrolled k loop).  Used for wide steps with short
+// reductions; covers the whole k range (naive_tables over all high-k blocks).
 template <class SR, int U, class LoadA, class LoadB, class Sink>
 __device__ __forceinline__ void naive_chunk_wide(const StepGeom& g, LoadA loadA, LoadB loadB, Sink sink,
                                                  const ModParams& mp, int64_t c_begin, int64_t c_end,
                                                  NaiveSmem<SR>& sm) {
   using Acc = typename SR::Acc;
   const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
-  const int64_t nklo = int64_t(1) << kl, nkhi = int64_t(1) << (g.nk - kl);
+  const int64_t mlo = (int64_t(1) << kl) - 1, nterm = int64_t(1) << g.nk;
   const int a_k0 = g.nb + g.nm, b_k0 = g.nb;
+  const bool tab = (nterm >> kl) <= kNaiveKHi;
   const int64_t mask_n = (int64_t(1) << g.nn) - 1, mask_m = (int64_t(1) << g.nm) - 1;
   for (int64_t cb = c_begin; cb < c_end; cb += int64_t(U) * kBlock) {
     int64_t base_a[U], base_b[U];
@@ -149,20 +183,19 @@ __device__ __forceinline__ void naive_chunk_wide(const StepGeom& g, LoadA loadA,
       base_b[u] = deposit(b, g.b_pos, 0, g.nb) | deposit(n, g.b_pos, g.nb + g.nk, g.nn);
       acc[u] = SR::zero(mp);
     }
-    for (int64_t kh = 0; kh < nkhi; ++kh) {
-      const int64_t da = deposit(kh, g.a_pos, a_k0 + kl, g.nk - kl);
-      const int64_t db = deposit(kh, g.b_pos, b_k0 + kl, g.nk - kl);
-      for (int64_t k = 0; k < nklo; ++k) {
-        const int64_t ka = sm.ka[k] | da, kb = sm.kb[k] | db;
-        typename SR::Val va[U], vb[U];
+#pragma unroll 2
+    for (int64_t j = 0; j < nterm; ++j) {
+      const int64_t h = j >> kl;
+      const int64_t ka = (tab ? sm.kha[h] : deposit(h, g.a_pos, a_k0 + kl, g.nk - kl)) | sm.ka[j & mlo];
+      const int64_t kb = (tab ? sm.khb[h] : deposit(h, g.b_pos, b_k0 + kl, g.nk - kl)) | sm.kb[j & mlo];
+      typename SR::Val va[U], vb[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          va[u] = loadA(base_a[u] | ka);
-          vb[u] = loadB(base_b[u] | kb);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) SR::mac(acc[u], va[u], vb[u], mp);
+      for (int u = 0; u < U; ++u) {
+        va[u] = loadA(base_a[u] | ka);
+        vb[u] = loadB(base_b[u] | kb);
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) SR::mac(acc[u], va[u], vb[u], mp);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -208,7 +241,7 @@ inline NaiveShape naive_shape(int rc, int nk, bool allow_ksplit) {
   const int kl = nk < kNaiveKLoBits ? nk : kNaiveKLoBits;
   const int64_t nkhi = int64_t(1) << (nk - kl);
   int ks = 1;
-  while (allow_ksplit && s.nchunks * ks < 304 && ks * 2 <= nkhi && K / (int64_t(R) * ks * 2) >= 16 && ks < 256)
+  while (allow_ksplit && s.nchunks * ks < 304 && ks * 2 <= nkhi && K / (int64_t(R) * ks * 2) >= 8 && ks < 256)
     ks *= 2;
   s.ks = ks;
   s.ntasks = s.nchunks * ks;

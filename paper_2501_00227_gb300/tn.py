@@ -230,7 +230,7 @@ def tn_contract_timed(plan, semiring, primes, ws_ptr: int, ws_bytes: int, stream
 def tn_contract_trace(plan, semiring, primes, ws_ptr: int, ws_bytes: int, stream: int, trace_ptr: int,
                       ntasks: int, nsteps: int):
     """(result dict, task_step, task_kind, step_level); the trace itself is in
-    the caller's device buffer at trace_ptr (4 uint64 per task)."""
+    the caller's device buffer at trace_ptr (8 uint64 per task)."""
     pr, k = _primes(primes)
     r = tn_result_t()
     ts = np.zeros(ntasks, dtype=np.int32)
