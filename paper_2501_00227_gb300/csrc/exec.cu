@@ -135,19 +135,20 @@ __device__ __noinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& s
   const int64_t M = int64_t(1) << g.nm, N = int64_t(1) << g.nn, K = int64_t(1) << g.nk;
   const int64_t kspan = split > 1 ? K / split : K;
   const int64_t kbeg = int64_t(rank) * kspan;
-  const Operand A = exec_operand(a, g.a_kind, st.a_off);
-  const Operand B = exec_operand(a, g.b_kind, st.b_off);
-  Output C{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride};
+  const Operand A = at_prime(exec_operand(a, g.a_kind, st.a_off), q);
+  const Operand B = at_prime(exec_operand(a, g.b_kind, st.b_off), q);
+  const Output C = at_prime(Output{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride}, q);
 
   Acc acc[TM][TN];
   if constexpr (std::is_same<SR, SrCnt>::value)
     tile_mainloop_counting<Cfg, true>(g, A, B, mp, b, tm, tn_, kbeg, kbeg + kspan, smem, acc);
   else
-    tile_mainloop<SR, Cfg, FOLD, true>(g, A, B, mp, q, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
+    tile_mainloop<SR, Cfg, FOLD, true>(g, A, B, mp, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
   tile_merge_groups<SR, Cfg>(acc, reinterpret_cast<Acc*>(smem), mp);
 
-  const int64_t m0 = tm * BM, n0 = tn_ * BN;
-  const int64_t cbase = b << (g.nn + g.nm);
+  const uint32_t m0 = static_cast<uint32_t>(tm) * BM, n0 = static_cast<uint32_t>(tn_) * BN;
+  const uint32_t cbase = static_cast<uint32_t>(b) << (g.nn + g.nm);
+  const uint32_t M32 = 1u << g.nm, N32 = 1u << g.nn;
   static_assert(TN % 4 == 0, "vector epilogue");
   if (a.trace && tid == 0) g_trace_mark[0] = global_ns();
   if (split > 1) {
@@ -168,8 +169,8 @@ __device__ __noinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& s
     if (!arrive_last(a.arrive + st.arrive_off + int64_t(q) * ntiles + tile, split, s_last)) return;
     if (a.trace && tid == 0) g_trace_mark[1] = global_ns();
     for (int e = 4 * tid; e < BM * BN; e += 4 * kBlock) {
-      const int64_t m = m0 + e / BN, n = n0 + e % BN;
-      if (m >= M || n >= N) continue;
+      const uint32_t m = m0 + e / BN, n = n0 + e % BN;
+      if (m >= M32 || n >= N32) continue;
       Acc v[4];
       SR::ldcg4(part + e, v);
 #pragma unroll 4
@@ -180,11 +181,11 @@ __device__ __noinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& s
         for (int u = 0; u < 4; ++u) SR::merge(v[u], o[u], mp);
       }
       if (g.nn >= 2) {
-        SR::store4(C, cbase + (m << g.nn) + n, q, v, mp);  // N >= 4: the 4 entries are in range, 16-byte aligned
+        SR::store4(C, cbase + (m << g.nn) + n, v, mp);  // N >= 4: the 4 entries are in range, 16-byte aligned
       } else {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (n + u < N) SR::store(C, cbase + (m << g.nn) + n + u, q, v[u], mp);
+          if (n + u < N32) SR::store(C, cbase + (m << g.nn) + n + u, v[u], mp);
       }
     }
     return;
@@ -193,18 +194,18 @@ __device__ __noinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& s
   if (grp != 0) return;
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
-    const int64_t m = m0 + ty * TM + i;
-    if (m >= M) continue;
+    const uint32_t m = m0 + ty * TM + i;
+    if (m >= M32) continue;
 #pragma unroll
     for (int j = 0; j < TN; j += 4) {
-      const int64_t n = n0 + tx * TN + j;
+      const uint32_t n = n0 + tx * TN + j;
       const Acc v[4] = {acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]};
       if (g.nn >= 2) {
-        if (n < N) SR::store4(C, cbase + (m << g.nn) + n, q, v, mp);
+        if (n < N32) SR::store4(C, cbase + (m << g.nn) + n, v, mp);
       } else {
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (n + u < N) SR::store(C, cbase + (m << g.nn) + n + u, q, v[u], mp);
+          if (n + u < N32) SR::store(C, cbase + (m << g.nn) + n + u, v[u], mp);
       }
     }
   }
@@ -215,10 +216,10 @@ __device__ __forceinline__ void exec_naive_task_q(const ExecArgs& a, const ExecS
                                                   int q, unsigned char* smem, int* s_last);
 
 // High-k block range [kh0, kh1) of a general-step task (k split `ks`).
-__device__ __forceinline__ void naive_task_kh(const ExecStep& st, const ExecTask& task, int64_t* kh0,
-                                              int64_t* kh1) {
+__device__ __forceinline__ void naive_task_kh(const ExecStep& st, const ExecTask& task, int32_t* kh0,
+                                              int32_t* kh1) {
   const int kl = st.g.nk < kNaiveKLoBits ? st.g.nk : kNaiveKLoBits;
-  const int64_t nkhi = int64_t(1) << (st.g.nk - kl);
+  const int32_t nkhi = 1 << (st.g.nk - kl);
   const int r = task.local % st.ks;
   *kh0 = nkhi / st.ks * r;
   *kh1 = *kh0 + nkhi / st.ks;
@@ -228,7 +229,7 @@ template <class SR>
 __device__ __noinline__ void exec_naive_task(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
                                              unsigned char* smem, int* s_last) {
   auto& sm = *reinterpret_cast<NaiveSmem<SR>*>(smem);
-  int64_t kh0, kh1;
+  int32_t kh0, kh1;
   naive_task_kh(st, task, &kh0, &kh1);
   naive_tables<SR>(st.g, sm, kh0, kh1);
   if (task.prime >= 0) {
@@ -245,23 +246,24 @@ __device__ __forceinline__ void exec_naive_task_q(const ExecArgs& a, const ExecS
   auto& sm = *reinterpret_cast<NaiveSmem<SR>*>(smem);
   const StepGeom& g = st.g;
   const ModParams mp = a.mods.q[q];
-  const Operand A = exec_operand(a, g.a_kind, st.a_off);
-  const Operand B = exec_operand(a, g.b_kind, st.b_off);
-  Output C{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride};
-  const int64_t E = int64_t(1) << g.rc;
+  const Operand A = at_prime(exec_operand(a, g.a_kind, st.a_off), q);
+  const Operand B = at_prime(exec_operand(a, g.b_kind, st.b_off), q);
+  const Output C = at_prime(Output{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride}, q);
+  const int32_t E = 1 << g.rc;
   const int ks = st.ks;
-  const int64_t chunk_id = task.local / ks;
+  const int32_t chunk = static_cast<int32_t>(st.chunk);
+  const int32_t chunk_id = task.local / ks;
   const int r = task.local % ks;
-  const int64_t c0 = chunk_id * st.chunk;
-  const int64_t c1 = c0 + st.chunk < E ? c0 + st.chunk : E;
-  int64_t kh0, kh1;
+  const int32_t c0 = chunk_id * chunk;
+  const int32_t c1 = c0 + chunk < E ? c0 + chunk : E;
+  int32_t kh0, kh1;
   naive_task_kh(st, task, &kh0, &kh1);
-  auto la = [&](int64_t e) { return SR::template load<true>(A, e, q); };
-  auto lb = [&](int64_t e) { return SR::template load<true>(B, e, q); };
+  auto la = [&](uint32_t e) { return SR::template load<true>(A, e); };
+  auto lb = [&](uint32_t e) { return SR::template load<true>(B, e); };
   if (a.trace && threadIdx.x == 0) g_trace_mark[0] = global_ns();
   if (ks == 1) {
-    auto sink = [&](int64_t c, const Acc& v) { SR::store(C, c, q, v, mp); };
-    if (st.R == 1 && st.chunk % (int64_t(kNaiveWideU) * kBlock) == 0)
+    auto sink = [&](uint32_t c, const Acc& v) { SR::store(C, c, v, mp); };
+    if (st.R == 1 && chunk % (kNaiveWideU * kBlock) == 0)
       naive_chunk_wide<SR, kNaiveWideU>(g, la, lb, sink, mp, c0, c1, sm);
     else
       naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, kh0, kh1, st.R, sm);
@@ -271,28 +273,28 @@ __device__ __forceinline__ void exec_naive_task_q(const ExecArgs& a, const ExecS
   // k split: partial results to scratch; the last CTA of the chunk merges
   Acc* part = reinterpret_cast<Acc*>(a.scratch + st.scratch_off) +
               (int64_t(q) * st.nchunks + chunk_id) * ks * st.chunk;
-  auto sink = [&](int64_t c, const Acc& v) { part[int64_t(r) * st.chunk + (c - c0)] = v; };
+  auto sink = [&](uint32_t c, const Acc& v) { part[r * chunk + (static_cast<int32_t>(c) - c0)] = v; };
   naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, kh0, kh1, st.R, sm);
   if (!arrive_last(a.arrive + st.arrive_off + int64_t(q) * st.nchunks + chunk_id, ks, s_last)) return;
   if (a.trace && threadIdx.x == 0) g_trace_mark[1] = global_ns();
-  if (st.chunk * ks <= kBlock && ks <= 32) {
+  if (chunk * ks <= kBlock && ks <= 32) {
     // one partial per thread, merged across the ks lanes of each entry
     const int cl = threadIdx.x / ks, rr = threadIdx.x % ks;
-    const int64_t c = c0 + cl;
+    const int32_t c = c0 + cl;
     Acc v = SR::zero(mp);
-    if (cl < st.chunk && c < c1) v = ldcg_acc(part + int64_t(rr) * st.chunk + cl);
+    if (cl < chunk && c < c1) v = ldcg_acc(part + rr * chunk + cl);
     for (int off = ks / 2; off >= 1; off >>= 1) {
       Acc o = shfl_xor_val(v, off);
       SR::merge(v, o, mp);
     }
-    if (rr == 0 && cl < st.chunk && c < c1) SR::store(C, c, q, v, mp);
+    if (rr == 0 && cl < chunk && c < c1) SR::store(C, static_cast<uint32_t>(c), v, mp);
     return;
   }
-  for (int64_t c = c0 + threadIdx.x; c < c1; c += kBlock) {
+  for (int32_t c = c0 + threadIdx.x; c < c1; c += kBlock) {
     Acc v = ldcg_acc(part + (c - c0));
 #pragma unroll 4
-    for (int rr = 1; rr < ks; ++rr) SR::merge(v, ldcg_acc(part + int64_t(rr) * st.chunk + (c - c0)), mp);
-    SR::store(C, c, q, v, mp);
+    for (int rr = 1; rr < ks; ++rr) SR::merge(v, ldcg_acc(part + rr * chunk + (c - c0)), mp);
+    SR::store(C, static_cast<uint32_t>(c), v, mp);
   }
 }
 
@@ -306,16 +308,16 @@ __device__ __forceinline__ void exec_naive_whole(const ExecArgs& a, const ExecSt
   auto& sm = *reinterpret_cast<NaiveSmem<SR>*>(smem);
   const StepGeom& g = st.g;
   const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
-  const int64_t nkhi = int64_t(1) << (g.nk - kl);
+  const int32_t nkhi = 1 << (g.nk - kl);
   naive_tables<SR>(g, sm, 0, nkhi);
   const ModParams mp = a.mods.q[q];
-  const Operand A = exec_operand(a, g.a_kind, st.a_off);
-  const Operand B = exec_operand(a, g.b_kind, st.b_off);
-  Output C{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride};
-  auto la = [&](int64_t e) { return SR::template load<true>(A, e, q); };
-  auto lb = [&](int64_t e) { return SR::template load<true>(B, e, q); };
-  auto sink = [&](int64_t c, const typename SR::Acc& v) { SR::store(C, c, q, v, mp); };
-  naive_chunk<SR>(g, la, lb, sink, mp, 0, int64_t(1) << g.rc, 0, nkhi, st.R, sm);
+  const Operand A = at_prime(exec_operand(a, g.a_kind, st.a_off), q);
+  const Operand B = at_prime(exec_operand(a, g.b_kind, st.b_off), q);
+  const Output C = at_prime(Output{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride}, q);
+  auto la = [&](uint32_t e) { return SR::template load<true>(A, e); };
+  auto lb = [&](uint32_t e) { return SR::template load<true>(B, e); };
+  auto sink = [&](uint32_t c, const typename SR::Acc& v) { SR::store(C, c, v, mp); };
+  naive_chunk<SR>(g, la, lb, sink, mp, 0, 1 << g.rc, 0, nkhi, st.R, sm);
 }
 
 // A group of tiny steps, run back to back by this CTA: barriers between the

@@ -23,18 +23,21 @@ __global__ void __launch_bounds__(kBlock) k_step_naive(const __grid_constant__ S
                                                        int64_t chunk) {
   __shared__ NaiveSmem<SR> sm;
   const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
-  naive_tables<SR>(g, sm, 0, int64_t(1) << (g.nk - kl));
+  const int32_t nkhi = 1 << (g.nk - kl);
+  naive_tables<SR>(g, sm, 0, nkhi);
   const int q = blockIdx.y;
   const ModParams mp = mods.q[q];
-  const int64_t E = int64_t(1) << g.rc;
-  const int64_t c0 = int64_t(blockIdx.x) * chunk;
-  const int64_t c1 = c0 + chunk < E ? c0 + chunk : E;
-  auto la = [&](int64_t e) { return SR::load(A, e, q); };
-  auto lb = [&](int64_t e) { return SR::load(B, e, q); };
-  auto sink = [&](int64_t c, const typename SR::Acc& acc) {
-    SR::store(C, g.c_identity ? c : deposit(c, g.c_pos, 0, g.rc), q, acc, mp);
+  const Operand Aq = at_prime(A, q), Bq = at_prime(B, q);
+  const Output Cq = at_prime(C, q);
+  const int32_t E = 1 << g.rc;
+  const int32_t c0 = static_cast<int32_t>(blockIdx.x) * static_cast<int32_t>(chunk);
+  const int32_t c1 = c0 + chunk < E ? c0 + static_cast<int32_t>(chunk) : E;
+  auto la = [&](uint32_t e) { return SR::load(Aq, e); };
+  auto lb = [&](uint32_t e) { return SR::load(Bq, e); };
+  auto sink = [&](uint32_t c, const typename SR::Acc& acc) {
+    SR::store(Cq, g.c_identity ? c : deposit(c, g.c_pos, 0, g.rc), acc, mp);
   };
-  naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, 0, int64_t(1) << (g.nk - kl), R, sm);
+  naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, 0, nkhi, R, sm);
 }
 
 template <class SR>

@@ -47,29 +47,32 @@ __global__ void __launch_bounds__(kBlock, 2) k_step_tiled(const __grid_constant_
   const int64_t b = blockIdx.y;
   const int q = blockIdx.z;
   const ModParams mp = args.mods.q[q];
-  const int64_t M = int64_t(1) << g.nm, N = int64_t(1) << g.nn, K = int64_t(1) << g.nk;
+  const int64_t K = int64_t(1) << g.nk;
   const int64_t kspan = split > 1 ? K / split : K;
   const int64_t kbeg = int64_t(rank) * kspan;
+  const Operand A = at_prime(args.A, q), B = at_prime(args.B, q);
+  const Output C = at_prime(args.C, q);
 
   Acc acc[TM][TN];
   if constexpr (std::is_same<SR, SrCnt>::value)
-    tile_mainloop_counting<Cfg, false>(g, args.A, args.B, mp, b, tm, tn_, kbeg, kbeg + kspan, smem, acc);
+    tile_mainloop_counting<Cfg, false>(g, A, B, mp, b, tm, tn_, kbeg, kbeg + kspan, smem, acc);
   else
-    tile_mainloop<SR, Cfg, FOLD, false>(g, args.A, args.B, mp, q, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
+    tile_mainloop<SR, Cfg, FOLD, false>(g, A, B, mp, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
   tile_merge_groups<SR, Cfg>(acc, reinterpret_cast<Acc*>(smem), mp);
 
-  const int64_t m0 = tm * BM, n0 = tn_ * BN;
-  const int64_t cbase = b << (g.nn + g.nm);
+  const uint32_t M = 1u << g.nm, N = 1u << g.nn;
+  const uint32_t m0 = static_cast<uint32_t>(tm) * BM, n0 = static_cast<uint32_t>(tn_) * BN;
+  const uint32_t cbase = static_cast<uint32_t>(b) << (g.nn + g.nm);
   if (split == 1) {
     if (grp != 0) return;
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-      const int64_t m = m0 + ty * TM + i;
+      const uint32_t m = m0 + ty * TM + i;
       if (m >= M) continue;
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
-        const int64_t n = n0 + tx * TN + j;
-        if (n < N) SR::store(args.C, cbase + (m << g.nn) + n, q, acc[i][j], mp);
+        const uint32_t n = n0 + tx * TN + j;
+        if (n < N) SR::store(C, cbase + (m << g.nn) + n, acc[i][j], mp);
       }
     }
     return;
@@ -93,8 +96,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_step_tiled(const __grid_constant_
       const Acc* peer = cluster.map_shared_rank(red, r);
       SR::merge(v, peer[e], mp);
     }
-    const int64_t m = m0 + e / BN, n = n0 + e % BN;
-    if (m < M && n < N) SR::store(args.C, cbase + (m << g.nn) + n, q, v, mp);
+    const uint32_t m = m0 + e / BN, n = n0 + e % BN;
+    if (m < M && n < N) SR::store(C, cbase + (m << g.nn) + n, v, mp);
   }
   cluster.sync();
 }

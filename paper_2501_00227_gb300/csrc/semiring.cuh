@@ -22,7 +22,8 @@ namespace dev {
 constexpr int32_t kNegInf = TN_I32_NEG_INF;
 
 // One operand of a step: an array in device memory or a leaf generated on
-// the fly (its entry index is the only input).
+// the fly (its entry index is the only input).  Entry indices are 32-bit
+// (tensor ranks are at most 30).
 struct Operand {
   int32_t kind;          // OperandKind
   int32_t pad_;
@@ -36,6 +37,17 @@ struct Output {
   void* p1;
   int64_t prime_stride;
 };
+
+// The same operand / output seen at the block of prime index q (mod p keeps
+// one residue array per prime; the element accessors below read p0 only).
+__device__ __forceinline__ Operand at_prime(Operand o, int q) {
+  if (o.kind == kOpArena && q) o.p0 = static_cast<const uint32_t*>(o.p0) + q * o.prime_stride;
+  return o;
+}
+__device__ __forceinline__ Output at_prime(Output o, int q) {
+  if (q) o.p0 = static_cast<uint32_t*>(o.p0) + q * o.prime_stride;
+  return o;
+}
 
 // Constants of one modulus p (2 <= p < 2^31):
 //   r32 = 2^32 mod p   (folds the high word of a 64-bit accumulator)
@@ -77,17 +89,17 @@ struct SrF32 {
   using Val = float;
   using Acc = float;
   static __device__ __forceinline__ Acc zero(const ModParams&) { return -__int_as_float(0x7f800000); }
-  static __device__ __forceinline__ Val leaf(int32_t kind, int64_t e) {
+  static __device__ __forceinline__ Val leaf(int32_t kind, uint32_t e) {
     if (kind == kOpEdge) return e == 3 ? -__int_as_float(0x7f800000) : 0.0f;
     if (kind == kOpVertex) return e == 1 ? 1.0f : 0.0f;
     return 0.0f;
   }
   template <bool CG = false>
-  static __device__ __forceinline__ Val load(const Operand& o, int64_t e, int) {
+  static __device__ __forceinline__ Val load(const Operand& o, uint32_t e) {
     if (o.kind != kOpArena) return leaf(o.kind, e);
     return ldg_t<CG>(static_cast<const float*>(o.p0) + e);
   }
-  static __device__ __forceinline__ void copy_async(Val* dst, const Operand& o, int64_t e, int) {
+  static __device__ __forceinline__ void copy_async(Val* dst, const Operand& o, uint32_t e) {
     cp_async4(dst, static_cast<const float*>(o.p0) + e);
   }
   static __device__ __forceinline__ void mac(Acc& acc, Val a, Val b, const ModParams&) {
@@ -96,13 +108,11 @@ struct SrF32 {
   static __device__ __forceinline__ void merge(Acc& acc, const Acc& o, const ModParams&) {
     acc = fmaxf(acc, o);
   }
-  static __device__ __forceinline__ void store(const Output& o, int64_t e, int, const Acc& acc,
-                                               const ModParams&) {
+  static __device__ __forceinline__ void store(const Output& o, uint32_t e, const Acc& acc, const ModParams&) {
     static_cast<float*>(o.p0)[e] = acc;
   }
   // four consecutive entries e .. e+3 (e a multiple of 4, 16-byte aligned)
-  static __device__ __forceinline__ void store4(const Output& o, int64_t e, int, const Acc (&v)[4],
-                                                const ModParams&) {
+  static __device__ __forceinline__ void store4(const Output& o, uint32_t e, const Acc (&v)[4], const ModParams&) {
     *reinterpret_cast<float4*>(static_cast<float*>(o.p0) + e) = make_float4(v[0], v[1], v[2], v[3]);
   }
   static __device__ __forceinline__ void st4(Acc* p, const Acc (&v)[4]) {
@@ -122,17 +132,17 @@ struct SrI32 {
   using Val = int32_t;
   using Acc = int32_t;
   static __device__ __forceinline__ Acc zero(const ModParams&) { return kNegInf; }
-  static __device__ __forceinline__ Val leaf(int32_t kind, int64_t e) {
+  static __device__ __forceinline__ Val leaf(int32_t kind, uint32_t e) {
     if (kind == kOpEdge) return e == 3 ? kNegInf : 0;
     if (kind == kOpVertex) return e == 1 ? 1 : 0;
     return 0;
   }
   template <bool CG = false>
-  static __device__ __forceinline__ Val load(const Operand& o, int64_t e, int) {
+  static __device__ __forceinline__ Val load(const Operand& o, uint32_t e) {
     if (o.kind != kOpArena) return leaf(o.kind, e);
     return ldg_t<CG>(static_cast<const int32_t*>(o.p0) + e);
   }
-  static __device__ __forceinline__ void copy_async(Val* dst, const Operand& o, int64_t e, int) {
+  static __device__ __forceinline__ void copy_async(Val* dst, const Operand& o, uint32_t e) {
     cp_async4(dst, static_cast<const int32_t*>(o.p0) + e);
   }
   static __device__ __forceinline__ void mac(Acc& acc, Val a, Val b, const ModParams&) {
@@ -141,12 +151,10 @@ struct SrI32 {
   static __device__ __forceinline__ void merge(Acc& acc, const Acc& o, const ModParams&) {
     acc = max(acc, o);
   }
-  static __device__ __forceinline__ void store(const Output& o, int64_t e, int, const Acc& acc,
-                                               const ModParams&) {
+  static __device__ __forceinline__ void store(const Output& o, uint32_t e, const Acc& acc, const ModParams&) {
     static_cast<int32_t*>(o.p0)[e] = acc;
   }
-  static __device__ __forceinline__ void store4(const Output& o, int64_t e, int, const Acc (&v)[4],
-                                                const ModParams&) {
+  static __device__ __forceinline__ void store4(const Output& o, uint32_t e, const Acc (&v)[4], const ModParams&) {
     *reinterpret_cast<int4*>(static_cast<int32_t*>(o.p0) + e) = make_int4(v[0], v[1], v[2], v[3]);
   }
   static __device__ __forceinline__ void st4(Acc* p, const Acc (&v)[4]) {
@@ -179,18 +187,18 @@ struct SrCnt {
   using Val = CntVal;
   using Acc = CntVal;
   static __device__ __forceinline__ Acc zero(const ModParams&) { return CntVal{kNegInf, 0ull}; }
-  static __device__ __forceinline__ Val leaf(int32_t kind, int64_t e) {
+  static __device__ __forceinline__ Val leaf(int32_t kind, uint32_t e) {
     if (kind == kOpEdge) return e == 3 ? CntVal{kNegInf, 0ull} : CntVal{0, 1ull};
     if (kind == kOpVertex) return e == 1 ? CntVal{1, 1ull} : CntVal{0, 1ull};
     return CntVal{0, 1ull};
   }
   template <bool CG = false>
-  static __device__ __forceinline__ Val load(const Operand& o, int64_t e, int) {
+  static __device__ __forceinline__ Val load(const Operand& o, uint32_t e) {
     if (o.kind != kOpArena) return leaf(o.kind, e);
     return CntVal{ldg_t<CG>(static_cast<const int32_t*>(o.p0) + e),
                   ldg_t<CG>(static_cast<const uint64_t*>(o.p1) + e)};
   }
-  static __device__ __forceinline__ void copy_async(Val* dst, const Operand& o, int64_t e, int) {
+  static __device__ __forceinline__ void copy_async(Val* dst, const Operand& o, uint32_t e) {
     cp_async4(&dst->v, static_cast<const int32_t*>(o.p0) + e);
     cp_async8(&dst->c, static_cast<const uint64_t*>(o.p1) + e);
   }
@@ -207,13 +215,11 @@ struct SrCnt {
     if (o.v > acc.v) acc = o;
     else if (o.v == acc.v) acc.c = sat_add_u64(acc.c, o.c);
   }
-  static __device__ __forceinline__ void store(const Output& o, int64_t e, int, const Acc& acc,
-                                               const ModParams&) {
+  static __device__ __forceinline__ void store(const Output& o, uint32_t e, const Acc& acc, const ModParams&) {
     static_cast<int32_t*>(o.p0)[e] = acc.v;
     static_cast<uint64_t*>(o.p1)[e] = acc.c;
   }
-  static __device__ __forceinline__ void store4(const Output& o, int64_t e, int, const Acc (&v)[4],
-                                                const ModParams&) {
+  static __device__ __forceinline__ void store4(const Output& o, uint32_t e, const Acc (&v)[4], const ModParams&) {
     *reinterpret_cast<int4*>(static_cast<int32_t*>(o.p0) + e) = make_int4(v[0].v, v[1].v, v[2].v, v[3].v);
     ulonglong2* c = reinterpret_cast<ulonglong2*>(static_cast<uint64_t*>(o.p1) + e);
     c[0] = make_ulonglong2(v[0].c, v[1].c);
@@ -254,18 +260,18 @@ struct SrMod {
   using Val = uint32_t;
   using Acc = uint64_t;
   static __device__ __forceinline__ Acc zero(const ModParams&) { return 0ull; }
-  static __device__ __forceinline__ Val leaf(int32_t kind, int64_t e) {
+  static __device__ __forceinline__ Val leaf(int32_t kind, uint32_t e) {
     // beta = 0: every allowed configuration weighs 1, a forbidden one 0
     if (kind == kOpEdge) return e == 3 ? 0u : 1u;
     return 1u;
   }
   template <bool CG = false>
-  static __device__ __forceinline__ Val load(const Operand& o, int64_t e, int q) {
+  static __device__ __forceinline__ Val load(const Operand& o, uint32_t e) {
     if (o.kind != kOpArena) return leaf(o.kind, e);
-    return ldg_t<CG>(static_cast<const uint32_t*>(o.p0) + q * o.prime_stride + e);
+    return ldg_t<CG>(static_cast<const uint32_t*>(o.p0) + e);
   }
-  static __device__ __forceinline__ void copy_async(Val* dst, const Operand& o, int64_t e, int q) {
-    cp_async4(dst, static_cast<const uint32_t*>(o.p0) + q * o.prime_stride + e);
+  static __device__ __forceinline__ void copy_async(Val* dst, const Operand& o, uint32_t e) {
+    cp_async4(dst, static_cast<const uint32_t*>(o.p0) + e);
   }
   static __device__ __forceinline__ void mac(Acc& acc, Val a, Val b, const ModParams& mp) {
     acc = fold32(acc + static_cast<uint64_t>(a) * b, mp.r32);
@@ -273,13 +279,12 @@ struct SrMod {
   static __device__ __forceinline__ void merge(Acc& acc, const Acc& o, const ModParams& mp) {
     acc = static_cast<uint64_t>(barrett64(acc, mp)) + barrett64(o, mp);  // < 2p
   }
-  static __device__ __forceinline__ void store(const Output& o, int64_t e, int q, const Acc& acc,
-                                               const ModParams& mp) {
-    static_cast<uint32_t*>(o.p0)[q * o.prime_stride + e] = barrett64(acc, mp);
+  static __device__ __forceinline__ void store(const Output& o, uint32_t e, const Acc& acc, const ModParams& mp) {
+    static_cast<uint32_t*>(o.p0)[e] = barrett64(acc, mp);
   }
-  static __device__ __forceinline__ void store4(const Output& o, int64_t e, int q, const Acc (&v)[4],
+  static __device__ __forceinline__ void store4(const Output& o, uint32_t e, const Acc (&v)[4],
                                                 const ModParams& mp) {
-    *reinterpret_cast<uint4*>(static_cast<uint32_t*>(o.p0) + q * o.prime_stride + e) =
+    *reinterpret_cast<uint4*>(static_cast<uint32_t*>(o.p0) + e) =
         make_uint4(barrett64(v[0], mp), barrett64(v[1], mp), barrett64(v[2], mp), barrett64(v[3], mp));
   }
   static __device__ __forceinline__ void st4(Acc* p, const Acc (&v)[4]) {

@@ -1,11 +1,15 @@
 // step_device.cuh -- device building blocks shared by the per-step kernels
-// and the persistent plan executor: bit-position maps and the general
-// ("naive chunk") step body with K-parallel reduction.
+// and the persistent plan executor: gather tables (operand offsets of an
+// output or reduction index) and the general ("naive chunk") step body with
+// K-parallel reduction.
 //
 // A step (Sec. 4.1 of arXiv:2501.00227) computes
 //   C[b, m, n] = (+)_k A[b, m, k] (x) B[b, k, n],
 // C stored contiguously as c = n | m << nn | b << (nn + nm) (or scattered
-// through c_pos when the caller fixes the output label order).
+// through c_pos when the caller fixes the output label order).  Operands are
+// read in place: the entry of A holding (b, m, k) has its label bits at the
+// positions a_pos of A's own layout (likewise b_pos for B), so no permuted
+// copy of an operand is ever made.
 #pragma once
 
 #include <cstdint>
@@ -15,31 +19,87 @@
 namespace tn {
 namespace dev {
 
-// Scatter the bits of x into the positions pos[first .. first+count).
-__device__ __forceinline__ int64_t deposit(int64_t x, const int8_t* pos, int first, int count) {
-  int64_t r = 0;
+// Scatter the bits of x into the positions pos[first .. first+count) (used
+// for outputs whose label order the caller fixed).
+__device__ __forceinline__ uint32_t deposit(uint32_t x, const int8_t* pos, int first, int count) {
+  uint32_t r = 0;
   for (int j = 0; j < count; ++j)
-    if ((x >> j) & 1) {
-      int p = pos[first + j];
-      if (p >= 0) r |= int64_t(1) << p;
+    if ((x >> j) & 1u) {
+      const int p = pos[first + j];
+      if (p >= 0) r |= 1u << p;
     }
   return r;
 }
 
+constexpr int kBlock = 256;         // threads per CTA of every libtn kernel
+constexpr int kNib = 8;             // 4-bit nibbles of a 32-bit index
 constexpr int kNaiveKLoBits = 9;    // k offsets of the low 9 bits come from a table
 constexpr int kNaiveKHi = 256;      // high-k blocks per task whose offsets are tabulated
-constexpr int kBlock = 256;         // threads per CTA of every libtn kernel
 constexpr int kNaiveWideU = 4;      // entries per thread in naive_chunk_wide
 
-// Shared-memory scratch of one naive chunk: offsets of the low k bits
-// (ka / kb) and of the high-k blocks [kh_begin, kh_begin + kNaiveKHi) of
-// the task (kha / khb).
+__device__ __forceinline__ int nibbles(int bits) { return (bits + 3) >> 2; }
+
+// Gather tables of one step.  The output index c (rc bits) and the
+// reduction index k (nk bits) are cut into 4-bit nibbles; entry [i][v] is
+// the pair (offset in A, offset in B) contributed by the value v of nibble i.
+// Different bits of an index land on different operand positions, so the
+// offsets of an index are the sums of one entry per nibble: the bit
+// permutation between the step's index space and each operand's layout is
+// resolved by table lookups instead of bit-by-bit scatters.
+struct GatherTabs {
+  uint2 c[kNib][16];
+  uint2 k[kNib][16];
+};
+
+// Fills the gather tables of step g (one entry per thread; no barrier).
+__device__ __forceinline__ void gather_build(const StepGeom& g, GatherTabs& t) {
+  for (int e = threadIdx.x; e < 2 * kNib * 16; e += kBlock) {
+    const int field = e >> 7, i = (e >> 4) & (kNib - 1), v = e & 15;
+    uint32_t oa = 0, ob = 0;
+#pragma unroll
+    for (int bit = 0; bit < 4; ++bit) {
+      if (!((v >> bit) & 1)) continue;
+      const int j = 4 * i + bit;
+      int pa = -1, pb = -1;
+      if (field == 0) {  // output index bit j: n bits, then m bits, then batch bits
+        if (j < g.nn) {
+          pb = g.b_pos[g.nb + g.nk + j];
+        } else if (j < g.nn + g.nm) {
+          pa = g.a_pos[g.nb + j - g.nn];
+        } else if (j < g.rc) {
+          pa = g.a_pos[j - g.nn - g.nm];
+          pb = g.b_pos[j - g.nn - g.nm];
+        }
+      } else if (j < g.nk) {  // reduction index bit j
+        pa = g.a_pos[g.nb + g.nm + j];
+        pb = g.b_pos[g.nb + j];
+      }
+      if (pa >= 0) oa |= 1u << pa;
+      if (pb >= 0) ob |= 1u << pb;
+    }
+    (field ? t.k : t.c)[i][v] = make_uint2(oa, ob);
+  }
+}
+
+// (offset in A, offset in B) of index x from nnib nibble tables.
+__device__ __forceinline__ uint2 gather(const uint2 (*tab)[16], int nnib, uint32_t x) {
+  uint2 r = make_uint2(0u, 0u);
+  for (int i = 0; i < nnib; ++i) {
+    const uint2 e = tab[i][(x >> (4 * i)) & 15u];
+    r.x += e.x;
+    r.y += e.y;
+  }
+  return r;
+}
+
+// Shared-memory scratch of one naive chunk: the gather tables, offsets of
+// the low kNaiveKLoBits reduction bits (klo) and of the high-k blocks
+// [kh_begin, kh_begin + kNaiveKHi) of the task (khi).
 template <class SR>
 struct NaiveSmem {
-  int64_t ka[1 << kNaiveKLoBits];
-  int64_t kb[1 << kNaiveKLoBits];
-  int64_t kha[kNaiveKHi];
-  int64_t khb[kNaiveKHi];
+  GatherTabs gt;
+  uint2 klo[1 << kNaiveKLoBits];
+  uint2 khi[kNaiveKHi];
   typename SR::Acc red[kBlock / 32];
 };
 
@@ -60,41 +120,38 @@ __device__ __forceinline__ CntVal shfl_xor_val(CntVal v, int off) {
   return r;
 }
 
-// Fills the k-offset tables of a step for the high-k blocks
-// [kh_begin, kh_end) (all threads of the CTA; ends with a barrier).
+// Fills the tables of a step for the high-k blocks [kh_begin, kh_end) (all
+// threads of the CTA; ends with a barrier).
 template <class SR>
-__device__ __forceinline__ void naive_tables(const StepGeom& g, NaiveSmem<SR>& sm, int64_t kh_begin,
-                                             int64_t kh_end) {
+__device__ __forceinline__ void naive_tables(const StepGeom& g, NaiveSmem<SR>& sm, int32_t kh_begin,
+                                             int32_t kh_end) {
+  gather_build(g, sm.gt);
+  __syncthreads();
   const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
-  const int a_k0 = g.nb + g.nm, b_k0 = g.nb;
-  for (int i = threadIdx.x; i < (1 << kl); i += kBlock) {
-    sm.ka[i] = deposit(i, g.a_pos, a_k0, kl);
-    sm.kb[i] = deposit(i, g.b_pos, b_k0, kl);
-  }
+  const int nkn = nibbles(g.nk);
+  for (int i = threadIdx.x; i < (1 << kl); i += kBlock) sm.klo[i] = gather(sm.gt.k, nkn, static_cast<uint32_t>(i));
   if (kh_end - kh_begin <= kNaiveKHi)
-    for (int i = threadIdx.x; i < kh_end - kh_begin; i += kBlock) {
-      sm.kha[i] = deposit(kh_begin + i, g.a_pos, a_k0 + kl, g.nk - kl);
-      sm.khb[i] = deposit(kh_begin + i, g.b_pos, b_k0 + kl, g.nk - kl);
-    }
+    for (int i = threadIdx.x; i < kh_end - kh_begin; i += kBlock)
+      sm.khi[i] = gather(sm.gt.k, nkn, static_cast<uint32_t>(kh_begin + i) << kl);
   __syncthreads();
 }
 
-// Computes output entries [c_begin, c_end) of a step for prime index q,
-// over the high-k blocks [kh_begin, kh_end) (each block is 2^min(nk, 9) k's;
-// naive_tables must have been called with the same block range).
-// R threads (a power of two, 1..256, R <= 2^nk) share each output entry:
-// lane l takes the terms l, l + R, l + 2R, ... of the entry's flattened
-// (block, low k) range, NaiveUnroll loads per operand in flight (a batch
-// beyond the range is padded with the edge tensor's forbidden entry, the
-// semiring zero: (max,+) -inf, (max, count) (-inf, 0), mod p 0), then the R
-// partial results are merged with the semiring (+) by warp shuffles
-// (R <= 32) or through shared memory.  The merged value of entry c goes to
-// sink(c, acc) (called by one thread).  Every thread of the CTA must call
-// this (it uses barriers when R > 32).
+// Computes output entries [c_begin, c_end) of a step over the high-k blocks
+// [kh_begin, kh_end) (each block is 2^min(nk, 9) k's; naive_tables must
+// have been called with the same block range).  R threads (a power of two,
+// 1..256, R <= 2^nk) share each output entry: lane l takes the terms l,
+// l + R, l + 2R, ... of the entry's flattened (block, low k) range,
+// NaiveUnroll loads per operand in flight (a batch beyond the range is
+// padded with the edge tensor's forbidden entry, the semiring zero: (max,+)
+// -inf, (max, count) (-inf, 0), mod p 0), then the R partial results are
+// merged with the semiring (+) by warp shuffles (R <= 32) or through shared
+// memory.  The merged value of entry c goes to sink(c, acc) (called by one
+// thread).  Every thread of the CTA must call this (it uses barriers when
+// R > 32).
 template <class SR, class LoadA, class LoadB, class Sink>
 __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, LoadB loadB, Sink sink,
-                                            const ModParams& mp, int64_t c_begin, int64_t c_end,
-                                            int64_t kh_begin, int64_t kh_end, int R, NaiveSmem<SR>& sm) {
+                                            const ModParams& mp, int32_t c_begin, int32_t c_end,
+                                            int32_t kh_begin, int32_t kh_end, int R, NaiveSmem<SR>& sm) {
   using Acc = typename SR::Acc;
   using Val = typename SR::Val;
   constexpr int U = NaiveUnroll<SR>::v;
@@ -102,38 +159,34 @@ __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, Load
   const int slot = tid / R, lane = tid % R;
   const int per_pass = kBlock / R;
   const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
-  const int64_t mlo = (int64_t(1) << kl) - 1;
-  const int a_k0 = g.nb + g.nm, b_k0 = g.nb;
-  const int64_t mask_n = (int64_t(1) << g.nn) - 1, mask_m = (int64_t(1) << g.nm) - 1;
-  const int64_t nterm = (kh_end - kh_begin) << kl;
+  const uint32_t mlo = (1u << kl) - 1u;
+  const int ncn = nibbles(g.rc), nkn = nibbles(g.nk);
+  const int32_t nterm = (kh_end - kh_begin) << kl;
   const bool tab = kh_end - kh_begin <= kNaiveKHi;
-  // offsets of term j inside A and B (high block from the table or computed)
-  auto koffA = [&](int64_t j) -> int64_t {
-    const int64_t h = j >> kl;
-    return (tab ? sm.kha[h] : deposit(kh_begin + h, g.a_pos, a_k0 + kl, g.nk - kl)) | sm.ka[j & mlo];
+  // offsets (in A, in B) of term j of the task's k range
+  auto koff = [&](int32_t j) -> uint2 {
+    const int32_t h = j >> kl;
+    const uint2 hi = tab ? sm.khi[h] : gather(sm.gt.k, nkn, static_cast<uint32_t>(kh_begin + h) << kl);
+    const uint2 lo = sm.klo[static_cast<uint32_t>(j) & mlo];
+    return make_uint2(hi.x + lo.x, hi.y + lo.y);
   };
-  auto koffB = [&](int64_t j) -> int64_t {
-    const int64_t h = j >> kl;
-    return (tab ? sm.khb[h] : deposit(kh_begin + h, g.b_pos, b_k0 + kl, g.nk - kl)) | sm.kb[j & mlo];
-  };
-  for (int64_t cb = c_begin; cb < c_end; cb += per_pass) {
-    const int64_t c = cb + slot;
+  for (int32_t cb = c_begin; cb < c_end; cb += per_pass) {
+    const int32_t c = cb + slot;
     const bool valid = c < c_end;
     Acc acc = SR::zero(mp);
     if (valid) {
-      const int64_t n = c & mask_n, m = (c >> g.nn) & mask_m, b = c >> (g.nn + g.nm);
-      const int64_t base_a = deposit(b, g.a_pos, 0, g.nb) | deposit(m, g.a_pos, g.nb, g.nm);
-      const int64_t base_b = deposit(b, g.b_pos, 0, g.nb) | deposit(n, g.b_pos, g.nb + g.nk, g.nn);
+      const uint2 base = gather(sm.gt.c, ncn, static_cast<uint32_t>(c));
       // U terms per batch; the last batch pads with the semiring zero, so
       // its loads are in flight together as well
-      for (int64_t j = lane; j < nterm; j += U * R) {
+      for (int32_t j = lane; j < nterm; j += U * R) {
         Val va[U], vb[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          const int64_t jj = j + u * R;
+          const int32_t jj = j + u * R;
           const bool in = jj < nterm;
-          va[u] = in ? loadA(base_a | koffA(jj)) : SR::leaf(kOpEdge, 3);
-          vb[u] = in ? loadB(base_b | koffB(jj)) : SR::leaf(kOpEdge, 3);
+          const uint2 o = koff(in ? jj : j);
+          va[u] = in ? loadA(base.x + o.x) : SR::leaf(kOpEdge, 3);
+          vb[u] = in ? loadB(base.y + o.y) : SR::leaf(kOpEdge, 3);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) SR::mac(acc, va[u], vb[u], mp);
@@ -153,7 +206,7 @@ __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, Load
       }
       __syncthreads();
     }
-    if (valid && lane == 0) sink(c, acc);
+    if (valid && lane == 0) sink(static_cast<uint32_t>(c), acc);
   }
 }
 
@@ -163,44 +216,43 @@ __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, Load
 // reductions; covers the whole k range (naive_tables over all high-k blocks).
 template <class SR, int U, class LoadA, class LoadB, class Sink>
 __device__ __forceinline__ void naive_chunk_wide(const StepGeom& g, LoadA loadA, LoadB loadB, Sink sink,
-                                                 const ModParams& mp, int64_t c_begin, int64_t c_end,
+                                                 const ModParams& mp, int32_t c_begin, int32_t c_end,
                                                  NaiveSmem<SR>& sm) {
   using Acc = typename SR::Acc;
   const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
-  const int64_t mlo = (int64_t(1) << kl) - 1, nterm = int64_t(1) << g.nk;
-  const int a_k0 = g.nb + g.nm, b_k0 = g.nb;
+  const uint32_t mlo = (1u << kl) - 1u;
+  const int32_t nterm = 1 << g.nk;
+  const int ncn = nibbles(g.rc), nkn = nibbles(g.nk);
   const bool tab = (nterm >> kl) <= kNaiveKHi;
-  const int64_t mask_n = (int64_t(1) << g.nn) - 1, mask_m = (int64_t(1) << g.nm) - 1;
-  for (int64_t cb = c_begin; cb < c_end; cb += int64_t(U) * kBlock) {
-    int64_t base_a[U], base_b[U];
+  for (int32_t cb = c_begin; cb < c_end; cb += U * kBlock) {
+    uint2 base[U];
     Acc acc[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t c = cb + threadIdx.x + int64_t(u) * kBlock;
-      const int64_t cc = c < c_end ? c : c_begin;  // out-of-range lanes recompute a valid entry
-      const int64_t n = cc & mask_n, m = (cc >> g.nn) & mask_m, b = cc >> (g.nn + g.nm);
-      base_a[u] = deposit(b, g.a_pos, 0, g.nb) | deposit(m, g.a_pos, g.nb, g.nm);
-      base_b[u] = deposit(b, g.b_pos, 0, g.nb) | deposit(n, g.b_pos, g.nb + g.nk, g.nn);
+      const int32_t c = cb + static_cast<int32_t>(threadIdx.x) + u * kBlock;
+      const int32_t cc = c < c_end ? c : c_begin;  // out-of-range lanes recompute a valid entry
+      base[u] = gather(sm.gt.c, ncn, static_cast<uint32_t>(cc));
       acc[u] = SR::zero(mp);
     }
 #pragma unroll 2
-    for (int64_t j = 0; j < nterm; ++j) {
-      const int64_t h = j >> kl;
-      const int64_t ka = (tab ? sm.kha[h] : deposit(h, g.a_pos, a_k0 + kl, g.nk - kl)) | sm.ka[j & mlo];
-      const int64_t kb = (tab ? sm.khb[h] : deposit(h, g.b_pos, b_k0 + kl, g.nk - kl)) | sm.kb[j & mlo];
+    for (int32_t j = 0; j < nterm; ++j) {
+      const int32_t h = j >> kl;
+      const uint2 hi = tab ? sm.khi[h] : gather(sm.gt.k, nkn, static_cast<uint32_t>(h) << kl);
+      const uint2 lo = sm.klo[static_cast<uint32_t>(j) & mlo];
+      const uint32_t ka = hi.x + lo.x, kb = hi.y + lo.y;
       typename SR::Val va[U], vb[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        va[u] = loadA(base_a[u] | ka);
-        vb[u] = loadB(base_b[u] | kb);
+        va[u] = loadA(base[u].x + ka);
+        vb[u] = loadB(base[u].y + kb);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) SR::mac(acc[u], va[u], vb[u], mp);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t c = cb + threadIdx.x + int64_t(u) * kBlock;
-      if (c < c_end) sink(c, acc[u]);
+      const int32_t c = cb + static_cast<int32_t>(threadIdx.x) + u * kBlock;
+      if (c < c_end) sink(static_cast<uint32_t>(c), acc[u]);
     }
   }
 }

@@ -12,10 +12,11 @@
 // the semiring (+) at the end.  KG > 1 lets small M x N tiles (32 x 32) keep
 // 4 x 4 register blocking.
 //
-// Operands are read in place through bit-position maps: the offset of
-// A[b, m, k] is dep_b(b) + dep_m(m) + dep_k(k).  A tile covers the low bits of
-// m, n and k, so each thread's staging offsets are fixed for the whole tile
-// and only a per-chunk base (the high k bits) changes.
+// Operands are read in place through the step's gather tables (see
+// step_device.cuh): the offset of A[b, m, k] is the sum of the offset of the
+// output index (b, m, n = 0) and of the reduction index k.  A tile covers the
+// low bits of m, n and k, so each thread's staging offsets are fixed for the
+// whole tile and only a per-chunk base (the high k bits) changes.
 #pragma once
 
 #include "semiring.cuh"
@@ -75,15 +76,68 @@ struct Stages {
   static constexpr int v = sizeof(typename SR::Val) <= 4 ? 3 : 2;
 };
 
+// Index part of a tile's shared memory (same place for every element type,
+// so the two passes of the counting tile share it).
+template <class C>
+struct TileIdx {
+  GatherTabs gt;
+  uint32_t offAm[C::BM];
+  uint32_t offBn[C::BN];
+  uint32_t offAk[C::BK];
+  uint32_t offBk[C::BK];
+};
+
 template <class SR, class C>
 struct TileSmem {
-  typename SR::Val As[Stages<SR>::v][C::BK * C::BM];
-  typename SR::Val Bs[Stages<SR>::v][C::BK * C::BN];
-  int64_t offAm[C::BM];
-  int64_t offBn[C::BN];
-  int64_t offAk[C::BK];
-  int64_t offBk[C::BK];
+  TileIdx<C> idx;
+  alignas(16) typename SR::Val As[Stages<SR>::v][C::BK * C::BM];
+  alignas(16) typename SR::Val Bs[Stages<SR>::v][C::BK * C::BN];
 };
+
+// Staging offsets of tile (tm, tn_) of batch b for this thread (element
+// e = tid + 256 j of a chunk: A as [k][m], B as [k][n]), -1 for padding
+// outside M, N or K.  All threads must call it (it has barriers).
+template <class C>
+__device__ __forceinline__ void tile_offsets(const StepGeom& g, TileIdx<C>& ix, int64_t b, int64_t tm,
+                                             int64_t tn_, int32_t (&offA)[C::EA], int32_t (&offB)[C::EB]) {
+  constexpr int BM = C::BM, BN = C::BN, BK = C::BK;
+  const int tid = threadIdx.x;
+  const uint32_t M = 1u << g.nm, N = 1u << g.nn, K = 1u << g.nk;
+  const uint32_t m0 = static_cast<uint32_t>(tm) * BM, n0 = static_cast<uint32_t>(tn_) * BN;
+  const int ncn = nibbles(g.rc), nkn = nibbles(g.nk);
+  gather_build(g, ix.gt);
+  __syncthreads();
+  const uint32_t cb = static_cast<uint32_t>(b) << (g.nn + g.nm);
+  for (int i = tid; i < BM; i += kBlock)
+    ix.offAm[i] = m0 + i < M ? gather(ix.gt.c, ncn, cb | ((m0 + i) << g.nn)).x : 0u;
+  for (int i = tid; i < BN; i += kBlock) ix.offBn[i] = n0 + i < N ? gather(ix.gt.c, ncn, cb | (n0 + i)).y : 0u;
+  for (int i = tid; i < BK; i += kBlock) {
+    const uint2 o = gather(ix.gt.k, nkn, static_cast<uint32_t>(i) < K ? static_cast<uint32_t>(i) : 0u);
+    ix.offAk[i] = o.x;
+    ix.offBk[i] = o.y;
+  }
+  __syncthreads();
+  const uint32_t kvalid = K < BK ? K : BK;  // k rows that exist inside a chunk
+#pragma unroll
+  for (int j = 0; j < C::EA; ++j) {
+    const int e = tid + kBlock * j, kk = e / BM, mm = e % BM;
+    const bool ok = (m0 + mm < M) && (static_cast<uint32_t>(kk) < kvalid);
+    offA[j] = ok ? static_cast<int32_t>(ix.offAm[mm] + ix.offAk[kk]) : -1;
+  }
+#pragma unroll
+  for (int j = 0; j < C::EB; ++j) {
+    const int e = tid + kBlock * j, kk = e / BN, nn = e % BN;
+    const bool ok = (n0 + nn < N) && (static_cast<uint32_t>(kk) < kvalid);
+    offB[j] = ok ? static_cast<int32_t>(ix.offBn[nn] + ix.offBk[kk]) : -1;
+  }
+}
+
+// Offsets (in A, in B) of the chunk of k rows starting at k0 (a multiple of
+// BK: its bits are disjoint from those of the rows inside the chunk).
+template <class C>
+__device__ __forceinline__ uint2 tile_chunk_base(const StepGeom& g, const TileIdx<C>& ix, int64_t k0) {
+  return gather(ix.gt.k, nibbles(g.nk), static_cast<uint32_t>(k0));
+}
 
 // Fragment of T consecutive 4-byte values from shared memory (16-byte
 // vector loads when T is a multiple of 4; the address is 16-byte aligned).
@@ -120,50 +174,19 @@ struct Log2<1> {
 // threads of the CTA must call it.
 template <class SR, class C, int FOLD, bool CG>
 __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& A, const Operand& B,
-                                              const ModParams& mp, int q, int64_t b, int64_t tm,
-                                              int64_t tn_, int64_t kbeg, int64_t kend,
-                                              TileSmem<SR, C>& sm,
+                                              const ModParams& mp, int64_t b, int64_t tm, int64_t tn_,
+                                              int64_t kbeg, int64_t kend, TileSmem<SR, C>& sm,
                                               typename SR::Acc (&acc)[C::TM][C::TN]) {
   using Val = typename SR::Val;
   using T = Tiled<SR>;
   constexpr int kStages = Stages<SR>::v;
   constexpr int BM = C::BM, BN = C::BN, BK = C::BK, TM = C::TM, TN = C::TN;
-  constexpr int lbm = Log2<BM>::v, lbn = Log2<BN>::v, lbk = Log2<BK>::v;
   const int tid = threadIdx.x;
   const int grp = tid / C::GT, gt = tid % C::GT;
   const int tx = gt % C::WN, ty = gt / C::WN;
-  const int64_t M = int64_t(1) << g.nm, N = int64_t(1) << g.nn, K = int64_t(1) << g.nk;
-  const int64_t m0 = tm * BM, n0 = tn_ * BN;
-  const int a_k0 = g.nb + g.nm, b_k0 = g.nb, b_n0 = g.nb + g.nk;
 
-  for (int i = tid; i < BM; i += kBlock) sm.offAm[i] = deposit(i, g.a_pos, g.nb, min(lbm, g.nm));
-  for (int i = tid; i < BN; i += kBlock) sm.offBn[i] = deposit(i, g.b_pos, b_n0, min(lbn, g.nn));
-  for (int i = tid; i < BK; i += kBlock) {
-    sm.offAk[i] = deposit(i, g.a_pos, a_k0, min(lbk, g.nk));
-    sm.offBk[i] = deposit(i, g.b_pos, b_k0, min(lbk, g.nk));
-  }
-  const int64_t baseA = deposit(b, g.a_pos, 0, g.nb) +
-                        (g.nm > lbm ? deposit(m0 >> lbm, g.a_pos, g.nb + lbm, g.nm - lbm) : 0);
-  const int64_t baseB = deposit(b, g.b_pos, 0, g.nb) +
-                        (g.nn > lbn ? deposit(n0 >> lbn, g.b_pos, b_n0 + lbn, g.nn - lbn) : 0);
-  __syncthreads();
-
-  // this thread's staging slots: element e = tid + 256 j of the chunk; the
-  // entry offset inside the operand (< 2^30), or -1 for padding
   int32_t offA[C::EA], offB[C::EB];
-  const int64_t kvalid = K < BK ? K : BK;  // k rows that exist inside a chunk
-#pragma unroll
-  for (int j = 0; j < C::EA; ++j) {
-    const int e = tid + kBlock * j, kk = e / BM, mm = e % BM;
-    const bool ok = (m0 + mm < M) && (kk < kvalid);
-    offA[j] = ok ? static_cast<int32_t>(baseA + sm.offAm[mm] + sm.offAk[kk]) : -1;
-  }
-#pragma unroll
-  for (int j = 0; j < C::EB; ++j) {
-    const int e = tid + kBlock * j, kk = e / BN, nn = e % BN;
-    const bool ok = (n0 + nn < N) && (kk < kvalid);
-    offB[j] = ok ? static_cast<int32_t>(baseB + sm.offBn[nn] + sm.offBk[kk]) : -1;
-  }
+  tile_offsets<C>(g, sm.idx, b, tm, tn_, offA, offB);
 
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -185,19 +208,20 @@ __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& 
   // operands, plain loads for leaves generated on the fly
   const bool a_async = A.kind == kOpArena, b_async = B.kind == kOpArena;
   auto issue = [&](int st, int64_t k0) {
-    const int64_t kA = g.nk > lbk ? deposit(k0 >> lbk, g.a_pos, a_k0 + lbk, g.nk - lbk) : 0;
-    const int64_t kB = g.nk > lbk ? deposit(k0 >> lbk, g.b_pos, b_k0 + lbk, g.nk - lbk) : 0;
+    const uint2 kb = tile_chunk_base<C>(g, sm.idx, k0);
 #pragma unroll
     for (int j = 0; j < C::EA; ++j)
       if (offA[j] >= 0) {
-        if (a_async) SR::copy_async(&sm.As[st][tid + kBlock * j], A, offA[j] + kA, q);
-        else sm.As[st][tid + kBlock * j] = SR::template load<CG>(A, offA[j] + kA, q);
+        const uint32_t e = static_cast<uint32_t>(offA[j]) + kb.x;
+        if (a_async) SR::copy_async(&sm.As[st][tid + kBlock * j], A, e);
+        else sm.As[st][tid + kBlock * j] = SR::template load<CG>(A, e);
       }
 #pragma unroll
     for (int j = 0; j < C::EB; ++j)
       if (offB[j] >= 0) {
-        if (b_async) SR::copy_async(&sm.Bs[st][tid + kBlock * j], B, offB[j] + kB, q);
-        else sm.Bs[st][tid + kBlock * j] = SR::template load<CG>(B, offB[j] + kB, q);
+        const uint32_t e = static_cast<uint32_t>(offB[j]) + kb.y;
+        if (b_async) SR::copy_async(&sm.Bs[st][tid + kBlock * j], B, e);
+        else sm.Bs[st][tid + kBlock * j] = SR::template load<CG>(B, e);
       }
   };
 #pragma unroll
@@ -329,42 +353,17 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
                                                        CntVal (&acc)[C::TM][C::TN]) {
   constexpr int BM = C::BM, BN = C::BN, BK = C::BK, TM = C::TM, TN = C::TN;
   constexpr int kSt = Stages<SrCnt>::v;
-  constexpr int lbm = Log2<BM>::v, lbn = Log2<BN>::v, lbk = Log2<BK>::v;
   // pass 1: maxima of the values
   int32_t vmax[TM][TN];
-  tile_mainloop<SrI32, C, 1, CG>(g, A, B, mp, 0, b, tm, tn_, kbeg, kend,
+  tile_mainloop<SrI32, C, 1, CG>(g, A, B, mp, b, tm, tn_, kbeg, kend,
                                  *reinterpret_cast<TileSmem<SrI32, C>*>(smem_raw), vmax);
-  // pass 2: counts of the maximising terms
+  // pass 2: counts of the maximising terms (same index tables, same offsets)
   auto& sm = *reinterpret_cast<TileSmem<SrCnt, C>*>(smem_raw);
   const int tid = threadIdx.x;
   const int grp = tid / C::GT, gt = tid % C::GT;
   const int tx = gt % C::WN, ty = gt / C::WN;
-  const int64_t M = int64_t(1) << g.nm, N = int64_t(1) << g.nn, K = int64_t(1) << g.nk;
-  const int64_t m0 = tm * BM, n0 = tn_ * BN;
-  const int a_k0 = g.nb + g.nm, b_k0 = g.nb, b_n0 = g.nb + g.nk;
-  for (int i = tid; i < BM; i += kBlock) sm.offAm[i] = deposit(i, g.a_pos, g.nb, min(lbm, g.nm));
-  for (int i = tid; i < BN; i += kBlock) sm.offBn[i] = deposit(i, g.b_pos, b_n0, min(lbn, g.nn));
-  for (int i = tid; i < BK; i += kBlock) {
-    sm.offAk[i] = deposit(i, g.a_pos, a_k0, min(lbk, g.nk));
-    sm.offBk[i] = deposit(i, g.b_pos, b_k0, min(lbk, g.nk));
-  }
-  const int64_t baseA = deposit(b, g.a_pos, 0, g.nb) +
-                        (g.nm > lbm ? deposit(m0 >> lbm, g.a_pos, g.nb + lbm, g.nm - lbm) : 0);
-  const int64_t baseB = deposit(b, g.b_pos, 0, g.nb) +
-                        (g.nn > lbn ? deposit(n0 >> lbn, g.b_pos, b_n0 + lbn, g.nn - lbn) : 0);
-  __syncthreads();
   int32_t offA[C::EA], offB[C::EB];
-  const int64_t kvalid = K < BK ? K : BK;
-#pragma unroll
-  for (int j = 0; j < C::EA; ++j) {
-    const int e = tid + kBlock * j, kk = e / BM, mm = e % BM;
-    offA[j] = ((m0 + mm < M) && (kk < kvalid)) ? static_cast<int32_t>(baseA + sm.offAm[mm] + sm.offAk[kk]) : -1;
-  }
-#pragma unroll
-  for (int j = 0; j < C::EB; ++j) {
-    const int e = tid + kBlock * j, kk = e / BN, nn = e % BN;
-    offB[j] = ((n0 + nn < N) && (kk < kvalid)) ? static_cast<int32_t>(baseB + sm.offBn[nn] + sm.offBk[kk]) : -1;
-  }
+  tile_offsets<C>(g, sm.idx, b, tm, tn_, offA, offB);
   const CntVal zero = SrCnt::leaf(kOpEdge, 3);
 #pragma unroll
   for (int j = 0; j < C::EA; ++j)
@@ -383,19 +382,20 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
 
   const bool a_async = A.kind == kOpArena, b_async = B.kind == kOpArena;
   auto issue = [&](int st, int64_t k0) {
-    const int64_t kA = g.nk > lbk ? deposit(k0 >> lbk, g.a_pos, a_k0 + lbk, g.nk - lbk) : 0;
-    const int64_t kB = g.nk > lbk ? deposit(k0 >> lbk, g.b_pos, b_k0 + lbk, g.nk - lbk) : 0;
+    const uint2 kb = tile_chunk_base<C>(g, sm.idx, k0);
 #pragma unroll
     for (int j = 0; j < C::EA; ++j)
       if (offA[j] >= 0) {
-        if (a_async) SrCnt::copy_async(&sm.As[st][tid + kBlock * j], A, offA[j] + kA, 0);
-        else sm.As[st][tid + kBlock * j] = SrCnt::template load<CG>(A, offA[j] + kA, 0);
+        const uint32_t e = static_cast<uint32_t>(offA[j]) + kb.x;
+        if (a_async) SrCnt::copy_async(&sm.As[st][tid + kBlock * j], A, e);
+        else sm.As[st][tid + kBlock * j] = SrCnt::template load<CG>(A, e);
       }
 #pragma unroll
     for (int j = 0; j < C::EB; ++j)
       if (offB[j] >= 0) {
-        if (b_async) SrCnt::copy_async(&sm.Bs[st][tid + kBlock * j], B, offB[j] + kB, 0);
-        else sm.Bs[st][tid + kBlock * j] = SrCnt::template load<CG>(B, offB[j] + kB, 0);
+        const uint32_t e = static_cast<uint32_t>(offB[j]) + kb.y;
+        if (b_async) SrCnt::copy_async(&sm.Bs[st][tid + kBlock * j], B, e);
+        else sm.Bs[st][tid + kBlock * j] = SrCnt::template load<CG>(B, e);
       }
   };
 #pragma unroll
