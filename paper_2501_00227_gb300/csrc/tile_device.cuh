@@ -19,6 +19,8 @@
 // whole tile and only a per-chunk base (the high k bits) changes.
 #pragma once
 
+#include <type_traits>
+
 #include "semiring.cuh"
 #include "step_device.cuh"
 
@@ -298,12 +300,18 @@ __device__ __forceinline__ void tile_merge_groups(typename SR::Acc (&acc)[C::TM]
   }
 }
 
-// Shared memory a tile needs: staging, or the group-merge buffer.
+template <class C>
+struct TileSmemCnt;
+
+// Shared memory a tile needs: staging (both passes for counting), or the
+// group-merge buffer.
 template <class SR, class C>
 constexpr size_t tile_smem_bytes() {
-  return sizeof(TileSmem<SR, C>) > sizeof(typename SR::Acc) * (C::KG - 1) * C::BM * C::BN
-             ? sizeof(TileSmem<SR, C>)
-             : sizeof(typename SR::Acc) * (C::KG - 1) * C::BM * C::BN;
+  size_t stage = sizeof(TileSmem<SR, C>);
+  if constexpr (std::is_same<SR, SrCnt>::value)
+    stage = sizeof(TileSmemCnt<C>) > sizeof(TileSmem<SrI32, C>) ? sizeof(TileSmemCnt<C>) : sizeof(TileSmem<SrI32, C>);
+  const size_t merge = sizeof(typename SR::Acc) * (C::KG - 1) * C::BM * C::BN;
+  return stage > merge ? stage : merge;
 }
 
 }  // namespace dev
@@ -346,6 +354,43 @@ __device__ __forceinline__ void cnt_add64(uint32_t& c0, uint32_t& c1, uint32_t& 
       : "r"(static_cast<uint32_t>(p)), "r"(static_cast<uint32_t>(p >> 32)));
 }
 
+// (c1 : c0) += a * b when s == vmax (64-bit multiply-add; the caller
+// guarantees no carry out of c1)
+__device__ __forceinline__ void cnt_fma_wide(uint32_t& c0, uint32_t& c1, int32_t s, int32_t vmax, uint32_t a,
+                                             uint32_t b) {
+  asm("{\n\t.reg .pred p;\n\t.reg .u64 t;\n\t"
+      "setp.eq.s32 p, %2, %3;\n\t"
+      "mov.b64 t, {%0, %1};\n\t"
+      "@p mad.wide.u32 t, %4, %5, t;\n\t"
+      "mov.b64 {%0, %1}, t;\n\t}"
+      : "+r"(c0), "+r"(c1)
+      : "r"(s), "r"(vmax), "r"(a), "r"(b));
+}
+
+// Low 32 bits of T consecutive uint64 counts in shared memory (16-byte loads).
+template <int T>
+__device__ __forceinline__ void load_lo_frag(const uint64_t* p, uint32_t (&out)[T]) {
+  static_assert(T % 2 == 0, "pairs of counts");
+#pragma unroll
+  for (int i = 0; i < T; i += 2) {
+    const uint4 w = *reinterpret_cast<const uint4*>(p + i);
+    out[i] = w.x;
+    out[i + 1] = w.z;
+  }
+}
+
+// Shared memory of the counting tile's second pass: values and counts of
+// each staged chunk in separate arrays.
+template <class C>
+struct TileSmemCnt {
+  static constexpr int kSt = Stages<SrCnt>::v;
+  TileIdx<C> idx;
+  alignas(16) int32_t Av[kSt][C::BK * C::BM];
+  alignas(16) int32_t Bv[kSt][C::BK * C::BN];
+  alignas(16) uint64_t Ac[kSt][C::BK * C::BM];
+  alignas(16) uint64_t Bc[kSt][C::BK * C::BN];
+};
+
 template <class C, bool CG>
 __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const Operand& A, const Operand& B,
                                                        const ModParams& mp, int64_t b, int64_t tm, int64_t tn_,
@@ -357,23 +402,31 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
   int32_t vmax[TM][TN];
   tile_mainloop<SrI32, C, 1, CG>(g, A, B, mp, b, tm, tn_, kbeg, kend,
                                  *reinterpret_cast<TileSmem<SrI32, C>*>(smem_raw), vmax);
-  // pass 2: counts of the maximising terms (same index tables, same offsets)
-  auto& sm = *reinterpret_cast<TileSmem<SrCnt, C>*>(smem_raw);
+  // pass 2: counts of the maximising terms (same index tables, same offsets);
+  // values and counts are staged in separate arrays, so every fragment is a
+  // run of 16-byte shared loads
+  auto& sm = *reinterpret_cast<TileSmemCnt<C>*>(smem_raw);
   const int tid = threadIdx.x;
   const int grp = tid / C::GT, gt = tid % C::GT;
   const int tx = gt % C::WN, ty = gt / C::WN;
   int32_t offA[C::EA], offB[C::EB];
   tile_offsets<C>(g, sm.idx, b, tm, tn_, offA, offB);
-  const CntVal zero = SrCnt::leaf(kOpEdge, 3);
 #pragma unroll
   for (int j = 0; j < C::EA; ++j)
     if (offA[j] < 0)
-      for (int st = 0; st < kSt; ++st) sm.As[st][tid + kBlock * j] = zero;
+      for (int st = 0; st < kSt; ++st) {
+        sm.Av[st][tid + kBlock * j] = kNegInf;
+        sm.Ac[st][tid + kBlock * j] = 0ull;
+      }
 #pragma unroll
   for (int j = 0; j < C::EB; ++j)
     if (offB[j] < 0)
-      for (int st = 0; st < kSt; ++st) sm.Bs[st][tid + kBlock * j] = zero;
+      for (int st = 0; st < kSt; ++st) {
+        sm.Bv[st][tid + kBlock * j] = kNegInf;
+        sm.Bc[st][tid + kBlock * j] = 0ull;
+      }
 
+  // count of entry (i, j) = c2 * 2^64 + (c1 : c0)
   uint32_t c0[TM][TN], c1[TM][TN], c2[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -387,15 +440,27 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
     for (int j = 0; j < C::EA; ++j)
       if (offA[j] >= 0) {
         const uint32_t e = static_cast<uint32_t>(offA[j]) + kb.x;
-        if (a_async) SrCnt::copy_async(&sm.As[st][tid + kBlock * j], A, e);
-        else sm.As[st][tid + kBlock * j] = SrCnt::template load<CG>(A, e);
+        if (a_async) {
+          cp_async4(&sm.Av[st][tid + kBlock * j], static_cast<const int32_t*>(A.p0) + e);
+          cp_async8(&sm.Ac[st][tid + kBlock * j], static_cast<const uint64_t*>(A.p1) + e);
+        } else {
+          const CntVal v = SrCnt::template load<CG>(A, e);
+          sm.Av[st][tid + kBlock * j] = v.v;
+          sm.Ac[st][tid + kBlock * j] = v.c;
+        }
       }
 #pragma unroll
     for (int j = 0; j < C::EB; ++j)
       if (offB[j] >= 0) {
         const uint32_t e = static_cast<uint32_t>(offB[j]) + kb.y;
-        if (b_async) SrCnt::copy_async(&sm.Bs[st][tid + kBlock * j], B, e);
-        else sm.Bs[st][tid + kBlock * j] = SrCnt::template load<CG>(B, e);
+        if (b_async) {
+          cp_async4(&sm.Bv[st][tid + kBlock * j], static_cast<const int32_t*>(B.p0) + e);
+          cp_async8(&sm.Bc[st][tid + kBlock * j], static_cast<const uint64_t*>(B.p1) + e);
+        } else {
+          const CntVal v = SrCnt::template load<CG>(B, e);
+          sm.Bv[st][tid + kBlock * j] = v.v;
+          sm.Bc[st][tid + kBlock * j] = v.c;
+        }
       }
   };
 #pragma unroll
@@ -406,46 +471,69 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
   int cur = 0;
   for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
     cp_async_wait<kSt - 2>();
-    // this thread's own copies of the chunk are complete: do they all fit 32 bits?
-    uint32_t hi = 0;
+    // this thread's own copies of the chunk are complete.  Fast chunk: every
+    // count < 2^16 (products < 2^32) and every accumulator < 2^62, so 64-bit
+    // multiply-adds cannot carry out of (c1 : c0).
+    uint64_t hi = 0;
 #pragma unroll
-    for (int j = 0; j < C::EA; ++j) hi |= static_cast<uint32_t>(sm.As[cur][tid + kBlock * j].c >> 32);
+    for (int j = 0; j < C::EA; ++j) hi |= sm.Ac[cur][tid + kBlock * j];
 #pragma unroll
-    for (int j = 0; j < C::EB; ++j) hi |= static_cast<uint32_t>(sm.Bs[cur][tid + kBlock * j].c >> 32);
-    const bool wide = __syncthreads_or(hi != 0) != 0;
+    for (int j = 0; j < C::EB; ++j) hi |= sm.Bc[cur][tid + kBlock * j];
+    uint32_t big = 0;
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) big |= c1[i][j] >> 30;
+    const bool slow = __syncthreads_or((hi >> 16) != 0 || big != 0) != 0;
+    const bool wide = slow && __syncthreads_or((hi >> 32) != 0) != 0;
     {
       const int64_t kn = k0 + (kSt - 1) * BK;
       const int nxt = (cur + kSt - 1) % kSt;
       if (kn < kend) issue(nxt, kn);
       cp_async_commit();
     }
-    const CntVal* Ag = sm.As[cur] + grp * C::BKG * BM;
-    const CntVal* Bg = sm.Bs[cur] + grp * C::BKG * BN;
-    if (!wide) {
+    const int32_t* Agv = sm.Av[cur] + grp * C::BKG * BM;
+    const int32_t* Bgv = sm.Bv[cur] + grp * C::BKG * BN;
+    const uint64_t* Agc = sm.Ac[cur] + grp * C::BKG * BM;
+    const uint64_t* Bgc = sm.Bc[cur] + grp * C::BKG * BN;
+    if (!slow) {
 #pragma unroll 2
       for (int kk = 0; kk < C::BKG; ++kk) {
-        CntVal a[TM], bv[TN];
+        int32_t av[TM], bv[TN];
+        uint32_t ac[TM], bc[TN];
+        load_frag<TM>(Agv + kk * BM + ty * TM, av);
+        load_frag<TN>(Bgv + kk * BN + tx * TN, bv);
+        load_lo_frag<TM>(Agc + kk * BM + ty * TM, ac);
+        load_lo_frag<TN>(Bgc + kk * BN + tx * TN, bc);
 #pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = Ag[kk * BM + ty * TM + i];
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) bv[j] = Bg[kk * BN + tx * TN + j];
+          for (int j = 0; j < TN; ++j) cnt_fma_wide(c0[i][j], c1[i][j], av[i] + bv[j], vmax[i][j], ac[i], bc[j]);
+      }
+    } else if (!wide) {
+      for (int kk = 0; kk < C::BKG; ++kk) {
+        int32_t av[TM], bv[TN];
+        uint32_t ac[TM], bc[TN];
+        load_frag<TM>(Agv + kk * BM + ty * TM, av);
+        load_frag<TN>(Bgv + kk * BN + tx * TN, bv);
+        load_lo_frag<TM>(Agc + kk * BM + ty * TM, ac);
+        load_lo_frag<TN>(Bgc + kk * BN + tx * TN, bc);
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
           for (int j = 0; j < TN; ++j)
-            cnt_fma32(c0[i][j], c1[i][j], c2[i][j], a[i].v + bv[j].v, vmax[i][j], static_cast<uint32_t>(a[i].c),
-                      static_cast<uint32_t>(bv[j].c));
+            cnt_fma32(c0[i][j], c1[i][j], c2[i][j], av[i] + bv[j], vmax[i][j], ac[i], bc[j]);
       }
     } else {
       for (int kk = 0; kk < C::BKG; ++kk) {
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
-          const CntVal a = Ag[kk * BM + ty * TM + i];
+          const int32_t av = Agv[kk * BM + ty * TM + i];
+          const uint64_t ac = Agc[kk * BM + ty * TM + i];
 #pragma unroll
-          for (int j = 0; j < TN; ++j) {
-            const CntVal bb = Bg[kk * BN + tx * TN + j];
-            if (a.v + bb.v == vmax[i][j]) cnt_add64(c0[i][j], c1[i][j], c2[i][j], sat_mul_u64(a.c, bb.c));
-          }
+          for (int j = 0; j < TN; ++j)
+            if (av + Bgv[kk * BN + tx * TN + j] == vmax[i][j])
+              cnt_add64(c0[i][j], c1[i][j], c2[i][j], sat_mul_u64(ac, Bgc[kk * BN + tx * TN + j]));
         }
       }
     }
