@@ -115,7 +115,7 @@ __device__ __forceinline__ bool arrive_last(int32_t* ctr, int split, int* s_flag
 // register allocation under the kernel's 128-register bound.
 template <class SR, class Cfg, int FOLD>
 __device__ __noinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
-                                               unsigned char* smem, int* s_last) {
+                                               unsigned char* smem, int* s_last, bool prepared) {
   constexpr int BM = Cfg::BM, BN = Cfg::BN, TM = Cfg::TM, TN = Cfg::TN;
   using Acc = typename SR::Acc;
   auto& sm = *reinterpret_cast<TileSmem<SR, Cfg>*>(smem);
@@ -141,9 +141,9 @@ __device__ __noinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& s
 
   Acc acc[TM][TN];
   if constexpr (std::is_same<SR, SrCnt>::value)
-    tile_mainloop_counting<Cfg, true>(g, A, B, mp, b, tm, tn_, kbeg, kbeg + kspan, smem, acc);
+    tile_mainloop_counting<Cfg, true>(g, A, B, mp, b, tm, tn_, kbeg, kbeg + kspan, smem, acc, prepared);
   else
-    tile_mainloop<SR, Cfg, FOLD, true>(g, A, B, mp, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
+    tile_mainloop<SR, Cfg, FOLD, true>(g, A, B, mp, b, tm, tn_, kbeg, kbeg + kspan, sm, acc, prepared);
   tile_merge_groups<SR, Cfg>(acc, reinterpret_cast<Acc*>(smem), mp);
 
   const uint32_t m0 = static_cast<uint32_t>(tm) * BM, n0 = static_cast<uint32_t>(tn_) * BN;
@@ -227,11 +227,11 @@ __device__ __forceinline__ void naive_task_kh(const ExecStep& st, const ExecTask
 
 template <class SR>
 __device__ __noinline__ void exec_naive_task(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
-                                             unsigned char* smem, int* s_last) {
+                                             unsigned char* smem, int* s_last, bool prepared) {
   auto& sm = *reinterpret_cast<NaiveSmem<SR>*>(smem);
   int32_t kh0, kh1;
   naive_task_kh(st, task, &kh0, &kh1);
-  naive_tables<SR>(st.g, sm, kh0, kh1);
+  if (!prepared) naive_tables<SR>(st.g, sm, kh0, kh1);
   if (task.prime >= 0) {
     exec_naive_task_q<SR>(a, st, task, task.prime, smem, s_last);
   } else {
@@ -362,6 +362,39 @@ __device__ __forceinline__ void exec_final(const ExecArgs& a, const ExecStep& st
   *reinterpret_cast<uint32_t*>(raw + 96) = ld_relaxed_u32(a.status);
 }
 
+// Warps 1..7 build the index tables of the claimed task while warp 0 waits
+// for its dependencies (the tables depend on the step's geometry only), so
+// that work leaves the critical path.  Barrier 1 spans exactly these 224
+// threads; the tables are complete after the CTA-wide barrier that ends the
+// wait.
+__device__ __forceinline__ void bar_warps_1_7() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
+
+template <class Cfg>
+__device__ __forceinline__ void exec_prepare_tile(const ExecStep& st, const ExecTask& task, unsigned char* smem) {
+  const int64_t tile = task.local / st.split;
+  const int64_t per_b = int64_t(st.tiles_m) * st.tiles_n;
+  tile_tables<Cfg>(st.g, *reinterpret_cast<TileIdx<Cfg>*>(smem), tile / per_b, (tile % per_b) / st.tiles_n,
+                   tile % st.tiles_n, threadIdx.x - 32, kBlock - 32, bar_warps_1_7);
+}
+
+template <class SR>
+__device__ __noinline__ void exec_prepare(const ExecStep& st, const ExecTask& task, unsigned char* smem) {
+  if (task.kind == kTaskNaive) {
+    int32_t kh0, kh1;
+    naive_task_kh(st, task, &kh0, &kh1);
+    naive_prepare<SR>(st.g, *reinterpret_cast<NaiveSmem<SR>*>(smem), kh0, kh1, threadIdx.x - 32, kBlock - 32,
+                      bar_warps_1_7);
+    return;
+  }
+  switch (st.tile) {
+    case 0: exec_prepare_tile<TileC0>(st, task, smem); break;
+    case 1: exec_prepare_tile<TileC1>(st, task, smem); break;
+    case 2: exec_prepare_tile<TileC2>(st, task, smem); break;
+    case 3: exec_prepare_tile<TileC3>(st, task, smem); break;
+    default: exec_prepare_tile<TileC4>(st, task, smem); break;
+  }
+}
+
 template <class SR, int FOLD>
 __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ ExecArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -388,6 +421,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
     }
     __syncthreads();
     if (a.trace && tid == 0) t_loaded = global_ns();
+    const bool prepared = s_task.kind == kTaskNaive || s_task.kind == kTaskTile;
+    if (tid >= 32 && prepared) exec_prepare<SR>(s_step, s_task, smem);
     // wait for the steps this one depends on (warp 0, one dependency per lane)
     if (tid < 32) {
       const bool final_task = s_task.kind == kTaskFinal;
@@ -429,18 +464,18 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
     if (s_task.kind == kTaskFinal) {
       exec_final(a, s_step, s_task.local);
     } else if (s_task.kind == kTaskNaive) {
-      exec_naive_task<SR>(a, s_step, s_task, smem, &s_last);
+      exec_naive_task<SR>(a, s_step, s_task, smem, &s_last, prepared);
     } else if (s_task.kind == kTaskGroup) {
       exec_group_task<SR>(a, s_task, &s_step, smem);
     } else {
       switch (s_step.tile) {
         case 0:
-          if constexpr (ExecTile<SR>::kBig) exec_tile_task<SR, TileC0, FOLD>(a, s_step, s_task, smem, &s_last);
+          if constexpr (ExecTile<SR>::kBig) exec_tile_task<SR, TileC0, FOLD>(a, s_step, s_task, smem, &s_last, prepared);
           break;
-        case 1: exec_tile_task<SR, TileC1, FOLD>(a, s_step, s_task, smem, &s_last); break;
-        case 2: exec_tile_task<SR, TileC2, FOLD>(a, s_step, s_task, smem, &s_last); break;
-        case 3: exec_tile_task<SR, TileC3, FOLD>(a, s_step, s_task, smem, &s_last); break;
-        default: exec_tile_task<SR, TileC4, FOLD>(a, s_step, s_task, smem, &s_last); break;
+        case 1: exec_tile_task<SR, TileC1, FOLD>(a, s_step, s_task, smem, &s_last, prepared); break;
+        case 2: exec_tile_task<SR, TileC2, FOLD>(a, s_step, s_task, smem, &s_last, prepared); break;
+        case 3: exec_tile_task<SR, TileC3, FOLD>(a, s_step, s_task, smem, &s_last, prepared); break;
+        default: exec_tile_task<SR, TileC4, FOLD>(a, s_step, s_task, smem, &s_last, prepared); break;
       }
     }
     __syncthreads();

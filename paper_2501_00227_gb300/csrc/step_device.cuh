@@ -51,9 +51,11 @@ struct GatherTabs {
   uint2 k[kNib][16];
 };
 
-// Fills the gather tables of step g (one entry per thread; no barrier).
-__device__ __forceinline__ void gather_build(const StepGeom& g, GatherTabs& t) {
-  for (int e = threadIdx.x; e < 2 * kNib * 16; e += kBlock) {
+// Fills the gather tables of step g: threads first, first + stride, ... of
+// the CTA compute one entry each (no barrier).
+__device__ __forceinline__ void gather_build(const StepGeom& g, GatherTabs& t, int first = threadIdx.x,
+                                             int stride = kBlock) {
+  for (int e = first; e < 2 * kNib * 16; e += stride) {
     const int field = e >> 7, i = (e >> 4) & (kNib - 1), v = e & 15;
     uint32_t oa = 0, ob = 0;
 #pragma unroll
@@ -120,19 +122,28 @@ __device__ __forceinline__ CntVal shfl_xor_val(CntVal v, int off) {
   return r;
 }
 
-// Fills the tables of a step for the high-k blocks [kh_begin, kh_end) (all
-// threads of the CTA; ends with a barrier).
+// Fills the tables of a step for the high-k blocks [kh_begin, kh_end) with
+// threads first, first + stride, ...; sync() is a barrier over exactly those
+// threads.  The tables are complete for the CTA after the next CTA-wide
+// barrier.
+template <class SR, class Sync>
+__device__ __forceinline__ void naive_prepare(const StepGeom& g, NaiveSmem<SR>& sm, int32_t kh_begin,
+                                              int32_t kh_end, int first, int stride, Sync sync) {
+  gather_build(g, sm.gt, first, stride);
+  sync();
+  const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
+  const int nkn = nibbles(g.nk);
+  for (int i = first; i < (1 << kl); i += stride) sm.klo[i] = gather(sm.gt.k, nkn, static_cast<uint32_t>(i));
+  if (kh_end - kh_begin <= kNaiveKHi)
+    for (int i = first; i < kh_end - kh_begin; i += stride)
+      sm.khi[i] = gather(sm.gt.k, nkn, static_cast<uint32_t>(kh_begin + i) << kl);
+}
+
+// The same with every thread of the CTA (ends with a barrier).
 template <class SR>
 __device__ __forceinline__ void naive_tables(const StepGeom& g, NaiveSmem<SR>& sm, int32_t kh_begin,
                                              int32_t kh_end) {
-  gather_build(g, sm.gt);
-  __syncthreads();
-  const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
-  const int nkn = nibbles(g.nk);
-  for (int i = threadIdx.x; i < (1 << kl); i += kBlock) sm.klo[i] = gather(sm.gt.k, nkn, static_cast<uint32_t>(i));
-  if (kh_end - kh_begin <= kNaiveKHi)
-    for (int i = threadIdx.x; i < kh_end - kh_begin; i += kBlock)
-      sm.khi[i] = gather(sm.gt.k, nkn, static_cast<uint32_t>(kh_begin + i) << kl);
+  naive_prepare<SR>(g, sm, kh_begin, kh_end, threadIdx.x, kBlock, [] { __syncthreads(); });
   __syncthreads();
 }
 

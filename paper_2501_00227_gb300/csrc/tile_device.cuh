@@ -96,29 +96,40 @@ struct TileSmem {
   alignas(16) typename SR::Val Bs[Stages<SR>::v][C::BK * C::BN];
 };
 
-// Staging offsets of tile (tm, tn_) of batch b for this thread (element
-// e = tid + 256 j of a chunk: A as [k][m], B as [k][n]), -1 for padding
-// outside M, N or K.  All threads must call it (it has barriers).
-template <class C>
-__device__ __forceinline__ void tile_offsets(const StepGeom& g, TileIdx<C>& ix, int64_t b, int64_t tm,
-                                             int64_t tn_, int32_t (&offA)[C::EA], int32_t (&offB)[C::EB]) {
+// Index tables of tile (tm, tn_) of batch b: gather tables and the offsets
+// of the tile's rows, columns and chunk rows, computed by threads first,
+// first + stride, ...; sync() is a barrier over exactly those threads.  The
+// tables are complete for the CTA after the next CTA-wide barrier.
+template <class C, class Sync>
+__device__ __forceinline__ void tile_tables(const StepGeom& g, TileIdx<C>& ix, int64_t b, int64_t tm, int64_t tn_,
+                                            int first, int stride, Sync sync) {
   constexpr int BM = C::BM, BN = C::BN, BK = C::BK;
-  const int tid = threadIdx.x;
   const uint32_t M = 1u << g.nm, N = 1u << g.nn, K = 1u << g.nk;
   const uint32_t m0 = static_cast<uint32_t>(tm) * BM, n0 = static_cast<uint32_t>(tn_) * BN;
   const int ncn = nibbles(g.rc), nkn = nibbles(g.nk);
-  gather_build(g, ix.gt);
-  __syncthreads();
+  gather_build(g, ix.gt, first, stride);
+  sync();
   const uint32_t cb = static_cast<uint32_t>(b) << (g.nn + g.nm);
-  for (int i = tid; i < BM; i += kBlock)
+  for (int i = first; i < BM; i += stride)
     ix.offAm[i] = m0 + i < M ? gather(ix.gt.c, ncn, cb | ((m0 + i) << g.nn)).x : 0u;
-  for (int i = tid; i < BN; i += kBlock) ix.offBn[i] = n0 + i < N ? gather(ix.gt.c, ncn, cb | (n0 + i)).y : 0u;
-  for (int i = tid; i < BK; i += kBlock) {
+  for (int i = first; i < BN; i += stride) ix.offBn[i] = n0 + i < N ? gather(ix.gt.c, ncn, cb | (n0 + i)).y : 0u;
+  for (int i = first; i < BK; i += stride) {
     const uint2 o = gather(ix.gt.k, nkn, static_cast<uint32_t>(i) < K ? static_cast<uint32_t>(i) : 0u);
     ix.offAk[i] = o.x;
     ix.offBk[i] = o.y;
   }
-  __syncthreads();
+}
+
+// This thread's staging offsets (element e = tid + 256 j of a chunk: A as
+// [k][m], B as [k][n]) from complete index tables, -1 for padding outside M,
+// N or K.
+template <class C>
+__device__ __forceinline__ void tile_slots(const StepGeom& g, const TileIdx<C>& ix, int64_t tm, int64_t tn_,
+                                           int32_t (&offA)[C::EA], int32_t (&offB)[C::EB]) {
+  constexpr int BM = C::BM, BN = C::BN, BK = C::BK;
+  const int tid = threadIdx.x;
+  const uint32_t M = 1u << g.nm, N = 1u << g.nn, K = 1u << g.nk;
+  const uint32_t m0 = static_cast<uint32_t>(tm) * BM, n0 = static_cast<uint32_t>(tn_) * BN;
   const uint32_t kvalid = K < BK ? K : BK;  // k rows that exist inside a chunk
 #pragma unroll
   for (int j = 0; j < C::EA; ++j) {
@@ -132,6 +143,20 @@ __device__ __forceinline__ void tile_offsets(const StepGeom& g, TileIdx<C>& ix, 
     const bool ok = (n0 + nn < N) && (static_cast<uint32_t>(kk) < kvalid);
     offB[j] = ok ? static_cast<int32_t>(ix.offBn[nn] + ix.offBk[kk]) : -1;
   }
+}
+
+// Staging offsets of tile (tm, tn_) of batch b for this thread; builds the
+// index tables first unless `ready`.  All threads must call it (it has
+// barriers).
+template <class C>
+__device__ __forceinline__ void tile_offsets(const StepGeom& g, TileIdx<C>& ix, int64_t b, int64_t tm,
+                                             int64_t tn_, int32_t (&offA)[C::EA], int32_t (&offB)[C::EB],
+                                             bool ready = false) {
+  if (!ready) {
+    tile_tables<C>(g, ix, b, tm, tn_, threadIdx.x, kBlock, [] { __syncthreads(); });
+    __syncthreads();
+  }
+  tile_slots<C>(g, ix, tm, tn_, offA, offB);
 }
 
 // Offsets (in A, in B) of the chunk of k rows starting at k0 (a multiple of
@@ -178,7 +203,7 @@ template <class SR, class C, int FOLD, bool CG>
 __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& A, const Operand& B,
                                               const ModParams& mp, int64_t b, int64_t tm, int64_t tn_,
                                               int64_t kbeg, int64_t kend, TileSmem<SR, C>& sm,
-                                              typename SR::Acc (&acc)[C::TM][C::TN]) {
+                                              typename SR::Acc (&acc)[C::TM][C::TN], bool ready = false) {
   using Val = typename SR::Val;
   using T = Tiled<SR>;
   constexpr int kStages = Stages<SR>::v;
@@ -188,7 +213,7 @@ __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& 
   const int tx = gt % C::WN, ty = gt / C::WN;
 
   int32_t offA[C::EA], offB[C::EB];
-  tile_offsets<C>(g, sm.idx, b, tm, tn_, offA, offB);
+  tile_offsets<C>(g, sm.idx, b, tm, tn_, offA, offB, ready);
 
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -395,13 +420,13 @@ template <class C, bool CG>
 __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const Operand& A, const Operand& B,
                                                        const ModParams& mp, int64_t b, int64_t tm, int64_t tn_,
                                                        int64_t kbeg, int64_t kend, unsigned char* smem_raw,
-                                                       CntVal (&acc)[C::TM][C::TN]) {
+                                                       CntVal (&acc)[C::TM][C::TN], bool ready = false) {
   constexpr int BM = C::BM, BN = C::BN, BK = C::BK, TM = C::TM, TN = C::TN;
   constexpr int kSt = Stages<SrCnt>::v;
   // pass 1: maxima of the values
   int32_t vmax[TM][TN];
   tile_mainloop<SrI32, C, 1, CG>(g, A, B, mp, b, tm, tn_, kbeg, kend,
-                                 *reinterpret_cast<TileSmem<SrI32, C>*>(smem_raw), vmax);
+                                 *reinterpret_cast<TileSmem<SrI32, C>*>(smem_raw), vmax, ready);
   // pass 2: counts of the maximising terms (same index tables, same offsets);
   // values and counts are staged in separate arrays, so every fragment is a
   // run of 16-byte shared loads
@@ -410,7 +435,7 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
   const int grp = tid / C::GT, gt = tid % C::GT;
   const int tx = gt % C::WN, ty = gt / C::WN;
   int32_t offA[C::EA], offB[C::EB];
-  tile_offsets<C>(g, sm.idx, b, tm, tn_, offA, offB);
+  tile_offsets<C>(g, sm.idx, b, tm, tn_, offA, offB, true);  // tables of pass 1
 #pragma unroll
   for (int j = 0; j < C::EA; ++j)
     if (offA[j] < 0)
