@@ -225,6 +225,65 @@ __device__ __forceinline__ void naive_task_kh(const ExecStep& st, const ExecTask
   *kh1 = *kh0 + nkhi / st.ks;
 }
 
+// Outputs [c0, c1) of a mod-p general step for primes q0 .. q0+NP-1 in one
+// pass: every term's residues of all NP primes are loaded together.  The
+// step's tables must be in shared memory (they do not depend on the prime).
+template <int NP>
+__device__ __forceinline__ void exec_naive_mp(const ExecArgs& a, const ExecStep& st, int32_t c0, int32_t c1,
+                                              int32_t kh0, int32_t kh1, bool whole, int q0, unsigned char* smem) {
+  using SRN = SrModN<NP>;
+  auto& sm = *reinterpret_cast<NaiveSmem<SRN>*>(smem);
+  const StepGeom& g = st.g;
+  ModParamsN<NP> mp;
+  const uint32_t* pa[NP];
+  const uint32_t* pb[NP];
+  uint32_t* pc[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    mp.q[q] = a.mods.q[q0 + q];
+    const int64_t off = int64_t(q0 + q) * a.prime_stride;
+    pa[q] = reinterpret_cast<const uint32_t*>(a.r0 + 4 * st.a_off) + off;
+    pb[q] = reinterpret_cast<const uint32_t*>(a.r0 + 4 * st.b_off) + off;
+    pc[q] = reinterpret_cast<uint32_t*>(a.r0 + 4 * st.c_off) + off;
+  }
+  auto la = [&](uint32_t e) {
+    if (g.a_kind != kOpArena) return SRN::leaf(g.a_kind, e);
+    ModValN<NP> v;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) v.v[q] = __ldcg(pa[q] + e);
+    return v;
+  };
+  auto lb = [&](uint32_t e) {
+    if (g.b_kind != kOpArena) return SRN::leaf(g.b_kind, e);
+    ModValN<NP> v;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) v.v[q] = __ldcg(pb[q] + e);
+    return v;
+  };
+  auto sink = [&](uint32_t c, const ModAccN<NP>& v) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) pc[q][c] = barrett64(v.a[q], mp.q[q]);
+  };
+  if (!whole && st.R == 1 && (c1 - c0) % (kNaiveWideU * kBlock) == 0 && st.chunk % (kNaiveWideU * kBlock) == 0)
+    naive_chunk_wide<SRN, kNaiveWideU>(g, la, lb, sink, mp, c0, c1, sm);
+  else
+    naive_chunk<SRN>(g, la, lb, sink, mp, c0, c1, kh0, kh1, st.R, sm);
+}
+
+// Every prime of a mod-p general step (k not split), in groups of up to 4.
+__device__ __forceinline__ void exec_naive_all_primes(const ExecArgs& a, const ExecStep& st, int32_t c0,
+                                                      int32_t c1, int32_t kh0, int32_t kh1, bool whole,
+                                                      unsigned char* smem) {
+  for (int q0 = 0; q0 < a.nprimes; q0 += 4) {
+    switch (a.nprimes - q0 < 4 ? a.nprimes - q0 : 4) {
+      case 1: exec_naive_mp<1>(a, st, c0, c1, kh0, kh1, whole, q0, smem); break;
+      case 2: exec_naive_mp<2>(a, st, c0, c1, kh0, kh1, whole, q0, smem); break;
+      case 3: exec_naive_mp<3>(a, st, c0, c1, kh0, kh1, whole, q0, smem); break;
+      default: exec_naive_mp<4>(a, st, c0, c1, kh0, kh1, whole, q0, smem); break;
+    }
+  }
+}
+
 template <class SR>
 __device__ __noinline__ void exec_naive_task(const ExecArgs& a, const ExecStep& st, const ExecTask& task,
                                              unsigned char* smem, int* s_last, bool prepared) {
@@ -232,6 +291,14 @@ __device__ __noinline__ void exec_naive_task(const ExecArgs& a, const ExecStep& 
   int32_t kh0, kh1;
   naive_task_kh(st, task, &kh0, &kh1);
   if (!prepared) naive_tables<SR>(st.g, sm, kh0, kh1);
+  if constexpr (std::is_same<SR, SrMod>::value) {
+    if (task.prime < 0) {  // k is not split: all primes in one pass
+      const int32_t E = 1 << st.g.rc, chunk = static_cast<int32_t>(st.chunk);
+      const int32_t c0 = task.local * chunk, c1 = c0 + chunk < E ? c0 + chunk : E;
+      exec_naive_all_primes(a, st, c0, c1, kh0, kh1, false, smem);
+      return;
+    }
+  }
   if (task.prime >= 0) {
     exec_naive_task_q<SR>(a, st, task, task.prime, smem, s_last);
   } else {
@@ -335,6 +402,12 @@ __device__ __noinline__ void exec_group_task(const ExecArgs& a, const ExecTask& 
     __syncthreads();
     if (task.prime >= 0) {
       exec_naive_whole<SR>(a, *s_step, task.prime, smem);
+    } else if constexpr (std::is_same<SR, SrMod>::value) {
+      const StepGeom& g = s_step->g;
+      const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
+      const int32_t nkhi = 1 << (g.nk - kl);
+      naive_tables<SR>(g, *reinterpret_cast<NaiveSmem<SR>*>(smem), 0, nkhi);
+      exec_naive_all_primes(a, *s_step, 0, 1 << g.rc, 0, nkhi, true, smem);
     } else {
       for (int q = 0; q < a.nprimes; ++q) {
         __syncthreads();
@@ -504,7 +577,8 @@ template <class SR, int FOLD>
 static size_t smem_for() {
   size_t t = tile_smem_bytes<SR, TileC1>();
   const size_t cands[] = {ExecTile<SR>::kBig ? tile_smem_bytes<SR, TileC0>() : 0, tile_smem_bytes<SR, TileC2>(),
-                          tile_smem_bytes<SR, TileC3>(), tile_smem_bytes<SR, TileC4>(), sizeof(NaiveSmem<SR>)};
+                          tile_smem_bytes<SR, TileC3>(), tile_smem_bytes<SR, TileC4>(), sizeof(NaiveSmem<SR>),
+                          std::is_same<SR, SrMod>::value ? sizeof(NaiveSmem<SrModN<4>>) : 0};
   for (size_t c : cands) t = c > t ? c : t;
   return t;
 }

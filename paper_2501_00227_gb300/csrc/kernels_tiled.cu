@@ -187,13 +187,14 @@ int launch_step_tiled(tn_semiring_t s, const StepGeom& g, const Operand& A, cons
   return TN_EINVAL;
 }
 
-// Heuristic kernel choice (the "step kernels" table of the design notes).
-// The tiled GEMM needs some reduction depth (K >= 8), an M x N extent that
-// fills at least a 16 x 64 tile, a batch that fits gridDim.y and enough work.
-// Among the tile shapes the one maximising (tile efficiency) x (useful
-// fraction of the tile) x (fraction of ~2 CTAs per SM it can occupy with
-// split-K) wins; split-K then doubles until two CTAs per SM have work, while
-// every split keeps at least 4 chunks of its k range.
+// Heuristic kernel choice.  The tiled GEMM needs some reduction depth
+// (K >= 8), an M x N extent that fills at least a 16 x 64 tile, a batch that
+// fits gridDim.y and enough work.  Among tile shapes t and split-K factors s
+// the choice minimises an estimate of the step's time on 2 CTAs x 152 SMs:
+//   waves(tasks) x (kTaskFixed + padded work per task / tile efficiency),
+// where waves = ceil(tasks / 304) and kTaskFixed is the fixed cost of one
+// task (claim, tables, pipeline fill, epilogue, publication) expressed in
+// multiply-adds of the semiring.  Every split keeps at least one k chunk.
 // TN_KERNEL=naive|tiled in the environment forces one path (tests).
 void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, int* tile, int* split) {
   const char* force = getenv("TN_KERNEL");
@@ -208,23 +209,26 @@ void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, i
   const bool tropical = (s == TN_TROPICAL_F32 || s == TN_TROPICAL_I32);
   const int64_t M = int64_t(1) << g.nm, N = int64_t(1) << g.nn, K = int64_t(1) << g.nk;
   const int64_t batch = (int64_t(1) << g.nb) * (s == TN_COUNT_MODP ? nprimes : 1);
-  constexpr int64_t kFull = 2 * 152;
-  float best = -1.0f;
+  constexpr double kSlots = 2 * 152;
+  // fixed cost of a task in multiply-adds: ~5 us at the per-CTA rate of each
+  // semiring's tile (tropical ~20, mod p ~10, counting ~5 Gop/s per CTA)
+  const double kTaskFixed = tropical ? 100e3 : (s == TN_COUNT_MODP ? 50e3 : 25e3);
+  double best = -1.0;
   int best_tile = 1, best_split = 1;
   for (int t = 0; t < kNumTiles; ++t) {
     if (t == 0 && !tropical) continue;
     const int64_t bm = kTileBM[t], bn = kTileBN[t], bk = kTileBK[t];
-    const int64_t tmn = (M + bm - 1) / bm, tnn = (N + bn - 1) / bn;
-    const float util = float(M) / float(tmn * bm) * float(N) / float(tnn * bn);
-    const int64_t tiles = tmn * tnn * batch;
-    int sp = 1;
-    while (tiles * sp < kFull && sp < 16 && K / (2 * sp) >= 4 * bk) sp *= 2;
-    const float par = tiles * sp >= kFull ? 1.0f : float(tiles * sp) / float(kFull);
-    const float score = kTileEff[t] * util * par;
-    if (score > best) {
-      best = score;
-      best_tile = t;
-      best_split = sp;
+    const int64_t tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn) * batch;
+    for (int sp = 1; sp <= 16 && K / sp >= bk; sp *= 2) {
+      const double tasks = double(tiles) * sp;
+      const double waves = static_cast<double>(static_cast<int64_t>((tasks + kSlots - 1) / kSlots));
+      const double work = double(bm) * double(bn) * double(K / sp) / kTileEff[t];
+      const double est = waves * (kTaskFixed + work);
+      if (best < 0 || est < best) {
+        best = est;
+        best_tile = t;
+        best_split = sp;
+      }
     }
   }
   *tile = best_tile;

@@ -122,6 +122,57 @@ __device__ __forceinline__ CntVal shfl_xor_val(CntVal v, int off) {
   return r;
 }
 
+// Several primes at once: the (+,*) ring modulo NP primes as one element
+// type, so that a general step reads the residues of every prime of a term
+// together (one round of loads instead of one per prime).
+template <int NP>
+struct ModParamsN {
+  ModParams q[NP];
+};
+
+template <int NP>
+struct ModValN {
+  uint32_t v[NP];
+};
+template <int NP>
+struct ModAccN {
+  uint64_t a[NP];
+};
+
+template <int NP>
+struct SrModN {
+  using Val = ModValN<NP>;
+  using Acc = ModAccN<NP>;
+  static __device__ __forceinline__ Acc zero(const ModParamsN<NP>&) {
+    Acc r;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r.a[q] = 0ull;
+    return r;
+  }
+  static __device__ __forceinline__ Val leaf(int32_t kind, uint32_t e) {
+    Val r;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r.v[q] = SrMod::leaf(kind, e);
+    return r;
+  }
+  static __device__ __forceinline__ void mac(Acc& acc, const Val& a, const Val& b, const ModParamsN<NP>& mp) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) SrMod::mac(acc.a[q], a.v[q], b.v[q], mp.q[q]);
+  }
+  static __device__ __forceinline__ void merge(Acc& acc, const Acc& o, const ModParamsN<NP>& mp) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) SrMod::merge(acc.a[q], o.a[q], mp.q[q]);
+  }
+};
+
+template <int NP>
+__device__ __forceinline__ ModAccN<NP> shfl_xor_val(ModAccN<NP> v, int off) {
+  ModAccN<NP> r;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) r.a[q] = __shfl_xor_sync(0xffffffffu, v.a[q], off);
+  return r;
+}
+
 // Fills the tables of a step for the high-k blocks [kh_begin, kh_end) with
 // threads first, first + stride, ...; sync() is a barrier over exactly those
 // threads.  The tables are complete for the CTA after the next CTA-wide
@@ -159,9 +210,9 @@ __device__ __forceinline__ void naive_tables(const StepGeom& g, NaiveSmem<SR>& s
 // memory.  The merged value of entry c goes to sink(c, acc) (called by one
 // thread).  Every thread of the CTA must call this (it uses barriers when
 // R > 32).
-template <class SR, class LoadA, class LoadB, class Sink>
+template <class SR, class LoadA, class LoadB, class Sink, class MP>
 __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, LoadB loadB, Sink sink,
-                                            const ModParams& mp, int32_t c_begin, int32_t c_end,
+                                            const MP& mp, int32_t c_begin, int32_t c_end,
                                             int32_t kh_begin, int32_t kh_end, int R, NaiveSmem<SR>& sm) {
   using Acc = typename SR::Acc;
   using Val = typename SR::Val;
@@ -225,9 +276,9 @@ __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, Load
 // once (entries cb + tid + 256 u), so U independent loads per operand are in
 // flight (2U with the unrolled k loop).  Used for wide steps with short
 // reductions; covers the whole k range (naive_tables over all high-k blocks).
-template <class SR, int U, class LoadA, class LoadB, class Sink>
+template <class SR, int U, class LoadA, class LoadB, class Sink, class MP>
 __device__ __forceinline__ void naive_chunk_wide(const StepGeom& g, LoadA loadA, LoadB loadB, Sink sink,
-                                                 const ModParams& mp, int32_t c_begin, int32_t c_end,
+                                                 const MP& mp, int32_t c_begin, int32_t c_end,
                                                  NaiveSmem<SR>& sm) {
   using Acc = typename SR::Acc;
   const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
