@@ -9,6 +9,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <type_traits>
 
@@ -213,6 +214,8 @@ void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, i
   // fixed cost of a task in multiply-adds: ~5 us at the per-CTA rate of each
   // semiring's tile (tropical ~20, mod p ~10, counting ~5 Gop/s per CTA)
   const double kTaskFixed = tropical ? 100e3 : (s == TN_COUNT_MODP ? 50e3 : 25e3);
+  const double acc_bytes = tropical ? 4.0 : (s == TN_COUNT_MODP ? 8.0 : 16.0);
+  const double out_bytes = double(M) * double(N) * double(batch) * acc_bytes;
   double best = -1.0;
   int best_tile = 1, best_split = 1;
   for (int t = 0; t < kNumTiles; ++t) {
@@ -220,6 +223,10 @@ void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, i
     const int64_t bm = kTileBM[t], bn = kTileBN[t], bk = kTileBK[t];
     const int64_t tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn) * batch;
     for (int sp = 1; sp <= 16 && K / sp >= bk; sp *= 2) {
+      // split-K scratch (one partial tile per task) at most max(4 x the
+      // step's output, 1 MiB), so splitting never dominates the workspace
+      const double scratch = sp > 1 ? double(tiles) * sp * bm * bn * acc_bytes : 0.0;
+      if (scratch > std::max(4.0 * out_bytes, double(1 << 20))) break;
       const double tasks = double(tiles) * sp;
       const double waves = static_cast<double>(static_cast<int64_t>((tasks + kSlots - 1) / kSlots));
       const double work = double(bm) * double(bn) * double(K / sp) / kTileEff[t];
