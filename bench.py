@@ -230,6 +230,42 @@ def batching_bench(tn, torch, count: int = 4096):
     return out
 
 
+def largest_bench(tn, torch, peak_tops: float):
+    """The largest tropical contractions of the configs: King's subgraph 20 x 20
+    at filling 0.8 (seeds 1-3, ~320 vertices, tc ~ 2^31), tropical int32, one
+    executor launch each, L2 flushed before each launch; Tops/s and fraction of
+    the int32 (max,+) issue peak."""
+    out = {"workload": "King's subgraph 20x20 p=0.8 seeds 1-3, tropical int32, greedy (nrepeat 10)"}
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    rows = []
+    for seed in (1, 2, 3):
+        p = tn.Plan(*graphgen.kings_subgraph(20, 0.8, seed), nrepeat=10, seed=1)
+        ws = torch.empty(p.workspace_bytes("tropical_i32"), dtype=torch.uint8, device="cuda")
+        raw = torch.zeros(tn.TN_RAW_BYTES, dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            tn.tn_contract_async(p.handle, "tropical_i32", None, ws.data_ptr(), ws.numel(), stream.cuda_stream,
+                                 raw.data_ptr())
+        ms = []
+        for _ in range(5):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tn.tn_contract_async(p.handle, "tropical_i32", None, ws.data_ptr(), ws.numel(), stream.cuda_stream,
+                                 raw.data_ptr())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        tc = p.info("tropical_i32")["tc"]
+        tops = tc / (statistics.median(ms) * 1e-3) / 1e12
+        rows.append({"seed": seed, "log2_tc": float(np.log2(tc)), "ms": statistics.median(ms), "tops": tops,
+                     "frac": tops / peak_tops})
+        p.close()
+    out["instances"] = rows
+    out["best_frac"] = max(r["frac"] for r in rows)
+    return out
+
+
 def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120):
     """Poisson request stream mixing random 3-regular graphs (n even in
     [40,160]) and King's subgraphs (L in [8,16], filling 0.8), each asking the
@@ -439,6 +475,8 @@ def run_tn(args):
             "gpu_launches": None, "roofline": roofline, "clocks": csum}
     # one executor launch per contraction
     line["gpu_launches"] = args.steps * len(jobs)
+    if rank == 0:
+        line["largest_tropical"] = largest_bench(tn, torch, peak_ops)
     if rank == 0 and not args.no_batching:
         line["batching"] = batching_bench(tn, torch)
     if rank == 0 and not args.no_serving:

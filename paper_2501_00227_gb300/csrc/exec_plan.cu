@@ -43,8 +43,9 @@ namespace {
 // (write-after-read), so the releasers become dependencies.
 class LevelArena {
  public:
+  explicit LevelArena(int64_t align = kArenaAlign) : align_(align) {}
   int64_t alloc(int64_t size, std::vector<int32_t>* war) {
-    size = static_cast<int64_t>(align_up(static_cast<size_t>(size), kArenaAlign));
+    size = static_cast<int64_t>(align_up(static_cast<size_t>(size), static_cast<size_t>(align_)));
     for (auto it = free_.begin(); it != free_.end(); ++it) {
       if (it->second.len >= size) {
         int64_t off = it->first;
@@ -60,7 +61,7 @@ class LevelArena {
     return off;
   }
   void release(int64_t off, int64_t size, int32_t releaser) {
-    size = static_cast<int64_t>(align_up(static_cast<size_t>(size), kArenaAlign));
+    size = static_cast<int64_t>(align_up(static_cast<size_t>(size), static_cast<size_t>(align_)));
     auto it = free_.emplace(off, Block{size, {releaser}}).first;
     auto next = std::next(it);
     if (next != free_.end() && it->first + it->second.len == next->first) {
@@ -90,6 +91,7 @@ class LevelArena {
   }
   std::map<int64_t, Block> free_;
   int64_t top_ = 0;
+  int64_t align_;
 };
 
 int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X) {
@@ -154,9 +156,40 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   // levels; the releasing steps become (write-after-read) dependencies.
   // Inputs consumed inside a group are released when the group's root level
   // is reached, by the root.
+  // launch shape of every step, and the split-K scratch it needs (bytes)
+  const size_t acc_bytes = exec_acc_bytes(s);
+  struct Launch {
+    int kernel, tile, split;
+    dev::NaiveShape sh;
+    size_t scratch;
+  };
+  std::vector<Launch> ln(ns);
+  for (int st = 0; st < ns; ++st) {
+    Launch& L = ln[st];
+    const StepGeom& g = p->steps[st].g;
+    dev::pick_launch(g, s, np, &L.kernel, &L.tile, &L.split);
+    L.scratch = 0;
+    if (groot[st] >= 0) {
+      L.kernel = kKernNaive;
+      L.sh = dev::naive_shape(g.rc, g.nk, false);
+    } else if (L.kernel == kKernTiled && g.c_identity) {
+      const int64_t bm = dev::tiled_tile_bm(L.tile), bn = dev::tiled_tile_bn(L.tile);
+      const int64_t ntiles = ((int64_t(1) << g.nm) + bm - 1) / bm * (((int64_t(1) << g.nn) + bn - 1) / bn) << g.nb;
+      if (L.split > 1) L.scratch = static_cast<size_t>(ntiles * np * L.split * bm * bn) * acc_bytes;
+    } else {
+      L.kernel = kKernNaive;
+      L.sh = dev::naive_shape(g.rc, g.nk, true);
+      if (L.sh.ks > 1) L.scratch = static_cast<size_t>(L.sh.nchunks * np * L.sh.ks * L.sh.chunk) * acc_bytes;
+    }
+  }
+
   std::vector<std::vector<int32_t>> dep(ns);  // in plan-step indices
   std::vector<int64_t> c_off(ns, 0);
   LevelArena arena;
+  // split-K scratch, in 256-byte blocks: a step's scratch is free again once
+  // the step has completed, so later steps may reuse it (with a dependency)
+  LevelArena sarena(1);
+  std::vector<int64_t> s_off(ns, 0);
   for (int i = 0; i < ns;) {
     int j = i;
     while (j < ns && level[order[j]] == level[order[i]]) ++j;
@@ -167,6 +200,11 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
       std::vector<int32_t> war;
       c_off[st] = arena.alloc(int64_t(1) << S.g.rc, &war);
       dep[st] = war;
+      if (ln[st].scratch) {
+        war.clear();
+        s_off[st] = sarena.alloc(static_cast<int64_t>((ln[st].scratch + 255) / 256), &war);
+        dep[st].insert(dep[st].end(), war.begin(), war.end());
+      }
     }
     for (int x = i; x < j; ++x) {
       const int st = order[x];
@@ -181,6 +219,11 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
           arena.release(c_off[pr], int64_t(1) << p->steps[pr].g.rc, st);
         }
       }
+    }
+    for (int x = i; x < j; ++x) {
+      const int st = order[x];
+      if (!internal(st) && ln[st].scratch)
+        sarena.release(s_off[st], static_cast<int64_t>((ln[st].scratch + 255) / 256), st);
     }
     i = j;
   }
@@ -222,13 +265,12 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   }
 
   // steps, tasks, split-K scratch and arrival counters
-  const size_t acc_bytes = exec_acc_bytes(s);
   X->steps.assign(ns, ExecStep());
   X->deps.clear();
   X->tasks.clear();
   X->group_begin.clear();
   X->group_members.clear();
-  size_t scratch = 0;
+  const size_t scratch = static_cast<size_t>(sarena.top()) * 256;
   int32_t arrive = 0;
   for (int x = 0; x < ns; ++x) {
     const int st = order[x];
@@ -276,8 +318,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
       if (split > 1) {
         E.arrive_off = arrive;
         arrive += static_cast<int32_t>(ntiles * np);
-        E.scratch_off = static_cast<int64_t>(scratch);
-        scratch += align_up(static_cast<size_t>(ntiles * np * split * bm * bn) * acc_bytes, 256);
+        E.scratch_off = s_off[st] * 256;
       }
     } else {
       const dev::NaiveShape sh = dev::naive_shape(S.g.rc, S.g.nk, true);
@@ -290,10 +331,10 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
       if (sh.ks > 1) {
         E.arrive_off = arrive;
         arrive += static_cast<int32_t>(sh.nchunks * np);
-        E.scratch_off = static_cast<int64_t>(scratch);
-        scratch += align_up(static_cast<size_t>(sh.nchunks * np * sh.ks * sh.chunk) * acc_bytes, 256);
+        E.scratch_off = s_off[st] * 256;
       }
     }
+    if ((E.split > 1 || E.ks > 1) != (ln[st].scratch > 0)) return TN_EINVAL;  // launch shapes disagree
     if (groot[st] < 0) {
       if (E.kernel == kKernNaive && E.ks == 1 && np > 1) {
         // a general step without k split does every prime inside each task
@@ -336,6 +377,20 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
         if (internal(sx) || internal(sy)) return TN_EINVAL;  // internal tensors are never shared
         const int cons = p->tensors[p->steps[sx].c_id].consumer;
         if (cons < 0 || !is_anc(pos[owner(cons)], y)) return TN_EINVAL;
+      }
+    }
+    // split-K scratch: a later step may only overlap the scratch of a step it
+    // (transitively) depends on
+    for (int y = 0; y < ns; ++y) {
+      const int sy = order[y];
+      if (!ln[sy].scratch || internal(sy)) continue;
+      const int64_t y0 = s_off[sy] * 256, y1 = y0 + static_cast<int64_t>(ln[sy].scratch);
+      for (int x = 0; x < y; ++x) {
+        const int sx = order[x];
+        if (!ln[sx].scratch || internal(sx)) continue;
+        const int64_t x0 = s_off[sx] * 256, x1 = x0 + static_cast<int64_t>(ln[sx].scratch);
+        if (x1 <= y0 || y1 <= x0) continue;
+        if (!is_anc(x, y)) return TN_EINVAL;
       }
     }
   }

@@ -223,10 +223,10 @@ void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, i
     const int64_t bm = kTileBM[t], bn = kTileBN[t], bk = kTileBK[t];
     const int64_t tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn) * batch;
     for (int sp = 1; sp <= 16 && K / sp >= bk; sp *= 2) {
-      // split-K scratch (one partial tile per task) at most max(4 x the
-      // step's output, 1 MiB), so splitting never dominates the workspace
+      // split-K scratch (one partial tile per task; reused by later steps)
+      // at most max(2 x the step's output, 4 MiB)
       const double scratch = sp > 1 ? double(tiles) * sp * bm * bn * acc_bytes : 0.0;
-      if (scratch > std::max(4.0 * out_bytes, double(1 << 20))) break;
+      if (scratch > std::max(2.0 * out_bytes, double(4 << 20))) break;
       const double tasks = double(tiles) * sp;
       const double waves = static_cast<double>(static_cast<int64_t>((tasks + kSlots - 1) / kSlots));
       const double work = double(bm) * double(bn) * double(K / sp) / kTileEff[t];
