@@ -133,17 +133,20 @@ __device__ __noinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& s
   const int q = task.prime;
   const ModParams mp = a.mods.q[q];
   const int64_t M = int64_t(1) << g.nm, N = int64_t(1) << g.nn, K = int64_t(1) << g.nk;
-  const int64_t kspan = split > 1 ? K / split : K;
-  const int64_t kbeg = int64_t(rank) * kspan;
+  // rank r of `split` takes the k chunks [nch r / split, nch (r+1) / split)
+  const int64_t nch = K > Cfg::BK ? K / Cfg::BK : 1;
+  const int64_t kbeg = nch * rank / split * Cfg::BK;
+  const int64_t kend_ = nch * (rank + 1) / split * Cfg::BK;
+  const int64_t kstop = kend_ < K ? kend_ : K;
   const Operand A = at_prime(exec_operand(a, g.a_kind, st.a_off), q);
   const Operand B = at_prime(exec_operand(a, g.b_kind, st.b_off), q);
   const Output C = at_prime(Output{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride}, q);
 
   Acc acc[TM][TN];
   if constexpr (std::is_same<SR, SrCnt>::value)
-    tile_mainloop_counting<Cfg, true>(g, A, B, mp, b, tm, tn_, kbeg, kbeg + kspan, smem, acc, prepared);
+    tile_mainloop_counting<Cfg, true>(g, A, B, mp, b, tm, tn_, kbeg, kstop, smem, acc, prepared);
   else
-    tile_mainloop<SR, Cfg, FOLD, true>(g, A, B, mp, b, tm, tn_, kbeg, kbeg + kspan, sm, acc, prepared);
+    tile_mainloop<SR, Cfg, FOLD, true>(g, A, B, mp, b, tm, tn_, kbeg, kstop, sm, acc, prepared);
   tile_merge_groups<SR, Cfg>(acc, reinterpret_cast<Acc*>(smem), mp);
 
   const uint32_t m0 = static_cast<uint32_t>(tm) * BM, n0 = static_cast<uint32_t>(tn_) * BN;

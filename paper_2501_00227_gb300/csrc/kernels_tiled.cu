@@ -49,16 +49,19 @@ __global__ void __launch_bounds__(kBlock, 2) k_step_tiled(const __grid_constant_
   const int q = blockIdx.z;
   const ModParams mp = args.mods.q[q];
   const int64_t K = int64_t(1) << g.nk;
-  const int64_t kspan = split > 1 ? K / split : K;
-  const int64_t kbeg = int64_t(rank) * kspan;
+  // rank r of `split` takes the k chunks [nch r / split, nch (r+1) / split)
+  const int64_t nch = K > Cfg::BK ? K / Cfg::BK : 1;
+  const int64_t kbeg = nch * rank / split * Cfg::BK;
+  const int64_t kend_ = nch * (rank + 1) / split * Cfg::BK;
+  const int64_t kstop = kend_ < K ? kend_ : K;
   const Operand A = at_prime(args.A, q), B = at_prime(args.B, q);
   const Output C = at_prime(args.C, q);
 
   Acc acc[TM][TN];
   if constexpr (std::is_same<SR, SrCnt>::value)
-    tile_mainloop_counting<Cfg, false>(g, A, B, mp, b, tm, tn_, kbeg, kbeg + kspan, smem, acc);
+    tile_mainloop_counting<Cfg, false>(g, A, B, mp, b, tm, tn_, kbeg, kstop, smem, acc);
   else
-    tile_mainloop<SR, Cfg, FOLD, false>(g, A, B, mp, b, tm, tn_, kbeg, kbeg + kspan, sm, acc);
+    tile_mainloop<SR, Cfg, FOLD, false>(g, A, B, mp, b, tm, tn_, kbeg, kstop, sm, acc);
   tile_merge_groups<SR, Cfg>(acc, reinterpret_cast<Acc*>(smem), mp);
 
   const uint32_t M = 1u << g.nm, N = 1u << g.nn;
@@ -222,14 +225,15 @@ void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, i
     if (t == 0 && !tropical) continue;
     const int64_t bm = kTileBM[t], bn = kTileBN[t], bk = kTileBK[t];
     const int64_t tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn) * batch;
-    for (int sp = 1; sp <= 16 && K / sp >= bk; sp *= 2) {
+    const int64_t nch = K > bk ? K / bk : 1;  // k chunks
+    for (int sp = 1; sp <= 16 && sp <= nch; ++sp) {
       // split-K scratch (one partial tile per task; reused by later steps)
       // at most max(2 x the step's output, 4 MiB)
       const double scratch = sp > 1 ? double(tiles) * sp * bm * bn * acc_bytes : 0.0;
       if (scratch > std::max(2.0 * out_bytes, double(4 << 20))) break;
       const double tasks = double(tiles) * sp;
       const double waves = static_cast<double>(static_cast<int64_t>((tasks + kSlots - 1) / kSlots));
-      const double work = double(bm) * double(bn) * double(K / sp) / kTileEff[t];
+      const double work = double(bm) * double(bn) * double(K) / sp / kTileEff[t];
       const double est = waves * (kTaskFixed + work);
       if (best < 0 || est < best) {
         best = est;
@@ -247,9 +251,8 @@ void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, i
   static const int force_split = getenv("TN_SPLIT") ? atoi(getenv("TN_SPLIT")) : -1;
   if (force_tile >= 0 && force_tile < kNumTiles && (tropical || force_tile != 0)) *tile = force_tile;
   if (force_split >= 1) {
-    int sp = 1;
-    while (sp * 2 <= force_split && K / (sp * 2) >= kTileBK[*tile]) sp *= 2;
-    *split = sp;
+    const int64_t nch = K > kTileBK[*tile] ? K / kTileBK[*tile] : 1;
+    *split = static_cast<int>(force_split < nch ? force_split : nch);
   }
 }
 
@@ -257,7 +260,10 @@ int launch_step(tn_semiring_t s, const StepGeom& g, const Operand& A, const Oper
                 const Output& C, const ModTable& mods, int nprimes, cudaStream_t st, int* kernel_used) {
   int kernel, tile, split;
   pick_launch(g, s, nprimes, &kernel, &tile, &split);
-  if (split > 8) split = 8;  // portable cluster size for the per-step launch
+  // per-step launch: a power-of-two cluster of at most 8 CTAs (portable size)
+  int sp2 = 1;
+  while (sp2 * 2 <= split && sp2 < 8) sp2 *= 2;
+  split = sp2;
   if (kernel_used) *kernel_used = kernel;
   if (kernel == kKernTiled && g.c_identity)
     return launch_step_tiled(s, g, A, B, C, mods, nprimes, tile, split, st);
