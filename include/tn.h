@@ -201,6 +201,29 @@ int tn_contract_pair(tn_semiring_t semiring, const uint32_t *primes, int32_t npr
                      const void *d_b, const int32_t *lb, int32_t rb,
                      const int32_t *lc, int32_t rc, void *d_c, void *cuda_stream);
 
+/* Measured launch shapes.  The paper leaves the kernel schedule to the
+ * contraction backend; this table lets an autotuner (tune.py in the Python
+ * package) replace the host's estimate for given step shapes.  entries holds
+ * count records of 7 int32: (semiring, nb, nm, nn, nk, tile, split), where
+ * nb / nm / nn / nk are the numbers of batch, A-only, B-only and summed
+ * labels of a pairwise step (Sec. 4.1), tile is 0..4 (0 = 128 x 128, tropical
+ * only; 1 = 64 x 64; 2 = 32 x 32; 3 = 16 x 64; 4 = 64 x 16) or -1 (general
+ * kernel), and split (1..16) is the number of CTAs sharing one output tile
+ * along k.  The record applies to steps the host would run as GEMM tiles.
+ * count = 0 removes the table.  The table is process-wide; executor plans
+ * built before the call are rebuilt on their next use (the old ones are
+ * kept until their plan is destroyed).  Returns TN_EINVAL for a malformed
+ * record (nothing is changed then). */
+int tn_tune_set(const int32_t *entries, int32_t count);
+
+/* Launch report of a plan: for every pairwise step i (plan order) writes 10
+ * int32 at out[10 i]: its index in the executor's task order (the step index
+ * of tn_contract_trace), its dependency level, kernel (0 general, 1 GEMM
+ * tile), tile shape (-1 for the general kernel), split-K (or k split of the
+ * general kernel), number of tasks, then nb, nm, nn, nk.  nsteps must equal
+ * tn_plan_info().nsteps. */
+int tn_plan_step_info(tn_plan_t plan, tn_semiring_t semiring, int32_t nprimes, int32_t *out, int32_t nsteps);
+
 /* Contraction without any device allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that

@@ -55,6 +55,8 @@ struct ExecPlan {
   std::vector<int32_t> deps;
   std::vector<ExecTask> tasks;
   std::vector<int32_t> step_level;   // dependency level of each exec step
+  std::vector<int32_t> exec_to_plan; // plan step index of each exec step
+  int32_t tune_gen = 0;              // launch-table generation the plan was built under
   std::vector<int32_t> group_begin;  // group g's members: group_members[begin[g] .. begin[g+1])
   std::vector<int32_t> group_members;  // exec-step indices, in execution order
   int32_t ngroups = 0;
@@ -86,6 +88,11 @@ ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc)
 ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int height, int* rc);
 // TN_GROUP_HEIGHT, else 1.
 int group_height();
+
+// Measured launch shapes (tune.cu): the table's generation, and the entry
+// for a step geometry if one is installed.
+int32_t tune_generation();
+bool tune_lookup(tn_semiring_t s, const StepGeom& g, int* tile, int* split);
 void exec_plans_free(tn_plan_s* p);
 
 // Enqueues one contraction through the executor (exec.cu).

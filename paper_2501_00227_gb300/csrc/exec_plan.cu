@@ -116,6 +116,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   X->nlevels = ns ? level[order[ns - 1]] + 1 : 0;
   X->step_level.resize(ns);
   for (int i = 0; i < ns; ++i) X->step_level[i] = level[order[i]];
+  X->exec_to_plan = order;
 
   // ---- groups: trees of tiny steps (one output chunk, little work) of
   // height <= H run back to back inside one CTA (one task, barriers between
@@ -446,12 +447,15 @@ ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H,
   const int np = s == TN_COUNT_MODP ? nprimes : 1;
   std::lock_guard<std::mutex> lk(c->mu);
   for (auto& x : c->plans)
-    if (x->semiring == s && x->nprimes == np && x->group_h == H) {
+    if (x->semiring == s && x->nprimes == np && x->group_h == H && x->tune_gen == tune_generation()) {
       *rc = TN_OK;
       return x.get();
     }
+  // plans built under an older launch table stay alive (a caller may still
+  // hold them); the current one is appended
   std::unique_ptr<ExecPlan> X(new ExecPlan());
   X->group_h = H;
+  X->tune_gen = tune_generation();
   *rc = build_exec(p, s, nprimes, X.get());
   if (*rc != TN_OK) return nullptr;
   c->plans.push_back(std::move(X));

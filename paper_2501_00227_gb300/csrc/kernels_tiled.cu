@@ -13,6 +13,7 @@
 #include <cstdlib>
 #include <type_traits>
 
+#include "exec.h"
 #include "kernels.h"
 #include "semiring.cuh"
 #include "tile_device.cuh"
@@ -245,6 +246,21 @@ void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, i
   *tile = best_tile;
   *split = best_split;
   *kernel = kKernTiled;
+  // a measured shape installed by tn_tune_set replaces the estimate
+  int tt, ts;
+  if (tune_lookup(s, g, &tt, &ts)) {
+    if (tt < 0) {
+      *kernel = kKernNaive;
+      *tile = 1;
+      *split = 1;
+      return;
+    }
+    if (tt < kNumTiles && (tropical || tt != 0)) {
+      const int64_t nch = K > kTileBK[tt] ? K / kTileBK[tt] : 1;
+      *tile = tt;
+      *split = static_cast<int>(ts < nch ? ts : nch);
+    }
+  }
   // TN_TILE / TN_SPLIT in the environment force the tile shape / split-K of
   // every tiled step (measurement and tests)
   static const int force_tile = getenv("TN_TILE") ? atoi(getenv("TN_TILE")) : -1;

@@ -87,6 +87,8 @@ def lib():
         L.tn_contract_trace.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.c_size_t, vp, vp, i32p, i32p,
                                         i32p, ctypes.POINTER(tn_result_t)]
         L.tn_contract_static.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.POINTER(tn_result_t)]
+        L.tn_tune_set.argtypes = [i32p, i32]
+        L.tn_plan_step_info.argtypes = [vp, ctypes.c_int, i32, i32p, i32]
         L.tn_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_int, u32p, i32, ctypes.POINTER(vp)]
         L.tn_batch_info.argtypes = [vp, ctypes.POINTER(u64), i32p, i32p, ctypes.POINTER(u64)]
         L.tn_batch_contract.argtypes = [vp, vp, ctypes.c_size_t, vp, vp]
@@ -276,6 +278,23 @@ def tn_contract_pair(semiring, primes, a_ptr, la, b_ptr, lb, lc, c_ptr, stream: 
     _check(lib().tn_contract_pair(_sr(semiring), _u32p(pr), k, ctypes.c_void_p(a_ptr), _p32(la), la.size,
                                   ctypes.c_void_p(b_ptr), _p32(lb), lb.size, _p32(lc), lc.size,
                                   ctypes.c_void_p(c_ptr), ctypes.c_void_p(stream)), "tn_contract_pair")
+
+
+def tn_tune_set(entries) -> None:
+    """Install measured launch shapes: rows (semiring, nb, nm, nn, nk, tile,
+    split); an empty list removes the table."""
+    rows = [[int(SEMIRINGS[r[0]]) if isinstance(r[0], str) else int(r[0]), *map(int, r[1:])] for r in entries]
+    arr = _i32(np.array(rows, dtype=np.int32).reshape(-1)) if rows else np.zeros(1, dtype=np.int32)
+    _check(lib().tn_tune_set(_p32(arr), len(rows)), "tn_tune_set")
+
+
+def tn_plan_step_info(plan, semiring, nprimes: int = 1) -> np.ndarray:
+    """(nsteps, 10) int32: exec index, level, kernel, tile, split, tasks, nb,
+    nm, nn, nk of every pairwise step (plan order)."""
+    n = tn_plan_info(plan, semiring, nprimes)["nsteps"]
+    out = np.zeros(10 * max(n, 1), dtype=np.int32)
+    _check(lib().tn_plan_step_info(plan, _sr(semiring), int(nprimes), _p32(out), n), "tn_plan_step_info")
+    return out[:10 * n].reshape(n, 10)
 
 
 def tn_server_create(hbm_budget_bytes: int, max_inflight: int) -> int:
