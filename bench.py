@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the host cost model's tile choices")
     return ap.parse_args()
 
 
@@ -179,6 +180,17 @@ def run_reference(args):
     return 0
 
 
+_TUNE_ROWS = []
+
+
+def _current_rows(rows=None):
+    """The launch-shape rows installed so far in this process (set with rows)."""
+    global _TUNE_ROWS
+    if rows is not None:
+        _TUNE_ROWS = list(rows)
+    return list(_TUNE_ROWS)
+
+
 def batching_bench(tn, torch, count: int = 4096):
     """Grouped persistent launch of `count` random 3-regular graphs with n
     uniform over the even numbers in [30, 60] (seed 0), MIS size and MIS count
@@ -193,8 +205,14 @@ def batching_bench(tn, torch, count: int = 4096):
            "plan_s": plan_s}
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    from paper_2501_00227_gb300 import tune
+    sample = sorted(plans, key=lambda p: -p.info("tropical_i32", 1)["tc"])[:32]
     for sr in ("tropical_i32", "counting"):
         ops = sum(p.info(sr, 1)["tc"] for p in plans)
+        # measured tile shapes for the largest instances' GEMM steps (kept
+        # only if they beat the cost model on those instances)
+        tr = tune.autotune(sample, sr, None, min_ops_bits=16, keep=_current_rows())
+        _current_rows(tr["rows"])
         b = tn.Batch(plans, sr)
         res = b.run(graph=True)
         for _ in range(3):
@@ -221,7 +239,8 @@ def batching_bench(tn, torch, count: int = 4096):
         e1.record(stream)
         torch.cuda.synchronize()
         per_ms = e0.elapsed_time(e1) / S
-        out[sr] = {"ms_per_batch": ms, "inst_per_s": count / ms * 1e3, "gops": ops / ms / 1e6,
+        out[sr] = {"autotune": {k: tr[k] for k in ("baseline_ms", "tuned_ms", "kept", "shapes")},
+                   "ms_per_batch": ms, "inst_per_s": count / ms * 1e3, "gops": ops / ms / 1e6,
                    "per_instance_launch_inst_per_s": 1e3 / per_ms,
                    "speedup_vs_per_instance": (count / ms) / (1.0 / per_ms), "tasks": b.info["tasks"]}
         b.close()
@@ -371,6 +390,20 @@ def run_tn(args):
         for sr, pr in SEMIRINGS:
             jobs.append((p, sr, pr, info["tc"] * (len(pr) if pr else 1), info["nsteps"]))
     ops_per_step = sum(j[3] for j in jobs)
+    # measured tile / split-K shapes for the GEMM steps of these plans (before
+    # timing, like the plans themselves)
+    tune_report = {}
+    if not args.no_autotune:
+        from paper_2501_00227_gb300 import tune
+        t0 = time.perf_counter()
+        rows = []
+        for sr, pr in SEMIRINGS:
+            r = tune.autotune(plans, sr, pr, keep=rows)
+            rows = r["rows"]
+            tune_report[sr] = {k: r[k] for k in ("baseline_ms", "tuned_ms", "kept", "shapes", "candidates")}
+        tune_report["tune_s"] = time.perf_counter() - t0
+        tune_report["table_rows"] = len(rows)
+        _current_rows(rows)
     ws_bytes = max(p.workspace_bytes(sr, len(pr) if pr else 1) for p, sr, pr, _, _ in jobs)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     raw = torch.zeros(len(jobs) * tn.TN_RAW_BYTES, dtype=torch.uint8, device=dev)
@@ -469,7 +502,8 @@ def run_tn(args):
             "config": {"workload": "random 3-regular n=100 and n=140, seeds 1-3, greedy order (nrepeat 10)",
                        "semirings": ["tropical_i32", "counting(int32,uint64)", "modp x3 (31-bit) + CRT"],
                        "ops_per_step": ops_per_step, "contractions_per_step": len(jobs),
-                       "l2": "flushed (256 MiB write) before each timed step", "plan_ms": plan_ms},
+                       "l2": "flushed (256 MiB write) before each timed step", "plan_ms": plan_ms,
+                       "autotune": tune_report or "off"},
             "e2e": {"value": e2e_val, "unit": "Gop/s", "h2d_bytes_per_step": h2d // e2e_steps,
                     "d2h_bytes_per_step": tn.TN_RAW_BYTES * len(jobs)},
             "gpu_launches": None, "roofline": roofline, "clocks": csum}
