@@ -516,10 +516,11 @@ def run_tn(args):
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_bench(tn, torch)
     if rank == 0 and not args.no_cpu_baseline:
-        ops, secs, used = cpu_reference([("reg3", 140, 1), ("reg3", 140, 2)], os.cpu_count() or 1)
+        sample = GRAPHS + [g for g in GRAPHS if g[1] == 140]
+        ops, secs, used = cpu_reference(sample, os.cpu_count() or 1)
         line["cpu_baseline"] = {"value": ops / secs / 1e9, "unit": "Gop/s", "cores": used, "kind": "oracle",
-                                "sample": "reg3 n=140 seeds 1-2 (oracle greedy order), tropical + counting + "
-                                          f"3 primes, {secs:.1f} s"}
+                                "sample": "the six headline graphs, then the three n=140 ones again (oracle greedy "
+                                          f"order), tropical + counting + 3 primes each, {secs:.1f} s"}
     if rank == 0:
         print(json.dumps(line))
     for p in plans:

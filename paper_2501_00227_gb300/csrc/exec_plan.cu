@@ -128,7 +128,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   auto tiny = [&](int st) {
     const StepGeom& g = p->steps[st].g;
     int kernel, tile, split;
-    dev::pick_launch(g, s, np, &kernel, &tile, &split);
+    dev::pick_launch(g, s, np, &kernel, &tile, &split, X->group_h > 1);
     return kernel == kKernNaive && g.rc <= 10 && g.rc + g.nk <= 13;
   };
   if (H > 1) {
@@ -168,7 +168,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   for (int st = 0; st < ns; ++st) {
     Launch& L = ln[st];
     const StepGeom& g = p->steps[st].g;
-    dev::pick_launch(g, s, np, &L.kernel, &L.tile, &L.split);
+    dev::pick_launch(g, s, np, &L.kernel, &L.tile, &L.split, X->group_h > 1);
     L.scratch = 0;
     if (groot[st] >= 0) {
       L.kernel = kKernNaive;
@@ -287,7 +287,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
     E.dep_count = static_cast<int32_t>(red[st].size());
     X->deps.insert(X->deps.end(), red[st].begin(), red[st].end());
     int kernel, tile, split;
-    dev::pick_launch(S.g, s, np, &kernel, &tile, &split);
+    dev::pick_launch(S.g, s, np, &kernel, &tile, &split, X->group_h > 1);
     if (internal(st) || groot[st] == st) {
       // group member: one whole-output chunk, no k split
       const dev::NaiveShape sh = dev::naive_shape(S.g.rc, S.g.nk, false);

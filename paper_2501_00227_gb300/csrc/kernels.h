@@ -25,7 +25,11 @@ int tiled_tile_bk(int tile);
 
 // Kernel choice for one step: fills kernel (kKernNaive / kKernTiled), tile
 // and split from the step geometry, the semiring and the number of primes.
-void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, int* tile, int* split);
+// batched: the step runs beside the same step of many other networks (a
+// batch or a served group), so there is parallelism to spare and k is not
+// split.
+void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, int* tile, int* split,
+                 bool batched = false);
 int launch_step(tn_semiring_t s, const StepGeom& g, const Operand& A, const Operand& B,
                 const Output& C, const ModTable& mods, int nprimes, cudaStream_t st, int* kernel_used);
 

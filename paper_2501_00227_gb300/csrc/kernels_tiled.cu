@@ -201,7 +201,8 @@ int launch_step_tiled(tn_semiring_t s, const StepGeom& g, const Operand& A, cons
 // task (claim, tables, pipeline fill, epilogue, publication) expressed in
 // multiply-adds of the semiring.  Every split keeps at least one k chunk.
 // TN_KERNEL=naive|tiled in the environment forces one path (tests).
-void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, int* tile, int* split) {
+void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, int* tile, int* split,
+                 bool batched) {
   const char* force = getenv("TN_KERNEL");
   const bool force_naive = force && force[0] == 'n';
   const bool force_tiled = force && force[0] == 't';
@@ -227,13 +228,16 @@ void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, i
     const int64_t bm = kTileBM[t], bn = kTileBN[t], bk = kTileBK[t];
     const int64_t tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn) * batch;
     const int64_t nch = K > bk ? K / bk : 1;  // k chunks
-    for (int sp = 1; sp <= 16 && sp <= nch; ++sp) {
+    for (int sp = 1; sp <= (batched ? 1 : 16) && sp <= nch; ++sp) {
       // split-K scratch (one partial tile per task; reused by later steps)
       // at most max(2 x the step's output, 4 MiB)
       const double scratch = sp > 1 ? double(tiles) * sp * bm * bn * acc_bytes : 0.0;
       if (scratch > std::max(2.0 * out_bytes, double(4 << 20))) break;
       const double tasks = double(tiles) * sp;
-      const double waves = static_cast<double>(static_cast<int64_t>((tasks + kSlots - 1) / kSlots));
+      // batched: the other networks' tasks fill the waves, so the cost is the
+      // total over tasks
+      const double waves = batched ? tasks / kSlots
+                                   : static_cast<double>(static_cast<int64_t>((tasks + kSlots - 1) / kSlots));
       const double work = double(bm) * double(bn) * double(K) / sp / kTileEff[t];
       const double est = waves * (kTaskFixed + work);
       if (best < 0 || est < best) {
@@ -258,7 +262,7 @@ void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, i
     if (tt < kNumTiles && (tropical || tt != 0)) {
       const int64_t nch = K > kTileBK[tt] ? K / kTileBK[tt] : 1;
       *tile = tt;
-      *split = static_cast<int>(ts < nch ? ts : nch);
+      *split = batched ? 1 : static_cast<int>(ts < nch ? ts : nch);
     }
   }
   // TN_TILE / TN_SPLIT in the environment force the tile shape / split-K of
