@@ -203,7 +203,7 @@ __device__ __forceinline__ void naive_tables(const StepGeom& g, NaiveSmem<SR>& s
 // have been called with the same block range).  R threads (a power of two,
 // 1..256, R <= 2^nk) share each output entry: lane l takes the terms l,
 // l + R, l + 2R, ... of the entry's flattened (block, low k) range,
-// NaiveUnroll loads per operand in flight (a batch beyond the range is
+// NaiveUnroll loads per operand in flight (the last, shorter batches are
 // padded with the edge tensor's forbidden entry, the semiring zero: (max,+)
 // -inf, (max, count) (-inf, 0), mod p 0), then the R partial results are
 // merged with the semiring (+) by warp shuffles (R <= 32) or through shared
@@ -238,12 +238,25 @@ __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, Load
     Acc acc = SR::zero(mp);
     if (valid) {
       const uint2 base = gather(sm.gt.c, ncn, static_cast<uint32_t>(c));
-      // U terms per batch; the last batch pads with the semiring zero, so
-      // its loads are in flight together as well
-      for (int32_t j = lane; j < nterm; j += U * R) {
+      // full batches of U terms, then the rest in batches of TU padded with
+      // the semiring zero, so the loads of every batch are in flight together
+      constexpr int TU = U > 4 ? 4 : 2;
+      int32_t j = lane;
+      for (; j + (U - 1) * R < nterm; j += U * R) {
         Val va[U], vb[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
+          const uint2 o = koff(j + u * R);
+          va[u] = loadA(base.x + o.x);
+          vb[u] = loadB(base.y + o.y);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) SR::mac(acc, va[u], vb[u], mp);
+      }
+      for (; j < nterm; j += TU * R) {
+        Val va[TU], vb[TU];
+#pragma unroll
+        for (int u = 0; u < TU; ++u) {
           const int32_t jj = j + u * R;
           const bool in = jj < nterm;
           const uint2 o = koff(in ? jj : j);
@@ -251,7 +264,7 @@ __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, Load
           vb[u] = in ? loadB(base.y + o.y) : SR::leaf(kOpEdge, 3);
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) SR::mac(acc, va[u], vb[u], mp);
+        for (int u = 0; u < TU; ++u) SR::mac(acc, va[u], vb[u], mp);
       }
     }
     // merge the R partial accumulators of each output entry
