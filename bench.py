@@ -285,6 +285,49 @@ def largest_bench(tn, torch, peak_tops: float):
     return out
 
 
+def limb_ablation_bench(tn, torch):
+    """Tensor-core ablation of the mod-p GEMM (config 4): the largest King's
+    subgraph 20x20 step shape, (batch, M, N, K) = (2, 1024, 512, 1024), 4
+    primes, on 8-bit limbs with integer MMAs vs the CUDA-core tile path
+    (tn_contract_pair) on the same buffers."""
+    primes = tuple(tn.PRIMES31[:4])
+    batch, m, n, k = 2, 1024, 512, 1024
+    g = torch.Generator(device="cuda").manual_seed(7)
+    a = torch.randint(0, 2 ** 31 - 1, (4 * batch * m * k,), dtype=torch.int64, device="cuda", generator=g)
+    b = torch.randint(0, 2 ** 31 - 1, (4 * batch * n * k,), dtype=torch.int64, device="cuda", generator=g)
+    pr = torch.tensor(primes, dtype=torch.int64, device="cuda")
+    a = (a.view(4, -1) % pr[:, None]).to(torch.int32).reshape(-1)
+    b = (b.view(4, -1) % pr[:, None]).to(torch.int32).reshape(-1)
+    c1 = torch.zeros(4 * batch * m * n, dtype=torch.int32, device="cuda")
+    c2 = torch.zeros_like(c1)
+    st = torch.cuda.current_stream().cuda_stream
+    lk, lm, ln, lb = list(range(0, 10)), list(range(20, 30)), list(range(40, 49)), [60]
+
+    def limb():
+        tn.tn_modp_gemm_limb(primes, a.data_ptr(), b.data_ptr(), c1.data_ptr(), batch, m, n, k, st)
+
+    def core():
+        tn.tn_contract_pair("modp", primes, a.data_ptr(), lk + lm + lb, b.data_ptr(), lk + ln + lb, ln + lm + lb,
+                            c2.data_ptr(), st)
+
+    out = {"shape": {"batch": batch, "M": m, "N": n, "K": k, "primes": 4}}
+    ops = 4.0 * batch * m * n * k
+    for name, fn in (("tensor_core_u8_limbs", limb), ("cuda_core_tile", core)):
+        for _ in range(2):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        out[name] = {"ms": ms, "tops": ops / (ms * 1e-3) / 1e12}
+    out["equal"] = bool(torch.equal(c1, c2))
+    out["note"] = "tcgen05.mma kind::i8 is rejected by ptxas for sm_103a; the tensor path is mma.sync u8"
+    return out
+
+
 def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120):
     """Poisson request stream mixing random 3-regular graphs (n even in
     [40,160]) and King's subgraphs (L in [8,16], filling 0.8), each asking the
@@ -511,6 +554,7 @@ def run_tn(args):
     line["gpu_launches"] = args.steps * len(jobs)
     if rank == 0:
         line["largest_tropical"] = largest_bench(tn, torch, peak_ops)
+        line["modp_tensor_core_ablation"] = limb_ablation_bench(tn, torch)
     if rank == 0 and not args.no_batching:
         line["batching"] = batching_bench(tn, torch)
     if rank == 0 and not args.no_serving:

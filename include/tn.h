@@ -224,6 +224,20 @@ int tn_tune_set(const int32_t *entries, int32_t count);
  * tn_plan_info().nsteps. */
 int tn_plan_step_info(tn_plan_t plan, tn_semiring_t semiring, int32_t nprimes, int32_t *out, int32_t nsteps);
 
+/* Ablation of the tensor cores for the count modulo p (not used by the
+ * contraction).  The batched mod-p GEMM of one pairwise step (Sec. 4.1, the
+ * ordinary (+,*) ring of Sec. 5.1 modulo each prime):
+ *   C[q][b][i][j] = sum_l A[q][b][i][l] * B[q][b][j][l]  mod primes[q]
+ * A: nprimes x batch x m x k, B: nprimes x batch x n x k, C: nprimes x batch
+ * x m x n, all uint32 residues < primes[q], row-major, caller-owned device
+ * memory.  Residues are cut into four 8-bit limbs whose 16 products run as
+ * integer tensor-core MMAs (mma.sync u8 x u8 -> s32; tcgen05.mma kind::i8 is
+ * not offered for sm_103a), then recombined mod p.  m must be a multiple of
+ * 64, n of 32, k of 32; 1 <= batch <= 65535; primes as for tn_contract.
+ * TN_EINVAL otherwise.  Enqueued on cuda_stream; does not wait. */
+int tn_modp_gemm_limb(const uint32_t *primes, int32_t nprimes, const void *d_a, const void *d_b, void *d_c,
+                      int32_t batch, int32_t m, int32_t n, int32_t k, void *cuda_stream);
+
 /* Contraction without any device allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that

@@ -176,11 +176,13 @@ __device__ __forceinline__ ModAccN<NP> shfl_xor_val(ModAccN<NP> v, int off) {
 // Fills the tables of a step for the high-k blocks [kh_begin, kh_end) with
 // threads first, first + stride, ...; sync() is a barrier over exactly those
 // threads.  The tables are complete for the CTA after the next CTA-wide
-// barrier.
+// barrier.  Steps with at most 4 summed labels use the first k nibble table
+// directly (no low / high k tables).
 template <class SR, class Sync>
 __device__ __forceinline__ void naive_prepare(const StepGeom& g, NaiveSmem<SR>& sm, int32_t kh_begin,
                                               int32_t kh_end, int first, int stride, Sync sync) {
   gather_build(g, sm.gt, first, stride);
+  if (g.nk <= 4) return;  // the first k nibble table covers every term
   sync();
   const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
   const int nkn = nibbles(g.nk);
@@ -227,6 +229,7 @@ __device__ __forceinline__ void naive_chunk(const StepGeom& g, LoadA loadA, Load
   const bool tab = kh_end - kh_begin <= kNaiveKHi;
   // offsets (in A, in B) of term j of the task's k range
   auto koff = [&](int32_t j) -> uint2 {
+    if (g.nk <= 4) return sm.gt.k[0][j];  // one nibble: a single k block
     const int32_t h = j >> kl;
     const uint2 hi = tab ? sm.khi[h] : gather(sm.gt.k, nkn, static_cast<uint32_t>(kh_begin + h) << kl);
     const uint2 lo = sm.klo[static_cast<uint32_t>(j) & mlo];
@@ -311,10 +314,17 @@ __device__ __forceinline__ void naive_chunk_wide(const StepGeom& g, LoadA loadA,
     }
 #pragma unroll 2
     for (int32_t j = 0; j < nterm; ++j) {
-      const int32_t h = j >> kl;
-      const uint2 hi = tab ? sm.khi[h] : gather(sm.gt.k, nkn, static_cast<uint32_t>(h) << kl);
-      const uint2 lo = sm.klo[static_cast<uint32_t>(j) & mlo];
-      const uint32_t ka = hi.x + lo.x, kb = hi.y + lo.y;
+      uint32_t ka, kb;
+      if (g.nk <= 4) {
+        ka = sm.gt.k[0][j].x;
+        kb = sm.gt.k[0][j].y;
+      } else {
+        const int32_t h = j >> kl;
+        const uint2 hi = tab ? sm.khi[h] : gather(sm.gt.k, nkn, static_cast<uint32_t>(h) << kl);
+        const uint2 lo = sm.klo[static_cast<uint32_t>(j) & mlo];
+        ka = hi.x + lo.x;
+        kb = hi.y + lo.y;
+      }
       typename SR::Val va[U], vb[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {

@@ -88,6 +88,7 @@ def lib():
                                         i32p, ctypes.POINTER(tn_result_t)]
         L.tn_contract_static.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.POINTER(tn_result_t)]
         L.tn_tune_set.argtypes = [i32p, i32]
+        L.tn_modp_gemm_limb.argtypes = [u32p, i32, vp, vp, vp, i32, i32, i32, i32, vp]
         L.tn_plan_step_info.argtypes = [vp, ctypes.c_int, i32, i32p, i32]
         L.tn_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_int, u32p, i32, ctypes.POINTER(vp)]
         L.tn_batch_info.argtypes = [vp, ctypes.POINTER(u64), i32p, i32p, ctypes.POINTER(u64)]
@@ -278,6 +279,16 @@ def tn_contract_pair(semiring, primes, a_ptr, la, b_ptr, lb, lc, c_ptr, stream: 
     _check(lib().tn_contract_pair(_sr(semiring), _u32p(pr), k, ctypes.c_void_p(a_ptr), _p32(la), la.size,
                                   ctypes.c_void_p(b_ptr), _p32(lb), lb.size, _p32(lc), lc.size,
                                   ctypes.c_void_p(c_ptr), ctypes.c_void_p(stream)), "tn_contract_pair")
+
+
+def tn_modp_gemm_limb(primes, a_ptr: int, b_ptr: int, c_ptr: int, batch: int, m: int, n: int, k: int,
+                      stream: int) -> None:
+    """Tensor-core (8-bit limb) mod-p batched GEMM, an ablation of the
+    CUDA-core path: C[q,b] = A[q,b] B[q,b]^T mod primes[q]."""
+    pr, kk = _primes(primes)
+    _check(lib().tn_modp_gemm_limb(_u32p(pr), kk, ctypes.c_void_p(a_ptr), ctypes.c_void_p(b_ptr),
+                                   ctypes.c_void_p(c_ptr), int(batch), int(m), int(n), int(k),
+                                   ctypes.c_void_p(stream)), "tn_modp_gemm_limb")
 
 
 def tn_tune_set(entries) -> None:
