@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the host cost model's tile choices")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the largest-contraction and tensor-core ablation sections")
     return ap.parse_args()
 
 
@@ -552,7 +554,7 @@ def run_tn(args):
             "gpu_launches": None, "roofline": roofline, "clocks": csum}
     # one executor launch per contraction
     line["gpu_launches"] = args.steps * len(jobs)
-    if rank == 0:
+    if rank == 0 and not args.no_extras:
         line["largest_tropical"] = largest_bench(tn, torch, peak_ops)
         line["modp_tensor_core_ablation"] = limb_ablation_bench(tn, torch)
     if rank == 0 and not args.no_batching:
