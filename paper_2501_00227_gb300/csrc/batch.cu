@@ -62,7 +62,7 @@ int build_batch_plan(tn_plan_s* const* plans, int32_t count, tn_semiring_t semir
   std::vector<ExecPlan*> xs(count);
   for (int i = 0; i < count; ++i) {
     int rc;
-    xs[i] = exec_plan_get_h(plans[i], semiring, nprimes, group_h, &rc);
+    xs[i] = exec_plan_get_h(plans[i], semiring, nprimes, group_h, true, &rc);
     if (!xs[i]) return rc;
   }
   ExecPlan& M = *out;
@@ -112,7 +112,7 @@ int build_batch_plan(tn_plan_s* const* plans, int32_t count, tn_semiring_t semir
       ExecStep e = x.steps[s];
       if (e.g.a_kind == kOpArena) e.a_off += arena_base[i];
       if (e.g.b_kind == kOpArena) e.b_off += arena_base[i];
-      e.c_off += arena_base[i];
+      if (!e.c_shared) e.c_off += arena_base[i];
       e.scratch_off += static_cast<int64_t>(scratch_base[i]);
       e.arrive_off += arrive_base[i];
       const int32_t db = static_cast<int32_t>(M.deps.size());

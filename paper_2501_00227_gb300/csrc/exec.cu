@@ -80,6 +80,27 @@ __device__ __forceinline__ Operand exec_operand(const ExecArgs& a, int32_t kind,
   return o;
 }
 
+// Operand / output of a group member: an arena tensor, a leaf, or a tensor
+// of rank `rank` in the group's shared memory at byte offset off (layout of
+// shared_tensor_bytes: values, then counts or further primes).
+__device__ __forceinline__ Operand exec_operand_g(const ExecArgs& a, int32_t kind, int64_t off, int rank,
+                                                  unsigned char* gsm) {
+  if (kind != kOpShared) return exec_operand(a, kind, off);
+  const int64_t e = int64_t(1) << rank;
+  Operand o;
+  o.kind = kOpShared;
+  o.pad_ = 0;
+  o.p0 = gsm + off;
+  o.p1 = gsm + off + (4 * e + 7) / 8 * 8;
+  o.prime_stride = e;
+  return o;
+}
+__device__ __forceinline__ Output exec_output_g(const ExecArgs& a, const ExecStep& st, unsigned char* gsm) {
+  if (!st.c_shared) return Output{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride};
+  const int64_t e = int64_t(1) << st.g.rc;
+  return Output{gsm + st.c_off, gsm + st.c_off + (4 * e + 7) / 8 * 8, e};
+}
+
 template <class SR>
 struct ExecTile {
   // tropical steps may use 8 x 8 micro-tiles; counting and mod p use 4 x 4
@@ -233,7 +254,8 @@ __device__ __forceinline__ void naive_task_kh(const ExecStep& st, const ExecTask
 // step's tables must be in shared memory (they do not depend on the prime).
 template <int NP>
 __device__ __forceinline__ void exec_naive_mp(const ExecArgs& a, const ExecStep& st, int32_t c0, int32_t c1,
-                                              int32_t kh0, int32_t kh1, bool whole, int q0, unsigned char* smem) {
+                                              int32_t kh0, int32_t kh1, bool whole, int q0, unsigned char* smem,
+                                              unsigned char* gsm) {
   using SRN = SrModN<NP>;
   auto& sm = *reinterpret_cast<NaiveSmem<SRN>*>(smem);
   const StepGeom& g = st.g;
@@ -245,20 +267,33 @@ __device__ __forceinline__ void exec_naive_mp(const ExecArgs& a, const ExecStep&
   for (int q = 0; q < NP; ++q) {
     mp.q[q] = a.mods.q[q0 + q];
     const int64_t off = int64_t(q0 + q) * a.prime_stride;
-    pa[q] = reinterpret_cast<const uint32_t*>(a.r0 + 4 * st.a_off) + off;
-    pb[q] = reinterpret_cast<const uint32_t*>(a.r0 + 4 * st.b_off) + off;
-    pc[q] = reinterpret_cast<uint32_t*>(a.r0 + 4 * st.c_off) + off;
+    pa[q] = g.a_kind == kOpShared ? reinterpret_cast<const uint32_t*>(gsm + st.a_off) + (int64_t(q0 + q) << g.ra)
+                                  : reinterpret_cast<const uint32_t*>(a.r0 + 4 * st.a_off) + off;
+    pb[q] = g.b_kind == kOpShared ? reinterpret_cast<const uint32_t*>(gsm + st.b_off) + (int64_t(q0 + q) << g.rb)
+                                  : reinterpret_cast<const uint32_t*>(a.r0 + 4 * st.b_off) + off;
+    pc[q] = st.c_shared ? reinterpret_cast<uint32_t*>(gsm + st.c_off) + (int64_t(q0 + q) << g.rc)
+                        : reinterpret_cast<uint32_t*>(a.r0 + 4 * st.c_off) + off;
   }
   auto la = [&](uint32_t e) {
-    if (g.a_kind != kOpArena) return SRN::leaf(g.a_kind, e);
     ModValN<NP> v;
+    if (g.a_kind == kOpShared) {
+#pragma unroll
+      for (int q = 0; q < NP; ++q) v.v[q] = pa[q][e];
+      return v;
+    }
+    if (g.a_kind != kOpArena) return SRN::leaf(g.a_kind, e);
 #pragma unroll
     for (int q = 0; q < NP; ++q) v.v[q] = __ldcg(pa[q] + e);
     return v;
   };
   auto lb = [&](uint32_t e) {
-    if (g.b_kind != kOpArena) return SRN::leaf(g.b_kind, e);
     ModValN<NP> v;
+    if (g.b_kind == kOpShared) {
+#pragma unroll
+      for (int q = 0; q < NP; ++q) v.v[q] = pb[q][e];
+      return v;
+    }
+    if (g.b_kind != kOpArena) return SRN::leaf(g.b_kind, e);
 #pragma unroll
     for (int q = 0; q < NP; ++q) v.v[q] = __ldcg(pb[q] + e);
     return v;
@@ -276,13 +311,13 @@ __device__ __forceinline__ void exec_naive_mp(const ExecArgs& a, const ExecStep&
 // Every prime of a mod-p general step (k not split), in groups of up to 4.
 __device__ __forceinline__ void exec_naive_all_primes(const ExecArgs& a, const ExecStep& st, int32_t c0,
                                                       int32_t c1, int32_t kh0, int32_t kh1, bool whole,
-                                                      unsigned char* smem) {
+                                                      unsigned char* smem, unsigned char* gsm) {
   for (int q0 = 0; q0 < a.nprimes; q0 += 4) {
     switch (a.nprimes - q0 < 4 ? a.nprimes - q0 : 4) {
-      case 1: exec_naive_mp<1>(a, st, c0, c1, kh0, kh1, whole, q0, smem); break;
-      case 2: exec_naive_mp<2>(a, st, c0, c1, kh0, kh1, whole, q0, smem); break;
-      case 3: exec_naive_mp<3>(a, st, c0, c1, kh0, kh1, whole, q0, smem); break;
-      default: exec_naive_mp<4>(a, st, c0, c1, kh0, kh1, whole, q0, smem); break;
+      case 1: exec_naive_mp<1>(a, st, c0, c1, kh0, kh1, whole, q0, smem, gsm); break;
+      case 2: exec_naive_mp<2>(a, st, c0, c1, kh0, kh1, whole, q0, smem, gsm); break;
+      case 3: exec_naive_mp<3>(a, st, c0, c1, kh0, kh1, whole, q0, smem, gsm); break;
+      default: exec_naive_mp<4>(a, st, c0, c1, kh0, kh1, whole, q0, smem, gsm); break;
     }
   }
 }
@@ -298,7 +333,7 @@ __device__ __noinline__ void exec_naive_task(const ExecArgs& a, const ExecStep& 
     if (task.prime < 0) {  // k is not split: all primes in one pass
       const int32_t E = 1 << st.g.rc, chunk = static_cast<int32_t>(st.chunk);
       const int32_t c0 = task.local * chunk, c1 = c0 + chunk < E ? c0 + chunk : E;
-      exec_naive_all_primes(a, st, c0, c1, kh0, kh1, false, smem);
+      exec_naive_all_primes(a, st, c0, c1, kh0, kh1, false, smem, nullptr);
       return;
     }
   }
@@ -374,24 +409,35 @@ __device__ __forceinline__ void exec_naive_task_q(const ExecArgs& a, const ExecS
 // All outputs of one general step over its whole k range (a member of a
 // group of tiny steps).
 template <class SR>
-__device__ __forceinline__ void exec_naive_whole(const ExecArgs& a, const ExecStep& st, int q, unsigned char* smem) {
+__device__ __forceinline__ void exec_naive_whole(const ExecArgs& a, const ExecStep& st, int q, unsigned char* smem,
+                                                 unsigned char* gsm) {
   auto& sm = *reinterpret_cast<NaiveSmem<SR>*>(smem);
   const StepGeom& g = st.g;
   const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
   const int32_t nkhi = 1 << (g.nk - kl);
   naive_tables<SR>(g, sm, 0, nkhi);
   const ModParams mp = a.mods.q[q];
-  const Operand A = at_prime(exec_operand(a, g.a_kind, st.a_off), q);
-  const Operand B = at_prime(exec_operand(a, g.b_kind, st.b_off), q);
-  const Output C = at_prime(Output{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride}, q);
+  const Operand A = at_prime(exec_operand_g(a, g.a_kind, st.a_off, g.ra, gsm), q);
+  const Operand B = at_prime(exec_operand_g(a, g.b_kind, st.b_off, g.rb, gsm), q);
+  const Output C = at_prime(exec_output_g(a, st, gsm), q);
   auto la = [&](uint32_t e) { return SR::template load<true>(A, e); };
   auto lb = [&](uint32_t e) { return SR::template load<true>(B, e); };
   auto sink = [&](uint32_t c, const typename SR::Acc& v) { SR::store(C, c, v, mp); };
   naive_chunk<SR>(g, la, lb, sink, mp, 0, 1 << g.rc, 0, nkhi, st.R, sm);
 }
 
+// Byte offset of a group task's tensors in dynamic shared memory (after the
+// general-step tables).
+template <class SR>
+constexpr size_t group_smem_off() {
+  size_t t = sizeof(NaiveSmem<SR>);
+  if (std::is_same<SR, SrMod>::value && sizeof(NaiveSmem<SrModN<4>>) > t) t = sizeof(NaiveSmem<SrModN<4>>);
+  return (t + 127) / 128 * 128;
+}
+
 // A group of tiny steps, run back to back by this CTA: barriers between the
-// steps make each step's outputs visible to the next.
+// steps make each step's outputs visible to the next; internal tensors that
+// fit live in shared memory after the tables.
 template <class SR>
 __device__ __noinline__ void exec_group_task(const ExecArgs& a, const ExecTask& task, ExecStep* s_step,
                                              unsigned char* smem) {
@@ -403,18 +449,19 @@ __device__ __noinline__ void exec_group_task(const ExecArgs& a, const ExecTask& 
     int32_t* dst = reinterpret_cast<int32_t*>(s_step);
     for (int w = threadIdx.x; w < static_cast<int>(sizeof(ExecStep) / 4); w += kBlock) dst[w] = __ldg(src + w);
     __syncthreads();
+    unsigned char* gsm = smem + group_smem_off<SR>();
     if (task.prime >= 0) {
-      exec_naive_whole<SR>(a, *s_step, task.prime, smem);
+      exec_naive_whole<SR>(a, *s_step, task.prime, smem, gsm);
     } else if constexpr (std::is_same<SR, SrMod>::value) {
       const StepGeom& g = s_step->g;
       const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
       const int32_t nkhi = 1 << (g.nk - kl);
       naive_tables<SR>(g, *reinterpret_cast<NaiveSmem<SR>*>(smem), 0, nkhi);
-      exec_naive_all_primes(a, *s_step, 0, 1 << g.rc, 0, nkhi, true, smem);
+      exec_naive_all_primes(a, *s_step, 0, 1 << g.rc, 0, nkhi, true, smem, gsm);
     } else {
       for (int q = 0; q < a.nprimes; ++q) {
         __syncthreads();
-        exec_naive_whole<SR>(a, *s_step, q, smem);
+        exec_naive_whole<SR>(a, *s_step, q, smem, gsm);
       }
     }
   }
@@ -581,7 +628,8 @@ static size_t smem_for() {
   size_t t = tile_smem_bytes<SR, TileC1>();
   const size_t cands[] = {ExecTile<SR>::kBig ? tile_smem_bytes<SR, TileC0>() : 0, tile_smem_bytes<SR, TileC2>(),
                           tile_smem_bytes<SR, TileC3>(), tile_smem_bytes<SR, TileC4>(), sizeof(NaiveSmem<SR>),
-                          std::is_same<SR, SrMod>::value ? sizeof(NaiveSmem<SrModN<4>>) : 0};
+                          std::is_same<SR, SrMod>::value ? sizeof(NaiveSmem<SrModN<4>>) : 0,
+                          group_smem_off<SR>() + static_cast<size_t>(kGroupSmem)};
   for (size_t c : cands) t = c > t ? c : t;
   return t;
 }

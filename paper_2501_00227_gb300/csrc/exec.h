@@ -36,7 +36,23 @@ struct ExecStep {
   int32_t ks;                    // naive: k splits per output chunk
   int32_t nchunks;               // naive: output chunks
   int32_t done_target;           // tasks of this step (its done counter's final value)
+  int32_t c_shared;              // 1: the output lives in the group task's shared memory at byte c_off
+  int32_t pad_;
 };
+
+// Shared memory of a group task reserved for its internal tensors (bytes).
+constexpr int64_t kGroupSmem = 32 * 1024;
+
+// Bytes of an intermediate of rank r in shared memory: values (4 bytes),
+// then counts (8 bytes, 8-aligned) for counting, one residue array per prime
+// for mod p (prime-major); 16-byte aligned.
+inline int64_t shared_tensor_bytes(tn_semiring_t s, int32_t nprimes, int r) {
+  const int64_t e = int64_t(1) << r;
+  int64_t b = 4 * e;
+  if (s == TN_COUNTING_TROPICAL) b = (4 * e + 7) / 8 * 8 + 8 * e;
+  if (s == TN_COUNT_MODP) b = 4 * e * (nprimes < 1 ? 1 : nprimes);
+  return (b + 15) / 16 * 16;
+}
 
 enum ExecTaskKind : int32_t { kTaskNaive = 0, kTaskTile = 1, kTaskFinal = 2, kTaskGroup = 3 };
 
@@ -61,6 +77,7 @@ struct ExecPlan {
   std::vector<int32_t> group_members;  // exec-step indices, in execution order
   int32_t ngroups = 0;
   int32_t group_h = 1;               // group height limit the plan was built with
+  bool batched = false;              // built for a batch / served group
   int64_t arena_entries = 0;
   int64_t root_off = 0;
   int32_t root_step = -1;
@@ -85,7 +102,9 @@ struct ExecPlan {
 ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc);
 // The same with an explicit group height (largest tree of tiny steps one
 // CTA runs back to back; 1 disables grouping).
-ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int height, int* rc);
+// height: group height limit; batched: the plan runs inside a batch or a
+// served group (launch shapes assume parallelism across networks).
+ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int height, bool batched, int* rc);
 // TN_GROUP_HEIGHT, else 1.
 int group_height();
 

@@ -128,7 +128,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   auto tiny = [&](int st) {
     const StepGeom& g = p->steps[st].g;
     int kernel, tile, split;
-    dev::pick_launch(g, s, np, &kernel, &tile, &split, X->group_h > 1);
+    dev::pick_launch(g, s, np, &kernel, &tile, &split, X->batched);
     return kernel == kKernNaive && g.rc <= 10 && g.rc + g.nk <= 13;
   };
   if (H > 1) {
@@ -168,7 +168,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   for (int st = 0; st < ns; ++st) {
     Launch& L = ln[st];
     const StepGeom& g = p->steps[st].g;
-    dev::pick_launch(g, s, np, &L.kernel, &L.tile, &L.split, X->group_h > 1);
+    dev::pick_launch(g, s, np, &L.kernel, &L.tile, &L.split, X->batched);
     L.scratch = 0;
     if (groot[st] >= 0) {
       L.kernel = kKernNaive;
@@ -228,10 +228,53 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
     }
     i = j;
   }
-  // internal tensors after the shared arena
+  // internal tensors: in the group CTA's shared memory where they fit
+  // (first fit over the members in execution order; a tensor is live from
+  // its producer to its consumer), else in the global region below
+  std::vector<int64_t> sh_off(ns, -1);
+  for (int st = 0; st < ns; ++st) {
+    if (groot[st] != st) continue;
+    std::vector<int32_t> mem = gmem[st];
+    std::sort(mem.begin(), mem.end(), [&](int a, int b) { return pos[a] < pos[b]; });
+    std::map<int64_t, int64_t> free_blocks{{0, kGroupSmem}};  // offset -> length
+    auto take = [&](int64_t size) -> int64_t {
+      for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it)
+        if (it->second >= size) {
+          const int64_t off = it->first, len = it->second;
+          free_blocks.erase(it);
+          if (len > size) free_blocks[off + size] = len - size;
+          return off;
+        }
+      return -1;
+    };
+    auto give = [&](int64_t off, int64_t size) {
+      auto it = free_blocks.emplace(off, size).first;
+      auto nx = std::next(it);
+      if (nx != free_blocks.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        free_blocks.erase(nx);
+      }
+      if (it != free_blocks.begin()) {
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+          pv->second += it->second;
+          free_blocks.erase(it);
+        }
+      }
+    };
+    for (int32_t m : mem) {
+      if (internal(m)) sh_off[m] = take(shared_tensor_bytes(s, np, p->steps[m].g.rc));
+      for (int32_t id : {p->steps[m].a_id, p->steps[m].b_id}) {
+        const int pr = prod(id);
+        if (pr >= 0 && internal(pr) && groot[pr] == st && sh_off[pr] >= 0)
+          give(sh_off[pr], shared_tensor_bytes(s, np, p->steps[pr].g.rc));
+      }
+    }
+  }
+  // the remaining internal tensors after the shared arena
   int64_t top = arena.top();
   for (int st = 0; st < ns; ++st)
-    if (internal(st)) {
+    if (internal(st) && sh_off[st] < 0) {
       c_off[st] = top;
       top += static_cast<int64_t>(align_up(size_t(1) << p->steps[st].g.rc, kArenaAlign));
     }
@@ -279,15 +322,21 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
     ExecStep& E = X->steps[x];
     std::memset(&E, 0, sizeof(E));
     E.g = S.g;
-    auto off = [&](int32_t id) -> int64_t { return prod(id) >= 0 ? c_off[prod(id)] : 0; };
+    auto off = [&](int32_t id) -> int64_t {
+      const int pr = prod(id);
+      return pr < 0 ? 0 : (sh_off[pr] >= 0 ? sh_off[pr] : c_off[pr]);
+    };
     E.a_off = off(S.a_id);
     E.b_off = off(S.b_id);
-    E.c_off = c_off[st];
+    if (prod(S.a_id) >= 0 && sh_off[prod(S.a_id)] >= 0) E.g.a_kind = kOpShared;
+    if (prod(S.b_id) >= 0 && sh_off[prod(S.b_id)] >= 0) E.g.b_kind = kOpShared;
+    E.c_shared = sh_off[st] >= 0 ? 1 : 0;
+    E.c_off = E.c_shared ? sh_off[st] : c_off[st];
     E.dep_begin = static_cast<int32_t>(X->deps.size());
     E.dep_count = static_cast<int32_t>(red[st].size());
     X->deps.insert(X->deps.end(), red[st].begin(), red[st].end());
     int kernel, tile, split;
-    dev::pick_launch(S.g, s, np, &kernel, &tile, &split, X->group_h > 1);
+    dev::pick_launch(S.g, s, np, &kernel, &tile, &split, X->batched);
     if (internal(st) || groot[st] == st) {
       // group member: one whole-output chunk, no k split
       const dev::NaiveShape sh = dev::naive_shape(S.g.rc, S.g.nk, false);
@@ -370,9 +419,11 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
     };
     for (int y = 0; y < ns; ++y) {
       const int sy = order[y];
+      if (sh_off[sy] >= 0) continue;  // in a group's shared memory
       const int64_t y0 = c_off[sy], y1 = y0 + (int64_t(1) << p->steps[sy].g.rc);
       for (int x = 0; x < y; ++x) {
         const int sx = order[x];
+        if (sh_off[sx] >= 0) continue;
         const int64_t x0 = c_off[sx], x1 = x0 + (int64_t(1) << p->steps[sx].g.rc);
         if (x1 <= y0 || y1 <= x0) continue;
         if (internal(sx) || internal(sy)) return TN_EINVAL;  // internal tensors are never shared
@@ -434,10 +485,10 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
 }  // namespace
 
 ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc) {
-  return exec_plan_get_h(p, s, nprimes, group_height(), rc);
+  return exec_plan_get_h(p, s, nprimes, group_height(), false, rc);
 }
 
-ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H, int* rc) {
+ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H, bool batched, int* rc) {
   if (!p->exec_cache) {
     static std::mutex init_mu;
     std::lock_guard<std::mutex> lk(init_mu);
@@ -447,7 +498,8 @@ ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H,
   const int np = s == TN_COUNT_MODP ? nprimes : 1;
   std::lock_guard<std::mutex> lk(c->mu);
   for (auto& x : c->plans)
-    if (x->semiring == s && x->nprimes == np && x->group_h == H && x->tune_gen == tune_generation()) {
+    if (x->semiring == s && x->nprimes == np && x->group_h == H && x->batched == batched &&
+        x->tune_gen == tune_generation()) {
       *rc = TN_OK;
       return x.get();
     }
@@ -455,6 +507,7 @@ ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H,
   // hold them); the current one is appended
   std::unique_ptr<ExecPlan> X(new ExecPlan());
   X->group_h = H;
+  X->batched = batched;
   X->tune_gen = tune_generation();
   *rc = build_exec(p, s, nprimes, X.get());
   if (*rc != TN_OK) return nullptr;

@@ -41,7 +41,7 @@ struct Output {
 // The same operand / output seen at the block of prime index q (mod p keeps
 // one residue array per prime; the element accessors below read p0 only).
 __device__ __forceinline__ Operand at_prime(Operand o, int q) {
-  if (o.kind == kOpArena && q) o.p0 = static_cast<const uint32_t*>(o.p0) + q * o.prime_stride;
+  if ((o.kind == kOpArena || o.kind == kOpShared) && q) o.p0 = static_cast<const uint32_t*>(o.p0) + q * o.prime_stride;
   return o;
 }
 __device__ __forceinline__ Output at_prime(Output o, int q) {
@@ -96,6 +96,7 @@ struct SrF32 {
   }
   template <bool CG = false>
   static __device__ __forceinline__ Val load(const Operand& o, uint32_t e) {
+    if (o.kind == kOpShared) return static_cast<const float*>(o.p0)[e];
     if (o.kind != kOpArena) return leaf(o.kind, e);
     return ldg_t<CG>(static_cast<const float*>(o.p0) + e);
   }
@@ -139,6 +140,7 @@ struct SrI32 {
   }
   template <bool CG = false>
   static __device__ __forceinline__ Val load(const Operand& o, uint32_t e) {
+    if (o.kind == kOpShared) return static_cast<const int32_t*>(o.p0)[e];
     if (o.kind != kOpArena) return leaf(o.kind, e);
     return ldg_t<CG>(static_cast<const int32_t*>(o.p0) + e);
   }
@@ -194,6 +196,8 @@ struct SrCnt {
   }
   template <bool CG = false>
   static __device__ __forceinline__ Val load(const Operand& o, uint32_t e) {
+    if (o.kind == kOpShared)
+      return CntVal{static_cast<const int32_t*>(o.p0)[e], static_cast<const uint64_t*>(o.p1)[e]};
     if (o.kind != kOpArena) return leaf(o.kind, e);
     return CntVal{ldg_t<CG>(static_cast<const int32_t*>(o.p0) + e),
                   ldg_t<CG>(static_cast<const uint64_t*>(o.p1) + e)};
@@ -267,6 +271,7 @@ struct SrMod {
   }
   template <bool CG = false>
   static __device__ __forceinline__ Val load(const Operand& o, uint32_t e) {
+    if (o.kind == kOpShared) return static_cast<const uint32_t*>(o.p0)[e];
     if (o.kind != kOpArena) return leaf(o.kind, e);
     return ldg_t<CG>(static_cast<const uint32_t*>(o.p0) + e);
   }

@@ -26,6 +26,7 @@ enum OperandKind : int32_t {
   kOpEdge = 1,    // an edge leaf B(n_u, n_v): generated in the kernel
   kOpVertex = 2,  // a vertex leaf W(n_v): generated in the kernel
   kOpOne = 3,     // the rank-0 multiplicative identity (single-leaf networks)
+  kOpShared = 4,  // an intermediate inside a group task, in the CTA's shared memory
 };
 
 // Geometry of one pairwise step, as seen by the kernels.
