@@ -439,17 +439,21 @@ constexpr size_t group_smem_off() {
 // steps make each step's outputs visible to the next; internal tensors that
 // fit live in shared memory after the tables.
 template <class SR>
-__device__ __noinline__ void exec_group_task(const ExecArgs& a, const ExecTask& task, ExecStep* s_step,
+__device__ __noinline__ void exec_group_task(const ExecArgs& a, const ExecTask& task, ExecStep*,
                                              unsigned char* smem) {
   const int b0 = a.group_begin[task.local], b1 = a.group_begin[task.local + 1];
+  unsigned char* gsm = smem + group_smem_off<SR>();
+  // every member's step record, copied together (one round of loads)
+  ExecStep* recs = reinterpret_cast<ExecStep*>(gsm + kGroupSmem);
+  constexpr int kWords = static_cast<int>(sizeof(ExecStep) / 4);
+  for (int w = threadIdx.x; w < (b1 - b0) * kWords; w += kBlock) {
+    const int i = w / kWords;
+    reinterpret_cast<int32_t*>(recs + i)[w % kWords] =
+        __ldg(reinterpret_cast<const int32_t*>(a.steps + a.group_members[b0 + i]) + w % kWords);
+  }
   for (int i = b0; i < b1; ++i) {
-    const int m = a.group_members[i];
     __syncthreads();
-    const int32_t* src = reinterpret_cast<const int32_t*>(a.steps + m);
-    int32_t* dst = reinterpret_cast<int32_t*>(s_step);
-    for (int w = threadIdx.x; w < static_cast<int>(sizeof(ExecStep) / 4); w += kBlock) dst[w] = __ldg(src + w);
-    __syncthreads();
-    unsigned char* gsm = smem + group_smem_off<SR>();
+    ExecStep* s_step = recs + (i - b0);
     if (task.prime >= 0) {
       exec_naive_whole<SR>(a, *s_step, task.prime, smem, gsm);
     } else if constexpr (std::is_same<SR, SrMod>::value) {
@@ -629,7 +633,8 @@ static size_t smem_for() {
   const size_t cands[] = {ExecTile<SR>::kBig ? tile_smem_bytes<SR, TileC0>() : 0, tile_smem_bytes<SR, TileC2>(),
                           tile_smem_bytes<SR, TileC3>(), tile_smem_bytes<SR, TileC4>(), sizeof(NaiveSmem<SR>),
                           std::is_same<SR, SrMod>::value ? sizeof(NaiveSmem<SrModN<4>>) : 0,
-                          group_smem_off<SR>() + static_cast<size_t>(kGroupSmem)};
+                          group_smem_off<SR>() + static_cast<size_t>(kGroupSmem) +
+                              sizeof(ExecStep) * kGroupMaxMembers};
   for (size_t c : cands) t = c > t ? c : t;
   return t;
 }

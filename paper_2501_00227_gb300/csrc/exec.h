@@ -40,8 +40,11 @@ struct ExecStep {
   int32_t pad_;
 };
 
-// Shared memory of a group task reserved for its internal tensors (bytes).
+// Shared memory of a group task reserved for its internal tensors (bytes),
+// and the most members a group may have (their step records are copied to
+// shared memory together when the group starts).
 constexpr int64_t kGroupSmem = 32 * 1024;
+constexpr int kGroupMaxMembers = 16;
 
 // Bytes of an intermediate of rank r in shared memory: values (4 bytes),
 // then counts (8 bytes, 8-aligned) for counting, one residue array per prime

@@ -139,7 +139,9 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
       gmem[st] = {st};
       for (int32_t id : {p->steps[st].a_id, p->steps[st].b_id}) {
         const int pr = prod(id);
-        if (pr < 0 || groot[pr] != pr || gh[pr] + 1 > H) continue;
+        if (pr < 0 || groot[pr] != pr || gh[pr] + 1 > H ||
+            gmem[st].size() + gmem[pr].size() > static_cast<size_t>(kGroupMaxMembers))
+          continue;
         for (int32_t m : gmem[pr]) groot[m] = st;
         gmem[st].insert(gmem[st].end(), gmem[pr].begin(), gmem[pr].end());
         gmem[pr].clear();
