@@ -124,9 +124,11 @@ __device__ __forceinline__ CntVal ldcg_acc(const CntVal* p) {
 __device__ __forceinline__ bool arrive_last(int32_t* ctr, int split, int* s_flag) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    *s_flag = atomicAdd(ctr, 1) == split - 1;
-    __threadfence();
+    // acquire-release: publishes this CTA's partial (ordered by the barrier
+    // above) and, for the last arriver, makes the other partials visible
+    int32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(ctr) : "memory");
+    *s_flag = old == split - 1;
   }
   __syncthreads();
   return *s_flag != 0;
@@ -568,7 +570,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
               break;
             }
             __nanosleep(ns);
-            if (ns < 256) ns *= 2;
+            if (ns < 128) ns *= 2;
           }
         }
       }
@@ -608,8 +610,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
     __syncthreads();
     if (tid == 0) {
       const unsigned long long t_body = a.trace ? global_ns() : 0;
-      __threadfence();
-      atomicAdd(a.done + s_task.step, 1);
+      // release: the CTA's writes (ordered by the barrier above) become
+      // visible to any CTA that acquires the counter
+      asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(a.done + s_task.step) : "memory");
       if (a.trace) {
         unsigned smid;
         asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
