@@ -238,6 +238,16 @@ int tn_plan_step_info(tn_plan_t plan, tn_semiring_t semiring, int32_t nprimes, i
 int tn_modp_gemm_limb(const uint32_t *primes, int32_t nprimes, const void *d_a, const void *d_b, void *d_c,
                       int32_t batch, int32_t m, int32_t n, int32_t k, void *cuda_stream);
 
+/* The same product on the 5th-generation tensor cores: tcgen05.mma kind::f16
+ * with bf16 limbs (exact integers 0..255), fp32 accumulators in tensor
+ * memory, one accumulator per limb diagonal, folded mod p after every 64
+ * terms (each accumulator stays below 2^24, so it is exact).  m must be a
+ * multiple of 128, n of 64, k of 64, d_c 16-byte aligned; other arguments as
+ * for tn_modp_gemm_limb.  Waits for the stream; TN_ETIMEOUT if the tensor
+ * cores did not complete within 2 s (the result is then unspecified). */
+int tn_modp_gemm_umma(const uint32_t *primes, int32_t nprimes, const void *d_a, const void *d_b, void *d_c,
+                      int32_t batch, int32_t m, int32_t n, int32_t k, void *cuda_stream);
+
 /* Contraction without any device allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that

@@ -1,0 +1,293 @@
+// ablation_umma.cu -- tn_modp_gemm_umma: the batched mod-p GEMM of one
+// pairwise step on the 5th-generation tensor cores (tcgen05.mma, operands in
+// shared memory, accumulators in tensor memory), as an ablation of the
+// CUDA-core path (the contraction itself never calls it).
+//
+//   C[q][b][m][n] = sum_k A[q][b][m][k] * B[q][b][n][k]  mod p_q
+//
+// Residues (< 2^31) are cut into four 8-bit limbs.  A limb is an integer
+// 0..255, exact in bf16; a limb product is at most 255^2 and a sum of them
+// stays exact in fp32 while it is below 2^24.  For every chunk of 64 k the
+// 16 limb products (i, j) are accumulated by kind::f16 MMAs (M = 128,
+// N = 64, K = 16, bf16 x bf16 -> fp32) into seven tensor-memory
+// accumulators, one per diagonal d = i + j (at most 4 x 64 x 255^2 < 2^24,
+// so every accumulator is an exact integer).  After each chunk the
+// accumulators are read back (tcgen05.ld), converted to integers and folded
+// into the residues: res = res + S_d (2^(8d) mod p) mod p, with Barrett
+// reductions (Barrett 1986).
+//
+// One CTA of 128 threads owns a 128 x 64 block of C for one (prime, batch);
+// thread t owns row t (tensor-memory lane t).  Every wait on the MMA
+// completion barrier is bounded (2 s); on a timeout the CTA records it in
+// the status word, releases its tensor memory and returns.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "semiring.cuh"
+#include "tn_internal.h"
+
+namespace tn {
+namespace dev {
+namespace {
+
+constexpr int kUM = 128, kUN = 64, kUK = 64;  // C tile rows, columns; k chunk
+constexpr int kUDiag = 7;                     // limb diagonals 0..6
+constexpr int kUCols = 512;                   // tensor-memory columns allocated (7 x 64 used)
+// shared memory: 4 A limb tiles (128 x 64 bf16) and 4 B limb tiles (64 x 64)
+constexpr int kUATile = kUM * kUK * 2, kUBTile = kUN * kUK * 2;
+constexpr int kUSmemOps = 4 * kUATile + 4 * kUBTile;        // 98304
+constexpr int kUSmem = kUSmemOps + 1024 + 16 * 1024;       // + barrier / slot + slack, > 113 KB: 1 CTA / SM
+
+__device__ uint32_t g_umma_status;
+
+struct UmmaArgs {
+  const uint32_t* A;
+  const uint32_t* B;
+  uint32_t* C;
+  ModTable mods;
+  int32_t batch, m, n, k;
+};
+
+// Byte offset of element (row, kk) of a K-major tile with 8 x (16-byte)
+// core matrices: core matrices adjacent in k are 128 bytes apart (leading
+// byte offset), row groups of 8 are 1024 bytes apart (stride byte offset).
+__device__ __forceinline__ uint32_t umma_off(int row, int kk) {
+  return static_cast<uint32_t>((row >> 3) * 1024 + (kk >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2);
+}
+
+// Shared-memory matrix descriptor (no swizzle, K-major): start address,
+// leading byte offset 128, stride byte offset 1024, descriptor version 1.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFF);
+  d |= static_cast<uint64_t>(128 >> 4) << 16;
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both
+// K-major, N = 64, M = 128.
+constexpr uint32_t kUIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(kUN >> 3) << 17) |
+                             (static_cast<uint32_t>(kUM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits until the barrier's phase `parity` has completed; false after 2 s.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = now_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (now_ns() - t0 > 2000000000ull) return false;
+  }
+}
+
+__global__ void __launch_bounds__(128, 1) k_modp_gemm_umma(const __grid_constant__ UmmaArgs args) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* a_tiles = smem;
+  unsigned char* b_tiles = smem + 4 * kUATile;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kUSmemOps);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kUSmemOps + 64);
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tiles_n = args.n / kUN;
+  const int m0 = (blockIdx.x / tiles_n) * kUM, n0 = (blockIdx.x % tiles_n) * kUN;
+  const int b = blockIdx.y, q = blockIdx.z;
+  const ModParams mp = args.mods.q[q];
+  const uint32_t* A = args.A + (int64_t(q) * args.batch + b) * int64_t(args.m) * args.k;
+  const uint32_t* B = args.B + (int64_t(q) * args.batch + b) * int64_t(args.n) * args.k;
+
+  if (tid == 0) {
+    s_fail = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kUCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+
+  // 2^(8d) mod p
+  uint32_t w[kUDiag];
+  w[0] = 1u % mp.p;
+#pragma unroll
+  for (int d = 1; d < kUDiag; ++d) w[d] = barrett64(static_cast<uint64_t>(w[d - 1]) * (256u % mp.p), mp);
+  uint32_t res[kUN];
+#pragma unroll
+  for (int c = 0; c < kUN; ++c) res[c] = 0u;
+
+  uint32_t parity = 0;
+  for (int k0 = 0; k0 < args.k; k0 += kUK) {
+    // stage the chunk: limb planes in bf16, K-major core-matrix layout
+    for (int e = tid; e < kUM * kUK; e += 128) {
+      const int row = e / kUK, kk = e % kUK;
+      const uint32_t v = A[int64_t(m0 + row) * args.k + k0 + kk];
+      const uint32_t off = umma_off(row, kk);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float f = static_cast<float>((v >> (8 * i)) & 0xFFu);
+        *reinterpret_cast<uint16_t*>(a_tiles + i * kUATile + off) = static_cast<uint16_t>(__float_as_uint(f) >> 16);
+      }
+    }
+    for (int e = tid; e < kUN * kUK; e += 128) {
+      const int row = e / kUK, kk = e % kUK;
+      const uint32_t v = B[int64_t(n0 + row) * args.k + k0 + kk];
+      const uint32_t off = umma_off(row, kk);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float f = static_cast<float>((v >> (8 * j)) & 0xFFu);
+        *reinterpret_cast<uint16_t*>(b_tiles + j * kUBTile + off) = static_cast<uint16_t>(__float_as_uint(f) >> 16);
+      }
+    }
+    // make the generic-proxy writes visible to the tensor core, then issue
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      bool first[kUDiag];
+#pragma unroll
+      for (int d = 0; d < kUDiag; ++d) first[d] = true;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int kk = 0; kk < kUK; kk += 16) {
+            const int d = i + j;
+            const uint64_t ad = umma_desc(smem_u32(a_tiles + i * kUATile + (kk >> 3) * 128));
+            const uint64_t bd = umma_desc(smem_u32(b_tiles + j * kUBTile + (kk >> 3) * 128));
+            const uint32_t acc = first[d] ? 0u : 1u;
+            first[d] = false;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "setp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + d * kUN),
+                "l"(ad), "l"(bd), "r"(kUIdesc), "r"(acc)
+                : "memory");
+          }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(bar))
+                   : "memory");
+    }
+    if (!mbar_wait(smem_u32(bar), parity)) s_fail = 1;
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (s_fail) break;
+    // drain: thread tid reads lane tid, 64 columns of each diagonal
+    const uint32_t lane_addr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+#pragma unroll 1
+    for (int d = 0; d < kUDiag; ++d) {
+      uint32_t r[kUN];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,"
+          "%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, "
+          "[%64];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+            "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+            "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+            "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]),
+            "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
+            "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
+            "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+            "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+          : "r"(lane_addr + d * kUN)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int c = 0; c < kUN; ++c) {
+        const uint32_t s = static_cast<uint32_t>(__uint_as_float(r[c]));  // exact integer < 2^24 < p
+        res[c] = barrett64(static_cast<uint64_t>(res[c]) + static_cast<uint64_t>(s) * w[d], mp);
+      }
+    }
+    // the next chunk's MMAs overwrite the accumulators and the tiles
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  if (s_fail) {
+    if (tid == 0) atomicOr(&g_umma_status, 1u);
+  } else {
+    uint32_t* C = args.C + (int64_t(q) * args.batch + b) * int64_t(args.m) * args.n + int64_t(m0 + tid) * args.n + n0;
+#pragma unroll
+    for (int c = 0; c < kUN; c += 4) *reinterpret_cast<uint4*>(C + c) = make_uint4(res[c], res[c + 1], res[c + 2], res[c + 3]);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kUCols) : "memory");
+}
+
+}  // namespace
+}  // namespace dev
+
+int make_mod_table_checked(tn_semiring_t s, const uint32_t* primes, int32_t nprimes, void* mods);
+
+}  // namespace tn
+
+extern "C" int tn_modp_gemm_umma(const uint32_t* primes, int32_t nprimes, const void* d_a, const void* d_b,
+                                 void* d_c, int32_t batch, int32_t m, int32_t n, int32_t k, void* cuda_stream) {
+  using namespace tn;
+  if (!d_a || !d_b || !d_c || batch < 1 || batch > 65535 || m < dev::kUM || n < dev::kUN || k < dev::kUK ||
+      m % dev::kUM || n % dev::kUN || k % dev::kUK || int64_t(m / dev::kUM) * (n / dev::kUN) > (1ll << 30) ||
+      (reinterpret_cast<uintptr_t>(d_c) & 15))
+    return TN_EINVAL;
+  dev::UmmaArgs a;
+  int rc = make_mod_table_checked(TN_COUNT_MODP, primes, nprimes, &a.mods);
+  if (rc) return rc;
+  a.A = static_cast<const uint32_t*>(d_a);
+  a.B = static_cast<const uint32_t*>(d_b);
+  a.C = static_cast<uint32_t*>(d_c);
+  a.batch = batch;
+  a.m = m;
+  a.n = n;
+  a.k = k;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(dev::k_modp_gemm_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::kUSmem) !=
+        cudaSuccess)
+      return TN_ECUDA;
+    attr = true;
+  }
+  const uint32_t zero = 0;
+  if (cudaMemcpyToSymbolAsync(dev::g_umma_status, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return TN_ECUDA;
+  const dim3 grid(static_cast<unsigned>((m / dev::kUM) * (n / dev::kUN)), static_cast<unsigned>(batch),
+                  static_cast<unsigned>(nprimes));
+  dev::k_modp_gemm_umma<<<grid, 128, dev::kUSmem, st>>>(a);
+  if (cudaGetLastError() != cudaSuccess) return TN_ECUDA;
+  uint32_t status = 0;
+  if (cudaMemcpyFromSymbolAsync(&status, dev::g_umma_status, sizeof(status), 0, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return TN_ECUDA;
+  return status ? TN_ETIMEOUT : TN_OK;
+}

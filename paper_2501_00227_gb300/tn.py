@@ -89,6 +89,7 @@ def lib():
         L.tn_contract_static.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.POINTER(tn_result_t)]
         L.tn_tune_set.argtypes = [i32p, i32]
         L.tn_modp_gemm_limb.argtypes = [u32p, i32, vp, vp, vp, i32, i32, i32, i32, vp]
+        L.tn_modp_gemm_umma.argtypes = [u32p, i32, vp, vp, vp, i32, i32, i32, i32, vp]
         L.tn_plan_step_info.argtypes = [vp, ctypes.c_int, i32, i32p, i32]
         L.tn_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_int, u32p, i32, ctypes.POINTER(vp)]
         L.tn_batch_info.argtypes = [vp, ctypes.POINTER(u64), i32p, i32p, ctypes.POINTER(u64)]
@@ -289,6 +290,16 @@ def tn_modp_gemm_limb(primes, a_ptr: int, b_ptr: int, c_ptr: int, batch: int, m:
     _check(lib().tn_modp_gemm_limb(_u32p(pr), kk, ctypes.c_void_p(a_ptr), ctypes.c_void_p(b_ptr),
                                    ctypes.c_void_p(c_ptr), int(batch), int(m), int(n), int(k),
                                    ctypes.c_void_p(stream)), "tn_modp_gemm_limb")
+
+
+def tn_modp_gemm_umma(primes, a_ptr: int, b_ptr: int, c_ptr: int, batch: int, m: int, n: int, k: int,
+                      stream: int) -> None:
+    """The same product on tcgen05 tensor cores (bf16 limbs, fp32 tensor-memory
+    accumulators); waits for the stream."""
+    pr, kk = _primes(primes)
+    _check(lib().tn_modp_gemm_umma(_u32p(pr), kk, ctypes.c_void_p(a_ptr), ctypes.c_void_p(b_ptr),
+                                   ctypes.c_void_p(c_ptr), int(batch), int(m), int(n), int(k),
+                                   ctypes.c_void_p(stream)), "tn_modp_gemm_umma")
 
 
 def tn_tune_set(entries) -> None:

@@ -1,7 +1,8 @@
-"""Tensor-core limb ablation of the mod-p GEMM (tn_modp_gemm_limb): exact
-against plain integer arithmetic on a small case, and bit-identical to the
-CUDA-core path (tn_contract_pair on the same buffers) on larger ones,
-including k longer than one exact 8192-term diagonal block."""
+"""Tensor-core limb ablations of the mod-p GEMM (tn_modp_gemm_limb on integer
+MMAs, tn_modp_gemm_umma on tcgen05): exact against plain integer arithmetic
+on a small case, and bit-identical to the CUDA-core path (tn_contract_pair
+on the same buffers) on larger ones, including k longer than one exact
+8192-term diagonal block."""
 import numpy as np
 import pytest
 
@@ -26,11 +27,11 @@ def _residues(rng, primes, shape):
     return out
 
 
-def _limb(primes, A, B, batch, m, n, k):
+def _limb(primes, A, B, batch, m, n, k, fn=None):
+    fn = fn or tn.tn_modp_gemm_limb
     a, b = torch.from_numpy(A.view(np.int32)).cuda(), torch.from_numpy(B.view(np.int32)).cuda()
     c = torch.zeros(len(primes) * batch * m * n, dtype=torch.int32, device="cuda")
-    tn.tn_modp_gemm_limb(primes, a.data_ptr(), b.data_ptr(), c.data_ptr(), batch, m, n, k,
-                         torch.cuda.current_stream().cuda_stream)
+    fn(primes, a.data_ptr(), b.data_ptr(), c.data_ptr(), batch, m, n, k, torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     return c.cpu().numpy().view(np.uint32).reshape(len(primes), batch, m, n)
 
@@ -71,3 +72,23 @@ def test_limb_gemm_rejects_unsupported_shapes():
     with pytest.raises(tn.TNError) as ei:
         tn.tn_modp_gemm_limb(tn.PRIMES31[:1], 1, 1, 1, 1, 48, 32, 32, 0)
     assert ei.value.code == tn.TN_EINVAL
+
+
+def test_umma_gemm_exact_small():
+    primes = tn.PRIMES31[:1]
+    rng = np.random.default_rng(11)
+    batch, m, n, k = 1, 128, 64, 64
+    A = _residues(rng, primes, (batch, m, k))
+    B = _residues(rng, primes, (batch, n, k))
+    got = _limb(primes, A, B, batch, m, n, k, tn.tn_modp_gemm_umma)
+    ref = (A[0, 0].astype(object) @ B[0, 0].astype(object).T) % primes[0]
+    assert (got[0, 0].astype(object) == ref).all()
+
+
+@pytest.mark.parametrize("batch,m,n,k,nprimes", [(2, 256, 128, 256, 3), (1, 128, 64, 1024, 4)])
+def test_umma_gemm_matches_integer_mma(batch, m, n, k, nprimes):
+    primes = tn.PRIMES31[:nprimes]
+    rng = np.random.default_rng(batch * 77 + k)
+    A = _residues(rng, primes, (batch, m, k))
+    B = _residues(rng, primes, (batch, n, k))
+    assert (_limb(primes, A, B, batch, m, n, k, tn.tn_modp_gemm_umma) == _limb(primes, A, B, batch, m, n, k)).all()
