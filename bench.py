@@ -305,8 +305,13 @@ def limb_ablation_bench(tn, torch):
     st = torch.cuda.current_stream().cuda_stream
     lk, lm, ln, lb = list(range(0, 10)), list(range(20, 30)), list(range(40, 49)), [60]
 
+    c3 = torch.zeros_like(c1)
+
     def limb():
         tn.tn_modp_gemm_limb(primes, a.data_ptr(), b.data_ptr(), c1.data_ptr(), batch, m, n, k, st)
+
+    def umma():
+        tn.tn_modp_gemm_umma(primes, a.data_ptr(), b.data_ptr(), c3.data_ptr(), batch, m, n, k, st)
 
     def core():
         tn.tn_contract_pair("modp", primes, a.data_ptr(), lk + lm + lb, b.data_ptr(), lk + ln + lb, ln + lm + lb,
@@ -314,19 +319,24 @@ def limb_ablation_bench(tn, torch):
 
     out = {"shape": {"batch": batch, "M": m, "N": n, "K": k, "primes": 4}}
     ops = 4.0 * batch * m * n * k
-    for name, fn in (("tensor_core_u8_limbs", limb), ("cuda_core_tile", core)):
+    for name, fn in (("tcgen05_bf16_limbs", umma), ("mma_sync_u8_limbs", limb), ("cuda_core_tile", core)):
         for _ in range(2):
             fn()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
+        times = []
         for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
             fn()
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / 5
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
         out[name] = {"ms": ms, "tops": ops / (ms * 1e-3) / 1e12}
-    out["equal"] = bool(torch.equal(c1, c2))
-    out["note"] = "tcgen05.mma kind::i8 is rejected by ptxas for sm_103a; the tensor path is mma.sync u8"
+    out["equal"] = bool(torch.equal(c1, c2)) and bool(torch.equal(c3, c2))
+    # tensor work of the tcgen05 path: 16 limb products, 2 flops per multiply-add
+    out["tcgen05_bf16_tflops"] = 16 * 2 * ops / (out["tcgen05_bf16_limbs"]["ms"] * 1e-3) / 1e12
+    out["note"] = ("tcgen05.mma kind::i8 is rejected by ptxas for sm_103a: the tcgen05 path uses kind::f16 on "
+                   "bf16 limbs (exact integers) with fp32 accumulators; mma.sync u8 is the integer tensor path")
     return out
 
 
