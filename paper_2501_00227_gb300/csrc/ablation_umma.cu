@@ -9,15 +9,18 @@
 // 0..255, exact in bf16; a limb product is at most 255^2 and a sum of them
 // stays exact in fp32 while it is below 2^24.  For every chunk of 64 k the
 // 16 limb products (i, j) are accumulated by kind::f16 MMAs (M = 128,
-// N = 64, K = 16, bf16 x bf16 -> fp32) into seven tensor-memory
+// N = 32, K = 16, bf16 x bf16 -> fp32) into seven tensor-memory
 // accumulators, one per diagonal d = i + j (at most 4 x 64 x 255^2 < 2^24,
 // so every accumulator is an exact integer).  After each chunk the
 // accumulators are read back (tcgen05.ld), converted to integers and folded
-// into the residues: res = res + S_d (2^(8d) mod p) mod p, with Barrett
-// reductions (Barrett 1986).
+// into the residues: res = (res + sum_d S_d (2^(8d) mod p)) mod p, one
+// Barrett reduction (Barrett 1986) per entry and chunk.
 //
-// One CTA of 128 threads owns a 128 x 64 block of C for one (prime, batch);
-// thread t owns row t (tensor-memory lane t).  Every wait on the MMA
+// One CTA of 128 threads owns a 128 x 32 block of C for one (prime, batch);
+// thread t owns row t (tensor-memory lane t).  Shared memory and tensor
+// memory are double-buffered: chunk c + 1 is staged (16-byte loads, limbs
+// split in registers) while the tensor cores work on chunk c, and chunk c
+// is drained while they work on chunk c + 1.  Every wait on an MMA
 // completion barrier is bounded (2 s); on a timeout the CTA records it in
 // the status word, releases its tensor memory and returns.
 #include <cuda_runtime.h>
@@ -31,13 +34,13 @@ namespace tn {
 namespace dev {
 namespace {
 
-constexpr int kUM = 128, kUN = 64, kUK = 64;  // C tile rows, columns; k chunk
+constexpr int kUM = 128, kUN = 32, kUK = 64;  // C tile rows, columns; k chunk
 constexpr int kUDiag = 7;                     // limb diagonals 0..6
-constexpr int kUCols = 512;                   // tensor-memory columns allocated (7 x 64 used)
-// shared memory: 4 A limb tiles (128 x 64 bf16) and 4 B limb tiles (64 x 64)
+constexpr int kUCols = 512;                   // tensor-memory columns allocated: 2 buffers x 7 x 32 used
+// one stage of shared memory: 4 A limb tiles (128 x 64 bf16), 4 B limb tiles (32 x 64)
 constexpr int kUATile = kUM * kUK * 2, kUBTile = kUN * kUK * 2;
-constexpr int kUSmemOps = 4 * kUATile + 4 * kUBTile;        // 98304
-constexpr int kUSmem = kUSmemOps + 1024 + 16 * 1024;       // + barrier / slot + slack, > 113 KB: 1 CTA / SM
+constexpr int kUStage = 4 * kUATile + 4 * kUBTile;       // 81920
+constexpr int kUSmem = 2 * kUStage + 1024;               // two stages + barriers / slot: 1 CTA / SM
 
 __device__ uint32_t g_umma_status;
 
@@ -68,7 +71,7 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
 }
 
 // Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both
-// K-major, N = 64, M = 128.
+// K-major, N = 32, M = 128.
 constexpr uint32_t kUIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(kUN >> 3) << 17) |
                              (static_cast<uint32_t>(kUM >> 4) << 24);
 
@@ -99,12 +102,85 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
+// Stages the k chunk starting at k0 into stage buffer `buf` (bf16 limb planes
+// in the K-major core-matrix layout).  Every thread issues all its 16-byte
+// loads before splitting them.
+__device__ __forceinline__ void umma_stage(const uint32_t* A, const uint32_t* B, int lda, int m0, int n0, int k0,
+                                           unsigned char* buf) {
+  constexpr int kA = kUM * kUK / 4 / 128, kB = kUN * kUK / 4 / 128;  // uint4 per thread: 16, 4
+  uint4 va[kA], vb[kB];
+#pragma unroll
+  for (int u = 0; u < kA; ++u) {
+    const int e = threadIdx.x + 128 * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
+    va[u] = __ldg(reinterpret_cast<const uint4*>(A + int64_t(m0 + row) * lda + k0) + k4);
+  }
+#pragma unroll
+  for (int u = 0; u < kB; ++u) {
+    const int e = threadIdx.x + 128 * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
+    vb[u] = __ldg(reinterpret_cast<const uint4*>(B + int64_t(n0 + row) * lda + k0) + k4);
+  }
+#pragma unroll
+  for (int u = 0; u < kA; ++u) {
+    const int e = threadIdx.x + 128 * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
+    const uint32_t off = umma_off(row, 4 * k4);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t b0 = __float_as_uint(static_cast<float>((va[u].x >> (8 * i)) & 0xFFu)) >> 16;
+      const uint32_t b1 = __float_as_uint(static_cast<float>((va[u].y >> (8 * i)) & 0xFFu)) >> 16;
+      const uint32_t b2 = __float_as_uint(static_cast<float>((va[u].z >> (8 * i)) & 0xFFu)) >> 16;
+      const uint32_t b3 = __float_as_uint(static_cast<float>((va[u].w >> (8 * i)) & 0xFFu)) >> 16;
+      *reinterpret_cast<uint2*>(buf + i * kUATile + off) = make_uint2(b0 | (b1 << 16), b2 | (b3 << 16));
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kB; ++u) {
+    const int e = threadIdx.x + 128 * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
+    const uint32_t off = umma_off(row, 4 * k4);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t b0 = __float_as_uint(static_cast<float>((vb[u].x >> (8 * j)) & 0xFFu)) >> 16;
+      const uint32_t b1 = __float_as_uint(static_cast<float>((vb[u].y >> (8 * j)) & 0xFFu)) >> 16;
+      const uint32_t b2 = __float_as_uint(static_cast<float>((vb[u].z >> (8 * j)) & 0xFFu)) >> 16;
+      const uint32_t b3 = __float_as_uint(static_cast<float>((vb[u].w >> (8 * j)) & 0xFFu)) >> 16;
+      *reinterpret_cast<uint2*>(buf + 4 * kUATile + j * kUBTile + off) = make_uint2(b0 | (b1 << 16), b2 | (b3 << 16));
+    }
+  }
+}
+
+// Issues the 16 x 4 MMAs of one staged chunk into accumulator buffer `half`
+// (columns half * 224 + d * 32) and commits them to barrier `bar` (one thread).
+__device__ __forceinline__ void umma_issue(uint32_t tmem, int half, const unsigned char* buf, uint32_t bar) {
+  bool first[kUDiag];
+#pragma unroll
+  for (int d = 0; d < kUDiag; ++d) first[d] = true;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int kk = 0; kk < kUK; kk += 16) {
+        const int d = i + j;
+        const uint64_t ad = umma_desc(smem_u32(buf + i * kUATile + (kk >> 3) * 128));
+        const uint64_t bd = umma_desc(smem_u32(buf + 4 * kUATile + j * kUBTile + (kk >> 3) * 128));
+        const uint32_t acc = first[d] ? 0u : 1u;
+        first[d] = false;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                tmem + static_cast<uint32_t>(half * kUDiag * kUN + d * kUN)),
+            "l"(ad), "l"(bd), "r"(kUIdesc), "r"(acc)
+            : "memory");
+      }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
 __global__ void __launch_bounds__(128, 1) k_modp_gemm_umma(const __grid_constant__ UmmaArgs args) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* a_tiles = smem;
-  unsigned char* b_tiles = smem + 4 * kUATile;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kUSmemOps);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kUSmemOps + 64);
+  unsigned char* stage0 = smem;
+  unsigned char* stage1 = smem + kUStage;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * kUStage);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 2 * kUStage + 64);
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int tiles_n = args.n / kUN;
@@ -113,10 +189,12 @@ __global__ void __launch_bounds__(128, 1) k_modp_gemm_umma(const __grid_constant
   const ModParams mp = args.mods.q[q];
   const uint32_t* A = args.A + (int64_t(q) * args.batch + b) * int64_t(args.m) * args.k;
   const uint32_t* B = args.B + (int64_t(q) * args.batch + b) * int64_t(args.n) * args.k;
+  const uint32_t bar0 = smem_u32(bars), bar1 = smem_u32(bars + 1);
 
   if (tid == 0) {
     s_fail = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -139,94 +217,51 @@ __global__ void __launch_bounds__(128, 1) k_modp_gemm_umma(const __grid_constant
 #pragma unroll
   for (int c = 0; c < kUN; ++c) res[c] = 0u;
 
-  uint32_t parity = 0;
-  for (int k0 = 0; k0 < args.k; k0 += kUK) {
-    // stage the chunk: limb planes in bf16, K-major core-matrix layout
-    for (int e = tid; e < kUM * kUK; e += 128) {
-      const int row = e / kUK, kk = e % kUK;
-      const uint32_t v = A[int64_t(m0 + row) * args.k + k0 + kk];
-      const uint32_t off = umma_off(row, kk);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float f = static_cast<float>((v >> (8 * i)) & 0xFFu);
-        *reinterpret_cast<uint16_t*>(a_tiles + i * kUATile + off) = static_cast<uint16_t>(__float_as_uint(f) >> 16);
-      }
-    }
-    for (int e = tid; e < kUN * kUK; e += 128) {
-      const int row = e / kUK, kk = e % kUK;
-      const uint32_t v = B[int64_t(n0 + row) * args.k + k0 + kk];
-      const uint32_t off = umma_off(row, kk);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float f = static_cast<float>((v >> (8 * j)) & 0xFFu);
-        *reinterpret_cast<uint16_t*>(b_tiles + j * kUBTile + off) = static_cast<uint16_t>(__float_as_uint(f) >> 16);
-      }
-    }
-    // make the generic-proxy writes visible to the tensor core, then issue
+  const int nch = args.k / kUK;
+  umma_stage(A, B, args.k, m0, n0, 0, stage0);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (tid == 0) umma_issue(tmem, 0, stage0, bar0);
+  const uint32_t lane_addr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  for (int c = 0; c < nch; ++c) {
+    const int half = c & 1;
+    // stage the next chunk while the tensor cores work on this one (its
+    // buffer's previous MMAs completed one iteration ago)
+    if (c + 1 < nch) umma_stage(A, B, args.k, m0, n0, (c + 1) * kUK, half ? stage0 : stage1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (!mbar_wait(half ? bar1 : bar0, static_cast<uint32_t>((c >> 1) & 1))) s_fail = 1;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (tid == 0) {
-      bool first[kUDiag];
-#pragma unroll
-      for (int d = 0; d < kUDiag; ++d) first[d] = true;
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int kk = 0; kk < kUK; kk += 16) {
-            const int d = i + j;
-            const uint64_t ad = umma_desc(smem_u32(a_tiles + i * kUATile + (kk >> 3) * 128));
-            const uint64_t bd = umma_desc(smem_u32(b_tiles + j * kUBTile + (kk >> 3) * 128));
-            const uint32_t acc = first[d] ? 0u : 1u;
-            first[d] = false;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "setp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + d * kUN),
-                "l"(ad), "l"(bd), "r"(kUIdesc), "r"(acc)
-                : "memory");
-          }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(bar))
-                   : "memory");
-    }
-    if (!mbar_wait(smem_u32(bar), parity)) s_fail = 1;
-    parity ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    __syncthreads();
     if (s_fail) break;
-    // drain: thread tid reads lane tid, 64 columns of each diagonal
-    const uint32_t lane_addr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+    if (c + 1 < nch && tid == 0) umma_issue(tmem, half ^ 1, half ? stage0 : stage1, half ? bar0 : bar1);
+    // drain this chunk's accumulators (lane tid) while the next chunk runs
+    uint64_t t[kUN];
+#pragma unroll
+    for (int col = 0; col < kUN; ++col) t[col] = res[col];
 #pragma unroll 1
     for (int d = 0; d < kUDiag; ++d) {
       uint32_t r[kUN];
       asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,"
-          "%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, "
-          "[%64];"
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
             "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
             "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
             "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-            "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]),
-            "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
-            "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
-            "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
-            "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-          : "r"(lane_addr + d * kUN)
+            "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(lane_addr + static_cast<uint32_t>(half * kUDiag * kUN + d * kUN))
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int c = 0; c < kUN; ++c) {
-        const uint32_t s = static_cast<uint32_t>(__uint_as_float(r[c]));  // exact integer < 2^24 < p
-        res[c] = barrett64(static_cast<uint64_t>(res[c]) + static_cast<uint64_t>(s) * w[d], mp);
-      }
+      for (int col = 0; col < kUN; ++col)  // exact integers < 2^24; the sum stays below 2^59
+        t[col] += static_cast<uint64_t>(static_cast<uint32_t>(__uint_as_float(r[col]))) * w[d];
     }
-    // the next chunk's MMAs overwrite the accumulators and the tiles
+#pragma unroll
+    for (int col = 0; col < kUN; ++col) res[col] = barrett64(t[col], mp);
+    // the drained buffer is overwritten by the MMAs issued next iteration
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -256,7 +291,7 @@ extern "C" int tn_modp_gemm_umma(const uint32_t* primes, int32_t nprimes, const 
   using namespace tn;
   if (!d_a || !d_b || !d_c || batch < 1 || batch > 65535 || m < dev::kUM || n < dev::kUN || k < dev::kUK ||
       m % dev::kUM || n % dev::kUN || k % dev::kUK || int64_t(m / dev::kUM) * (n / dev::kUN) > (1ll << 30) ||
-      (reinterpret_cast<uintptr_t>(d_c) & 15))
+      ((reinterpret_cast<uintptr_t>(d_a) | reinterpret_cast<uintptr_t>(d_b) | reinterpret_cast<uintptr_t>(d_c)) & 15))
     return TN_EINVAL;
   dev::UmmaArgs a;
   int rc = make_mod_table_checked(TN_COUNT_MODP, primes, nprimes, &a.mods);
