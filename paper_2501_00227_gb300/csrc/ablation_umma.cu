@@ -16,8 +16,9 @@
 // into the residues: res = (res + sum_d S_d (2^(8d) mod p)) mod p, one
 // Barrett reduction (Barrett 1986) per entry and chunk.
 //
-// One CTA of 128 threads owns a 128 x 32 block of C for one (prime, batch);
-// thread t owns row t (tensor-memory lane t).  Shared memory and tensor
+// One CTA of 256 threads owns a 128 x 32 block of C for one (prime, batch);
+// warps w and w + 4 read lanes 32 (w % 4) .. + 31 (rows of C), each half of
+// the columns.  Shared memory and tensor
 // memory are double-buffered: chunk c + 1 is staged (16-byte loads, limbs
 // split in registers) while the tensor cores work on chunk c, and chunk c
 // is drained while they work on chunk c + 1.  Every wait on an MMA
@@ -41,6 +42,7 @@ constexpr int kUCols = 512;                   // tensor-memory columns allocated
 constexpr int kUATile = kUM * kUK * 2, kUBTile = kUN * kUK * 2;
 constexpr int kUStage = 4 * kUATile + 4 * kUBTile;       // 81920
 constexpr int kUSmem = 2 * kUStage + 1024;               // two stages + barriers / slot: 1 CTA / SM
+constexpr int kUThreads = 256;                           // 8 warps; warps w and w + 4 share lane quadrant w % 4
 
 __device__ uint32_t g_umma_status;
 
@@ -107,21 +109,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 // loads before splitting them.
 __device__ __forceinline__ void umma_stage(const uint32_t* A, const uint32_t* B, int lda, int m0, int n0, int k0,
                                            unsigned char* buf) {
-  constexpr int kA = kUM * kUK / 4 / 128, kB = kUN * kUK / 4 / 128;  // uint4 per thread: 16, 4
+  constexpr int kA = kUM * kUK / 4 / kUThreads, kB = kUN * kUK / 4 / kUThreads;  // uint4 per thread: 8, 2
   uint4 va[kA], vb[kB];
 #pragma unroll
   for (int u = 0; u < kA; ++u) {
-    const int e = threadIdx.x + 128 * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
+    const int e = threadIdx.x + kUThreads * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
     va[u] = __ldg(reinterpret_cast<const uint4*>(A + int64_t(m0 + row) * lda + k0) + k4);
   }
 #pragma unroll
   for (int u = 0; u < kB; ++u) {
-    const int e = threadIdx.x + 128 * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
+    const int e = threadIdx.x + kUThreads * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
     vb[u] = __ldg(reinterpret_cast<const uint4*>(B + int64_t(n0 + row) * lda + k0) + k4);
   }
 #pragma unroll
   for (int u = 0; u < kA; ++u) {
-    const int e = threadIdx.x + 128 * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
+    const int e = threadIdx.x + kUThreads * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
     const uint32_t off = umma_off(row, 4 * k4);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -134,7 +136,7 @@ __device__ __forceinline__ void umma_stage(const uint32_t* A, const uint32_t* B,
   }
 #pragma unroll
   for (int u = 0; u < kB; ++u) {
-    const int e = threadIdx.x + 128 * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
+    const int e = threadIdx.x + kUThreads * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
     const uint32_t off = umma_off(row, 4 * k4);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -175,7 +177,7 @@ __device__ __forceinline__ void umma_issue(uint32_t tmem, int half, const unsign
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__global__ void __launch_bounds__(128, 1) k_modp_gemm_umma(const __grid_constant__ UmmaArgs args) {
+__global__ void __launch_bounds__(kUThreads, 1) k_modp_gemm_umma(const __grid_constant__ UmmaArgs args) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* stage0 = smem;
   unsigned char* stage1 = smem + kUStage;
@@ -213,9 +215,11 @@ __global__ void __launch_bounds__(128, 1) k_modp_gemm_umma(const __grid_constant
   w[0] = 1u % mp.p;
 #pragma unroll
   for (int d = 1; d < kUDiag; ++d) w[d] = barrett64(static_cast<uint64_t>(w[d - 1]) * (256u % mp.p), mp);
-  uint32_t res[kUN];
+  constexpr int kUH = kUN / 2;  // columns drained per thread
+  uint32_t res[kUH];
 #pragma unroll
-  for (int c = 0; c < kUN; ++c) res[c] = 0u;
+  for (int c = 0; c < kUH; ++c) res[c] = 0u;
+  const int col0 = (warp >> 2) * kUH, row = (warp & 3) * 32 + (tid & 31);
 
   const int nch = args.k / kUK;
   umma_stage(A, B, args.k, m0, n0, 0, stage0);
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(128, 1) k_modp_gemm_umma(const __grid_constant
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (tid == 0) umma_issue(tmem, 0, stage0, bar0);
-  const uint32_t lane_addr = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  const uint32_t lane_addr = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
   for (int c = 0; c < nch; ++c) {
     const int half = c & 1;
     // stage the next chunk while the tensor cores work on this one (its
@@ -237,30 +241,27 @@ __global__ void __launch_bounds__(128, 1) k_modp_gemm_umma(const __grid_constant
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (s_fail) break;
     if (c + 1 < nch && tid == 0) umma_issue(tmem, half ^ 1, half ? stage0 : stage1, half ? bar0 : bar1);
-    // drain this chunk's accumulators (lane tid) while the next chunk runs
-    uint64_t t[kUN];
+    // drain this chunk's accumulators while the next chunk runs: thread t
+    // reads lane 32 (w % 4) + t % 32, columns 16 (w / 4) .. + 15 of each diagonal
+    uint64_t t[kUH];
 #pragma unroll
-    for (int col = 0; col < kUN; ++col) t[col] = res[col];
+    for (int col = 0; col < kUH; ++col) t[col] = res[col];
 #pragma unroll 1
     for (int d = 0; d < kUDiag; ++d) {
-      uint32_t r[kUN];
+      uint32_t r[kUH];
       asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-            "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-            "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-            "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(lane_addr + static_cast<uint32_t>(half * kUDiag * kUN + d * kUN))
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(lane_addr + static_cast<uint32_t>(half * kUDiag * kUN + d * kUN + col0))
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int col = 0; col < kUN; ++col)  // exact integers < 2^24; the sum stays below 2^59
+      for (int col = 0; col < kUH; ++col)  // exact integers < 2^24; the sum stays below 2^59
         t[col] += static_cast<uint64_t>(static_cast<uint32_t>(__uint_as_float(r[col]))) * w[d];
     }
 #pragma unroll
-    for (int col = 0; col < kUN; ++col) res[col] = barrett64(t[col], mp);
+    for (int col = 0; col < kUH; ++col) res[col] = barrett64(t[col], mp);
     // the drained buffer is overwritten by the MMAs issued next iteration
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -269,9 +270,10 @@ __global__ void __launch_bounds__(128, 1) k_modp_gemm_umma(const __grid_constant
   if (s_fail) {
     if (tid == 0) atomicOr(&g_umma_status, 1u);
   } else {
-    uint32_t* C = args.C + (int64_t(q) * args.batch + b) * int64_t(args.m) * args.n + int64_t(m0 + tid) * args.n + n0;
+    uint32_t* C = args.C + (int64_t(q) * args.batch + b) * int64_t(args.m) * args.n + int64_t(m0 + row) * args.n +
+                  n0 + col0;
 #pragma unroll
-    for (int c = 0; c < kUN; c += 4) *reinterpret_cast<uint4*>(C + c) = make_uint4(res[c], res[c + 1], res[c + 2], res[c + 3]);
+    for (int c = 0; c < kUH; c += 4) *reinterpret_cast<uint4*>(C + c) = make_uint4(res[c], res[c + 1], res[c + 2], res[c + 3]);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -317,7 +319,7 @@ extern "C" int tn_modp_gemm_umma(const uint32_t* primes, int32_t nprimes, const 
     return TN_ECUDA;
   const dim3 grid(static_cast<unsigned>((m / dev::kUM) * (n / dev::kUN)), static_cast<unsigned>(batch),
                   static_cast<unsigned>(nprimes));
-  dev::k_modp_gemm_umma<<<grid, 128, dev::kUSmem, st>>>(a);
+  dev::k_modp_gemm_umma<<<grid, dev::kUThreads, dev::kUSmem, st>>>(a);
   if (cudaGetLastError() != cudaSuccess) return TN_ECUDA;
   uint32_t status = 0;
   if (cudaMemcpyFromSymbolAsync(&status, dev::g_umma_status, sizeof(status), 0, cudaMemcpyDeviceToHost, st) !=
