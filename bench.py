@@ -251,7 +251,7 @@ def batching_bench(tn, torch, count: int = 4096):
     return out
 
 
-def largest_bench(tn, torch, peak_tops: float):
+def largest_bench(tn, torch, peak_tops: float, autotune: bool = True):
     """The largest tropical contractions of the configs: King's subgraph 20 x 20
     at filling 0.8 (seeds 1-3, ~320 vertices, tc ~ 2^31), tropical int32, one
     executor launch each, L2 flushed before each launch; Tops/s and fraction of
@@ -262,6 +262,12 @@ def largest_bench(tn, torch, peak_tops: float):
     rows = []
     for seed in (1, 2, 3):
         p = tn.Plan(*graphgen.kings_subgraph(20, 0.8, seed), nrepeat=10, seed=1)
+        tuned = None
+        if autotune:  # measured tile shapes for this instance's steps, before timing
+            from paper_2501_00227_gb300 import tune
+            r = tune.autotune([p], "tropical_i32", None, keep=_current_rows())
+            _current_rows(r["rows"])
+            tuned = r["kept"]
         ws = torch.empty(p.workspace_bytes("tropical_i32"), dtype=torch.uint8, device="cuda")
         raw = torch.zeros(tn.TN_RAW_BYTES, dtype=torch.uint8, device="cuda")
         for _ in range(2):
@@ -280,7 +286,7 @@ def largest_bench(tn, torch, peak_tops: float):
         tc = p.info("tropical_i32")["tc"]
         tops = tc / (statistics.median(ms) * 1e-3) / 1e12
         rows.append({"seed": seed, "log2_tc": float(np.log2(tc)), "ms": statistics.median(ms), "tops": tops,
-                     "frac": tops / peak_tops})
+                     "frac": tops / peak_tops, "autotuned": tuned})
         p.close()
     out["instances"] = rows
     out["best_frac"] = max(r["frac"] for r in rows)
@@ -565,7 +571,7 @@ def run_tn(args):
     # one executor launch per contraction
     line["gpu_launches"] = args.steps * len(jobs)
     if rank == 0 and not args.no_extras:
-        line["largest_tropical"] = largest_bench(tn, torch, peak_ops)
+        line["largest_tropical"] = largest_bench(tn, torch, peak_ops, autotune=not args.no_autotune)
         line["modp_tensor_core_ablation"] = limb_ablation_bench(tn, torch)
     if rank == 0 and not args.no_batching:
         line["batching"] = batching_bench(tn, torch)

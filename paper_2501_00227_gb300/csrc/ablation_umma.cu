@@ -104,6 +104,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
+// Element e of a staged chunk (16-byte group k4 of row `row`): the 16 threads
+// of a half-warp cover 8 rows x 2 adjacent groups, i.e. 128 distinct bytes
+// of one core-matrix column, so their shared-memory stores are free of bank
+// conflicts, and a warp reads 64 contiguous bytes of 8 rows from global
+// memory.
+__device__ __forceinline__ int umma_k4(int e) { return (((e >> 4) & 7) << 1) | (e & 1); }
+__device__ __forceinline__ int umma_row(int e) { return ((e >> 1) & 7) | ((e >> 7) << 3); }
+
 // Stages the k chunk starting at k0 into stage buffer `buf` (bf16 limb planes
 // in the K-major core-matrix layout).  Every thread issues all its 16-byte
 // loads before splitting them.
@@ -113,17 +121,17 @@ __device__ __forceinline__ void umma_stage(const uint32_t* A, const uint32_t* B,
   uint4 va[kA], vb[kB];
 #pragma unroll
   for (int u = 0; u < kA; ++u) {
-    const int e = threadIdx.x + kUThreads * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
+    const int e = threadIdx.x + kUThreads * u, row = umma_row(e), k4 = umma_k4(e);
     va[u] = __ldg(reinterpret_cast<const uint4*>(A + int64_t(m0 + row) * lda + k0) + k4);
   }
 #pragma unroll
   for (int u = 0; u < kB; ++u) {
-    const int e = threadIdx.x + kUThreads * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
+    const int e = threadIdx.x + kUThreads * u, row = umma_row(e), k4 = umma_k4(e);
     vb[u] = __ldg(reinterpret_cast<const uint4*>(B + int64_t(n0 + row) * lda + k0) + k4);
   }
 #pragma unroll
   for (int u = 0; u < kA; ++u) {
-    const int e = threadIdx.x + kUThreads * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
+    const int e = threadIdx.x + kUThreads * u, row = umma_row(e), k4 = umma_k4(e);
     const uint32_t off = umma_off(row, 4 * k4);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -136,7 +144,7 @@ __device__ __forceinline__ void umma_stage(const uint32_t* A, const uint32_t* B,
   }
 #pragma unroll
   for (int u = 0; u < kB; ++u) {
-    const int e = threadIdx.x + kUThreads * u, row = e / (kUK / 4), k4 = e % (kUK / 4);
+    const int e = threadIdx.x + kUThreads * u, row = umma_row(e), k4 = umma_k4(e);
     const uint32_t off = umma_off(row, 4 * k4);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
