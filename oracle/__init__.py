@@ -65,6 +65,7 @@ def _load():
             lib.or_contract_tropical.argtypes = [I, i32p, I, i32p, I, i64p]
             lib.or_contract_counting.argtypes = [I, i32p, I, i32p, I, i64p, u64p, u64p]
             lib.or_contract_modp.argtypes = [I, i32p, I, i32p, I, u32p, I, u64p]
+            lib.or_contract_modp_x.argtypes = [I, i32p, I, i32p, I, u32p, u32p, I, u64p]
             lib.or_pair_tropical.argtypes = [i64p, i32p, I, i64p, i32p, I, i32p, I, i64p]
             lib.or_pair_counting.argtypes = [i64p, u64p, i32p, I, i64p, u64p, i32p, I, i32p, I, i64p, u64p, u64p]
             lib.or_pair_modp.argtypes = [u64p, i32p, I, u64p, i32p, I, i32p, I, ctypes.c_uint32, u64p]
@@ -161,6 +162,56 @@ def count_modp(n, edges, order, primes=PRIMES31[:3]):
                                      _p(pr, ctypes.c_uint32), len(pr), _p(res, ctypes.c_uint64)),
            "contract_modp")
     return [int(x) for x in res]
+
+
+def evaluate_modp(n, edges, order, primes, xs):
+    """The independence polynomial I(G, x) of Eq. 13 evaluated at xs[q]
+    modulo primes[q]: the network of Eqs. 6-7 with vertex tensors W = [1, x]
+    (e^{beta w} = x) contracted in the ring of integers mod p."""
+    n, e, m = _graph(n, edges)
+    o, k = _order(order)
+    pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint32))
+    xv = np.ascontiguousarray(np.asarray(xs, dtype=np.uint32))
+    res = np.zeros(len(pr), dtype=np.uint64)
+    _check(_load().or_contract_modp_x(n, _p(e, ctypes.c_int32), m, _p(o, ctypes.c_int32), k,
+                                       _p(pr, ctypes.c_uint32), _p(xv, ctypes.c_uint32), len(pr),
+                                       _p(res, ctypes.c_uint64)), "contract_modp_x")
+    return [int(x) for x in res]
+
+
+def interpolate_modp(xs, ys, p):
+    """Coefficients (lowest first) of the polynomial of degree < len(xs)
+    through the points (xs[i], ys[i]) modulo the prime p (Lagrange's form,
+    expanded term by term)."""
+    n = len(xs)
+    coeffs = [0] * n
+    for i in range(n):
+        # basis polynomial prod_{j != i} (x - xs[j]) / (xs[i] - xs[j])
+        basis = [1]
+        denom = 1
+        for j in range(n):
+            if j == i:
+                continue
+            basis = [(a - xs[j] * b) % p for a, b in zip([0] + basis, basis + [0])]
+            denom = denom * (xs[i] - xs[j]) % p
+        scale = ys[i] * pow(denom, -1, p) % p
+        for d in range(n):
+            coeffs[d] = (coeffs[d] + scale * basis[d]) % p
+    return coeffs
+
+
+def independence_polynomial(n, edges, order, primes):
+    """Exact coefficients c_0 .. c_n of the independence polynomial (Eq. 13;
+    the finite-field method of Sec. 6.2): evaluations at x = 1 .. n+1 modulo
+    each prime, Lagrange interpolation modulo each prime, CRT per
+    coefficient.  Exact when prod(primes) exceeds the largest coefficient
+    (at most 2^n)."""
+    xs = list(range(1, n + 2))
+    per_prime = []
+    for p in primes:
+        ys = [evaluate_modp(n, edges, order, [p], [x])[0] for x in xs]
+        per_prime.append(interpolate_modp(xs, ys, int(p)))
+    return [crt([c[d] for c in per_prime], primes)[0] for d in range(n + 1)]
 
 
 def crt(residues, primes):

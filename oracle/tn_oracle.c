@@ -138,10 +138,13 @@ static int check_order(int T, const int32_t *order, int nsteps) {
     return rc;
 }
 
-/* Leaf tensors of the IS network, Eqs. (5)-(7) with unit weights:
+/* Leaf tensors of the IS network, Eqs. (5)-(7):
  *   B(n_u, n_v) = [[one, one], [one, zero]]      (edge)
  *   W(n_v)      = [one, x]  with x = e^{beta w}:  tropical 1, counting (1,1),
- *                                                 counting all IS (beta = 0): 1. */
+ *                 counting all IS (beta = 0): 1; the independence
+ *                 polynomial I(G, x) of Eq. 13 evaluated at x: x mod p in
+ *                 each prime slot (g_vertex_x == NULL: x = 1). */
+static const uint32_t *g_vertex_x = NULL;
 static int make_leaf(tensor_t *t, int kind, const uint32_t *primes, int nprimes, int is_edge,
                      int32_t u, int32_t v) {
     t->rank = is_edge ? 2 : 1;
@@ -162,7 +165,11 @@ static int make_leaf(tensor_t *t, int kind, const uint32_t *primes, int nprimes,
             else { d[x].n = occupied ? 1 : 0; d[x].c = 1; }
         } else {
             uint64_t *d = t->data;
-            for (int q = 0; q < nprimes; q++) d[x * nprimes + q] = both ? 0 : 1 % primes[q];
+            for (int q = 0; q < nprimes; q++) {
+                uint64_t val = both ? 0 : 1 % primes[q];
+                if (occupied && g_vertex_x) val = g_vertex_x[q] % primes[q];
+                d[x * nprimes + q] = val;
+            }
         }
     }
     return OR_OK;
@@ -367,6 +374,16 @@ int or_contract_counting(int n, const int32_t *edges, int m, const int32_t *orde
 int or_contract_modp(int n, const int32_t *edges, int m, const int32_t *order, int nsteps,
                      const uint32_t *primes, int nprimes, uint64_t *residues) {
     return contract_network(OR_MODP, primes, nprimes, n, edges, m, order, nsteps, residues);
+}
+
+/* As or_contract_modp with vertex tensors W = [1, xs[q]] in prime slot q:
+ * residues[q] = sum over independent sets S of xs[q]^|S|  mod primes[q]. */
+int or_contract_modp_x(int n, const int32_t *edges, int m, const int32_t *order, int nsteps,
+                       const uint32_t *primes, const uint32_t *xs, int nprimes, uint64_t *residues) {
+    g_vertex_x = xs;
+    int rc = contract_network(OR_MODP, primes, nprimes, n, edges, m, order, nsteps, residues);
+    g_vertex_x = NULL;
+    return rc;
 }
 
 /* One pairwise contraction on caller tensors (labels as above, LC given). */

@@ -344,3 +344,81 @@ def test_crt_roundtrip():
             x = int(rng.integers(0, 2 ** 62)) * int(rng.integers(0, 2 ** 62)) * int(rng.integers(1, 2 ** 62))
             x %= M
             assert O.crt([x % p for p in pr], pr) == (x, M)
+
+
+# ---------------------------------------------------------------- independence polynomial (Eq. 13)
+
+def test_petersen_polynomial_printed():
+    """Sec. 5.3 / Sec. 6.2 print I(Petersen, x) = 1 + 10x + 30x^2 + 30x^3 + 5x^4
+    (GraphPolynomial, finite-field method)."""
+    gd = _gold("petersen.json")
+    n, e = g.petersen()
+    o = O.greedy_order(n, e, nrepeat=4, seed=1)
+    poly = O.independence_polynomial(n, e, o, O.PRIMES31[:1])
+    want = gd["independence_polynomial"]
+    assert poly == want + [0] * (n + 1 - len(want))
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 20, 45])
+def test_path_polynomial_closed_form(n):
+    """Choosing k pairwise non-adjacent vertices of a path of n vertices:
+    c_k = C(n - k + 1, k)."""
+    nn, e = g.path(n)
+    o = O.sweep_order(nn, e)
+    poly = O.independence_polynomial(nn, e, o, O.PRIMES31[:2])
+    assert poly == [math.comb(n - k + 1, k) for k in range(n + 1)]
+
+
+@pytest.mark.parametrize("n", [3, 4, 9, 30])
+def test_cycle_polynomial_closed_form(n):
+    """On a cycle of n vertices: c_0 = 1, c_k = n / (n - k) * C(n - k, k)."""
+    nn, e = g.cycle(n)
+    o = O.greedy_order(nn, e, nrepeat=2, seed=n)
+    poly = O.independence_polynomial(nn, e, o, O.PRIMES31[:1])
+    want = [1] + [n * math.comb(n - k, k) // (n - k) for k in range(1, n)] + [0]
+    assert poly == want
+
+
+@pytest.mark.parametrize("n", [1, 6, 40])
+def test_empty_and_complete_polynomials(n):
+    """No edges: (1 + x)^n.  Complete graph: 1 + n x."""
+    nn, e = g.empty(n)
+    o = O.greedy_order(nn, e, nrepeat=1, seed=2)
+    assert O.independence_polynomial(nn, e, o, O.PRIMES31[:2]) == [math.comb(n, k) for k in range(n + 1)]
+    if n >= 2:
+        nn, e = g.complete(n)
+        o = O.greedy_order(nn, e, nrepeat=1, seed=2)
+        assert O.independence_polynomial(nn, e, o, O.PRIMES31[:1]) == [1, n] + [0] * (n - 1)
+
+
+@pytest.mark.parametrize("name,graph", _small_graphs()[:5], ids=lambda x: x if isinstance(x, str) else "")
+def test_polynomial_equals_bruteforce(name, graph):
+    n, e = graph
+    o = O.greedy_order(n, e, nrepeat=2, seed=9)
+    assert O.independence_polynomial(n, e, o, O.PRIMES31[:1]) == O.bruteforce_poly(n, e)
+
+
+def test_weighted_evaluation_matches_bruteforce_sum():
+    """Vertex weight x in each prime slot: the contraction equals
+    sum_S x^|S| mod p over the brute-force size counts, for large x (no
+    confusion with the edge entries) and for repeated primes."""
+    n, e = g.erdos_renyi(14, 0.25, 3)
+    poly = O.bruteforce_poly(n, e)
+    o = O.greedy_order(n, e, nrepeat=2, seed=1)
+    p0, p1 = O.PRIMES31[0], O.PRIMES31[3]
+    primes = [p0, p0, p0, p1, p1]
+    xs = [0, 2, p0 - 1, 1 << 30, 12345]
+    got = O.evaluate_modp(n, e, o, primes, xs)
+    assert got == [sum(c * pow(x, k, p) for k, c in enumerate(poly)) % p for p, x in zip(primes, xs)]
+    assert got[0] == 1                                  # only the empty set survives x = 0
+
+
+def test_interpolation_recovers_random_polynomials():
+    """Lagrange interpolation mod p inverts evaluation at distinct points."""
+    rng = np.random.default_rng(8)
+    p = O.PRIMES31[2]
+    for d in (0, 1, 5, 17):
+        coeffs = [int(c) for c in rng.integers(0, p, size=d + 1)]
+        xs = list(range(3, 3 + d + 1))
+        ys = [sum(c * pow(x, k, p) for k, c in enumerate(coeffs)) % p for x in xs]
+        assert O.interpolate_modp(xs, ys, p) == coeffs
