@@ -201,6 +201,44 @@ int tn_contract_pair(tn_semiring_t semiring, const uint32_t *primes, int32_t npr
                      const void *d_b, const int32_t *lb, int32_t rb,
                      const int32_t *lc, int32_t rc, void *d_c, void *cuda_stream);
 
+/* Weighted evaluation on the mod-p path.  Slot q is the pair (primes[q],
+ * xs[q]): the network's vertex tensors become W = [1, xs[q] mod primes[q]]
+ * (Eq. 7 with e^{beta w} = x; the edge tensors stay the 0/1 matrix of Eq. 6),
+ * so residues[q] = I(G, xs[q]) mod primes[q], where I(G, x) = sum_k c_k x^k
+ * is the independence polynomial (Eq. 13, Sec. 6.2; c_k = number of
+ * independent sets of size k).  xs[q] = 1 gives the count of all sets.
+ * nslots in 1..TN_MAX_PRIMES; moduli in [2, 2^31), repeats allowed (several
+ * points per prime).  d_workspace: at least tn_plan_info(plan,
+ * TN_COUNT_MODP, nslots).peak_bytes[TN_COUNT_MODP - 1] bytes, 256-byte
+ * aligned, caller-owned.  Synchronous (waits for cuda_stream).  Errors:
+ * TN_EINVAL, TN_ENOMEM (workspace too small), TN_ECUDA, TN_ETIMEOUT. */
+int tn_contract_modp_x(tn_plan_t plan, const uint32_t *primes, const uint32_t *xs, int32_t nslots,
+                       void *d_workspace, size_t ws_bytes, void *cuda_stream, uint32_t *residues);
+
+/* The independence polynomial (the GraphPolynomial property of Sec. 5.3, by
+ * the finite-field method of Sec. 6.2): I(G, x) is evaluated on the GPU at
+ * x = 1 .. degree + 1 modulo every prime (tn_contract_modp_x, up to
+ * TN_MAX_PRIMES evaluations per contraction), the coefficients c_0 ..
+ * c_degree are interpolated modulo each prime on the host (Newton divided
+ * differences), and combined by Garner's CRT.
+ *   primes   nprimes distinct primes in [3, 2^31), each > degree + 1;
+ *            nprimes in 1..TN_POLY_MAX_PRIMES.  The result is exact when
+ *            prod primes > max_k c_k (2^n always suffices).
+ *   degree   at least the independence number alpha(G) (the tropical
+ *            contraction's result; n always suffices), at most n.
+ *   d_workspace  as for tn_contract_modp_x with nslots =
+ *            min(TN_MAX_PRIMES, nprimes * (degree + 1)).
+ * Outputs (each may be NULL): coeff_residues[k * nprimes + q] = c_k mod
+ * primes[q]; coeff_limbs[k * TN_POLY_LIMBS ..] = c_k mod prod primes as
+ * little-endian 32-bit limbs (zero-padded), coeff_nlimbs[k] its significant
+ * limbs; k = 0 .. degree.  Synchronous; errors as tn_contract_modp_x.
+ * (No counterpart in the paper's API: it returns a polynomial object.) */
+#define TN_POLY_MAX_PRIMES 32
+#define TN_POLY_LIMBS 32
+int tn_independence_polynomial(tn_plan_t plan, const uint32_t *primes, int32_t nprimes, int32_t degree,
+                               void *d_workspace, size_t ws_bytes, void *cuda_stream,
+                               uint32_t *coeff_residues, uint32_t *coeff_limbs, int32_t *coeff_nlimbs);
+
 /* Measured launch shapes.  The paper leaves the kernel schedule to the
  * contraction backend; this table lets an autotuner (tune.py in the Python
  * package) replace the host's estimate for given step shapes.  entries holds

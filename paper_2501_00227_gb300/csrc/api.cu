@@ -55,6 +55,23 @@ int make_mods(tn_semiring_t s, const uint32_t* primes, int32_t nprimes, ModTable
     mt->q[i].p = p;
     mt->q[i].r32 = static_cast<uint32_t>((uint64_t(1) << 32) % p);
     mt->q[i].mu = ~0ull / p;
+    mt->q[i].x = 1;
+  }
+  return TN_OK;
+}
+
+// Prime slots (primes[q], xs[q]) of a weighted mod-p contraction: the moduli
+// need not be distinct (several points per prime), only each in [2, 2^31).
+int make_mods_slots(const uint32_t* primes, const uint32_t* xs, int32_t nslots, ModTable* mt) {
+  std::memset(mt, 0, sizeof(*mt));
+  if (primes == nullptr || xs == nullptr || nslots < 1 || nslots > TN_MAX_PRIMES) return TN_EINVAL;
+  for (int i = 0; i < nslots; ++i) {
+    const uint32_t p = primes[i];
+    if (p < 2 || p >= (1u << 31)) return TN_EINVAL;
+    mt->q[i].p = p;
+    mt->q[i].r32 = static_cast<uint32_t>((uint64_t(1) << 32) % p);
+    mt->q[i].mu = ~0ull / p;
+    mt->q[i].x = xs[i] % p;
   }
   return TN_OK;
 }
@@ -80,6 +97,7 @@ Operand operand_of(const tn_plan_s* p, const Regions& rg, int32_t id) {
   Operand o;
   std::memset(&o, 0, sizeof(o));
   o.kind = t.kind;
+  o.vx = 1;
   if (t.kind == kOpArena) {
     o.p0 = rg.r0 + 4 * t.offset;
     o.p1 = rg.r1 ? rg.r1 + 8 * t.offset : nullptr;
@@ -100,6 +118,9 @@ int make_mod_table_checked(tn_semiring_t s, const uint32_t* primes, int32_t npri
 }
 int decode_raw(tn_semiring_t s, const ModTable& mods, int32_t nprimes, const unsigned char* raw,
                tn_result_t* out);
+int make_mod_table_slots(const uint32_t* primes, const uint32_t* xs, int32_t nslots, void* mods) {
+  return make_mods_slots(primes, xs, nslots, static_cast<ModTable*>(mods));
+}
 int decode_raw_any(tn_semiring_t s, const void* mods, int32_t nprimes, const unsigned char* raw,
                    tn_result_t* out) {
   return decode_raw(s, *static_cast<const ModTable*>(mods), nprimes, raw, out);

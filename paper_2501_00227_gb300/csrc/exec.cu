@@ -73,7 +73,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ Operand exec_operand(const ExecArgs& a, int32_t kind, int64_t off) {
   Operand o;
   o.kind = kind;
-  o.pad_ = 0;
+  o.vx = 1;
   o.p0 = a.r0 + 4 * off;
   o.p1 = a.r1 ? a.r1 + 8 * off : nullptr;
   o.prime_stride = a.prime_stride;
@@ -89,7 +89,7 @@ __device__ __forceinline__ Operand exec_operand_g(const ExecArgs& a, int32_t kin
   const int64_t e = int64_t(1) << rank;
   Operand o;
   o.kind = kOpShared;
-  o.pad_ = 0;
+  o.vx = 1;
   o.p0 = gsm + off;
   o.p1 = gsm + off + (4 * e + 7) / 8 * 8;
   o.prime_stride = e;
@@ -161,8 +161,8 @@ __device__ __noinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& s
   const int64_t kbeg = nch * rank / split * Cfg::BK;
   const int64_t kend_ = nch * (rank + 1) / split * Cfg::BK;
   const int64_t kstop = kend_ < K ? kend_ : K;
-  const Operand A = at_prime(exec_operand(a, g.a_kind, st.a_off), q);
-  const Operand B = at_prime(exec_operand(a, g.b_kind, st.b_off), q);
+  const Operand A = at_prime(exec_operand(a, g.a_kind, st.a_off), q, mp);
+  const Operand B = at_prime(exec_operand(a, g.b_kind, st.b_off), q, mp);
   const Output C = at_prime(Output{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride}, q);
 
   Acc acc[TM][TN];
@@ -283,7 +283,7 @@ __device__ __forceinline__ void exec_naive_mp(const ExecArgs& a, const ExecStep&
       for (int q = 0; q < NP; ++q) v.v[q] = pa[q][e];
       return v;
     }
-    if (g.a_kind != kOpArena) return SRN::leaf(g.a_kind, e);
+    if (g.a_kind != kOpArena) return SRN::leaf(g.a_kind, e, mp);
 #pragma unroll
     for (int q = 0; q < NP; ++q) v.v[q] = __ldcg(pa[q] + e);
     return v;
@@ -295,7 +295,7 @@ __device__ __forceinline__ void exec_naive_mp(const ExecArgs& a, const ExecStep&
       for (int q = 0; q < NP; ++q) v.v[q] = pb[q][e];
       return v;
     }
-    if (g.b_kind != kOpArena) return SRN::leaf(g.b_kind, e);
+    if (g.b_kind != kOpArena) return SRN::leaf(g.b_kind, e, mp);
 #pragma unroll
     for (int q = 0; q < NP; ++q) v.v[q] = __ldcg(pb[q] + e);
     return v;
@@ -353,8 +353,8 @@ __device__ __forceinline__ void exec_naive_task_q(const ExecArgs& a, const ExecS
   auto& sm = *reinterpret_cast<NaiveSmem<SR>*>(smem);
   const StepGeom& g = st.g;
   const ModParams mp = a.mods.q[q];
-  const Operand A = at_prime(exec_operand(a, g.a_kind, st.a_off), q);
-  const Operand B = at_prime(exec_operand(a, g.b_kind, st.b_off), q);
+  const Operand A = at_prime(exec_operand(a, g.a_kind, st.a_off), q, mp);
+  const Operand B = at_prime(exec_operand(a, g.b_kind, st.b_off), q, mp);
   const Output C = at_prime(Output{a.r0 + 4 * st.c_off, a.r1 ? a.r1 + 8 * st.c_off : nullptr, a.prime_stride}, q);
   const int32_t E = 1 << g.rc;
   const int ks = st.ks;
@@ -419,8 +419,8 @@ __device__ __forceinline__ void exec_naive_whole(const ExecArgs& a, const ExecSt
   const int32_t nkhi = 1 << (g.nk - kl);
   naive_tables<SR>(g, sm, 0, nkhi);
   const ModParams mp = a.mods.q[q];
-  const Operand A = at_prime(exec_operand_g(a, g.a_kind, st.a_off, g.ra, gsm), q);
-  const Operand B = at_prime(exec_operand_g(a, g.b_kind, st.b_off, g.rb, gsm), q);
+  const Operand A = at_prime(exec_operand_g(a, g.a_kind, st.a_off, g.ra, gsm), q, mp);
+  const Operand B = at_prime(exec_operand_g(a, g.b_kind, st.b_off, g.rb, gsm), q, mp);
   const Output C = at_prime(exec_output_g(a, st, gsm), q);
   auto la = [&](uint32_t e) { return SR::template load<true>(A, e); };
   auto lb = [&](uint32_t e) { return SR::template load<true>(B, e); };

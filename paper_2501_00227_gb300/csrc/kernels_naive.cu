@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kBlock) k_step_naive(const __grid_constant__ S
   naive_tables<SR>(g, sm, 0, nkhi);
   const int q = blockIdx.y;
   const ModParams mp = mods.q[q];
-  const Operand Aq = at_prime(A, q), Bq = at_prime(B, q);
+  const Operand Aq = at_prime(A, q, mp), Bq = at_prime(B, q, mp);
   const Output Cq = at_prime(C, q);
   const int32_t E = 1 << g.rc;
   const int32_t c0 = static_cast<int32_t>(blockIdx.x) * static_cast<int32_t>(chunk);

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_step_tiled(const __grid_constant_
   const int64_t kbeg = nch * rank / split * Cfg::BK;
   const int64_t kend_ = nch * (rank + 1) / split * Cfg::BK;
   const int64_t kstop = kend_ < K ? kend_ : K;
-  const Operand A = at_prime(args.A, q), B = at_prime(args.B, q);
+  const Operand A = at_prime(args.A, q, mp), B = at_prime(args.B, q, mp);
   const Output C = at_prime(args.C, q);
 
   Acc acc[TM][TN];

@@ -26,7 +26,7 @@ constexpr int32_t kNegInf = TN_I32_NEG_INF;
 // (tensor ranks are at most 30).
 struct Operand {
   int32_t kind;          // OperandKind
-  int32_t pad_;
+  uint32_t vx;           // mod p: a vertex leaf is W = [1, vx] (the prime slot's weight x)
   const void* p0;        // float / int32 values, or residues of prime 0
   const void* p1;        // uint64 counts (counting semiring)
   int64_t prime_stride;  // entries between consecutive prime blocks
@@ -38,24 +38,29 @@ struct Output {
   int64_t prime_stride;
 };
 
-// The same operand / output seen at the block of prime index q (mod p keeps
-// one residue array per prime; the element accessors below read p0 only).
-__device__ __forceinline__ Operand at_prime(Operand o, int q) {
+// Constants of one prime slot (2 <= p < 2^31):
+//   r32 = 2^32 mod p   (folds the high word of a 64-bit accumulator)
+//   mu  = floor((2^64 - 1) / p)   (Barrett 1986 reciprocal)
+//   x   = the vertex weight of the slot, reduced mod p: vertex leaves are
+//         W = [1, x] (Eq. 7 with x = e^{beta w}), so the slot's result is the
+//         independence polynomial evaluated at x; counting all sets is x = 1
+struct ModParams {
+  uint32_t p, r32;
+  uint64_t mu;
+  uint32_t x, pad_;
+};
+
+// The same operand / output seen at the block of prime slot q (mod p keeps
+// one residue array per slot; the element accessors below read p0 only).
+__device__ __forceinline__ Operand at_prime(Operand o, int q, const ModParams& mp) {
   if ((o.kind == kOpArena || o.kind == kOpShared) && q) o.p0 = static_cast<const uint32_t*>(o.p0) + q * o.prime_stride;
+  o.vx = mp.x;
   return o;
 }
 __device__ __forceinline__ Output at_prime(Output o, int q) {
   if (q) o.p0 = static_cast<uint32_t*>(o.p0) + q * o.prime_stride;
   return o;
 }
-
-// Constants of one modulus p (2 <= p < 2^31):
-//   r32 = 2^32 mod p   (folds the high word of a 64-bit accumulator)
-//   mu  = floor((2^64 - 1) / p)   (Barrett 1986 reciprocal)
-struct ModParams {
-  uint32_t p, r32;
-  uint64_t mu;
-};
 
 struct ModTable {
   ModParams q[TN_MAX_PRIMES];
@@ -264,15 +269,19 @@ struct SrMod {
   using Val = uint32_t;
   using Acc = uint64_t;
   static __device__ __forceinline__ Acc zero(const ModParams&) { return 0ull; }
-  static __device__ __forceinline__ Val leaf(int32_t kind, uint32_t e) {
-    // beta = 0: every allowed configuration weighs 1, a forbidden one 0
+  // Leaves with vertex weight x (already reduced mod p): a forbidden edge
+  // configuration weighs 0, an allowed one 1; W = [1, x].
+  static __device__ __forceinline__ Val leaf(int32_t kind, uint32_t e, uint32_t x) {
     if (kind == kOpEdge) return e == 3 ? 0u : 1u;
+    if (kind == kOpVertex) return e == 1 ? x : 1u;
     return 1u;
   }
+  // x = 1 (counting all sets); leaf(kOpEdge, 3) is the additive zero
+  static __device__ __forceinline__ Val leaf(int32_t kind, uint32_t e) { return leaf(kind, e, 1u); }
   template <bool CG = false>
   static __device__ __forceinline__ Val load(const Operand& o, uint32_t e) {
     if (o.kind == kOpShared) return static_cast<const uint32_t*>(o.p0)[e];
-    if (o.kind != kOpArena) return leaf(o.kind, e);
+    if (o.kind != kOpArena) return leaf(o.kind, e, o.vx);
     return ldg_t<CG>(static_cast<const uint32_t*>(o.p0) + e);
   }
   static __device__ __forceinline__ void copy_async(Val* dst, const Operand& o, uint32_t e) {

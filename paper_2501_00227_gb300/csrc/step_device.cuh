@@ -149,6 +149,13 @@ struct SrModN {
     for (int q = 0; q < NP; ++q) r.a[q] = 0ull;
     return r;
   }
+  static __device__ __forceinline__ Val leaf(int32_t kind, uint32_t e, const ModParamsN<NP>& mp) {
+    Val r;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r.v[q] = SrMod::leaf(kind, e, mp.q[q].x);
+    return r;
+  }
+  // the additive zero (the padding of short reduction batches)
   static __device__ __forceinline__ Val leaf(int32_t kind, uint32_t e) {
     Val r;
 #pragma unroll

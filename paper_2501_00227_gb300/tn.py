@@ -25,6 +25,8 @@ TN_TROPICAL_F32, TN_TROPICAL_I32, TN_COUNTING_TROPICAL, TN_COUNT_MODP = 1, 2, 3,
 TN_I32_NEG_INF = -(1 << 30)
 TN_MAX_PRIMES = 16
 TN_RAW_BYTES = 128
+TN_POLY_MAX_PRIMES = 32
+TN_POLY_LIMBS = 32
 
 SEMIRINGS = {"tropical_f32": TN_TROPICAL_F32, "tropical_i32": TN_TROPICAL_I32,
              "counting": TN_COUNTING_TROPICAL, "modp": TN_COUNT_MODP}
@@ -91,6 +93,8 @@ def lib():
         L.tn_modp_gemm_limb.argtypes = [u32p, i32, vp, vp, vp, i32, i32, i32, i32, vp]
         L.tn_modp_gemm_umma.argtypes = [u32p, i32, vp, vp, vp, i32, i32, i32, i32, vp]
         L.tn_plan_step_info.argtypes = [vp, ctypes.c_int, i32, i32p, i32]
+        L.tn_contract_modp_x.argtypes = [vp, u32p, u32p, i32, vp, ctypes.c_size_t, vp, u32p]
+        L.tn_independence_polynomial.argtypes = [vp, u32p, i32, i32, vp, ctypes.c_size_t, vp, u32p, u32p, i32p]
         L.tn_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_int, u32p, i32, ctypes.POINTER(vp)]
         L.tn_batch_info.argtypes = [vp, ctypes.POINTER(u64), i32p, i32p, ctypes.POINTER(u64)]
         L.tn_batch_contract.argtypes = [vp, vp, ctypes.c_size_t, vp, vp]
@@ -274,6 +278,68 @@ def tn_result_decode(semiring, primes, raw: bytes) -> dict:
     return result_dict(r, semiring)
 
 
+def tn_contract_modp_x(plan, primes, xs, ws_ptr: int, ws_bytes: int, stream: int) -> list:
+    """Residues I(G, xs[q]) mod primes[q] of the independence polynomial, one
+    slot per (prime, point) pair (at most TN_MAX_PRIMES slots)."""
+    pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint32).reshape(-1))
+    xv = np.ascontiguousarray(np.asarray(xs, dtype=np.uint32).reshape(-1))
+    if pr.size != xv.size:
+        raise TNError(TN_EINVAL, "tn_contract_modp_x: primes and xs differ in length")
+    out = np.zeros(pr.size, dtype=np.uint32)
+    _check(lib().tn_contract_modp_x(plan, _u32p(pr), _u32p(xv), pr.size, ctypes.c_void_p(ws_ptr), ws_bytes,
+                                    ctypes.c_void_p(stream), _u32p(out)), "tn_contract_modp_x")
+    return [int(v) for v in out]
+
+
+def tn_independence_polynomial(plan, primes, degree: int, ws_ptr: int, ws_bytes: int, stream: int):
+    """Coefficients c_0 .. c_degree of the independence polynomial (exact
+    when prod(primes) exceeds every coefficient) and their residues,
+    shape (degree + 1, len(primes))."""
+    pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint32).reshape(-1))
+    d = int(degree)
+    res = np.zeros((max(d + 1, 1), max(pr.size, 1)), dtype=np.uint32)
+    limbs = np.zeros((max(d + 1, 1), TN_POLY_LIMBS), dtype=np.uint32)
+    nl = np.zeros(max(d + 1, 1), dtype=np.int32)
+    _check(lib().tn_independence_polynomial(plan, _u32p(pr), pr.size, d, ctypes.c_void_p(ws_ptr), ws_bytes,
+                                            ctypes.c_void_p(stream), _u32p(res), _u32p(limbs), _p32(nl)),
+           "tn_independence_polynomial")
+    coeffs = [sum(int(limbs[k, i]) << (32 * i) for i in range(int(nl[k]))) for k in range(d + 1)]
+    return coeffs, res
+
+
+def _is_prime32(p: int) -> bool:
+    """Deterministic Miller-Rabin for p < 2^32 (bases 2, 7, 61)."""
+    if p < 2:
+        return False
+    for sp in (2, 3, 5, 7, 11, 13, 61):
+        if p % sp == 0:
+            return p == sp
+    d, r = p - 1, 0
+    while d % 2 == 0:
+        d, r = d // 2, r + 1
+    for a in (2, 7, 61):
+        x = pow(a, d, p)
+        if x in (1, p - 1):
+            continue
+        for _ in range(r - 1):
+            x = x * x % p
+            if x == p - 1:
+                break
+        else:
+            return False
+    return True
+
+
+def primes31(count: int) -> tuple:
+    """The `count` largest primes below 2^31 (the first eight are PRIMES31)."""
+    out, p = [], (1 << 31) - 1
+    while len(out) < count:
+        if _is_prime32(p):
+            out.append(p)
+        p -= 1
+    return tuple(out)
+
+
 def tn_contract_pair(semiring, primes, a_ptr, la, b_ptr, lb, lc, c_ptr, stream: int):
     pr, k = _primes(primes)
     la, lb, lc = _i32(la).reshape(-1), _i32(lb).reshape(-1), _i32(lc).reshape(-1)
@@ -408,6 +474,37 @@ class Plan:
         st = stream if stream is not None else torch.cuda.current_stream()
         return tn_contract(self.handle, semiring, primes, workspace.data_ptr(), workspace.numel(),
                            st.cuda_stream)
+
+    def evaluate(self, primes, xs, workspace=None, stream=None) -> list:
+        """I(G, xs[q]) mod primes[q] for every slot (tn_contract_modp_x)."""
+        import torch
+        need = self.workspace_bytes("modp", len(primes))
+        if workspace is None:
+            workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        return tn_contract_modp_x(self.handle, primes, xs, workspace.data_ptr(), workspace.numel(), st.cuda_stream)
+
+    def independence_polynomial(self, primes=None, degree=None, workspace=None, stream=None) -> list:
+        """Exact coefficients of I(G, x) (tn_independence_polynomial).  degree
+        defaults to the MIS size from a tropical contraction; primes default
+        to the fewest 31-bit primes whose product exceeds 2^n."""
+        import torch
+        if degree is None:
+            degree = max(0, self.contract("tropical_i32", workspace=workspace, stream=stream)["max_i32"])
+        if primes is None:
+            k, prod = 0, 1
+            while prod <= (1 << self.n):
+                k += 1
+                prod *= primes31(k)[-1]
+            primes = primes31(k)
+        slots = min(TN_MAX_PRIMES, len(primes) * (int(degree) + 1))
+        need = self.workspace_bytes("modp", slots)
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        coeffs, _ = tn_independence_polynomial(self.handle, primes, degree, workspace.data_ptr(), workspace.numel(),
+                                               st.cuda_stream)
+        return coeffs
 
     def close(self):
         if getattr(self, "handle", None):

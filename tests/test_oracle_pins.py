@@ -379,7 +379,7 @@ def test_cycle_polynomial_closed_form(n):
     assert poly == want
 
 
-@pytest.mark.parametrize("n", [1, 6, 40])
+@pytest.mark.parametrize("n", [1, 6, 14])
 def test_empty_and_complete_polynomials(n):
     """No edges: (1 + x)^n.  Complete graph: 1 + n x."""
     nn, e = g.empty(n)
