@@ -490,7 +490,7 @@ class Plan:
         to the fewest 31-bit primes whose product exceeds 2^n."""
         import torch
         if degree is None:
-            degree = max(0, self.contract("tropical_i32", workspace=workspace, stream=stream)["max_i32"])
+            degree = self.contract("tropical_i32", workspace=workspace, stream=stream)["max"] or 0
         if primes is None:
             k, prod = 0, 1
             while prod <= (1 << self.n):
