@@ -200,18 +200,20 @@ def interpolate_modp(xs, ys, p):
     return coeffs
 
 
-def independence_polynomial(n, edges, order, primes):
-    """Exact coefficients c_0 .. c_n of the independence polynomial (Eq. 13;
-    the finite-field method of Sec. 6.2): evaluations at x = 1 .. n+1 modulo
-    each prime, Lagrange interpolation modulo each prime, CRT per
-    coefficient.  Exact when prod(primes) exceeds the largest coefficient
-    (at most 2^n)."""
-    xs = list(range(1, n + 2))
+def independence_polynomial(n, edges, order, primes, degree=None):
+    """Exact coefficients c_0 .. c_degree of the independence polynomial
+    (Eq. 13; the finite-field method of Sec. 6.2): evaluations at x = 1 ..
+    degree + 1 modulo each prime, Lagrange interpolation modulo each prime,
+    CRT per coefficient.  Exact when prod(primes) exceeds the largest
+    coefficient (at most 2^n) and degree >= alpha(G) (the sum of Eq. 13
+    stops at alpha(G)); degree defaults to n."""
+    d = n if degree is None else int(degree)
+    xs = list(range(1, d + 2))
     per_prime = []
     for p in primes:
         ys = [evaluate_modp(n, edges, order, [p], [x])[0] for x in xs]
         per_prime.append(interpolate_modp(xs, ys, int(p)))
-    return [crt([c[d] for c in per_prime], primes)[0] for d in range(n + 1)]
+    return [crt([c[k] for c in per_prime], primes)[0] for k in range(d + 1)]
 
 
 def crt(residues, primes):

@@ -357,6 +357,9 @@ def test_petersen_polynomial_printed():
     poly = O.independence_polynomial(n, e, o, O.PRIMES31[:1])
     want = gd["independence_polynomial"]
     assert poly == want + [0] * (n + 1 - len(want))
+    # the sum of Eq. 13 stops at alpha = 4: five points determine it
+    assert O.independence_polynomial(n, e, o, O.PRIMES31[:1], degree=4) == want
+    assert O.independence_polynomial(n, e, o, O.PRIMES31[:1], degree=3) != want[:4]
 
 
 @pytest.mark.parametrize("n", [1, 2, 7, 20, 45])
