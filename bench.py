@@ -346,6 +346,55 @@ def limb_ablation_bench(tn, torch):
     return out
 
 
+def polynomial_bench(tn, torch, plans, cpu: bool = True):
+    """Independence polynomial (Eq. 13, finite-field method) of the headline
+    graphs: degree = alpha from a tropical contraction, the fewest 31-bit
+    primes whose product exceeds 2^n, (alpha + 1) x nprimes weighted mod-p
+    evaluations in launches of 16 slots, Newton interpolation and CRT on the
+    host.  Timed end to end (the call is synchronous).  The oracle computes
+    the same polynomial of the first n=100 graph beside it."""
+    out = {"workload": "random 3-regular n=100 and n=140 seeds 1-3 (the headline plans), degree alpha, "
+                       "x = 1..alpha+1 per prime", "instances": []}
+    st = torch.cuda.current_stream()
+    for (kind, n, seed), p in zip(GRAPHS, plans):
+        alpha = p.contract("tropical_i32")["max"]
+        k, prod = 0, 1
+        while prod <= (1 << n):
+            k += 1
+            prod *= tn.primes31(k)[-1]
+        primes = tn.primes31(k)
+        slots = (alpha + 1) * k
+        ws = torch.empty(p.workspace_bytes("modp", min(tn.TN_MAX_PRIMES, slots)), dtype=torch.uint8, device="cuda")
+        tn.tn_independence_polynomial(p.handle, primes, alpha, ws.data_ptr(), ws.numel(), st.cuda_stream)
+        times = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            coeffs, _ = tn.tn_independence_polynomial(p.handle, primes, alpha, ws.data_ptr(), ws.numel(),
+                                                      st.cuda_stream)
+            times.append(time.perf_counter() - t)
+        sec = statistics.median(times)
+        tc = p.info("modp", 1)["tc"]
+        out["instances"].append({"n": n, "seed": seed, "alpha": alpha, "primes": k, "evaluations": slots,
+                                 "launches": -(-slots // tn.TN_MAX_PRIMES), "ms": sec * 1e3,
+                                 "evals_per_s": slots / sec, "gops": tc * slots / sec / 1e9,
+                                 "coeff_sum_bits": int(sum(coeffs)).bit_length()})
+        del ws
+    if cpu:
+        import oracle
+        oracle.build()
+        cores = oracle.set_threads(os.cpu_count() or 1)
+        kind, n, seed = GRAPHS[0]
+        nn, e = graphgen.random_regular3(n, seed)
+        first = out["instances"][0]
+        t = time.perf_counter()
+        oracle.independence_polynomial(nn, e, plans[0].order, tn.primes31(first["primes"]), degree=first["alpha"])
+        sec = time.perf_counter() - t
+        out["cpu_baseline"] = {"value": sec * 1e3, "unit": "ms per polynomial", "cores": cores, "kind": "oracle",
+                               "sample": f"the n={n} seed {seed} polynomial, same order, primes and degree"}
+    return out
+
+
 def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120):
     """Poisson request stream mixing random 3-regular graphs (n even in
     [40,160]) and King's subgraphs (L in [8,16], filling 0.8), each asking the
@@ -573,6 +622,7 @@ def run_tn(args):
     if rank == 0 and not args.no_extras:
         line["largest_tropical"] = largest_bench(tn, torch, peak_ops, autotune=not args.no_autotune)
         line["modp_tensor_core_ablation"] = limb_ablation_bench(tn, torch)
+        line["independence_polynomial"] = polynomial_bench(tn, torch, plans, cpu=not args.no_cpu_baseline)
     if rank == 0 and not args.no_batching:
         line["batching"] = batching_bench(tn, torch)
     if rank == 0 and not args.no_serving:

@@ -155,3 +155,62 @@ def test_polynomial_full_size_properties():
         assert [sum(c * pow(x, k, q) for k, c in enumerate(coeffs)) % q for q, x in zip(pr, xs)] == want
     finally:
         p.close()
+
+
+# ------------------------------------------------------------------ k-best properties (Sec. 5.3)
+
+def _all_sizes(n, e):
+    """Sizes of all independent sets, by enumeration of every subset."""
+    adj = [0] * n
+    for u, v in e:
+        adj[int(u)] |= 1 << int(v)
+        adj[int(v)] |= 1 << int(u)
+    out = []
+    for s in range(1 << n):
+        if all(not (s >> v) & 1 or not (adj[v] & s) for v in range(n)):
+            out.append(bin(s).count("1"))
+    return sorted(out)
+
+
+def test_k_best_from_polynomial_petersen_printed():
+    """Sec. 5.3 prints SizeMax(2) = [4.0, 4.0] and CountingMax(2) = 30x^3 + 5x^4."""
+    import json
+    from paper_2501_00227_gb300 import properties as P
+    gd = json.load(open(os.path.join(GOLD, "petersen.json")))
+    n, e = g.petersen()
+    poly = O.bruteforce_poly(n, e)
+    assert P.size_max(None, 2, poly) == gd["size_max_2"]
+    assert P.counting_max(None, 2, poly) == {int(k): v for k, v in gd["counting_max_2"].items()}
+    assert P.counting_max(None, 1, poly) == {gd["mis_count"][0]: gd["mis_count"][1]}
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_k_best_matches_enumeration(seed):
+    from paper_2501_00227_gb300 import properties as P
+    n, e = g.erdos_renyi(12, 0.3, 40 + seed)
+    poly = O.bruteforce_poly(n, e)
+    sizes = _all_sizes(n, e)
+    for k in (1, 2, 3, 7, 50, 10 ** 6):
+        assert P.size_max(None, k, poly) == sizes[-k:]
+        top = sorted(set(sizes))[-k:]
+        assert P.counting_max(None, k, poly) == {s: sizes.count(s) for s in top}
+
+
+@pytest.mark.gpu
+def test_k_best_on_gpu_petersen_and_reg3():
+    _cuda()
+    from paper_2501_00227_gb300 import properties as P
+    n, e, o, p = _plan("petersen")
+    try:
+        assert P.size_max(p, 2) == [4, 4]
+        assert P.counting_max(p, 2) == {3: 30, 4: 5}
+    finally:
+        p.close()
+    n, e, o, p = _plan("reg3:100:2")
+    try:
+        alpha, nmax = O.mis_count(n, e, o)
+        assert P.counting_max(p, 1) == {alpha: nmax}
+        want = O.independence_polynomial(n, e, o, tn.PRIMES31[:4], degree=alpha)
+        assert P.counting_max(p, 3) == {alpha - j: want[alpha - j] for j in range(3)}
+    finally:
+        p.close()
