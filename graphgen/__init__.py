@@ -29,6 +29,8 @@ __all__ = [
     "kings_subgraph",
     "random_regular3",
     "erdos_renyi",
+    "fullerene",
+    "random_weights",
     "by_name",
 ]
 
@@ -141,9 +143,45 @@ def erdos_renyi(n: int, p: float, seed: int) -> tuple[int, np.ndarray]:
     return canonical(n, np.stack([iu[mask], ju[mask]], axis=1))
 
 
+def fullerene() -> tuple[int, np.ndarray]:
+    """The Buckyball C60 (truncated icosahedron, Sec. 6.4): 60 vertices, 90
+    edges.  Built combinatorially: the icosahedron's 12 vertices are the
+    cyclic permutations of (0, +-1, +-phi), joined when at distance 2; each
+    directed edge (u -> v) becomes a vertex near u; (u -> v) is joined to
+    (v -> u) (the hexagon-hexagon edges) and to (u -> w) for the two
+    neighbours w of u adjacent to v (the pentagon around u)."""
+    phi = (1 + 5 ** 0.5) / 2
+    pts = []
+    for a in (-1.0, 1.0):
+        for b in (-phi, phi):
+            pts += [(0.0, a, b), (a, b, 0.0), (b, 0.0, a)]
+    pts = np.array(pts)
+    d = np.linalg.norm(pts[:, None, :] - pts[None, :, :], axis=2)
+    adj = [[j for j in range(12) if j != i and abs(d[i, j] - 2.0) < 1e-9] for i in range(12)]
+    ids = {}
+    for u in range(12):
+        for v in adj[u]:
+            ids[(u, v)] = len(ids)
+    pairs = []
+    for (u, v), i in ids.items():
+        pairs.append((i, ids[(v, u)]))
+        for w in adj[u]:
+            if w in adj[v]:
+                pairs.append((i, ids[(u, w)]))
+    return canonical(len(ids), pairs)
+
+
+def random_weights(count: int, seed: int, values=(-1, 1)) -> np.ndarray:
+    """``count`` integers drawn uniformly from ``values`` (seeded): spin-glass
+    couplings J_ij / fields h_i, or vertex weights."""
+    rng = np.random.default_rng(seed)
+    return np.asarray(values, dtype=np.int32)[rng.integers(0, len(values), size=count)]
+
+
 def by_name(spec: str) -> tuple[int, np.ndarray]:
     """Parse a short graph spec, e.g. ``reg3:140:1``, ``ksg:20:0.8:1``, ``square:20``,
-    ``petersen``, ``path:10``, ``cycle:9``, ``complete:5``, ``empty:6``, ``er:12:0.3:7``."""
+    ``petersen``, ``path:10``, ``cycle:9``, ``complete:5``, ``empty:6``, ``er:12:0.3:7``,
+    ``fullerene``."""
     parts = spec.split(":")
     kind = parts[0]
     if kind == "petersen":
@@ -164,4 +202,6 @@ def by_name(spec: str) -> tuple[int, np.ndarray]:
         return random_regular3(int(parts[1]), int(parts[2]))
     if kind == "er":
         return erdos_renyi(int(parts[1]), float(parts[2]), int(parts[3]))
+    if kind == "fullerene":
+        return fullerene()
     raise ValueError(f"unknown graph spec {spec!r}")

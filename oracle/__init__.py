@@ -18,6 +18,7 @@ each one is pinned by brute force, closed forms or numbers the paper prints.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -66,6 +67,12 @@ def _load():
             lib.or_contract_counting.argtypes = [I, i32p, I, i32p, I, i64p, u64p, u64p]
             lib.or_contract_modp.argtypes = [I, i32p, I, i32p, I, u32p, I, u64p]
             lib.or_contract_modp_x.argtypes = [I, i32p, I, i32p, I, u32p, u32p, I, u64p]
+            lib.or_contract_weighted.argtypes = [I, I, I, i32p, I, i32p, i32p, i32p, I, u32p, u32p, I,
+                                                 i64p, i64p, u64p, u64p, u64p]
+            lib.or_spin_energy.argtypes = [I, i32p, I, i32p, i32p, ctypes.POINTER(ctypes.c_int8)]
+            lib.or_spin_energy.restype = ctypes.c_int64
+            lib.or_bruteforce_spin.argtypes = [I, i32p, I, i32p, i32p, ctypes.c_int64, u64p]
+            lib.or_bruteforce_weighted_is.argtypes = [I, i32p, I, i32p, u64p]
             lib.or_pair_tropical.argtypes = [i64p, i32p, I, i64p, i32p, I, i32p, I, i64p]
             lib.or_pair_counting.argtypes = [i64p, u64p, i32p, I, i64p, u64p, i32p, I, i32p, I, i64p, u64p, u64p]
             lib.or_pair_modp.argtypes = [u64p, i32p, I, u64p, i32p, I, i32p, I, ctypes.c_uint32, u64p]
@@ -214,6 +221,116 @@ def independence_polynomial(n, edges, order, primes, degree=None):
         ys = [evaluate_modp(n, edges, order, [p], [x])[0] for x in xs]
         per_prime.append(interpolate_modp(xs, ys, int(p)))
     return [crt([c[k] for c in per_prime], primes)[0] for k in range(d + 1)]
+
+
+PROBLEMS = {"is": 0, "spin": 1}
+
+
+def _weights(w, size):
+    if w is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(w, dtype=np.int32).reshape(-1))
+    if a.size != size:
+        raise OracleError("weights: wrong length")
+    return a
+
+
+def _p_opt(a, ctype):
+    return None if a is None else _p(a, ctype)
+
+
+def weighted_contract(kind: str, problem: str, n, edges, order, edge_w=None, vertex_w=None, primes=None, xs=None):
+    """Contraction of a weighted network in one element type.
+    problem 'is': vertex weights w_v (None: 1) -- tropical: the largest total
+    weight of an independent set; counting: (that weight, number of sets);
+    modp: sum_S x^{w(S)} per slot (primes[q], xs[q]).
+    problem 'spin': the spin glass of Eq. 1 with couplings edge_w (None: 1)
+    and fields vertex_w (None: 0) -- tropical: max over sigma of -H;
+    counting: (-E_min, ground-state degeneracy); modp: sum_sigma
+    y^{H + sum|J| + sum|h|} per slot (primes[q], xs[q])."""
+    n, e, m = _graph(n, edges)
+    o, k = _order(order)
+    J, h = _weights(edge_w, m), _weights(vertex_w, n)
+    kid = {"tropical": 1, "counting": 2, "modp": 3}[kind]
+    pr = np.ascontiguousarray(np.asarray(primes if primes is not None else [2], dtype=np.uint32))
+    xv = None if xs is None else np.ascontiguousarray(np.asarray(xs, dtype=np.uint32))
+    t, cn, lo, hi = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_uint64()
+    res = np.zeros(len(pr), dtype=np.uint64)
+    _check(_load().or_contract_weighted(kid, PROBLEMS[problem], n, _p(e, ctypes.c_int32), m,
+                                        _p_opt(J, ctypes.c_int32), _p_opt(h, ctypes.c_int32),
+                                        _p(o, ctypes.c_int32), k, _p(pr, ctypes.c_uint32),
+                                        _p_opt(xv, ctypes.c_uint32), len(pr), ctypes.byref(t), ctypes.byref(cn),
+                                        ctypes.byref(lo), ctypes.byref(hi), _p(res, ctypes.c_uint64)),
+           "contract_weighted")
+    if kind == "tropical":
+        return None if t.value == OR_NEG_INF else int(t.value)
+    if kind == "counting":
+        return (None if cn.value == OR_NEG_INF else int(cn.value)), int(lo.value) | (int(hi.value) << 64)
+    return [int(x) for x in res]
+
+
+def spin_energy(n, edges, spins, edge_w=None, vertex_w=None):
+    """Eq. 1 for one configuration spins in {-1, +1}^n."""
+    n, e, m = _graph(n, edges)
+    J, h = _weights(edge_w, m), _weights(vertex_w, n)
+    sp = np.ascontiguousarray(np.asarray(spins, dtype=np.int8))
+    return int(_load().or_spin_energy(n, _p(e, ctypes.c_int32), m, _p_opt(J, ctypes.c_int32),
+                                      _p_opt(h, ctypes.c_int32), _p(sp, ctypes.c_int8)))
+
+
+def spin_shift(n, edges, edge_w=None, vertex_w=None):
+    """sum |J| + sum |h|: the largest |H| (J None: 1, h None: 0)."""
+    m = len(np.asarray(edges).reshape(-1, 2))
+    J = np.ones(m, dtype=np.int64) if edge_w is None else np.asarray(edge_w, dtype=np.int64)
+    h = np.zeros(int(n), dtype=np.int64) if vertex_w is None else np.asarray(vertex_w, dtype=np.int64)
+    return int(np.abs(J).sum() + np.abs(h).sum())
+
+
+def bruteforce_spin(n, edges, edge_w=None, vertex_w=None):
+    """Energy histogram over all 2^n spin configurations (n <= 30):
+    hist[k] = number of sigma with H(sigma) = k - shift."""
+    n, e, m = _graph(n, edges)
+    J, h = _weights(edge_w, m), _weights(vertex_w, n)
+    shift = spin_shift(n, e, edge_w, vertex_w)
+    hist = np.zeros(2 * shift + 1, dtype=np.uint64)
+    _check(_load().or_bruteforce_spin(n, _p(e, ctypes.c_int32), m, _p_opt(J, ctypes.c_int32),
+                                      _p_opt(h, ctypes.c_int32), shift, _p(hist, ctypes.c_uint64)), "bruteforce_spin")
+    return shift, [int(x) for x in hist]
+
+
+def bruteforce_weighted_is(n, edges, vertex_w):
+    """hist[k] = number of independent sets of total weight k (weights >= 0)."""
+    n, e, m = _graph(n, edges)
+    w = _weights(vertex_w, n)
+    hist = np.zeros(int(w.sum()) + 1, dtype=np.uint64)
+    _check(_load().or_bruteforce_weighted_is(n, _p(e, ctypes.c_int32), m, _p(w, ctypes.c_int32),
+                                             _p(hist, ctypes.c_uint64)), "bruteforce_weighted_is")
+    return [int(x) for x in hist]
+
+
+def weighted_polynomial(problem: str, n, edges, order, primes, degree, edge_w=None, vertex_w=None):
+    """Coefficients c_0 .. c_degree of the network's generating polynomial:
+    'is': c_k = number of independent sets of weight k (weights >= 0);
+    'spin': c_k = number of configurations with H = k - sum|J| - sum|h|.
+    Evaluations at x = 1 .. degree + 1 modulo each prime, Lagrange
+    interpolation, CRT (the finite-field method of Sec. 6.2)."""
+    d = int(degree)
+    xs = list(range(1, d + 2))
+    per_prime = []
+    for p in primes:
+        ys = weighted_contract("modp", problem, n, edges, order, edge_w, vertex_w, [p] * len(xs), xs)
+        per_prime.append(interpolate_modp(xs, ys, int(p)))
+    return [crt([c[k] for c in per_prime], primes)[0] for k in range(d + 1)]
+
+
+def log_partition_function(coeffs, shift, beta):
+    """ln Z(beta) for Z = sum_sigma e^{-beta H(sigma)} (Eq. 3 with the energy
+    of Eq. 1), from the exact energy histogram coeffs[k] = #{H = k - shift}:
+    ln Z = ln sum_k c_k e^{-beta (k - shift)}, summed relative to the largest
+    term (float64)."""
+    terms = [math.log(c) - beta * (k - shift) for k, c in enumerate(coeffs) if c]
+    top = max(terms)
+    return top + math.log(sum(math.exp(t - top) for t in terms))
 
 
 def crt(residues, primes):

@@ -22,7 +22,10 @@
  *   - the complexity measures tc / sc / rwc of a binary order (Sec. 4.1);
  *   - the greedy order of Sec. 4.2.1 (cost Eq. 9 with alpha = 0);
  *   - brute force over all 2^n vertex subsets (definition of an independent
- *     set, Sec. 2.1.1) as an independent second check.
+ *     set, Sec. 2.1.1) as an independent second check;
+ *   - weighted networks on the same pairwise contraction: vertex-weighted
+ *     independent sets and the spin glass of Eq. 1 (Sec. 2.1.1, Sec. 6.4),
+ *     with brute-force energy / weight histograms to check them.
  *
  * Representation: a tensor of rank r over labels L[0..r-1] (vertex ids) is a
  * dense array of 2^r entries; entry x holds the value for the assignment in
@@ -138,15 +141,38 @@ static int check_order(int T, const int32_t *order, int nsteps) {
     return rc;
 }
 
-/* Leaf tensors of the IS network, Eqs. (5)-(7):
- *   B(n_u, n_v) = [[one, one], [one, zero]]      (edge)
- *   W(n_v)      = [one, x]  with x = e^{beta w}:  tropical 1, counting (1,1),
- *                 counting all IS (beta = 0): 1; the independence
- *                 polynomial I(G, x) of Eq. 13 evaluated at x: x mod p in
- *                 each prime slot (g_vertex_x == NULL: x = 1). */
+/* The network being contracted.
+ *   IS (Eqs. (5)-(7)): edge tensor B(n_u, n_v) = [[one, one], [one, zero]];
+ *     vertex tensor W(n_v) = [one, e^{beta w_v}]: tropical (max,+) w_v,
+ *     counting (w_v, 1), mod p x^{w_v} for the prime slot's x (the
+ *     independence polynomial of Eq. 13 at x when w = 1).  Integer weights
+ *     g_vertex_w (NULL: w_v = 1); g_vertex_x NULL means x = 1 (count of all
+ *     sets).
+ *   Spin glass (Eq. 1): H(sigma) = sum_E J_ij s_i s_j + sum_V h_i s_i with
+ *     s = 2n - 1 in {-1, +1}.  Tropical / counting maximise -H:
+ *     B(n_u, n_v) = -J s_u s_v, W(n_v) = -h s_v (counts 1).  Mod p with the
+ *     slot's y: B = y^{J s_u s_v + |J|}, W = y^{h s_v + |h|}, so the network
+ *     is sum_sigma y^{H(sigma) + sum|J| + sum|h|} (an energy histogram).
+ *     g_edge_w = J (NULL: 1), g_vertex_w = h (NULL: 0).
+ * Leaves are numbered edges first (index e), then vertices (index v). */
+enum { OR_PROBLEM_IS = 0, OR_PROBLEM_SPIN = 1 };
+static int g_problem = OR_PROBLEM_IS;
+static const int32_t *g_edge_w = NULL;
+static const int32_t *g_vertex_w = NULL;
 static const uint32_t *g_vertex_x = NULL;
+
+/* b^e mod p by repeated multiplication (e >= 0 is small) */
+static uint64_t pow_mod_plain(uint64_t b, int64_t e, uint64_t p) {
+    uint64_t r = 1 % p;
+    b %= p;
+    for (int64_t i = 0; i < e; i++) r = r * b % p;
+    return r;
+}
+
+static int64_t iabs64(int64_t a) { return a < 0 ? -a : a; }
+
 static int make_leaf(tensor_t *t, int kind, const uint32_t *primes, int nprimes, int is_edge,
-                     int32_t u, int32_t v) {
+                     int32_t u, int32_t v, int32_t idx) {
     t->rank = is_edge ? 2 : 1;
     t->labels[0] = u;
     if (is_edge) t->labels[1] = v;
@@ -154,21 +180,43 @@ static int make_leaf(tensor_t *t, int kind, const uint32_t *primes, int nprimes,
     t->data = malloc(ne * elem_size(kind, nprimes));
     if (!t->data) return OR_ENOMEM;
     for (size_t x = 0; x < ne; x++) {
-        int both = is_edge && x == 3;          /* n_u = n_v = 1 */
-        int occupied = !is_edge && x == 1;     /* n_v = 1       */
+        /* value as an exponent: -inf marks a forbidden configuration (IS edge
+         * n_u = n_v = 1); mod p raises the slot's point to `mexp` */
+        int64_t val, mexp;
+        if (g_problem == OR_PROBLEM_IS) {
+            if (is_edge) {
+                val = x == 3 ? OR_NEG_INF : 0;
+                mexp = 0;
+            } else {
+                int64_t w = g_vertex_w ? g_vertex_w[idx] : 1;
+                val = x == 1 ? w : 0;
+                mexp = val;
+                if (kind == OR_MODP && mexp < 0) return OR_EINVAL;
+            }
+        } else {
+            if (is_edge) {
+                int64_t J = g_edge_w ? g_edge_w[idx] : 1;
+                int64_t su = 2 * (int64_t)(x & 1) - 1, sv = 2 * (int64_t)((x >> 1) & 1) - 1;
+                val = -J * su * sv;
+                mexp = J * su * sv + iabs64(J);
+            } else {
+                int64_t h = g_vertex_w ? g_vertex_w[idx] : 0;
+                int64_t sv = 2 * (int64_t)x - 1;
+                val = -h * sv;
+                mexp = h * sv + iabs64(h);
+            }
+        }
         if (kind == OR_TROPICAL) {
-            int64_t *d = t->data;
-            d[x] = both ? OR_NEG_INF : (occupied ? 1 : 0);
+            ((int64_t *)t->data)[x] = val;
         } else if (kind == OR_COUNTING) {
             cnt_t *d = t->data;
-            if (both) { d[x].n = OR_NEG_INF; d[x].c = 0; }
-            else { d[x].n = occupied ? 1 : 0; d[x].c = 1; }
+            d[x].n = val;
+            d[x].c = val == OR_NEG_INF ? 0 : 1;
         } else {
             uint64_t *d = t->data;
             for (int q = 0; q < nprimes; q++) {
-                uint64_t val = both ? 0 : 1 % primes[q];
-                if (occupied && g_vertex_x) val = g_vertex_x[q] % primes[q];
-                d[x * nprimes + q] = val;
+                uint64_t pt = g_vertex_x ? g_vertex_x[q] : 1;
+                d[x * nprimes + q] = val == OR_NEG_INF ? 0 : pow_mod_plain(pt, mexp, primes[q]);
             }
         }
     }
@@ -294,8 +342,8 @@ static int contract_network(int kind, const uint32_t *primes, int nprimes, int n
     tensor_t *t = calloc((size_t)(2 * T), sizeof(tensor_t));
     int *users = calloc((size_t)n, sizeof(int));
     if (!t || !users) { free(t); free(users); return OR_ENOMEM; }
-    for (int e = 0; e < m && !rc; e++) rc = make_leaf(&t[e], kind, primes, nprimes, 1, edges[2 * e], edges[2 * e + 1]);
-    for (int v = 0; v < n && !rc; v++) rc = make_leaf(&t[m + v], kind, primes, nprimes, 0, v, 0);
+    for (int e = 0; e < m && !rc; e++) rc = make_leaf(&t[e], kind, primes, nprimes, 1, edges[2 * e], edges[2 * e + 1], e);
+    for (int v = 0; v < n && !rc; v++) rc = make_leaf(&t[m + v], kind, primes, nprimes, 0, v, 0, v);
     for (int i = 0; i < T && !rc; i++) for (int k = 0; k < t[i].rank; k++) users[t[i].labels[k]]++;
 
     int root = 0;
@@ -384,6 +432,78 @@ int or_contract_modp_x(int n, const int32_t *edges, int m, const int32_t *order,
     int rc = contract_network(OR_MODP, primes, nprimes, n, edges, m, order, nsteps, residues);
     g_vertex_x = NULL;
     return rc;
+}
+
+/* Weighted networks (see make_leaf): problem OR_PROBLEM_IS with vertex
+ * weights vertex_w (NULL: 1), or OR_PROBLEM_SPIN with couplings edge_w
+ * (NULL: 1) and fields vertex_w (NULL: 0).  kind OR_TROPICAL -> *trop;
+ * OR_COUNTING -> (*cnt_n, count as lo/hi 64-bit halves); OR_MODP -> one
+ * residue per slot (primes[q], xs[q]) (xs NULL: x = 1). */
+int or_contract_weighted(int kind, int problem, int n, const int32_t *edges, int m, const int32_t *edge_w,
+                         const int32_t *vertex_w, const int32_t *order, int nsteps, const uint32_t *primes,
+                         const uint32_t *xs, int nprimes, int64_t *trop, int64_t *cnt_n, uint64_t *cnt_lo,
+                         uint64_t *cnt_hi, uint64_t *residues) {
+    if (problem != OR_PROBLEM_IS && problem != OR_PROBLEM_SPIN) return OR_EINVAL;
+    g_problem = problem;
+    g_edge_w = edge_w;
+    g_vertex_w = vertex_w;
+    g_vertex_x = xs;
+    int rc;
+    if (kind == OR_TROPICAL) {
+        rc = contract_network(OR_TROPICAL, NULL, 0, n, edges, m, order, nsteps, trop);
+    } else if (kind == OR_COUNTING) {
+        cnt_t r;
+        rc = contract_network(OR_COUNTING, NULL, 0, n, edges, m, order, nsteps, &r);
+        if (!rc) { *cnt_n = r.n; *cnt_lo = (uint64_t)r.c; *cnt_hi = (uint64_t)(r.c >> 64); }
+    } else {
+        rc = contract_network(OR_MODP, primes, nprimes, n, edges, m, order, nsteps, residues);
+    }
+    g_problem = OR_PROBLEM_IS;
+    g_edge_w = g_vertex_w = NULL;
+    g_vertex_x = NULL;
+    return rc;
+}
+
+/* Eq. (1): H(sigma) = sum_E J_ij s_i s_j + sum_V h_i s_i for one spin
+ * configuration s in {-1, +1}^n (J NULL: 1, h NULL: 0). */
+int64_t or_spin_energy(int n, const int32_t *edges, int m, const int32_t *J, const int32_t *h,
+                       const int8_t *spins) {
+    int64_t e = 0;
+    for (int k = 0; k < m; k++) e += (int64_t)(J ? J[k] : 1) * spins[edges[2 * k]] * spins[edges[2 * k + 1]];
+    for (int v = 0; v < n; v++) e += (int64_t)(h ? h[v] : 0) * spins[v];
+    return e;
+}
+
+/* Brute force over all 2^n spin configurations (n <= 30): hist[H + shift]
+ * counts the configurations of each energy, shift = sum |J| + sum |h|,
+ * hist has 2 * shift + 1 entries. */
+int or_bruteforce_spin(int n, const int32_t *edges, int m, const int32_t *J, const int32_t *h, int64_t shift,
+                       uint64_t *hist) {
+    if (n < 0 || n > 30) return OR_EINVAL;
+    int8_t s[32];
+    for (uint64_t c = 0; c < ((uint64_t)1 << n); c++) {
+        for (int v = 0; v < n; v++) s[v] = ((c >> v) & 1) ? 1 : -1;
+        int64_t e = or_spin_energy(n, edges, m, J, h, s) + shift;
+        if (e < 0 || e > 2 * shift) return OR_EINVAL;
+        hist[e]++;
+    }
+    return OR_OK;
+}
+
+/* Brute force over all 2^n vertex subsets (n <= 30): hist[w(S)] counts the
+ * independent sets S of each total weight w(S) = sum_{v in S} w_v (w_v >= 0;
+ * hist has sum w_v + 1 entries). */
+int or_bruteforce_weighted_is(int n, const int32_t *edges, int m, const int32_t *w, uint64_t *hist) {
+    if (n < 0 || n > 30) return OR_EINVAL;
+    for (uint64_t c = 0; c < ((uint64_t)1 << n); c++) {
+        int ok = 1;
+        for (int k = 0; k < m && ok; k++) ok = !(((c >> edges[2 * k]) & 1) && ((c >> edges[2 * k + 1]) & 1));
+        if (!ok) continue;
+        int64_t tot = 0;
+        for (int v = 0; v < n; v++) if ((c >> v) & 1) tot += w[v];
+        hist[tot]++;
+    }
+    return OR_OK;
 }
 
 /* One pairwise contraction on caller tensors (labels as above, LC given). */
@@ -647,8 +767,8 @@ int or_flat_contract(int kind, int n, const int32_t *edges, int m, const uint32_
     int T = m + n;
     tensor_t *t = calloc((size_t)T, sizeof(tensor_t));
     if (!t) return OR_ENOMEM;
-    for (int e = 0; e < m && !rc; e++) rc = make_leaf(&t[e], kind, primes, np_, 1, edges[2 * e], edges[2 * e + 1]);
-    for (int v = 0; v < n && !rc; v++) rc = make_leaf(&t[m + v], kind, primes, np_, 0, v, 0);
+    for (int e = 0; e < m && !rc; e++) rc = make_leaf(&t[e], kind, primes, np_, 1, edges[2 * e], edges[2 * e + 1], e);
+    for (int v = 0; v < n && !rc; v++) rc = make_leaf(&t[m + v], kind, primes, np_, 0, v, 0, v);
     if (!rc) {
         int64_t tacc = OR_NEG_INF;
         cnt_t cacc; cacc.n = OR_NEG_INF; cacc.c = 0;
