@@ -239,6 +239,48 @@ int tn_independence_polynomial(tn_plan_t plan, const uint32_t *primes, int32_t n
                                void *d_workspace, size_t ws_bytes, void *cuda_stream,
                                uint32_t *coeff_residues, uint32_t *coeff_limbs, int32_t *coeff_nlimbs);
 
+/* Weighted networks on the same contraction path (the plan, its order and
+ * the executor are those of the unit-weight IS network; only the leaf
+ * tensors change).  problem:
+ *   TN_PROBLEM_INDEPENDENT_SET  vertex weights w_v (Eqs. 5-7 with energy
+ *       -sum w_v n_v): tropical = the largest total weight of an independent
+ *       set; counting = (that weight, the number of sets reaching it); mod p
+ *       = sum_S x^{w(S)} per slot (p, x) (weights >= 0).  edge_w is ignored;
+ *       vertex_w NULL means w_v = 1.
+ *   TN_PROBLEM_SPIN_GLASS  the spin glass of Eq. 1 (Sec. 2.1.1, Sec. 6.4),
+ *       H = sum_E J_ij s_i s_j + sum_V h_i s_i, s = 2n - 1: tropical =
+ *       max_sigma -H = -E_min; counting = (-E_min, ground-state
+ *       degeneracy) (the paper's CountingMin with the sign flipped); mod p
+ *       = sum_sigma y^{H + sum|J| + sum|h|} per slot (p, y).  edge_w = J
+ *       (NULL: 1), vertex_w = h (NULL: 0).
+ * edge_w[m], vertex_w[n]: host arrays, copied into the workspace every call.
+ * Max-plus semirings need sum of |weights| <= 2^28 (2^24 for
+ * TN_TROPICAL_F32), else TN_EINVAL.  The leaf tensors are generated on the
+ * GPU into the workspace; d_workspace must hold tn_weighted_workspace_bytes
+ * (nslots prime slots for mod p; ignored otherwise), 256-byte aligned.
+ * tn_contract_weighted is synchronous; for mod p, out holds the slots'
+ * residues (no CRT: slots may repeat a prime).  Errors as tn_contract. */
+#define TN_PROBLEM_INDEPENDENT_SET 0
+#define TN_PROBLEM_SPIN_GLASS 1
+int tn_weighted_workspace_bytes(tn_plan_t plan, tn_semiring_t semiring, int32_t nslots, uint64_t *out);
+int tn_contract_weighted(tn_plan_t plan, tn_semiring_t semiring, int32_t problem, const int32_t *edge_w,
+                         const int32_t *vertex_w, const uint32_t *primes, const uint32_t *xs, int32_t nslots,
+                         void *d_workspace, size_t ws_bytes, void *cuda_stream, tn_result_t *out);
+
+/* The generating polynomial of a weighted network, by the finite-field
+ * method of tn_independence_polynomial: c_k = the number of independent sets
+ * of weight k (IS, weights >= 0), or the number of spin configurations with
+ * H = k - sum|J| - sum|h| (spin glass; the exact energy histogram, from which
+ * the partition function of Sec. 6.4 follows for any temperature).  degree
+ * at least the polynomial's degree (sum of the weights; 2 (sum|J| + sum|h|)
+ * for the spin glass), at most 2^20.  Workspace: tn_weighted_workspace_bytes
+ * with nslots = min(TN_MAX_PRIMES, nprimes * (degree + 1)).  Outputs and
+ * errors as tn_independence_polynomial. */
+int tn_weighted_polynomial(tn_plan_t plan, int32_t problem, const int32_t *edge_w, const int32_t *vertex_w,
+                           const uint32_t *primes, int32_t nprimes, int32_t degree, void *d_workspace,
+                           size_t ws_bytes, void *cuda_stream, uint32_t *coeff_residues, uint32_t *coeff_limbs,
+                           int32_t *coeff_nlimbs);
+
 /* Measured launch shapes.  The paper leaves the kernel schedule to the
  * contraction backend; this table lets an autotuner (tune.py in the Python
  * package) replace the host's estimate for given step shapes.  entries holds

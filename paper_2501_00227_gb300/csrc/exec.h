@@ -117,13 +117,25 @@ int32_t tune_generation();
 bool tune_lookup(tn_semiring_t s, const StepGeom& g, int* tile, int* split);
 void exec_plans_free(tn_plan_s* p);
 
-// Enqueues one contraction through the executor (exec.cu).
+// Leaf tensors stored in device memory (weighted networks, weighted.cu):
+// 4 entries per edge, then 2 per vertex, in the semiring's layout -- values
+// at l0 (float / int32 / uint32 residues), counts at l1 (counting), and for
+// mod p one block per prime slot, `stride` entries apart.  An ExecStep's
+// a_off / b_off of a leaf operand is its entry offset in this buffer.
+struct LeafBuffers {
+  const char* l0;
+  const char* l1;
+  int64_t stride;
+};
+
+// Enqueues one contraction through the executor (exec.cu); leaves NULL:
+// the unit-weight IS leaves are generated inside the kernels.
 int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods, int32_t nprimes, void* ws,
-                 size_t ws_bytes, void* stream, void* d_raw, void* d_trace);
+                 size_t ws_bytes, void* stream, void* d_raw, void* d_trace, const LeafBuffers* leaves = nullptr);
 
 // Launches the executor with the tables already on the device at d_tables.
 int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods, void* ws, void* stream, void* d_raw,
-                     void* d_trace, const void* d_tables);
+                     void* d_trace, const void* d_tables, const LeafBuffers* leaves = nullptr);
 
 // Merges the executor plans of several networks into one launch (batch.cu).
 int build_batch_plan(tn_plan_s* const* plans, int32_t count, tn_semiring_t semiring, int32_t nprimes,

@@ -326,7 +326,14 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
     E.g = S.g;
     auto off = [&](int32_t id) -> int64_t {
       const int pr = prod(id);
-      return pr < 0 ? 0 : (sh_off[pr] >= 0 ? sh_off[pr] : c_off[pr]);
+      if (pr < 0) {
+        // a leaf: its entry offset in a stored-leaf buffer (edges first, 4
+        // entries each, then vertices, 2 each); unused for generated leaves
+        if (id < p->m) return 4 * int64_t(id);
+        if (id < p->m + p->n) return 4 * int64_t(p->m) + 2 * int64_t(id - p->m);
+        return 0;
+      }
+      return sh_off[pr] >= 0 ? sh_off[pr] : c_off[pr];
     };
     E.a_off = off(S.a_id);
     E.b_off = off(S.b_id);

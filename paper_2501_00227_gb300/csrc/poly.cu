@@ -31,6 +31,10 @@ int make_mod_table_slots(const uint32_t* primes, const uint32_t* xs, int32_t nsl
 size_t required_bytes(tn_plan_s* p, tn_semiring_t s, int32_t nprimes);
 int contract_enqueue(const tn_plan_s* p, tn_semiring_t s, const ModTable& mods, int32_t nprimes, void* ws,
                      cudaStream_t st, void* d_raw, cudaEvent_t* step_events);
+int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw,
+                          const uint32_t* primes, const uint32_t* xs, int32_t nslots, void* d_ws, size_t ws_bytes,
+                          cudaStream_t st, unsigned char* raw_out);
+int weighted_checks(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw);
 }  // namespace tn
 
 namespace {
@@ -101,6 +105,50 @@ int contract_slots(tn_plan_s* plan, const uint32_t* primes, const uint32_t* xs, 
   return TN_OK;
 }
 
+// Coefficients c_0 .. c_degree of a polynomial given by an evaluator of
+// (prime, point) slots: x = 1 .. degree + 1 per prime, TN_MAX_PRIMES slots
+// per call, Newton interpolation per prime, Garner CRT per coefficient.
+template <class Eval>
+int polynomial_from_slots(Eval eval, const uint32_t* primes, int32_t nprimes, int32_t degree,
+                          uint32_t* coeff_residues, uint32_t* coeff_limbs, int32_t* coeff_nlimbs) {
+  const int npts = degree + 1;
+  const int total = npts * nprimes;
+  // slot s = q * npts + i evaluates at x = i + 1 modulo primes[q]
+  std::vector<uint32_t> sp(total), sx(total), sy(total);
+  for (int q = 0; q < nprimes; ++q)
+    for (int i = 0; i < npts; ++i) {
+      sp[q * npts + i] = primes[q];
+      sx[q * npts + i] = static_cast<uint32_t>(i + 1);
+    }
+  for (int s0 = 0; s0 < total; s0 += TN_MAX_PRIMES) {
+    const int ns = std::min(TN_MAX_PRIMES, total - s0);
+    const int rc = eval(sp.data() + s0, sx.data() + s0, ns, sy.data() + s0);
+    if (rc) return rc;
+  }
+  std::vector<uint32_t> res(static_cast<size_t>(npts) * nprimes);  // [coefficient][prime]
+  std::vector<uint32_t> c(npts);
+  for (int q = 0; q < nprimes; ++q) {
+    std::vector<uint32_t> xq(sx.begin() + q * npts, sx.begin() + (q + 1) * npts);
+    std::vector<uint32_t> yq(sy.begin() + q * npts, sy.begin() + (q + 1) * npts);
+    newton_interpolate(xq, yq, primes[q], c.data());
+    for (int k = 0; k < npts; ++k) res[static_cast<size_t>(k) * nprimes + q] = c[k];
+  }
+  if (coeff_residues) std::copy(res.begin(), res.end(), coeff_residues);
+  if (coeff_limbs || coeff_nlimbs) {
+    for (int k = 0; k < npts; ++k) {
+      uint32_t limbs[TN_POLY_LIMBS];
+      const int nl = crt_garner(res.data() + static_cast<size_t>(k) * nprimes, primes, nprimes, limbs, TN_POLY_LIMBS);
+      if (nl < 0) return TN_EINVAL;
+      if (coeff_limbs) {
+        std::memset(coeff_limbs + static_cast<size_t>(k) * TN_POLY_LIMBS, 0, 4 * TN_POLY_LIMBS);
+        std::memcpy(coeff_limbs + static_cast<size_t>(k) * TN_POLY_LIMBS, limbs, 4 * static_cast<size_t>(nl));
+      }
+      if (coeff_nlimbs) coeff_nlimbs[k] = nl;
+    }
+  }
+  return TN_OK;
+}
+
 bool prime_ok(uint32_t p) {
   if (p < 3 || p >= (1u << 31)) return false;
   for (uint32_t d = 2; d <= p / d; ++d)
@@ -125,58 +173,59 @@ int tn_contract_modp_x(tn_plan_t plan, const uint32_t* primes, const uint32_t* x
   }
 }
 
-int tn_independence_polynomial(tn_plan_t plan, const uint32_t* primes, int32_t nprimes, int32_t degree,
-                               void* d_workspace, size_t ws_bytes, void* cuda_stream, uint32_t* coeff_residues,
-                               uint32_t* coeff_limbs, int32_t* coeff_nlimbs) {
+// Argument checks shared by the polynomial entry points.
+static int poly_args_ok(tn_plan_t plan, void* d_workspace, const uint32_t* primes, int32_t nprimes, int32_t degree,
+                        int32_t max_degree) {
   if (!plan || !d_workspace || !primes || nprimes < 1 || nprimes > TN_POLY_MAX_PRIMES) return TN_EINVAL;
-  if (degree < 0 || degree > plan->n) return TN_EINVAL;
+  if (degree < 0 || degree > max_degree) return TN_EINVAL;
   if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0) return TN_EINVAL;
   for (int q = 0; q < nprimes; ++q) {
-    // d + 1 distinct points 1 .. d + 1 modulo every prime
+    // degree + 1 distinct points 1 .. degree + 1 modulo every prime
     if (!prime_ok(primes[q]) || static_cast<uint64_t>(degree) + 1 >= primes[q]) return TN_EINVAL;
     for (int r = 0; r < q; ++r)
       if (primes[r] == primes[q]) return TN_EINVAL;
   }
+  return TN_OK;
+}
+
+int tn_independence_polynomial(tn_plan_t plan, const uint32_t* primes, int32_t nprimes, int32_t degree,
+                               void* d_workspace, size_t ws_bytes, void* cuda_stream, uint32_t* coeff_residues,
+                               uint32_t* coeff_limbs, int32_t* coeff_nlimbs) {
+  int rc = poly_args_ok(plan, d_workspace, primes, nprimes, degree, plan ? plan->n : 0);
+  if (rc) return rc;
   try {
-    const int npts = degree + 1;
-    const int total = npts * nprimes;
-    // slot s = q * npts + i evaluates I(G, i + 1) mod primes[q]
-    std::vector<uint32_t> sp(total), sx(total), sy(total);
-    for (int q = 0; q < nprimes; ++q)
-      for (int i = 0; i < npts; ++i) {
-        sp[q * npts + i] = primes[q];
-        sx[q * npts + i] = static_cast<uint32_t>(i + 1);
-      }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    for (int s0 = 0; s0 < total; s0 += TN_MAX_PRIMES) {
-      const int ns = std::min(TN_MAX_PRIMES, total - s0);
-      const int rc = contract_slots(plan, sp.data() + s0, sx.data() + s0, ns, d_workspace, ws_bytes, st,
-                                    sy.data() + s0);
-      if (rc) return rc;
-    }
-    std::vector<uint32_t> res(static_cast<size_t>(npts) * nprimes);  // [coefficient][prime]
-    std::vector<uint32_t> c(npts);
-    for (int q = 0; q < nprimes; ++q) {
-      std::vector<uint32_t> xq(sx.begin() + q * npts, sx.begin() + (q + 1) * npts);
-      std::vector<uint32_t> yq(sy.begin() + q * npts, sy.begin() + (q + 1) * npts);
-      newton_interpolate(xq, yq, primes[q], c.data());
-      for (int k = 0; k < npts; ++k) res[static_cast<size_t>(k) * nprimes + q] = c[k];
-    }
-    if (coeff_residues) std::copy(res.begin(), res.end(), coeff_residues);
-    if (coeff_limbs || coeff_nlimbs) {
-      for (int k = 0; k < npts; ++k) {
-        uint32_t limbs[TN_POLY_LIMBS];
-        const int nl = crt_garner(res.data() + static_cast<size_t>(k) * nprimes, primes, nprimes, limbs,
-                                  TN_POLY_LIMBS);
-        if (nl < 0) return TN_EINVAL;
-        if (coeff_limbs) {
-          std::memset(coeff_limbs + static_cast<size_t>(k) * TN_POLY_LIMBS, 0, 4 * TN_POLY_LIMBS);
-          std::memcpy(coeff_limbs + static_cast<size_t>(k) * TN_POLY_LIMBS, limbs, 4 * static_cast<size_t>(nl));
-        }
-        if (coeff_nlimbs) coeff_nlimbs[k] = nl;
-      }
-    }
-    return TN_OK;
+    auto eval = [&](const uint32_t* sp, const uint32_t* sx, int ns, uint32_t* sy) {
+      return contract_slots(plan, sp, sx, ns, d_workspace, ws_bytes, st, sy);
+    };
+    return polynomial_from_slots(eval, primes, nprimes, degree, coeff_residues, coeff_limbs, coeff_nlimbs);
+  } catch (const std::bad_alloc&) {
+    return TN_ENOMEM;
+  }
+}
+
+int tn_weighted_polynomial(tn_plan_t plan, int32_t problem, const int32_t* edge_w, const int32_t* vertex_w,
+                           const uint32_t* primes, int32_t nprimes, int32_t degree, void* d_workspace,
+                           size_t ws_bytes, void* cuda_stream, uint32_t* coeff_residues, uint32_t* coeff_limbs,
+                           int32_t* coeff_nlimbs) {
+  int rc = poly_args_ok(plan, d_workspace, primes, nprimes, degree, 1 << 20);
+  if (rc) return rc;
+  rc = weighted_checks(plan, TN_COUNT_MODP, problem, edge_w, vertex_w);
+  if (rc) return rc;
+  try {
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    auto eval = [&](const uint32_t* sp, const uint32_t* sx, int ns, uint32_t* sy) {
+      unsigned char raw[TN_RAW_BYTES];
+      int r = contract_weighted_raw(plan, TN_COUNT_MODP, problem, edge_w, vertex_w, sp, sx, ns, d_workspace,
+                                    ws_bytes, st, raw);
+      if (r) return r;
+      uint32_t flags;
+      std::memcpy(&flags, raw + 96, 4);
+      if (flags) return static_cast<int>(TN_ETIMEOUT);
+      std::memcpy(sy, raw + 16, 4 * static_cast<size_t>(ns));
+      return static_cast<int>(TN_OK);
+    };
+    return polynomial_from_slots(eval, primes, nprimes, degree, coeff_residues, coeff_limbs, coeff_nlimbs);
   } catch (const std::bad_alloc&) {
     return TN_ENOMEM;
   }

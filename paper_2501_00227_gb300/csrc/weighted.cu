@@ -1,0 +1,286 @@
+// weighted.cu -- networks with integer weights on the same executor:
+// vertex-weighted independent sets (Eqs. 5-7 with weights w_v) and the spin
+// glass of Eq. 1 (couplings J_ij, fields h_i, spin s = 2n - 1).
+//
+// The unit-weight IS network generates its leaves inside the contraction
+// kernels from the entry index.  A weighted network's leaves depend on
+// per-edge / per-vertex data, so k_leaves writes every leaf tensor once per
+// contraction into a leaf buffer in the workspace (4 entries per edge, then
+// 2 per vertex, in the semiring's layout, one block per prime slot) and the
+// executor reads leaf operands from it like intermediates.
+//
+// Leaf values (entry x of an edge tensor: n_u = x & 1, n_v = x >> 1):
+//   IS          B = [one, one, one, zero]; W = [one, w_v]  (tropical w_v,
+//               counting (w_v, 1), mod p x^{w_v} for the slot's point x)
+//   spin glass  tropical / counting maximise -H: B = -J s_u s_v,
+//               W = -h s_v (count 1); mod p with the slot's point y:
+//               B = y^{J s_u s_v + |J|}, W = y^{h s_v + |h|}, so the network
+//               is sum_sigma y^{H(sigma) + sum|J| + sum|h|}.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "exec.h"
+#include "kernels.h"
+#include "tn_internal.h"
+
+using tn::dev::ModTable;
+
+namespace tn {
+int make_mod_table_slots(const uint32_t* primes, const uint32_t* xs, int32_t nslots, void* mods);
+int make_mod_table_checked(tn_semiring_t s, const uint32_t* primes, int32_t nprimes, void* mods);
+int decode_raw_any(tn_semiring_t s, const void* mods, int32_t nprimes, const unsigned char* raw, tn_result_t* out);
+size_t required_bytes(tn_plan_s* p, tn_semiring_t s, int32_t nprimes);
+}  // namespace tn
+
+namespace tn {
+namespace dev {
+namespace {
+
+struct LeafArgs {
+  int32_t m, n, problem, semiring;
+  int32_t nslots;
+  int32_t pad_;
+  int64_t entries;     // 4m + 2n
+  int64_t stride;      // entries between prime-slot blocks (mod p)
+  const int32_t* ew;   // J per edge (spin glass), or NULL
+  const int32_t* vw;   // w_v (IS) or h_v (spin glass), or NULL
+  char* l0;
+  char* l1;
+  uint32_t p[TN_MAX_PRIMES];
+  uint32_t x[TN_MAX_PRIMES];
+};
+
+__device__ uint32_t pow_mod(uint32_t b, int64_t e, uint32_t p) {
+  uint64_t r = 1u % p, base = b % p;
+  while (e > 0) {
+    if (e & 1) r = r * base % p;
+    base = base * base % p;
+    e >>= 1;
+  }
+  return static_cast<uint32_t>(r);
+}
+
+// (exponent / value, allowed) of leaf entry i: value for max-plus, exponent
+// of the slot's point for mod p
+__device__ void leaf_entry(const LeafArgs& a, int64_t i, int64_t* val, int64_t* mexp, bool* allowed) {
+  *allowed = true;
+  if (i < 4 * int64_t(a.m)) {
+    const int64_t k = i >> 2;
+    const int x = static_cast<int>(i & 3);
+    if (a.problem == TN_PROBLEM_INDEPENDENT_SET) {
+      *allowed = x != 3;
+      *val = 0;
+      *mexp = 0;
+    } else {
+      const int64_t J = a.ew ? a.ew[k] : 1;
+      const int64_t ss = ((x & 1) == (x >> 1)) ? 1 : -1;  // s_u s_v
+      *val = -J * ss;
+      *mexp = J * ss + (J < 0 ? -J : J);
+    }
+  } else {
+    const int64_t v = (i - 4 * int64_t(a.m)) >> 1;
+    const int x = static_cast<int>((i - 4 * int64_t(a.m)) & 1);
+    if (a.problem == TN_PROBLEM_INDEPENDENT_SET) {
+      const int64_t w = a.vw ? a.vw[v] : 1;
+      *val = x ? w : 0;
+      *mexp = *val;
+    } else {
+      const int64_t h = a.vw ? a.vw[v] : 0;
+      const int64_t s = x ? 1 : -1;
+      *val = -h * s;
+      *mexp = h * s + (h < 0 ? -h : h);
+    }
+  }
+}
+
+__global__ void k_leaves(const __grid_constant__ LeafArgs a) {
+  const int64_t total = a.entries * (a.semiring == TN_COUNT_MODP ? a.nslots : 1);
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = t % a.entries;
+    const int q = static_cast<int>(t / a.entries);
+    int64_t val, mexp;
+    bool ok;
+    leaf_entry(a, i, &val, &mexp, &ok);
+    switch (a.semiring) {
+      case TN_TROPICAL_F32:
+        reinterpret_cast<float*>(a.l0)[i] = ok ? static_cast<float>(val) : -INFINITY;
+        break;
+      case TN_TROPICAL_I32:
+        reinterpret_cast<int32_t*>(a.l0)[i] = ok ? static_cast<int32_t>(val) : TN_I32_NEG_INF;
+        break;
+      case TN_COUNTING_TROPICAL:
+        reinterpret_cast<int32_t*>(a.l0)[i] = ok ? static_cast<int32_t>(val) : TN_I32_NEG_INF;
+        reinterpret_cast<uint64_t*>(a.l1)[i] = ok ? 1ull : 0ull;
+        break;
+      default:
+        reinterpret_cast<uint32_t*>(a.l0)[q * a.stride + i] = ok ? pow_mod(a.x[q], mexp, a.p[q]) : 0u;
+        break;
+    }
+  }
+}
+
+}  // namespace
+}  // namespace dev
+
+namespace {
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? TN_OK : TN_ECUDA; }
+
+// Layout of the weighted part of the workspace, after the executor's bytes.
+struct WeightedLayout {
+  size_t exec_bytes, leaf_off, leaf1_off, ew_off, vw_off, total;
+  int64_t entries, stride;
+};
+
+WeightedLayout weighted_layout(tn_plan_s* p, tn_semiring_t s, int32_t nslots) {
+  WeightedLayout L;
+  L.entries = 4 * int64_t(p->m) + 2 * int64_t(p->n);
+  L.stride = static_cast<int64_t>(align256(4 * size_t(L.entries)) / 4);
+  L.exec_bytes = align256(required_bytes(p, s, nslots));
+  L.leaf_off = L.exec_bytes;
+  size_t leaf_bytes = 4 * size_t(L.stride) * (s == TN_COUNT_MODP ? size_t(nslots) : 1);
+  L.leaf1_off = L.leaf_off + leaf_bytes;
+  if (s == TN_COUNTING_TROPICAL) leaf_bytes += align256(8 * size_t(L.entries));
+  L.ew_off = L.leaf_off + leaf_bytes;
+  L.vw_off = L.ew_off + align256(4 * size_t(std::max(p->m, 1)));
+  L.total = L.vw_off + align256(4 * size_t(std::max(p->n, 1)));
+  return L;
+}
+
+// Host-side checks of the weights: int32 sums of the max-plus values stay far
+// from TN_I32_NEG_INF (and exact in float32); mod p needs exponents >= 0.
+int check_weights(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw) {
+  if (problem != TN_PROBLEM_INDEPENDENT_SET && problem != TN_PROBLEM_SPIN_GLASS) return TN_EINVAL;
+  double total = 0;
+  if (problem == TN_PROBLEM_SPIN_GLASS && ew)
+    for (int k = 0; k < p->m; ++k) total += std::fabs(double(ew[k]));
+  else if (problem == TN_PROBLEM_SPIN_GLASS)
+    total += p->m;
+  if (vw)
+    for (int v = 0; v < p->n; ++v) {
+      total += std::fabs(double(vw[v]));
+      if (problem == TN_PROBLEM_INDEPENDENT_SET && s == TN_COUNT_MODP && vw[v] < 0) return TN_EINVAL;
+    }
+  else if (problem == TN_PROBLEM_INDEPENDENT_SET)
+    total += p->n;
+  const double cap = s == TN_TROPICAL_F32 ? double(1 << 24) : double(1 << 28);
+  if (s != TN_COUNT_MODP && total > cap) return TN_EINVAL;
+  return TN_OK;
+}
+
+}  // namespace
+
+// Weighted contraction of slots (primes[q], xs[q]) (mod p) or of one
+// max-plus / counting network; the raw result block is copied to raw_out.
+int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw,
+                          const uint32_t* primes, const uint32_t* xs, int32_t nslots, void* d_ws, size_t ws_bytes,
+                          cudaStream_t st, unsigned char* raw_out) {
+  ModTable mods;
+  int rc = s == TN_COUNT_MODP ? make_mod_table_slots(primes, xs, nslots, &mods)
+                              : make_mod_table_checked(s, nullptr, 0, &mods);
+  if (rc) return rc;
+  const int32_t np = s == TN_COUNT_MODP ? nslots : 1;
+  const WeightedLayout L = weighted_layout(p, s, np);
+  if (ws_bytes < L.total) return TN_ENOMEM;
+  char* w = static_cast<char*>(d_ws);
+  // the weights (n + m integers) are copied every call: the layout depends on
+  // the number of slots
+  if (ew && p->m) rc = cuda_rc(cudaMemcpyAsync(w + L.ew_off, ew, 4 * size_t(p->m), cudaMemcpyHostToDevice, st));
+  if (!rc && vw && p->n) rc = cuda_rc(cudaMemcpyAsync(w + L.vw_off, vw, 4 * size_t(p->n), cudaMemcpyHostToDevice, st));
+  if (rc) return rc;
+  dev::LeafArgs la;
+  std::memset(&la, 0, sizeof(la));
+  la.m = p->m;
+  la.n = p->n;
+  la.problem = problem;
+  la.semiring = s;
+  la.nslots = np;
+  la.entries = L.entries;
+  la.stride = L.stride;
+  la.ew = ew ? reinterpret_cast<const int32_t*>(w + L.ew_off) : nullptr;
+  la.vw = vw ? reinterpret_cast<const int32_t*>(w + L.vw_off) : nullptr;
+  la.l0 = w + L.leaf_off;
+  la.l1 = s == TN_COUNTING_TROPICAL ? w + L.leaf1_off : nullptr;
+  for (int q = 0; q < np && s == TN_COUNT_MODP; ++q) {
+    la.p[q] = primes[q];
+    la.x[q] = xs[q] % primes[q];
+  }
+  const int64_t total = L.entries * np;
+  const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 1024));
+  dev::k_leaves<<<blocks, 256, 0, st>>>(la);
+  rc = cuda_rc(cudaGetLastError());
+  if (rc) return rc;
+  LeafBuffers lb{la.l0, la.l1, L.stride};
+  void* d_raw = w + 64;
+  rc = exec_enqueue(p, s, &mods, np, d_ws, L.exec_bytes, st, d_raw, nullptr, &lb);
+  if (rc) return rc;
+  rc = cuda_rc(cudaMemcpyAsync(raw_out, d_raw, TN_RAW_BYTES, cudaMemcpyDeviceToHost, st));
+  if (!rc) rc = cuda_rc(cudaStreamSynchronize(st));
+  return rc;
+}
+
+int weighted_checks(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw) {
+  return check_weights(p, s, problem, ew, vw);
+}
+
+size_t weighted_workspace(tn_plan_s* p, tn_semiring_t s, int32_t nslots) {
+  return weighted_layout(p, s, s == TN_COUNT_MODP ? nslots : 1).total;
+}
+
+}  // namespace tn
+
+using namespace tn;
+
+extern "C" {
+
+int tn_weighted_workspace_bytes(tn_plan_t plan, tn_semiring_t semiring, int32_t nslots, uint64_t* out) {
+  if (!plan || !out || semiring < TN_TROPICAL_F32 || semiring > TN_COUNT_MODP) return TN_EINVAL;
+  if (semiring == TN_COUNT_MODP && (nslots < 1 || nslots > TN_MAX_PRIMES)) return TN_EINVAL;
+  try {
+    *out = weighted_workspace(plan, semiring, nslots);
+  } catch (const std::bad_alloc&) {
+    return TN_ENOMEM;
+  }
+  return *out == ~size_t(0) ? TN_ENOMEM : TN_OK;
+}
+
+int tn_contract_weighted(tn_plan_t plan, tn_semiring_t semiring, int32_t problem, const int32_t* edge_w,
+                         const int32_t* vertex_w, const uint32_t* primes, const uint32_t* xs, int32_t nslots,
+                         void* d_workspace, size_t ws_bytes, void* cuda_stream, tn_result_t* out) {
+  if (!plan || !out || !d_workspace || semiring < TN_TROPICAL_F32 || semiring > TN_COUNT_MODP) return TN_EINVAL;
+  if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0) return TN_EINVAL;
+  if (semiring == TN_COUNT_MODP && (!primes || !xs || nslots < 1 || nslots > TN_MAX_PRIMES)) return TN_EINVAL;
+  int rc = check_weights(plan, semiring, problem, edge_w, vertex_w);
+  if (rc) return rc;
+  try {
+    unsigned char raw[TN_RAW_BYTES];
+    rc = contract_weighted_raw(plan, semiring, problem, edge_w, vertex_w, primes, xs, nslots, d_workspace, ws_bytes,
+                               static_cast<cudaStream_t>(cuda_stream), raw);
+    if (rc) return rc;
+    if (semiring != TN_COUNT_MODP) {
+      ModTable mods;
+      make_mod_table_checked(semiring, nullptr, 0, &mods);
+      return decode_raw_any(semiring, &mods, 0, raw, out);
+    }
+    // slots may repeat a prime: residues only, no CRT
+    std::memset(out, 0, sizeof(*out));
+    uint32_t flags;
+    std::memcpy(&flags, raw + 96, 4);
+    out->status = flags ? TN_ETIMEOUT : TN_OK;
+    out->nprimes = nslots;
+    for (int q = 0; q < nslots; ++q) {
+      out->primes[q] = primes[q];
+      std::memcpy(&out->residues[q], raw + 16 + 4 * q, 4);
+    }
+    return flags ? TN_ETIMEOUT : TN_OK;
+  } catch (const std::bad_alloc&) {
+    return TN_ENOMEM;
+  }
+}
+
+}  // extern "C"

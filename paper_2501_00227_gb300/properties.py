@@ -37,3 +37,33 @@ def size_max(plan, k: int = 1, polynomial=None) -> list:
         if len(out) == k:
             break
     return sorted(out)
+
+
+# --------------------------------------------------------------------------- spin glass (Eq. 1)
+
+def spin_glass_ground_state(plan, edge_w=None, vertex_w=None) -> tuple:
+    """(E_min, degeneracy) of H = sum J s_i s_j + sum h s_i (the paper's
+    CountingMin), from the counting contraction of -H on the GPU."""
+    r = plan.contract_weighted("counting", "spin", edge_w, vertex_w)
+    return -r["max"], r["count"]
+
+
+def energy_histogram(plan, edge_w=None, vertex_w=None) -> tuple:
+    """(shift, c) with c[k] = the exact number of spin configurations of
+    energy k - shift, shift = sum|J| + sum|h| (tn_weighted_polynomial)."""
+    import numpy as np
+    m = len(plan.edges)
+    sj = m if edge_w is None else int(np.abs(np.asarray(edge_w, dtype=np.int64)).sum())
+    sh = 0 if vertex_w is None else int(np.abs(np.asarray(vertex_w, dtype=np.int64)).sum())
+    return sj + sh, plan.weighted_polynomial("spin", edge_w, vertex_w)
+
+
+def log_partition_function(plan, beta: float, edge_w=None, vertex_w=None, histogram=None) -> float:
+    """ln Z(beta), Z = sum_sigma e^{-beta H(sigma)} (PartitionFunction of
+    Sec. 5.3), from the exact energy histogram: the largest term is factored
+    out and the rest summed in float64."""
+    import math
+    shift, c = histogram if histogram is not None else energy_histogram(plan, edge_w, vertex_w)
+    terms = [math.log(v) - beta * (k - shift) for k, v in enumerate(c) if v]
+    top = max(terms)
+    return top + math.log(sum(math.exp(t - top) for t in terms))

@@ -27,6 +27,8 @@ TN_MAX_PRIMES = 16
 TN_RAW_BYTES = 128
 TN_POLY_MAX_PRIMES = 32
 TN_POLY_LIMBS = 32
+TN_PROBLEM_INDEPENDENT_SET, TN_PROBLEM_SPIN_GLASS = 0, 1
+PROBLEMS = {"is": TN_PROBLEM_INDEPENDENT_SET, "spin": TN_PROBLEM_SPIN_GLASS}
 
 SEMIRINGS = {"tropical_f32": TN_TROPICAL_F32, "tropical_i32": TN_TROPICAL_I32,
              "counting": TN_COUNTING_TROPICAL, "modp": TN_COUNT_MODP}
@@ -95,6 +97,11 @@ def lib():
         L.tn_plan_step_info.argtypes = [vp, ctypes.c_int, i32, i32p, i32]
         L.tn_contract_modp_x.argtypes = [vp, u32p, u32p, i32, vp, ctypes.c_size_t, vp, u32p]
         L.tn_independence_polynomial.argtypes = [vp, u32p, i32, i32, vp, ctypes.c_size_t, vp, u32p, u32p, i32p]
+        L.tn_weighted_workspace_bytes.argtypes = [vp, ctypes.c_int, i32, ctypes.POINTER(u64)]
+        L.tn_contract_weighted.argtypes = [vp, ctypes.c_int, i32, i32p, i32p, u32p, u32p, i32, vp, ctypes.c_size_t,
+                                           vp, ctypes.POINTER(tn_result_t)]
+        L.tn_weighted_polynomial.argtypes = [vp, i32, i32p, i32p, u32p, i32, i32, vp, ctypes.c_size_t, vp, u32p,
+                                             u32p, i32p]
         L.tn_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_int, u32p, i32, ctypes.POINTER(vp)]
         L.tn_batch_info.argtypes = [vp, ctypes.POINTER(u64), i32p, i32p, ctypes.POINTER(u64)]
         L.tn_batch_contract.argtypes = [vp, vp, ctypes.c_size_t, vp, vp]
@@ -307,6 +314,72 @@ def tn_independence_polynomial(plan, primes, degree: int, ws_ptr: int, ws_bytes:
     return coeffs, res
 
 
+def _opt_i32(w):
+    """int32 array of weights (or None) and its pointer (or NULL)."""
+    if w is None:
+        return None, None
+    a = np.ascontiguousarray(np.asarray(w, dtype=np.int32).reshape(-1))
+    return a, _p32(a)
+
+
+def _problem(problem) -> int:
+    return PROBLEMS[problem] if isinstance(problem, str) else int(problem)
+
+
+def tn_weighted_workspace_bytes(plan, semiring, nslots: int = 1) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().tn_weighted_workspace_bytes(plan, _sr(semiring), int(nslots), ctypes.byref(out)),
+           "tn_weighted_workspace_bytes")
+    return int(out.value)
+
+
+def tn_contract_weighted(plan, semiring, problem, edge_w, vertex_w, primes, xs, ws_ptr: int, ws_bytes: int,
+                         stream: int) -> dict:
+    """Weighted IS / spin-glass contraction; for "modp" one residue per slot
+    (primes[q], xs[q]) in result["residues"]."""
+    ew, ewp = _opt_i32(edge_w)
+    vw, vwp = _opt_i32(vertex_w)
+    if _sr(semiring) == TN_COUNT_MODP:
+        pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint32).reshape(-1))
+        xv = np.ascontiguousarray(np.asarray(xs, dtype=np.uint32).reshape(-1))
+        if pr.size != xv.size:
+            raise TNError(TN_EINVAL, "tn_contract_weighted: primes and xs differ in length")
+        prp, xvp, k = _u32p(pr), _u32p(xv), pr.size
+    else:
+        prp, xvp, k = None, None, 0
+    r = tn_result_t()
+    _check(lib().tn_contract_weighted(plan, _sr(semiring), _problem(problem), ewp, vwp, prp, xvp, k,
+                                      ctypes.c_void_p(ws_ptr), ws_bytes, ctypes.c_void_p(stream), ctypes.byref(r)),
+           "tn_contract_weighted")
+    out = {"status": int(r.status)}
+    if _sr(semiring) == TN_COUNT_MODP:
+        out["primes"] = [int(x) for x in r.primes[:k]]
+        out["residues"] = [int(x) for x in r.residues[:k]]
+    else:
+        out["max"] = None if r.max_i32 == -(2 ** 31) else int(r.max_i32)
+        if _sr(semiring) == TN_COUNTING_TROPICAL:
+            out["count"] = int(r.count)
+    return out
+
+
+def tn_weighted_polynomial(plan, problem, edge_w, vertex_w, primes, degree: int, ws_ptr: int, ws_bytes: int,
+                           stream: int):
+    """Coefficients of a weighted network's generating polynomial and their
+    residues (see include/tn.h)."""
+    ew, ewp = _opt_i32(edge_w)
+    vw, vwp = _opt_i32(vertex_w)
+    pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint32).reshape(-1))
+    d = int(degree)
+    res = np.zeros((max(d + 1, 1), max(pr.size, 1)), dtype=np.uint32)
+    limbs = np.zeros((max(d + 1, 1), TN_POLY_LIMBS), dtype=np.uint32)
+    nl = np.zeros(max(d + 1, 1), dtype=np.int32)
+    _check(lib().tn_weighted_polynomial(plan, _problem(problem), ewp, vwp, _u32p(pr), pr.size, d,
+                                        ctypes.c_void_p(ws_ptr), ws_bytes, ctypes.c_void_p(stream), _u32p(res),
+                                        _u32p(limbs), _p32(nl)), "tn_weighted_polynomial")
+    coeffs = [sum(int(limbs[k, i]) << (32 * i) for i in range(int(nl[k]))) for k in range(d + 1)]
+    return coeffs, res
+
+
 def _is_prime32(p: int) -> bool:
     """Deterministic Miller-Rabin for p < 2^32 (bases 2, 7, 61)."""
     if p < 2:
@@ -504,6 +577,48 @@ class Plan:
         st = stream if stream is not None else torch.cuda.current_stream()
         coeffs, _ = tn_independence_polynomial(self.handle, primes, degree, workspace.data_ptr(), workspace.numel(),
                                                st.cuda_stream)
+        return coeffs
+
+    def contract_weighted(self, semiring, problem, edge_w=None, vertex_w=None, primes=None, xs=None,
+                          workspace=None, stream=None) -> dict:
+        """Weighted IS ("is") or spin-glass ("spin") contraction (tn_contract_weighted)."""
+        import torch
+        k = len(primes) if primes is not None else 1
+        need = tn_weighted_workspace_bytes(self.handle, semiring, k)
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        return tn_contract_weighted(self.handle, semiring, problem, edge_w, vertex_w, primes, xs,
+                                    workspace.data_ptr(), workspace.numel(), st.cuda_stream)
+
+    def weighted_polynomial(self, problem, edge_w=None, vertex_w=None, primes=None, degree=None,
+                            workspace=None, stream=None) -> list:
+        """Exact generating polynomial of a weighted network
+        (tn_weighted_polynomial).  degree defaults to its largest possible
+        value (sum of the weights; 2 (sum|J| + sum|h|) for the spin glass);
+        primes to the fewest 31-bit primes whose product exceeds 2^n."""
+        import torch
+        m = len(self.edges)
+        if degree is None:
+            if _problem(problem) == TN_PROBLEM_SPIN_GLASS:
+                sj = m if edge_w is None else int(np.abs(np.asarray(edge_w, dtype=np.int64)).sum())
+                sh = 0 if vertex_w is None else int(np.abs(np.asarray(vertex_w, dtype=np.int64)).sum())
+                degree = 2 * (sj + sh)
+            else:
+                degree = self.n if vertex_w is None else int(np.asarray(vertex_w, dtype=np.int64).sum())
+        if primes is None:
+            k, prod = 0, 1
+            while prod <= (1 << self.n):
+                k += 1
+                prod *= primes31(k)[-1]
+            primes = primes31(k)
+        slots = min(TN_MAX_PRIMES, len(primes) * (int(degree) + 1))
+        need = tn_weighted_workspace_bytes(self.handle, "modp", slots)
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        coeffs, _ = tn_weighted_polynomial(self.handle, problem, edge_w, vertex_w, primes, degree,
+                                           workspace.data_ptr(), workspace.numel(), st.cuda_stream)
         return coeffs
 
     def close(self):
