@@ -395,6 +395,62 @@ def polynomial_bench(tn, torch, plans, cpu: bool = True):
     return out
 
 
+def weighted_bench(tn, torch, plans, cpu: bool = True):
+    """Weighted networks on the headline plans: the spin glass of Eq. 1 with
+    seeded +-1 couplings (tropical and counting, stored leaves generated on
+    the GPU), next to the unit-weight IS contraction of the same plans; and
+    the Buckyball's exact energy histogram (ln Z at any temperature), with the
+    oracle computing the same histogram beside it."""
+    from paper_2501_00227_gb300 import properties as props
+
+    def med_ms(fn, reps=5):
+        fn()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t)
+        return statistics.median(ts) * 1e3
+
+    out = {"workload": "random 3-regular n=100 and n=140 seeds 1-3 (the headline plans), spin glass with "
+                       "couplings J uniform in {-1, +1} (seed = graph seed), h = 0; Buckyball C60, J = 1",
+           "spin_glass": []}
+    for (kind, n, seed), p in zip(GRAPHS, plans):
+        J = graphgen.random_weights(len(p.edges), seed)
+        row = {"n": n, "seed": seed}
+        for sr in ("tropical_i32", "counting"):
+            need = tn.tn_weighted_workspace_bytes(p.handle, sr, 1)
+            ws = torch.empty(max(need, p.workspace_bytes(sr)), dtype=torch.uint8, device="cuda")
+            st = torch.cuda.current_stream().cuda_stream
+            row[sr + "_ms"] = med_ms(lambda: tn.tn_contract_weighted(p.handle, sr, "spin", J, None, None, None,
+                                                                     ws.data_ptr(), ws.numel(), st))
+            row[sr + "_unit_is_ms"] = med_ms(lambda: tn.tn_contract(p.handle, sr, None, ws.data_ptr(), ws.numel(),
+                                                                    st))
+            del ws
+        r = p.contract_weighted("counting", "spin", J)
+        row["ground_energy"], row["degeneracy"] = -r["max"], r["count"]
+        out["spin_glass"].append(row)
+    n, e = graphgen.fullerene()
+    pb = tn.Plan(n, e, nrepeat=10, seed=1)
+    hist = props.energy_histogram(pb)
+    t_hist = med_ms(lambda: props.energy_histogram(pb), reps=3)
+    out["buckyball"] = {"histogram_ms": t_hist, "evaluations": 2 * (2 * hist[0] + 1), "primes": 2,
+                        "ground_state": props.spin_glass_ground_state(pb),
+                        "log_z_per_site_beta1": props.log_partition_function(pb, 1.0, histogram=hist) / n}
+    if cpu:
+        import oracle
+        oracle.build()
+        cores = oracle.set_threads(os.cpu_count() or 1)
+        t = time.perf_counter()
+        oracle.weighted_polynomial("spin", n, e, pb.order, tn.primes31(2), 2 * hist[0])
+        out["buckyball"]["cpu_baseline"] = {"value": (time.perf_counter() - t) * 1e3, "unit": "ms per histogram",
+                                            "cores": cores, "kind": "oracle",
+                                            "sample": "the Buckyball energy histogram, same order and primes"}
+    pb.close()
+    return out
+
+
 def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120):
     """Poisson request stream mixing random 3-regular graphs (n even in
     [40,160]) and King's subgraphs (L in [8,16], filling 0.8), each asking the
@@ -623,6 +679,7 @@ def run_tn(args):
         line["largest_tropical"] = largest_bench(tn, torch, peak_ops, autotune=not args.no_autotune)
         line["modp_tensor_core_ablation"] = limb_ablation_bench(tn, torch)
         line["independence_polynomial"] = polynomial_bench(tn, torch, plans, cpu=not args.no_cpu_baseline)
+        line["weighted"] = weighted_bench(tn, torch, plans, cpu=not args.no_cpu_baseline)
     if rank == 0 and not args.no_batching:
         line["batching"] = batching_bench(tn, torch)
     if rank == 0 and not args.no_serving:
