@@ -1,7 +1,8 @@
-"""Solution-space properties of Sec. 5.3 that follow from the independence
-polynomial I(G, x) = sum_k c_k x^k (Eq. 13), computed on the GPU by
-``Plan.independence_polynomial`` (weighted mod-p contractions, interpolation,
-CRT):
+"""Solution-space properties of Sec. 5.3 computed from the GPU contractions.
+
+From the independence polynomial I(G, x) = sum_k c_k x^k (Eq. 13), computed
+on the GPU by ``Plan.independence_polynomial`` (weighted mod-p contractions,
+interpolation, CRT):
 
   counting_max(plan, k)  the k highest nonzero orders of I with their
                          coefficients (CountingMax(k), a TruncatedPoly{k}
@@ -14,6 +15,11 @@ The paper computes both with dedicated element types in one contraction;
 here they are read off the exact polynomial, which costs alpha + 1
 evaluations per prime instead of one wider contraction but gives the same
 numbers (counts are exact integers, not saturated).
+
+For the spin glass of Eq. 1: the ground state (CountingMin) from the
+counting contraction of -H, the exact energy histogram from
+``Plan.weighted_polynomial``, and ln Z(beta) (PartitionFunction) summed from
+that histogram.
 """
 from __future__ import annotations
 
