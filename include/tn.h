@@ -281,6 +281,23 @@ int tn_weighted_polynomial(tn_plan_t plan, int32_t problem, const int32_t *edge_
                            size_t ws_bytes, void *cuda_stream, uint32_t *coeff_residues, uint32_t *coeff_limbs,
                            int32_t *coeff_nlimbs);
 
+/* One optimal configuration (the SingleConfigMax property of Sec. 5.3,
+ * Table 1): the (max,+) int32 contraction of the network (problem, edge_w,
+ * vertex_w as for tn_contract_weighted; unit-weight IS when both weight
+ * arrays are NULL) with every intermediate kept, then a backward pass on the
+ * GPU that fixes, from the root down, each step's summed labels to the
+ * first assignment reaching the step's output entry.  value = the maximum
+ * (MIS size / largest weight / -E_min); config[v] in {0, 1} for the n
+ * vertices (spin s = 2 config - 1 for the spin glass) is a configuration
+ * reaching it.  Where several do, which one is returned depends on the
+ * order (the lowest-index maximiser of each step).  d_workspace: at least
+ * tn_single_config_workspace_bytes (all intermediates of the plan at once,
+ * int32), 256-byte aligned.  Synchronous.  Errors as tn_contract_weighted;
+ * TN_EINVAL also when no configuration is allowed. */
+int tn_single_config_workspace_bytes(tn_plan_t plan, uint64_t *out);
+int tn_single_config_max(tn_plan_t plan, int32_t problem, const int32_t *edge_w, const int32_t *vertex_w,
+                         void *d_workspace, size_t ws_bytes, void *cuda_stream, int32_t *value, uint8_t *config);
+
 /* Measured launch shapes.  The paper leaves the kernel schedule to the
  * contraction backend; this table lets an autotuner (tune.py in the Python
  * package) replace the host's estimate for given step shapes.  entries holds

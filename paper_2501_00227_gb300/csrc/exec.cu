@@ -734,9 +734,9 @@ size_t exec_acc_bytes(tn_semiring_t s) {
 }
 
 int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods_v, int32_t nprimes, void* ws,
-                 size_t ws_bytes, void* stream, void* d_raw, void* d_trace, const LeafBuffers* leaves) {
+                 size_t ws_bytes, void* stream, void* d_raw, void* d_trace, const LeafBuffers* leaves, bool keep) {
   int rc;
-  ExecPlan* X = exec_plan_get(p, s, nprimes, &rc);
+  ExecPlan* X = keep ? exec_plan_get_h(p, s, nprimes, 1, false, &rc, true) : exec_plan_get(p, s, nprimes, &rc);
   if (!X) return rc;
   if (ws_bytes < X->total_bytes) return TN_ENOMEM;
   {

@@ -81,6 +81,7 @@ struct ExecPlan {
   int32_t ngroups = 0;
   int32_t group_h = 1;               // group height limit the plan was built with
   bool batched = false;              // built for a batch / served group
+  bool keep = false;                 // every intermediate keeps its own arena block (no reuse)
   int64_t arena_entries = 0;
   int64_t root_off = 0;
   int32_t root_step = -1;
@@ -107,7 +108,8 @@ ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc)
 // CTA runs back to back; 1 disables grouping).
 // height: group height limit; batched: the plan runs inside a batch or a
 // served group (launch shapes assume parallelism across networks).
-ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int height, bool batched, int* rc);
+ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int height, bool batched, int* rc,
+                          bool keep = false);
 // TN_GROUP_HEIGHT, else 1.
 int group_height();
 
@@ -130,8 +132,11 @@ struct LeafBuffers {
 
 // Enqueues one contraction through the executor (exec.cu); leaves NULL:
 // the unit-weight IS leaves are generated inside the kernels.
+// keep: use the plan whose intermediates all stay in the arena after the
+// launch (no block reuse, no groups), for a backward pass over them.
 int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods, int32_t nprimes, void* ws,
-                 size_t ws_bytes, void* stream, void* d_raw, void* d_trace, const LeafBuffers* leaves = nullptr);
+                 size_t ws_bytes, void* stream, void* d_raw, void* d_trace, const LeafBuffers* leaves = nullptr,
+                 bool keep = false);
 
 // Launches the executor with the tables already on the device at d_tables.
 int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods, void* ws, void* stream, void* d_raw,

@@ -219,7 +219,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
           const int pr = prod(id);
           if (pr < 0 || owner(pr) == st) continue;  // a leaf, or internal to this group
           dep[st].push_back(owner(pr));
-          arena.release(c_off[pr], int64_t(1) << p->steps[pr].g.rc, st);
+          if (!X->keep) arena.release(c_off[pr], int64_t(1) << p->steps[pr].g.rc, st);
         }
       }
     }
@@ -497,7 +497,8 @@ ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc)
   return exec_plan_get_h(p, s, nprimes, group_height(), false, rc);
 }
 
-ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H, bool batched, int* rc) {
+ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H, bool batched, int* rc, bool keep) {
+  if (keep) H = 1;
   if (!p->exec_cache) {
     static std::mutex init_mu;
     std::lock_guard<std::mutex> lk(init_mu);
@@ -507,7 +508,7 @@ ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H,
   const int np = s == TN_COUNT_MODP ? nprimes : 1;
   std::lock_guard<std::mutex> lk(c->mu);
   for (auto& x : c->plans)
-    if (x->semiring == s && x->nprimes == np && x->group_h == H && x->batched == batched &&
+    if (x->semiring == s && x->nprimes == np && x->group_h == H && x->batched == batched && x->keep == keep &&
         x->tune_gen == tune_generation()) {
       *rc = TN_OK;
       return x.get();
@@ -517,6 +518,7 @@ ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H,
   std::unique_ptr<ExecPlan> X(new ExecPlan());
   X->group_h = H;
   X->batched = batched;
+  X->keep = keep;
   X->tune_gen = tune_generation();
   *rc = build_exec(p, s, nprimes, X.get());
   if (*rc != TN_OK) return nullptr;

@@ -137,11 +137,17 @@ struct WeightedLayout {
   int64_t entries, stride;
 };
 
-WeightedLayout weighted_layout(tn_plan_s* p, tn_semiring_t s, int32_t nslots) {
+size_t keep_plan_bytes(tn_plan_s* p, tn_semiring_t s, int32_t nslots) {
+  int rc;
+  ExecPlan* X = exec_plan_get_h(p, s, nslots, 1, false, &rc, true);
+  return X ? X->total_bytes : ~size_t(0) / 2;
+}
+
+WeightedLayout weighted_layout(tn_plan_s* p, tn_semiring_t s, int32_t nslots, bool keep) {
   WeightedLayout L;
   L.entries = 4 * int64_t(p->m) + 2 * int64_t(p->n);
   L.stride = static_cast<int64_t>(align256(4 * size_t(L.entries)) / 4);
-  L.exec_bytes = align256(required_bytes(p, s, nslots));
+  L.exec_bytes = align256(keep ? keep_plan_bytes(p, s, nslots) : required_bytes(p, s, nslots));
   L.leaf_off = L.exec_bytes;
   size_t leaf_bytes = 4 * size_t(L.stride) * (s == TN_COUNT_MODP ? size_t(nslots) : 1);
   L.leaf1_off = L.leaf_off + leaf_bytes;
@@ -177,15 +183,18 @@ int check_weights(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t*
 
 // Weighted contraction of slots (primes[q], xs[q]) (mod p) or of one
 // max-plus / counting network; the raw result block is copied to raw_out.
+// keep: contract with the executor plan that keeps every intermediate
+// (its layout, and the leaf buffer's offset, are returned in *layout).
 int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw,
                           const uint32_t* primes, const uint32_t* xs, int32_t nslots, void* d_ws, size_t ws_bytes,
-                          cudaStream_t st, unsigned char* raw_out) {
+                          cudaStream_t st, unsigned char* raw_out, bool keep, size_t* leaf_off) {
   ModTable mods;
   int rc = s == TN_COUNT_MODP ? make_mod_table_slots(primes, xs, nslots, &mods)
                               : make_mod_table_checked(s, nullptr, 0, &mods);
   if (rc) return rc;
   const int32_t np = s == TN_COUNT_MODP ? nslots : 1;
-  const WeightedLayout L = weighted_layout(p, s, np);
+  const WeightedLayout L = weighted_layout(p, s, np, keep);
+  if (leaf_off) *leaf_off = L.leaf_off;
   if (ws_bytes < L.total) return TN_ENOMEM;
   char* w = static_cast<char*>(d_ws);
   // the weights (n + m integers) are copied every call: the layout depends on
@@ -217,7 +226,7 @@ int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const 
   if (rc) return rc;
   LeafBuffers lb{la.l0, la.l1, L.stride};
   void* d_raw = w + 64;
-  rc = exec_enqueue(p, s, &mods, np, d_ws, L.exec_bytes, st, d_raw, nullptr, &lb);
+  rc = exec_enqueue(p, s, &mods, np, d_ws, L.exec_bytes, st, d_raw, nullptr, &lb, keep);
   if (rc) return rc;
   rc = cuda_rc(cudaMemcpyAsync(raw_out, d_raw, TN_RAW_BYTES, cudaMemcpyDeviceToHost, st));
   if (!rc) rc = cuda_rc(cudaStreamSynchronize(st));
@@ -228,8 +237,8 @@ int weighted_checks(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_
   return check_weights(p, s, problem, ew, vw);
 }
 
-size_t weighted_workspace(tn_plan_s* p, tn_semiring_t s, int32_t nslots) {
-  return weighted_layout(p, s, s == TN_COUNT_MODP ? nslots : 1).total;
+size_t weighted_workspace(tn_plan_s* p, tn_semiring_t s, int32_t nslots, bool keep) {
+  return weighted_layout(p, s, s == TN_COUNT_MODP ? nslots : 1, keep).total;
 }
 
 }  // namespace tn
@@ -242,7 +251,7 @@ int tn_weighted_workspace_bytes(tn_plan_t plan, tn_semiring_t semiring, int32_t 
   if (!plan || !out || semiring < TN_TROPICAL_F32 || semiring > TN_COUNT_MODP) return TN_EINVAL;
   if (semiring == TN_COUNT_MODP && (nslots < 1 || nslots > TN_MAX_PRIMES)) return TN_EINVAL;
   try {
-    *out = weighted_workspace(plan, semiring, nslots);
+    *out = weighted_workspace(plan, semiring, nslots, false);
   } catch (const std::bad_alloc&) {
     return TN_ENOMEM;
   }
@@ -260,7 +269,7 @@ int tn_contract_weighted(tn_plan_t plan, tn_semiring_t semiring, int32_t problem
   try {
     unsigned char raw[TN_RAW_BYTES];
     rc = contract_weighted_raw(plan, semiring, problem, edge_w, vertex_w, primes, xs, nslots, d_workspace, ws_bytes,
-                               static_cast<cudaStream_t>(cuda_stream), raw);
+                               static_cast<cudaStream_t>(cuda_stream), raw, false, nullptr);
     if (rc) return rc;
     if (semiring != TN_COUNT_MODP) {
       ModTable mods;

@@ -98,6 +98,9 @@ def lib():
         L.tn_contract_modp_x.argtypes = [vp, u32p, u32p, i32, vp, ctypes.c_size_t, vp, u32p]
         L.tn_independence_polynomial.argtypes = [vp, u32p, i32, i32, vp, ctypes.c_size_t, vp, u32p, u32p, i32p]
         L.tn_weighted_workspace_bytes.argtypes = [vp, ctypes.c_int, i32, ctypes.POINTER(u64)]
+        L.tn_single_config_workspace_bytes.argtypes = [vp, ctypes.POINTER(u64)]
+        L.tn_single_config_max.argtypes = [vp, i32, i32p, i32p, vp, ctypes.c_size_t, vp, i32p,
+                                           ctypes.POINTER(ctypes.c_uint8)]
         L.tn_contract_weighted.argtypes = [vp, ctypes.c_int, i32, i32p, i32p, u32p, u32p, i32, vp, ctypes.c_size_t,
                                            vp, ctypes.POINTER(tn_result_t)]
         L.tn_weighted_polynomial.argtypes = [vp, i32, i32p, i32p, u32p, i32, i32, vp, ctypes.c_size_t, vp, u32p,
@@ -380,6 +383,24 @@ def tn_weighted_polynomial(plan, problem, edge_w, vertex_w, primes, degree: int,
     return coeffs, res
 
 
+def tn_single_config_workspace_bytes(plan) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().tn_single_config_workspace_bytes(plan, ctypes.byref(out)), "tn_single_config_workspace_bytes")
+    return int(out.value)
+
+
+def tn_single_config_max(plan, problem, edge_w, vertex_w, n: int, ws_ptr: int, ws_bytes: int, stream: int):
+    """(maximum, configuration as a uint8 array of n 0/1 values)."""
+    ew, ewp = _opt_i32(edge_w)
+    vw, vwp = _opt_i32(vertex_w)
+    val = np.zeros(1, dtype=np.int32)
+    cfg = np.zeros(max(int(n), 1), dtype=np.uint8)
+    _check(lib().tn_single_config_max(plan, _problem(problem), ewp, vwp, ctypes.c_void_p(ws_ptr), ws_bytes,
+                                      ctypes.c_void_p(stream), _p32(val),
+                                      cfg.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))), "tn_single_config_max")
+    return int(val[0]), cfg[: int(n)]
+
+
 def _is_prime32(p: int) -> bool:
     """Deterministic Miller-Rabin for p < 2^32 (bases 2, 7, 61)."""
     if p < 2:
@@ -620,6 +641,16 @@ class Plan:
         coeffs, _ = tn_weighted_polynomial(self.handle, problem, edge_w, vertex_w, primes, degree,
                                            workspace.data_ptr(), workspace.numel(), st.cuda_stream)
         return coeffs
+
+    def single_config_max(self, problem="is", edge_w=None, vertex_w=None, workspace=None, stream=None):
+        """(maximum, one configuration reaching it) (tn_single_config_max)."""
+        import torch
+        need = tn_single_config_workspace_bytes(self.handle)
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        return tn_single_config_max(self.handle, problem, edge_w, vertex_w, self.n, workspace.data_ptr(),
+                                    workspace.numel(), st.cuda_stream)
 
     def close(self):
         if getattr(self, "handle", None):
