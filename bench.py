@@ -451,6 +451,43 @@ def weighted_bench(tn, torch, plans, cpu: bool = True):
     return out
 
 
+def single_config_bench(tn, torch, plans):
+    """SingleConfigMax on the headline plans: the (max,+) contraction with
+    every intermediate kept plus the GPU backward pass, timed end to end
+    (synchronous call), next to the plain tropical contraction; the returned
+    configuration is checked for independence and size."""
+    out = {"workload": "random 3-regular n=100 and n=140 seeds 1-3 (the headline plans), unit weights",
+           "instances": []}
+    st = torch.cuda.current_stream().cuda_stream
+    for (kind, n, seed), p in zip(GRAPHS, plans):
+        ws = torch.empty(tn.tn_single_config_workspace_bytes(p.handle), dtype=torch.uint8, device="cuda")
+
+        def run():
+            return tn.tn_single_config_max(p.handle, "is", None, None, p.n, ws.data_ptr(), ws.numel(), st)
+
+        def plain():
+            return tn.tn_contract(p.handle, "tropical_i32", None, ws.data_ptr(), ws.numel(), st)
+
+        res = {}
+        for name, fn in (("single_config", run), ("tropical", plain)):
+            fn()
+            ts = []
+            for _ in range(5):
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                r = fn()
+                ts.append(time.perf_counter() - t)
+            res[name] = (statistics.median(ts) * 1e3, r)
+        val, cfg = res["single_config"][1]
+        e = p.edges
+        valid = not bool(np.any(cfg[e[:, 0]].astype(bool) & cfg[e[:, 1]].astype(bool))) and int(cfg.sum()) == val
+        out["instances"].append({"n": n, "seed": seed, "mis": val, "valid": valid,
+                                 "single_config_ms": res["single_config"][0], "tropical_ms": res["tropical"][0],
+                                 "keep_workspace_mb": ws.numel() / 2 ** 20})
+        del ws
+    return out
+
+
 def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120):
     """Poisson request stream mixing random 3-regular graphs (n even in
     [40,160]) and King's subgraphs (L in [8,16], filling 0.8), each asking the
@@ -680,6 +717,7 @@ def run_tn(args):
         line["modp_tensor_core_ablation"] = limb_ablation_bench(tn, torch)
         line["independence_polynomial"] = polynomial_bench(tn, torch, plans, cpu=not args.no_cpu_baseline)
         line["weighted"] = weighted_bench(tn, torch, plans, cpu=not args.no_cpu_baseline)
+        line["single_config"] = single_config_bench(tn, torch, plans)
     if rank == 0 and not args.no_batching:
         line["batching"] = batching_bench(tn, torch)
     if rank == 0 and not args.no_serving:
