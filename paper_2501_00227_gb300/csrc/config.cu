@@ -3,8 +3,8 @@
 //
 // The forward pass is the (max,+) contraction of the network (unit-weight
 // or weighted IS, or the spin glass maximising -H) with the executor plan
-// that keeps every intermediate in the arena.  The backward pass walks the
-// pairwise steps from the root down.  When a step is reached, the labels of
+// that keeps every intermediate, and the leaves, in the arena.  The
+// backward pass walks the pairwise steps from the root down.  When a step is reached, the labels of
 // its output C are already fixed (by the step that consumed C), so its
 // output entry c is known; the step's summed labels K are then set to the
 // first assignment t (lowest index) with A[a(c, t)] + B[b(c, t)] = C[c],
@@ -29,7 +29,7 @@
 namespace tn {
 int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw,
                           const uint32_t* primes, const uint32_t* xs, int32_t nslots, void* d_ws, size_t ws_bytes,
-                          cudaStream_t st, unsigned char* raw_out, bool keep, size_t* leaf_off);
+                          cudaStream_t st, unsigned char* raw_out, bool keep, ExecPlan** Xout);
 int weighted_checks(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw);
 size_t weighted_workspace(tn_plan_s* p, tn_semiring_t s, int32_t nslots, bool keep);
 }  // namespace tn
@@ -38,22 +38,22 @@ namespace tn {
 namespace dev {
 namespace {
 
-// Step record of the backward walk (plan order); operand sources: 0 = arena
-// intermediate, 1 = stored leaf, 2 = the rank-0 identity.  Source codes of
-// an operand bit: j < 32 -> output bit j, 32 + j -> summed bit j.
+// Step record of the backward walk (plan order); operand sources: 0 = an
+// arena tensor (intermediate, or leaf of the stored-leaf plan), 2 = the
+// rank-0 identity.  Source codes of an operand bit: j < 32 -> output bit j,
+// 32 + j -> summed bit j.
 struct BtStep {
   int32_t ra, rb, rc, nk;
   int32_t a_src, b_src;
   int32_t lab;   // first entry in the label pool: LC (rc), K (nk), codes of A (ra), codes of B (rb)
   int32_t pad_;
-  int64_t a_off, b_off, c_off;  // entry offsets (arena or leaf buffer)
+  int64_t a_off, b_off, c_off;  // arena entry offsets
 };
 
 struct BtArgs {
   const BtStep* steps;
   const int32_t* pool;
-  const int32_t* arena;   // int32 (max,+) values of the intermediates
-  const int32_t* leaves;  // int32 (max,+) values of the leaf tensors
+  const int32_t* arena;   // int32 (max,+) values of the intermediates and leaves
   int8_t* asg;            // out: the value of every label (vertex)
   int32_t* status;        // out: 0, or 1 + the step where no maximiser was found
   int32_t nsteps;
@@ -62,7 +62,7 @@ struct BtArgs {
 
 __device__ __forceinline__ int32_t bt_value(const BtArgs& a, int32_t src, int64_t off, uint32_t e) {
   if (src == 2) return 0;
-  return (src == 1 ? a.leaves : a.arena)[off + e];
+  return a.arena[off + e];
 }
 
 __global__ void __launch_bounds__(256) k_backtrack(const __grid_constant__ BtArgs a) {
@@ -132,11 +132,11 @@ int build_bt(tn_plan_s* p, const ExecPlan* X, BtImage* B) {
       *src = 0;
       *off = c_off[t.producer];
     } else if (t.kind == kOpEdge) {
-      *src = 1;
-      *off = 4 * int64_t(id);
+      *src = 0;
+      *off = X->leaf_base + 4 * int64_t(id);
     } else if (t.kind == kOpVertex) {
-      *src = 1;
-      *off = 4 * int64_t(p->m) + 2 * int64_t(id - p->m);
+      *src = 0;
+      *off = X->leaf_base + 4 * int64_t(p->m) + 2 * int64_t(id - p->m);
     } else {
       *src = 2;
       *off = 0;
@@ -212,17 +212,18 @@ int tn_single_config_max(tn_plan_t plan, int32_t problem, const int32_t* edge_w,
     size_t bt_off;
     if (ws_bytes < config_workspace(plan, &bt_off)) return TN_ENOMEM;
     int rcx;
-    ExecPlan* X = exec_plan_get_h(plan, TN_TROPICAL_I32, 1, 1, false, &rcx, true);
+    ExecPlan* X = exec_plan_get_h(plan, TN_TROPICAL_I32, 1, 1, false, &rcx, true, true);
     if (!X) return rcx;
     BtImage B;
     rc = build_bt(plan, X, &B);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     unsigned char raw[TN_RAW_BYTES];
-    size_t leaf_off;
+    ExecPlan* Xc = nullptr;
     rc = contract_weighted_raw(plan, TN_TROPICAL_I32, problem, edge_w, vertex_w, nullptr, nullptr, 0, d_workspace,
-                               bt_off, st, raw, true, &leaf_off);
+                               bt_off, st, raw, true, &Xc);
     if (rc) return rc;
+    if (Xc != X) return TN_EINVAL;  // the tables above describe the plan that ran
     uint32_t flags;
     std::memcpy(&flags, raw + 96, 4);
     if (flags) return TN_ETIMEOUT;
@@ -243,7 +244,6 @@ int tn_single_config_max(tn_plan_t plan, int32_t problem, const int32_t* edge_w,
     a.steps = reinterpret_cast<const dev::BtStep*>(d_steps);
     a.pool = reinterpret_cast<const int32_t*>(d_pool);
     a.arena = reinterpret_cast<const int32_t*>(w + X->arena_base);
-    a.leaves = reinterpret_cast<const int32_t*>(w + leaf_off);
     a.asg = reinterpret_cast<int8_t*>(d_asg);
     a.status = reinterpret_cast<int32_t*>(d_status);
     a.nsteps = static_cast<int32_t>(B.steps.size());

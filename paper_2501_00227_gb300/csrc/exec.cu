@@ -46,12 +46,6 @@ struct ExecArgs {
   unsigned long long* trace;  // optional: 8 words per task (see tn_contract_trace)
   int32_t nraw;               // raw result slots (networks in the launch)
   int32_t pad2_;
-  // stored leaves (weighted networks): when leaf0 is set, edge and vertex
-  // leaf operands are read from this buffer at their step's a_off / b_off
-  // (values; counts at leaf1; mod p blocks leaf_stride entries apart)
-  const char* leaf0;
-  const char* leaf1;
-  int64_t leaf_stride;
 };
 
 constexpr uint32_t kStatusTimeout = 1u;
@@ -76,21 +70,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-__device__ __forceinline__ bool stored_leaf(const ExecArgs& a, int32_t kind) {
-  return a.leaf0 != nullptr && (kind == kOpEdge || kind == kOpVertex);
-}
-
 __device__ __forceinline__ Operand exec_operand(const ExecArgs& a, int32_t kind, int64_t off) {
   Operand o;
-  o.vx = 1;
-  if (stored_leaf(a, kind)) {
-    o.kind = kOpArena;
-    o.p0 = a.leaf0 + 4 * off;
-    o.p1 = a.leaf1 ? a.leaf1 + 8 * off : nullptr;
-    o.prime_stride = a.leaf_stride;
-    return o;
-  }
   o.kind = kind;
+  o.vx = 1;
   o.p0 = a.r0 + 4 * off;
   o.p1 = a.r1 ? a.r1 + 8 * off : nullptr;
   o.prime_stride = a.prime_stride;
@@ -282,43 +265,37 @@ __device__ __forceinline__ void exec_naive_mp(const ExecArgs& a, const ExecStep&
   const uint32_t* pa[NP];
   const uint32_t* pb[NP];
   uint32_t* pc[NP];
-  // stored leaves are read like arena tensors, from the leaf buffer
-  const bool a_leaf = stored_leaf(a, g.a_kind), b_leaf = stored_leaf(a, g.b_kind);
-  const int32_t a_kind = a_leaf ? kOpArena : g.a_kind, b_kind = b_leaf ? kOpArena : g.b_kind;
-  const char* a_base = a_leaf ? a.leaf0 : a.r0;
-  const char* b_base = b_leaf ? a.leaf0 : a.r0;
-  const int64_t a_stride = a_leaf ? a.leaf_stride : a.prime_stride;
-  const int64_t b_stride = b_leaf ? a.leaf_stride : a.prime_stride;
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
     mp.q[q] = a.mods.q[q0 + q];
-    pa[q] = a_kind == kOpShared ? reinterpret_cast<const uint32_t*>(gsm + st.a_off) + (int64_t(q0 + q) << g.ra)
-                                : reinterpret_cast<const uint32_t*>(a_base + 4 * st.a_off) + int64_t(q0 + q) * a_stride;
-    pb[q] = b_kind == kOpShared ? reinterpret_cast<const uint32_t*>(gsm + st.b_off) + (int64_t(q0 + q) << g.rb)
-                                : reinterpret_cast<const uint32_t*>(b_base + 4 * st.b_off) + int64_t(q0 + q) * b_stride;
+    const int64_t off = int64_t(q0 + q) * a.prime_stride;
+    pa[q] = g.a_kind == kOpShared ? reinterpret_cast<const uint32_t*>(gsm + st.a_off) + (int64_t(q0 + q) << g.ra)
+                                  : reinterpret_cast<const uint32_t*>(a.r0 + 4 * st.a_off) + off;
+    pb[q] = g.b_kind == kOpShared ? reinterpret_cast<const uint32_t*>(gsm + st.b_off) + (int64_t(q0 + q) << g.rb)
+                                  : reinterpret_cast<const uint32_t*>(a.r0 + 4 * st.b_off) + off;
     pc[q] = st.c_shared ? reinterpret_cast<uint32_t*>(gsm + st.c_off) + (int64_t(q0 + q) << g.rc)
-                        : reinterpret_cast<uint32_t*>(a.r0 + 4 * st.c_off) + int64_t(q0 + q) * a.prime_stride;
+                        : reinterpret_cast<uint32_t*>(a.r0 + 4 * st.c_off) + off;
   }
   auto la = [&](uint32_t e) {
     ModValN<NP> v;
-    if (a_kind == kOpShared) {
+    if (g.a_kind == kOpShared) {
 #pragma unroll
       for (int q = 0; q < NP; ++q) v.v[q] = pa[q][e];
       return v;
     }
-    if (a_kind != kOpArena) return SRN::leaf(a_kind, e, mp);
+    if (g.a_kind != kOpArena) return SRN::leaf(g.a_kind, e, mp);
 #pragma unroll
     for (int q = 0; q < NP; ++q) v.v[q] = __ldcg(pa[q] + e);
     return v;
   };
   auto lb = [&](uint32_t e) {
     ModValN<NP> v;
-    if (b_kind == kOpShared) {
+    if (g.b_kind == kOpShared) {
 #pragma unroll
       for (int q = 0; q < NP; ++q) v.v[q] = pb[q][e];
       return v;
     }
-    if (b_kind != kOpArena) return SRN::leaf(b_kind, e, mp);
+    if (g.b_kind != kOpArena) return SRN::leaf(g.b_kind, e, mp);
 #pragma unroll
     for (int q = 0; q < NP; ++q) v.v[q] = __ldcg(pb[q] + e);
     return v;
@@ -734,9 +711,10 @@ size_t exec_acc_bytes(tn_semiring_t s) {
 }
 
 int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods_v, int32_t nprimes, void* ws,
-                 size_t ws_bytes, void* stream, void* d_raw, void* d_trace, const LeafBuffers* leaves, bool keep) {
+                 size_t ws_bytes, void* stream, void* d_raw, void* d_trace, bool keep, bool stored_leaves) {
   int rc;
-  ExecPlan* X = keep ? exec_plan_get_h(p, s, nprimes, 1, false, &rc, true) : exec_plan_get(p, s, nprimes, &rc);
+  ExecPlan* X = keep || stored_leaves ? exec_plan_get_h(p, s, nprimes, 1, false, &rc, keep, stored_leaves)
+                                      : exec_plan_get(p, s, nprimes, &rc);
   if (!X) return rc;
   if (ws_bytes < X->total_bytes) return TN_ENOMEM;
   {
@@ -755,11 +733,11 @@ int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods_v, int32_t npri
       X->grid = 0;
     }
   }
-  return exec_launch_core(X, s, mods_v, ws, stream, d_raw, d_trace, X->d_tables, leaves);
+  return exec_launch_core(X, s, mods_v, ws, stream, d_raw, d_trace, X->d_tables);
 }
 
 int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods_v, void* ws, void* stream, void* d_raw,
-                     void* d_trace, const void* d_tables, const LeafBuffers* leaves) {
+                     void* d_trace, const void* d_tables) {
   const dev::ModTable& mods = *static_cast<const dev::ModTable*>(mods_v);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ws);
@@ -792,11 +770,6 @@ int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods_v, void* ws,
   a.timeout_ns = 2000000000ull;  // 2 s per wait
   a.trace = static_cast<unsigned long long*>(d_trace);
   a.nraw = X->nraw;
-  if (leaves) {
-    a.leaf0 = leaves->l0;
-    a.leaf1 = leaves->l1;
-    a.leaf_stride = leaves->stride;
-  }
   switch (s) {
     case TN_TROPICAL_F32: return dev::exec_launch_t<dev::SrF32, 1>(X, a, st);
     case TN_TROPICAL_I32: return dev::exec_launch_t<dev::SrI32, 1>(X, a, st);

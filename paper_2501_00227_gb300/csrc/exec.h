@@ -82,6 +82,8 @@ struct ExecPlan {
   int32_t group_h = 1;               // group height limit the plan was built with
   bool batched = false;              // built for a batch / served group
   bool keep = false;                 // every intermediate keeps its own arena block (no reuse)
+  bool stored_leaves = false;        // leaf operands are arena tensors at leaf_base (weighted networks)
+  int64_t leaf_base = 0;             // arena entry offset of the leaf tensors: 4 per edge, then 2 per vertex
   int64_t arena_entries = 0;
   int64_t root_off = 0;
   int32_t root_step = -1;
@@ -109,7 +111,7 @@ ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc)
 // height: group height limit; batched: the plan runs inside a batch or a
 // served group (launch shapes assume parallelism across networks).
 ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int height, bool batched, int* rc,
-                          bool keep = false);
+                          bool keep = false, bool stored_leaves = false);
 // TN_GROUP_HEIGHT, else 1.
 int group_height();
 
@@ -119,28 +121,18 @@ int32_t tune_generation();
 bool tune_lookup(tn_semiring_t s, const StepGeom& g, int* tile, int* split);
 void exec_plans_free(tn_plan_s* p);
 
-// Leaf tensors stored in device memory (weighted networks, weighted.cu):
-// 4 entries per edge, then 2 per vertex, in the semiring's layout -- values
-// at l0 (float / int32 / uint32 residues), counts at l1 (counting), and for
-// mod p one block per prime slot, `stride` entries apart.  An ExecStep's
-// a_off / b_off of a leaf operand is its entry offset in this buffer.
-struct LeafBuffers {
-  const char* l0;
-  const char* l1;
-  int64_t stride;
-};
-
-// Enqueues one contraction through the executor (exec.cu); leaves NULL:
-// the unit-weight IS leaves are generated inside the kernels.
-// keep: use the plan whose intermediates all stay in the arena after the
-// launch (no block reuse, no groups), for a backward pass over them.
+// Enqueues one contraction through the executor (exec.cu).  keep: use the
+// plan whose intermediates all stay in the arena after the launch (no block
+// reuse, no groups), for a backward pass over them.  stored_leaves: use the
+// plan whose edge / vertex leaves are arena tensors at leaf_base (written by
+// the caller before the launch) instead of being generated in the kernels.
 int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods, int32_t nprimes, void* ws,
-                 size_t ws_bytes, void* stream, void* d_raw, void* d_trace, const LeafBuffers* leaves = nullptr,
-                 bool keep = false);
+                 size_t ws_bytes, void* stream, void* d_raw, void* d_trace, bool keep = false,
+                 bool stored_leaves = false);
 
 // Launches the executor with the tables already on the device at d_tables.
 int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods, void* ws, void* stream, void* d_raw,
-                     void* d_trace, const void* d_tables, const LeafBuffers* leaves = nullptr);
+                     void* d_trace, const void* d_tables);
 
 // Merges the executor plans of several networks into one launch (batch.cu).
 int build_batch_plan(tn_plan_s* const* plans, int32_t count, tn_semiring_t semiring, int32_t nprimes,

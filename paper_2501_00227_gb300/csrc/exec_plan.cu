@@ -281,6 +281,11 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
       top += static_cast<int64_t>(align_up(size_t(1) << p->steps[st].g.rc, kArenaAlign));
     }
   X->arena_entries = std::max<int64_t>(top, kArenaAlign);
+  if (X->stored_leaves) {
+    // the leaf tensors of a weighted network, after the intermediates
+    X->leaf_base = static_cast<int64_t>(align_up(static_cast<size_t>(X->arena_entries), kArenaAlign));
+    X->arena_entries = X->leaf_base + static_cast<int64_t>(align_up(4 * size_t(p->m) + 2 * size_t(p->n), kArenaAlign));
+  }
 
   // transitive reduction of the dependencies (ancestor bitsets, exec order)
   const int words = (ns + 63) / 64;
@@ -324,19 +329,23 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
     ExecStep& E = X->steps[x];
     std::memset(&E, 0, sizeof(E));
     E.g = S.g;
+    // a stored leaf (edges first, 4 entries each, then vertices, 2 each) is
+    // an arena tensor at leaf_base; a generated leaf needs no offset
+    auto stored = [&](int32_t id) {
+      return X->stored_leaves && (p->tensors[id].kind == kOpEdge || p->tensors[id].kind == kOpVertex);
+    };
     auto off = [&](int32_t id) -> int64_t {
       const int pr = prod(id);
       if (pr < 0) {
-        // a leaf: its entry offset in a stored-leaf buffer (edges first, 4
-        // entries each, then vertices, 2 each); unused for generated leaves
-        if (id < p->m) return 4 * int64_t(id);
-        if (id < p->m + p->n) return 4 * int64_t(p->m) + 2 * int64_t(id - p->m);
-        return 0;
+        if (!stored(id)) return 0;
+        return X->leaf_base + (id < p->m ? 4 * int64_t(id) : 4 * int64_t(p->m) + 2 * int64_t(id - p->m));
       }
       return sh_off[pr] >= 0 ? sh_off[pr] : c_off[pr];
     };
     E.a_off = off(S.a_id);
     E.b_off = off(S.b_id);
+    if (stored(S.a_id)) E.g.a_kind = kOpArena;
+    if (stored(S.b_id)) E.g.b_kind = kOpArena;
     if (prod(S.a_id) >= 0 && sh_off[prod(S.a_id)] >= 0) E.g.a_kind = kOpShared;
     if (prod(S.b_id) >= 0 && sh_off[prod(S.b_id)] >= 0) E.g.b_kind = kOpShared;
     E.c_shared = sh_off[st] >= 0 ? 1 : 0;
@@ -497,8 +506,9 @@ ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc)
   return exec_plan_get_h(p, s, nprimes, group_height(), false, rc);
 }
 
-ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H, bool batched, int* rc, bool keep) {
-  if (keep) H = 1;
+ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H, bool batched, int* rc, bool keep,
+                          bool stored_leaves) {
+  if (keep || stored_leaves) H = 1;
   if (!p->exec_cache) {
     static std::mutex init_mu;
     std::lock_guard<std::mutex> lk(init_mu);
@@ -509,7 +519,7 @@ ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H,
   std::lock_guard<std::mutex> lk(c->mu);
   for (auto& x : c->plans)
     if (x->semiring == s && x->nprimes == np && x->group_h == H && x->batched == batched && x->keep == keep &&
-        x->tune_gen == tune_generation()) {
+        x->stored_leaves == stored_leaves && x->tune_gen == tune_generation()) {
       *rc = TN_OK;
       return x.get();
     }
@@ -519,6 +529,7 @@ ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H,
   X->group_h = H;
   X->batched = batched;
   X->keep = keep;
+  X->stored_leaves = stored_leaves;
   X->tune_gen = tune_generation();
   *rc = build_exec(p, s, nprimes, X.get());
   if (*rc != TN_OK) return nullptr;

@@ -33,7 +33,7 @@ int contract_enqueue(const tn_plan_s* p, tn_semiring_t s, const ModTable& mods, 
                      cudaStream_t st, void* d_raw, cudaEvent_t* step_events);
 int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw,
                           const uint32_t* primes, const uint32_t* xs, int32_t nslots, void* d_ws, size_t ws_bytes,
-                          cudaStream_t st, unsigned char* raw_out, bool keep, size_t* leaf_off);
+                          cudaStream_t st, unsigned char* raw_out, bool keep, ExecPlan** Xout);
 int weighted_checks(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw);
 }  // namespace tn
 

@@ -4,10 +4,12 @@
 //
 // The unit-weight IS network generates its leaves inside the contraction
 // kernels from the entry index.  A weighted network's leaves depend on
-// per-edge / per-vertex data, so k_leaves writes every leaf tensor once per
-// contraction into a leaf buffer in the workspace (4 entries per edge, then
-// 2 per vertex, in the semiring's layout, one block per prime slot) and the
-// executor reads leaf operands from it like intermediates.
+// per-edge / per-vertex data, so it runs with the executor plan whose leaf
+// operands are arena tensors (4 entries per edge, then 2 per vertex, at the
+// plan's leaf_base, in every prime block and in the count region alike):
+// k_leaves writes them there before each launch, and the contraction
+// kernels read them exactly like intermediates (no extra test on the hot
+// path).
 //
 // Leaf values (entry x of an edge tensor: n_u = x & 1, n_v = x >> 1):
 //   IS          B = [one, one, one, zero]; W = [one, w_v]  (tropical w_v,
@@ -33,7 +35,6 @@ namespace tn {
 int make_mod_table_slots(const uint32_t* primes, const uint32_t* xs, int32_t nslots, void* mods);
 int make_mod_table_checked(tn_semiring_t s, const uint32_t* primes, int32_t nprimes, void* mods);
 int decode_raw_any(tn_semiring_t s, const void* mods, int32_t nprimes, const unsigned char* raw, tn_result_t* out);
-size_t required_bytes(tn_plan_s* p, tn_semiring_t s, int32_t nprimes);
 }  // namespace tn
 
 namespace tn {
@@ -48,8 +49,8 @@ struct LeafArgs {
   int64_t stride;      // entries between prime-slot blocks (mod p)
   const int32_t* ew;   // J per edge (spin glass), or NULL
   const int32_t* vw;   // w_v (IS) or h_v (spin glass), or NULL
-  char* l0;
-  char* l1;
+  char* l0;            // values of the first leaf entry (prime block 0)
+  char* l1;            // counts of the first leaf entry (counting)
   uint32_t p[TN_MAX_PRIMES];
   uint32_t x[TN_MAX_PRIMES];
 };
@@ -131,28 +132,22 @@ namespace {
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? TN_OK : TN_ECUDA; }
 
-// Layout of the weighted part of the workspace, after the executor's bytes.
+// Workspace of a weighted contraction: the executor's (stored-leaf plan),
+// then the weights (n + m int32).
 struct WeightedLayout {
-  size_t exec_bytes, leaf_off, leaf1_off, ew_off, vw_off, total;
-  int64_t entries, stride;
+  size_t exec_bytes, ew_off, vw_off, total;
 };
 
-size_t keep_plan_bytes(tn_plan_s* p, tn_semiring_t s, int32_t nslots) {
-  int rc;
-  ExecPlan* X = exec_plan_get_h(p, s, nslots, 1, false, &rc, true);
-  return X ? X->total_bytes : ~size_t(0) / 2;
+ExecPlan* weighted_plan(tn_plan_s* p, tn_semiring_t s, int32_t nslots, bool keep, int* rc) {
+  return exec_plan_get_h(p, s, nslots, 1, false, rc, keep, true);
 }
 
-WeightedLayout weighted_layout(tn_plan_s* p, tn_semiring_t s, int32_t nslots, bool keep) {
-  WeightedLayout L;
-  L.entries = 4 * int64_t(p->m) + 2 * int64_t(p->n);
-  L.stride = static_cast<int64_t>(align256(4 * size_t(L.entries)) / 4);
-  L.exec_bytes = align256(keep ? keep_plan_bytes(p, s, nslots) : required_bytes(p, s, nslots));
-  L.leaf_off = L.exec_bytes;
-  size_t leaf_bytes = 4 * size_t(L.stride) * (s == TN_COUNT_MODP ? size_t(nslots) : 1);
-  L.leaf1_off = L.leaf_off + leaf_bytes;
-  if (s == TN_COUNTING_TROPICAL) leaf_bytes += align256(8 * size_t(L.entries));
-  L.ew_off = L.leaf_off + leaf_bytes;
+WeightedLayout weighted_layout(tn_plan_s* p, tn_semiring_t s, int32_t nslots, bool keep, int* rc) {
+  WeightedLayout L{};
+  ExecPlan* X = weighted_plan(p, s, nslots, keep, rc);
+  if (!X) return L;
+  L.exec_bytes = align256(X->total_bytes);
+  L.ew_off = L.exec_bytes;
   L.vw_off = L.ew_off + align256(4 * size_t(std::max(p->m, 1)));
   L.total = L.vw_off + align256(4 * size_t(std::max(p->n, 1)));
   return L;
@@ -183,25 +178,31 @@ int check_weights(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t*
 
 // Weighted contraction of slots (primes[q], xs[q]) (mod p) or of one
 // max-plus / counting network; the raw result block is copied to raw_out.
-// keep: contract with the executor plan that keeps every intermediate
-// (its layout, and the leaf buffer's offset, are returned in *layout).
+// keep: contract with the plan that keeps every intermediate; *Xout is the
+// executor plan used (its arena holds the leaves at leaf_base).
 int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw,
                           const uint32_t* primes, const uint32_t* xs, int32_t nslots, void* d_ws, size_t ws_bytes,
-                          cudaStream_t st, unsigned char* raw_out, bool keep, size_t* leaf_off) {
+                          cudaStream_t st, unsigned char* raw_out, bool keep, ExecPlan** Xout) {
   ModTable mods;
   int rc = s == TN_COUNT_MODP ? make_mod_table_slots(primes, xs, nslots, &mods)
                               : make_mod_table_checked(s, nullptr, 0, &mods);
   if (rc) return rc;
   const int32_t np = s == TN_COUNT_MODP ? nslots : 1;
-  const WeightedLayout L = weighted_layout(p, s, np, keep);
-  if (leaf_off) *leaf_off = L.leaf_off;
+  const WeightedLayout L = weighted_layout(p, s, np, keep, &rc);
+  if (rc) return rc;
+  ExecPlan* X = weighted_plan(p, s, np, keep, &rc);
+  if (!X) return rc;
+  if (Xout) *Xout = X;
   if (ws_bytes < L.total) return TN_ENOMEM;
   char* w = static_cast<char*>(d_ws);
-  // the weights (n + m integers) are copied every call: the layout depends on
-  // the number of slots
+  // the weights (n + m integers) are copied every call
   if (ew && p->m) rc = cuda_rc(cudaMemcpyAsync(w + L.ew_off, ew, 4 * size_t(p->m), cudaMemcpyHostToDevice, st));
   if (!rc && vw && p->n) rc = cuda_rc(cudaMemcpyAsync(w + L.vw_off, vw, 4 * size_t(p->n), cudaMemcpyHostToDevice, st));
   if (rc) return rc;
+  // arena regions as the executor lays them out (exec_launch_core)
+  const size_t e = static_cast<size_t>(X->arena_entries);
+  const size_t b4 = align256(4 * e);
+  char* r0 = w + X->arena_base;
   dev::LeafArgs la;
   std::memset(&la, 0, sizeof(la));
   la.m = p->m;
@@ -209,24 +210,25 @@ int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const 
   la.problem = problem;
   la.semiring = s;
   la.nslots = np;
-  la.entries = L.entries;
-  la.stride = L.stride;
+  la.entries = 4 * int64_t(p->m) + 2 * int64_t(p->n);
+  la.stride = static_cast<int64_t>(b4 / 4);
   la.ew = ew ? reinterpret_cast<const int32_t*>(w + L.ew_off) : nullptr;
   la.vw = vw ? reinterpret_cast<const int32_t*>(w + L.vw_off) : nullptr;
-  la.l0 = w + L.leaf_off;
-  la.l1 = s == TN_COUNTING_TROPICAL ? w + L.leaf1_off : nullptr;
+  la.l0 = r0 + 4 * X->leaf_base;
+  la.l1 = s == TN_COUNTING_TROPICAL ? r0 + b4 + 8 * X->leaf_base : nullptr;
   for (int q = 0; q < np && s == TN_COUNT_MODP; ++q) {
     la.p[q] = primes[q];
     la.x[q] = xs[q] % primes[q];
   }
-  const int64_t total = L.entries * np;
+  const int64_t total = la.entries * np;
   const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 1024));
-  dev::k_leaves<<<blocks, 256, 0, st>>>(la);
-  rc = cuda_rc(cudaGetLastError());
-  if (rc) return rc;
-  LeafBuffers lb{la.l0, la.l1, L.stride};
+  if (total > 0) {
+    dev::k_leaves<<<blocks, 256, 0, st>>>(la);
+    rc = cuda_rc(cudaGetLastError());
+    if (rc) return rc;
+  }
   void* d_raw = w + 64;
-  rc = exec_enqueue(p, s, &mods, np, d_ws, L.exec_bytes, st, d_raw, nullptr, &lb, keep);
+  rc = exec_enqueue(p, s, &mods, np, d_ws, L.exec_bytes, st, d_raw, nullptr, keep, true);
   if (rc) return rc;
   rc = cuda_rc(cudaMemcpyAsync(raw_out, d_raw, TN_RAW_BYTES, cudaMemcpyDeviceToHost, st));
   if (!rc) rc = cuda_rc(cudaStreamSynchronize(st));
@@ -238,7 +240,9 @@ int weighted_checks(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_
 }
 
 size_t weighted_workspace(tn_plan_s* p, tn_semiring_t s, int32_t nslots, bool keep) {
-  return weighted_layout(p, s, s == TN_COUNT_MODP ? nslots : 1, keep).total;
+  int rc = TN_OK;
+  const WeightedLayout L = weighted_layout(p, s, s == TN_COUNT_MODP ? nslots : 1, keep, &rc);
+  return rc ? ~size_t(0) : L.total;
 }
 
 }  // namespace tn
