@@ -137,6 +137,32 @@ int tn_plan(int32_t n_vertices, const int32_t *edges, int32_t m,
 int tn_order_greedy(int32_t n, const int32_t *edges, int32_t m, double alpha,
                     int32_t nrepeat, uint64_t seed, int32_t *order_out);
 
+/* Local-search order of Sec. 4.2.2 (TreeSA): simulated annealing over
+ * binary contraction trees with the four rewrites (A*B)*C = (A*C)*B =
+ * (C*B)*A and A*(B*C) = B*(A*C) = C*(B*A), cost (Eq. 10, on log2 scales)
+ *   L = log2 tc + sc_weight * max(0, log2 sc - sc_target) + rw_weight * log2 rwc,
+ * Metropolis acceptance min(1, e^{-beta dL}) (Eq. 11) for beta = beta_start,
+ * beta_start + beta_step, ... <= beta_stop, niters sweeps over all internal
+ * nodes per beta.  ntrials independent trials (host threads, nthreads = 0:
+ * one per core), each started from a greedy order (Sec. 4.2.1, one run,
+ * its own seed) or, with random_init, a random tree; the best tree seen is
+ * returned.  The paper's defaults: sc_target 20, betas 0.01:0.05:15,
+ * ntrials 10, niters 50, sc_weight 1, rw_weight 0.2.  Slicing is not part of
+ * this optimiser.  order_out: 2 * (n + m - 1) int32 (an SSA order for
+ * tn_plan); log2_out (may be NULL): log2 of tc, sc, rwc of that order. */
+typedef struct {
+    double sc_target;
+    double beta_start, beta_step, beta_stop;
+    int32_t niters;
+    int32_t ntrials;
+    double sc_weight, rw_weight;
+    int32_t random_init;
+    int32_t nthreads;
+    uint64_t seed;
+} tn_treesa_params_t;
+int tn_order_treesa(int32_t n, const int32_t *edges, int32_t m, const tn_treesa_params_t *params,
+                    int32_t *order_out, double *log2_out);
+
 /* Complexity and workspace sizes of a plan; nprimes sizes the mod-p entry. */
 int tn_plan_info(tn_plan_t plan, tn_semiring_t semiring, int32_t nprimes, tn_plan_info_t *out);
 

@@ -38,6 +38,13 @@ PRIMES31 = (2147483647, 2147483629, 2147483587, 2147483579,
             2147483563, 2147483549, 2147483543, 2147483497)
 
 
+class tn_treesa_params_t(ctypes.Structure):
+    _fields_ = [("sc_target", ctypes.c_double), ("beta_start", ctypes.c_double), ("beta_step", ctypes.c_double),
+                ("beta_stop", ctypes.c_double), ("niters", ctypes.c_int32), ("ntrials", ctypes.c_int32),
+                ("sc_weight", ctypes.c_double), ("rw_weight", ctypes.c_double), ("random_init", ctypes.c_int32),
+                ("nthreads", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
 class tn_plan_info_t(ctypes.Structure):
     _fields_ = [("log2_tc", ctypes.c_double), ("log2_sc", ctypes.c_double), ("log2_rwc", ctypes.c_double),
                 ("tc", ctypes.c_uint64), ("sc_elems", ctypes.c_uint64), ("rwc", ctypes.c_uint64),
@@ -99,6 +106,8 @@ def lib():
         L.tn_independence_polynomial.argtypes = [vp, u32p, i32, i32, vp, ctypes.c_size_t, vp, u32p, u32p, i32p]
         L.tn_weighted_workspace_bytes.argtypes = [vp, ctypes.c_int, i32, ctypes.POINTER(u64)]
         L.tn_single_config_workspace_bytes.argtypes = [vp, ctypes.POINTER(u64)]
+        L.tn_order_treesa.argtypes = [i32, i32p, i32, ctypes.POINTER(tn_treesa_params_t), i32p,
+                                      ctypes.POINTER(ctypes.c_double)]
         L.tn_single_config_max.argtypes = [vp, i32, i32p, i32p, vp, ctypes.c_size_t, vp, i32p,
                                            ctypes.POINTER(ctypes.c_uint8)]
         L.tn_contract_weighted.argtypes = [vp, ctypes.c_int, i32, i32p, i32p, u32p, u32p, i32, vp, ctypes.c_size_t,
@@ -383,6 +392,24 @@ def tn_weighted_polynomial(plan, problem, edge_w, vertex_w, primes, degree: int,
     return coeffs, res
 
 
+def tn_order_treesa(n, edges, *, sc_target: float = 20.0, betas=(1.0, 0.05, 15.0), niters: int = 50,
+                    ntrials: int = 10, sc_weight: float = 1.0, rw_weight: float = 0.2, random_init: bool = False,
+                    nthreads: int = 0, seed: int = 0):
+    """TreeSA order (Sec. 4.2.2) and log2 (tc, sc, rwc) of it.  The defaults
+    are the paper's except the first inverse temperature (1.0, not 0.01): on
+    this cost's log2 scale a start hotter than about 0.3 melts the greedy
+    starting trees of 100+ vertex graphs beyond what the schedule recovers."""
+    e = _i32(edges).reshape(-1, 2)
+    prm = tn_treesa_params_t(float(sc_target), float(betas[0]), float(betas[1]), float(betas[2]), int(niters),
+                             int(ntrials), float(sc_weight), float(rw_weight), int(bool(random_init)), int(nthreads),
+                             int(seed))
+    T = int(n) + len(e)
+    order = np.zeros((max(T - 1, 0), 2), dtype=np.int32)
+    lg = (ctypes.c_double * 3)()
+    _check(lib().tn_order_treesa(int(n), _p32(e), len(e), ctypes.byref(prm), _p32(order), lg), "tn_order_treesa")
+    return order, tuple(float(x) for x in lg)
+
+
 def tn_single_config_workspace_bytes(plan) -> int:
     out = ctypes.c_uint64()
     _check(lib().tn_single_config_workspace_bytes(plan, ctypes.byref(out)), "tn_single_config_workspace_bytes")
@@ -545,11 +572,23 @@ def tn_batch_destroy(batch):
 class Plan:
     """A contraction plan (graph + order) owning its libtn handle."""
 
-    def __init__(self, n, edges, order=None, *, nrepeat: int = 10, seed: int = 0, alpha: float = 0.0):
+    def __init__(self, n, edges, order=None, *, nrepeat: int = 10, seed: int = 0, alpha: float = 0.0,
+                 optimizer: str = "greedy", treesa=None):
+        """order None: found by `optimizer` -- "greedy" (Sec. 4.2.1, nrepeat /
+        seed / alpha) or "treesa" (Sec. 4.2.2, keyword arguments of
+        tn_order_treesa in the dict `treesa`, seed defaulting to `seed`)."""
         self.n = int(n)
         self.edges = _i32(edges).reshape(-1, 2)
-        self.order = (tn_order_greedy(n, self.edges, alpha, nrepeat, seed) if order is None
-                      else _i32(order).reshape(-1, 2))
+        if order is not None:
+            self.order = _i32(order).reshape(-1, 2)
+        elif optimizer == "treesa":
+            kw = dict(treesa or {})
+            kw.setdefault("seed", seed)
+            self.order, _ = tn_order_treesa(n, self.edges, **kw)
+        elif optimizer == "greedy":
+            self.order = tn_order_greedy(n, self.edges, alpha, nrepeat, seed)
+        else:
+            raise TNError(TN_EINVAL, f"unknown optimizer {optimizer!r}")
         self.handle = tn_plan(self.n, self.edges, self.order)
 
     def info(self, semiring=TN_TROPICAL_I32, nprimes: int = 1) -> dict:

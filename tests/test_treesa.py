@@ -1,0 +1,108 @@
+"""The TreeSA order optimiser (Sec. 4.2.2): host code, tested on the CPU.
+Its orders must be valid SSA orders, contract to the same results, carry the
+complexities the oracle computes for them, never be worse (Eq. 10) than the
+greedy tree the first trial starts from, and reach the optimum the paper
+prints for the 4-cycle of Sec. 4.1."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import graphgen as g
+import oracle as O
+from paper_2501_00227_gb300 import tn
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    from paper_2501_00227_gb300 import build as B
+    B.build()
+
+
+def _cost(lg, sc_target=20.0, ws=1.0, wrw=0.2):
+    return lg[0] + ws * max(0.0, lg[1] - sc_target) + wrw * lg[2]
+
+
+def _log2c(n, e, o):
+    return tuple(math.log2(x) for x in O.complexity(n, e, o))
+
+
+def test_c4_reaches_the_printed_optimum():
+    """Sec. 4.1: the largest tensor of the 4-cycle network has rank >= 2 in
+    any order; TreeSA prints tc = 2^5.087 (34), sc = 2^2, rwc = 2^6.109 (69)."""
+    gd = json.load(open(os.path.join(GOLD, "c4_tree.json")))
+    edges = [(u - 1, v - 1) for u, v in gd["edges_1based"]]
+    o, lg = tn.tn_order_treesa(4, edges, seed=3, ntrials=2)
+    assert O.check_order(4, edges, o)
+    assert lg[1] == 2.0 and lg[0] <= gd["tree_log2"][0] + 1e-12
+    assert lg == pytest.approx(_log2c(4, edges, o), abs=1e-12)
+
+
+@pytest.mark.parametrize("spec", ["petersen", "reg3:40:1", "er:20:0.2:3", "ksg:6:0.8:2", "square:6", "path:30",
+                                  "cycle:25", "empty:5", "complete:6"])
+def test_orders_are_valid_and_contract_to_the_same_values(spec):
+    n, e = g.by_name(spec)
+    o, lg = tn.tn_order_treesa(n, e, seed=2, ntrials=3, nthreads=2)
+    assert O.check_order(n, e, o)
+    assert lg == pytest.approx(_log2c(n, e, o), abs=1e-9)
+    ref = O.greedy_order(n, e, nrepeat=2, seed=1)
+    assert O.mis_count(n, e, o) == O.mis_count(n, e, ref)
+    assert O.count_modp(n, e, o) == O.count_modp(n, e, ref)
+
+
+@pytest.mark.parametrize("spec", ["reg3:100:1", "ksg:12:0.8:1", "square:9"])
+def test_never_worse_than_its_greedy_start(spec):
+    n, e = g.by_name(spec)
+    seed = 11
+    o, lg = tn.tn_order_treesa(n, e, seed=seed, ntrials=2, niters=10)
+    start = tn.tn_order_greedy(n, e, 0.0, 1, seed)      # the first trial's starting tree
+    assert _cost(lg) <= _cost(_log2c(n, e, start)) + 1e-9
+
+
+def test_improves_on_greedy_for_a_3_regular_graph():
+    """On a 100-vertex random 3-regular graph the annealed order needs fewer
+    multiply-adds than the best of 10 greedy runs."""
+    n, e = g.random_regular3(100, 1)
+    o, lg = tn.tn_order_treesa(n, e, seed=1, ntrials=4)
+    greedy = _log2c(n, e, tn.tn_order_greedy(n, e, 0.0, 10, 1))
+    assert lg[0] < greedy[0] - 1.0
+
+
+def test_trees_and_grids_get_small_intermediates():
+    """A path needs rank 1 only; an L x L grid can be swept with rank L."""
+    n, e = g.path(40)
+    assert tn.tn_order_treesa(n, e, seed=1, ntrials=2)[1][1] <= 1.0
+    n, e = g.square_lattice(8)
+    assert tn.tn_order_treesa(n, e, seed=1, ntrials=4)[1][1] <= 8.0
+
+
+def test_deterministic_for_a_seed_and_random_start():
+    n, e = g.erdos_renyi(24, 0.2, 5)
+    a = tn.tn_order_treesa(n, e, seed=9, ntrials=3, nthreads=3, niters=5)
+    b = tn.tn_order_treesa(n, e, seed=9, ntrials=3, nthreads=1, niters=5)
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1]
+    o, lg = tn.tn_order_treesa(n, e, seed=4, ntrials=2, niters=20, random_init=True)
+    assert O.check_order(n, e, o)
+
+
+@pytest.mark.parametrize("kw", [dict(betas=(1.0, 0.0, 2.0)), dict(betas=(3.0, 0.1, 2.0)), dict(ntrials=0),
+                                dict(niters=-1), dict(sc_weight=-1.0)])
+def test_rejects_bad_parameters(kw):
+    n, e = g.petersen()
+    with pytest.raises(tn.TNError) as ei:
+        tn.tn_order_treesa(n, e, **kw)
+    assert ei.value.code == tn.TN_EINVAL
+
+
+def test_plan_with_treesa_order():
+    n, e = g.random_regular3(60, 2)
+    p = tn.Plan(n, e, optimizer="treesa", seed=3, treesa={"ntrials": 2})
+    try:
+        assert O.check_order(n, e, p.order)
+        assert p.info("tropical_i32")["log2_tc"] == pytest.approx(_log2c(n, e, p.order)[0], abs=1e-9)
+    finally:
+        p.close()
