@@ -488,6 +488,50 @@ def single_config_bench(tn, torch, plans):
     return out
 
 
+def treesa_bench(tn, torch):
+    """Contraction order quality (Sec. 4.2): the headline 3-regular graphs and
+    the 20x20 King's subgraphs with the greedy order (nrepeat 10) and with a
+    TreeSA order (8 trials, the default schedule), each contracted in the
+    three element types on the GPU (device time, CUDA events)."""
+    st = torch.cuda.current_stream()
+    raw = torch.zeros(tn.TN_RAW_BYTES, dtype=torch.uint8, device="cuda")
+
+    def dev_ms(p, sr, primes):
+        k = len(primes) if primes else 1
+        ws = torch.empty(p.workspace_bytes(sr, k), dtype=torch.uint8, device="cuda")
+        f = lambda: tn.tn_contract_async(p.handle, sr, primes, ws.data_ptr(), ws.numel(), st.cuda_stream,
+                                         raw.data_ptr())
+        f()
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            f()
+            e1.record(st)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    out = {"workload": "random 3-regular n=100, 140 seeds 1-3 and King's subgraphs 20x20 p=0.8 seeds 1-3; "
+                       "tropical_i32 + counting + modp x3 per graph", "graphs": []}
+    specs = [(f"reg3:{n}:{s}", graphgen.random_regular3(n, s)) for _, n, s in GRAPHS]
+    specs += [(f"ksg:20:0.8:{s}", graphgen.kings_subgraph(20, 0.8, s)) for s in (1, 2, 3)]
+    for name, (n, e) in specs:
+        row = {"graph": name}
+        for opt in ("greedy", "treesa"):
+            t = time.perf_counter()
+            p = tn.Plan(n, e, nrepeat=10, seed=1, optimizer=opt, treesa={"ntrials": 8})
+            opt_s = time.perf_counter() - t
+            info = p.info("tropical_i32")
+            ms = sum(dev_ms(p, sr, pr) for sr, pr in SEMIRINGS)
+            row[opt] = {"log2_tc": info["log2_tc"], "log2_sc": info["log2_sc"], "optimize_s": opt_s,
+                        "gpu_ms_3_semirings": ms}
+            p.close()
+        row["speedup"] = row["greedy"]["gpu_ms_3_semirings"] / row["treesa"]["gpu_ms_3_semirings"]
+        out["graphs"].append(row)
+    return out
+
+
 def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120):
     """Poisson request stream mixing random 3-regular graphs (n even in
     [40,160]) and King's subgraphs (L in [8,16], filling 0.8), each asking the
@@ -718,6 +762,7 @@ def run_tn(args):
         line["independence_polynomial"] = polynomial_bench(tn, torch, plans, cpu=not args.no_cpu_baseline)
         line["weighted"] = weighted_bench(tn, torch, plans, cpu=not args.no_cpu_baseline)
         line["single_config"] = single_config_bench(tn, torch, plans)
+        line["treesa"] = treesa_bench(tn, torch)
     if rank == 0 and not args.no_batching:
         line["batching"] = batching_bench(tn, torch)
     if rank == 0 and not args.no_serving:
