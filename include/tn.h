@@ -324,6 +324,41 @@ int tn_single_config_workspace_bytes(tn_plan_t plan, uint64_t *out);
 int tn_single_config_max(tn_plan_t plan, int32_t problem, const int32_t *edge_w, const int32_t *vertex_w,
                          void *d_workspace, size_t ws_bytes, void *cuda_stream, int32_t *value, uint8_t *config);
 
+/* Slicing (Sec. 4.2.2): fix s vertex labels, contract the network once per
+ * assignment of them (slice k gives sliced label j the value bit j of k),
+ * and add the 2^s results in the element type.  Each slice's tensors lose
+ * the sliced labels, so the largest intermediate shrinks by up to 2^s, for
+ * up to 2^s times the work; slices are independent units (several GPUs take
+ * disjoint slice ranges and combine with tn_result_combine).
+ *
+ * tn_slice_labels: nslices (0..62) labels for the given order, picked one at
+ *   a time as the label whose removal leaves the smallest largest
+ *   intermediate, ties by the smallest total work.  sliced_out: nslices
+ *   int32; log2_out (may be NULL): log2 of the work of all slices together
+ *   and log2 of the largest intermediate of one slice.
+ * tn_plan_sliced: as tn_plan, with the leaves' sliced labels dropped
+ *   (sliced: nsliced distinct vertex labels, at most 62).  Such a plan runs
+ *   with stored leaves only: tn_contract, tn_contract_async and
+ *   tn_single_config_max reject it with TN_EINVAL.
+ * tn_contract_sliced: slices [slice_begin, slice_end) of a sliced plan (any
+ *   plan: 0 sliced labels is one slice), arguments and workspace
+ *   (tn_weighted_workspace_bytes) as tn_contract_weighted (problem, weights,
+ *   prime slots); out = the element type's sum of those slices (mod p:
+ *   residues per slot, no CRT).  Synchronous.
+ * tn_result_combine: out = a (+) b in the element type: max (tropical), max
+ *   with counts of ties added and saturated at 2^64 - 1 (counting), residues
+ *   added mod their slot's prime (mod p; the slots must agree, else
+ *   TN_EINVAL). */
+int tn_slice_labels(int32_t n, const int32_t *edges, int32_t m, const int32_t *order, int32_t order_len,
+                    int32_t nslices, int32_t *sliced_out, double *log2_out);
+int tn_plan_sliced(int32_t n_vertices, const int32_t *edges, int32_t m, const int32_t *order, int32_t order_len,
+                   const int32_t *sliced, int32_t nsliced, tn_plan_t *out);
+int tn_contract_sliced(tn_plan_t plan, tn_semiring_t semiring, int32_t problem, const int32_t *edge_w,
+                       const int32_t *vertex_w, const uint32_t *primes, const uint32_t *xs, int32_t nslots,
+                       uint64_t slice_begin, uint64_t slice_end, void *d_workspace, size_t ws_bytes,
+                       void *cuda_stream, tn_result_t *out);
+int tn_result_combine(tn_semiring_t semiring, const tn_result_t *a, const tn_result_t *b, tn_result_t *out);
+
 /* Measured launch shapes.  The paper leaves the kernel schedule to the
  * contraction backend; this table lets an autotuner (tune.py in the Python
  * package) replace the host's estimate for given step shapes.  entries holds

@@ -250,10 +250,16 @@ int tn_plan_info(tn_plan_t plan, tn_semiring_t semiring, int32_t nprimes, tn_pla
   out->log2_sc = std::log2(static_cast<double>(plan->sc));
   out->log2_rwc = std::log2(static_cast<double>(plan->rwc));
   out->nsteps = static_cast<int32_t>(plan->steps.size());
+  // a sliced plan runs only with stored leaves (tn_contract_sliced)
+  const bool stored = !plan->sliced.empty();
+  auto xplan = [&](tn_semiring_t sk, int* rc) {
+    const int np = nprimes < 1 ? 1 : nprimes;
+    return stored ? exec_plan_get_h(plan, sk, np, 1, false, rc, false, true) : exec_plan_get(plan, sk, np, rc);
+  };
   for (int k = 0; k < 4; ++k) {
     int rc;
     tn_semiring_t sk = static_cast<tn_semiring_t>(k + 1);
-    ExecPlan* X = exec_plan_get(plan, sk, nprimes < 1 ? 1 : nprimes, &rc);
+    ExecPlan* X = xplan(sk, &rc);
     if (!X) return rc;
     out->peak_bytes[k] = std::max(workspace_bytes(plan, sk, nprimes), X->total_bytes);
   }
@@ -265,7 +271,7 @@ int tn_plan_info(tn_plan_t plan, tn_semiring_t semiring, int32_t nprimes, tn_pla
   }
   out->nlaunch_steps = wide;
   int rc;
-  ExecPlan* X = exec_plan_get(plan, semiring, nprimes < 1 ? 1 : nprimes, &rc);
+  ExecPlan* X = xplan(semiring, &rc);
   if (!X) return rc;
   out->exec_table_bytes = X->table_bytes;
   out->exec_tasks = static_cast<int32_t>(X->tasks.size());
@@ -278,7 +284,7 @@ int tn_plan_info(tn_plan_t plan, tn_semiring_t semiring, int32_t nprimes, tn_pla
 int tn_contract_async(tn_plan_t plan, tn_semiring_t semiring, const uint32_t* primes,
                       int32_t nprimes, void* d_workspace, size_t ws_bytes, void* cuda_stream,
                       void* d_raw) {
-  if (!plan || !semiring_ok(semiring) || !d_workspace || !d_raw) return TN_EINVAL;
+  if (!plan || !semiring_ok(semiring) || !d_workspace || !d_raw || !plan->sliced.empty()) return TN_EINVAL;
   if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0) return TN_EINVAL;
   ModTable mods;
   int rc = make_mods(semiring, primes, nprimes, &mods);

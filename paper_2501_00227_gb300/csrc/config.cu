@@ -29,7 +29,7 @@
 namespace tn {
 int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw,
                           const uint32_t* primes, const uint32_t* xs, int32_t nslots, void* d_ws, size_t ws_bytes,
-                          cudaStream_t st, unsigned char* raw_out, bool keep, ExecPlan** Xout);
+                          cudaStream_t st, unsigned char* raw_out, bool keep, ExecPlan** Xout, uint64_t slice);
 int weighted_checks(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw);
 size_t weighted_workspace(tn_plan_s* p, tn_semiring_t s, int32_t nslots, bool keep);
 }  // namespace tn
@@ -131,12 +131,9 @@ int build_bt(tn_plan_s* p, const ExecPlan* X, BtImage* B) {
     if (t.kind == kOpArena) {
       *src = 0;
       *off = c_off[t.producer];
-    } else if (t.kind == kOpEdge) {
+    } else if (t.kind == kOpEdge || t.kind == kOpVertex) {
       *src = 0;
-      *off = X->leaf_base + 4 * int64_t(id);
-    } else if (t.kind == kOpVertex) {
-      *src = 0;
-      *off = X->leaf_base + 4 * int64_t(p->m) + 2 * int64_t(id - p->m);
+      *off = X->leaf_base + p->leaf_off[id];
     } else {
       *src = 2;
       *off = 0;
@@ -204,7 +201,7 @@ int tn_single_config_workspace_bytes(tn_plan_t plan, uint64_t* out) {
 
 int tn_single_config_max(tn_plan_t plan, int32_t problem, const int32_t* edge_w, const int32_t* vertex_w,
                          void* d_workspace, size_t ws_bytes, void* cuda_stream, int32_t* value, uint8_t* config) {
-  if (!plan || !d_workspace || !value || !config) return TN_EINVAL;
+  if (!plan || !d_workspace || !value || !config || !plan->sliced.empty()) return TN_EINVAL;
   if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0) return TN_EINVAL;
   int rc = weighted_checks(plan, TN_TROPICAL_I32, problem, edge_w, vertex_w);
   if (rc) return rc;
@@ -221,7 +218,7 @@ int tn_single_config_max(tn_plan_t plan, int32_t problem, const int32_t* edge_w,
     unsigned char raw[TN_RAW_BYTES];
     ExecPlan* Xc = nullptr;
     rc = contract_weighted_raw(plan, TN_TROPICAL_I32, problem, edge_w, vertex_w, nullptr, nullptr, 0, d_workspace,
-                               bt_off, st, raw, true, &Xc);
+                               bt_off, st, raw, true, &Xc, 0);
     if (rc) return rc;
     if (Xc != X) return TN_EINVAL;  // the tables above describe the plan that ran
     uint32_t flags;

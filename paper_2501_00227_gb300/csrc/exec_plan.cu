@@ -284,7 +284,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   if (X->stored_leaves) {
     // the leaf tensors of a weighted network, after the intermediates
     X->leaf_base = static_cast<int64_t>(align_up(static_cast<size_t>(X->arena_entries), kArenaAlign));
-    X->arena_entries = X->leaf_base + static_cast<int64_t>(align_up(4 * size_t(p->m) + 2 * size_t(p->n), kArenaAlign));
+    X->arena_entries = X->leaf_base + static_cast<int64_t>(align_up(static_cast<size_t>(p->leaf_entries), kArenaAlign));
   }
 
   // transitive reduction of the dependencies (ancestor bitsets, exec order)
@@ -329,17 +329,14 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
     ExecStep& E = X->steps[x];
     std::memset(&E, 0, sizeof(E));
     E.g = S.g;
-    // a stored leaf (edges first, 4 entries each, then vertices, 2 each) is
-    // an arena tensor at leaf_base; a generated leaf needs no offset
+    // a stored leaf (edges first, then vertices, 2^rank entries each) is an
+    // arena tensor at leaf_base; a generated leaf needs no offset
     auto stored = [&](int32_t id) {
       return X->stored_leaves && (p->tensors[id].kind == kOpEdge || p->tensors[id].kind == kOpVertex);
     };
     auto off = [&](int32_t id) -> int64_t {
       const int pr = prod(id);
-      if (pr < 0) {
-        if (!stored(id)) return 0;
-        return X->leaf_base + (id < p->m ? 4 * int64_t(id) : 4 * int64_t(p->m) + 2 * int64_t(id - p->m));
-      }
+      if (pr < 0) return stored(id) ? X->leaf_base + p->leaf_off[id] : 0;
       return sh_off[pr] >= 0 ? sh_off[pr] : c_off[pr];
     };
     E.a_off = off(S.a_id);
@@ -508,6 +505,11 @@ ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc)
 
 ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H, bool batched, int* rc, bool keep,
                           bool stored_leaves) {
+  if (!stored_leaves && !p->sliced.empty()) {
+    // the leaves of a sliced network depend on the slice: stored leaves only
+    *rc = TN_EINVAL;
+    return nullptr;
+  }
   if (keep || stored_leaves) H = 1;
   if (!p->exec_cache) {
     static std::mutex init_mu;

@@ -155,25 +155,40 @@ size_t workspace_bytes(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes) {
 }
 
 int build_plan(int32_t n, const int32_t* edges, int32_t m, const int32_t* order, int32_t nsteps,
-               tn_plan_s* p) {
+               tn_plan_s* p, const int32_t* sliced, int32_t nsliced) {
   if (!graph_ok(n, edges, m)) return TN_EINVAL;
   const int32_t T = n + m;
   if (nsteps != T - 1 || (nsteps > 0 && order == nullptr)) return TN_EINVAL;
+  if (nsliced < 0 || nsliced > 62 || (nsliced > 0 && sliced == nullptr)) return TN_EINVAL;
+  std::vector<char> is_sliced(static_cast<size_t>(n), 0);
+  for (int32_t j = 0; j < nsliced; ++j) {
+    if (sliced[j] < 0 || sliced[j] >= n || is_sliced[sliced[j]]) return TN_EINVAL;
+    is_sliced[sliced[j]] = 1;
+  }
   p->n = n;
   p->m = m;
   p->T = T;
   p->edges.assign(edges, edges + 2 * static_cast<size_t>(m));
   p->order.assign(order, order + 2 * static_cast<size_t>(nsteps));
+  p->sliced.assign(sliced, sliced + nsliced);
 
-  // Leaves: edges first, then vertices (the flattened einsum of Sec. 3.2).
+  // Leaves: edges first, then vertices (the flattened einsum of Sec. 3.2);
+  // a sliced label is fixed per slice, so it is dropped from every leaf.
   p->tensors.assign(static_cast<size_t>(T), TensorInfo());
   for (int32_t e = 0; e < m; ++e) {
-    p->tensors[e].labels = {edges[2 * e], edges[2 * e + 1]};
+    for (int k = 0; k < 2; ++k)
+      if (!is_sliced[edges[2 * e + k]]) p->tensors[e].labels.push_back(edges[2 * e + k]);
     p->tensors[e].kind = kOpEdge;
   }
   for (int32_t v = 0; v < n; ++v) {
-    p->tensors[m + v].labels = {v};
+    if (!is_sliced[v]) p->tensors[m + v].labels = {v};
     p->tensors[m + v].kind = kOpVertex;
+  }
+  p->leaf_off.assign(static_cast<size_t>(T), 0);
+  p->leaf_entries = 0;
+  for (int32_t t = 0; t < T; ++t) {
+    p->leaf_off[t] = p->leaf_entries;
+    p->leaf_entries += int64_t(1) << p->tensors[t].labels.size();
   }
   // Internal step list.  A network with a single leaf (one vertex, no edge)
   // has no pairwise step; it is reduced by contracting it with the rank-0

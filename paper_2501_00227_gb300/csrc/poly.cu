@@ -33,7 +33,7 @@ int contract_enqueue(const tn_plan_s* p, tn_semiring_t s, const ModTable& mods, 
                      cudaStream_t st, void* d_raw, cudaEvent_t* step_events);
 int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw,
                           const uint32_t* primes, const uint32_t* xs, int32_t nslots, void* d_ws, size_t ws_bytes,
-                          cudaStream_t st, unsigned char* raw_out, bool keep, ExecPlan** Xout);
+                          cudaStream_t st, unsigned char* raw_out, bool keep, ExecPlan** Xout, uint64_t slice);
 int weighted_checks(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw);
 }  // namespace tn
 
@@ -217,7 +217,7 @@ int tn_weighted_polynomial(tn_plan_t plan, int32_t problem, const int32_t* edge_
     auto eval = [&](const uint32_t* sp, const uint32_t* sx, int ns, uint32_t* sy) {
       unsigned char raw[TN_RAW_BYTES];
       int r = contract_weighted_raw(plan, TN_COUNT_MODP, problem, edge_w, vertex_w, sp, sx, ns, d_workspace,
-                                    ws_bytes, st, raw, false, nullptr);
+                                    ws_bytes, st, raw, false, nullptr, 0);
       if (r) return r;
       uint32_t flags;
       std::memcpy(&flags, raw + 96, 4);

@@ -88,13 +88,18 @@ struct tn_plan_s {
   uint64_t tc = 0, rwc = 0, sc = 0;
   int32_t root = -1;                     // id of the scalar result
   void* exec_cache = nullptr;            // executor plans (exec_plan.cu)
+  // Slicing (Sec. 4.2.2): sliced vertex labels are fixed per slice and
+  // dropped from every leaf; such a plan runs with stored leaves only.
+  std::vector<int32_t> sliced;           // sliced labels, in slice-bit order
+  std::vector<int64_t> leaf_off;         // entry offset of each leaf in a stored-leaf block
+  int64_t leaf_entries = 0;              // entries of all leaves (sum of 2^rank)
 };
 
 namespace tn {
 
 // Host planner (plan.cpp).
 int build_plan(int32_t n, const int32_t* edges, int32_t m, const int32_t* order, int32_t nsteps,
-               tn_plan_s* p);
+               tn_plan_s* p, const int32_t* sliced = nullptr, int32_t nsliced = 0);
 int greedy_order(int32_t n, const int32_t* edges, int32_t m, double alpha, int32_t nrepeat,
                  uint64_t seed, int32_t* order_out);
 // Label classification of one pairwise step (shared by build_plan and

@@ -42,15 +42,16 @@ namespace dev {
 namespace {
 
 struct LeafArgs {
-  int32_t m, n, problem, semiring;
+  int32_t m, n, T, problem, semiring;
   int32_t nslots;
-  int32_t pad_;
-  int64_t entries;     // 4m + 2n
-  int64_t stride;      // entries between prime-slot blocks (mod p)
-  const int32_t* ew;   // J per edge (spin glass), or NULL
-  const int32_t* vw;   // w_v (IS) or h_v (spin glass), or NULL
-  char* l0;            // values of the first leaf entry (prime block 0)
-  char* l1;            // counts of the first leaf entry (counting)
+  int64_t stride;         // entries between prime-slot blocks (mod p)
+  const int32_t* edges;   // 2m endpoints
+  const int64_t* loff;    // entry offset of each leaf (edges, then vertices)
+  const int8_t* fixed;    // per vertex: -1, or the value of a sliced label in this slice
+  const int32_t* ew;      // J per edge (spin glass), or NULL
+  const int32_t* vw;      // w_v (IS) or h_v (spin glass), or NULL
+  char* l0;               // values of leaf entry 0 (prime block 0)
+  char* l1;               // counts of leaf entry 0 (counting)
   uint32_t p[TN_MAX_PRIMES];
   uint32_t x[TN_MAX_PRIMES];
 };
@@ -65,61 +66,74 @@ __device__ uint32_t pow_mod(uint32_t b, int64_t e, uint32_t p) {
   return static_cast<uint32_t>(r);
 }
 
-// (exponent / value, allowed) of leaf entry i: value for max-plus, exponent
-// of the slot's point for mod p
-__device__ void leaf_entry(const LeafArgs& a, int64_t i, int64_t* val, int64_t* mexp, bool* allowed) {
-  *allowed = true;
-  if (i < 4 * int64_t(a.m)) {
-    const int64_t k = i >> 2;
-    const int x = static_cast<int>(i & 3);
-    if (a.problem == TN_PROBLEM_INDEPENDENT_SET) {
-      *allowed = x != 3;
-      *val = 0;
-      *mexp = 0;
-    } else {
-      const int64_t J = a.ew ? a.ew[k] : 1;
-      const int64_t ss = ((x & 1) == (x >> 1)) ? 1 : -1;  // s_u s_v
-      *val = -J * ss;
-      *mexp = J * ss + (J < 0 ? -J : J);
-    }
+// (value, exponent, allowed) of an edge / vertex tensor entry for the 0/1
+// labels n_u, n_v (vertex: n_v only): value for max-plus, exponent of the
+// slot's point for mod p
+__device__ void edge_entry(const LeafArgs& a, int64_t k, int nu, int nv, int64_t* val, int64_t* mexp, bool* ok) {
+  *ok = true;
+  if (a.problem == TN_PROBLEM_INDEPENDENT_SET) {
+    *ok = !(nu && nv);
+    *val = 0;
+    *mexp = 0;
   } else {
-    const int64_t v = (i - 4 * int64_t(a.m)) >> 1;
-    const int x = static_cast<int>((i - 4 * int64_t(a.m)) & 1);
-    if (a.problem == TN_PROBLEM_INDEPENDENT_SET) {
-      const int64_t w = a.vw ? a.vw[v] : 1;
-      *val = x ? w : 0;
-      *mexp = *val;
-    } else {
-      const int64_t h = a.vw ? a.vw[v] : 0;
-      const int64_t s = x ? 1 : -1;
-      *val = -h * s;
-      *mexp = h * s + (h < 0 ? -h : h);
-    }
+    const int64_t J = a.ew ? a.ew[k] : 1;
+    const int64_t ss = nu == nv ? 1 : -1;  // s_u s_v
+    *val = -J * ss;
+    *mexp = J * ss + (J < 0 ? -J : J);
+  }
+}
+__device__ void vertex_entry(const LeafArgs& a, int64_t v, int nv, int64_t* val, int64_t* mexp, bool* ok) {
+  *ok = true;
+  if (a.problem == TN_PROBLEM_INDEPENDENT_SET) {
+    const int64_t w = a.vw ? a.vw[v] : 1;
+    *val = nv ? w : 0;
+    *mexp = *val;
+  } else {
+    const int64_t h = a.vw ? a.vw[v] : 0;
+    const int64_t s = nv ? 1 : -1;
+    *val = -h * s;
+    *mexp = h * s + (h < 0 ? -h : h);
   }
 }
 
+// One thread per (prime slot, leaf): every entry of the leaf.  A leaf keeps
+// its unsliced labels in order (u, then v); entry bit j is the j-th of them,
+// and a sliced label takes its value in this slice.
 __global__ void k_leaves(const __grid_constant__ LeafArgs a) {
-  const int64_t total = a.entries * (a.semiring == TN_COUNT_MODP ? a.nslots : 1);
+  const int nq = a.semiring == TN_COUNT_MODP ? a.nslots : 1;
+  const int64_t total = int64_t(a.T) * nq;
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t i = t % a.entries;
-    const int q = static_cast<int>(t / a.entries);
-    int64_t val, mexp;
-    bool ok;
-    leaf_entry(a, i, &val, &mexp, &ok);
-    switch (a.semiring) {
-      case TN_TROPICAL_F32:
-        reinterpret_cast<float*>(a.l0)[i] = ok ? static_cast<float>(val) : -INFINITY;
-        break;
-      case TN_TROPICAL_I32:
-        reinterpret_cast<int32_t*>(a.l0)[i] = ok ? static_cast<int32_t>(val) : TN_I32_NEG_INF;
-        break;
-      case TN_COUNTING_TROPICAL:
-        reinterpret_cast<int32_t*>(a.l0)[i] = ok ? static_cast<int32_t>(val) : TN_I32_NEG_INF;
-        reinterpret_cast<uint64_t*>(a.l1)[i] = ok ? 1ull : 0ull;
-        break;
-      default:
-        reinterpret_cast<uint32_t*>(a.l0)[q * a.stride + i] = ok ? pow_mod(a.x[q], mexp, a.p[q]) : 0u;
-        break;
+    const int32_t leaf = static_cast<int32_t>(t % a.T);
+    const int q = static_cast<int>(t / a.T);
+    const bool edge = leaf < a.m;
+    const int32_t u = edge ? a.edges[2 * leaf] : leaf - a.m;
+    const int32_t v = edge ? a.edges[2 * leaf + 1] : -1;
+    const int fu = a.fixed[u], fv = edge ? a.fixed[v] : 0;
+    const int rank = (fu < 0 ? 1 : 0) + (edge && fv < 0 ? 1 : 0);
+    for (int x = 0; x < (1 << rank); ++x) {
+      int bit = 0;
+      const int nu = fu < 0 ? (x >> bit++) & 1 : fu;
+      const int nv = edge ? (fv < 0 ? (x >> bit) & 1 : fv) : 0;
+      int64_t val, mexp;
+      bool ok;
+      if (edge) edge_entry(a, leaf, nu, nv, &val, &mexp, &ok);
+      else vertex_entry(a, u, nu, &val, &mexp, &ok);
+      const int64_t i = a.loff[leaf] + x;
+      switch (a.semiring) {
+        case TN_TROPICAL_F32:
+          reinterpret_cast<float*>(a.l0)[i] = ok ? static_cast<float>(val) : -INFINITY;
+          break;
+        case TN_TROPICAL_I32:
+          reinterpret_cast<int32_t*>(a.l0)[i] = ok ? static_cast<int32_t>(val) : TN_I32_NEG_INF;
+          break;
+        case TN_COUNTING_TROPICAL:
+          reinterpret_cast<int32_t*>(a.l0)[i] = ok ? static_cast<int32_t>(val) : TN_I32_NEG_INF;
+          reinterpret_cast<uint64_t*>(a.l1)[i] = ok ? 1ull : 0ull;
+          break;
+        default:
+          reinterpret_cast<uint32_t*>(a.l0)[q * a.stride + i] = ok ? pow_mod(a.x[q], mexp, a.p[q]) : 0u;
+          break;
+      }
     }
   }
 }
@@ -133,9 +147,10 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? TN_OK : TN_ECUDA; }
 
 // Workspace of a weighted contraction: the executor's (stored-leaf plan),
-// then the weights (n + m int32).
+// then the weights (n + m int32), the edge list, the leaf offsets and the
+// sliced-label values.
 struct WeightedLayout {
-  size_t exec_bytes, ew_off, vw_off, total;
+  size_t exec_bytes, ew_off, vw_off, edges_off, loff_off, fixed_off, total;
 };
 
 ExecPlan* weighted_plan(tn_plan_s* p, tn_semiring_t s, int32_t nslots, bool keep, int* rc) {
@@ -149,7 +164,10 @@ WeightedLayout weighted_layout(tn_plan_s* p, tn_semiring_t s, int32_t nslots, bo
   L.exec_bytes = align256(X->total_bytes);
   L.ew_off = L.exec_bytes;
   L.vw_off = L.ew_off + align256(4 * size_t(std::max(p->m, 1)));
-  L.total = L.vw_off + align256(4 * size_t(std::max(p->n, 1)));
+  L.edges_off = L.vw_off + align256(4 * size_t(std::max(p->n, 1)));
+  L.loff_off = L.edges_off + align256(8 * size_t(std::max(p->m, 1)));
+  L.fixed_off = L.loff_off + align256(8 * size_t(p->T));
+  L.total = L.fixed_off + align256(size_t(std::max(p->n, 1)));
   return L;
 }
 
@@ -182,7 +200,7 @@ int check_weights(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t*
 // executor plan used (its arena holds the leaves at leaf_base).
 int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw,
                           const uint32_t* primes, const uint32_t* xs, int32_t nslots, void* d_ws, size_t ws_bytes,
-                          cudaStream_t st, unsigned char* raw_out, bool keep, ExecPlan** Xout) {
+                          cudaStream_t st, unsigned char* raw_out, bool keep, ExecPlan** Xout, uint64_t slice) {
   ModTable mods;
   int rc = s == TN_COUNT_MODP ? make_mod_table_slots(primes, xs, nslots, &mods)
                               : make_mod_table_checked(s, nullptr, 0, &mods);
@@ -195,9 +213,17 @@ int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const 
   if (Xout) *Xout = X;
   if (ws_bytes < L.total) return TN_ENOMEM;
   char* w = static_cast<char*>(d_ws);
-  // the weights (n + m integers) are copied every call
+  // the weights, edges, leaf offsets and this slice's label values (a few KB)
+  // are copied every call; the copies finish before this call returns
+  std::vector<int8_t> fixed(static_cast<size_t>(p->n), -1);
+  for (size_t j = 0; j < p->sliced.size(); ++j) fixed[p->sliced[j]] = static_cast<int8_t>((slice >> j) & 1);
   if (ew && p->m) rc = cuda_rc(cudaMemcpyAsync(w + L.ew_off, ew, 4 * size_t(p->m), cudaMemcpyHostToDevice, st));
   if (!rc && vw && p->n) rc = cuda_rc(cudaMemcpyAsync(w + L.vw_off, vw, 4 * size_t(p->n), cudaMemcpyHostToDevice, st));
+  if (!rc && p->m)
+    rc = cuda_rc(cudaMemcpyAsync(w + L.edges_off, p->edges.data(), 8 * size_t(p->m), cudaMemcpyHostToDevice, st));
+  if (!rc)
+    rc = cuda_rc(cudaMemcpyAsync(w + L.loff_off, p->leaf_off.data(), 8 * size_t(p->T), cudaMemcpyHostToDevice, st));
+  if (!rc) rc = cuda_rc(cudaMemcpyAsync(w + L.fixed_off, fixed.data(), size_t(p->n), cudaMemcpyHostToDevice, st));
   if (rc) return rc;
   // arena regions as the executor lays them out (exec_launch_core)
   const size_t e = static_cast<size_t>(X->arena_entries);
@@ -207,11 +233,14 @@ int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const 
   std::memset(&la, 0, sizeof(la));
   la.m = p->m;
   la.n = p->n;
+  la.T = p->T;
   la.problem = problem;
   la.semiring = s;
   la.nslots = np;
-  la.entries = 4 * int64_t(p->m) + 2 * int64_t(p->n);
   la.stride = static_cast<int64_t>(b4 / 4);
+  la.edges = reinterpret_cast<const int32_t*>(w + L.edges_off);
+  la.loff = reinterpret_cast<const int64_t*>(w + L.loff_off);
+  la.fixed = reinterpret_cast<const int8_t*>(w + L.fixed_off);
   la.ew = ew ? reinterpret_cast<const int32_t*>(w + L.ew_off) : nullptr;
   la.vw = vw ? reinterpret_cast<const int32_t*>(w + L.vw_off) : nullptr;
   la.l0 = r0 + 4 * X->leaf_base;
@@ -220,7 +249,7 @@ int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const 
     la.p[q] = primes[q];
     la.x[q] = xs[q] % primes[q];
   }
-  const int64_t total = la.entries * np;
+  const int64_t total = int64_t(p->T) * np;
   const int blocks = static_cast<int>(std::min<int64_t>((total + 255) / 256, 1024));
   if (total > 0) {
     dev::k_leaves<<<blocks, 256, 0, st>>>(la);
@@ -273,7 +302,7 @@ int tn_contract_weighted(tn_plan_t plan, tn_semiring_t semiring, int32_t problem
   try {
     unsigned char raw[TN_RAW_BYTES];
     rc = contract_weighted_raw(plan, semiring, problem, edge_w, vertex_w, primes, xs, nslots, d_workspace, ws_bytes,
-                               static_cast<cudaStream_t>(cuda_stream), raw, false, nullptr);
+                               static_cast<cudaStream_t>(cuda_stream), raw, false, nullptr, 0);
     if (rc) return rc;
     if (semiring != TN_COUNT_MODP) {
       ModTable mods;

@@ -108,6 +108,12 @@ def lib():
         L.tn_single_config_workspace_bytes.argtypes = [vp, ctypes.POINTER(u64)]
         L.tn_order_treesa.argtypes = [i32, i32p, i32, ctypes.POINTER(tn_treesa_params_t), i32p,
                                       ctypes.POINTER(ctypes.c_double)]
+        L.tn_slice_labels.argtypes = [i32, i32p, i32, i32p, i32, i32, i32p, ctypes.POINTER(ctypes.c_double)]
+        L.tn_plan_sliced.argtypes = [i32, i32p, i32, i32p, i32, i32p, i32, ctypes.POINTER(vp)]
+        L.tn_contract_sliced.argtypes = [vp, ctypes.c_int, i32, i32p, i32p, u32p, u32p, i32, u64, u64, vp,
+                                         ctypes.c_size_t, vp, ctypes.POINTER(tn_result_t)]
+        L.tn_result_combine.argtypes = [ctypes.c_int, ctypes.POINTER(tn_result_t), ctypes.POINTER(tn_result_t),
+                                        ctypes.POINTER(tn_result_t)]
         L.tn_single_config_max.argtypes = [vp, i32, i32p, i32p, vp, ctypes.c_size_t, vp, i32p,
                                            ctypes.POINTER(ctypes.c_uint8)]
         L.tn_contract_weighted.argtypes = [vp, ctypes.c_int, i32, i32p, i32p, u32p, u32p, i32, vp, ctypes.c_size_t,
@@ -410,6 +416,80 @@ def tn_order_treesa(n, edges, *, sc_target: float = 20.0, betas=(1.0, 0.05, 15.0
     return order, tuple(float(x) for x in lg)
 
 
+def tn_slice_labels(n, edges, order, nslices: int):
+    """Labels to slice for `order` and log2 (work of all slices, largest
+    intermediate of one slice)."""
+    e = _i32(edges).reshape(-1, 2)
+    o = _i32(order).reshape(-1, 2)
+    out = np.zeros(max(int(nslices), 1), dtype=np.int32)
+    lg = (ctypes.c_double * 2)()
+    _check(lib().tn_slice_labels(int(n), _p32(e), len(e), _p32(o), len(o), int(nslices), _p32(out), lg),
+           "tn_slice_labels")
+    return out[: int(nslices)], (float(lg[0]), float(lg[1]))
+
+
+def tn_plan_sliced(n, edges, order, sliced):
+    e = _i32(edges).reshape(-1, 2)
+    o = _i32(order).reshape(-1, 2)
+    sl = _i32(sliced).reshape(-1)
+    out = ctypes.c_void_p()
+    _check(lib().tn_plan_sliced(int(n), _p32(e), len(e), _p32(o), len(o), _p32(sl), sl.size, ctypes.byref(out)),
+           "tn_plan_sliced")
+    return out.value
+
+
+def _result_from(d, semiring) -> "tn_result_t":
+    r = tn_result_t()
+    r.status = d.get("status", 0)
+    if _sr(semiring) == TN_COUNT_MODP:
+        r.nprimes = len(d["primes"])
+        for q, (p, x) in enumerate(zip(d["primes"], d["residues"])):
+            r.primes[q], r.residues[q] = p, x
+    else:
+        mx = d.get("max")
+        r.max_i32 = -(2 ** 31) if mx is None else int(mx)
+        r.max_f32 = float("-inf") if mx is None else float(mx)
+        r.count = int(d.get("count", 0))
+    return r
+
+
+def _result_dict(r, semiring) -> dict:
+    out = {"status": int(r.status)}
+    if _sr(semiring) == TN_COUNT_MODP:
+        out["primes"] = [int(x) for x in r.primes[: r.nprimes]]
+        out["residues"] = [int(x) for x in r.residues[: r.nprimes]]
+    else:
+        out["max"] = None if r.max_i32 == -(2 ** 31) else int(r.max_i32)
+        if _sr(semiring) == TN_COUNTING_TROPICAL:
+            out["count"] = int(r.count)
+    return out
+
+
+def tn_result_combine(semiring, a: dict, b: dict) -> dict:
+    """a (+) b in the element type (results as returned by the contract calls)."""
+    ra, rb, rc = _result_from(a, semiring), _result_from(b, semiring), tn_result_t()
+    _check(lib().tn_result_combine(_sr(semiring), ctypes.byref(ra), ctypes.byref(rb), ctypes.byref(rc)),
+           "tn_result_combine")
+    return _result_dict(rc, semiring)
+
+
+def tn_contract_sliced(plan, semiring, problem, edge_w, vertex_w, primes, xs, slice_begin: int, slice_end: int,
+                       ws_ptr: int, ws_bytes: int, stream: int) -> dict:
+    ew, ewp = _opt_i32(edge_w)
+    vw, vwp = _opt_i32(vertex_w)
+    if _sr(semiring) == TN_COUNT_MODP:
+        pr = np.ascontiguousarray(np.asarray(primes, dtype=np.uint32).reshape(-1))
+        xv = np.ascontiguousarray(np.asarray(xs, dtype=np.uint32).reshape(-1))
+        prp, xvp, k = _u32p(pr), _u32p(xv), pr.size
+    else:
+        prp, xvp, k = None, None, 0
+    r = tn_result_t()
+    _check(lib().tn_contract_sliced(plan, _sr(semiring), _problem(problem), ewp, vwp, prp, xvp, k, int(slice_begin),
+                                    int(slice_end), ctypes.c_void_p(ws_ptr), ws_bytes, ctypes.c_void_p(stream),
+                                    ctypes.byref(r)), "tn_contract_sliced")
+    return _result_dict(r, semiring)
+
+
 def tn_single_config_workspace_bytes(plan) -> int:
     out = ctypes.c_uint64()
     _check(lib().tn_single_config_workspace_bytes(plan, ctypes.byref(out)), "tn_single_config_workspace_bytes")
@@ -573,10 +653,12 @@ class Plan:
     """A contraction plan (graph + order) owning its libtn handle."""
 
     def __init__(self, n, edges, order=None, *, nrepeat: int = 10, seed: int = 0, alpha: float = 0.0,
-                 optimizer: str = "greedy", treesa=None):
+                 optimizer: str = "greedy", treesa=None, sliced=None):
         """order None: found by `optimizer` -- "greedy" (Sec. 4.2.1, nrepeat /
         seed / alpha) or "treesa" (Sec. 4.2.2, keyword arguments of
-        tn_order_treesa in the dict `treesa`, seed defaulting to `seed`)."""
+        tn_order_treesa in the dict `treesa`, seed defaulting to `seed`).
+        sliced: vertex labels to slice (tn_plan_sliced; contract with
+        contract_sliced), or an int s to pick s labels with tn_slice_labels."""
         self.n = int(n)
         self.edges = _i32(edges).reshape(-1, 2)
         if order is not None:
@@ -589,7 +671,11 @@ class Plan:
             self.order = tn_order_greedy(n, self.edges, alpha, nrepeat, seed)
         else:
             raise TNError(TN_EINVAL, f"unknown optimizer {optimizer!r}")
-        self.handle = tn_plan(self.n, self.edges, self.order)
+        if isinstance(sliced, (int, np.integer)):
+            sliced = tn_slice_labels(self.n, self.edges, self.order, int(sliced))[0]
+        self.sliced = None if sliced is None else _i32(sliced).reshape(-1)
+        self.handle = (tn_plan(self.n, self.edges, self.order) if self.sliced is None
+                       else tn_plan_sliced(self.n, self.edges, self.order, self.sliced))
 
     def info(self, semiring=TN_TROPICAL_I32, nprimes: int = 1) -> dict:
         return tn_plan_info(self.handle, semiring, nprimes)
@@ -680,6 +766,21 @@ class Plan:
         coeffs, _ = tn_weighted_polynomial(self.handle, problem, edge_w, vertex_w, primes, degree,
                                            workspace.data_ptr(), workspace.numel(), st.cuda_stream)
         return coeffs
+
+    def contract_sliced(self, semiring, problem="is", edge_w=None, vertex_w=None, primes=None, xs=None,
+                        slices=None, workspace=None, stream=None) -> dict:
+        """Sum of the slices in range `slices` (default: all) in the element
+        type (tn_contract_sliced)."""
+        import torch
+        nsl = 1 << (0 if self.sliced is None else len(self.sliced))
+        b, e = (0, nsl) if slices is None else (int(slices[0]), int(slices[1]))
+        k = len(primes) if primes is not None else 1
+        need = tn_weighted_workspace_bytes(self.handle, semiring, k)
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        return tn_contract_sliced(self.handle, semiring, problem, edge_w, vertex_w, primes, xs, b, e,
+                                  workspace.data_ptr(), workspace.numel(), st.cuda_stream)
 
     def single_config_max(self, problem="is", edge_w=None, vertex_w=None, workspace=None, stream=None):
         """(maximum, one configuration reaching it) (tn_single_config_max)."""
