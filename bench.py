@@ -532,6 +532,38 @@ def treesa_bench(tn, torch):
     return out
 
 
+def slicing_bench(tn, torch):
+    """Slicing (Sec. 4.2.2) on the 20x20 King's subgraph (seed 1, greedy
+    order): s labels picked by tn_slice_labels, all 2^s slices contracted
+    (counting element type, stored leaves written per slice) and added; the
+    workspace and the time against s."""
+    n, e = graphgen.kings_subgraph(20, 0.8, 1)
+    order = tn.tn_order_greedy(n, e, 0.0, 10, 1)
+    out = {"workload": "King's subgraph 20x20 p=0.8 seed 1, greedy order (nrepeat 10), counting", "rows": []}
+    ref = None
+    for s in (0, 2, 4, 6):
+        p = tn.Plan(n, e, order, sliced=s)
+        need = tn.tn_weighted_workspace_bytes(p.handle, "counting", 1)
+        ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        run = lambda: tn.tn_contract_sliced(p.handle, "counting", "is", None, None, None, None, 0, 1 << s,
+                                            ws.data_ptr(), ws.numel(), torch.cuda.current_stream().cuda_stream)
+        r = run()
+        ref = ref or r
+        ts = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            run()
+            ts.append(time.perf_counter() - t)
+        info = p.info("counting")
+        out["rows"].append({"slices": 1 << s, "log2_sc_per_slice": info["log2_sc"],
+                            "log2_tc_all_slices": info["log2_tc"] + s, "workspace_mb": need / 2 ** 20,
+                            "ms": statistics.median(ts) * 1e3, "same_result": r == ref})
+        del ws
+        p.close()
+    return out
+
+
 def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120):
     """Poisson request stream mixing random 3-regular graphs (n even in
     [40,160]) and King's subgraphs (L in [8,16], filling 0.8), each asking the
@@ -763,6 +795,7 @@ def run_tn(args):
         line["weighted"] = weighted_bench(tn, torch, plans, cpu=not args.no_cpu_baseline)
         line["single_config"] = single_config_bench(tn, torch, plans)
         line["treesa"] = treesa_bench(tn, torch)
+        line["slicing"] = slicing_bench(tn, torch)
     if rank == 0 and not args.no_batching:
         line["batching"] = batching_bench(tn, torch)
     if rank == 0 and not args.no_serving:
