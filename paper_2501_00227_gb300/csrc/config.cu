@@ -13,8 +13,12 @@
 // every vertex once, and the configuration reaches the maximum: each fixed
 // entry of each tensor lies on a maximising path.
 //
-// k_backtrack runs the walk in one CTA: per step, thread 0 forms c, all
-// threads scan t, and an atomicMin picks the first maximiser.
+// k_backtrack runs the walk in one CTA, level by level from the root (a
+// step's depth is its consumer's plus one): the steps of one level fix
+// disjoint labels and read only labels fixed at lower depths, so each warp
+// takes one step of the level, scans t in rounds of 32 lanes and stops at
+// the first round with a match (a ballot gives the lowest t); a barrier
+// separates the levels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,7 +55,10 @@ struct BtStep {
 };
 
 struct BtArgs {
-  const BtStep* steps;
+  const BtStep* steps;    // ordered by depth from the root
+  const int32_t* level;   // steps of depth d: [level[d], level[d + 1])
+  int32_t nlevels;
+  int32_t pad_;
   const int32_t* pool;
   const int32_t* arena;   // int32 (max,+) values of the intermediates and leaves
   int8_t* asg;            // out: the value of every label (vertex)
@@ -66,42 +73,42 @@ __device__ __forceinline__ int32_t bt_value(const BtArgs& a, int32_t src, int64_
 }
 
 __global__ void __launch_bounds__(256) k_backtrack(const __grid_constant__ BtArgs a) {
-  __shared__ uint32_t s_c;
-  __shared__ int32_t s_target;
-  __shared__ uint32_t s_best;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int v = threadIdx.x; v < a.n; v += blockDim.x) a.asg[v] = -1;
   __syncthreads();
-  for (int s = a.nsteps - 1; s >= 0; --s) {
-    const BtStep st = a.steps[s];
-    const int32_t* lc = a.pool + st.lab;
-    const int32_t* lk = lc + st.rc;
-    const int32_t* ca = lk + st.nk;
-    const int32_t* cb = ca + st.ra;
-    if (threadIdx.x == 0) {
+  for (int d = 0; d < a.nlevels; ++d) {
+    for (int s = a.level[d] + warp; s < a.level[d + 1]; s += nwarps) {
+      const BtStep st = a.steps[s];
+      const int32_t* lc = a.pool + st.lab;
+      const int32_t* lk = lc + st.rc;
+      const int32_t* ca = lk + st.nk;
+      const int32_t* cb = ca + st.ra;
       uint32_t c = 0;
       for (int j = 0; j < st.rc; ++j) c |= uint32_t(a.asg[lc[j]] > 0) << j;
-      s_c = c;
-      s_target = a.arena[st.c_off + c];
-      s_best = UINT_MAX;
-    }
-    __syncthreads();
-    const uint32_t c = s_c;
-    const int32_t target = s_target;
-    const uint32_t nt = 1u << st.nk;
-    for (uint32_t t = threadIdx.x; t < nt && t < s_best; t += blockDim.x) {
-      uint32_t ea = 0, eb = 0;
-      for (int j = 0; j < st.ra; ++j) ea |= ((ca[j] < 32 ? c >> ca[j] : t >> (ca[j] - 32)) & 1u) << j;
-      for (int j = 0; j < st.rb; ++j) eb |= ((cb[j] < 32 ? c >> cb[j] : t >> (cb[j] - 32)) & 1u) << j;
-      const int32_t va = bt_value(a, st.a_src, st.a_off, ea), vb = bt_value(a, st.b_src, st.b_off, eb);
-      if (va > TN_I32_NEG_INF / 2 && vb > TN_I32_NEG_INF / 2 && va + vb == target) atomicMin(&s_best, t);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if (s_best == UINT_MAX) {
-        if (*a.status == 0) *a.status = 1 + s;
-      } else {
-        for (int j = 0; j < st.nk; ++j) a.asg[lk[j]] = static_cast<int8_t>((s_best >> j) & 1u);
+      const int32_t target = a.arena[st.c_off + c];
+      const uint32_t nt = 1u << st.nk;
+      uint32_t best = UINT_MAX;
+      for (uint32_t t0 = 0; t0 < nt && best == UINT_MAX; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        bool hit = false;
+        if (t < nt) {
+          uint32_t ea = 0, eb = 0;
+          for (int j = 0; j < st.ra; ++j) ea |= ((ca[j] < 32 ? c >> ca[j] : t >> (ca[j] - 32)) & 1u) << j;
+          for (int j = 0; j < st.rb; ++j) eb |= ((cb[j] < 32 ? c >> cb[j] : t >> (cb[j] - 32)) & 1u) << j;
+          const int32_t va = bt_value(a, st.a_src, st.a_off, ea), vb = bt_value(a, st.b_src, st.b_off, eb);
+          hit = va > TN_I32_NEG_INF / 2 && vb > TN_I32_NEG_INF / 2 && va + vb == target;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (m) best = t0 + (__ffs(m) - 1);
       }
+      if (lane == 0) {
+        if (best == UINT_MAX) {
+          atomicCAS(a.status, 0, 1 + s);
+        } else {
+          for (int j = 0; j < st.nk; ++j) a.asg[lk[j]] = static_cast<int8_t>((best >> j) & 1u);
+        }
+      }
+      __syncwarp();
     }
     __syncthreads();
   }
@@ -117,7 +124,8 @@ int cuda_rc(cudaError_t e) { return e == cudaSuccess ? TN_OK : TN_ECUDA; }
 
 // Host image of the backward walk's tables (steps, then the label pool).
 struct BtImage {
-  std::vector<dev::BtStep> steps;
+  std::vector<dev::BtStep> steps;  // by depth from the root
+  std::vector<int32_t> level;      // nlevels + 1 offsets into steps
   std::vector<int32_t> pool;
   size_t bytes() const { return align256(sizeof(dev::BtStep) * steps.size()) + align256(4 * pool.size()); }
 };
@@ -140,8 +148,25 @@ int build_bt(tn_plan_s* p, const ExecPlan* X, BtImage* B) {
     }
     return *src != 0 || *off >= 0;
   };
+  // depth from the root: the root step is the last; a step's output is
+  // consumed by a later step, one level nearer the root
+  std::vector<int32_t> depth(ns, 0);
+  int32_t maxd = 0;
+  for (int s = ns - 2; s >= 0; --s) {
+    const int32_t cons = p->tensors[p->steps[s].c_id].consumer;
+    if (cons <= s || cons >= ns) return TN_EINVAL;
+    depth[s] = depth[cons] + 1;
+    maxd = std::max(maxd, depth[s]);
+  }
+  std::vector<int32_t> by_depth(ns);
+  for (int s = 0; s < ns; ++s) by_depth[s] = s;
+  std::stable_sort(by_depth.begin(), by_depth.end(), [&](int32_t x, int32_t y) { return depth[x] < depth[y]; });
+  B->level.assign(maxd + 2, 0);
+  for (int s = 0; s < ns; ++s) B->level[depth[s] + 1]++;
+  for (int d = 0; d <= maxd; ++d) B->level[d + 1] += B->level[d];
   B->steps.resize(ns);
-  for (int s = 0; s < ns; ++s) {
+  for (int k = 0; k < ns; ++k) {
+    const int s = by_depth[k];
     const Step& S = p->steps[s];
     const auto& la = p->tensors[S.a_id].labels;
     const auto& lb = p->tensors[S.b_id].labels;
@@ -152,7 +177,7 @@ int build_bt(tn_plan_s* p, const ExecPlan* X, BtImage* B) {
         if (std::find(lc.begin(), lc.end(), l) == lc.end() && std::find(lk.begin(), lk.end(), l) == lk.end())
           lk.push_back(l);
     if (lk.size() > 30 || lc.size() > 30 || la.size() > 30 || lb.size() > 30) return TN_EINVAL;
-    dev::BtStep& b = B->steps[s];
+    dev::BtStep& b = B->steps[k];
     std::memset(&b, 0, sizeof(b));
     b.ra = static_cast<int32_t>(la.size());
     b.rb = static_cast<int32_t>(lb.size());
@@ -179,7 +204,8 @@ size_t config_workspace(tn_plan_s* p, size_t* bt_off) {
   // tables: one record per step and at most 4 * 30 pool entries per step;
   // then the label values and the status word
   const size_t ns = p->steps.size();
-  return w + align256(sizeof(dev::BtStep) * ns) + align256(4 * 120 * ns) + align256(size_t(p->n)) + 256;
+  return w + align256(sizeof(dev::BtStep) * ns) + align256(4 * 120 * ns) + align256(size_t(p->n)) + 256 +
+         align256(4 * (ns + 2));
 }
 
 }  // namespace
@@ -232,13 +258,18 @@ int tn_single_config_max(tn_plan_t plan, int32_t problem, const int32_t* edge_w,
     char* d_pool = d_steps + align256(sizeof(dev::BtStep) * B.steps.size());
     char* d_asg = d_pool + align256(4 * 120 * B.steps.size());
     char* d_status = d_asg + align256(size_t(plan->n));
+    char* d_level = d_status + 256;
     rc = cuda_rc(cudaMemcpyAsync(d_steps, B.steps.data(), sizeof(dev::BtStep) * B.steps.size(),
                                  cudaMemcpyHostToDevice, st));
     if (!rc) rc = cuda_rc(cudaMemcpyAsync(d_pool, B.pool.data(), 4 * B.pool.size(), cudaMemcpyHostToDevice, st));
+    if (!rc) rc = cuda_rc(cudaMemcpyAsync(d_level, B.level.data(), 4 * B.level.size(), cudaMemcpyHostToDevice, st));
     if (!rc) rc = cuda_rc(cudaMemsetAsync(d_status, 0, 4, st));
     if (rc) return rc;
     dev::BtArgs a;
     a.steps = reinterpret_cast<const dev::BtStep*>(d_steps);
+    a.level = reinterpret_cast<const int32_t*>(d_level);
+    a.nlevels = static_cast<int32_t>(B.level.size()) - 1;
+    a.pad_ = 0;
     a.pool = reinterpret_cast<const int32_t*>(d_pool);
     a.arena = reinterpret_cast<const int32_t*>(w + X->arena_base);
     a.asg = reinterpret_cast<int8_t*>(d_asg);
