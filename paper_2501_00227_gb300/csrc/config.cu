@@ -15,10 +15,11 @@
 //
 // k_backtrack runs the walk in one CTA, level by level from the root (a
 // step's depth is its consumer's plus one): the steps of one level fix
-// disjoint labels and read only labels fixed at lower depths, so each warp
-// takes one step of the level, scans t in rounds of 32 lanes and stops at
-// the first round with a match (a ballot gives the lowest t); a barrier
-// separates the levels.
+// disjoint labels and read only labels fixed at lower depths.  Steps with at
+// most 8 summed labels go one per warp (t scanned in rounds of 32 lanes,
+// stop at the first round with a match, a ballot gives the lowest t);
+// longer scans take the whole CTA in rounds of 256 with an atomicMin; a
+// barrier separates the levels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -72,43 +73,74 @@ __device__ __forceinline__ int32_t bt_value(const BtArgs& a, int32_t src, int64_
   return a.arena[off + e];
 }
 
+// the output entry c of step st and its value, from the labels fixed so far
+__device__ __forceinline__ uint32_t bt_entry(const BtArgs& a, const BtStep& st) {
+  const int32_t* lc = a.pool + st.lab;
+  uint32_t c = 0;
+  for (int j = 0; j < st.rc; ++j) c |= uint32_t(a.asg[lc[j]] > 0) << j;
+  return c;
+}
+
+// does summed-label assignment t reach C[c]?
+__device__ __forceinline__ bool bt_hit(const BtArgs& a, const BtStep& st, uint32_t c, int32_t target, uint32_t t) {
+  const int32_t* ca = a.pool + st.lab + st.rc + st.nk;
+  const int32_t* cb = ca + st.ra;
+  uint32_t ea = 0, eb = 0;
+  for (int j = 0; j < st.ra; ++j) ea |= ((ca[j] < 32 ? c >> ca[j] : t >> (ca[j] - 32)) & 1u) << j;
+  for (int j = 0; j < st.rb; ++j) eb |= ((cb[j] < 32 ? c >> cb[j] : t >> (cb[j] - 32)) & 1u) << j;
+  const int32_t va = bt_value(a, st.a_src, st.a_off, ea), vb = bt_value(a, st.b_src, st.b_off, eb);
+  return va > TN_I32_NEG_INF / 2 && vb > TN_I32_NEG_INF / 2 && va + vb == target;
+}
+
+__device__ __forceinline__ void bt_fix(const BtArgs& a, const BtStep& st, int s, uint32_t best) {
+  if (best == UINT_MAX) {
+    atomicCAS(a.status, 0, 1 + s);
+    return;
+  }
+  const int32_t* lk = a.pool + st.lab + st.rc;
+  for (int j = 0; j < st.nk; ++j) a.asg[lk[j]] = static_cast<int8_t>((best >> j) & 1u);
+}
+
+constexpr int kBtWarpMaxK = 8;  // steps summing more labels are scanned by the whole CTA
+
 __global__ void __launch_bounds__(256) k_backtrack(const __grid_constant__ BtArgs a) {
+  __shared__ uint32_t s_best;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int v = threadIdx.x; v < a.n; v += blockDim.x) a.asg[v] = -1;
   __syncthreads();
   for (int d = 0; d < a.nlevels; ++d) {
+    // short scans: one warp per step, rounds of 32 assignments
     for (int s = a.level[d] + warp; s < a.level[d + 1]; s += nwarps) {
       const BtStep st = a.steps[s];
-      const int32_t* lc = a.pool + st.lab;
-      const int32_t* lk = lc + st.rc;
-      const int32_t* ca = lk + st.nk;
-      const int32_t* cb = ca + st.ra;
-      uint32_t c = 0;
-      for (int j = 0; j < st.rc; ++j) c |= uint32_t(a.asg[lc[j]] > 0) << j;
+      if (st.nk > kBtWarpMaxK) continue;
+      const uint32_t c = bt_entry(a, st);
       const int32_t target = a.arena[st.c_off + c];
       const uint32_t nt = 1u << st.nk;
       uint32_t best = UINT_MAX;
       for (uint32_t t0 = 0; t0 < nt && best == UINT_MAX; t0 += 32) {
-        const uint32_t t = t0 + lane;
-        bool hit = false;
-        if (t < nt) {
-          uint32_t ea = 0, eb = 0;
-          for (int j = 0; j < st.ra; ++j) ea |= ((ca[j] < 32 ? c >> ca[j] : t >> (ca[j] - 32)) & 1u) << j;
-          for (int j = 0; j < st.rb; ++j) eb |= ((cb[j] < 32 ? c >> cb[j] : t >> (cb[j] - 32)) & 1u) << j;
-          const int32_t va = bt_value(a, st.a_src, st.a_off, ea), vb = bt_value(a, st.b_src, st.b_off, eb);
-          hit = va > TN_I32_NEG_INF / 2 && vb > TN_I32_NEG_INF / 2 && va + vb == target;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        const unsigned m = __ballot_sync(0xffffffffu, t0 + lane < nt && bt_hit(a, st, c, target, t0 + lane));
         if (m) best = t0 + (__ffs(m) - 1);
       }
-      if (lane == 0) {
-        if (best == UINT_MAX) {
-          atomicCAS(a.status, 0, 1 + s);
-        } else {
-          for (int j = 0; j < st.nk; ++j) a.asg[lk[j]] = static_cast<int8_t>((best >> j) & 1u);
-        }
-      }
+      if (lane == 0) bt_fix(a, st, s, best);
       __syncwarp();
+    }
+    // long scans: the whole CTA per step, rounds of blockDim assignments
+    for (int s = a.level[d]; s < a.level[d + 1]; ++s) {
+      const BtStep st = a.steps[s];
+      if (st.nk <= kBtWarpMaxK) continue;
+      __syncthreads();
+      const uint32_t c = bt_entry(a, st);
+      const int32_t target = a.arena[st.c_off + c];
+      if (threadIdx.x == 0) s_best = UINT_MAX;
+      __syncthreads();
+      const uint32_t nt = 1u << st.nk;
+      for (uint32_t t0 = 0; t0 < nt; t0 += blockDim.x) {
+        const uint32_t t = t0 + threadIdx.x;
+        if (t < nt && bt_hit(a, st, c, target, t)) atomicMin(&s_best, t);
+        __syncthreads();
+        if (s_best != UINT_MAX) break;
+      }
+      if (threadIdx.x == 0) bt_fix(a, st, s, s_best);
     }
     __syncthreads();
   }
