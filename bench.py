@@ -535,31 +535,34 @@ def treesa_bench(tn, torch):
 def slicing_bench(tn, torch):
     """Slicing (Sec. 4.2.2) on the 20x20 King's subgraph (seed 1, greedy
     order): s labels picked by tn_slice_labels, all 2^s slices contracted
-    (counting element type, stored leaves written per slice) and added; the
-    workspace and the time against s."""
+    (counting element type, stored leaves written per slice) and added, one
+    slice per launch and all slices in one merged launch; workspace and time
+    against s."""
     n, e = graphgen.kings_subgraph(20, 0.8, 1)
     order = tn.tn_order_greedy(n, e, 0.0, 10, 1)
     out = {"workload": "King's subgraph 20x20 p=0.8 seed 1, greedy order (nrepeat 10), counting", "rows": []}
     ref = None
+    st = torch.cuda.current_stream().cuda_stream
     for s in (0, 2, 4, 6):
         p = tn.Plan(n, e, order, sliced=s)
-        need = tn.tn_weighted_workspace_bytes(p.handle, "counting", 1)
-        ws = torch.empty(need, dtype=torch.uint8, device="cuda")
-        run = lambda: tn.tn_contract_sliced(p.handle, "counting", "is", None, None, None, None, 0, 1 << s,
-                                            ws.data_ptr(), ws.numel(), torch.cuda.current_stream().cuda_stream)
-        r = run()
-        ref = ref or r
-        ts = []
-        for _ in range(3):
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            run()
-            ts.append(time.perf_counter() - t)
         info = p.info("counting")
-        out["rows"].append({"slices": 1 << s, "log2_sc_per_slice": info["log2_sc"],
-                            "log2_tc_all_slices": info["log2_tc"] + s, "workspace_mb": need / 2 ** 20,
-                            "ms": statistics.median(ts) * 1e3, "same_result": r == ref})
-        del ws
+        row = {"slices": 1 << s, "log2_sc_per_slice": info["log2_sc"], "log2_tc_all_slices": info["log2_tc"] + s}
+        for name, batch in (("one_per_launch", 1), ("batched", 1 << s)):
+            need = tn.tn_sliced_workspace_bytes(p.handle, "counting", 1, batch)
+            ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+            run = lambda: tn.tn_contract_sliced(p.handle, "counting", "is", None, None, None, None, 0, 1 << s,
+                                                ws.data_ptr(), ws.numel(), st)
+            r = run()
+            ref = ref or r
+            ts = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                run()
+                ts.append(time.perf_counter() - t)
+            row[name] = {"workspace_mb": need / 2 ** 20, "ms": statistics.median(ts) * 1e3, "same_result": r == ref}
+            del ws
+        out["rows"].append(row)
         p.close()
     return out
 

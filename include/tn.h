@@ -345,6 +345,10 @@ int tn_single_config_max(tn_plan_t plan, int32_t problem, const int32_t *edge_w,
  *   (tn_weighted_workspace_bytes) as tn_contract_weighted (problem, weights,
  *   prime slots); out = the element type's sum of those slices (mod p:
  *   residues per slot, no CRT).  Synchronous.
+ *   Slices run up to 256 per executor launch (one merged plan of that many
+ *   copies, cached with the plan) when the workspace holds
+ *   tn_sliced_workspace_bytes(plan, semiring, nslots, batch) for the batch;
+ *   with less, fewer per launch, down to one slice per launch.
  * tn_result_combine: out = a (+) b in the element type: max (tropical), max
  *   with counts of ties added and saturated at 2^64 - 1 (counting), residues
  *   added mod their slot's prime (mod p; the slots must agree, else
@@ -358,6 +362,7 @@ int tn_contract_sliced(tn_plan_t plan, tn_semiring_t semiring, int32_t problem, 
                        uint64_t slice_begin, uint64_t slice_end, void *d_workspace, size_t ws_bytes,
                        void *cuda_stream, tn_result_t *out);
 int tn_result_combine(tn_semiring_t semiring, const tn_result_t *a, const tn_result_t *b, tn_result_t *out);
+int tn_sliced_workspace_bytes(tn_plan_t plan, tn_semiring_t semiring, int32_t nslots, int32_t batch, uint64_t *out);
 
 /* Measured launch shapes.  The paper leaves the kernel schedule to the
  * contraction backend; this table lets an autotuner (tune.py in the Python

@@ -26,6 +26,8 @@ using tn::dev::Output;
 
 namespace tn {
 
+void slice_cache_free(tn_plan_s* p);
+
 namespace {
 
 bool semiring_ok(tn_semiring_t s) {
@@ -427,6 +429,7 @@ int tn_contract_pair(tn_semiring_t semiring, const uint32_t* primes, int32_t npr
 
 void tn_plan_destroy(tn_plan_t plan) {
   if (!plan) return;
+  slice_cache_free(plan);
   exec_plans_free(plan);
   delete plan;
 }

@@ -58,11 +58,11 @@ namespace tn {
 // Merges the executor plans of `count` networks into one plan M (see the
 // file comment).  nprimes: as given to the mod-p semiring (1 otherwise).
 int build_batch_plan(tn_plan_s* const* plans, int32_t count, tn_semiring_t semiring, int32_t nprimes,
-                     int group_h, ExecPlan* out) {
+                     int group_h, ExecPlan* out, bool stored_leaves) {
   std::vector<ExecPlan*> xs(count);
   for (int i = 0; i < count; ++i) {
     int rc;
-    xs[i] = exec_plan_get_h(plans[i], semiring, nprimes, group_h, true, &rc);
+    xs[i] = exec_plan_get_h(plans[i], semiring, nprimes, group_h, true, &rc, false, stored_leaves);
     if (!xs[i]) return rc;
   }
   ExecPlan& M = *out;
@@ -146,6 +146,9 @@ int build_batch_plan(tn_plan_s* const* plans, int32_t count, tn_semiring_t semir
   for (auto& v : by_level) M.tasks.insert(M.tasks.end(), v.begin(), v.end());
   if (M.tasks.size() > static_cast<size_t>(INT32_MAX)) return TN_EINVAL;
   M.arena_entries = std::max<int64_t>(arena, kArenaAlign);
+  M.net_arena_base = arena_base;
+  M.stored_leaves = stored_leaves;
+  M.leaf_base = count ? xs[0]->leaf_base : 0;
   M.scratch_bytes = scratch;
   M.n_arrive = static_cast<int32_t>(arrive);
   M.nlevels = maxlev;

@@ -83,7 +83,8 @@ struct ExecPlan {
   bool batched = false;              // built for a batch / served group
   bool keep = false;                 // every intermediate keeps its own arena block (no reuse)
   bool stored_leaves = false;        // leaf operands are arena tensors at leaf_base (weighted networks)
-  int64_t leaf_base = 0;             // arena entry offset of the leaf tensors: 4 per edge, then 2 per vertex
+  int64_t leaf_base = 0;             // arena entry offset of the leaf tensors (plan leaf_off within)
+  std::vector<int64_t> net_arena_base;  // merged plans: arena entry offset of each network
   int64_t arena_entries = 0;
   int64_t root_off = 0;
   int32_t root_step = -1;
@@ -135,8 +136,10 @@ int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods, void* ws, v
                      void* d_trace, const void* d_tables);
 
 // Merges the executor plans of several networks into one launch (batch.cu).
+// stored_leaves: the networks' stored-leaf plans (their leaves are arena
+// tensors at each network's net_arena_base + leaf_base).
 int build_batch_plan(tn_plan_s* const* plans, int32_t count, tn_semiring_t semiring, int32_t nprimes,
-                     int group_h, ExecPlan* out);
+                     int group_h, ExecPlan* out, bool stored_leaves = false);
 
 // One-time kernel set-up of the executor instantiation a launch would use
 // (attributes, occupancy), so that a later launch can be graph-captured.

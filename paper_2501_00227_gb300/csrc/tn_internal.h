@@ -93,6 +93,7 @@ struct tn_plan_s {
   std::vector<int32_t> sliced;           // sliced labels, in slice-bit order
   std::vector<int64_t> leaf_off;         // entry offset of each leaf in a stored-leaf block
   int64_t leaf_entries = 0;              // entries of all leaves (sum of 2^rank)
+  void* slice_cache = nullptr;           // merged plans of slice batches (slice.cu)
 };
 
 namespace tn {

@@ -52,6 +52,7 @@ struct LeafArgs {
   const int32_t* vw;      // w_v (IS) or h_v (spin glass), or NULL
   char* l0;               // values of leaf entry 0 (prime block 0)
   char* l1;               // counts of leaf entry 0 (counting)
+  int64_t net_stride;     // several networks (blockIdx.y): arena entries between their leaves
   uint32_t p[TN_MAX_PRIMES];
   uint32_t x[TN_MAX_PRIMES];
 };
@@ -102,13 +103,16 @@ __device__ void vertex_entry(const LeafArgs& a, int64_t v, int nv, int64_t* val,
 __global__ void k_leaves(const __grid_constant__ LeafArgs a) {
   const int nq = a.semiring == TN_COUNT_MODP ? a.nslots : 1;
   const int64_t total = int64_t(a.T) * nq;
+  // network blockIdx.y (a slice of a batch): its own label values and leaves
+  const int8_t* fixed = a.fixed + int64_t(blockIdx.y) * a.n;
+  const int64_t base = int64_t(blockIdx.y) * a.net_stride;
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
     const int32_t leaf = static_cast<int32_t>(t % a.T);
     const int q = static_cast<int>(t / a.T);
     const bool edge = leaf < a.m;
     const int32_t u = edge ? a.edges[2 * leaf] : leaf - a.m;
     const int32_t v = edge ? a.edges[2 * leaf + 1] : -1;
-    const int fu = a.fixed[u], fv = edge ? a.fixed[v] : 0;
+    const int fu = fixed[u], fv = edge ? fixed[v] : 0;
     const int rank = (fu < 0 ? 1 : 0) + (edge && fv < 0 ? 1 : 0);
     for (int x = 0; x < (1 << rank); ++x) {
       int bit = 0;
@@ -118,7 +122,7 @@ __global__ void k_leaves(const __grid_constant__ LeafArgs a) {
       bool ok;
       if (edge) edge_entry(a, leaf, nu, nv, &val, &mexp, &ok);
       else vertex_entry(a, u, nu, &val, &mexp, &ok);
-      const int64_t i = a.loff[leaf] + x;
+      const int64_t i = base + a.loff[leaf] + x;
       switch (a.semiring) {
         case TN_TROPICAL_F32:
           reinterpret_cast<float*>(a.l0)[i] = ok ? static_cast<float>(val) : -INFINITY;
@@ -262,6 +266,42 @@ int contract_weighted_raw(tn_plan_s* p, tn_semiring_t s, int32_t problem, const 
   rc = cuda_rc(cudaMemcpyAsync(raw_out, d_raw, TN_RAW_BYTES, cudaMemcpyDeviceToHost, st));
   if (!rc) rc = cuda_rc(cudaStreamSynchronize(st));
   return rc;
+}
+
+// Leaves of `count` copies of plan p in one merged executor plan (slices of
+// a sliced network): copy k's leaves at arena entry net_base0 + k *
+// net_stride + leaf_base, label values fixed[k * n ..].  The device buffers
+// (weights, edges, leaf offsets, fixed values) are already in place.
+int enqueue_leaves_batch(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* d_ew, const int32_t* d_vw,
+                         const int32_t* d_edges, const int64_t* d_loff, const int8_t* d_fixed, int32_t count,
+                         char* r0, char* r1, int64_t prime_stride, int64_t first_leaf, int64_t net_stride,
+                         const uint32_t* primes, const uint32_t* xs, int32_t np, cudaStream_t st) {
+  dev::LeafArgs la;
+  std::memset(&la, 0, sizeof(la));
+  la.m = p->m;
+  la.n = p->n;
+  la.T = p->T;
+  la.problem = problem;
+  la.semiring = s;
+  la.nslots = np;
+  la.stride = prime_stride;
+  la.edges = d_edges;
+  la.loff = d_loff;
+  la.fixed = d_fixed;
+  la.ew = d_ew;
+  la.vw = d_vw;
+  la.l0 = r0 + 4 * first_leaf;
+  la.l1 = r1 ? r1 + 8 * first_leaf : nullptr;
+  la.net_stride = net_stride;
+  for (int q = 0; q < np && s == TN_COUNT_MODP; ++q) {
+    la.p[q] = primes[q];
+    la.x[q] = xs[q] % primes[q];
+  }
+  const int64_t total = int64_t(p->T) * np;
+  if (total <= 0 || count < 1 || count > 65535) return total <= 0 ? TN_OK : TN_EINVAL;
+  const dim3 grid(static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 1024)), static_cast<unsigned>(count));
+  dev::k_leaves<<<grid, 256, 0, st>>>(la);
+  return cuda_rc(cudaGetLastError());
 }
 
 int weighted_checks(tn_plan_s* p, tn_semiring_t s, int32_t problem, const int32_t* ew, const int32_t* vw) {

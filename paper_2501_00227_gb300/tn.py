@@ -114,6 +114,7 @@ def lib():
                                          ctypes.c_size_t, vp, ctypes.POINTER(tn_result_t)]
         L.tn_result_combine.argtypes = [ctypes.c_int, ctypes.POINTER(tn_result_t), ctypes.POINTER(tn_result_t),
                                         ctypes.POINTER(tn_result_t)]
+        L.tn_sliced_workspace_bytes.argtypes = [vp, ctypes.c_int, i32, i32, ctypes.POINTER(u64)]
         L.tn_single_config_max.argtypes = [vp, i32, i32p, i32p, vp, ctypes.c_size_t, vp, i32p,
                                            ctypes.POINTER(ctypes.c_uint8)]
         L.tn_contract_weighted.argtypes = [vp, ctypes.c_int, i32, i32p, i32p, u32p, u32p, i32, vp, ctypes.c_size_t,
@@ -465,6 +466,13 @@ def _result_dict(r, semiring) -> dict:
     return out
 
 
+def tn_sliced_workspace_bytes(plan, semiring, nslots: int = 1, batch: int = 1) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().tn_sliced_workspace_bytes(plan, _sr(semiring), int(nslots), int(batch), ctypes.byref(out)),
+           "tn_sliced_workspace_bytes")
+    return int(out.value)
+
+
 def tn_result_combine(semiring, a: dict, b: dict) -> dict:
     """a (+) b in the element type (results as returned by the contract calls)."""
     ra, rb, rc = _result_from(a, semiring), _result_from(b, semiring), tn_result_t()
@@ -768,14 +776,15 @@ class Plan:
         return coeffs
 
     def contract_sliced(self, semiring, problem="is", edge_w=None, vertex_w=None, primes=None, xs=None,
-                        slices=None, workspace=None, stream=None) -> dict:
+                        slices=None, batch: int = 1, workspace=None, stream=None) -> dict:
         """Sum of the slices in range `slices` (default: all) in the element
-        type (tn_contract_sliced)."""
+        type (tn_contract_sliced), with a workspace for `batch` slices per
+        launch."""
         import torch
         nsl = 1 << (0 if self.sliced is None else len(self.sliced))
         b, e = (0, nsl) if slices is None else (int(slices[0]), int(slices[1]))
         k = len(primes) if primes is not None else 1
-        need = tn_weighted_workspace_bytes(self.handle, semiring, k)
+        need = tn_sliced_workspace_bytes(self.handle, semiring, k, batch)
         if workspace is None or workspace.numel() < need:
             workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
         st = stream if stream is not None else torch.cuda.current_stream()

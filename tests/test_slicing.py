@@ -209,3 +209,31 @@ def test_single_slices_match_the_fixed_graphs():
             assert (r["max"], r["count"]) == (a + ones, poly[a])
     finally:
         p.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("spec,s,batch", [("reg3:40:1", 4, 16), ("ksg:8:0.8:2", 5, 8), ("reg3:100:3", 3, 8),
+                                          ("er:16:0.2:1", 6, 64)])
+def test_batched_slices_equal_one_at_a_time(spec, s, batch):
+    """Several slices per executor launch (one merged plan) give the results
+    of one launch per slice and of the oracle."""
+    _cuda()
+    n, e = g.by_name(spec)
+    o = O.greedy_order(n, e, nrepeat=4, seed=1)
+    p = tn.Plan(n, e, o, sliced=s)
+    try:
+        for sr, pr in (("tropical_i32", None), ("counting", None), ("modp", list(tn.PRIMES31[:2]))):
+            xs = [1] * len(pr) if pr else None
+            one = p.contract_sliced(sr, primes=pr, xs=xs, batch=1)
+            many = p.contract_sliced(sr, primes=pr, xs=xs, batch=batch)
+            assert one == many
+        r = p.contract_sliced("counting", batch=batch, slices=(1, (1 << s) - 1))
+        ref = p.contract_sliced("counting", batch=1, slices=(1, (1 << s) - 1))
+        assert r == ref
+        full = p.contract_sliced("counting", batch=batch)
+        assert (full["max"], full["count"]) == O.mis_count(n, e, o)
+        J = g.random_weights(len(e), s)
+        r = p.contract_sliced("counting", "spin", J, batch=batch)
+        assert (r["max"], r["count"]) == O.weighted_contract("counting", "spin", n, e, o, J)
+    finally:
+        p.close()
