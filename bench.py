@@ -756,14 +756,17 @@ def run_tn(args):
     # plan from the host edge list + order (its task tables are uploaded to the
     # device on first use), contract, read the result back to the host
     e2e_steps = max(1, min(args.steps, 3))
+    # bytes each contraction uploads (its step / task tables), from the same
+    # plans, counted before the timed region
+    table_bytes = [p.info(sr, len(pr) if pr else 1)["exec_table_bytes"] for p, sr, pr, _, _ in jobs]
     torch.cuda.synchronize()
     h2d = 0
     t = time.perf_counter()
     for _ in range(e2e_steps):
-        for p, sr, pr, _, _ in jobs:
+        for (p, sr, pr, _, _), tb in zip(jobs, table_bytes):
             h = tn.tn_plan(p.n, p.edges, p.order)
             tn.tn_contract(h, sr, pr, ws.data_ptr(), ws_bytes, sptr)
-            h2d += tn.tn_plan_info(h, sr, len(pr) if pr else 1)["exec_table_bytes"]
+            h2d += tb
             tn.tn_plan_destroy(h)
     e2e_s = time.perf_counter() - t
     e2e_val = ops_per_step * e2e_steps / e2e_s / 1e9
