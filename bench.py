@@ -752,21 +752,23 @@ def run_tn(args):
             a[2] += 1
     dom_sr, (dom_ms, dom_ops, dom_n) = max(per.items(), key=lambda kv: kv[1][0])
 
-    # ---- end to end through the public API: for every contraction, build the
-    # plan from the host edge list + order (its task tables are uploaded to the
-    # device on first use), contract, read the result back to the host
+    # ---- end to end through the public API: for every graph, build the plan
+    # from the host edge list + order, contract it in the three element types
+    # (each contraction uploads its step / task tables on first use and reads
+    # its result back to the host), destroy the plan
     e2e_steps = max(1, min(args.steps, 3))
-    # bytes each contraction uploads (its step / task tables), from the same
-    # plans, counted before the timed region
-    table_bytes = [p.info(sr, len(pr) if pr else 1)["exec_table_bytes"] for p, sr, pr, _, _ in jobs]
+    # bytes each contraction uploads (its tables), from the same plans,
+    # counted before the timed region
+    table_bytes = {(id(p), sr): p.info(sr, len(pr) if pr else 1)["exec_table_bytes"] for p, sr, pr, _, _ in jobs}
     torch.cuda.synchronize()
     h2d = 0
     t = time.perf_counter()
     for _ in range(e2e_steps):
-        for (p, sr, pr, _, _), tb in zip(jobs, table_bytes):
+        for p in plans:
             h = tn.tn_plan(p.n, p.edges, p.order)
-            tn.tn_contract(h, sr, pr, ws.data_ptr(), ws_bytes, sptr)
-            h2d += tb
+            for sr, pr in SEMIRINGS:
+                tn.tn_contract(h, sr, pr, ws.data_ptr(), ws_bytes, sptr)
+                h2d += table_bytes[(id(p), sr)]
             tn.tn_plan_destroy(h)
     e2e_s = time.perf_counter() - t
     e2e_val = ops_per_step * e2e_steps / e2e_s / 1e9
