@@ -422,7 +422,8 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   // depends only on steps earlier in the execution order and (2) whenever
   // the output of a step y overlaps the memory of an earlier tensor x, every
   // reader of x (its consumer) is an ancestor of y, so y cannot overwrite x
-  // while it is still being read.
+  // while it is still being read; (3) stored leaves overlap no intermediate
+  // and (4) the plan that keeps its intermediates has no two overlapping.
   const char* chk = getenv("TN_EXEC_CHECK");
   if (chk && chk[0] == '1') {
     for (int x = 0; x < ns; ++x)
@@ -445,6 +446,19 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
         const int cons = p->tensors[p->steps[sx].c_id].consumer;
         if (cons < 0 || !is_anc(pos[owner(cons)], y)) return TN_EINVAL;
       }
+    }
+    // stored leaves lie after every intermediate; a kept plan reuses no block
+    for (int y = 0; y < ns; ++y) {
+      const int sy = order[y];
+      if (sh_off[sy] >= 0) continue;
+      const int64_t y0 = c_off[sy], y1 = y0 + (int64_t(1) << p->steps[sy].g.rc);
+      if (X->stored_leaves && y1 > X->leaf_base) return TN_EINVAL;
+      if (X->keep)
+        for (int x = 0; x < y; ++x) {
+          const int sx = order[x];
+          const int64_t x0 = c_off[sx], x1 = x0 + (int64_t(1) << p->steps[sx].g.rc);
+          if (sh_off[sx] < 0 && x0 < y1 && y0 < x1) return TN_EINVAL;
+        }
     }
     // split-K scratch: a later step may only overlap the scratch of a step it
     // (transitively) depends on

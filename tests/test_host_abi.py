@@ -179,3 +179,27 @@ def test_executor_schedule_self_check(spec, height, monkeypatch):
             assert info["exec_levels"] >= 1
     finally:
         tn.tn_plan_destroy(p)
+
+
+@pytest.mark.parametrize("spec", ["reg3:60:2", "ksg:8:0.8:1", "petersen"])
+def test_exec_self_check_on_plan_variants(monkeypatch, spec):
+    """The executor plans behind weighted networks (stored leaves), the
+    backward pass (every intermediate kept) and sliced networks pass the
+    schedule self-check (leaves after every intermediate; no reuse when
+    kept)."""
+    monkeypatch.setenv("TN_EXEC_CHECK", "1")
+    n, e = g.by_name(spec)
+    o = tn.tn_order_greedy(n, e, 0.0, 2, 3)
+    p = tn.tn_plan(n, e, o)
+    ps = tn.tn_plan_sliced(n, e, o, [0, n - 1])
+    try:
+        for sr in ("tropical_i32", "counting", "modp"):
+            assert tn.tn_weighted_workspace_bytes(p, sr, 3) > 0
+            assert tn.tn_weighted_workspace_bytes(ps, sr, 3) > 0
+            assert tn.tn_sliced_workspace_bytes(ps, sr, 3, 4) > 0
+        assert tn.tn_single_config_workspace_bytes(p) > 0
+        info = tn.tn_plan_info(ps, tn.TN_COUNTING_TROPICAL, 1)
+        assert info["exec_tasks"] >= info["nsteps"] + 1
+    finally:
+        tn.tn_plan_destroy(p)
+        tn.tn_plan_destroy(ps)
