@@ -567,20 +567,27 @@ def slicing_bench(tn, torch):
     return out
 
 
-def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120):
+def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120, optimizer: str = "greedy",
+                  sweep_rates: bool = True):
     """Poisson request stream mixing random 3-regular graphs (n even in
     [40,160]) and King's subgraphs (L in [8,16], filling 0.8), each asking the
     MIS size, the MIS count or the count of all independent sets mod 4 primes,
     served with continuous batching under a 120 GB budget.  Plain baseline:
-    the same requests one at a time (synchronous tn_contract)."""
+    the same requests one at a time (synchronous tn_contract).  optimizer:
+    the contraction orders of the pool ("greedy": the paper's default,
+    Sec. 4.2.1; "treesa": a light TreeSA run, Sec. 4.2.2), the same for both
+    arms."""
     rng = np.random.default_rng(5)
     pool = []
+    t_opt = time.perf_counter()
     for i in range(96):
         if i % 2 == 0:
             n, e = graphgen.random_regular3(int(rng.integers(20, 81)) * 2, 20000 + i)
         else:
             n, e = graphgen.kings_subgraph(int(rng.integers(8, 17)), 0.8, 30000 + i)
-        pool.append(tn.Plan(n, e, nrepeat=10, seed=1))  # the paper's greedy default (Sec. 4.2.1)
+        pool.append(tn.Plan(n, e, nrepeat=10, seed=1, optimizer=optimizer,
+                            treesa={"ntrials": 2, "niters": 10}))
+    t_opt = time.perf_counter() - t_opt
     kinds = [("tropical_i32", None), ("counting", None), ("modp", tuple(tn.PRIMES31[:4]))]
     reqs = [(pool[int(rng.integers(0, len(pool)))], *kinds[int(rng.integers(0, 3))]) for _ in range(nreq)]
     need = max(p.workspace_bytes(sr, len(pr) if pr else 1) for p, sr, pr in reqs)
@@ -634,12 +641,14 @@ def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120):
                 "p50_ms": 1e3 * float(np.percentile(lats, 50)), "p99_ms": 1e3 * float(np.percentile(lats, 99))}
 
     sat = serve(0)  # every request offered at once
-    sweep = [serve(f * sat["inst_per_s"]) for f in (0.25, 0.5, 1.0)]
+    sweep = [serve(f * sat["inst_per_s"]) for f in (0.25, 0.5, 1.0)] if sweep_rates else None
+    pool_tc = sum(2.0 ** p.info("tropical_i32")["log2_tc"] for p in pool)
     for p in pool:
         p.close()
     return {"workload": f"{nreq} requests, Poisson arrivals (seed 5), 50/50 3-regular n in [40,160] / "
                         "King's subgraph L in [8,16] p=0.8, MIS size | MIS count | count mod 4 primes, "
                         f"{budget_gb} GB budget, 4 launch slots",
+            "orders": optimizer, "order_s": t_opt, "log2_pool_tc": float(np.log2(pool_tc)),
             "plain_one_at_a_time": plain, "served_saturated": sat, "served_rate_sweep": sweep,
             "speedup_inst_per_s": sat["inst_per_s"] / plain["inst_per_s"]}
 
@@ -808,6 +817,7 @@ def run_tn(args):
         line["batching"] = batching_bench(tn, torch)
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_bench(tn, torch)
+        line["serving_treesa_orders"] = serving_bench(tn, torch, optimizer="treesa", sweep_rates=False)
     if rank == 0 and not args.no_cpu_baseline:
         sample = GRAPHS + [g for g in GRAPHS if g[1] == 140]
         ops, secs, used = cpu_reference(sample, os.cpu_count() or 1)
