@@ -611,7 +611,7 @@ def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120, optimizer: s
         server = tn.tn_server_create(budget_gb << 30, 4)
         try:
             arrive = np.cumsum(rng.exponential(1.0 / rate, size=nreq)) if rate else np.zeros(nreq)
-            tickets, done, outstanding = [], {}, []
+            tickets, done, meta = [], {}, {}
             t_start = time.perf_counter()
             i = 0
             while len(done) < nreq:
@@ -620,16 +620,14 @@ def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120, optimizer: s
                     p, sr, pr = reqs[i]
                     tk = (tn.tn_submit(server, p.handle, sr, pr), sr, arrive[i])
                     tickets.append(tk)
-                    outstanding.append(tk)
+                    meta[tk[0]] = (sr, arrive[i])
                     i += 1
-                still = []
-                for t, sr, a in outstanding:
-                    r = tn.tn_poll(server, t, sr)
-                    if r is None:
-                        still.append((t, sr, a))
-                    else:
-                        done[t] = (r, time.perf_counter() - t_start - a)
-                outstanding = still
+                fin = tn.tn_server_completed(server)
+                if fin:
+                    now = time.perf_counter() - t_start
+                    for t in fin:
+                        sr, a = meta[t]
+                        done[t] = (tn.tn_poll(server, t, sr), now - a)
             total = time.perf_counter() - t_start
         finally:
             tn.tn_server_destroy(server)

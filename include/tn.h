@@ -480,6 +480,11 @@ int tn_server_create(size_t hbm_budget_bytes, int32_t max_inflight, tn_server_t 
 int tn_submit(tn_server_t server, tn_plan_t plan, tn_semiring_t semiring, const uint32_t *primes,
               int32_t nprimes, uint64_t *ticket);
 int tn_poll(tn_server_t server, uint64_t ticket, tn_result_t *out);
+/* Tickets finished since the last call, oldest first (at most max_tickets;
+ * *count of them written to tickets).  Each is reported once; its result is
+ * then fetched with tn_poll.  Lets a client wait on many requests without
+ * polling every outstanding ticket. */
+int tn_server_completed(tn_server_t server, uint64_t *tickets, int32_t max_tickets, int32_t *count);
 
 void tn_plan_destroy(tn_plan_t plan);
 void tn_server_destroy(tn_server_t server);

@@ -80,6 +80,7 @@ struct tn_server_s {
   std::deque<Request> pending;
   std::unordered_map<uint64_t, tn_result_t> done;
   std::unordered_map<uint64_t, int> state;  // 0 pending, 1 running, 2 done
+  std::deque<uint64_t> completed;            // finished tickets not yet reported by tn_server_completed
   std::vector<Flight> flights;
   uint64_t next_ticket = 1;
   int group_h = 4;  // height of the groups of tiny steps one CTA runs back to back
@@ -96,6 +97,7 @@ void finish_with_status(tn_server_s* S, const std::vector<Request>& reqs, int st
     res.status = status;
     S->done[r.ticket] = res;
     S->state[r.ticket] = 2;
+    S->completed.push_back(r.ticket);
   }
 }
 
@@ -167,6 +169,7 @@ void worker_loop(tn_server_s* S) {
         }
         S->done[f.reqs[i].ticket] = res;
         S->state[f.reqs[i].ticket] = 2;
+        S->completed.push_back(f.reqs[i].ticket);
       }
       S->used -= f.bytes;
       release_flight(f);
@@ -189,7 +192,11 @@ void worker_loop(tn_server_s* S) {
       }
       if (take.empty()) break;  // the oldest request waits for memory
       for (const Request& r : take) S->state[r.ticket] = 1;
+      // merging the plans and enqueueing the launch touch only this flight
+      // and the requests' plans: clients may submit and poll meanwhile
+      lk.unlock();
       int rc = launch_flight(S, f, std::move(take));
+      lk.lock();
       if (rc != TN_OK) {
         finish_with_status(S, f.reqs, rc);
         release_flight(f);
@@ -274,6 +281,18 @@ int tn_poll(tn_server_t S, uint64_t ticket, tn_result_t* out) {
   *out = S->done[ticket];
   S->done.erase(ticket);
   S->state.erase(st);
+  return TN_OK;
+}
+
+int tn_server_completed(tn_server_t S, uint64_t* tickets, int32_t max_tickets, int32_t* count) {
+  if (!S || !count || max_tickets < 0 || (max_tickets > 0 && !tickets)) return TN_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  int32_t k = 0;
+  while (k < max_tickets && !S->completed.empty()) {
+    tickets[k++] = S->completed.front();
+    S->completed.pop_front();
+  }
+  *count = k;
   return TN_OK;
 }
 

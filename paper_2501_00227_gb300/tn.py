@@ -131,6 +131,7 @@ def lib():
         L.tn_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
         L.tn_submit.argtypes = [vp, vp, ctypes.c_int, u32p, i32, ctypes.POINTER(u64)]
         L.tn_poll.argtypes = [vp, u64, ctypes.POINTER(tn_result_t)]
+        L.tn_server_completed.argtypes = [vp, ctypes.POINTER(u64), i32, i32p]
         L.tn_plan_destroy.argtypes = [vp]
         L.tn_server_destroy.argtypes = [vp]
         L.tn_strerror.argtypes = [ctypes.c_int]
@@ -615,6 +616,14 @@ def tn_poll(server, ticket: int, semiring):
         return None
     _check(rc, "tn_poll")
     return result_dict(r, semiring)
+
+
+def tn_server_completed(server, max_tickets: int = 4096) -> list:
+    """Tickets finished since the last call (each reported once)."""
+    buf = (ctypes.c_uint64 * max(int(max_tickets), 1))()
+    n = ctypes.c_int32()
+    _check(lib().tn_server_completed(server, buf, int(max_tickets), ctypes.byref(n)), "tn_server_completed")
+    return [int(buf[i]) for i in range(n.value)]
 
 
 def tn_server_destroy(server):

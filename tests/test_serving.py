@@ -81,3 +81,24 @@ def test_request_larger_than_budget_rejected():
     finally:
         tn.tn_server_destroy(server)
         p.close()
+
+
+def test_completed_tickets_are_reported_once_in_order_of_completion():
+    reqs = _requests(30, 11)
+    alone = [p.contract(sr, pr) for p, sr, pr in reqs]
+    server = tn.tn_server_create(4096 << 20, 3)
+    try:
+        tickets = {tn.tn_submit(server, p.handle, sr, pr): (i, sr) for i, (p, sr, pr) in enumerate(reqs)}
+        seen, t0 = [], time.time()
+        while len(seen) < len(tickets) and time.time() - t0 < 60:
+            seen += tn.tn_server_completed(server, 7)
+            time.sleep(0.0005)
+        assert sorted(seen) == sorted(tickets) and len(set(seen)) == len(seen)
+        assert tn.tn_server_completed(server) == []
+        for t in seen:
+            i, sr = tickets[t]
+            assert tn.tn_poll(server, t, sr) == alone[i]
+    finally:
+        tn.tn_server_destroy(server)
+        for p, _, _ in reqs:
+            p.close()
