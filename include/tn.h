@@ -364,6 +364,16 @@ int tn_contract_sliced(tn_plan_t plan, tn_semiring_t semiring, int32_t problem, 
 int tn_result_combine(tn_semiring_t semiring, const tn_result_t *a, const tn_result_t *b, tn_result_t *out);
 int tn_sliced_workspace_bytes(tn_plan_t plan, tn_semiring_t semiring, int32_t nslots, int32_t batch, uint64_t *out);
 
+/* Register-only throughput of the contraction kernels' inner arithmetic,
+ * the denominators of their ALU rooflines (no counterpart in the paper):
+ * kind 0 = (max,+) int32 multiply-adds (one __viaddmax_s32 each), kind 1 =
+ * mod-p multiply-adds (64-bit accumulate of a 32 x 32-bit product, the high
+ * word folded back every third term).  Runs one warm-up and one timed
+ * launch of 8 CTAs per SM, 16 independent chains per thread, `iters` terms
+ * each (3 .. 2^24); *tops_out = terms per second / 1e12.  Synchronous;
+ * allocates and frees a small device buffer. */
+int tn_alu_peak(int32_t kind, int32_t iters, void *cuda_stream, double *tops_out);
+
 /* Measured launch shapes.  The paper leaves the kernel schedule to the
  * contraction backend; this table lets an autotuner (tune.py in the Python
  * package) replace the host's estimate for given step shapes.  entries holds

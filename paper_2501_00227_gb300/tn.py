@@ -132,6 +132,7 @@ def lib():
         L.tn_submit.argtypes = [vp, vp, ctypes.c_int, u32p, i32, ctypes.POINTER(u64)]
         L.tn_poll.argtypes = [vp, u64, ctypes.POINTER(tn_result_t)]
         L.tn_server_completed.argtypes = [vp, ctypes.POINTER(u64), i32, i32p]
+        L.tn_alu_peak.argtypes = [i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
         L.tn_plan_destroy.argtypes = [vp]
         L.tn_server_destroy.argtypes = [vp]
         L.tn_strerror.argtypes = [ctypes.c_int]
@@ -624,6 +625,14 @@ def tn_server_completed(server, max_tickets: int = 4096) -> list:
     n = ctypes.c_int32()
     _check(lib().tn_server_completed(server, buf, int(max_tickets), ctypes.byref(n)), "tn_server_completed")
     return [int(buf[i]) for i in range(n.value)]
+
+
+def tn_alu_peak(kind: str, iters: int = 1 << 14, stream: int = 0) -> float:
+    """Register-only Tops/s of the "maxplus" or "modp" inner step."""
+    out = ctypes.c_double()
+    _check(lib().tn_alu_peak({"maxplus": 0, "modp": 1}[kind], int(iters), ctypes.c_void_p(stream),
+                             ctypes.byref(out)), "tn_alu_peak")
+    return float(out.value)
 
 
 def tn_server_destroy(server):

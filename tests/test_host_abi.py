@@ -1,6 +1,7 @@
 """Host-side checks of libtn through its C ABI (no GPU needed): the library
 loads and exports every symbol include/tn.h declares; orders, plans, the
 complexity report and the CRT decode agree with the oracle and the paper."""
+import ctypes
 import json
 import math
 import os
@@ -203,3 +204,23 @@ def test_exec_self_check_on_plan_variants(monkeypatch, spec):
     finally:
         tn.tn_plan_destroy(p)
         tn.tn_plan_destroy(ps)
+
+
+@pytest.mark.parametrize("kind,iters", [(2, 1024), (-1, 1024), (0, 2), (1, (1 << 24) + 1)])
+def test_alu_peak_rejects_bad_arguments(kind, iters):
+    out = ctypes.c_double()
+    assert tn.lib().tn_alu_peak(kind, iters, None, ctypes.byref(out)) == tn.TN_EINVAL
+
+
+@pytest.mark.gpu
+def test_alu_peaks_are_plausible():
+    """The register-only rates behind the ALU rooflines: (max,+) near one
+    term per lane per clock (64 per SM), the folded mod-p step slower."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mp = tn.tn_alu_peak("maxplus")
+    md = tn.tn_alu_peak("modp")
+    assert 0.3 * sms * 64 * 1.0e9 / 1e12 < mp < 1.2 * sms * 64 * 2.2e9 / 1e12
+    assert 0 < md < mp
