@@ -214,3 +214,20 @@ def test_k_best_on_gpu_petersen_and_reg3():
         assert P.counting_max(p, 3) == {alpha - j: want[alpha - j] for j in range(3)}
     finally:
         p.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("spec", ["empty:6", "path:1", "complete:9", "path:2"])
+def test_polynomial_edge_cases(spec):
+    """No edges ((1 + x)^n), a single vertex, a clique (1 + n x)."""
+    _cuda()
+    n, e = g.by_name(spec)
+    o = O.greedy_order(n, e, nrepeat=1, seed=1) if n + len(e) > 1 else np.zeros((0, 2), dtype=np.int32)
+    p = tn.Plan(n, e, o)
+    try:
+        want = O.bruteforce_poly(n, e)
+        alpha = max(k for k, c in enumerate(want) if c)
+        assert p.independence_polynomial() == want[: alpha + 1]
+        assert p.independence_polynomial(primes=tn.PRIMES31[:1], degree=n) == want
+    finally:
+        p.close()

@@ -237,3 +237,24 @@ def test_batched_slices_equal_one_at_a_time(spec, s, batch):
         assert (r["max"], r["count"]) == O.weighted_contract("counting", "spin", n, e, o, J)
     finally:
         p.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("spec,sliced", [("path:3", [0, 1, 2]), ("empty:4", [1, 3]), ("complete:5", [0, 4]),
+                                         ("path:1", [0]), ("cycle:6", [0, 1, 2, 3, 4, 5])])
+def test_edge_case_slicings(spec, sliced):
+    """Every label sliced (all leaves rank 0), isolated vertices, a single
+    vertex: the slices still add up to the oracle's counts."""
+    _cuda()
+    n, e = g.by_name(spec)
+    o = O.greedy_order(n, e, nrepeat=1, seed=1) if n + len(e) > 1 else np.zeros((0, 2), dtype=np.int32)
+    p = tn.Plan(n, e, o, sliced=sliced)
+    try:
+        r = p.contract_sliced("counting", batch=1)
+        poly = O.bruteforce_poly(n, e)
+        a = max(k for k, c in enumerate(poly) if c)
+        assert (r["max"], r["count"]) == (a, poly[a])
+        r = p.contract_sliced("modp", primes=[tn.PRIMES31[0]], xs=[3], batch=1 << len(sliced))
+        assert r["residues"] == [sum(c * 3 ** k for k, c in enumerate(poly)) % tn.PRIMES31[0]]
+    finally:
+        p.close()
