@@ -42,7 +42,7 @@ def test_step_info_reports_every_step_and_follows_the_table():
 
 
 @pytest.mark.parametrize("row", [("counting", 1, 5, 5, 5, 0, 1),     # 128 x 128 tile is tropical only
-                                 ("modp", 1, 5, 5, 5, 5, 1),         # no tile shape 5
+                                 ("modp", 1, 5, 5, 5, 6, 1),         # no tile shape 6
                                  ("tropical_i32", 1, 5, 5, 5, 1, 17),
                                  ("tropical_i32", -1, 5, 5, 5, 1, 1)])
 def test_tune_set_rejects_malformed_rows(row):
@@ -67,4 +67,36 @@ def test_autotuned_plans_give_the_same_results(semiring, primes):
         assert [p.contract(semiring, primes) for p in plans] == ref
     finally:
         for p in plans:
+            p.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5])
+def test_every_tile_shape_gives_the_oracle_results(tile):
+    """Every GEMM-tile step forced to one tile shape (with and without k
+    split) through the launch table: results equal the oracle's."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle as O
+    for spec in ("reg3:60:1", "ksg:9:0.8:2"):
+        n, e = g.by_name(spec)
+        o = O.greedy_order(n, e, nrepeat=4, seed=1)
+        p = tn.Plan(n, e, o)
+        try:
+            want = {"tropical_i32": O.mis_size(n, e, o), "counting": O.mis_count(n, e, o),
+                    "modp": O.count_modp(n, e, o, tn.PRIMES31[:2])}
+            for sr, pr in (("tropical_i32", None), ("counting", None), ("modp", tn.PRIMES31[:2])):
+                if tile == 0 and sr != "tropical_i32":
+                    continue
+                info = tn.tn_plan_step_info(p.handle, sr, len(pr) if pr else 1)
+                shapes = {tuple(int(v) for v in r[6:10]) for r in info if int(r[2]) == 1}
+                for split in (1, 2):
+                    tn.tn_tune_set([(sr, *sh, tile, split) for sh in shapes])
+                    r = p.contract(sr, pr)
+                    got = {"tropical_i32": r.get("max"), "counting": (r.get("max"), r.get("count")),
+                           "modp": r.get("residues")}[sr]
+                    assert got == want[sr], (spec, sr, tile, split)
+        finally:
+            tn.tn_tune_set([])
             p.close()
