@@ -379,9 +379,8 @@ int tn_alu_peak(int32_t kind, int32_t iters, void *cuda_stream, double *tops_out
  * package) replace the host's estimate for given step shapes.  entries holds
  * count records of 7 int32: (semiring, nb, nm, nn, nk, tile, split), where
  * nb / nm / nn / nk are the numbers of batch, A-only, B-only and summed
- * labels of a pairwise step (Sec. 4.1), tile is 0..6 (0 = 128 x 128, tropical
- * only; 1 = 64 x 64; 2 = 32 x 32; 3 = 16 x 64; 4 = 64 x 16; 5 = 32 x 128;
- * 6 = 128 x 32) or -1 (general
+ * labels of a pairwise step (Sec. 4.1), tile is 0..5 (0 = 128 x 128, tropical
+ * only; 1 = 64 x 64; 2 = 32 x 32; 3 = 16 x 64; 4 = 64 x 16; 5 = 32 x 128) or -1 (general
  * kernel), and split (1..16) is the number of CTAs sharing one output tile
  * along k.  The record applies to steps the host would run as GEMM tiles.
  * count = 0 removes the table.  The table is process-wide; executor plans

@@ -521,8 +521,7 @@ __device__ __noinline__ void exec_prepare(const ExecStep& st, const ExecTask& ta
     case 2: exec_prepare_tile<TileC2>(st, task, smem); break;
     case 3: exec_prepare_tile<TileC3>(st, task, smem); break;
     case 4: exec_prepare_tile<TileC4>(st, task, smem); break;
-    case 5: exec_prepare_tile<TileC5>(st, task, smem); break;
-    default: exec_prepare_tile<TileC6>(st, task, smem); break;
+    default: exec_prepare_tile<TileC5>(st, task, smem); break;
   }
 }
 
@@ -607,8 +606,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
         case 2: exec_tile_task<SR, TileC2, FOLD>(a, s_step, s_task, smem, &s_last, prepared); break;
         case 3: exec_tile_task<SR, TileC3, FOLD>(a, s_step, s_task, smem, &s_last, prepared); break;
         case 4: exec_tile_task<SR, TileC4, FOLD>(a, s_step, s_task, smem, &s_last, prepared); break;
-        case 5: exec_tile_task<SR, TileC5, FOLD>(a, s_step, s_task, smem, &s_last, prepared); break;
-        default: exec_tile_task<SR, TileC6, FOLD>(a, s_step, s_task, smem, &s_last, prepared); break;
+        default: exec_tile_task<SR, TileC5, FOLD>(a, s_step, s_task, smem, &s_last, prepared); break;
       }
     }
     __syncthreads();
@@ -639,7 +637,7 @@ static size_t smem_for() {
   size_t t = tile_smem_bytes<SR, TileC1>();
   const size_t cands[] = {ExecTile<SR>::kBig ? tile_smem_bytes<SR, TileC0>() : 0, tile_smem_bytes<SR, TileC2>(),
                           tile_smem_bytes<SR, TileC3>(), tile_smem_bytes<SR, TileC4>(),
-                          tile_smem_bytes<SR, TileC5>(), tile_smem_bytes<SR, TileC6>(), sizeof(NaiveSmem<SR>),
+                          tile_smem_bytes<SR, TileC5>(), sizeof(NaiveSmem<SR>),
                           std::is_same<SR, SrMod>::value ? sizeof(NaiveSmem<SrModN<4>>) : 0,
                           group_smem_off<SR>() + static_cast<size_t>(kGroupSmem) +
                               sizeof(ExecStep) * kGroupMaxMembers};

@@ -140,15 +140,12 @@ static int launch_tiled_t(const TiledArgs& a, int nprimes, cudaStream_t st) {
   return e == cudaSuccess ? TN_OK : TN_ECUDA;
 }
 
-// Tile shapes: see TileC0..TileC6 in tile_device.cuh.
-static const int kTileBM[kNumTiles] = {TileC0::BM, TileC1::BM, TileC2::BM, TileC3::BM,
-                                        TileC4::BM, TileC5::BM, TileC6::BM};
-static const int kTileBN[kNumTiles] = {TileC0::BN, TileC1::BN, TileC2::BN, TileC3::BN,
-                                        TileC4::BN, TileC5::BN, TileC6::BN};
-static const int kTileBK[kNumTiles] = {TileC0::BK, TileC1::BK, TileC2::BK, TileC3::BK,
-                                        TileC4::BK, TileC5::BK, TileC6::BK};
+// Tile shapes: see TileC0..TileC5 in tile_device.cuh.
+static const int kTileBM[kNumTiles] = {TileC0::BM, TileC1::BM, TileC2::BM, TileC3::BM, TileC4::BM, TileC5::BM};
+static const int kTileBN[kNumTiles] = {TileC0::BN, TileC1::BN, TileC2::BN, TileC3::BN, TileC4::BN, TileC5::BN};
+static const int kTileBK[kNumTiles] = {TileC0::BK, TileC1::BK, TileC2::BK, TileC3::BK, TileC4::BK, TileC5::BK};
 // relative throughput of a fully used tile (register blocking, sliced-K merge)
-static const float kTileEff[kNumTiles] = {1.0f, 0.8f, 0.72f, 0.68f, 0.68f, 0.8f, 0.8f};
+static const float kTileEff[kNumTiles] = {1.0f, 0.8f, 0.72f, 0.68f, 0.68f, 0.8f};
 
 int tiled_tile_bm(int tile) { return kTileBM[tile]; }
 int tiled_tile_bn(int tile) { return kTileBN[tile]; }
@@ -162,7 +159,6 @@ static int launch_cfg(const TiledArgs& a, int tile, int nprimes, cudaStream_t st
     case 3: return launch_tiled_t<SR, TileC3, FOLD>(a, nprimes, st);
     case 4: return launch_tiled_t<SR, TileC4, FOLD>(a, nprimes, st);
     case 5: return launch_tiled_t<SR, TileC5, FOLD>(a, nprimes, st);
-    case 6: return launch_tiled_t<SR, TileC6, FOLD>(a, nprimes, st);
   }
   return TN_EINVAL;
 }

@@ -63,17 +63,15 @@ struct TileCfg {
 };
 
 // Tile shapes (index = ExecStep.tile / the tile argument of the launchers).
-// Shapes 0-4 stage 4 A and 4 B elements per thread and chunk; shapes 5 and 6
-// (short reductions over few rows and many columns, or the reverse) 2 and 8
-// or 8 and 2.
+// Shapes 0-4 stage 4 A and 4 B elements per thread and chunk; shape 5 (for
+// short reductions over few rows and many columns) 2 and 8.
 using TileC0 = TileCfg<8, 8, 16, 16, 1, 8>;   // 128 x 128, BK 8, tropical only
 using TileC1 = TileCfg<4, 4, 16, 16, 1, 16>;  // 64 x 64, BK 16
 using TileC2 = TileCfg<4, 4, 8, 8, 4, 8>;     // 32 x 32, sliced K 4 x 8
 using TileC3 = TileCfg<4, 4, 4, 16, 4, 8>;    // 16 x 64, sliced K 4 x 8
 using TileC4 = TileCfg<4, 4, 16, 4, 4, 8>;    // 64 x 16, sliced K 4 x 8
 using TileC5 = TileCfg<4, 4, 8, 32, 1, 16>;   // 32 x 128, BK 16
-using TileC6 = TileCfg<4, 4, 32, 8, 1, 16>;   // 128 x 32, BK 16
-constexpr int kNumTiles = 7;
+constexpr int kNumTiles = 6;
 
 // cp.async pipeline depth of the tile main loop: three stages for 4-byte
 // elements, two for the 16-byte (max, count) pairs

@@ -64,7 +64,7 @@ int tn_tune_set(const int32_t* entries, int32_t count) {
     const int32_t s = e[0], tile = e[5], split = e[6];
     if (s < TN_TROPICAL_F32 || s > TN_COUNT_MODP) return TN_EINVAL;
     if (e[1] < 0 || e[2] < 0 || e[3] < 0 || e[4] < 0 || e[1] + e[2] + e[3] + e[4] > kMaxStepBits) return TN_EINVAL;
-    if (tile < -1 || tile > 6 || split < 1 || split > 16) return TN_EINVAL;  // shapes 0..6
+    if (tile < -1 || tile > 5 || split < 1 || split > 16) return TN_EINVAL;  // shapes 0..5
     if (tile == 0 && s != TN_TROPICAL_F32 && s != TN_TROPICAL_I32) return TN_EINVAL;
     (*t)[Key{s, e[1], e[2], e[3], e[4]}] = Entry{tile, split};
   }

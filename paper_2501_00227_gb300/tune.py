@@ -20,7 +20,7 @@ import numpy as np
 
 from . import tn
 
-TILES_BK = {0: 8, 1: 16, 2: 32, 3: 32, 4: 32, 5: 16, 6: 16}   # k rows per staged chunk of each tile shape
+TILES_BK = {0: 8, 1: 16, 2: 32, 3: 32, 4: 32, 5: 16}   # k rows per staged chunk of each tile shape
 SPLITS = (1, 2, 3, 4, 6, 8, 12, 16)
 
 
