@@ -161,3 +161,29 @@ def test_unit_weights_reproduce_the_plain_network():
             p.contract("modp", tn.PRIMES31[:3])["residues"]
     finally:
         p.close()
+
+
+@pytest.mark.gpu
+def test_full_size_spin_glass_and_weighted_is():
+    """The 140-vertex 3-regular graph of the bench, +-1 couplings and random
+    fields / vertex weights 0..3, every element type against the oracle."""
+    _cuda()
+    n, e = g.random_regular3(140, 2)
+    o, p = _plan(n, e)
+    try:
+        J = g.random_weights(len(e), 7)
+        h = g.random_weights(n, 8, (-1, 0, 1))
+        r = p.contract_weighted("counting", "spin", J, h)
+        assert (r["max"], r["count"]) == O.weighted_contract("counting", "spin", n, e, o, J, h)
+        pr, ys = [tn.PRIMES31[0]] * 2 + [tn.PRIMES31[1]] * 2, [3, 2 ** 30 + 3, 5, 77]
+        assert p.contract_weighted("modp", "spin", J, h, pr, ys)["residues"] == \
+            O.weighted_contract("modp", "spin", n, e, o, J, h, pr, ys)
+        w = g.random_weights(n, 9, (0, 1, 2, 3))
+        r = p.contract_weighted("counting", "is", vertex_w=w)
+        assert (r["max"], r["count"]) == O.weighted_contract("counting", "is", n, e, o, vertex_w=w)
+        val, cfg = p.single_config_max("is", vertex_w=w)
+        assert val == r["max"]
+        cfgb = cfg.astype(bool)
+        assert not np.any(cfgb[e[:, 0]] & cfgb[e[:, 1]]) and int(w[cfgb].sum()) == val
+    finally:
+        p.close()
