@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -99,6 +100,9 @@ struct SliceBatch {
 struct SliceCache {
   std::vector<std::unique_ptr<SliceBatch>> v;
 };
+// Plans may be shared across threads: the slice-batch caches (creation,
+// lookup, the one-time table upload) are guarded by one lock.
+std::mutex g_slice_mu;
 
 constexpr int32_t kMaxSliceBatch = 256;
 
@@ -120,6 +124,7 @@ SliceLayout slice_layout(const tn_plan_s* p, const ExecPlan& X, int32_t count) {
 }
 
 SliceBatch* slice_batch(tn_plan_s* p, tn_semiring_t s, int32_t np, int32_t count, int* rc) {
+  std::lock_guard<std::mutex> lk(g_slice_mu);
   if (!p->slice_cache) p->slice_cache = new SliceCache();
   auto* C = static_cast<SliceCache*>(p->slice_cache);
   for (auto& b : C->v)
@@ -136,6 +141,7 @@ SliceBatch* slice_batch(tn_plan_s* p, tn_semiring_t s, int32_t np, int32_t count
 }
 
 int upload(SliceBatch* B) {
+  std::lock_guard<std::mutex> lk(g_slice_mu);
   int dev;
   if (cudaGetDevice(&dev) != cudaSuccess) return TN_ECUDA;
   if (B->X.d_tables && B->device == dev) return TN_OK;
@@ -217,6 +223,7 @@ int contract_slice_batch(tn_plan_s* p, SliceBatch* B, tn_semiring_t s, int32_t p
 
 namespace tn {
 void slice_cache_free(tn_plan_s* p) {
+  std::lock_guard<std::mutex> lk(g_slice_mu);
   auto* C = static_cast<SliceCache*>(p->slice_cache);
   if (!C) return;
   for (auto& b : C->v)
