@@ -156,6 +156,8 @@ static int check_order(int T, const int32_t *order, int nsteps) {
  *     g_edge_w = J (NULL: 1), g_vertex_w = h (NULL: 0).
  * Leaves are numbered edges first (index e), then vertices (index v). */
 enum { OR_PROBLEM_IS = 0, OR_PROBLEM_SPIN = 1 };
+/* set for the duration of one weighted contraction (not reentrant: the
+ * oracle is called from one thread at a time) */
 static int g_problem = OR_PROBLEM_IS;
 static const int32_t *g_edge_w = NULL;
 static const int32_t *g_vertex_w = NULL;
