@@ -4,7 +4,7 @@ standalone mod-p step GEMM (the tensor-core ablations).
     python -m paper_2501_00227_gb300.run --graph reg3:140:1 --semiring tropical_i32 --repeat 3
     python -m paper_2501_00227_gb300.run --gemm umma --shape 2,1024,512,1024 --primes 4
 
-Builds the greedy order and plan on the host, contracts the network
+Builds the order (greedy, or TreeSA with --order treesa) and plan on the host, contracts the network
 `--repeat` times through the C ABI (the persistent executor) and prints the
 result and the device time of the last contraction.  Graph specs are those of
 graphgen.by_name (reg3:n:seed, ksg:L:p:seed, square:L, petersen, ...).
@@ -27,6 +27,8 @@ def main(argv=None) -> int:
     ap.add_argument("--semiring", default="tropical_i32", choices=["tropical_f32", "tropical_i32", "counting", "modp"])
     ap.add_argument("--primes", type=int, default=3, help="number of 31-bit primes for modp")
     ap.add_argument("--nrepeat", type=int, default=10, help="greedy order restarts")
+    ap.add_argument("--order", default="greedy", choices=["greedy", "treesa"],
+                    help="contraction order: greedy (Sec. 4.2.1) or TreeSA (Sec. 4.2.2, 8 trials)")
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--gemm", choices=["umma", "limb", "core"],
                     help="run one mod-p step GEMM instead: tcgen05 limbs, mma.sync limbs or the CUDA-core tile")
@@ -43,7 +45,7 @@ def main(argv=None) -> int:
 
     build.build()
     n, e = graphgen.by_name(args.graph)
-    plan = tn.Plan(n, e, nrepeat=args.nrepeat, seed=1)
+    plan = tn.Plan(n, e, nrepeat=args.nrepeat, seed=1, optimizer=args.order, treesa={"ntrials": 8})
     primes = tn.PRIMES31[: args.primes] if args.semiring == "modp" else None
     ws = torch.empty(plan.workspace_bytes(args.semiring, args.primes), dtype=torch.uint8, device="cuda")
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
