@@ -299,7 +299,7 @@ int tn_contract_weighted(tn_plan_t plan, tn_semiring_t semiring, int32_t problem
  * H = k - sum|J| - sum|h| (spin glass; the exact energy histogram, from which
  * the partition function of Sec. 6.4 follows for any temperature).  degree
  * at least the polynomial's degree (sum of the weights; 2 (sum|J| + sum|h|)
- * for the spin glass), at most 2^20.  Workspace: tn_weighted_workspace_bytes
+ * for the spin glass), at most 2^15.  Workspace: tn_weighted_workspace_bytes
  * with nslots = min(TN_MAX_PRIMES, nprimes * (degree + 1)).  Outputs and
  * errors as tn_independence_polynomial. */
 int tn_weighted_polynomial(tn_plan_t plan, int32_t problem, const int32_t *edge_w, const int32_t *vertex_w,

@@ -62,13 +62,19 @@ uint32_t inv_mod_prime(uint32_t a, uint32_t p) {
 void newton_interpolate(const std::vector<uint32_t>& xs, const std::vector<uint32_t>& ys, uint32_t p,
                         uint32_t* coeffs) {
   const int n = static_cast<int>(xs.size());
+  // consecutive points (x_i = x_0 + i, as used here): every difference
+  // x_i - x_{i-j} is j, so one inverse per round
+  bool consecutive = true;
+  for (int i = 1; i < n && consecutive; ++i) consecutive = xs[i] == xs[0] + static_cast<uint32_t>(i);
   std::vector<uint32_t> dd(ys);  // divided differences f[x_0 .. x_i] after the loop
-  for (int j = 1; j < n; ++j)
+  for (int j = 1; j < n; ++j) {
+    const uint32_t inv_j = consecutive ? inv_mod_prime(static_cast<uint32_t>(j) % p, p) : 0u;
     for (int i = n - 1; i >= j; --i) {
       const uint32_t num = (dd[i] + p - dd[i - 1]) % p;
-      const uint32_t den = (xs[i] + p - xs[i - j]) % p;
-      dd[i] = mul_mod(num, inv_mod_prime(den, p), p);
+      const uint32_t inv = consecutive ? inv_j : inv_mod_prime((xs[i] + p - xs[i - j]) % p, p);
+      dd[i] = mul_mod(num, inv, p);
     }
+  }
   // P(x) = dd[0] + (x - x_0)(dd[1] + (x - x_1)(dd[2] + ...)), expanded from
   // the innermost factor outwards
   std::vector<uint32_t> c(n, 0);
@@ -208,7 +214,7 @@ int tn_weighted_polynomial(tn_plan_t plan, int32_t problem, const int32_t* edge_
                            const uint32_t* primes, int32_t nprimes, int32_t degree, void* d_workspace,
                            size_t ws_bytes, void* cuda_stream, uint32_t* coeff_residues, uint32_t* coeff_limbs,
                            int32_t* coeff_nlimbs) {
-  int rc = poly_args_ok(plan, d_workspace, primes, nprimes, degree, 1 << 20);
+  int rc = poly_args_ok(plan, d_workspace, primes, nprimes, degree, 1 << 15);
   if (rc) return rc;
   rc = weighted_checks(plan, TN_COUNT_MODP, problem, edge_w, vertex_w);
   if (rc) return rc;
