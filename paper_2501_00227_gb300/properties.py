@@ -24,18 +24,28 @@ that histogram.
 from __future__ import annotations
 
 
-def counting_max(plan, k: int = 1, polynomial=None) -> dict:
+def _poly(plan, polynomial, vertex_w):
+    if polynomial is not None:
+        return polynomial
+    if vertex_w is not None:  # sizes are total weights (weights >= 0)
+        return plan.weighted_polynomial("is", vertex_w=vertex_w)
+    return plan.independence_polynomial()
+
+
+def counting_max(plan, k: int = 1, polynomial=None, vertex_w=None) -> dict:
     """{size: count} for the k largest sizes that occur (fewer if the graph
-    has fewer distinct sizes).  k = 1 is CountingMax()."""
-    c = polynomial if polynomial is not None else plan.independence_polynomial()
+    has fewer distinct sizes).  k = 1 is CountingMax().  vertex_w: integer
+    weights >= 0, sizes then being total weights."""
+    c = _poly(plan, polynomial, vertex_w)
     sizes = [s for s in range(len(c) - 1, -1, -1) if c[s]][:k]
     return {s: c[s] for s in sorted(sizes)}
 
 
-def size_max(plan, k: int = 1, polynomial=None) -> list:
-    """The k largest independent-set sizes, each repeated by the number of
-    sets of that size, in ascending order.  k = 1 is SizeMax()."""
-    c = polynomial if polynomial is not None else plan.independence_polynomial()
+def size_max(plan, k: int = 1, polynomial=None, vertex_w=None) -> list:
+    """The k largest independent-set sizes (total weights with vertex_w),
+    each repeated by the number of sets of that size, in ascending order.
+    k = 1 is SizeMax()."""
+    c = _poly(plan, polynomial, vertex_w)
     out = []
     for s in range(len(c) - 1, -1, -1):
         take = min(c[s], k - len(out))

@@ -231,3 +231,23 @@ def test_polynomial_edge_cases(spec):
         assert p.independence_polynomial(primes=tn.PRIMES31[:1], degree=n) == want
     finally:
         p.close()
+
+
+@pytest.mark.gpu
+def test_k_best_with_vertex_weights():
+    """SizeMax(k) / CountingMax(k) over total weights, from the GPU's weighted
+    polynomial, against the brute-force weight histogram."""
+    _cuda()
+    from paper_2501_00227_gb300 import properties as P
+    n, e = g.erdos_renyi(16, 0.25, 21)
+    w = g.random_weights(n, 4, (0, 1, 2, 3))
+    hist = O.bruteforce_weighted_is(n, e, w)
+    sizes = sorted(s for s, c in enumerate(hist) for _ in range(c))
+    p = tn.Plan(n, e, nrepeat=2, seed=1)
+    try:
+        for k in (1, 3, 10):
+            assert P.size_max(p, k, vertex_w=w) == sizes[-k:]
+            top = sorted(set(sizes))[-k:]
+            assert P.counting_max(p, k, vertex_w=w) == {s: hist[s] for s in top}
+    finally:
+        p.close()
