@@ -258,3 +258,22 @@ def test_edge_case_slicings(spec, sliced):
         assert r["residues"] == [sum(c * 3 ** k for k, c in enumerate(poly)) % tn.PRIMES31[0]]
     finally:
         p.close()
+
+
+def test_result_combine_is_commutative_and_associative():
+    """Slice ranges may be combined in any grouping and order."""
+    rng = np.random.default_rng(17)
+    c = tn.tn_result_combine
+    for _ in range(200):
+        xs = [{"max": int(rng.integers(0, 4)) if rng.random() < 0.9 else None,
+               "count": int(rng.integers(0, 1 << 62))} for _ in range(3)]
+        for x in xs:
+            if x["max"] is None:
+                x["count"] = 0
+        a, b, d = xs
+        assert c("counting", a, b) == c("counting", b, a)
+        assert c("counting", c("counting", a, b), d) == c("counting", a, c("counting", b, d))
+        p = [tn.PRIMES31[0], 1000003]
+        ra, rb, rd = ({"primes": p, "residues": [int(rng.integers(0, q)) for q in p]} for _ in range(3))
+        assert c("modp", ra, rb) == c("modp", rb, ra)
+        assert c("modp", c("modp", ra, rb), rd) == c("modp", ra, c("modp", rb, rd))
