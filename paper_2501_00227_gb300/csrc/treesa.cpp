@@ -248,7 +248,7 @@ double anneal(Tree* t, const Params& P, Rng* rng, std::vector<int32_t>* best_ord
           t->RW.add(b1, d);
           t->RW.add(b2, d);
         };
-        // the move is judged by the cost of the two rewritten contractions
+        // the move is scored by the cost of the two rewritten contractions
         // (their log2 tc sum, rank penalty and log2 rw sum); the tree's cost
         // of Eq. 10 picks the best tree seen
         auto local = [&](int tc1, int tc2, int r1, int a1, int a2, int b1, int b2) {

@@ -425,3 +425,95 @@ def test_interpolation_recovers_random_polynomials():
         xs = list(range(3, 3 + d + 1))
         ys = [sum(c * pow(x, k, p) for k, c in enumerate(coeffs)) % p for x in xs]
         assert O.interpolate_modp(xs, ys, p) == coeffs
+
+
+# ---------------------------------------------------------------- recurrences (sizes beyond brute force)
+
+def _induced(n, e, keep):
+    """The subgraph induced by the vertex set `keep`, relabelled 0 .. |keep|-1."""
+    idx = {v: i for i, v in enumerate(sorted(keep))}
+    sub = [(idx[a], idx[b]) for a, b in np.asarray(e).reshape(-1, 2).tolist() if a in idx and b in idx]
+    return len(idx), np.asarray(sub, dtype=np.int32).reshape(-1, 2)
+
+
+def _poly_of(n, e, seed=1):
+    if n == 0:
+        return [1]
+    o = O.greedy_order(n, e, nrepeat=2, seed=seed)
+    return O.independence_polynomial(n, e, o, O.PRIMES31[:2])
+
+
+def _polymul(a, b):
+    out = [0] * (len(a) + len(b) - 1)
+    for i, x in enumerate(a):
+        for j, y in enumerate(b):
+            out[i + j] += x * y
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_polynomial_vertex_recurrence(seed):
+    """Every independent set either avoids v or holds v and nothing of its
+    closed neighbourhood: I(G) = I(G - v) + x I(G - N[v]).  Checked on a
+    28-vertex graph (2^28 subsets: out of brute-force reach)."""
+    n, e = g.erdos_renyi(28, 0.14, 300 + seed)
+    rng = np.random.default_rng(seed)
+    v = int(rng.integers(0, n))
+    nbr = {int(b) for a, b in e.tolist() if a == v} | {int(a) for a, b in e.tolist() if b == v}
+    full = _poly_of(n, e, seed)
+    minus_v = _poly_of(*_induced(n, e, set(range(n)) - {v}), seed)
+    minus_nv = _poly_of(*_induced(n, e, set(range(n)) - {v} - nbr), seed)
+    rhs = [0] * (n + 1)
+    for k, c in enumerate(minus_v):
+        rhs[k] += c
+    for k, c in enumerate(minus_nv):
+        rhs[k + 1] += c
+    assert full == rhs
+    # the unit-weight counting contraction agrees with the polynomial's top term
+    o = O.greedy_order(n, e, nrepeat=2, seed=seed)
+    alpha = max(k for k, c in enumerate(full) if c)
+    assert O.mis_count(n, e, o) == (alpha, full[alpha])
+
+
+def test_polynomial_of_disjoint_union_is_product():
+    """Independent sets of a disjoint union are pairs of independent sets:
+    I(G + H) = I(G) I(H)."""
+    n1, e1 = g.petersen()
+    n2, e2 = g.cycle(7)
+    e = np.concatenate([e1, e2 + n1])
+    assert _poly_of(n1 + n2, e) == _polymul(_poly_of(n1, e1), _poly_of(n2, e2))
+
+
+@pytest.mark.parametrize("a,b", [(1, 1), (2, 5), (6, 6), (9, 4)])
+def test_complete_bipartite_polynomial(a, b):
+    """An independent set of K_{a,b} lies inside one side:
+    I = (1 + x)^a + (1 + x)^b - 1."""
+    e = np.asarray([(i, a + j) for i in range(a) for j in range(b)], dtype=np.int32)
+    want = [math.comb(a, k) + math.comb(b, k) - (k == 0) for k in range(a + b + 1)]
+    assert _poly_of(a + b, e) == want
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_weighted_is_vertex_recurrence(seed):
+    """MWIS(G) = max(MWIS(G - v), w_v + MWIS(G - N[v])), and the numbers of
+    optimal sets add up accordingly, on a 26-vertex graph with weights 1..5."""
+    n, e = g.erdos_renyi(26, 0.15, 400 + seed)
+    w = g.random_weights(n, seed, (1, 2, 3, 4, 5))
+    rng = np.random.default_rng(10 + seed)
+    v = int(rng.integers(0, n))
+    nbr = {int(b) for a, b in e.tolist() if a == v} | {int(a) for a, b in e.tolist() if b == v}
+
+    def best(keep):
+        keep = sorted(keep)
+        if not keep:
+            return 0, 1
+        nn, ee = _induced(n, e, set(keep))
+        o = O.greedy_order(nn, ee, nrepeat=2, seed=seed)
+        return O.weighted_contract("counting", "is", nn, ee, o, vertex_w=w[keep])
+
+    full = best(range(n))
+    out_v = best(set(range(n)) - {v})
+    in_v = best(set(range(n)) - {v} - nbr)
+    in_v = (in_v[0] + int(w[v]), in_v[1])
+    top = max(out_v[0], in_v[0])
+    assert full == (top, (out_v[1] if out_v[0] == top else 0) + (in_v[1] if in_v[0] == top else 0))
