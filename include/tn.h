@@ -147,9 +147,24 @@ int tn_order_greedy(int32_t n, const int32_t *edges, int32_t m, double alpha,
  * one per core), each started from a greedy order (Sec. 4.2.1, one run,
  * its own seed) or, with random_init, a random tree; the best tree seen is
  * returned.  The paper's defaults: sc_target 20, betas 0.01:0.05:15,
- * ntrials 10, niters 50, sc_weight 1, rw_weight 0.2.  Slicing is not part of
- * this optimiser.  order_out: 2 * (n + m - 1) int32 (an SSA order for
- * tn_plan); log2_out (may be NULL): log2 of tc, sc, rwc of that order. */
+ * ntrials 10, niters 50, sc_weight 1, rw_weight 0.2.  order_out: 2 * (n +
+ * m - 1) int32 (an SSA order for tn_plan); log2_out (may be NULL): log2 of
+ * tc, sc, rwc of that order.
+ *
+ * tn_order_treesa_sliced: the same annealing with slicing (Sec. 4.2.2,
+ * the paper's nslices and fixed_slices): the nfixed labels fixed_slices
+ * are sliced from the start, and nslices more are picked while annealing,
+ * one at a time after a beta step (the label whose slicing leaves the
+ * smallest largest intermediate, ties by the smallest work, as
+ * tn_slice_labels), whenever the tree is above sc_target and in any case
+ * from the middle of the schedule on, the rest at its end; costs are those
+ * of one slice, so the tree keeps adapting to the labels sliced so far.
+ * nfixed + nslices <= min(n, 62); fixed_slices distinct labels in [0, n).
+ * order_out as above (an order for tn_plan_sliced with sliced_out);
+ * sliced_out: nfixed + nslices int32, the fixed labels then the picked
+ * ones; log2_out (may be NULL): log2 of the work of all slices together,
+ * of the largest intermediate of one slice, and of the reads and writes
+ * of all slices together. */
 typedef struct {
     double sc_target;
     double beta_start, beta_step, beta_stop;
@@ -162,6 +177,9 @@ typedef struct {
 } tn_treesa_params_t;
 int tn_order_treesa(int32_t n, const int32_t *edges, int32_t m, const tn_treesa_params_t *params,
                     int32_t *order_out, double *log2_out);
+int tn_order_treesa_sliced(int32_t n, const int32_t *edges, int32_t m, const tn_treesa_params_t *params,
+                           int32_t nslices, const int32_t *fixed_slices, int32_t nfixed, int32_t *order_out,
+                           int32_t *sliced_out, double *log2_out);
 
 /* Complexity and workspace sizes of a plan; nprimes sizes the mod-p entry. */
 int tn_plan_info(tn_plan_t plan, tn_semiring_t semiring, int32_t nprimes, tn_plan_info_t *out);

@@ -26,6 +26,11 @@
 // order, niters sweeps per beta.  Trials start from greedy orders
 // (Sec. 4.2.1, one run each, own seed) or random trees, run on host threads,
 // and the best tree seen over all trials is returned as an SSA order.
+//
+// Slicing (the optimiser's nslices / fixed_slices): a sliced label leaves
+// every tensor, so it is cut from every node's label set and the sums are
+// recounted; costs are then those of one slice.  Fixed labels are cut from
+// the start, the others picked while annealing (struct Slicer).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -102,6 +107,8 @@ double cost(const Tree& t, double sc_target, double ws, double wrw) {
   return t.TC.log2sum() + ws * std::max(0.0, t.sc() - sc_target) + wrw * t.RW.log2sum();
 }
 
+void recount(Tree* t);
+
 // Tree from an SSA order; leaf labels: edge e = {u, v}, vertex v = {v}.
 void build_tree(int32_t n, const int32_t* edges, int32_t m, const int32_t* order, Tree* t) {
   const int T = n + m, N = 2 * T - 1;
@@ -124,7 +131,6 @@ void build_tree(int32_t n, const int32_t* edges, int32_t m, const int32_t* order
     t->L(m + v)[v / 64] |= 1ull << (v % 64);
     total[v]++;
   }
-  for (int x = 0; x < T; ++x) t->rank[x] = t->popc(t->L(x));
   // internal nodes: labels of the union still carried by some leaf outside;
   // cs[x] = (label, leaves of x's subtree carrying it), sorted by label
   std::vector<std::vector<std::pair<int32_t, int32_t>>> cs(N);
@@ -156,9 +162,16 @@ void build_tree(int32_t n, const int32_t* edges, int32_t m, const int32_t* order
     std::vector<std::pair<int32_t, int32_t>>().swap(cs[b]);
   }
   t->root = N - 1;
-  t->rank_hist.assign(n + 2, 0);
-  t->TC.reset(n + 2);
-  t->RW.reset(n + 2);
+  recount(t);
+}
+
+// Ranks of all nodes and the running sums, from the label sets.
+void recount(Tree* t) {
+  const int T = t->T, N = static_cast<int>(t->left.size()), nl = t->W * 64;
+  t->rank_hist.assign(nl + 2, 0);
+  t->TC.reset(nl + 2);
+  t->RW.reset(nl + 2);
+  for (int x = 0; x < T; ++x) t->rank[x] = t->popc(t->L(x));
   for (int c = T; c < N; ++c) {
     t->rank[c] = t->popc(t->L(c));
     const int a = t->left[c], b = t->right[c];
@@ -169,6 +182,41 @@ void build_tree(int32_t n, const int32_t* edges, int32_t m, const int32_t* order
     t->RW.add(t->rank[c], 1);
     t->rank_hist[t->rank[c]]++;
   }
+}
+
+// Slice label v: it leaves every tensor (a sliced network's leaves do not
+// carry it), so it leaves every node's label set.
+void slice_label(Tree* t, int v) {
+  const int N = static_cast<int>(t->left.size());
+  for (int x = 0; x < N; ++x) t->L(x)[v / 64] &= ~(1ull << (v % 64));
+  recount(t);
+}
+
+// The label whose slicing leaves the smallest largest intermediate, ties by
+// the smallest total work (the rule of tn_slice_labels, on the tree's
+// current label sets); -1 when every label is sliced already.
+int pick_slice(const Tree& t, int n, const std::vector<char>& cut) {
+  const int T = t.T, N = static_cast<int>(t.left.size());
+  int best = -1, bsc = 0;
+  double btc = 0;
+  for (int v = 0; v < n; ++v) {
+    if (cut[v]) continue;
+    const int w = v / 64;
+    const uint64_t bit = 1ull << (v % 64);
+    int sc = 0;
+    double tc = 0;
+    for (int c = T; c < N; ++c) {
+      sc = std::max(sc, t.rank[c] - ((t.L(c)[w] & bit) ? 1 : 0));
+      const bool in = ((t.L(t.left[c])[w] | t.L(t.right[c])[w]) & bit) != 0;
+      tc += std::ldexp(1.0, t.tce[c] - (in ? 1 : 0));
+    }
+    if (best < 0 || sc < bsc || (sc == bsc && tc < btc)) {
+      best = v;
+      bsc = sc;
+      btc = tc;
+    }
+  }
+  return best;
 }
 
 // SSA order of the tree (children before parents, post-order).
@@ -199,9 +247,63 @@ struct Params {
   int niters;
 };
 
+// Slicing inside the annealing: `want` more labels are sliced, one at a time
+// (pick_slice) after a beta step, whenever the tree is above sc_target and
+// in any case once the schedule is half done, so that the tree keeps
+// adapting to the slices; any still missing at the end are picked then.
+struct Slicer {
+  int n = 0, m = 0, want = 0;
+  const int32_t* edges = nullptr;
+  std::vector<int32_t> fixed;
+  std::vector<char> cut;          // sliced labels (fixed ones included)
+  std::vector<int32_t> picked;    // in the order picked
+  std::vector<int32_t> best_picked;  // those of the best tree
+};
+
+void slice_one(Tree* t, Slicer* sl) {
+  const int v = pick_slice(*t, sl->n, sl->cut);
+  if (v < 0) {  // every label sliced already: nothing more to take
+    sl->want = static_cast<int>(sl->picked.size());
+    return;
+  }
+  sl->cut[v] = 1;
+  sl->picked.push_back(v);
+  slice_label(t, v);
+}
+
+// Once all slices are in: pick them again, from scratch, on the current
+// tree (rebuilt from its order with the fixed labels cut), and keep the new
+// set if the tree's cost drops -- labels picked on an early tree would
+// otherwise stay whatever the annealing made of it.
+bool reslice(Tree* t, Slicer* sl, const Params& P) {
+  std::vector<int32_t> ord(2 * size_t(t->T - 1));
+  tree_order(*t, ord.data());
+  Tree u;
+  build_tree(sl->n, sl->edges, sl->m, ord.data(), &u);
+  std::vector<char> cut(static_cast<size_t>(sl->n), 0);
+  for (int32_t f : sl->fixed) {
+    cut[f] = 1;
+    slice_label(&u, f);
+  }
+  std::vector<int32_t> picked;
+  for (int j = 0; j < sl->want; ++j) {
+    const int v = pick_slice(u, sl->n, cut);
+    if (v < 0) return false;
+    cut[v] = 1;
+    picked.push_back(v);
+    slice_label(&u, v);
+  }
+  if (!(cost(u, P.sc_target, P.ws, P.wrw) < cost(*t, P.sc_target, P.ws, P.wrw) - 1e-12)) return false;
+  *t = std::move(u);
+  sl->cut = std::move(cut);
+  sl->picked = std::move(picked);
+  return true;
+}
+
 // One annealing run on t; returns the best cost seen and leaves the best
-// tree's SSA order in best_order.
-double anneal(Tree* t, const Params& P, Rng* rng, std::vector<int32_t>* best_order) {
+// tree's SSA order in best_order.  With a slicer, the best tree is taken
+// among those carrying all of its slices.
+double anneal(Tree* t, const Params& P, Rng* rng, std::vector<int32_t>* best_order, Slicer* sl = nullptr) {
   const int N = static_cast<int>(t->left.size());
   const int W = t->W;
   std::vector<int32_t> internal;
@@ -210,7 +312,12 @@ double anneal(Tree* t, const Params& P, Rng* rng, std::vector<int32_t>* best_ord
   double cur = cost(*t, P.sc_target, P.ws, P.wrw);
   double best = cur;
   best_order->assign(2 * size_t(t->T - 1), 0);
-  tree_order(*t, best_order->data());
+  auto keep_best = [&]() {
+    best = cur;
+    tree_order(*t, best_order->data());
+    if (sl) sl->best_picked = sl->picked;
+  };
+  keep_best();
   const int nbeta = static_cast<int>(std::floor((P.b1 - P.b0) / P.db + 1e-9)) + 1;
   for (int bi = 0; bi < nbeta; ++bi) {
     const double beta = P.b0 + bi * P.db;
@@ -277,12 +384,22 @@ double anneal(Tree* t, const Params& P, Rng* rng, std::vector<int32_t>* best_ord
           t->tce[I] = tcI;
           t->tce[Nn] = tcN;
           cur = c2;
-          if (cur < best - 1e-12) {
-            best = cur;
-            tree_order(*t, best_order->data());
-          }
+          if (cur < best - 1e-12) keep_best();
         }
       }
+    }
+    if (!sl) continue;
+    if (static_cast<int>(sl->picked.size()) < sl->want) {
+      if (t->sc() > P.sc_target || 2 * (bi + 1) >= nbeta || bi + 1 == nbeta) {
+        do slice_one(t, sl);
+        while (bi + 1 == nbeta && static_cast<int>(sl->picked.size()) < sl->want);
+        // the trees seen so far carry fewer slices: start the best over
+        cur = cost(*t, P.sc_target, P.ws, P.wrw);
+        keep_best();
+      }
+    } else if (sl->want > 0 && reslice(t, sl, P)) {
+      cur = cost(*t, P.sc_target, P.ws, P.wrw);
+      if (cur < best - 1e-12) keep_best();
     }
   }
   return best;
@@ -307,15 +424,31 @@ void random_order(int T, Rng* rng, int32_t* order) {
 }  // namespace
 }  // namespace tn
 
-extern "C" int tn_order_treesa(int32_t n, const int32_t* edges, int32_t m, const tn_treesa_params_t* prm,
-                               int32_t* order_out, double* log2_out) {
-  using namespace tn;
+namespace tn {
+namespace {
+
+// Both entry points: anneal ntrials trees (the fixed slices cut from the
+// start, nslices more picked while annealing) and return the best.
+int treesa_run(int32_t n, const int32_t* edges, int32_t m, const tn_treesa_params_t* prm, const int32_t* fixed,
+               int32_t nfixed, int32_t nslices, int32_t* order_out, int32_t* sliced_out, double* log2_out) {
   if (!prm || !order_out || n < 1 || m < 0 || (m > 0 && !edges)) return TN_EINVAL;
   if (!(prm->beta_step > 0) || !(prm->beta_stop >= prm->beta_start) || prm->niters < 0 || prm->ntrials < 1 ||
       !(prm->sc_weight >= 0) || !(prm->rw_weight >= 0) || (prm->beta_stop - prm->beta_start) / prm->beta_step > 1e6)
     return TN_EINVAL;
+  if (nfixed < 0 || nslices < 0 || nfixed + nslices > std::min(n, 62) || (nfixed > 0 && !fixed) ||
+      (nfixed + nslices > 0 && !sliced_out))
+    return TN_EINVAL;
+  std::vector<char> cut0(static_cast<size_t>(n), 0);
+  for (int j = 0; j < nfixed; ++j) {
+    if (fixed[j] < 0 || fixed[j] >= n || cut0[fixed[j]]) return TN_EINVAL;
+    cut0[fixed[j]] = 1;
+  }
   const int32_t T = n + m;
-  if (T < 2) return TN_OK;
+  if (T < 2) {  // one vertex tensor, no contraction: label 0 is the only one
+    for (int j = 0; j < nfixed + nslices; ++j) sliced_out[j] = 0;
+    if (log2_out) log2_out[0] = log2_out[1] = log2_out[2] = 0;
+    return TN_OK;
+  }
   try {
     // validate the graph (and get a greedy order) through the greedy optimiser
     std::vector<int32_t> init(2 * size_t(T - 1));
@@ -325,7 +458,7 @@ extern "C" int tn_order_treesa(int32_t n, const int32_t* edges, int32_t m, const
              prm->niters};
     const int trials = prm->ntrials;
     std::vector<double> best(trials, INFINITY);
-    std::vector<std::vector<int32_t>> orders(trials);
+    std::vector<std::vector<int32_t>> orders(trials), picks(trials);
     std::vector<int> rcs(trials, TN_OK);
     auto run = [&](int k) {
       try {
@@ -342,7 +475,16 @@ extern "C" int tn_order_treesa(int32_t n, const int32_t* edges, int32_t m, const
         }
         Tree t;
         build_tree(n, edges, m, start.data(), &t);
-        best[k] = anneal(&t, P, &rng, &orders[k]);
+        for (int j = 0; j < nfixed; ++j) slice_label(&t, fixed[j]);
+        Slicer sl;
+        sl.n = n;
+        sl.m = m;
+        sl.edges = edges;
+        sl.fixed.assign(fixed, fixed + nfixed);
+        sl.want = nslices;
+        sl.cut = cut0;
+        best[k] = anneal(&t, P, &rng, &orders[k], nslices > 0 ? &sl : nullptr);
+        picks[k] = sl.best_picked;
       } catch (const std::bad_alloc&) {
         rcs[k] = TN_ENOMEM;
       }
@@ -359,16 +501,36 @@ extern "C" int tn_order_treesa(int32_t n, const int32_t* edges, int32_t m, const
       if (rcs[k]) return rcs[k];
       if (kb < 0 || best[k] < best[kb]) kb = k;
     }
+    if (static_cast<int>(picks[kb].size()) != nslices) return TN_EINVAL;
     std::copy(orders[kb].begin(), orders[kb].end(), order_out);
+    for (int j = 0; j < nfixed; ++j) sliced_out[j] = fixed[j];
+    for (int j = 0; j < nslices; ++j) sliced_out[nfixed + j] = picks[kb][j];
     if (log2_out) {
+      // per slice: work, largest intermediate, reads and writes; the work
+      // and traffic of all 2^s slices are 2^s times one slice's
       Tree t;
       build_tree(n, edges, m, order_out, &t);
-      log2_out[0] = t.TC.log2sum();
+      for (int j = 0; j < nfixed + nslices; ++j) slice_label(&t, sliced_out[j]);
+      log2_out[0] = t.TC.log2sum() + nfixed + nslices;
       log2_out[1] = t.sc();
-      log2_out[2] = t.RW.log2sum();
+      log2_out[2] = t.RW.log2sum() + nfixed + nslices;
     }
     return TN_OK;
   } catch (const std::bad_alloc&) {
     return TN_ENOMEM;
   }
+}
+
+}  // namespace
+}  // namespace tn
+
+extern "C" int tn_order_treesa(int32_t n, const int32_t* edges, int32_t m, const tn_treesa_params_t* prm,
+                               int32_t* order_out, double* log2_out) {
+  return tn::treesa_run(n, edges, m, prm, nullptr, 0, 0, order_out, nullptr, log2_out);
+}
+
+extern "C" int tn_order_treesa_sliced(int32_t n, const int32_t* edges, int32_t m, const tn_treesa_params_t* prm,
+                                      int32_t nslices, const int32_t* fixed_slices, int32_t nfixed,
+                                      int32_t* order_out, int32_t* sliced_out, double* log2_out) {
+  return tn::treesa_run(n, edges, m, prm, fixed_slices, nfixed, nslices, order_out, sliced_out, log2_out);
 }

@@ -108,6 +108,8 @@ def lib():
         L.tn_single_config_workspace_bytes.argtypes = [vp, ctypes.POINTER(u64)]
         L.tn_order_treesa.argtypes = [i32, i32p, i32, ctypes.POINTER(tn_treesa_params_t), i32p,
                                       ctypes.POINTER(ctypes.c_double)]
+        L.tn_order_treesa_sliced.argtypes = [i32, i32p, i32, ctypes.POINTER(tn_treesa_params_t), i32, i32p, i32,
+                                             i32p, i32p, ctypes.POINTER(ctypes.c_double)]
         L.tn_slice_labels.argtypes = [i32, i32p, i32, i32p, i32, i32, i32p, ctypes.POINTER(ctypes.c_double)]
         L.tn_plan_sliced.argtypes = [i32, i32p, i32, i32p, i32, i32p, i32, ctypes.POINTER(vp)]
         L.tn_contract_sliced.argtypes = [vp, ctypes.c_int, i32, i32p, i32p, u32p, u32p, i32, u64, u64, vp,
@@ -409,14 +411,36 @@ def tn_order_treesa(n, edges, *, sc_target: float = 20.0, betas=(1.0, 0.05, 15.0
     this cost's log2 scale a start hotter than about 0.3 melts the greedy
     starting trees of 100+ vertex graphs beyond what the schedule recovers."""
     e = _i32(edges).reshape(-1, 2)
-    prm = tn_treesa_params_t(float(sc_target), float(betas[0]), float(betas[1]), float(betas[2]), int(niters),
-                             int(ntrials), float(sc_weight), float(rw_weight), int(bool(random_init)), int(nthreads),
-                             int(seed))
-    T = int(n) + len(e)
-    order = np.zeros((max(T - 1, 0), 2), dtype=np.int32)
+    prm = _treesa_params(sc_target, betas, niters, ntrials, sc_weight, rw_weight, random_init, nthreads, seed)
+    order = np.zeros((max(int(n) + len(e) - 1, 0), 2), dtype=np.int32)
     lg = (ctypes.c_double * 3)()
     _check(lib().tn_order_treesa(int(n), _p32(e), len(e), ctypes.byref(prm), _p32(order), lg), "tn_order_treesa")
     return order, tuple(float(x) for x in lg)
+
+
+def _treesa_params(sc_target, betas, niters, ntrials, sc_weight, rw_weight, random_init, nthreads, seed):
+    return tn_treesa_params_t(float(sc_target), float(betas[0]), float(betas[1]), float(betas[2]), int(niters),
+                              int(ntrials), float(sc_weight), float(rw_weight), int(bool(random_init)),
+                              int(nthreads), int(seed))
+
+
+def tn_order_treesa_sliced(n, edges, *, nslices: int = 0, fixed_slices=(), sc_target: float = 20.0,
+                           betas=(1.0, 0.05, 15.0), niters: int = 50, ntrials: int = 10, sc_weight: float = 1.0,
+                           rw_weight: float = 0.2, random_init: bool = False, nthreads: int = 0, seed: int = 0):
+    """TreeSA with slicing (Sec. 4.2.2): `fixed_slices` sliced from the
+    start, `nslices` more picked while annealing.  Returns (order, sliced
+    labels -- the fixed ones first --, log2 (work of all slices, largest
+    intermediate of one slice, reads and writes of all slices))."""
+    e = _i32(edges).reshape(-1, 2)
+    fx = _i32(list(fixed_slices)).reshape(-1)
+    prm = _treesa_params(sc_target, betas, niters, ntrials, sc_weight, rw_weight, random_init, nthreads, seed)
+    order = np.zeros((max(int(n) + len(e) - 1, 0), 2), dtype=np.int32)
+    sl = np.zeros(max(fx.size + int(nslices), 1), dtype=np.int32)
+    lg = (ctypes.c_double * 3)()
+    _check(lib().tn_order_treesa_sliced(int(n), _p32(e), len(e), ctypes.byref(prm), int(nslices),
+                                        _p32(fx) if fx.size else None, fx.size, _p32(order), _p32(sl), lg),
+           "tn_order_treesa_sliced")
+    return order, sl[: fx.size + int(nslices)], tuple(float(x) for x in lg)
 
 
 def tn_slice_labels(n, edges, order, nslices: int):
@@ -682,7 +706,9 @@ class Plan:
                  optimizer: str = "greedy", treesa=None, sliced=None):
         """order None: found by `optimizer` -- "greedy" (Sec. 4.2.1, nrepeat /
         seed / alpha) or "treesa" (Sec. 4.2.2, keyword arguments of
-        tn_order_treesa in the dict `treesa`, seed defaulting to `seed`).
+        tn_order_treesa in the dict `treesa`, seed defaulting to `seed`;
+        with "nslices" or "fixed_slices" among them, the labels sliced while
+        annealing, tn_order_treesa_sliced, become the plan's slices).
         sliced: vertex labels to slice (tn_plan_sliced; contract with
         contract_sliced), or an int s to pick s labels with tn_slice_labels."""
         self.n = int(n)
@@ -692,7 +718,12 @@ class Plan:
         elif optimizer == "treesa":
             kw = dict(treesa or {})
             kw.setdefault("seed", seed)
-            self.order, _ = tn_order_treesa(n, self.edges, **kw)
+            if "nslices" in kw or "fixed_slices" in kw:
+                if sliced is not None:
+                    raise TNError(TN_EINVAL, "slices come from the annealing or from `sliced`, not both")
+                self.order, sliced, _ = tn_order_treesa_sliced(n, self.edges, **kw)
+            else:
+                self.order, _ = tn_order_treesa(n, self.edges, **kw)
         elif optimizer == "greedy":
             self.order = tn_order_greedy(n, self.edges, alpha, nrepeat, seed)
         else:

@@ -190,6 +190,26 @@ def test_sliced_contraction_equals_unsliced(spec, s):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("spec,s,fixed", [("reg3:60:2", 3, ()), ("ksg:8:0.8:2", 2, (5,))])
+def test_annealed_sliced_plans_equal_the_oracle(spec, s, fixed):
+    """Orders and slices from the annealing with slicing (TreeSA, Sec.
+    4.2.2) contract to the oracle's unsliced values."""
+    _cuda()
+    n, e = g.by_name(spec)
+    p = tn.Plan(n, e, optimizer="treesa", seed=4,
+                treesa={"ntrials": 2, "niters": 5, "nslices": s, "fixed_slices": fixed, "sc_target": 4.0})
+    try:
+        assert len(p.sliced) == s + len(fixed)
+        ref = O.greedy_order(n, e, nrepeat=2, seed=1)
+        r = p.contract_sliced("counting")
+        assert (r["max"], r["count"]) == O.mis_count(n, e, ref)
+        pr = list(tn.PRIMES31[:2])
+        assert p.contract_sliced("modp", primes=pr, xs=[1, 1])["residues"] == O.count_modp(n, e, ref, pr)
+    finally:
+        p.close()
+
+
+@pytest.mark.gpu
 def test_single_slices_match_the_fixed_graphs():
     _cuda()
     n, e = g.erdos_renyi(18, 0.2, 3)

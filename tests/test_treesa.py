@@ -106,3 +106,82 @@ def test_plan_with_treesa_order():
         assert p.info("tropical_i32")["log2_tc"] == pytest.approx(_log2c(n, e, p.order)[0], abs=1e-9)
     finally:
         p.close()
+
+
+# ------------------------------------------------------------------ slicing inside the annealing
+
+def _plan_log2(n, e, o, sliced):
+    """log2 (work of all slices, largest intermediate of one slice, reads and
+    writes of all slices) of a sliced plan, from the plan builder."""
+    p = tn.Plan(n, e, o, sliced=sliced)
+    try:
+        info = p.info("tropical_i32")
+    finally:
+        p.close()
+    s = len(sliced)
+    return info["log2_tc"] + s, info["log2_sc"], info["log2_rwc"] + s
+
+
+@pytest.mark.parametrize("spec,s,fixed", [("reg3:60:2", 2, ()), ("reg3:100:1", 4, ()), ("ksg:10:0.8:3", 3, (7,)),
+                                          ("petersen", 1, (0, 9)), ("square:6", 0, (14,))])
+def test_sliced_orders_are_valid_and_carry_their_complexities(spec, s, fixed):
+    n, e = g.by_name(spec)
+    o, sl, lg = tn.tn_order_treesa_sliced(n, e, nslices=s, fixed_slices=fixed, sc_target=6.0, seed=2, ntrials=3,
+                                          niters=5)
+    assert O.check_order(n, e, o)
+    assert len(sl) == len(fixed) + s and len(set(sl.tolist())) == len(sl)
+    assert tuple(sl[: len(fixed)].tolist()) == tuple(fixed) and all(0 <= v < n for v in sl)
+    assert lg == pytest.approx(_plan_log2(n, e, o, sl), abs=1e-9)
+
+
+@pytest.mark.parametrize("spec,s", [("reg3:100:1", 2), ("reg3:100:1", 4), ("reg3:140:1", 4), ("ksg:12:0.8:1", 4)])
+def test_annealed_slices_against_slicing_afterwards(spec, s):
+    """Target s below the unsliced annealed tree's largest intermediate, s
+    labels to slice: slicing inside the annealing ends with an intermediate
+    no larger than slicing the annealed tree afterwards (tn_slice_labels),
+    for at most twice its work; on the 3-regular graphs, where every slice
+    takes a rank off, it meets the target."""
+    n, e = g.by_name(spec)
+    sc0 = tn.tn_order_treesa(n, e, seed=1, ntrials=4, niters=10)[1][1]
+    o, sl, lg = tn.tn_order_treesa_sliced(n, e, nslices=s, sc_target=sc0 - s, seed=1, ntrials=4, niters=10)
+    o0, _ = tn.tn_order_treesa(n, e, sc_target=sc0 - s, seed=1, ntrials=4, niters=10)
+    post = tn.tn_slice_labels(n, e, o0, s)[1]
+    assert lg[1] <= post[1] and lg[0] <= post[0] + 1.0
+    if spec.startswith("reg3"):
+        assert lg[1] <= sc0 - s
+
+
+def test_no_slices_is_the_plain_optimiser():
+    n, e = g.erdos_renyi(30, 0.15, 2)
+    a = tn.tn_order_treesa(n, e, seed=5, ntrials=2, niters=5)
+    o, sl, lg = tn.tn_order_treesa_sliced(n, e, seed=5, ntrials=2, niters=5)
+    assert np.array_equal(a[0], o) and a[1] == lg and len(sl) == 0
+
+
+def test_sliced_deterministic_for_a_seed():
+    n, e = g.random_regular3(60, 3)
+    a = tn.tn_order_treesa_sliced(n, e, nslices=3, sc_target=5.0, seed=9, ntrials=3, nthreads=3, niters=5)
+    b = tn.tn_order_treesa_sliced(n, e, nslices=3, sc_target=5.0, seed=9, ntrials=3, nthreads=1, niters=5)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
+
+
+@pytest.mark.parametrize("kw", [dict(nslices=-1), dict(nslices=63), dict(fixed_slices=(3, 3)),
+                                dict(fixed_slices=(-1,)), dict(fixed_slices=(10,)), dict(nslices=8, fixed_slices=(1, 2, 3))])
+def test_sliced_rejects_bad_arguments(kw):
+    n, e = g.petersen()
+    with pytest.raises(tn.TNError) as ei:
+        tn.tn_order_treesa_sliced(n, e, **kw)
+    assert ei.value.code == tn.TN_EINVAL
+
+
+def test_plan_with_annealed_slices():
+    n, e = g.random_regular3(60, 2)
+    sc0 = tn.tn_order_treesa(n, e, seed=3, ntrials=2)[1][1]
+    p = tn.Plan(n, e, optimizer="treesa", seed=3, treesa={"ntrials": 2, "nslices": 2, "sc_target": sc0 - 2})
+    try:
+        assert O.check_order(n, e, p.order) and len(p.sliced) == 2
+        assert p.info("tropical_i32")["log2_sc"] <= sc0 - 2
+    finally:
+        p.close()
+    with pytest.raises(tn.TNError):
+        tn.Plan(n, e, optimizer="treesa", treesa={"nslices": 1}, sliced=[0])
