@@ -16,6 +16,11 @@ here they are read off the exact polynomial, which costs alpha + 1
 evaluations per prime instead of one wider contraction but gives the same
 numbers (counts are exact integers, not saturated).
 
+SingleConfigMax(k) (single_config_max_k): k distinct sets with the k
+largest sizes or total weights, by Lawler's partition of the solution space
+over the GPU's optimal-configuration pass (tn_single_config_max), vertices
+forced in or out through their weights.
+
 For the spin glass of Eq. 1: the ground state (CountingMin) from the
 counting contraction of -H, the exact energy histogram from
 ``Plan.weighted_polynomial``, and ln Z(beta) (PartitionFunction) summed from
@@ -83,3 +88,72 @@ def log_partition_function(plan, beta: float, edge_w=None, vertex_w=None, histog
     terms = [math.log(v) - beta * (k - shift) for k, v in enumerate(c) if v]
     top = max(terms)
     return top + math.log(sum(math.exp(t - top) for t in terms))
+
+
+# --------------------------------------------------------------------------- k best configurations
+
+def single_config_max_k(plan, k: int = 1, vertex_w=None, solve=None) -> list:
+    """SingleConfigMax(k) of Sec. 5.3: k distinct independent sets whose
+    total weights (sizes with vertex_w None) are the k largest over all
+    independent sets, ties in any order, as [(weight, config)] by
+    non-increasing weight (fewer if the graph has fewer sets).
+
+    Lawler's partition of the solution space: the best set x of a subspace
+    (vertices forced in F1, forced out F0) splits the rest of that subspace
+    into disjoint subspaces, one per free vertex v_i in index order, each
+    agreeing with x on v_1 .. v_{i-1} and differing on v_i; the best of
+    every open subspace waits in a heap.  A subspace's best set comes from
+    one optimal-configuration pass on the GPU (Plan.single_config_max, or
+    `solve(weights) -> (max, config)`): with B = 2 sum|w| + 1, vertices of
+    F1 weigh w + B and those of F0 w - B, so every optimum avoids F0 and
+    holds all of F1 when F1 is independent; its weight is max - B |F1|."""
+    import heapq
+
+    import numpy as np
+    n = plan.n
+    e = np.asarray(plan.edges).reshape(-1, 2)
+    w = np.ones(n, dtype=np.int64) if vertex_w is None else np.asarray(vertex_w, dtype=np.int64).reshape(-1)
+    if w.size != n:
+        raise ValueError("vertex_w needs one weight per vertex")
+    big = 2 * int(np.abs(w).sum()) + 1
+    if int(np.abs(w).sum()) + big * n > 2 ** 28:       # the int32 max-plus path's bound on sum |w|
+        raise ValueError("weights too large to force vertices in or out")
+    if solve is None:
+        def solve(wf):
+            return plan.single_config_max("is", vertex_w=wf)
+    nbr = [set() for _ in range(n)]
+    for a, b in e.tolist():
+        nbr[a].add(b)
+        nbr[b].add(a)
+
+    def best(f1, f0):
+        if any(nbr[v] & f1 for v in f1):
+            return None
+        wf = w.copy()
+        wf[list(f1)] += big
+        wf[list(f0)] -= big
+        val, cfg = solve(wf.astype(np.int32))
+        cfg = np.asarray(cfg, dtype=np.uint8)
+        if any(cfg[v] == 0 for v in f1) or any(cfg[v] == 1 for v in f0):
+            return None
+        return int(val) - big * len(f1), cfg
+
+    out, heap, tick = [], [], 0
+    first = best(frozenset(), frozenset())
+    if first is not None:
+        heap.append((-first[0], tick, first[1], frozenset(), frozenset()))
+    while heap and len(out) < k:
+        negv, _, cfg, f1, f0 = heapq.heappop(heap)
+        out.append((-negv, cfg))
+        in_, out_ = set(f1), set(f0)
+        for v in range(n):
+            if v in f1 or v in f0:
+                continue
+            # the subspace agreeing with cfg before v and differing at v
+            f1n, f0n = (frozenset(in_), frozenset(out_ | {v})) if cfg[v] else (frozenset(in_ | {v}), frozenset(out_))
+            r = best(f1n, f0n)
+            if r is not None:
+                tick += 1
+                heapq.heappush(heap, (-r[0], tick, r[1], f1n, f0n))
+            (in_ if cfg[v] else out_).add(v)
+    return out

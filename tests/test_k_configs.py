@@ -1,0 +1,126 @@
+"""SingleConfigMax(k) (Sec. 5.3): k distinct independent sets with the k
+largest total weights, by Lawler's partition over optimal-configuration
+passes.  The partition logic is checked on the CPU with a brute-force
+solver in its place; the GPU tests run it on the single-configuration pass
+and compare the weights with the oracle's polynomial / weight histogram."""
+import numpy as np
+import pytest
+
+import graphgen as g
+import oracle as O
+from paper_2501_00227_gb300 import properties as P
+from paper_2501_00227_gb300 import tn
+
+
+class _Graph:
+    """What single_config_max_k reads of a plan, without a plan handle."""
+
+    def __init__(self, n, e):
+        self.n, self.edges = n, np.asarray(e, dtype=np.int32).reshape(-1, 2)
+
+
+def _brute_solver(n, e):
+    """Best total weight over all 2^n subsets and the lowest-index subset
+    reaching it (test stand-in for the GPU pass; n <= 16)."""
+    masks = np.arange(1 << n, dtype=np.int64)
+    bits = ((masks[:, None] >> np.arange(n)) & 1).astype(np.int64)
+    ok = np.ones(1 << n, dtype=bool)
+    for a, b in np.asarray(e).reshape(-1, 2).tolist():
+        ok &= ~((bits[:, a] == 1) & (bits[:, b] == 1))
+
+    def solve(wf):
+        vals = np.where(ok, bits @ np.asarray(wf, dtype=np.int64), np.iinfo(np.int64).min)
+        i = int(np.argmax(vals))
+        return int(vals[i]), bits[i].astype(np.uint8)
+    return solve
+
+
+def _weights_of_all_sets(n, e, w):
+    """Total weights of all independent sets, largest first (brute force)."""
+    hist = O.bruteforce_weighted_is(n, e, w) if w is not None else O.bruteforce_poly(n, e)
+    return [s for s in range(len(hist) - 1, -1, -1) for _ in range(hist[s])]
+
+
+def _check(n, e, res, k, w):
+    want = _weights_of_all_sets(n, e, w)[:k]
+    assert [v for v, _ in res] == want
+    seen = set()
+    ww = np.ones(n, dtype=np.int64) if w is None else np.asarray(w, dtype=np.int64)
+    for v, cfg in res:
+        assert all(not (cfg[a] and cfg[b]) for a, b in np.asarray(e).reshape(-1, 2).tolist())
+        assert int(ww @ cfg.astype(np.int64)) == v
+        seen.add(cfg.tobytes())
+    assert len(seen) == len(res)
+
+
+def test_petersen_two_best_printed():
+    """Sec. 5.3 prints SingleConfigMax(2) of the Petersen graph: two
+    different sets of size 4 (which two depends on the solver)."""
+    n, e = g.petersen()
+    res = P.single_config_max_k(_Graph(n, e), 2, solve=_brute_solver(n, e))
+    assert [v for v, _ in res] == [4, 4]
+    _check(n, e, res, 2, None)
+
+
+@pytest.mark.parametrize("spec,k", [("petersen", 12), ("er:12:0.3:2", 40), ("cycle:9", 7), ("path:3", 10),
+                                    ("complete:5", 8), ("empty:4", 16)])
+def test_partition_enumerates_in_weight_order(spec, k):
+    n, e = g.by_name(spec)
+    res = P.single_config_max_k(_Graph(n, e), k, solve=_brute_solver(n, e))
+    _check(n, e, res, k, None)
+    assert len(res) == min(k, sum(O.bruteforce_poly(n, e)))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_partition_with_weights(seed):
+    n, e = g.erdos_renyi(12, 0.3, 70 + seed)
+    w = g.random_weights(n, seed, (0, 1, 2, 5))
+    res = P.single_config_max_k(_Graph(n, e), 25, vertex_w=w, solve=_brute_solver(n, e))
+    _check(n, e, res, 25, w)
+
+
+def test_all_sets_of_a_small_graph():
+    """k beyond the number of sets enumerates every independent set once."""
+    n, e = g.cycle(6)
+    res = P.single_config_max_k(_Graph(n, e), 100, solve=_brute_solver(n, e))
+    assert len(res) == 18                                   # the Lucas number L_6
+    _check(n, e, res, 100, None)
+
+
+def test_rejects_weights_too_large_to_force():
+    n, e = g.path(4)
+    with pytest.raises(ValueError):
+        P.single_config_max_k(_Graph(n, e), 2, vertex_w=[1 << 25] * 4, solve=_brute_solver(n, e))
+
+
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("spec,k", [("petersen", 2), ("petersen", 20), ("er:14:0.25:3", 30), ("ksg:4:0.8:1", 12)])
+def test_k_best_configurations_on_gpu(spec, k):
+    _cuda()
+    n, e = g.by_name(spec)
+    p = tn.Plan(n, e, nrepeat=2, seed=1)
+    try:
+        res = P.single_config_max_k(p, k)
+    finally:
+        p.close()
+    _check(n, e, res, k, None)
+
+
+@pytest.mark.gpu
+def test_k_best_weighted_configurations_on_gpu():
+    _cuda()
+    n, e = g.erdos_renyi(13, 0.3, 5)
+    w = g.random_weights(n, 3, (0, 1, 2, 3))
+    p = tn.Plan(n, e, nrepeat=2, seed=1)
+    try:
+        res = P.single_config_max_k(p, 15, vertex_w=w)
+    finally:
+        p.close()
+    _check(n, e, res, 15, w)
