@@ -106,7 +106,10 @@ def single_config_max_k(plan, k: int = 1, vertex_w=None, solve=None) -> list:
     one optimal-configuration pass on the GPU (Plan.single_config_max, or
     `solve(weights) -> (max, config)`): with B = 2 sum|w| + 1, vertices of
     F1 weigh w + B and those of F0 w - B, so every optimum avoids F0 and
-    holds all of F1 when F1 is independent; its weight is max - B |F1|."""
+    holds all of F1 when F1 is independent; its weight is max - B |F1|.
+    Subspaces are solved only when their bound (the parent's weight)
+    reaches the top of the heap, so k sets take far fewer than k n passes
+    when many sets share the top weights."""
     import heapq
 
     import numpy as np
@@ -119,8 +122,13 @@ def single_config_max_k(plan, k: int = 1, vertex_w=None, solve=None) -> list:
     if int(np.abs(w).sum()) + big * n > 2 ** 28:       # the int32 max-plus path's bound on sum |w|
         raise ValueError("weights too large to force vertices in or out")
     if solve is None:
+        import torch
+
+        from . import tn
+        ws = torch.empty(tn.tn_single_config_workspace_bytes(plan.handle), dtype=torch.uint8, device="cuda")
+
         def solve(wf):
-            return plan.single_config_max("is", vertex_w=wf)
+            return plan.single_config_max("is", vertex_w=wf, workspace=ws)
     nbr = [set() for _ in range(n)]
     for a, b in e.tolist():
         nbr[a].add(b)
@@ -138,22 +146,30 @@ def single_config_max_k(plan, k: int = 1, vertex_w=None, solve=None) -> list:
             return None
         return int(val) - big * len(f1), cfg
 
-    out, heap, tick = [], [], 0
-    first = best(frozenset(), frozenset())
-    if first is not None:
-        heap.append((-first[0], tick, first[1], frozenset(), frozenset()))
+    # heap entries (-bound, tick, cfg, f1, f0): cfg None marks a subspace not
+    # solved yet, whose bound is its parent's weight (no set of a subspace
+    # outweighs the best of the subspace containing it); it is solved when
+    # it reaches the top and goes back in with its own weight
+    out, heap, tick = [], [(0, 0, None, frozenset(), frozenset())], 0
     while heap and len(out) < k:
         negv, _, cfg, f1, f0 = heapq.heappop(heap)
+        if cfg is None:
+            r = best(f1, f0)
+            if r is not None:
+                tick += 1
+                heapq.heappush(heap, (-r[0], tick, r[1], f1, f0))
+            continue
         out.append((-negv, cfg))
         in_, out_ = set(f1), set(f0)
         for v in range(n):
             if v in f1 or v in f0:
                 continue
             # the subspace agreeing with cfg before v and differing at v
-            f1n, f0n = (frozenset(in_), frozenset(out_ | {v})) if cfg[v] else (frozenset(in_ | {v}), frozenset(out_))
-            r = best(f1n, f0n)
-            if r is not None:
+            if not cfg[v] and nbr[v] & in_:
+                pass                                    # v cannot join: the subspace is empty
+            else:
+                f1n, f0n = (frozenset(in_), frozenset(out_ | {v})) if cfg[v] else (frozenset(in_ | {v}), frozenset(out_))
                 tick += 1
-                heapq.heappush(heap, (-r[0], tick, r[1], f1n, f0n))
+                heapq.heappush(heap, (negv, tick, None, f1n, f0n))
             (in_ if cfg[v] else out_).add(v)
     return out

@@ -87,6 +87,44 @@ def test_all_sets_of_a_small_graph():
     _check(n, e, res, 100, None)
 
 
+def test_default_pass_reuses_one_workspace(monkeypatch):
+    """Without `solve`, every subspace goes through Plan.single_config_max
+    with one workspace sized by tn_single_config_workspace_bytes (the GPU
+    call replaced here by brute force)."""
+    torch = pytest.importorskip("torch")
+    n, e = g.petersen()
+    brute = _brute_solver(n, e)
+    sizes, seen = [], []
+    monkeypatch.setattr(tn, "tn_single_config_workspace_bytes", lambda h: sizes.append(h) or 4096)
+    monkeypatch.setattr(torch, "empty", lambda *a, **kw: ("ws", a, kw.get("device")))
+
+    class FakePlan(_Graph):
+        handle = "plan-handle"
+
+        def single_config_max(self, problem, vertex_w=None, workspace=None):
+            assert problem == "is"
+            seen.append(workspace)
+            return brute(vertex_w)
+
+    res = P.single_config_max_k(FakePlan(n, e), 3)
+    assert sizes == ["plan-handle"] and all(s == ("ws", (4096,), "cuda") for s in seen)
+    _check(n, e, res, 3, None)
+
+
+def test_lazy_subspaces_take_few_passes():
+    """Subspaces are solved only when their bound reaches the top: the 5
+    maximum sets of the Petersen graph take far fewer than 5 n passes."""
+    n, e = g.petersen()
+    brute, calls = _brute_solver(n, e), []
+
+    def counted(wf):
+        calls.append(1)
+        return brute(wf)
+    res = P.single_config_max_k(_Graph(n, e), 5, solve=counted)
+    assert [v for v, _ in res] == [4] * 5
+    assert len(calls) < 5 * n
+
+
 def test_rejects_weights_too_large_to_force():
     n, e = g.path(4)
     with pytest.raises(ValueError):
