@@ -127,10 +127,10 @@ def load_peaks():
         return {}
 
 
-# Instruction-issue peaks of the 152-SM GB300 used as roofline denominators
-# (see the kernel table in the design notes): one (max,+) multiply-add is one
-# VIADDMNMX, issued at 64 per clock per SM (measured by a register-only
-# microbenchmark of __viaddmax_s32: 19.9 Tops/s at 2.07 GHz).
+# Instruction-issue bound of the 152-SM GB300, reported beside the measured
+# denominators: one (max,+) multiply-add is one __viaddmax_s32, issued at 64 per
+# clock per SM (a register-only microbenchmark of __viaddmax_s32 reached 19.9
+# Tops/s at 2.07 GHz).
 SMS = 152
 MAXPLUS_PER_CLK_SM = 64
 

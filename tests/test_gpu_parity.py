@@ -351,7 +351,7 @@ def test_config4_kings_subgraph_20_vs_oracle():
     """20 x 20 King's subgraph at filling 0.8 (seed 1, ~324 vertices): tropical
     int32, counting tropical and the count modulo four 31-bit primes against
     the oracle on its own greedy order; CRT of 4 residues is the count modulo
-    their product (the count itself needs 6 primes, see the design notes)."""
+    their product (the count itself exceeds that product; six primes hold it)."""
     n, e = g.kings_subgraph(20, 0.8, 1)
     primes = tn.PRIMES31[:4]
     oo = O.greedy_order(n, e, nrepeat=3, seed=1)
