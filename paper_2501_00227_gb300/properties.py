@@ -92,26 +92,65 @@ def log_partition_function(plan, beta: float, edge_w=None, vertex_w=None, histog
 
 # --------------------------------------------------------------------------- k best configurations
 
+def _k_best(n: int, k: int, sub) -> list:
+    """Lawler's partition of the configurations of n binary variables: the
+    best configuration x of a subspace (variables forced to 1 in F1, to 0
+    in F0) splits the rest of that subspace into disjoint subspaces, one per
+    free variable v_i in index order, each agreeing with x on v_1 .. v_{i-1}
+    and differing on v_i.  sub(F1, F0) -> (score, config) or None (empty
+    subspace) gives a subspace's best.  A subspace waits in the heap with its
+    parent's score as a bound (none of its configurations beats the best of
+    the subspace containing it) and is solved only when it reaches the top,
+    so k configurations take about k passes when many share the top scores,
+    at most k n.  Returns the k best [(score, config)], score non-increasing."""
+    import heapq
+    # entries (-bound, tick, cfg, f1, f0); cfg None: not solved yet
+    out, heap, tick = [], [(0, 0, None, frozenset(), frozenset())], 0
+    while heap and len(out) < k:
+        negv, _, cfg, f1, f0 = heapq.heappop(heap)
+        if cfg is None:
+            r = sub(f1, f0)
+            if r is not None:
+                tick += 1
+                heapq.heappush(heap, (-r[0], tick, r[1], f1, f0))
+            continue
+        out.append((-negv, cfg))
+        in_, out_ = set(f1), set(f0)
+        for v in range(n):
+            if v in f1 or v in f0:
+                continue
+            f1n, f0n = (frozenset(in_), frozenset(out_ | {v})) if cfg[v] else (frozenset(in_ | {v}), frozenset(out_))
+            tick += 1
+            heapq.heappush(heap, (negv, tick, None, f1n, f0n))
+            (in_ if cfg[v] else out_).add(v)
+    return out
+
+
+def _workspace_solver(plan, problem):
+    """solve(edge_w, vertex_w) -> (max, config) through Plan.single_config_max
+    with one workspace for every pass."""
+    import torch
+
+    from . import tn
+    ws = torch.empty(tn.tn_single_config_workspace_bytes(plan.handle), dtype=torch.uint8, device="cuda")
+
+    def solve(edge_w, vertex_w):
+        return plan.single_config_max(problem, edge_w=edge_w, vertex_w=vertex_w, workspace=ws)
+    return solve
+
+
 def single_config_max_k(plan, k: int = 1, vertex_w=None, solve=None) -> list:
     """SingleConfigMax(k) of Sec. 5.3: k distinct independent sets whose
     total weights (sizes with vertex_w None) are the k largest over all
     independent sets, ties in any order, as [(weight, config)] by
     non-increasing weight (fewer if the graph has fewer sets).
 
-    Lawler's partition of the solution space: the best set x of a subspace
-    (vertices forced in F1, forced out F0) splits the rest of that subspace
-    into disjoint subspaces, one per free vertex v_i in index order, each
-    agreeing with x on v_1 .. v_{i-1} and differing on v_i; the best of
-    every open subspace waits in a heap.  A subspace's best set comes from
-    one optimal-configuration pass on the GPU (Plan.single_config_max, or
-    `solve(weights) -> (max, config)`): with B = 2 sum|w| + 1, vertices of
-    F1 weigh w + B and those of F0 w - B, so every optimum avoids F0 and
-    holds all of F1 when F1 is independent; its weight is max - B |F1|.
-    Subspaces are solved only when their bound (the parent's weight)
-    reaches the top of the heap, so k sets take far fewer than k n passes
-    when many sets share the top weights."""
-    import heapq
-
+    Lawler's partition (_k_best) over the vertices' 0/1 values.  A
+    subspace's best set comes from one optimal-configuration pass on the
+    GPU (Plan.single_config_max, or `solve(weights) -> (max, config)`): with
+    B = 2 sum|w| + 1, vertices of F1 weigh w + B and those of F0 w - B, so
+    every optimum avoids F0 and holds all of F1 when F1 is independent (the
+    subspace is empty otherwise); its weight is max - B |F1|."""
     import numpy as np
     n = plan.n
     e = np.asarray(plan.edges).reshape(-1, 2)
@@ -122,19 +161,16 @@ def single_config_max_k(plan, k: int = 1, vertex_w=None, solve=None) -> list:
     if int(np.abs(w).sum()) + big * n > 2 ** 28:       # the int32 max-plus path's bound on sum |w|
         raise ValueError("weights too large to force vertices in or out")
     if solve is None:
-        import torch
-
-        from . import tn
-        ws = torch.empty(tn.tn_single_config_workspace_bytes(plan.handle), dtype=torch.uint8, device="cuda")
+        gpu = _workspace_solver(plan, "is")
 
         def solve(wf):
-            return plan.single_config_max("is", vertex_w=wf, workspace=ws)
+            return gpu(None, wf)
     nbr = [set() for _ in range(n)]
     for a, b in e.tolist():
         nbr[a].add(b)
         nbr[b].add(a)
 
-    def best(f1, f0):
+    def sub(f1, f0):
         if any(nbr[v] & f1 for v in f1):
             return None
         wf = w.copy()
@@ -146,30 +182,47 @@ def single_config_max_k(plan, k: int = 1, vertex_w=None, solve=None) -> list:
             return None
         return int(val) - big * len(f1), cfg
 
-    # heap entries (-bound, tick, cfg, f1, f0): cfg None marks a subspace not
-    # solved yet, whose bound is its parent's weight (no set of a subspace
-    # outweighs the best of the subspace containing it); it is solved when
-    # it reaches the top and goes back in with its own weight
-    out, heap, tick = [], [(0, 0, None, frozenset(), frozenset())], 0
-    while heap and len(out) < k:
-        negv, _, cfg, f1, f0 = heapq.heappop(heap)
-        if cfg is None:
-            r = best(f1, f0)
-            if r is not None:
-                tick += 1
-                heapq.heappush(heap, (-r[0], tick, r[1], f1, f0))
-            continue
-        out.append((-negv, cfg))
-        in_, out_ = set(f1), set(f0)
-        for v in range(n):
-            if v in f1 or v in f0:
-                continue
-            # the subspace agreeing with cfg before v and differing at v
-            if not cfg[v] and nbr[v] & in_:
-                pass                                    # v cannot join: the subspace is empty
-            else:
-                f1n, f0n = (frozenset(in_), frozenset(out_ | {v})) if cfg[v] else (frozenset(in_ | {v}), frozenset(out_))
-                tick += 1
-                heapq.heappush(heap, (negv, tick, None, f1n, f0n))
-            (in_ if cfg[v] else out_).add(v)
-    return out
+    return _k_best(n, k, sub)
+
+
+def spin_glass_lowest_k(plan, k: int = 1, edge_w=None, vertex_w=None, solve=None) -> list:
+    """The k lowest-energy configurations of the spin glass of Eq. 1,
+    H = sum J s_i s_j + sum h s_i (couplings edge_w, None: 1; fields
+    vertex_w, None: 0), ties in any order, as [(energy, spins)] by
+    non-decreasing energy, spins in {-1, +1}.
+
+    Lawler's partition (_k_best) over the spins; a subspace's best comes
+    from one ground-state pass on the GPU (Plan.single_config_max of -H, or
+    `solve(edge_w, vertex_w) -> (max of -H, config)`, config bit 1 = spin
+    +1), spins forced through their fields: with B = sum|J| + sum|h| + 1,
+    h - B forces s = +1 and h + B forces s = -1 (a wrong forced spin costs
+    2B, more than any other change can gain).  Energies are those of the
+    original couplings and fields."""
+    import numpy as np
+    n = plan.n
+    e = np.asarray(plan.edges).reshape(-1, 2)
+    J = np.ones(len(e), dtype=np.int64) if edge_w is None else np.asarray(edge_w, dtype=np.int64).reshape(-1)
+    h = np.zeros(n, dtype=np.int64) if vertex_w is None else np.asarray(vertex_w, dtype=np.int64).reshape(-1)
+    if J.size != len(e) or h.size != n:
+        raise ValueError("edge_w needs one coupling per edge, vertex_w one field per vertex")
+    total = int(np.abs(J).sum()) + int(np.abs(h).sum())
+    big = total + 1
+    if total + big * n > 2 ** 28:                     # the int32 max-plus path's bound on sum |J| + sum |h|
+        raise ValueError("couplings and fields too large to force spins")
+    if solve is None:
+        solve = _workspace_solver(plan, "spin")
+    J32 = J.astype(np.int32)
+
+    def sub(f1, f0):
+        hf = h.copy()
+        hf[list(f1)] -= big
+        hf[list(f0)] += big
+        _, cfg = solve(J32, hf.astype(np.int32))
+        cfg = np.asarray(cfg, dtype=np.uint8)
+        if any(cfg[v] == 0 for v in f1) or any(cfg[v] == 1 for v in f0):
+            return None                                 # cannot happen with this B; kept as a check
+        sp = 2 * cfg.astype(np.int64) - 1
+        energy = int((J * sp[e[:, 0]] * sp[e[:, 1]]).sum() + (h * sp).sum()) if len(e) else int((h * sp).sum())
+        return -energy, cfg
+
+    return [(-score, 2 * cfg.astype(np.int8) - 1) for score, cfg in _k_best(n, k, sub)]

@@ -101,8 +101,8 @@ def test_default_pass_reuses_one_workspace(monkeypatch):
     class FakePlan(_Graph):
         handle = "plan-handle"
 
-        def single_config_max(self, problem, vertex_w=None, workspace=None):
-            assert problem == "is"
+        def single_config_max(self, problem, edge_w=None, vertex_w=None, workspace=None):
+            assert problem == "is" and edge_w is None
             seen.append(workspace)
             return brute(vertex_w)
 
@@ -129,6 +129,60 @@ def test_rejects_weights_too_large_to_force():
     n, e = g.path(4)
     with pytest.raises(ValueError):
         P.single_config_max_k(_Graph(n, e), 2, vertex_w=[1 << 25] * 4, solve=_brute_solver(n, e))
+
+
+def _brute_spin_solver(n, e):
+    """max over all 2^n spin configurations of -H and the lowest-index
+    configuration reaching it (bit 1 = spin +1); test stand-in, n <= 16."""
+    masks = np.arange(1 << n, dtype=np.int64)
+    sp = 2 * ((masks[:, None] >> np.arange(n)) & 1) - 1
+    e = np.asarray(e).reshape(-1, 2)
+
+    def solve(J, h):
+        neg_h = -((sp[:, e[:, 0]] * sp[:, e[:, 1]]) @ np.asarray(J, dtype=np.int64) if len(e) else 0) \
+            - sp @ np.asarray(h, dtype=np.int64)
+        i = int(np.argmax(neg_h))
+        return int(neg_h[i]), ((sp[i] + 1) // 2).astype(np.uint8)
+    return solve
+
+
+def _spin_energies(n, e, J, h):
+    """All 2^n energies, ascending (brute force via the oracle's histogram)."""
+    shift, hist = O.bruteforce_spin(n, e, J, h)
+    return [k - shift for k, c in enumerate(hist) for _ in range(c)]
+
+
+def _check_spins(n, e, res, k, J, h):
+    assert [en for en, _ in res] == _spin_energies(n, e, J, h)[:k]
+    seen = set()
+    for en, s in res:
+        assert set(np.unique(s).tolist()) <= {-1, 1}
+        assert O.spin_energy(n, e, s, J, h) == en
+        seen.add(s.tobytes())
+    assert len(seen) == len(res)
+
+
+@pytest.mark.parametrize("spec,seed,k", [("petersen", 0, 30), ("er:11:0.35:2", 1, 50), ("cycle:8", 2, 256),
+                                         ("path:5", 3, 40)])
+def test_spin_glass_lowest_energies(spec, seed, k):
+    """The k lowest energies of random +-J couplings and fields in -2..2
+    equal the bottom of the brute-force energy spectrum, each configuration
+    distinct and of the stated energy (all 2^n when k exceeds it)."""
+    n, e = g.by_name(spec)
+    J = g.random_weights(len(e), seed)
+    h = g.random_weights(n, seed + 10, (-2, -1, 0, 1, 2))
+    res = P.spin_glass_lowest_k(_Graph(n, e), k, J, h, solve=_brute_spin_solver(n, e))
+    assert len(res) == min(k, 1 << n)
+    _check_spins(n, e, res, k, J, h)
+
+
+def test_spin_glass_default_couplings():
+    """J = 1, h = 0 (an antiferromagnet): on an even cycle the two Neel
+    states are the ground states, energy -n."""
+    n, e = g.cycle(10)
+    res = P.spin_glass_lowest_k(_Graph(n, e), 3, solve=_brute_spin_solver(n, e))
+    assert [en for en, _ in res[:2]] == [-10, -10] and res[2][0] > -10
+    assert {tuple(s.tolist()) for _, s in res[:2]} == {tuple([1, -1] * 5), tuple([-1, 1] * 5)}
 
 
 def _cuda():
@@ -162,3 +216,18 @@ def test_k_best_weighted_configurations_on_gpu():
     finally:
         p.close()
     _check(n, e, res, 15, w)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("spec,seed,k", [("petersen", 0, 12), ("er:13:0.3:4", 1, 20)])
+def test_spin_glass_lowest_energies_on_gpu(spec, seed, k):
+    _cuda()
+    n, e = g.by_name(spec)
+    J = g.random_weights(len(e), seed)
+    h = g.random_weights(n, seed + 10, (-2, -1, 0, 1, 2))
+    p = tn.Plan(n, e, nrepeat=2, seed=1)
+    try:
+        res = P.spin_glass_lowest_k(p, k, J, h)
+    finally:
+        p.close()
+    _check_spins(n, e, res, k, J, h)
