@@ -185,3 +185,38 @@ def test_plan_with_annealed_slices():
         p.close()
     with pytest.raises(tn.TNError):
         tn.Plan(n, e, optimizer="treesa", treesa={"nslices": 1}, sliced=[0])
+
+
+def _replay_sliced(n, e, order, sliced):
+    """log2 (tc of all slices, sc of one, rwc of all slices) of an SSA order
+    with the labels `sliced` removed from every tensor, replayed from the
+    definitions of Sec. 4.1: a contraction's output keeps the labels that a
+    tensor outside it still carries; tc = sum 2^|A u B|, sc = max 2^|C|,
+    rwc = sum 2^|A| + 2^|B| + 2^|C|; each 2^s-fold for the slices."""
+    cut = {int(v) for v in sliced}
+    m = len(e)
+    live = {i: frozenset(int(x) for x in e[i]) - cut for i in range(m)}
+    live.update({m + v: frozenset([v]) - cut for v in range(n)})
+    nxt, tc, sc, rw = m + n, 0, 0, 0
+    for a, b in np.asarray(order).reshape(-1, 2).tolist():
+        A, B = live.pop(a), live.pop(b)
+        outside = set().union(*live.values()) if live else set()
+        C = (A | B) & outside
+        tc += 2 ** len(A | B)
+        sc = max(sc, len(C))
+        rw += 2 ** len(A) + 2 ** len(B) + 2 ** len(C)
+        live[nxt] = frozenset(C)
+        nxt += 1
+    s = len(cut)
+    return math.log2(tc) + s, float(sc), math.log2(rw) + s
+
+
+@pytest.mark.parametrize("spec,s,fixed", [("reg3:40:3", 3, ()), ("ksg:6:0.8:1", 2, (4, 9)), ("cycle:20", 1, ())])
+def test_sliced_complexities_equal_a_plain_replay(spec, s, fixed):
+    n, e = g.by_name(spec)
+    o, sl, lg = tn.tn_order_treesa_sliced(n, e, nslices=s, fixed_slices=fixed, sc_target=3.0, seed=7, ntrials=2,
+                                          niters=5)
+    assert lg == pytest.approx(_replay_sliced(n, e, o, sl), abs=1e-9)
+    # with nothing sliced the replay is the oracle's complexity
+    o0, lg0 = tn.tn_order_treesa(n, e, seed=7, ntrials=2, niters=5)
+    assert _replay_sliced(n, e, o0, []) == pytest.approx(_log2c(n, e, o0), abs=1e-9)
