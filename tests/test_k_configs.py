@@ -3,6 +3,9 @@ largest total weights, by Lawler's partition over optimal-configuration
 passes.  The partition logic is checked on the CPU with a brute-force
 solver in its place; the GPU tests run it on the single-configuration pass
 and compare the weights with the oracle's polynomial / weight histogram."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -60,6 +63,26 @@ def test_petersen_two_best_printed():
     res = P.single_config_max_k(_Graph(n, e), 2, solve=_brute_solver(n, e))
     assert [v for v, _ in res] == [4, 4]
     _check(n, e, res, 2, None)
+
+
+def _printed_configs():
+    with open(os.path.join(os.path.dirname(__file__), "golden", "petersen.json")) as f:
+        gd = json.load(f)
+    return [np.array([int(c) for c in s], dtype=np.uint8) for s in [gd["single_config_max"]] + gd["single_config_max_2"]]
+
+
+def test_printed_petersen_configurations_are_among_the_five_maximum_sets():
+    """The configurations Sec. 5.3 prints for SingleConfigMax() and
+    SingleConfigMax(2) are maximum independent sets of the Petersen graph
+    (with its vertices numbered as the paper's); the partition enumerates
+    all five maximum sets, those three among them."""
+    n, e = g.petersen()
+    res = P.single_config_max_k(_Graph(n, e), 5, solve=_brute_solver(n, e))
+    assert [v for v, _ in res] == [4] * 5
+    got = {cfg.tobytes() for _, cfg in res}
+    for cfg in _printed_configs():
+        assert all(not (cfg[a] and cfg[b]) for a, b in e.tolist()) and cfg.sum() == 4
+        assert cfg.tobytes() in got
 
 
 @pytest.mark.parametrize("spec,k", [("petersen", 12), ("er:12:0.3:2", 40), ("cycle:9", 7), ("path:3", 10),
@@ -203,6 +226,20 @@ def test_k_best_configurations_on_gpu(spec, k):
     finally:
         p.close()
     _check(n, e, res, k, None)
+
+
+@pytest.mark.gpu
+def test_printed_petersen_configurations_on_gpu():
+    _cuda()
+    n, e = g.petersen()
+    p = tn.Plan(n, e, nrepeat=2, seed=1)
+    try:
+        res = P.single_config_max_k(p, 5)
+    finally:
+        p.close()
+    assert [v for v, _ in res] == [4] * 5
+    got = {cfg.tobytes() for _, cfg in res}
+    assert all(cfg.tobytes() in got for cfg in _printed_configs())
 
 
 @pytest.mark.gpu
