@@ -382,6 +382,17 @@ int tn_contract_sliced(tn_plan_t plan, tn_semiring_t semiring, int32_t problem, 
 int tn_result_combine(tn_semiring_t semiring, const tn_result_t *a, const tn_result_t *b, tn_result_t *out);
 int tn_sliced_workspace_bytes(tn_plan_t plan, tn_semiring_t semiring, int32_t nslots, int32_t batch, uint64_t *out);
 
+/* Limit of the executor's dependency waits (no counterpart in the paper).
+ * Every task of a contraction waits, bounded, for the steps it reads; a wait
+ * that runs past the limit gives up, the launch stops claiming tasks and
+ * every CTA returns, and the result's status is TN_ETIMEOUT (the workspace
+ * is reset by the next launch, so the context stays usable).  ns: the limit
+ * for every launch enqueued after this call, at most 60 s; 0 restores the
+ * default of 2 s.  Process-wide; CUDA graphs keep the limit they were
+ * captured with.  TN_EINVAL above 60 s.  Tests shorten it to make a wait run
+ * out without any fault. */
+int tn_set_wait_timeout_ns(uint64_t ns);
+
 /* Register-only throughput of the contraction kernels' inner arithmetic,
  * the denominators of their ALU rooflines (no counterpart in the paper):
  * kind 0 = (max,+) int32 multiply-adds (one __viaddmax_s32 each), kind 1 =

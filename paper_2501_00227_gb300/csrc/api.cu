@@ -318,7 +318,8 @@ int tn_contract(tn_plan_t plan, tn_semiring_t semiring, const uint32_t* primes, 
   if (rc) return rc;
   rc = cuda_rc(cudaStreamSynchronize(st));
   if (rc) return rc;
-  return tn_result_decode(semiring, primes, nprimes, raw, out);
+  rc = tn_result_decode(semiring, primes, nprimes, raw, out);
+  return rc ? rc : out->status == TN_ETIMEOUT ? TN_ETIMEOUT : TN_OK;
 }
 
 int tn_contract_timed(tn_plan_t plan, tn_semiring_t semiring, const uint32_t* primes,

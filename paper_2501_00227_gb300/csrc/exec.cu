@@ -9,6 +9,7 @@
 // written during the launch are read through L2 only (ld.global.cg).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <type_traits>
 
@@ -739,6 +740,11 @@ int exec_enqueue(tn_plan_s* p, tn_semiring_t s, const void* mods_v, int32_t npri
   return exec_launch_core(X, s, mods_v, ws, stream, d_raw, d_trace, X->d_tables);
 }
 
+// Limit of every dependency wait of the launches that follow (ns); see
+// tn_set_wait_timeout_ns.
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;  // 2 s
+std::atomic<unsigned long long> g_wait_timeout_ns{kDefaultWaitNs};
+
 int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods_v, void* ws, void* stream, void* d_raw,
                      void* d_trace, const void* d_tables) {
   const dev::ModTable& mods = *static_cast<const dev::ModTable*>(mods_v);
@@ -770,7 +776,7 @@ int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods_v, void* ws,
   a.raw = static_cast<unsigned char*>(d_raw);
   a.mods = mods;
   a.semiring = s;
-  a.timeout_ns = 2000000000ull;  // 2 s per wait
+  a.timeout_ns = g_wait_timeout_ns.load(std::memory_order_relaxed);
   a.trace = static_cast<unsigned long long*>(d_trace);
   a.nraw = X->nraw;
   switch (s) {
@@ -787,3 +793,9 @@ int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods_v, void* ws,
 }
 
 }  // namespace tn
+
+extern "C" int tn_set_wait_timeout_ns(uint64_t ns) {
+  if (ns > 60000000000ull) return TN_EINVAL;
+  tn::g_wait_timeout_ns.store(ns ? ns : tn::kDefaultWaitNs, std::memory_order_relaxed);
+  return TN_OK;
+}

@@ -110,6 +110,7 @@ def lib():
                                       ctypes.POINTER(ctypes.c_double)]
         L.tn_order_treesa_sliced.argtypes = [i32, i32p, i32, ctypes.POINTER(tn_treesa_params_t), i32, i32p, i32,
                                              i32p, i32p, ctypes.POINTER(ctypes.c_double)]
+        L.tn_set_wait_timeout_ns.argtypes = [u64]
         L.tn_slice_labels.argtypes = [i32, i32p, i32, i32p, i32, i32, i32p, ctypes.POINTER(ctypes.c_double)]
         L.tn_plan_sliced.argtypes = [i32, i32p, i32, i32p, i32, i32p, i32, ctypes.POINTER(vp)]
         L.tn_contract_sliced.argtypes = [vp, ctypes.c_int, i32, i32p, i32p, u32p, u32p, i32, u64, u64, vp,
@@ -441,6 +442,12 @@ def tn_order_treesa_sliced(n, edges, *, nslices: int = 0, fixed_slices=(), sc_ta
                                         _p32(fx) if fx.size else None, fx.size, _p32(order), _p32(sl), lg),
            "tn_order_treesa_sliced")
     return order, sl[: fx.size + int(nslices)], tuple(float(x) for x in lg)
+
+
+def tn_set_wait_timeout_ns(ns: int):
+    """Limit of the executor's dependency waits for the launches that follow
+    (0: the default, 2 s)."""
+    _check(lib().tn_set_wait_timeout_ns(int(ns)), "tn_set_wait_timeout_ns")
 
 
 def tn_slice_labels(n, edges, order, nslices: int):

@@ -224,3 +224,19 @@ def test_alu_peaks_are_plausible():
     md = tn.tn_alu_peak("modp")
     assert 0.3 * sms * 64 * 1.0e9 / 1e12 < mp < 1.2 * sms * 64 * 2.2e9 / 1e12
     assert 0 < md < mp
+
+
+@pytest.mark.parametrize("ns,ok", [(0, True), (1, True), (2_000_000_000, True), (60_000_000_000, True),
+                                   (60_000_000_001, False), (2 ** 64 - 1, False)])
+def test_wait_timeout_setting_bounds(ns, ok):
+    """The executor's wait limit takes 0 (the default) .. 60 s; the setting is
+    restored to the default afterwards."""
+    try:
+        if ok:
+            tn.tn_set_wait_timeout_ns(ns)
+        else:
+            with pytest.raises(tn.TNError) as ei:
+                tn.tn_set_wait_timeout_ns(ns)
+            assert ei.value.code == tn.TN_EINVAL
+    finally:
+        tn.tn_set_wait_timeout_ns(0)
