@@ -268,3 +268,22 @@ def test_spin_glass_lowest_energies_on_gpu(spec, seed, k):
     finally:
         p.close()
     _check_spins(n, e, res, k, J, h)
+
+
+@pytest.mark.gpu
+def test_buckyball_lowest_energies_on_gpu():
+    """Sec. 6.4 prints the Buckyball's ground-state energy -66 with
+    degeneracy 16000: its four lowest-energy configurations are distinct
+    ground states."""
+    _cuda()
+    with open(os.path.join(os.path.dirname(__file__), "golden", "spin_glass.json")) as f:
+        gd = json.load(f)["buckyball"]
+    n, e = g.fullerene()
+    p = tn.Plan(n, e, nrepeat=4, seed=1)
+    try:
+        res = P.spin_glass_lowest_k(p, 4)
+    finally:
+        p.close()
+    assert [en for en, _ in res] == [gd["ground_energy"]] * 4
+    assert len({s.tobytes() for _, s in res}) == 4
+    assert all(O.spin_energy(n, e, s) == gd["ground_energy"] for _, s in res)
