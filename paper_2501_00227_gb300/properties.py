@@ -143,7 +143,8 @@ def single_config_max_k(plan, k: int = 1, vertex_w=None, solve=None) -> list:
     """SingleConfigMax(k) of Sec. 5.3: k distinct independent sets whose
     total weights (sizes with vertex_w None) are the k largest over all
     independent sets, ties in any order, as [(weight, config)] by
-    non-increasing weight (fewer if the graph has fewer sets).
+    non-increasing weight (fewer if the graph has fewer sets).  plan: an
+    unsliced Plan (the optimal-configuration pass needs every intermediate).
 
     Lawler's partition (_k_best) over the vertices' 0/1 values.  A
     subspace's best set comes from one optimal-configuration pass on the
@@ -189,7 +190,7 @@ def spin_glass_lowest_k(plan, k: int = 1, edge_w=None, vertex_w=None, solve=None
     """The k lowest-energy configurations of the spin glass of Eq. 1,
     H = sum J s_i s_j + sum h s_i (couplings edge_w, None: 1; fields
     vertex_w, None: 0), ties in any order, as [(energy, spins)] by
-    non-decreasing energy, spins in {-1, +1}.
+    non-decreasing energy, spins in {-1, +1}.  plan: an unsliced Plan.
 
     Lawler's partition (_k_best) over the spins; a subspace's best comes
     from one ground-state pass on the GPU (Plan.single_config_max of -H, or
