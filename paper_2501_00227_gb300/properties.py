@@ -23,8 +23,9 @@ forced in or out through their weights.
 
 For the spin glass of Eq. 1: the ground state (CountingMin) from the
 counting contraction of -H, the exact energy histogram from
-``Plan.weighted_polynomial``, and ln Z(beta) (PartitionFunction) summed from
-that histogram.
+``Plan.weighted_polynomial``, the k lowest energies with their counts
+(CountingMin(k)) and ln Z(beta) (PartitionFunction) read off that
+histogram, and the k lowest-energy configurations (spin_glass_lowest_k).
 """
 from __future__ import annotations
 
@@ -77,6 +78,16 @@ def energy_histogram(plan, edge_w=None, vertex_w=None) -> tuple:
     sj = m if edge_w is None else int(np.abs(np.asarray(edge_w, dtype=np.int64)).sum())
     sh = 0 if vertex_w is None else int(np.abs(np.asarray(vertex_w, dtype=np.int64)).sum())
     return sj + sh, plan.weighted_polynomial("spin", edge_w, vertex_w)
+
+
+def counting_min(plan, k: int = 1, edge_w=None, vertex_w=None, histogram=None) -> dict:
+    """{energy: number of configurations} for the k lowest energies that
+    occur (CountingMin(k) of Sec. 5.3 for the spin glass of Eq. 1), read off
+    the exact energy histogram (energy_histogram, or `histogram` = (shift,
+    c) as it returns).  k = 1 is the ground state and its degeneracy."""
+    shift, c = histogram if histogram is not None else energy_histogram(plan, edge_w, vertex_w)
+    levels = [i for i, v in enumerate(c) if v][:k]
+    return {i - shift: c[i] for i in levels}
 
 
 def log_partition_function(plan, beta: float, edge_w=None, vertex_w=None, histogram=None) -> float:

@@ -66,6 +66,29 @@ def test_weighted_workspace_covers_the_plain_one():
         p.close()
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_counting_min_from_the_histogram(seed):
+    """CountingMin(k) read off an energy histogram: the k lowest energies
+    with their multiplicities, the first the counting contraction's ground
+    state (host logic, histogram by brute force)."""
+    n, e = g.erdos_renyi(12, 0.3, 30 + seed)
+    J = g.random_weights(len(e), seed, (-2, -1, 1, 2))
+    h = g.random_weights(n, seed + 5, (-1, 0, 1))
+    shift, hist = O.bruteforce_spin(n, e, J, h)
+    energies = sorted(O.spin_energy(n, e, [1 if (m >> i) & 1 else -1 for i in range(n)], J, h)
+                      for m in range(1 << n))
+    for k in (1, 3, 1000):
+        got = P.counting_min(None, k, histogram=(shift, hist))
+        want = {}
+        for en in energies:
+            if en in want or len(want) < k:
+                want[en] = want.get(en, 0) + 1
+        assert got == want
+    o = O.greedy_order(n, e, nrepeat=2, seed=1)
+    top, cnt = O.weighted_contract("counting", "spin", n, e, o, J, h)
+    assert P.counting_min(None, 1, histogram=(shift, hist)) == {-top: cnt}
+
+
 # ------------------------------------------------------------------ GPU parity
 
 @pytest.mark.gpu
@@ -81,6 +104,7 @@ def test_buckyball_printed_values_gpu():
         shift, c = P.energy_histogram(p)
         assert sum(c) == 2 ** n and c[gd["ground_energy"] + shift] == gd["ground_degeneracy"]
         assert c == O.weighted_polynomial("spin", n, e, o, tn.PRIMES31[:2], 2 * shift)
+        assert P.counting_min(p, 1, histogram=(shift, c)) == {gd["ground_energy"]: gd["ground_degeneracy"]}
         lz = P.log_partition_function(p, 1.0, histogram=(shift, c)) / n
         assert lz == pytest.approx(gd["log_z_per_site_beta1"], rel=1e-13, abs=0)
     finally:
