@@ -199,7 +199,10 @@ int tn_contract(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *primes, 
 /* As tn_contract, without waiting: enqueues the contraction and a copy of
  * the raw scalar into d_raw (TN_RAW_BYTES bytes of caller device memory).
  * Decode it later (after the stream is done and the bytes are on the host)
- * with tn_result_decode. */
+ * with tn_result_decode, which returns TN_OK for any finished launch and
+ * puts the launch's outcome in out->status: TN_ETIMEOUT when a device wait
+ * gave up (the values are then meaningless), TN_EOVERFLOW when a count
+ * saturated. */
 #define TN_RAW_BYTES 128
 int tn_contract_async(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *primes, int32_t nprimes,
                       void *d_workspace, size_t ws_bytes, void *cuda_stream, void *d_raw);
