@@ -102,6 +102,22 @@ def test_partition_with_weights(seed):
     _check(n, e, res, 25, w)
 
 
+def test_partition_with_negative_weights():
+    """Negative weights: the forcing still holds (B > 2 sum|w|), and the k
+    best weights match a direct enumeration of every independent set."""
+    n, e = g.erdos_renyi(11, 0.3, 91)
+    w = g.random_weights(n, 4, (-3, -1, 0, 2, 4))
+    res = P.single_config_max_k(_Graph(n, e), 40, vertex_w=w, solve=_brute_solver(n, e))
+    ee = np.asarray(e).reshape(-1, 2)
+    weights = sorted((sum(int(w[v]) for v in range(n) if (m >> v) & 1) for m in range(1 << n)
+                      if all(not ((m >> a) & 1 and (m >> b) & 1) for a, b in ee.tolist())), reverse=True)
+    assert [v for v, _ in res] == weights[:40]
+    assert len({cfg.tobytes() for _, cfg in res}) == 40
+    for v, cfg in res:
+        assert int(np.asarray(w, dtype=np.int64) @ cfg.astype(np.int64)) == v
+        assert all(not (cfg[a] and cfg[b]) for a, b in ee.tolist())
+
+
 def test_all_sets_of_a_small_graph():
     """k beyond the number of sets enumerates every independent set once."""
     n, e = g.cycle(6)
