@@ -62,9 +62,15 @@ class tn_result_t(ctypes.Structure):
 
 
 class TNError(RuntimeError):
-    def __init__(self, code, what=""):
+    def __init__(self, code, what="", detail=None):
+        """detail: the message, when the library cannot describe the code
+        (it is not loaded); otherwise tn_strerror's text is used."""
         self.code = code
-        super().__init__(f"{what}: {tn_strerror(code)} ({code})" if what else f"{code}")
+        if detail is not None:
+            msg = f"{what}: {detail} ({code})"
+        else:
+            msg = f"{what}: {tn_strerror(code)} ({code})" if what else f"{code}"
+        super().__init__(msg)
 
 
 _lib = None
@@ -83,7 +89,8 @@ def lib():
             return _lib
         path = library_path()
         if not os.path.exists(path):
-            raise TNError(TN_EINVAL, f"libtn.so not built at {path}; run paper_2501_00227_gb300.build.build()")
+            # no tn_strerror here: it would call lib() under the held lock
+            raise TNError(TN_EINVAL, "libtn.so", f"not built at {path}; run paper_2501_00227_gb300.build.build()")
         L = ctypes.CDLL(path)
         vp, i32, u32, u64, i32p, u32p = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64,
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint32))

@@ -240,3 +240,17 @@ def test_wait_timeout_setting_bounds(ns, ok):
             assert ei.value.code == tn.TN_EINVAL
     finally:
         tn.tn_set_wait_timeout_ns(0)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library every entry point raises; nothing falls
+    back to another implementation."""
+    monkeypatch.setattr(tn, "_lib", None)
+    monkeypatch.setattr(tn, "library_path", lambda: str(tmp_path / "libtn.so"))
+    n, e = g.petersen()
+    with pytest.raises(tn.TNError, match="not built"):
+        tn.lib()
+    with pytest.raises(tn.TNError, match="not built"):
+        tn.Plan(n, e)
+    with pytest.raises(tn.TNError, match="not built"):
+        tn.tn_order_treesa(n, e)
