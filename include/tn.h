@@ -125,7 +125,10 @@ typedef struct {
 /* Build a plan from a graph and a complete SSA order (order_len = number of
  * steps = n + m - 1).  Host only; validates graph and order (TN_EINVAL).
  * The plan holds the per-step label classes, the kernel chosen for each
- * step and the offsets of every intermediate in the workspace. */
+ * step and the offsets of every intermediate in the workspace.  Every tensor
+ * of the order has rank <= 30 (2^30 entries) and every step at most 60
+ * labels in all, else TN_EINVAL: an order with a larger intermediate needs
+ * slicing (tn_plan_sliced) or a better order. */
 int tn_plan(int32_t n_vertices, const int32_t *edges, int32_t m,
             const int32_t *order, int32_t order_len, tn_plan_t *out);
 
