@@ -13,8 +13,9 @@ Metric: semiring-contraction Gop/s = sum over contractions of tc (Sec. 4.1:
 divided by device time.  L2 is flushed (a 256 MiB write) before every timed
 step, outside the timed events.
 
---impl reference times the CPU oracle (plain C loops, all host cores) on a
-bounded sample of the same workload.
+--impl reference times the CPU oracle (plain C loops, all host cores) on the
+same six graphs with the same orders (one whole headline step per step), and
+once on a single thread over a bounded sample.
 """
 from __future__ import annotations
 
@@ -127,23 +128,45 @@ def load_peaks():
         return {}
 
 
-# Instruction-issue bound of the 152-SM GB300, reported beside the measured
-# denominators: one (max,+) multiply-add is one __viaddmax_s32, issued at 64 per
-# clock per SM (a register-only microbenchmark of __viaddmax_s32 reached 19.9
-# Tops/s at 2.07 GHz).
+# The int32 roofline of every executor instantiation: the instruction-issue
+# bound of the 152-SM GB300 for int32 ALU instructions (64 per clock per SM;
+# one (max,+) multiply-add is one __viaddmax_s32) at the maximum SM clock,
+# or the register-only __viaddmax_s32 microbenchmark (tn_alu_peak), whichever
+# is higher.  The microbenchmark spends 1 of 17 instructions on varying its
+# operand and reached 17.9 Tops/s at 2.07 GHz, below the 20.1 Tops/s bound.
 SMS = 152
-MAXPLUS_PER_CLK_SM = 64
+INT32_PER_CLK_SM = 64
+
+# Thread instructions per semiring multiply-add of each executor (warp
+# instructions executed x 32 / (tc x primes)), from the ncu captures kept
+# under profiles/ (one launch on random 3-regular n = 140).
+INSTR_PER_OP = {
+    "tropical_i32": {"value": None, "profile": None},
+    "counting": {"value": 18.6, "profile": "profiles/k_exec_counting_reg3_n140_s3.md"},
+    "modp": {"value": 118.0e6 * 32 / 5.1e8, "profile": "profiles/k_exec_modp_reg3_n140.md"},
+}
 
 
-def cpu_reference(sample_graphs, threads: int):
-    """Times the CPU oracle on the given graphs in every element type."""
+def headline_orders():
+    """The headline graphs with the contraction orders the GPU arm uses (the
+    library's greedy order, nrepeat 10, seed 1; host code only, no GPU)."""
+    from paper_2501_00227_gb300 import tn
+    out = []
+    for kind, n, seed in GRAPHS:
+        nn, e = graphgen.random_regular3(n, seed)
+        out.append((f"reg3:{n}:{seed}", nn, e, tn.tn_order_greedy(nn, e, 0.0, 10, 1)))
+    return out
+
+
+def cpu_reference(graphs, threads: int):
+    """Times the CPU oracle over (name, n, edges, order) graphs in the three
+    element types of the headline (tropical, counting, 3 primes): returns
+    (semiring multiply-adds, seconds, threads used)."""
     import oracle
     oracle.build()
     used = oracle.set_threads(threads)
     ops, secs = 0, 0.0
-    for kind, n, seed in sample_graphs:
-        nn, e = graphgen.random_regular3(n, seed)
-        order = oracle.greedy_order(nn, e, nrepeat=4, seed=1)
+    for _, nn, e, order in graphs:
         tc = oracle.complexity(nn, e, order)[0]
         t = time.perf_counter()
         oracle.mis_size(nn, e, order)
@@ -154,29 +177,43 @@ def cpu_reference(sample_graphs, threads: int):
     return ops, secs, used
 
 
+def cpu_single_thread_sample(graphs):
+    """The oracle on one thread over a bounded sample of the headline: the
+    three n = 100 graphs and the n = 140 seed 1 graph (same orders)."""
+    sample = [g for g in graphs if g[0].startswith("reg3:100:")] + [g for g in graphs if g[0] == "reg3:140:1"]
+    ops, secs, used = cpu_reference(sample, 1)
+    return {"value": ops / secs / 1e9, "unit": "Gop/s", "cores": used, "seconds": secs,
+            "sample": "reg3 n=100 seeds 1-3 and n=140 seed 1, the GPU arm's orders, tropical + counting + 3 "
+                      "primes"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    sample = [("reg3", 140, 1)]
+    graphs = headline_orders()
     threads = os.cpu_count() or 1
     for _ in range(args.warmup):
-        cpu_reference(sample, threads)
+        cpu_reference(graphs, threads)
     ops = secs = 0.0
     used = threads
     for _ in range(args.steps):
-        o, s, used = cpu_reference(sample, threads)
+        o, s, used = cpu_reference(graphs, threads)
         ops += o
         secs += s
     val = ops / secs / 1e9
+    single = cpu_single_thread_sample(graphs)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gop/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
-            "config": {"workload": "random 3-regular n=140 seed 1 (bounded sample of the n=100/140 workload)",
-                       "semirings": ["tropical", "counting", "mod 3 primes"], "order": "oracle greedy"},
+            "config": {"workload": "random 3-regular n=100 and n=140, seeds 1-3, greedy order (nrepeat 10)",
+                       "semirings": ["tropical", "counting", "mod 3 primes"],
+                       "order": "the GPU arm's orders (library greedy, nrepeat 10, seed 1), computed before timing"},
             "cpu_baseline": {"value": val, "unit": "Gop/s", "cores": used, "kind": "oracle",
-                             "sample": "reg3 n=140 seed 1, tropical + counting + 3 primes, per step"},
+                             "sample": "the whole headline step (six graphs x tropical + counting + 3 primes) on "
+                                       "all cores, every step",
+                             "single_thread": single},
             "e2e": {"value": val, "unit": "Gop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -785,23 +822,23 @@ def run_tn(args):
 
     csum = clk.summary()
     clock_mhz = csum["sm_max_mhz"] or 2070.0
-    peak_ops = SMS * MAXPLUS_PER_CLK_SM * clock_mhz * 1e6 / 1e12   # Tops/s, (max,+) issue bound
-    # each kernel against its own inner step: (max,+) for tropical and for
-    # counting (its first pass; the count pass only adds work), the folded
-    # 64-bit multiply-add for mod p
-    kpeak = {"tropical_i32": alu["maxplus"], "counting": alu["maxplus"], "modp": alu["modp"]}
+    issue_peak = SMS * INT32_PER_CLK_SM * clock_mhz * 1e6 / 1e12   # Tops/s, int32 issue bound
+    peak = max(issue_peak, alu["maxplus"])
     achieved = dom_ops / (dom_ms * 1e-3) / 1e12
     per_tops = {k: v[1] / (v[0] * 1e-3) / 1e12 for k, v in per.items()}
-    roofline = {"bound": "alu", "kernel": f"k_exec<{dom_sr}>", "achieved": achieved, "peak": kpeak[dom_sr],
-                "unit": "Tops/s", "frac": achieved / kpeak[dom_sr], "traffic": None,
-                "peak_basis": "register-only rate of the kernel's inner step on this GPU (tn_alu_peak, measured "
-                              "in this run before timing)",
-                "alu_peaks_measured": alu,
-                "maxplus_issue_peak": {"value": peak_ops, "basis": f"{SMS} SMs x {MAXPLUS_PER_CLK_SM} (max,+)/clk/SM "
-                                                                     f"x {clock_mhz:.0f} MHz"},
+    roofline = {"bound": "alu", "kernel": f"k_exec<{dom_sr}>", "achieved": achieved, "peak": peak,
+                "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                "peak_basis": f"int32 issue bound: {SMS} SMs x {INT32_PER_CLK_SM} int32 instr/clk/SM x "
+                              f"{clock_mhz:.0f} MHz (max SM clock) = {issue_peak:.2f} Tops/s, or the "
+                              f"register-only __viaddmax_s32 rate {alu['maxplus']:.2f} Tops/s measured in this "
+                              "run, whichever is higher; one semiring multiply-add per op (tc)",
                 "time_share": dom_ms / sum(v[0] for v in per.values()), "launches": dom_n,
                 "per_semiring_tops": per_tops,
-                "per_semiring_frac": {k: per_tops[k] / kpeak[k] for k in per_tops}}
+                "per_semiring_frac": {k: per_tops[k] / peak for k in per_tops},
+                "instr_per_op": INSTR_PER_OP,
+                "inner_step_rates": {"unit": "Tops/s", "maxplus": alu["maxplus"], "modp_fold3": alu["modp"],
+                                     "note": "register-only rates of each kernel's inner step (tn_alu_peak); "
+                                             "context, not the denominator"}}
 
     line = {"metric": METRIC, "value": value, "unit": "Gop/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -817,7 +854,7 @@ def run_tn(args):
     # one executor launch per contraction
     line["gpu_launches"] = args.steps * len(jobs)
     if rank == 0 and not args.no_extras:
-        line["largest_tropical"] = largest_bench(tn, torch, peak_ops, autotune=not args.no_autotune)
+        line["largest_tropical"] = largest_bench(tn, torch, peak, autotune=not args.no_autotune)
         line["modp_tensor_core_ablation"] = limb_ablation_bench(tn, torch)
         line["independence_polynomial"] = polynomial_bench(tn, torch, plans, cpu=not args.no_cpu_baseline)
         line["weighted"] = weighted_bench(tn, torch, plans, cpu=not args.no_cpu_baseline)
@@ -830,11 +867,12 @@ def run_tn(args):
         line["serving"] = serving_bench(tn, torch)
         line["serving_treesa_orders"] = serving_bench(tn, torch, optimizer="treesa", sweep_rates=False)
     if rank == 0 and not args.no_cpu_baseline:
-        sample = GRAPHS + [g for g in GRAPHS if g[1] == 140]
-        ops, secs, used = cpu_reference(sample, os.cpu_count() or 1)
+        graphs = [(f"reg3:{n}:{seed}", p.n, p.edges, p.order) for (kind, n, seed), p in zip(GRAPHS, plans)]
+        ops, secs, used = cpu_reference(graphs, os.cpu_count() or 1)
         line["cpu_baseline"] = {"value": ops / secs / 1e9, "unit": "Gop/s", "cores": used, "kind": "oracle",
-                                "sample": "the six headline graphs, then the three n=140 ones again (oracle greedy "
-                                          f"order), tropical + counting + 3 primes each, {secs:.1f} s"}
+                                "sample": "the whole headline step on all cores: the six graphs with the GPU "
+                                          f"arm's orders, tropical + counting + 3 primes each, {secs:.1f} s",
+                                "single_thread": cpu_single_thread_sample(graphs)}
     if rank == 0:
         print(json.dumps(line))
     for p in plans:

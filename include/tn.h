@@ -477,7 +477,10 @@ int tn_modp_gemm_umma(const uint32_t *primes, int32_t nprimes, const void *d_a, 
  * before any stream capture.  All calls share the array, which keeps the
  * previous call's contents; each call clears what must start at zero, and
  * calls that overlap on the GPU (concurrent threads or streams) race on it.
- * Enqueues on cuda_stream and waits for it. */
+ * Enqueues on cuda_stream and waits for it.  Errors as tn_contract's:
+ * TN_EINVAL, TN_ENOMEM (beyond the array), TN_ECUDA and TN_ETIMEOUT (a
+ * dependency wait ran out; the result is then unspecified); out->status is
+ * TN_EOVERFLOW when a count saturated. */
 #define TN_STATIC_WORKSPACE_BYTES (64 * 1024 * 1024)
 int tn_contract_static(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *primes, int32_t nprimes,
                        void *cuda_stream, tn_result_t *out);

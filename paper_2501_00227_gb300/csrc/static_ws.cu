@@ -23,6 +23,7 @@ namespace tn {
 int make_mod_table_checked(tn_semiring_t s, const uint32_t* primes, int32_t nprimes, void* mods);
 int decode_raw_any(tn_semiring_t s, const void* mods, int32_t nprimes, const unsigned char* raw,
                    tn_result_t* out);
+size_t required_bytes(tn_plan_s* p, tn_semiring_t s, int32_t nprimes);
 }  // namespace tn
 
 namespace {
@@ -61,9 +62,11 @@ extern "C" int tn_contract_static(tn_plan_t plan, tn_semiring_t semiring, const 
   if (rc) return rc;
   ExecPlan* X = exec_plan_get(plan, semiring, nprimes, &rc);
   if (!X) return rc;
-  // layout inside the array: executor workspace | step / task tables
-  const size_t ws_bytes = align256(X->total_bytes);
-  if (ws_bytes + X->table_bytes > static_cast<size_t>(TN_STATIC_WORKSPACE_BYTES)) return TN_ENOMEM;
+  // layout inside the array: workspace | step / task tables.  The workspace
+  // part is sized by the same rule as tn_contract's (tn_plan_info
+  // peak_bytes), so a plan is accepted exactly when the header says it is.
+  const size_t ws_bytes = align256(required_bytes(plan, semiring, nprimes));
+  if (ws_bytes + align256(X->table_bytes) > static_cast<size_t>(TN_STATIC_WORKSPACE_BYTES)) return TN_ENOMEM;
   void* base;
   rc = static_base(&base);
   if (rc) return rc;
@@ -78,5 +81,8 @@ extern "C" int tn_contract_static(tn_plan_t plan, tn_semiring_t semiring, const 
   unsigned char raw[TN_RAW_BYTES];
   if (cudaMemcpyAsync(raw, d_raw, TN_RAW_BYTES, cudaMemcpyDeviceToHost, st) != cudaSuccess) return TN_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return TN_ECUDA;
-  return decode_raw_any(semiring, mods, nprimes, raw, out);
+  rc = decode_raw_any(semiring, mods, nprimes, raw, out);
+  // a dependency wait that ran out leaves an unspecified result: report it
+  // as tn_contract does
+  return rc ? rc : out->status == TN_ETIMEOUT ? TN_ETIMEOUT : TN_OK;
 }

@@ -43,7 +43,7 @@ CASES = [("petersen", "tropical_i32", None), ("petersen", "counting", None),
 def _static_need(plan, semiring, nprimes):
     info = plan.info(semiring, nprimes)
     ws = info["peak_bytes"][tn.SEMIRINGS[semiring] - 1]
-    return (ws + 255) // 256 * 256 + info["exec_table_bytes"]
+    return (ws + 255) // 256 * 256 + (info["exec_table_bytes"] + 255) // 256 * 256
 
 
 @pytest.mark.parametrize("spec,semiring,primes", CASES)
@@ -77,6 +77,47 @@ def test_static_alternating_plans_keep_results():
     finally:
         pa.close()
         pb.close()
+
+
+def test_static_call_allocates_no_device_memory():
+    """The defining property: once a first round of calls has looked up the
+    array's address and loaded the kernels, further calls change the
+    device's free memory by nothing (torch's caching allocator stays idle)."""
+    stream = torch.cuda.current_stream().cuda_stream
+    plan = tn.Plan(*g.random_regular3(100, 1), nrepeat=2, seed=1)
+    kinds = (("counting", None), ("modp", tn.PRIMES31[:3]), ("tropical_i32", None))
+    try:
+        ref = [tn.tn_contract_static(plan.handle, sr, pr, stream) for sr, pr in kinds]
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        again = [tn.tn_contract_static(plan.handle, sr, pr, stream) for sr, pr in kinds]
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert again == ref
+    finally:
+        plan.close()
+
+
+def test_static_accepts_exactly_the_plans_the_documented_rule_admits():
+    """Plans on both sides of the 64 MiB limit: a call succeeds exactly when
+    peak_bytes + exec_table_bytes (each rounded up to 256 bytes) fits."""
+    stream = torch.cuda.current_stream().cuda_stream
+    seen = set()
+    for L in range(10, 19):
+        plan = tn.Plan(*g.kings_subgraph(L, 0.8, 1), nrepeat=1, seed=1)
+        try:
+            fits = _static_need(plan, "counting", 1) <= tn.TN_STATIC_WORKSPACE_BYTES
+            if fits:
+                assert tn.tn_contract_static(plan.handle, "counting", None, stream) == \
+                    _with_workspace(plan, "counting", None)
+            else:
+                with pytest.raises(tn.TNError) as ei:
+                    tn.tn_contract_static(plan.handle, "counting", None, stream)
+                assert ei.value.code == tn.TN_ENOMEM
+            seen.add(fits)
+        finally:
+            plan.close()
+    assert seen == {True, False}
 
 
 def test_static_rejects_plans_beyond_the_array():

@@ -40,3 +40,30 @@ def test_wait_limit_expires_and_the_context_stays_usable():
         assert r["status"] == tn.TN_OK and (r["max"], r["count"]) == O.mis_count(n, e, o)
     finally:
         p.close()
+
+
+@pytest.mark.gpu
+def test_static_entry_point_reports_an_expired_wait():
+    """tn_contract_static maps an expired dependency wait to TN_ETIMEOUT like
+    tn_contract, and its next call (default limit) is exact again."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    n, e = g.random_regular3(140, 1)
+    o = O.greedy_order(n, e, nrepeat=4, seed=1)
+    p = tn.Plan(n, e, o)
+    stream = torch.cuda.current_stream().cuda_stream
+    try:
+        assert p.info("counting")["exec_levels"] > 10
+        tn.tn_contract_static(p.handle, "counting", None, stream)   # address set-up, default limit
+        tn.tn_set_wait_timeout_ns(1)
+        try:
+            with pytest.raises(tn.TNError) as ei:
+                tn.tn_contract_static(p.handle, "counting", None, stream)
+        finally:
+            tn.tn_set_wait_timeout_ns(0)
+        assert ei.value.code == tn.TN_ETIMEOUT
+        r = tn.tn_contract_static(p.handle, "counting", None, stream)
+        assert r["status"] == tn.TN_OK and (r["max"], r["count"]) == O.mis_count(n, e, o)
+    finally:
+        p.close()
