@@ -168,19 +168,7 @@ int build_batch_plan(tn_plan_s* const* plans, int32_t count, tn_semiring_t semir
     case TN_COUNT_MODP: regions = static_cast<size_t>(M.nprimes) * align_up(4 * e, 256); break;
   }
   M.total_bytes = M.arena_base + regions;
-  M.off_steps = 0;
-  M.off_deps = align_up(sizeof(ExecStep) * M.steps.size(), 256);
-  M.off_tasks = M.off_deps + align_up(sizeof(int32_t) * (M.deps.size() + 1), 256);
-  M.off_groups = M.off_tasks + align_up(sizeof(ExecTask) * M.tasks.size(), 256);
-  M.off_members = M.off_groups + align_up(sizeof(int32_t) * M.group_begin.size(), 256);
-  M.table_bytes = M.off_members + sizeof(int32_t) * (M.group_members.size() + 1);
-  M.table_image.assign(M.table_bytes, 0);
-  std::memcpy(M.table_image.data() + M.off_groups, M.group_begin.data(), sizeof(int32_t) * M.group_begin.size());
-  std::memcpy(M.table_image.data() + M.off_members, M.group_members.data(),
-              sizeof(int32_t) * M.group_members.size());
-  std::memcpy(M.table_image.data() + M.off_steps, M.steps.data(), sizeof(ExecStep) * M.steps.size());
-  std::memcpy(M.table_image.data() + M.off_deps, M.deps.data(), sizeof(int32_t) * M.deps.size());
-  std::memcpy(M.table_image.data() + M.off_tasks, M.tasks.data(), sizeof(ExecTask) * M.tasks.size());
+  exec_write_table_image(&M);
   return TN_OK;
 }
 

@@ -25,7 +25,7 @@ namespace dev {
 
 struct ExecArgs {
   const ExecStep* steps;
-  const int32_t* deps;
+  const int2* deps;              // (exec-step index, its done_target) pairs
   const ExecTask* tasks;
   const int32_t* group_begin;    // group g: group_members[group_begin[g] .. group_begin[g+1])
   const int32_t* group_members;  // exec-step indices
@@ -171,7 +171,7 @@ __device__ __noinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& s
     tile_mainloop_counting<Cfg, true>(g, A, B, mp, b, tm, tn_, kbeg, kstop, smem, acc, prepared);
   else
     tile_mainloop<SR, Cfg, FOLD, true>(g, A, B, mp, b, tm, tn_, kbeg, kstop, sm, acc, prepared);
-  tile_merge_groups<SR, Cfg>(acc, reinterpret_cast<Acc*>(smem), mp);
+  tile_merge_groups<SR, Cfg>(acc, reinterpret_cast<Acc*>(smem + tile_merge_off<Cfg>()), mp);
 
   const uint32_t m0 = static_cast<uint32_t>(tm) * BM, n0 = static_cast<uint32_t>(tn_) * BN;
   const uint32_t cbase = static_cast<uint32_t>(b) << (g.nn + g.nm);
@@ -500,29 +500,34 @@ __device__ __forceinline__ void exec_final(const ExecArgs& a, const ExecStep& st
 __device__ __forceinline__ void bar_warps_1_7() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
 
 template <class Cfg>
-__device__ __forceinline__ void exec_prepare_tile(const ExecStep& st, const ExecTask& task, unsigned char* smem) {
+__device__ __forceinline__ void exec_prepare_tile(const ExecStep& st, const ExecTask& task, unsigned char* smem,
+                                                  bool same_step) {
   const int64_t tile = task.local / st.split;
   const int64_t per_b = int64_t(st.tiles_m) * st.tiles_n;
   tile_tables<Cfg>(st.g, *reinterpret_cast<TileIdx<Cfg>*>(smem), tile / per_b, (tile % per_b) / st.tiles_n,
-                   tile % st.tiles_n, threadIdx.x - 32, kBlock - 32, bar_warps_1_7);
+                   tile % st.tiles_n, threadIdx.x - 32, kBlock - 32, bar_warps_1_7, same_step);
 }
 
+// Index tables of a task (warps 1-7).  same_step: the previous task of this
+// CTA belonged to the same step, so its gather tables (and the general
+// step's low-k table) are still in shared memory.
 template <class SR>
-__device__ __noinline__ void exec_prepare(const ExecStep& st, const ExecTask& task, unsigned char* smem) {
+__device__ __noinline__ void exec_prepare(const ExecStep& st, const ExecTask& task, unsigned char* smem,
+                                          bool same_step) {
   if (task.kind == kTaskNaive) {
     int32_t kh0, kh1;
     naive_task_kh(st, task, &kh0, &kh1);
     naive_prepare<SR>(st.g, *reinterpret_cast<NaiveSmem<SR>*>(smem), kh0, kh1, threadIdx.x - 32, kBlock - 32,
-                      bar_warps_1_7);
+                      bar_warps_1_7, same_step);
     return;
   }
   switch (st.tile) {
-    case 0: exec_prepare_tile<TileC0>(st, task, smem); break;
-    case 1: exec_prepare_tile<TileC1>(st, task, smem); break;
-    case 2: exec_prepare_tile<TileC2>(st, task, smem); break;
-    case 3: exec_prepare_tile<TileC3>(st, task, smem); break;
-    case 4: exec_prepare_tile<TileC4>(st, task, smem); break;
-    default: exec_prepare_tile<TileC5>(st, task, smem); break;
+    case 0: exec_prepare_tile<TileC0>(st, task, smem, same_step); break;
+    case 1: exec_prepare_tile<TileC1>(st, task, smem, same_step); break;
+    case 2: exec_prepare_tile<TileC2>(st, task, smem, same_step); break;
+    case 3: exec_prepare_tile<TileC3>(st, task, smem, same_step); break;
+    case 4: exec_prepare_tile<TileC4>(st, task, smem, same_step); break;
+    default: exec_prepare_tile<TileC5>(st, task, smem, same_step); break;
   }
 }
 
@@ -532,41 +537,48 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
   __shared__ ExecStep s_step;
   __shared__ ExecTask s_task;
   __shared__ int s_t, s_abort, s_last;
+  __shared__ unsigned long long s_tr[3];  // trace: claimed, records loaded, ready (thread 0)
   const int tid = threadIdx.x;
-  unsigned long long t_claim = 0, t_loaded = 0;
+  // exec step whose record is in s_step and whose index tables are in
+  // shared memory (-1: none, e.g. after a group task)
+  int cur_step = -1;
+  if (tid == 0) s_abort = 0;
   for (;;) {
     if (tid == 0) {
-      if (a.trace) t_claim = global_ns();
-      s_abort = ld_relaxed_u32(a.status) != 0;
-      s_t = s_abort ? a.ntasks_total : atomicAdd(a.task_ctr, 1);
+      if (a.trace) s_tr[0] = global_ns();
+      const int t = atomicAdd(a.task_ctr, 1);
+      s_t = t;
+      if (t < a.ntasks_total) s_task = a.tasks[t];
     }
     __syncthreads();
     const int t = s_t;
     if (t >= a.ntasks_total) break;
-    if (tid == 0) s_task = a.tasks[t];
-    __syncthreads();
-    {
+    // consecutive tasks of the same step share the step record and the
+    // gather tables, and the step's dependencies were met for the first one
+    const bool same_step = s_task.step == cur_step && (s_task.kind == kTaskTile || s_task.kind == kTaskNaive);
+    if (!same_step) {
       const int32_t* src = reinterpret_cast<const int32_t*>(a.steps + s_task.step);
       int32_t* dst = reinterpret_cast<int32_t*>(&s_step);
       for (int i = tid; i < static_cast<int>(sizeof(ExecStep) / 4); i += kBlock) dst[i] = __ldg(src + i);
+      __syncthreads();
     }
-    __syncthreads();
-    if (a.trace && tid == 0) t_loaded = global_ns();
+    cur_step = s_task.kind == kTaskGroup ? -1 : s_task.step;
+    if (a.trace && tid == 0) s_tr[1] = global_ns();
     const bool prepared = s_task.kind == kTaskNaive || s_task.kind == kTaskTile;
-    if (tid >= 32 && prepared) exec_prepare<SR>(s_step, s_task, smem);
+    if (tid >= 32 && prepared) exec_prepare<SR>(s_step, s_task, smem, same_step);
     // wait for the steps this one depends on (warp 0, one dependency per lane)
-    if (tid < 32) {
+    if (tid < 32 && !same_step) {
       const bool final_task = s_task.kind == kTaskFinal;
       const int nd = final_task ? 1 : s_step.dep_count;
       bool timed_out = false;
       for (int d0 = 0; d0 < nd; d0 += 32) {
         const int d = d0 + tid;
         if (d < nd) {
-          const int dep = final_task ? s_task.step : a.deps[s_step.dep_begin + d];
-          const int32_t target = a.steps[dep].done_target;
+          const int2 dp =
+              final_task ? make_int2(s_task.step, s_step.done_target) : __ldg(a.deps + s_step.dep_begin + d);
           const unsigned long long t0 = global_ns();
           unsigned ns = 32;
-          while (ld_acquire(a.done + dep) < target) {
+          while (ld_acquire(a.done + dp.x) < dp.y) {
             if (global_ns() - t0 > a.timeout_ns || ld_relaxed_u32(a.status) != 0) {
               timed_out = true;
               break;
@@ -587,9 +599,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
     }
     __syncthreads();
     if (s_abort) break;
-    unsigned long long t_ready = 0;
     if (a.trace && tid == 0) {
-      t_ready = global_ns();
+      s_tr[2] = global_ns();
       g_trace_mark[0] = g_trace_mark[1] = 0;
     }
     if (s_task.kind == kTaskFinal) {
@@ -620,9 +631,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
         unsigned smid;
         asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
         unsigned long long* tr = a.trace + 8 * static_cast<int64_t>(t);
-        tr[0] = t_claim;
-        tr[1] = t_loaded;
-        tr[2] = t_ready;
+        tr[0] = s_tr[0];
+        tr[1] = s_tr[1];
+        tr[2] = s_tr[2];
         tr[3] = t_body;
         tr[4] = global_ns();
         tr[5] = (static_cast<unsigned long long>(smid) << 32) | blockIdx.x;
@@ -756,7 +767,7 @@ int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods_v, void* ws,
   const int ns = static_cast<int>(X->steps.size());
   const char* tables = static_cast<const char*>(d_tables);
   a.steps = reinterpret_cast<const ExecStep*>(tables + X->off_steps);
-  a.deps = reinterpret_cast<const int32_t*>(tables + X->off_deps);
+  a.deps = reinterpret_cast<const int2*>(tables + X->off_deps);
   a.tasks = reinterpret_cast<const ExecTask*>(tables + X->off_tasks);
   a.group_begin = reinterpret_cast<const int32_t*>(tables + X->off_groups);
   a.group_members = reinterpret_cast<const int32_t*>(tables + X->off_members);

@@ -105,6 +105,13 @@ struct ExecPlan {
   size_t smem = 0;
 };
 
+// Lays out and fills the device table image of X from its steps, deps,
+// tasks and groups: steps | dependencies | tasks | group begins | group
+// members.  A dependency is written as the pair (exec-step index, that
+// step's done_target), so a waiting CTA reads the count it waits for with
+// the index.
+void exec_write_table_image(ExecPlan* X);
+
 // Builds (or returns the cached) executor plan; thread-safe.
 ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc);
 // The same with an explicit group height (largest tree of tiny steps one

@@ -494,10 +494,16 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   }
   X->total_bytes = X->arena_base + regions;
 
-  // device table image: steps | deps | tasks
+  exec_write_table_image(X);
+  return TN_OK;
+}
+
+}  // namespace
+
+void exec_write_table_image(ExecPlan* X) {
   X->off_steps = 0;
   X->off_deps = align_up(sizeof(ExecStep) * X->steps.size(), 256);
-  X->off_tasks = X->off_deps + align_up(sizeof(int32_t) * (X->deps.size() + 1), 256);
+  X->off_tasks = X->off_deps + align_up(2 * sizeof(int32_t) * (X->deps.size() + 1), 256);
   X->off_groups = X->off_tasks + align_up(sizeof(ExecTask) * X->tasks.size(), 256);
   X->off_members = X->off_groups + align_up(sizeof(int32_t) * X->group_begin.size(), 256);
   X->table_bytes = X->off_members + sizeof(int32_t) * (X->group_members.size() + 1);
@@ -506,12 +512,13 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   std::memcpy(X->table_image.data() + X->off_members, X->group_members.data(),
               sizeof(int32_t) * X->group_members.size());
   std::memcpy(X->table_image.data() + X->off_steps, X->steps.data(), sizeof(ExecStep) * X->steps.size());
-  std::memcpy(X->table_image.data() + X->off_deps, X->deps.data(), sizeof(int32_t) * X->deps.size());
+  int32_t* dp = reinterpret_cast<int32_t*>(X->table_image.data() + X->off_deps);
+  for (size_t i = 0; i < X->deps.size(); ++i) {
+    dp[2 * i] = X->deps[i];
+    dp[2 * i + 1] = X->steps[X->deps[i]].done_target;
+  }
   std::memcpy(X->table_image.data() + X->off_tasks, X->tasks.data(), sizeof(ExecTask) * X->tasks.size());
-  return TN_OK;
 }
-
-}  // namespace
 
 ExecPlan* exec_plan_get(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int* rc) {
   return exec_plan_get_h(p, s, nprimes, group_height(), false, rc);

@@ -185,15 +185,21 @@ __device__ __forceinline__ ModAccN<NP> shfl_xor_val(ModAccN<NP> v, int off) {
 // threads.  The tables are complete for the CTA after the next CTA-wide
 // barrier.  Steps with at most 4 summed labels use the first k nibble table
 // directly (no low / high k tables).
+// have_low: the gather tables and the low-k table of this step are already
+// in sm (an earlier task of the same step built them); only the high-k
+// table of the task's block range is rebuilt.
 template <class SR, class Sync>
 __device__ __forceinline__ void naive_prepare(const StepGeom& g, NaiveSmem<SR>& sm, int32_t kh_begin,
-                                              int32_t kh_end, int first, int stride, Sync sync) {
-  gather_build(g, sm.gt, first, stride);
+                                              int32_t kh_end, int first, int stride, Sync sync,
+                                              bool have_low = false) {
+  if (!have_low) gather_build(g, sm.gt, first, stride);
   if (g.nk <= 4) return;  // the first k nibble table covers every term
-  sync();
   const int kl = g.nk < kNaiveKLoBits ? g.nk : kNaiveKLoBits;
   const int nkn = nibbles(g.nk);
-  for (int i = first; i < (1 << kl); i += stride) sm.klo[i] = gather(sm.gt.k, nkn, static_cast<uint32_t>(i));
+  if (!have_low) {
+    sync();
+    for (int i = first; i < (1 << kl); i += stride) sm.klo[i] = gather(sm.gt.k, nkn, static_cast<uint32_t>(i));
+  }
   if (kh_end - kh_begin <= kNaiveKHi)
     for (int i = first; i < kh_end - kh_begin; i += stride)
       sm.khi[i] = gather(sm.gt.k, nkn, static_cast<uint32_t>(kh_begin + i) << kl);

@@ -80,8 +80,7 @@ struct Stages {
   static constexpr int v = sizeof(typename SR::Val) <= 4 ? 3 : 2;
 };
 
-// Index part of a tile's shared memory (same place for every element type,
-// so the two passes of the counting tile share it).
+// Index part of a tile's shared memory (same place for every element type).
 template <class C>
 struct TileIdx {
   GatherTabs gt;
@@ -102,15 +101,19 @@ struct TileSmem {
 // of the tile's rows, columns and chunk rows, computed by threads first,
 // first + stride, ...; sync() is a barrier over exactly those threads.  The
 // tables are complete for the CTA after the next CTA-wide barrier.
+// have_gather: the gather tables of this step are already in ix.gt (an
+// earlier tile of the same step built them).
 template <class C, class Sync>
 __device__ __forceinline__ void tile_tables(const StepGeom& g, TileIdx<C>& ix, int64_t b, int64_t tm, int64_t tn_,
-                                            int first, int stride, Sync sync) {
+                                            int first, int stride, Sync sync, bool have_gather = false) {
   constexpr int BM = C::BM, BN = C::BN, BK = C::BK;
   const uint32_t M = 1u << g.nm, N = 1u << g.nn, K = 1u << g.nk;
   const uint32_t m0 = static_cast<uint32_t>(tm) * BM, n0 = static_cast<uint32_t>(tn_) * BN;
   const int ncn = nibbles(g.rc), nkn = nibbles(g.nk);
-  gather_build(g, ix.gt, first, stride);
-  sync();
+  if (!have_gather) {
+    gather_build(g, ix.gt, first, stride);
+    sync();
+  }
   const uint32_t cb = static_cast<uint32_t>(b) << (g.nn + g.nm);
   for (int i = first; i < BM; i += stride)
     ix.offAm[i] = m0 + i < M ? gather(ix.gt.c, ncn, cb | ((m0 + i) << g.nn)).x : 0u;
@@ -330,14 +333,22 @@ __device__ __forceinline__ void tile_merge_groups(typename SR::Acc (&acc)[C::TM]
 template <class C>
 struct TileSmemCnt;
 
-// Shared memory a tile needs: staging (both passes for counting), or the
-// group-merge buffer.
+// Byte offset of the group-merge buffer of tile_merge_groups: after the
+// index tables, which therefore survive a tile (the next tile of the same
+// step reuses its gather tables).
+template <class C>
+constexpr size_t tile_merge_off() {
+  return (sizeof(TileIdx<C>) + 15) / 16 * 16;
+}
+
+// Shared memory a tile needs: index tables and staging, or index tables
+// and the group-merge buffer.
 template <class SR, class C>
 constexpr size_t tile_smem_bytes() {
   size_t stage = sizeof(TileSmem<SR, C>);
   if constexpr (std::is_same<SR, SrCnt>::value)
     stage = sizeof(TileSmemCnt<C>) > sizeof(TileSmem<SrI32, C>) ? sizeof(TileSmemCnt<C>) : sizeof(TileSmem<SrI32, C>);
-  const size_t merge = sizeof(typename SR::Acc) * (C::KG - 1) * C::BM * C::BN;
+  const size_t merge = tile_merge_off<C>() + sizeof(typename SR::Acc) * (C::KG - 1) * C::BM * C::BN;
   return stage > merge ? stage : merge;
 }
 
@@ -348,49 +359,29 @@ namespace tn {
 namespace dev {
 
 // ---------------------------------------------------------------------------
-// Counting tropical in two passes over a tile (same result as the single
-// pass with SrCnt::mac, far fewer instructions per multiply-add):
-//   pass 1: the (max,+) tile of the values alone (tile_mainloop on SrI32);
-//   pass 2: count = sum over k of a.c * b.c for the terms whose a.v + b.v
-//           equals the pass-1 maximum of that entry.
-// Pass 2 accumulates exactly in 96 bits (32 x 32 -> 64 products added with
-// carry into a 32-bit overflow word) whenever every count staged in the
-// chunk fits in 32 bits; otherwise the chunk uses saturating 64 x 64
-// products.  The result is then min(exact count, 2^64 - 1), as for SrCnt.
+// Counting tropical (CountingMax of Sec. 5.3) over a tile, chunk by chunk.
+// Every staged chunk of k rows (values and counts, staged once) is read
+// twice from shared memory:
+//   1. the chunk's (max,+) tile of the values alone, m_c = max_k a.v + b.v;
+//      where m_c exceeds the running maximum the entry takes it and its count
+//      restarts from 0;
+//   2. count += a.c * b.c over the chunk's terms whose a.v + b.v equals the
+//      running maximum (only chunks whose maximum reached it have any).
+// The result equals the single pass with SrCnt::mac: counts are exact sums
+// of products over the maximising terms, saturated at 2^64 - 1.  A chunk
+// whose staged counts are all < 2^16 and whose accumulators are < 2^62 takes
+// one predicated 64-bit multiply-add per term (no carry can leave 64 bits);
+// other chunks use exact 64-bit products where counts are < 2^32 and
+// saturating 64 x 64 products otherwise, with saturating additions.
 // ---------------------------------------------------------------------------
 
-// c (96 bits: c2:c1:c0) += a * b when s == vmax
-__device__ __forceinline__ void cnt_fma32(uint32_t& c0, uint32_t& c1, uint32_t& c2, int32_t s, int32_t vmax,
-                                          uint32_t a, uint32_t b) {
+// c += a * b when s == vmax (64-bit multiply-add; the caller guarantees that
+// the sum stays below 2^64)
+__device__ __forceinline__ void cnt_fma_wide(uint64_t& c, int32_t s, int32_t vmax, uint32_t a, uint32_t b) {
   asm("{\n\t.reg .pred p;\n\t"
-      "setp.eq.s32 p, %3, %4;\n\t"
-      "@p mad.lo.cc.u32 %0, %5, %6, %0;\n\t"
-      "@p madc.hi.cc.u32 %1, %5, %6, %1;\n\t"
-      "@p addc.u32 %2, %2, 0;\n\t}"
-      : "+r"(c0), "+r"(c1), "+r"(c2)
-      : "r"(s), "r"(vmax), "r"(a), "r"(b));
-}
-
-// c (96 bits) += p (64 bits)
-__device__ __forceinline__ void cnt_add64(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint64_t p) {
-  asm("{\n\t"
-      "add.cc.u32 %0, %0, %3;\n\t"
-      "addc.cc.u32 %1, %1, %4;\n\t"
-      "addc.u32 %2, %2, 0;\n\t}"
-      : "+r"(c0), "+r"(c1), "+r"(c2)
-      : "r"(static_cast<uint32_t>(p)), "r"(static_cast<uint32_t>(p >> 32)));
-}
-
-// (c1 : c0) += a * b when s == vmax (64-bit multiply-add; the caller
-// guarantees no carry out of c1)
-__device__ __forceinline__ void cnt_fma_wide(uint32_t& c0, uint32_t& c1, int32_t s, int32_t vmax, uint32_t a,
-                                             uint32_t b) {
-  asm("{\n\t.reg .pred p;\n\t.reg .u64 t;\n\t"
-      "setp.eq.s32 p, %2, %3;\n\t"
-      "mov.b64 t, {%0, %1};\n\t"
-      "@p mad.wide.u32 t, %4, %5, t;\n\t"
-      "mov.b64 {%0, %1}, t;\n\t}"
-      : "+r"(c0), "+r"(c1)
+      "setp.eq.s32 p, %1, %2;\n\t"
+      "@p mad.wide.u32 %0, %3, %4, %0;\n\t}"
+      : "+l"(c)
       : "r"(s), "r"(vmax), "r"(a), "r"(b));
 }
 
@@ -406,8 +397,8 @@ __device__ __forceinline__ void load_lo_frag(const uint64_t* p, uint32_t (&out)[
   }
 }
 
-// Shared memory of the counting tile's second pass: values and counts of
-// each staged chunk in separate arrays.
+// Shared memory of the counting tile: values and counts of each staged
+// chunk in separate arrays.
 template <class C>
 struct TileSmemCnt {
   static constexpr int kSt = Stages<SrCnt>::v;
@@ -425,19 +416,13 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
                                                        CntVal (&acc)[C::TM][C::TN], bool ready = false) {
   constexpr int BM = C::BM, BN = C::BN, BK = C::BK, TM = C::TM, TN = C::TN;
   constexpr int kSt = Stages<SrCnt>::v;
-  // pass 1: maxima of the values
-  int32_t vmax[TM][TN];
-  tile_mainloop<SrI32, C, 1, CG>(g, A, B, mp, b, tm, tn_, kbeg, kend,
-                                 *reinterpret_cast<TileSmem<SrI32, C>*>(smem_raw), vmax, ready);
-  // pass 2: counts of the maximising terms (same index tables, same offsets);
-  // values and counts are staged in separate arrays, so every fragment is a
-  // run of 16-byte shared loads
   auto& sm = *reinterpret_cast<TileSmemCnt<C>*>(smem_raw);
   const int tid = threadIdx.x;
   const int grp = tid / C::GT, gt = tid % C::GT;
   const int tx = gt % C::WN, ty = gt / C::WN;
   int32_t offA[C::EA], offB[C::EB];
-  tile_offsets<C>(g, sm.idx, b, tm, tn_, offA, offB, true);  // tables of pass 1
+  tile_offsets<C>(g, sm.idx, b, tm, tn_, offA, offB, ready);
+  // padding slots (outside M / N / K) hold the semiring zero (-inf, 0)
 #pragma unroll
   for (int j = 0; j < C::EA; ++j)
     if (offA[j] < 0)
@@ -453,12 +438,15 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
         sm.Bc[st][tid + kBlock * j] = 0ull;
       }
 
-  // count of entry (i, j) = c2 * 2^64 + (c1 : c0)
-  uint32_t c0[TM][TN], c1[TM][TN], c2[TM][TN];
+  int32_t vmax[TM][TN];
+  uint64_t cnt[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) c0[i][j] = c1[i][j] = c2[i][j] = 0u;
+    for (int j = 0; j < TN; ++j) {
+      vmax[i][j] = kNegInf;
+      cnt[i][j] = 0ull;
+    }
 
   const bool a_async = A.kind == kOpArena, b_async = B.kind == kOpArena;
   auto issue = [&](int st, int64_t k0) {
@@ -498,21 +486,21 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
   int cur = 0;
   for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
     cp_async_wait<kSt - 2>();
-    // this thread's own copies of the chunk are complete.  Fast chunk: every
-    // count < 2^16 (products < 2^32) and every accumulator < 2^62, so 64-bit
-    // multiply-adds cannot carry out of (c1 : c0).
+    // this thread's own copies of the chunk are complete: the chunk is fast
+    // when every staged count is < 2^16 and every accumulator < 2^62 (16
+    // products < 2^32 cannot carry out of 64 bits); the barrier publishes the
+    // chunk to the CTA
     uint64_t hi = 0;
 #pragma unroll
     for (int j = 0; j < C::EA; ++j) hi |= sm.Ac[cur][tid + kBlock * j];
 #pragma unroll
     for (int j = 0; j < C::EB; ++j) hi |= sm.Bc[cur][tid + kBlock * j];
-    uint32_t big = 0;
+    uint64_t big = 0;
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < TN; ++j) big |= c1[i][j] >> 30;
+      for (int j = 0; j < TN; ++j) big |= cnt[i][j] >> 62;
     const bool slow = __syncthreads_or((hi >> 16) != 0 || big != 0) != 0;
-    const bool wide = slow && __syncthreads_or((hi >> 32) != 0) != 0;
     {
       const int64_t kn = k0 + (kSt - 1) * BK;
       const int nxt = (cur + kSt - 1) % kSt;
@@ -523,6 +511,33 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
     const int32_t* Bgv = sm.Bv[cur] + grp * C::BKG * BN;
     const uint64_t* Agc = sm.Ac[cur] + grp * C::BKG * BM;
     const uint64_t* Bgc = sm.Bc[cur] + grp * C::BKG * BN;
+    {
+      // 1: the chunk's maxima; a larger maximum restarts the entry's count
+      int32_t mc[TM][TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) mc[i][j] = kNegInf;
+#pragma unroll 4
+      for (int kk = 0; kk < C::BKG; ++kk) {
+        int32_t av[TM], bv[TN];
+        load_frag<TM>(Agv + kk * BM + ty * TM, av);
+        load_frag<TN>(Bgv + kk * BN + tx * TN, bv);
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) mc[i][j] = __viaddmax_s32(av[i], bv[j], mc[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j)
+          if (mc[i][j] > vmax[i][j]) {
+            vmax[i][j] = mc[i][j];
+            cnt[i][j] = 0ull;
+          }
+    }
+    // 2: counts of the chunk's terms that reach the running maximum
     if (!slow) {
 #pragma unroll 2
       for (int kk = 0; kk < C::BKG; ++kk) {
@@ -535,21 +550,7 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
-          for (int j = 0; j < TN; ++j) cnt_fma_wide(c0[i][j], c1[i][j], av[i] + bv[j], vmax[i][j], ac[i], bc[j]);
-      }
-    } else if (!wide) {
-      for (int kk = 0; kk < C::BKG; ++kk) {
-        int32_t av[TM], bv[TN];
-        uint32_t ac[TM], bc[TN];
-        load_frag<TM>(Agv + kk * BM + ty * TM, av);
-        load_frag<TN>(Bgv + kk * BN + tx * TN, bv);
-        load_lo_frag<TM>(Agc + kk * BM + ty * TM, ac);
-        load_lo_frag<TN>(Bgc + kk * BN + tx * TN, bc);
-#pragma unroll
-        for (int i = 0; i < TM; ++i)
-#pragma unroll
-          for (int j = 0; j < TN; ++j)
-            cnt_fma32(c0[i][j], c1[i][j], c2[i][j], av[i] + bv[j], vmax[i][j], ac[i], bc[j]);
+          for (int j = 0; j < TN; ++j) cnt_fma_wide(cnt[i][j], av[i] + bv[j], vmax[i][j], ac[i], bc[j]);
       }
     } else {
       for (int kk = 0; kk < C::BKG; ++kk) {
@@ -560,7 +561,7 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
 #pragma unroll
           for (int j = 0; j < TN; ++j)
             if (av + Bgv[kk * BN + tx * TN + j] == vmax[i][j])
-              cnt_add64(c0[i][j], c1[i][j], c2[i][j], sat_mul_u64(ac, Bgc[kk * BN + tx * TN + j]));
+              cnt[i][j] = sat_add_u64(cnt[i][j], sat_mul_u64(ac, Bgc[kk * BN + tx * TN + j]));
         }
       }
     }
@@ -573,7 +574,7 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       acc[i][j].v = vmax[i][j];
-      acc[i][j].c = c2[i][j] ? ~0ull : (static_cast<uint64_t>(c1[i][j]) << 32) | c0[i][j];
+      acc[i][j].c = cnt[i][j];
     }
 }
 

@@ -49,12 +49,14 @@ def test_static_entry_point_reports_an_expired_wait():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    n, e = g.random_regular3(140, 1)
+    n, e = g.random_regular3(100, 1)
     o = O.greedy_order(n, e, nrepeat=4, seed=1)
     p = tn.Plan(n, e, o)
     stream = torch.cuda.current_stream().cuda_stream
     try:
-        assert p.info("counting")["exec_levels"] > 10
+        info = p.info("counting")
+        assert info["exec_levels"] > 10
+        assert info["peak_bytes"][tn.TN_COUNTING_TROPICAL - 1] + info["exec_table_bytes"] < tn.TN_STATIC_WORKSPACE_BYTES
         tn.tn_contract_static(p.handle, "counting", None, stream)   # address set-up, default limit
         tn.tn_set_wait_timeout_ns(1)
         try:
