@@ -69,6 +69,7 @@ def _load():
             lib.or_contract_modp_x.argtypes = [I, i32p, I, i32p, I, u32p, u32p, I, u64p]
             lib.or_contract_weighted.argtypes = [I, I, I, i32p, I, i32p, i32p, i32p, I, u32p, u32p, I,
                                                  i64p, i64p, u64p, u64p, u64p]
+            lib.or_contract_kbest.argtypes = [I, I, I, i32p, I, i32p, i32p, i32p, I, I, i64p, i64p, u64p, u64p]
             lib.or_spin_energy.argtypes = [I, i32p, I, i32p, i32p, ctypes.POINTER(ctypes.c_int8)]
             lib.or_spin_energy.restype = ctypes.c_int64
             lib.or_bruteforce_spin.argtypes = [I, i32p, I, i32p, i32p, ctypes.c_int64, u64p]
@@ -267,6 +268,43 @@ def weighted_contract(kind: str, problem: str, n, edges, order, edge_w=None, ver
     if kind == "counting":
         return (None if cn.value == OR_NEG_INF else int(cn.value)), int(lo.value) | (int(hi.value) << 64)
     return [int(x) for x in res]
+
+
+#: largest k of the k-best element types
+MAX_K = 16
+
+
+def _kbest(kind, n, edges, order, k, problem, edge_w, vertex_w):
+    n, e, m = _graph(n, edges)
+    o, ns = _order(order)
+    J, h = _weights(edge_w, m), _weights(vertex_w, n)
+    vals = np.zeros(max(k, 1), dtype=np.int64)
+    lo, hi = np.zeros(max(k, 1), dtype=np.uint64), np.zeros(max(k, 1), dtype=np.uint64)
+    d = ctypes.c_int64()
+    _check(_load().or_contract_kbest(kind, PROBLEMS[problem], n, _p(e, ctypes.c_int32), m, _p_opt(J, ctypes.c_int32),
+                                     _p_opt(h, ctypes.c_int32), _p(o, ctypes.c_int32), ns, int(k),
+                                     _p(vals, ctypes.c_int64), ctypes.byref(d), _p(lo, ctypes.c_uint64),
+                                     _p(hi, ctypes.c_uint64)), "contract_kbest")
+    return vals, d.value, lo, hi
+
+
+def size_max_k(n, edges, order, k, problem="is", edge_w=None, vertex_w=None):
+    """SizeMax(k) (Sec. 5.3, Table 1: ExtendedTropical{k}): the k largest
+    total weights over all configurations of the network, counted with
+    multiplicity, in decreasing order (None where fewer than k exist).  For
+    the unit-weight IS network these are the k largest independent-set sizes;
+    for the spin glass, the k largest values of -H."""
+    vals, _, _, _ = _kbest(4, n, edges, order, k, problem, edge_w, vertex_w)
+    return [None if v == OR_NEG_INF else int(v) for v in vals[:k]]
+
+
+def counting_max_k(n, edges, order, k, problem="is", edge_w=None, vertex_w=None):
+    """CountingMax(k) (Sec. 5.3, Table 1: TruncatedPoly{k}): (d, [c_d,
+    c_{d-1}, ..., c_{d-k+1}]) where d is the largest total weight and c_w the
+    number of configurations of total weight w (for the IS network, the
+    polynomial's k highest-order coefficients, Eq. 13)."""
+    _, d, lo, hi = _kbest(5, n, edges, order, k, problem, edge_w, vertex_w)
+    return (None if d == OR_NEG_INF else int(d)), [int(a) | (int(b) << 64) for a, b in zip(lo[:k], hi[:k])]
 
 
 def spin_energy(n, edges, spins, edge_w=None, vertex_w=None):

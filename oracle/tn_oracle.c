@@ -19,6 +19,10 @@
  *       tropical  (max,+), zero = -inf, one = 0                   -> MIS size
  *       counting  (max,+) paired with a count                      -> #MIS
  *       mod-p     ordinary (+,*) reduced modulo a prime p          -> #IS mod p
+ *       k-max     the k largest configuration weights (ExtendedTropical{k})
+ *                                                                  -> SizeMax(k)
+ *       k-poly    the k highest-order terms of the polynomial of
+ *                 configuration counts by weight (TruncatedPoly{k}) -> CountingMax(k)
  *   - the complexity measures tc / sc / rwc of a binary order (Sec. 4.1);
  *   - the greedy order of Sec. 4.2.1 (cost Eq. 9 with alpha = 0);
  *   - brute force over all 2^n vertex subsets (definition of an independent
@@ -48,7 +52,8 @@
 #define OR_MAX_RANK 128
 
 enum { OR_OK = 0, OR_EINVAL = -1, OR_ENOMEM = -2, OR_ETOOBIG = -3 };
-enum { OR_TROPICAL = 1, OR_COUNTING = 2, OR_MODP = 3 };
+enum { OR_TROPICAL = 1, OR_COUNTING = 2, OR_MODP = 3, OR_KMAX = 4, OR_KPOLY = 5 };
+#define OR_MAX_K 16
 
 typedef unsigned __int128 u128;
 
@@ -94,6 +99,67 @@ static cnt_t cnt_add(cnt_t x, cnt_t y) {
     return r;
 }
 
+/* The k-best element types of Table 1 (Sec. 5.3).  k (1..OR_MAX_K) is the
+ * `nprimes` argument of the contraction routines; an element is a run of
+ * int64 words:
+ *   k-max (SizeMax(k), ExtendedTropical{k}): the k largest values of the
+ *     multiset of configuration weights, in decreasing order, padded with
+ *     -inf.  a (x) b = the k largest of all pairwise sums a_i + b_j;
+ *     a (+) b = the k largest of the union of the two multisets.
+ *     zero = all -inf, one = [0, -inf, ...].
+ *   k-poly (CountingMax(k), TruncatedPoly{k}): word 0 is the highest order d
+ *     (-inf: the zero polynomial), then k coefficients (u128, two words each)
+ *     of x^d, x^(d-1), ..., x^(d-k+1).  a (x) b = the product polynomial
+ *     truncated to its k highest orders; a (+) b = the sum, truncated to the
+ *     k highest orders of the larger leading order.  zero = (-inf, 0...),
+ *     one = (0, [1, 0, ...]).
+ * Counts saturate at 2^128 - 1 (never reached by the tests). */
+
+/* inserts x into the decreasing list v[0..k-1], dropping the smallest */
+static void kmax_insert(int64_t *v, int k, int64_t x) {
+    if (x == OR_NEG_INF || x <= v[k - 1]) return;
+    int j = k - 1;
+    while (j > 0 && v[j - 1] < x) { v[j] = v[j - 1]; j--; }
+    v[j] = x;
+}
+static void kmax_mul(const int64_t *a, const int64_t *b, int k, int64_t *r) {
+    for (int t = 0; t < k; t++) r[t] = OR_NEG_INF;
+    for (int i = 0; i < k; i++)
+        for (int j = 0; j < k; j++) kmax_insert(r, k, trop_mul(a[i], b[j]));
+}
+static void kmax_add_into(int64_t *acc, const int64_t *b, int k) {
+    for (int j = 0; j < k; j++) kmax_insert(acc, k, b[j]);
+}
+
+/* a k-poly element is k + 1 u128 words: word 0 holds d (as int64), words
+ * 1..k the coefficients */
+static int64_t kpoly_d(const u128 *p) { return (int64_t)(uint64_t)p[0]; }
+static void kpoly_set_zero(u128 *p, int k) {
+    memset(p, 0, sizeof(u128) * (size_t)(k + 1));
+    p[0] = (u128)(uint64_t)OR_NEG_INF;
+}
+/* coefficient of x^e in p */
+static u128 kpoly_coef(const u128 *p, int k, int64_t e) {
+    int64_t d = kpoly_d(p);
+    if (d == OR_NEG_INF || e > d || d - e >= k) return 0;
+    return p[1 + (d - e)];
+}
+static void kpoly_mul(const u128 *a, const u128 *b, int k, u128 *r) {
+    kpoly_set_zero(r, k);
+    if (kpoly_d(a) == OR_NEG_INF || kpoly_d(b) == OR_NEG_INF) return;
+    r[0] = (u128)(uint64_t)(kpoly_d(a) + kpoly_d(b));
+    for (int t = 0; t < k; t++)
+        for (int i = 0; i <= t; i++) r[1 + t] = sat_add128(r[1 + t], sat_mul128(a[1 + i], b[1 + t - i]));
+}
+static void kpoly_add_into(u128 *acc, const u128 *b, int k) {
+    if (kpoly_d(b) == OR_NEG_INF) return;
+    u128 r[OR_MAX_K + 1];
+    int64_t da = kpoly_d(acc), db = kpoly_d(b), d = da > db ? da : db;
+    r[0] = (u128)(uint64_t)d;
+    for (int t = 0; t < k; t++) r[1 + t] = sat_add128(kpoly_coef(acc, k, d - t), kpoly_coef(b, k, d - t));
+    memcpy(acc, r, sizeof(u128) * (size_t)(k + 1));
+}
+
 /* ------------------------------------------------------------------ */
 /* the network: leaves and SSA order                                   */
 /* ------------------------------------------------------------------ */
@@ -107,6 +173,8 @@ typedef struct {
 static size_t elem_size(int kind, int nprimes) {
     if (kind == OR_TROPICAL) return sizeof(int64_t);
     if (kind == OR_COUNTING) return sizeof(cnt_t);
+    if (kind == OR_KMAX) return sizeof(int64_t) * (size_t)nprimes;   /* k values */
+    if (kind == OR_KPOLY) return sizeof(u128) * (size_t)(nprimes + 1);  /* d, k coefficients */
     return sizeof(uint64_t) * (size_t)nprimes;   /* one residue per prime */
 }
 
@@ -214,6 +282,15 @@ static int make_leaf(tensor_t *t, int kind, const uint32_t *primes, int nprimes,
             cnt_t *d = t->data;
             d[x].n = val;
             d[x].c = val == OR_NEG_INF ? 0 : 1;
+        } else if (kind == OR_KMAX) {
+            int64_t *d = (int64_t *)t->data + x * (size_t)nprimes;
+            for (int q = 0; q < nprimes; q++) d[q] = OR_NEG_INF;
+            d[0] = val;
+        } else if (kind == OR_KPOLY) {
+            u128 *d = (u128 *)t->data + x * (size_t)(nprimes + 1);
+            kpoly_set_zero(d, nprimes);
+            d[0] = (u128)(uint64_t)val;
+            d[1] = val == OR_NEG_INF ? 0 : 1;
         } else {
             uint64_t *d = t->data;
             for (int q = 0; q < nprimes; q++) {
@@ -294,6 +371,23 @@ static int contract_pair(int kind, const uint32_t *primes, int nprimes,
             for (size_t s = 0; s < nsum; s++)
                 acc = cnt_add(acc, cnt_mul(a[ba | sa[s]], b[bb | sb[s]]));
             ((cnt_t *)C->data)[c] = acc;
+        } else if (kind == OR_KMAX) {
+            const int64_t *a = A->data, *b = B->data;
+            int64_t *acc = (int64_t *)C->data + c * (size_t)nprimes, prod[OR_MAX_K];
+            for (int q = 0; q < nprimes; q++) acc[q] = OR_NEG_INF;          /* zero */
+            for (size_t s = 0; s < nsum; s++) {
+                kmax_mul(a + (ba | sa[s]) * (size_t)nprimes, b + (bb | sb[s]) * (size_t)nprimes, nprimes, prod);
+                kmax_add_into(acc, prod, nprimes);
+            }
+        } else if (kind == OR_KPOLY) {
+            const u128 *a = A->data, *b = B->data;
+            const size_t w = (size_t)(nprimes + 1);
+            u128 *acc = (u128 *)C->data + c * w, prod[OR_MAX_K + 1];
+            kpoly_set_zero(acc, nprimes);                                  /* zero */
+            for (size_t s = 0; s < nsum; s++) {
+                kpoly_mul(a + (ba | sa[s]) * w, b + (bb | sb[s]) * w, nprimes, prod);
+                kpoly_add_into(acc, prod, nprimes);
+            }
         } else {
             const uint64_t *a = A->data, *b = B->data;
             uint64_t *out = (uint64_t *)C->data + c * nprimes;
@@ -341,6 +435,7 @@ static int contract_network(int kind, const uint32_t *primes, int nprimes, int n
         if (nprimes < 1) return OR_EINVAL;
         for (int q = 0; q < nprimes; q++) if (primes[q] < 2 || primes[q] >= (1u << 31)) return OR_EINVAL;
     }
+    if ((kind == OR_KMAX || kind == OR_KPOLY) && (nprimes < 1 || nprimes > OR_MAX_K)) return OR_EINVAL;
     tensor_t *t = calloc((size_t)(2 * T), sizeof(tensor_t));
     int *users = calloc((size_t)n, sizeof(int));
     if (!t || !users) { free(t); free(users); return OR_ENOMEM; }
@@ -372,6 +467,14 @@ static int contract_network(int kind, const uint32_t *primes, int nprimes, int n
             cnt_t acc; acc.n = OR_NEG_INF; acc.c = 0;
             for (size_t x = 0; x < ne; x++) acc = cnt_add(acc, ((cnt_t *)r->data)[x]);
             *(cnt_t *)result = acc;
+        } else if (kind == OR_KMAX) {
+            int64_t *acc = result;
+            for (int q = 0; q < nprimes; q++) acc[q] = OR_NEG_INF;
+            for (size_t x = 0; x < ne; x++) kmax_add_into(acc, (int64_t *)r->data + x * (size_t)nprimes, nprimes);
+        } else if (kind == OR_KPOLY) {
+            u128 *acc = result;
+            kpoly_set_zero(acc, nprimes);
+            for (size_t x = 0; x < ne; x++) kpoly_add_into(acc, (u128 *)r->data + x * (size_t)(nprimes + 1), nprimes);
         } else {
             for (int q = 0; q < nprimes; q++) {
                 uint64_t acc = 0;
@@ -463,6 +566,38 @@ int or_contract_weighted(int kind, int problem, int n, const int32_t *edges, int
     g_problem = OR_PROBLEM_IS;
     g_edge_w = g_vertex_w = NULL;
     g_vertex_x = NULL;
+    return rc;
+}
+
+/* The k-best properties of Sec. 5.3 (Table 1) on the networks of
+ * or_contract_weighted (problem, edge_w, vertex_w as there; NULL weights give
+ * the unit-weight IS network), along an SSA order, 1 <= k <= OR_MAX_K:
+ *   kind OR_KMAX  -> vals[0..k-1]: the k largest total weights over all
+ *                    configurations, with multiplicity, decreasing
+ *                    (SizeMax(k); INT64_MIN for -inf);
+ *   kind OR_KPOLY -> *d: the largest weight, and (c_lo, c_hi)[t]: the number
+ *                    of configurations of weight d - t, t < k (CountingMax(k)). */
+int or_contract_kbest(int kind, int problem, int n, const int32_t *edges, int m, const int32_t *edge_w,
+                      const int32_t *vertex_w, const int32_t *order, int nsteps, int k, int64_t *vals,
+                      int64_t *d, uint64_t *c_lo, uint64_t *c_hi) {
+    if ((kind != OR_KMAX && kind != OR_KPOLY) || (problem != OR_PROBLEM_IS && problem != OR_PROBLEM_SPIN))
+        return OR_EINVAL;
+    g_problem = problem;
+    g_edge_w = edge_w;
+    g_vertex_w = vertex_w;
+    int rc;
+    if (kind == OR_KMAX) {
+        rc = contract_network(OR_KMAX, NULL, k, n, edges, m, order, nsteps, vals);
+    } else {
+        u128 r[OR_MAX_K + 1];
+        rc = k < 1 || k > OR_MAX_K ? OR_EINVAL : contract_network(OR_KPOLY, NULL, k, n, edges, m, order, nsteps, r);
+        if (!rc) {
+            *d = kpoly_d(r);
+            for (int t = 0; t < k; t++) { c_lo[t] = (uint64_t)r[1 + t]; c_hi[t] = (uint64_t)(r[1 + t] >> 64); }
+        }
+    }
+    g_problem = OR_PROBLEM_IS;
+    g_edge_w = g_vertex_w = NULL;
     return rc;
 }
 
@@ -765,6 +900,7 @@ int or_flat_contract(int kind, int n, const int32_t *edges, int m, const uint32_
         if (nprimes < 1) return OR_EINVAL;
         for (int q = 0; q < nprimes; q++) if (primes[q] < 2 || primes[q] >= (1u << 31)) return OR_EINVAL;
     }
+    if ((kind == OR_KMAX || kind == OR_KPOLY) && (nprimes < 1 || nprimes > OR_MAX_K)) return OR_EINVAL;
     int np_ = kind == OR_MODP ? nprimes : 0;
     int T = m + n;
     tensor_t *t = calloc((size_t)T, sizeof(tensor_t));
