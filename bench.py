@@ -432,6 +432,38 @@ def polynomial_bench(tn, torch, plans, cpu: bool = True):
     return out
 
 
+def kbest_bench(tn, torch, plans, poly=None):
+    """SizeMax(k) and CountingMax(k) (Sec. 5.3, Table 1) of the headline graphs
+    in one contraction with the k-best element types (tn_contract_kbest,
+    synchronous, timed end to end), next to the polynomial route (the same
+    numbers read off the exact independence polynomial, from
+    independence_polynomial)."""
+    st = torch.cuda.current_stream().cuda_stream
+    out = {"workload": "random 3-regular n=100 and n=140 seeds 1-3 (the headline plans), unit weights",
+           "instances": []}
+    poly_ms = {(r["n"], r["seed"]): r["ms"] for r in (poly or {}).get("instances", [])}
+    for (kind, n, seed), p in zip(GRAPHS, plans):
+        row = {"n": n, "seed": seed}
+        for name in ("size_max", "counting_max"):
+            for k in (2, 4):
+                ws = torch.empty(tn.tn_kbest_workspace_bytes(p.handle, name, k), dtype=torch.uint8, device="cuda")
+                f = lambda: tn.tn_contract_kbest(p.handle, name, k, ws.data_ptr(), ws.numel(), st)
+                r = f()
+                ts = []
+                for _ in range(5):
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                    f()
+                    ts.append(time.perf_counter() - t)
+                row[f"{name}_{k}_ms"] = statistics.median(ts) * 1e3
+                row[f"{name}_{k}"] = r.get("values") or [r["max"], r["counts"]]
+                del ws
+        if (n, seed) in poly_ms:
+            row["polynomial_route_ms"] = poly_ms[(n, seed)]
+        out["instances"].append(row)
+    return out
+
+
 def weighted_bench(tn, torch, plans, cpu: bool = True):
     """Weighted networks on the headline plans: the spin glass of Eq. 1 with
     seeded +-1 couplings (tropical and counting, stored leaves generated on
@@ -643,6 +675,20 @@ def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120, optimizer: s
     plain_s = time.perf_counter() - t0
     plain = {"inst_per_s": nreq / plain_s, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
              "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+    # device time of every request alone (CUDA events around its launch, run
+    # back to back): what the GPU must spend on the stream if requests do not
+    # overlap, and its five largest requests' share
+    raw = torch.zeros(tn.TN_RAW_BYTES, dtype=torch.uint8, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in reqs]
+    torch.cuda.synchronize()
+    for (p, sr, pr), (e0, e1) in zip(reqs, evs):
+        e0.record()
+        tn.tn_contract_async(p.handle, sr, pr, ws.data_ptr(), need, st, raw.data_ptr())
+        e1.record()
+    torch.cuda.synchronize()
+    dev_ms = sorted((e0.elapsed_time(e1) for e0, e1 in evs), reverse=True)
+    device = {"sum_ms": float(sum(dev_ms)), "largest5_ms": float(sum(dev_ms[:5])),
+              "plain_s_over_device_sum": plain_s / (sum(dev_ms) * 1e-3)}
 
     def serve(rate):
         server = tn.tn_server_create(budget_gb << 30, 4)
@@ -676,7 +722,9 @@ def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120, optimizer: s
                 "p50_ms": 1e3 * float(np.percentile(lats, 50)), "p99_ms": 1e3 * float(np.percentile(lats, 99))}
 
     sat = serve(0)  # every request offered at once
-    sweep = [serve(f * sat["inst_per_s"]) for f in (0.25, 0.5, 1.0)] if sweep_rates else None
+    # Poisson rates from a quarter to four times the plain path's capacity
+    sweep = [dict(serve(f * plain["inst_per_s"]), of_plain_capacity=f) for f in (0.25, 0.5, 1.0, 2.0, 4.0)] \
+        if sweep_rates else None
     pool_tc = sum(2.0 ** p.info("tropical_i32")["log2_tc"] for p in pool)
     for p in pool:
         p.close()
@@ -685,6 +733,8 @@ def serving_bench(tn, torch, nreq: int = 600, budget_gb: int = 120, optimizer: s
                         f"{budget_gb} GB budget, 4 launch slots",
             "orders": optimizer, "order_s": t_opt, "log2_pool_tc": float(np.log2(pool_tc)),
             "plain_one_at_a_time": plain, "served_saturated": sat, "served_rate_sweep": sweep,
+            "device_time_alone": device,
+            "served_s_over_device_sum": (nreq / sat["inst_per_s"]) / (device["sum_ms"] * 1e-3),
             "speedup_inst_per_s": sat["inst_per_s"] / plain["inst_per_s"]}
 
 
@@ -857,6 +907,7 @@ def run_tn(args):
         line["largest_tropical"] = largest_bench(tn, torch, peak, autotune=not args.no_autotune)
         line["modp_tensor_core_ablation"] = limb_ablation_bench(tn, torch)
         line["independence_polynomial"] = polynomial_bench(tn, torch, plans, cpu=not args.no_cpu_baseline)
+        line["kbest"] = kbest_bench(tn, torch, plans, line["independence_polynomial"])
         line["weighted"] = weighted_bench(tn, torch, plans, cpu=not args.no_cpu_baseline)
         line["single_config"] = single_config_bench(tn, torch, plans)
         line["treesa"] = treesa_bench(tn, torch)
@@ -865,7 +916,7 @@ def run_tn(args):
         line["batching"] = batching_bench(tn, torch)
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_bench(tn, torch)
-        line["serving_treesa_orders"] = serving_bench(tn, torch, optimizer="treesa", sweep_rates=False)
+        line["serving_treesa_orders"] = serving_bench(tn, torch, optimizer="treesa")
     if rank == 0 and not args.no_cpu_baseline:
         graphs = [(f"reg3:{n}:{seed}", p.n, p.edges, p.order) for (kind, n, seed), p in zip(GRAPHS, plans)]
         ops, secs, used = cpu_reference(graphs, os.cpu_count() or 1)

@@ -73,7 +73,10 @@ typedef enum {
     TN_TROPICAL_F32 = 1,
     TN_TROPICAL_I32 = 2,
     TN_COUNTING_TROPICAL = 3,
-    TN_COUNT_MODP = 4
+    TN_COUNT_MODP = 4,
+    /* k-best element types (tn_contract_kbest only; see there) */
+    TN_SIZE_MAX_K = 5,
+    TN_COUNTING_MAX_K = 6
 } tn_semiring_t;
 
 #define TN_I32_NEG_INF (-(1 << 30))
@@ -455,6 +458,30 @@ int tn_modp_gemm_limb(const uint32_t *primes, int32_t nprimes, const void *d_a, 
  * cores did not complete within 2 s (the result is then unspecified). */
 int tn_modp_gemm_umma(const uint32_t *primes, int32_t nprimes, const void *d_a, const void *d_b, void *d_c,
                       int32_t batch, int32_t m, int32_t n, int32_t k, void *cuda_stream);
+
+/* SizeMax(k) and CountingMax(k) (Sec. 5.3, Table 1) in one contraction.
+ *
+ * The network of tn_contract (unit vertex weights) is contracted with a
+ * k-best element type (the ExtendedTropical{k} and TruncatedPoly{k} elements
+ * of Table 1) along the plan's order, in one executor launch:
+ *   TN_SIZE_MAX_K      values[0..k-1] = the k largest independent-set sizes,
+ *                      each set counted once (so repeated sizes repeat), in
+ *                      decreasing order; INT32_MIN where fewer than k sets
+ *                      exist.  counts is not used (may be NULL).
+ *   TN_COUNTING_MAX_K  values[0] = alpha (the largest size) and counts[t] =
+ *                      the number of independent sets of size alpha - t,
+ *                      t < k (the k highest coefficients of the independence
+ *                      polynomial, Eq. 13); counts saturate at UINT64_MAX.
+ * k in 1..TN_KBEST_MAX.  d_workspace: at least tn_kbest_workspace_bytes()
+ * bytes, 256-byte aligned, caller-owned; sliced plans are not accepted.
+ * Synchronous (waits for cuda_stream).  *status: TN_OK, TN_EOVERFLOW (a count
+ * saturated) or TN_ETIMEOUT.  Returns TN_OK, TN_EINVAL, TN_ENOMEM (workspace
+ * too small), TN_ECUDA or TN_ETIMEOUT (a dependency wait ran out; the
+ * outputs are then unspecified). */
+#define TN_KBEST_MAX 4
+int tn_kbest_workspace_bytes(tn_plan_t plan, tn_semiring_t semiring, int32_t k, uint64_t *bytes);
+int tn_contract_kbest(tn_plan_t plan, tn_semiring_t semiring, int32_t k, void *d_workspace, size_t ws_bytes,
+                      void *cuda_stream, int32_t *values, uint64_t *counts, int32_t *status);
 
 /* Contraction without any device allocation.
  *

@@ -37,7 +37,7 @@ struct ExecStep {
   int32_t nchunks;               // naive: output chunks
   int32_t done_target;           // tasks of this step (its done counter's final value)
   int32_t c_shared;              // 1: the output lives in the group task's shared memory at byte c_off
-  int32_t pad_;
+  int32_t vec;                   // tiles: operands staged in 16-byte runs (kVecA | kVecB of tile_device.cuh)
 };
 
 // Shared memory of a group task reserved for its internal tensors (bytes),
@@ -153,8 +153,17 @@ int build_batch_plan(tn_plan_s* const* plans, int32_t count, tn_semiring_t semir
 int exec_prepare_launch(tn_semiring_t s, const void* mods);
 
 // Bytes per accumulator / per staged value of the tiled tasks, and the
-// dynamic shared memory the executor needs (exec.cu).
-size_t exec_acc_bytes(tn_semiring_t s);
+// dynamic shared memory the executor needs (exec.cu).  kw: the width K of a
+// k-best element type.
+size_t exec_acc_bytes(tn_semiring_t s, int32_t kw = 1);
+
+// The k-best element types (TN_SIZE_MAX_K, TN_COUNTING_MAX_K): contracted
+// by the general step body only, one task set (no per-prime tasks), with
+// the element width K (2 or 4) in ExecPlan::nprimes.
+inline bool is_kbest(tn_semiring_t s) { return s == TN_SIZE_MAX_K || s == TN_COUNTING_MAX_K; }
+// Launches a k-best instantiation of the executor (kbest.cu); args is the
+// filled dev::ExecArgs of exec_launch_core.
+int kbest_launch(ExecPlan* X, tn_semiring_t s, const void* args, void* stream);
 size_t exec_smem_bytes(tn_semiring_t s);
 
 }  // namespace tn

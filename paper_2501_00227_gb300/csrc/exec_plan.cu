@@ -12,6 +12,7 @@
 #include "exec.h"
 #include "kernels.h"
 #include "step_device.cuh"
+#include "tile_device.cuh"
 
 namespace tn {
 
@@ -97,9 +98,13 @@ class LevelArena {
 int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X) {
   const int ns = static_cast<int>(p->steps.size());
   const int H = X->group_h;
-  const int np = s == TN_COUNT_MODP ? nprimes : 1;
+  // np: prime slots of mod p (one task set each) or the width of a k-best
+  // element type (one task set, np blocks per tensor)
+  const int np = s == TN_COUNT_MODP || is_kbest(s) ? nprimes : 1;
   X->semiring = s;
   X->nprimes = np;
+  const int kw = is_kbest(s) ? np : 1;
+  const int npt = s == TN_COUNT_MODP ? np : 1;  // task sets (one per prime slot)
 
   // dependency levels (leaves at -1)
   std::vector<int32_t> level(ns);
@@ -160,7 +165,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
   // Inputs consumed inside a group are released when the group's root level
   // is reached, by the root.
   // launch shape of every step, and the split-K scratch it needs (bytes)
-  const size_t acc_bytes = exec_acc_bytes(s);
+  const size_t acc_bytes = exec_acc_bytes(s, kw);
   struct Launch {
     int kernel, tile, split;
     dev::NaiveShape sh;
@@ -175,14 +180,14 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
     if (groot[st] >= 0) {
       L.kernel = kKernNaive;
       L.sh = dev::naive_shape(g.rc, g.nk, false);
-    } else if (L.kernel == kKernTiled && g.c_identity) {
+    } else if (L.kernel == kKernTiled) {
       const int64_t bm = dev::tiled_tile_bm(L.tile), bn = dev::tiled_tile_bn(L.tile);
       const int64_t ntiles = ((int64_t(1) << g.nm) + bm - 1) / bm * (((int64_t(1) << g.nn) + bn - 1) / bn) << g.nb;
-      if (L.split > 1) L.scratch = static_cast<size_t>(ntiles * np * L.split * bm * bn) * acc_bytes;
+      if (L.split > 1) L.scratch = static_cast<size_t>(ntiles * npt * L.split * bm * bn) * acc_bytes;
     } else {
       L.kernel = kKernNaive;
-      L.sh = dev::naive_shape(g.rc, g.nk, true);
-      if (L.sh.ks > 1) L.scratch = static_cast<size_t>(L.sh.nchunks * np * L.sh.ks * L.sh.chunk) * acc_bytes;
+      L.sh = dev::naive_shape(g.rc, g.nk, !is_kbest(s));
+      if (L.sh.ks > 1) L.scratch = static_cast<size_t>(L.sh.nchunks * npt * L.sh.ks * L.sh.chunk) * acc_bytes;
     }
   }
 
@@ -368,10 +373,10 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
         const int32_t gid = static_cast<int32_t>(X->group_begin.size());
         X->group_begin.push_back(static_cast<int32_t>(X->group_members.size()));
         for (int32_t m : mem) X->group_members.push_back(pos[m]);
-        X->tasks.push_back(ExecTask{x, gid, np > 1 ? -1 : 0, kTaskGroup});  // all primes in one task
+        X->tasks.push_back(ExecTask{x, gid, npt > 1 ? -1 : 0, kTaskGroup});  // all primes in one task
         E.done_target = 1;
       }
-    } else if (kernel == kKernTiled && S.g.c_identity) {
+    } else if (kernel == kKernTiled) {
       const int64_t bm = dev::tiled_tile_bm(tile), bn = dev::tiled_tile_bn(tile);
       E.kernel = kKernTiled;
       E.tile = tile;
@@ -380,13 +385,21 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
       E.tiles_n = static_cast<int32_t>(((int64_t(1) << S.g.nn) + bn - 1) / bn);
       const int64_t ntiles = int64_t(E.tiles_m) * E.tiles_n << S.g.nb;
       E.ntasks = static_cast<int32_t>(ntiles * split);
+      // 16-byte staging where an operand's two lowest stored bits are the
+      // step's m (n) bits 0 and 1 (the planner stores intermediates for that)
+      const StepGeom& G = S.g;
+      if (E.g.a_kind == kOpArena && G.nm >= 2 && G.a_pos[G.nb] == 0 && G.a_pos[G.nb + 1] == 1 && E.a_off % 4 == 0)
+        E.vec |= dev::kVecA;
+      if (E.g.b_kind == kOpArena && G.nn >= 2 && G.b_pos[G.nb + G.nk] == 0 && G.b_pos[G.nb + G.nk + 1] == 1 &&
+          E.b_off % 4 == 0)
+        E.vec |= dev::kVecB;
       if (split > 1) {
         E.arrive_off = arrive;
-        arrive += static_cast<int32_t>(ntiles * np);
+        arrive += static_cast<int32_t>(ntiles * npt);
         E.scratch_off = s_off[st] * 256;
       }
     } else {
-      const dev::NaiveShape sh = dev::naive_shape(S.g.rc, S.g.nk, true);
+      const dev::NaiveShape sh = dev::naive_shape(S.g.rc, S.g.nk, !is_kbest(s));
       E.kernel = kKernNaive;
       E.R = sh.R;
       E.chunk = sh.chunk;
@@ -395,21 +408,21 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
       E.ntasks = static_cast<int32_t>(sh.ntasks);
       if (sh.ks > 1) {
         E.arrive_off = arrive;
-        arrive += static_cast<int32_t>(sh.nchunks * np);
+        arrive += static_cast<int32_t>(sh.nchunks * npt);
         E.scratch_off = s_off[st] * 256;
       }
     }
     if ((E.split > 1 || E.ks > 1) != (ln[st].scratch > 0)) return TN_EINVAL;  // launch shapes disagree
     if (groot[st] < 0) {
-      if (E.kernel == kKernNaive && E.ks == 1 && np > 1) {
+      if (E.kernel == kKernNaive && E.ks == 1 && npt > 1) {
         // a general step without k split does every prime inside each task
         for (int t = 0; t < E.ntasks; ++t) X->tasks.push_back(ExecTask{x, t, -1, kTaskNaive});
         E.done_target = E.ntasks;
       } else {
-        for (int q = 0; q < np; ++q)
+        for (int q = 0; q < npt; ++q)
           for (int t = 0; t < E.ntasks; ++t)
             X->tasks.push_back(ExecTask{x, t, q, E.kernel == kKernTiled ? kTaskTile : kTaskNaive});
-        E.done_target = E.ntasks * np;
+        E.done_target = E.ntasks * npt;
       }
     }
   }
@@ -491,6 +504,10 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
     case TN_TROPICAL_I32: regions = align_up(4 * e, 256); break;
     case TN_COUNTING_TROPICAL: regions = align_up(4 * e, 256) + align_up(8 * e, 256); break;
     case TN_COUNT_MODP: regions = static_cast<size_t>(np) * align_up(4 * e, 256); break;
+    // k-best: K int32 blocks; or one int32 block and K uint64 blocks of twice
+    // its size (so that one entry stride serves both)
+    case TN_SIZE_MAX_K: regions = static_cast<size_t>(np) * align_up(4 * e, 256); break;
+    case TN_COUNTING_MAX_K: regions = static_cast<size_t>(2 * np + 1) * align_up(4 * e, 256); break;
   }
   X->total_bytes = X->arena_base + regions;
 
@@ -531,14 +548,14 @@ ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H,
     *rc = TN_EINVAL;
     return nullptr;
   }
-  if (keep || stored_leaves) H = 1;
+  if (keep || stored_leaves || is_kbest(s)) H = 1;
   if (!p->exec_cache) {
     static std::mutex init_mu;
     std::lock_guard<std::mutex> lk(init_mu);
     if (!p->exec_cache) p->exec_cache = new Cache();
   }
   Cache* c = static_cast<Cache*>(p->exec_cache);
-  const int np = s == TN_COUNT_MODP ? nprimes : 1;
+  const int np = s == TN_COUNT_MODP || is_kbest(s) ? nprimes : 1;
   std::lock_guard<std::mutex> lk(c->mu);
   for (auto& x : c->plans)
     if (x->semiring == s && x->nprimes == np && x->group_h == H && x->batched == batched && x->keep == keep &&

@@ -210,7 +210,7 @@ void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, i
   *kernel = kKernNaive;
   *tile = 1;
   *split = 1;
-  if (force_naive || g.nb > 15 || g.rc < 1) return;
+  if (force_naive || g.nb > 15 || g.rc < 1 || s == TN_SIZE_MAX_K || s == TN_COUNTING_MAX_K) return;
   const int ops_bits = g.nb + g.nm + g.nn + g.nk;
   if (!force_tiled && (ops_bits < 16 || g.nk < 3 || g.nm + g.nn < 10 || g.nm < 2 || g.nn < 2)) return;
   const bool tropical = (s == TN_TROPICAL_F32 || s == TN_TROPICAL_I32);

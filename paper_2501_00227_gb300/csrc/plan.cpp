@@ -80,7 +80,7 @@ class Arena {
 
 int classify_step(const std::vector<int32_t>& la, const std::vector<int32_t>& lb,
                   const std::vector<int32_t>& lc_set, StepGeom* g,
-                  std::vector<int32_t>* lc_order) {
+                  std::vector<int32_t>* lc_order, const std::vector<int32_t>* n_first) {
   if (la.size() > static_cast<size_t>(kMaxRank) || lb.size() > static_cast<size_t>(kMaxRank) ||
       lc_set.size() > static_cast<size_t>(kMaxRank))
     return TN_EINVAL;
@@ -98,6 +98,9 @@ int classify_step(const std::vector<int32_t>& la, const std::vector<int32_t>& lb
     if (in_a) continue;
     if (in_c) N.push_back(l);
     else K.push_back(l);
+  }
+  if (n_first) {
+    std::stable_partition(N.begin(), N.end(), [&](int32_t l) { return position(*n_first, l) >= 0; });
   }
   int total = static_cast<int>(bt.size() + M.size() + N.size() + K.size());
   if (total > kMaxStepBits) return TN_EINVAL;
@@ -152,6 +155,69 @@ size_t workspace_bytes(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes) {
       return kHeaderBytes + static_cast<size_t>(nprimes < 1 ? 1 : nprimes) * align256(4 * e);
   }
   return 0;
+}
+
+// Storage order of the intermediates.  A step's kernels stage operand A
+// along its M labels and operand B along its N labels (consecutive threads
+// take consecutive m, resp. n, and the M / N labels are numbered in the
+// operand's storage order).  The first pass stores every output as (N, M,
+// batch) of its own step; this pass re-stores each intermediate with the
+// labels its consumer stages along (the consumer's M labels if it is the
+// consumer's A, its N labels if B) as the lowest bits, the others after them
+// in the first pass's order, so that neighbouring staging threads read
+// neighbouring entries.  The producing step then writes through c_pos (its
+// output index bits scattered to the chosen positions).  Only orders change:
+// labels, sizes, arena offsets and the step's classes stay the same.
+int consumer_layouts(tn_plan_s* p) {
+  const int32_t ns = static_cast<int32_t>(p->steps.size());
+  std::vector<std::vector<int32_t>> natural(static_cast<size_t>(ns));  // (N, M, bt) of each step
+  for (int32_t s = 0; s < ns; ++s) natural[s] = p->tensors[p->steps[s].c_id].labels;
+  for (int32_t s = 0; s < ns; ++s) {
+    Step& st = p->steps[s];
+    const auto& la = p->tensors[st.a_id].labels;
+    const auto& lb = p->tensors[st.b_id].labels;
+    TensorInfo& c = p->tensors[st.c_id];
+    // only for consumers that run as GEMM tiles with real work (the same
+    // shape test as the launch choice; their class sizes are order-free)
+    auto big_tiled = [&](const StepGeom& qg) {
+      const int bits = qg.nb + qg.nm + qg.nn + qg.nk;
+      return bits >= 20 && qg.nk >= 3 && qg.nm + qg.nn >= 10 && qg.nm >= 2 && qg.nn >= 2;
+    };
+    // the consumer's staging labels (in c, not in the consumer's other
+    // operand, kept by the consumer)
+    std::vector<int32_t> staged;
+    if (c.consumer >= 0 && big_tiled(p->steps[c.consumer].g)) {
+      const Step& q = p->steps[c.consumer];
+      const auto& other = p->tensors[q.a_id == st.c_id ? q.b_id : q.a_id].labels;
+      for (int32_t l : natural[s])
+        if (position(other, l) < 0 && position(natural[c.consumer], l) >= 0) staged.push_back(l);
+    }
+    // classes and the output order of this step from the operands' final
+    // storage orders, numbering the staged N labels first: when two or more
+    // of them exist the output keeps index order (16-byte stores) and is
+    // still staged along its lowest two labels by the consumer
+    std::vector<int32_t> nat;
+    int rc = classify_step(la, lb, natural[s], &st.g, &nat, staged.empty() ? nullptr : &staged);
+    if (rc != TN_OK) return rc;
+    st.g.a_kind = p->tensors[st.a_id].kind;
+    st.g.b_kind = p->tensors[st.b_id].kind;
+    std::vector<int32_t> chosen = nat;
+    if (!staged.empty()) {
+      std::vector<int32_t> first, rest;
+      for (int32_t l : nat) (position(staged, l) >= 0 ? first : rest).push_back(l);
+      // already staged along its lowest two labels: keep the step's order;
+      // else the staged labels first (the producer then scatters its stores)
+      const bool natural_ok = first.size() >= 2 && position(first, nat[0]) >= 0 && position(first, nat[1]) >= 0;
+      if (!natural_ok) {
+        chosen = first;
+        chosen.insert(chosen.end(), rest.begin(), rest.end());
+      }
+    }
+    c.labels = chosen;
+    st.g.c_identity = chosen == nat ? 1 : 0;
+    for (int j = 0; j < st.g.rc; ++j) st.g.c_pos[j] = static_cast<int8_t>(position(chosen, nat[j]));
+  }
+  return TN_OK;
 }
 
 int build_plan(int32_t n, const int32_t* edges, int32_t m, const int32_t* order, int32_t nsteps,
@@ -264,7 +330,7 @@ int build_plan(int32_t n, const int32_t* edges, int32_t m, const int32_t* order,
   p->root = static_cast<int32_t>(p->tensors.size()) - 1;
   if (!p->tensors[p->root].labels.empty()) return TN_EINVAL;  // cannot happen for a full order
   p->arena_entries = std::max<int64_t>(arena.top(), kArenaAlign);
-  return TN_OK;
+  return consumer_layouts(p);
 }
 
 // ---------------------------------------------------------------------------

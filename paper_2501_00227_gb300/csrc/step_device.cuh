@@ -46,24 +46,32 @@ __device__ __forceinline__ int nibbles(int bits) { return (bits + 3) >> 2; }
 // offsets of an index are the sums of one entry per nibble: the bit
 // permutation between the step's index space and each operand's layout is
 // resolved by table lookups instead of bit-by-bit scatters.
+// o[i][v]: the offset in the stored output of the value v of output nibble
+// i (the output index bits scattered through c_pos; only built for steps
+// whose output is not stored in index order).
 struct GatherTabs {
   uint2 c[kNib][16];
   uint2 k[kNib][16];
+  uint32_t o[kNib][16];
 };
 
 // Fills the gather tables of step g: threads first, first + stride, ... of
 // the CTA compute one entry each (no barrier).
 __device__ __forceinline__ void gather_build(const StepGeom& g, GatherTabs& t, int first = threadIdx.x,
                                              int stride = kBlock) {
+  // read once: the table stores below may alias the step record for the compiler
+  const bool ident = g.c_identity != 0;
   for (int e = first; e < 2 * kNib * 16; e += stride) {
     const int field = e >> 7, i = (e >> 4) & (kNib - 1), v = e & 15;
     uint32_t oa = 0, ob = 0;
 #pragma unroll
+    uint32_t oc = 0;
     for (int bit = 0; bit < 4; ++bit) {
       if (!((v >> bit) & 1)) continue;
       const int j = 4 * i + bit;
       int pa = -1, pb = -1;
       if (field == 0) {  // output index bit j: n bits, then m bits, then batch bits
+        if (!ident && j < g.rc) oc |= 1u << g.c_pos[j];
         if (j < g.nn) {
           pb = g.b_pos[g.nb + g.nk + j];
         } else if (j < g.nn + g.nm) {
@@ -80,7 +88,18 @@ __device__ __forceinline__ void gather_build(const StepGeom& g, GatherTabs& t, i
       if (pb >= 0) ob |= 1u << pb;
     }
     (field ? t.k : t.c)[i][v] = make_uint2(oa, ob);
+    if (field == 0 && !ident) t.o[i][v] = oc;
   }
+}
+
+// Offset of output index c in the stored output of step g (the gather
+// tables' o part, or c itself for an output stored in index order).
+__device__ __forceinline__ uint32_t out_offset(const StepGeom& g, const GatherTabs& t, uint32_t c) {
+  if (g.c_identity) return c;
+  uint32_t r = 0;
+  const int nn = nibbles(g.rc);
+  for (int i = 0; i < nn; ++i) r += t.o[i][(c >> (4 * i)) & 15u];
+  return r;
 }
 
 // (offset in A, offset in B) of index x from nnib nibble tables.

@@ -81,6 +81,8 @@ struct Stages {
 };
 
 // Index part of a tile's shared memory (same place for every element type).
+// offCm / offCn: stored-output offsets of the tile's rows (with the batch)
+// and columns, for outputs not stored in index order.
 template <class C>
 struct TileIdx {
   GatherTabs gt;
@@ -88,6 +90,8 @@ struct TileIdx {
   uint32_t offBn[C::BN];
   uint32_t offAk[C::BK];
   uint32_t offBk[C::BK];
+  uint32_t offCm[C::BM];
+  uint32_t offCn[C::BN];
 };
 
 template <class SR, class C>
@@ -118,6 +122,11 @@ __device__ __forceinline__ void tile_tables(const StepGeom& g, TileIdx<C>& ix, i
   for (int i = first; i < BM; i += stride)
     ix.offAm[i] = m0 + i < M ? gather(ix.gt.c, ncn, cb | ((m0 + i) << g.nn)).x : 0u;
   for (int i = first; i < BN; i += stride) ix.offBn[i] = n0 + i < N ? gather(ix.gt.c, ncn, cb | (n0 + i)).y : 0u;
+  if (!g.c_identity) {
+    for (int i = first; i < BM; i += stride)
+      ix.offCm[i] = m0 + i < M ? out_offset(g, ix.gt, cb | ((m0 + i) << g.nn)) : 0u;
+    for (int i = first; i < BN; i += stride) ix.offCn[i] = n0 + i < N ? out_offset(g, ix.gt, n0 + i) : 0u;
+  }
   for (int i = first; i < BK; i += stride) {
     const uint2 o = gather(ix.gt.k, nkn, static_cast<uint32_t>(i) < K ? static_cast<uint32_t>(i) : 0u);
     ix.offAk[i] = o.x;
@@ -164,6 +173,42 @@ __device__ __forceinline__ void tile_offsets(const StepGeom& g, TileIdx<C>& ix, 
   tile_slots<C>(g, ix, tm, tn_, offA, offB);
 }
 
+// Vector staging.  kVecA / kVecB: the operand's two lowest stored bits are
+// the step's m (resp. n) bits 0 and 1, it is an arena tensor and its entry
+// offset is a multiple of 4 -- then every group of 4 consecutive m (n) of a
+// staged row is one aligned 16-byte run in memory, and a thread stages it
+// with one 16-byte cp.async instead of four 4-byte ones.  Slot s of a chunk
+// is the 4-element group starting at element 4 s of the [k][m] ([k][n])
+// staging array.
+constexpr int kVecA = 1, kVecB = 2;
+
+template <int ROW, int ELEMS>
+struct VecSlots {
+  static constexpr int total = ELEMS / 4;                       // 4-element groups per chunk
+  static constexpr int per_thread = (total + kBlock - 1) / kBlock;
+};
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+
+// This thread's 16-byte staging slots of one operand (ROW = BM or BN): the
+// offset of each slot's first element, -1 for slots outside the operand
+// (M / N or K padding) or beyond the chunk.
+template <int ROW, int BK, int NS>
+__device__ __forceinline__ void tile_slots4(const uint32_t* off_row, const uint32_t* off_k, uint32_t row0,
+                                            uint32_t rows, uint32_t kvalid, int32_t* off4) {
+  constexpr int total = BK * ROW / 4;
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    const int s = threadIdx.x + kBlock * j;
+    const int e = 4 * s, kk = e / ROW, rr = e % ROW;
+    const bool ok = s < total && (row0 + rr < rows) && (static_cast<uint32_t>(kk) < kvalid);
+    off4[j] = ok ? static_cast<int32_t>(off_row[rr] + off_k[kk]) : -1;
+  }
+}
+
 // Offsets (in A, in B) of the chunk of k rows starting at k0 (a multiple of
 // BK: its bits are disjoint from those of the rows inside the chunk).
 template <class C>
@@ -208,7 +253,8 @@ template <class SR, class C, int FOLD, bool CG>
 __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& A, const Operand& B,
                                               const ModParams& mp, int64_t b, int64_t tm, int64_t tn_,
                                               int64_t kbeg, int64_t kend, TileSmem<SR, C>& sm,
-                                              typename SR::Acc (&acc)[C::TM][C::TN], bool ready = false) {
+                                              typename SR::Acc (&acc)[C::TM][C::TN], bool ready = false,
+                                              int vec = 0) {
   using Val = typename SR::Val;
   using T = Tiled<SR>;
   constexpr int kStages = Stages<SR>::v;
@@ -219,6 +265,12 @@ __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& 
 
   int32_t offA[C::EA], offB[C::EB];
   tile_offsets<C>(g, sm.idx, b, tm, tn_, offA, offB, ready);
+  // 16-byte slots (only for 4-byte elements of arena operands); their
+  // offsets replace the first per-element offsets once the padding is set
+  constexpr int NSA = VecSlots<BM, BK * BM>::per_thread, NSB = VecSlots<BN, BK * BN>::per_thread;
+  static_assert(NSA <= C::EA && NSB <= C::EB, "a 16-byte slot covers four staged elements");
+  const bool va = sizeof(Val) == 4 && (vec & kVecA) && A.kind == kOpArena;
+  const bool vb = sizeof(Val) == 4 && (vec & kVecB) && B.kind == kOpArena;
 
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -235,26 +287,48 @@ __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& 
   for (int j = 0; j < C::EB; ++j)
     if (offB[j] < 0)
       for (int st = 0; st < kStages; ++st) sm.Bs[st][tid + kBlock * j] = T::zero_val();
+  {
+    const uint32_t K = 1u << g.nk, kvalid = K < BK ? K : BK;
+    if (va) tile_slots4<BM, BK, NSA>(sm.idx.offAm, sm.idx.offAk, static_cast<uint32_t>(tm) * BM, 1u << g.nm, kvalid, offA);
+    if (vb) tile_slots4<BN, BK, NSB>(sm.idx.offBn, sm.idx.offBk, static_cast<uint32_t>(tn_) * BN, 1u << g.nn, kvalid, offB);
+  }
 
   // stage the chunk starting at k0 into buffer st: cp.async for stored
-  // operands, plain loads for leaves generated on the fly
+  // operands (16-byte runs where the layout allows), plain loads for leaves
+  // generated on the fly
   const bool a_async = A.kind == kOpArena, b_async = B.kind == kOpArena;
   auto issue = [&](int st, int64_t k0) {
     const uint2 kb = tile_chunk_base<C>(g, sm.idx, k0);
+    if (va) {
 #pragma unroll
-    for (int j = 0; j < C::EA; ++j)
-      if (offA[j] >= 0) {
-        const uint32_t e = static_cast<uint32_t>(offA[j]) + kb.x;
-        if (a_async) SR::copy_async(&sm.As[st][tid + kBlock * j], A, e);
-        else sm.As[st][tid + kBlock * j] = SR::template load<CG>(A, e);
-      }
+      for (int j = 0; j < NSA; ++j)
+        if (offA[j] >= 0)
+          cp_async16(&sm.As[st][4 * (tid + kBlock * j)],
+                     static_cast<const Val*>(A.p0) + (static_cast<uint32_t>(offA[j]) + kb.x));
+    } else {
 #pragma unroll
-    for (int j = 0; j < C::EB; ++j)
-      if (offB[j] >= 0) {
-        const uint32_t e = static_cast<uint32_t>(offB[j]) + kb.y;
-        if (b_async) SR::copy_async(&sm.Bs[st][tid + kBlock * j], B, e);
-        else sm.Bs[st][tid + kBlock * j] = SR::template load<CG>(B, e);
-      }
+      for (int j = 0; j < C::EA; ++j)
+        if (offA[j] >= 0) {
+          const uint32_t e = static_cast<uint32_t>(offA[j]) + kb.x;
+          if (a_async) SR::copy_async(&sm.As[st][tid + kBlock * j], A, e);
+          else sm.As[st][tid + kBlock * j] = SR::template load<CG>(A, e);
+        }
+    }
+    if (vb) {
+#pragma unroll
+      for (int j = 0; j < NSB; ++j)
+        if (offB[j] >= 0)
+          cp_async16(&sm.Bs[st][4 * (tid + kBlock * j)],
+                     static_cast<const Val*>(B.p0) + (static_cast<uint32_t>(offB[j]) + kb.y));
+    } else {
+#pragma unroll
+      for (int j = 0; j < C::EB; ++j)
+        if (offB[j] >= 0) {
+          const uint32_t e = static_cast<uint32_t>(offB[j]) + kb.y;
+          if (b_async) SR::copy_async(&sm.Bs[st][tid + kBlock * j], B, e);
+          else sm.Bs[st][tid + kBlock * j] = SR::template load<CG>(B, e);
+        }
+    }
   };
 #pragma unroll
   for (int st = 0; st < kStages - 1; ++st) {
@@ -413,9 +487,13 @@ template <class C, bool CG>
 __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const Operand& A, const Operand& B,
                                                        const ModParams& mp, int64_t b, int64_t tm, int64_t tn_,
                                                        int64_t kbeg, int64_t kend, unsigned char* smem_raw,
-                                                       CntVal (&acc)[C::TM][C::TN], bool ready = false) {
+                                                       CntVal (&acc)[C::TM][C::TN], bool ready = false,
+                                                       int vec = 0) {
   constexpr int BM = C::BM, BN = C::BN, BK = C::BK, TM = C::TM, TN = C::TN;
   constexpr int kSt = Stages<SrCnt>::v;
+  constexpr int NSA = VecSlots<BM, BK * BM>::per_thread, NSB = VecSlots<BN, BK * BN>::per_thread;
+  static_assert(NSA <= C::EA && NSB <= C::EB, "a 16-byte slot covers four staged elements");
+  const bool va = (vec & kVecA) && A.kind == kOpArena, vb = (vec & kVecB) && B.kind == kOpArena;
   auto& sm = *reinterpret_cast<TileSmemCnt<C>*>(smem_raw);
   const int tid = threadIdx.x;
   const int grp = tid / C::GT, gt = tid % C::GT;
@@ -437,6 +515,13 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
         sm.Bv[st][tid + kBlock * j] = kNegInf;
         sm.Bc[st][tid + kBlock * j] = 0ull;
       }
+  {
+    // 16-byte slots (see tile_mainloop): four values, and four counts in two
+    // 16-byte halves
+    const uint32_t K = 1u << g.nk, kvalid = K < BK ? K : BK;
+    if (va) tile_slots4<BM, BK, NSA>(sm.idx.offAm, sm.idx.offAk, static_cast<uint32_t>(tm) * BM, 1u << g.nm, kvalid, offA);
+    if (vb) tile_slots4<BN, BK, NSB>(sm.idx.offBn, sm.idx.offBk, static_cast<uint32_t>(tn_) * BN, 1u << g.nn, kvalid, offB);
+  }
 
   int32_t vmax[TM][TN];
   uint64_t cnt[TM][TN];
@@ -451,9 +536,20 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
   const bool a_async = A.kind == kOpArena, b_async = B.kind == kOpArena;
   auto issue = [&](int st, int64_t k0) {
     const uint2 kb = tile_chunk_base<C>(g, sm.idx, k0);
+    if (va) {
+#pragma unroll
+      for (int j = 0; j < NSA; ++j)
+        if (offA[j] >= 0) {
+          const uint32_t e = static_cast<uint32_t>(offA[j]) + kb.x;
+          const int d = 4 * (tid + kBlock * j);
+          cp_async16(&sm.Av[st][d], static_cast<const int32_t*>(A.p0) + e);
+          cp_async16(&sm.Ac[st][d], static_cast<const uint64_t*>(A.p1) + e);
+          cp_async16(&sm.Ac[st][d + 2], static_cast<const uint64_t*>(A.p1) + e + 2);
+        }
+    }
 #pragma unroll
     for (int j = 0; j < C::EA; ++j)
-      if (offA[j] >= 0) {
+      if (!va && offA[j] >= 0) {
         const uint32_t e = static_cast<uint32_t>(offA[j]) + kb.x;
         if (a_async) {
           cp_async4(&sm.Av[st][tid + kBlock * j], static_cast<const int32_t*>(A.p0) + e);
@@ -464,9 +560,20 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
           sm.Ac[st][tid + kBlock * j] = v.c;
         }
       }
+    if (vb) {
+#pragma unroll
+      for (int j = 0; j < NSB; ++j)
+        if (offB[j] >= 0) {
+          const uint32_t e = static_cast<uint32_t>(offB[j]) + kb.y;
+          const int d = 4 * (tid + kBlock * j);
+          cp_async16(&sm.Bv[st][d], static_cast<const int32_t*>(B.p0) + e);
+          cp_async16(&sm.Bc[st][d], static_cast<const uint64_t*>(B.p1) + e);
+          cp_async16(&sm.Bc[st][d + 2], static_cast<const uint64_t*>(B.p1) + e + 2);
+        }
+    }
 #pragma unroll
     for (int j = 0; j < C::EB; ++j)
-      if (offB[j] >= 0) {
+      if (!vb && offB[j] >= 0) {
         const uint32_t e = static_cast<uint32_t>(offB[j]) + kb.y;
         if (b_async) {
           cp_async4(&sm.Bv[st][tid + kBlock * j], static_cast<const int32_t*>(B.p0) + e);

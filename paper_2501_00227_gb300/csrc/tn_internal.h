@@ -104,9 +104,12 @@ int build_plan(int32_t n, const int32_t* edges, int32_t m, const int32_t* order,
 int greedy_order(int32_t n, const int32_t* edges, int32_t m, double alpha, int32_t nrepeat,
                  uint64_t seed, int32_t* order_out);
 // Label classification of one pairwise step (shared by build_plan and
-// tn_contract_pair): fills geometry and the output label order.
+// tn_contract_pair): fills geometry and the output label order (N, M,
+// batch).  Labels of each class are numbered in their operand's storage
+// order, except that N labels listed in n_first (if given) come first.
 int classify_step(const std::vector<int32_t>& la, const std::vector<int32_t>& lb,
-                  const std::vector<int32_t>& lc_set, StepGeom* g, std::vector<int32_t>* lc_order);
+                  const std::vector<int32_t>& lc_set, StepGeom* g, std::vector<int32_t>* lc_order,
+                  const std::vector<int32_t>* n_first = nullptr);
 
 // Bytes per entry summed over the per-entry regions of a semiring.
 size_t bytes_per_entry(tn_semiring_t s, int32_t nprimes);

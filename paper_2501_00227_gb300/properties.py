@@ -11,10 +11,14 @@ interpolation, CRT):
                          repeated by multiplicity, ascending (SizeMax(k), an
                          ExtendedTropical{k} in the paper).
 
-The paper computes both with dedicated element types in one contraction;
-here they are read off the exact polynomial, which costs alpha + 1
-evaluations per prime instead of one wider contraction but gives the same
-numbers (counts are exact integers, not saturated).
+Both also have dedicated element types (the paper's route, one
+contraction): ``Plan.kbest("size_max" | "counting_max", k)`` for k up to
+TN_KBEST_MAX on unit-weight networks (tn_contract_kbest), whose counts are
+uint64 (saturating) and whose CountingMax(k) lists the k highest orders
+including zero coefficients.  The functions here read the same numbers off
+the exact polynomial instead, which costs alpha + 1 evaluations per prime,
+takes any k and vertex weights, keeps exact counts, and lists the k highest
+orders with nonzero coefficients.
 
 SingleConfigMax(k) (single_config_max_k): k distinct sets with the k
 largest sizes or total weights, by Lawler's partition of the solution space

@@ -22,6 +22,9 @@ from . import build as _build
 
 TN_OK, TN_EINVAL, TN_ENOMEM, TN_EOVERFLOW, TN_ETIMEOUT, TN_EAGAIN, TN_ECUDA = 0, -1, -2, -3, -4, -5, -6
 TN_TROPICAL_F32, TN_TROPICAL_I32, TN_COUNTING_TROPICAL, TN_COUNT_MODP = 1, 2, 3, 4
+TN_SIZE_MAX_K, TN_COUNTING_MAX_K = 5, 6
+TN_KBEST_MAX = 4
+KBEST = {"size_max": TN_SIZE_MAX_K, "counting_max": TN_COUNTING_MAX_K}
 TN_I32_NEG_INF = -(1 << 30)
 TN_MAX_PRIMES = 16
 TN_RAW_BYTES = 128
@@ -106,6 +109,9 @@ def lib():
                                         i32p, ctypes.POINTER(tn_result_t)]
         L.tn_contract_static.argtypes = [vp, ctypes.c_int, u32p, i32, vp, ctypes.POINTER(tn_result_t)]
         L.tn_tune_set.argtypes = [i32p, i32]
+        L.tn_kbest_workspace_bytes.argtypes = [vp, ctypes.c_int, i32, ctypes.POINTER(u64)]
+        L.tn_contract_kbest.argtypes = [vp, ctypes.c_int, i32, vp, ctypes.c_size_t, vp, i32p,
+                                        ctypes.POINTER(u64), i32p]
         L.tn_modp_gemm_limb.argtypes = [u32p, i32, vp, vp, vp, i32, i32, i32, i32, vp]
         L.tn_modp_gemm_umma.argtypes = [u32p, i32, vp, vp, vp, i32, i32, i32, i32, vp]
         L.tn_plan_step_info.argtypes = [vp, ctypes.c_int, i32, i32p, i32]
@@ -286,6 +292,35 @@ def tn_contract_trace(plan, semiring, primes, ws_ptr: int, ws_bytes: int, stream
                                    ctypes.c_void_p(stream), ctypes.c_void_p(trace_ptr), _p32(ts), _p32(tk),
                                    _p32(lv), ctypes.byref(r)), "tn_contract_trace")
     return result_dict(r, semiring), ts, tk, lv
+
+
+def _kb(kind):
+    return KBEST[kind] if isinstance(kind, str) else int(kind)
+
+
+def tn_kbest_workspace_bytes(plan, kind, k: int) -> int:
+    """Workspace bytes of tn_contract_kbest (kind 'size_max' or 'counting_max')."""
+    out = ctypes.c_uint64()
+    _check(lib().tn_kbest_workspace_bytes(plan, _kb(kind), int(k), ctypes.byref(out)), "tn_kbest_workspace_bytes")
+    return int(out.value)
+
+
+def tn_contract_kbest(plan, kind, k: int, ws_ptr: int, ws_bytes: int, stream: int) -> dict:
+    """SizeMax(k) / CountingMax(k) in one contraction (Sec. 5.3, Table 1).
+    'size_max': {"values": the k largest set sizes (None for -inf)};
+    'counting_max': {"max": alpha, "counts": [c_alpha, c_(alpha-1), ...]};
+    both with "status"."""
+    vals = np.zeros(max(int(k), 1), dtype=np.int32)
+    cnts = np.zeros(max(int(k), 1), dtype=np.uint64)
+    status = ctypes.c_int32()
+    _check(lib().tn_contract_kbest(plan, _kb(kind), int(k), ctypes.c_void_p(ws_ptr), ws_bytes,
+                                   ctypes.c_void_p(stream), _p32(vals),
+                                   cnts.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), ctypes.byref(status)),
+           "tn_contract_kbest")
+    if _kb(kind) == TN_SIZE_MAX_K:
+        return {"status": int(status.value), "values": [None if v == -2**31 else int(v) for v in vals[:k]]}
+    d = int(vals[0])
+    return {"status": int(status.value), "max": None if d == -2**31 else d, "counts": [int(c) for c in cnts[:k]]}
 
 
 TN_STATIC_WORKSPACE_BYTES = 64 * 1024 * 1024
@@ -764,6 +799,16 @@ class Plan:
         st = stream if stream is not None else torch.cuda.current_stream()
         return tn_contract(self.handle, semiring, primes, workspace.data_ptr(), workspace.numel(),
                            st.cuda_stream)
+
+    def kbest(self, kind, k: int, workspace=None, stream=None) -> dict:
+        """SizeMax(k) ('size_max') or CountingMax(k) ('counting_max') in one
+        contraction (tn_contract_kbest)."""
+        import torch
+        need = tn_kbest_workspace_bytes(self.handle, kind, k)
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        return tn_contract_kbest(self.handle, kind, k, workspace.data_ptr(), workspace.numel(), st.cuda_stream)
 
     def evaluate(self, primes, xs, workspace=None, stream=None) -> list:
         """I(G, xs[q]) mod primes[q] for every slot (tn_contract_modp_x)."""
