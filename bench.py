@@ -141,9 +141,9 @@ INT32_PER_CLK_SM = 64
 # instructions executed x 32 / (tc x primes)), from the ncu captures kept
 # under profiles/ (one launch on random 3-regular n = 140).
 INSTR_PER_OP = {
-    "tropical_i32": {"value": None, "profile": None},
-    "counting": {"value": 18.6, "profile": "profiles/k_exec_counting_reg3_n140_s3.md"},
-    "modp": {"value": 118.0e6 * 32 / 5.1e8, "profile": "profiles/k_exec_modp_reg3_n140.md"},
+    "tropical_i32": {"value": 51.48e6 * 32 / 4.423e8, "profile": "profiles/k_exec_tropical_i32_reg3_n140.md"},
+    "counting": {"value": 200.54e6 * 32 / 4.423e8, "profile": "profiles/k_exec_counting_reg3_n140_s3.md"},
+    "modp": {"value": 251.11e6 * 32 / (3 * 4.423e8), "profile": "profiles/k_exec_modp_reg3_n140.md"},
 }
 
 
