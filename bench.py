@@ -137,6 +137,15 @@ def load_peaks():
 SMS = 152
 INT32_PER_CLK_SM = 64
 
+# DRAM bytes (read + write) per executor launch over the bench workload:
+# one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum for every
+# launch of the small bench command (profiles/launches_bench_reg3_n100_n140.md),
+# averaged per instantiation.  Null once a kernel changes after the capture.
+DRAM_BYTES_PER_LAUNCH = {
+    "tropical_i32": 0.4e6, "counting": 56.7e6, "modp": 28.4e6,
+    "profile": "profiles/launches_bench_reg3_n100_n140.md",
+}
+
 # Thread instructions per semiring multiply-add of each executor (warp
 # instructions executed x 32 / (tc x primes)), from the ncu captures kept
 # under profiles/ (one launch on random 3-regular n = 140).
@@ -876,8 +885,17 @@ def run_tn(args):
     peak = max(issue_peak, alu["maxplus"])
     achieved = dom_ops / (dom_ms * 1e-3) / 1e12
     per_tops = {k: v[1] / (v[0] * 1e-3) / 1e12 for k, v in per.items()}
+    # algorithmic bytes of one launch of the dominant kernel: every operand and
+    # output entry of every step once (rwc entries, Sec. 4.1) x entry bytes,
+    # averaged over its launches
+    ebytes = {"tropical_i32": 4, "counting": 12, "modp": 4 * len(PRIMES3)}[dom_sr]
+    alg_bytes = statistics.mean(p.info(sr, len(pr) if pr else 1)["rwc"] * ebytes
+                                for p, sr, pr, _, _ in jobs if sr == dom_sr)
     roofline = {"bound": "alu", "kernel": f"k_exec<{dom_sr}>", "achieved": achieved, "peak": peak,
-                "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                "unit": "Tops/s", "frac": achieved / peak, "traffic": DRAM_BYTES_PER_LAUNCH[dom_sr],
+                "traffic_basis": "DRAM bytes read + written per launch of this kernel, mean over the bench "
+                                 "workload's launches, one ncu capture (" + DRAM_BYTES_PER_LAUNCH["profile"] + ")",
+                "algorithmic_bytes_per_launch": alg_bytes,
                 "peak_basis": f"int32 issue bound: {SMS} SMs x {INT32_PER_CLK_SM} int32 instr/clk/SM x "
                               f"{clock_mhz:.0f} MHz (max SM clock) = {issue_peak:.2f} Tops/s, or the "
                               f"register-only __viaddmax_s32 rate {alu['maxplus']:.2f} Tops/s measured in this "
