@@ -79,9 +79,23 @@ int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods_v, void* ws,
   const dev::ModTable& mods = *static_cast<const dev::ModTable*>(mods_v);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ws);
-  if (cudaMemsetAsync(w, 0, X->ctr_off + X->ctr_bytes, st) != cudaSuccess) return TN_ECUDA;
   dev::ExecArgs a;
   std::memset(&a, 0, sizeof(a));
+  // clear the header and counters: in the kernel (launch gate) unless the
+  // launch is being captured into a graph, whose replays would reuse the
+  // epoch -- then with a memset node before it
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return TN_ECUDA;
+  if (cap == cudaStreamCaptureStatusNone && X->ctr_off == kHeaderBytes) {
+    static std::atomic<unsigned long long> epoch{0x9e3779b97f4a7c15ull ^ reinterpret_cast<uintptr_t>(&epoch)};
+    unsigned long long e;
+    do e = epoch.fetch_add(1, std::memory_order_relaxed) + 1; while (e == 0);
+    a.epoch = e;
+    a.ws = reinterpret_cast<uint32_t*>(w);
+    a.ctr_words = static_cast<int32_t>(X->ctr_bytes / 4);
+  } else if (cudaMemsetAsync(w, 0, X->ctr_off + X->ctr_bytes, st) != cudaSuccess) {
+    return TN_ECUDA;
+  }
   const int ns = static_cast<int>(X->steps.size());
   const char* tables = static_cast<const char*>(d_tables);
   a.steps = reinterpret_cast<const ExecStep*>(tables + X->off_steps);

@@ -50,8 +50,18 @@ struct ExecArgs {
   unsigned long long timeout_ns;
   unsigned long long* trace;  // optional: 8 words per task (see tn_contract_trace)
   int32_t nraw;               // raw result slots (networks in the launch)
-  int32_t pad2_;
+  int32_t ctr_words;          // launch gate: 4-byte counter words at byte kHeaderBytes of the workspace
+  uint32_t* ws;               // launch gate: the workspace (header, then counters)
+  unsigned long long epoch;   // launch gate: nonzero = CTA 0 clears the header and counters itself
 };
+
+// Launch gate.  Instead of a host memset before the launch, CTA 0 clears the
+// workspace header (status word, result block) and the task counters, then
+// publishes the launch's epoch (unique per launch in the process) in the
+// header's gate word; every CTA waits for that epoch (acquire, bounded by 2 s)
+// before it claims a task.  A stale gate word can never match: it holds an
+// earlier launch's epoch.
+constexpr int kGateByte = 248;  // after the result block at 64..191, before the counters at kHeaderBytes
 
 constexpr uint32_t kStatusTimeout = 1u;
 
@@ -440,6 +450,23 @@ __device__ __forceinline__ void exec_naive_task_q(const ExecArgs& a, const ExecS
     if (rr == 0 && cl < chunk && c < c1) SR::store(C, out_offset(g, sm.gt, static_cast<uint32_t>(c)), v, mp);
     return;
   }
+  if (chunk == 1) {
+    // one entry (a step summing every label, e.g. the last one) from many
+    // partials: every thread merges a strided share, then warps and the CTA
+    Acc v = SR::zero(mp);
+    for (int rr = threadIdx.x; rr < ks; rr += kBlock) SR::merge(v, ldcg_acc(part + rr), mp);
+    for (int off = 16; off >= 1; off >>= 1) {
+      Acc o = shfl_xor_val(v, off);
+      SR::merge(v, o, mp);
+    }
+    if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kBlock / 32; ++w) SR::merge(v, sm.red[w], mp);
+      SR::store(C, out_offset(g, sm.gt, static_cast<uint32_t>(c0)), v, mp);
+    }
+    return;
+  }
   for (int32_t c = c0 + threadIdx.x; c < c1; c += kBlock) {
     Acc v = ldcg_acc(part + (c - c0));
 #pragma unroll 4
@@ -599,6 +626,36 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
   // shared memory (-1: none, e.g. after a group task)
   int cur_step = -1;
   if (tid == 0) s_abort = 0;
+  if (a.epoch) {
+    unsigned long long* gate = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(a.ws) + kGateByte);
+    if (blockIdx.x == 0) {
+      for (int i = tid; i < kGateByte / 4; i += kBlock) a.ws[i] = 0u;
+      for (int i = tid; i < a.ctr_words; i += kBlock) a.ws[kHeaderBytes / 4 + i] = 0u;
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(gate), "l"(a.epoch) : "memory");
+      }
+    }
+    if (tid == 0) {
+      const unsigned long long t0 = global_ns();
+      for (;;) {
+        unsigned long long e;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(e) : "l"(gate) : "memory");
+        if (e == a.epoch) break;
+        // CTA 0 is resident and opens the gate within microseconds; after 2 s
+        // (whatever the dependency wait limit) this CTA claims nothing, and
+        // the others still complete the contraction
+        if (global_ns() - t0 > 2000000000ull) {
+          s_abort = 1;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __syncthreads();
+    if (s_abort) return;
+  }
   for (;;) {
     if (tid == 0) {
       if (a.trace) s_tr[0] = global_ns();
