@@ -148,6 +148,8 @@ int build_batch_plan(tn_plan_s* const* plans, int32_t count, tn_semiring_t semir
   M.arena_entries = std::max<int64_t>(arena, kArenaAlign);
   M.net_arena_base = arena_base;
   M.stored_leaves = stored_leaves;
+  M.value_bound = 0;
+  for (int i = 0; i < count; ++i) M.value_bound = std::max(M.value_bound, xs[i]->value_bound);
   M.leaf_base = count ? xs[0]->leaf_base : 0;
   M.scratch_bytes = scratch;
   M.n_arrive = static_cast<int32_t>(arrive);

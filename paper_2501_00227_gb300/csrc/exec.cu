@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -12,13 +13,29 @@
 
 namespace tn {
 
+namespace {
+// Whether int32 tropical launches of X may use the packed 16-bit tile
+// (TN_PACKED=0 in the environment keeps the int32 tile, for measurement
+// and tests).
+bool use_packed(const ExecPlan* X) {
+  static const bool off = [] {
+    const char* e = getenv("TN_PACKED");
+    return e && e[0] == '0';
+  }();
+  return !off && X->value_bound <= dev::kPackedMax;
+}
+}  // namespace
+
 int exec_prepare_launch(tn_semiring_t s, const void* mods_v) {
   const dev::ModTable& mods = *static_cast<const dev::ModTable*>(mods_v);
   size_t smem;
   int r = 0;
   switch (s) {
     case TN_TROPICAL_F32: r = dev::exec_resident<dev::SrF32, 1>(&smem); break;
-    case TN_TROPICAL_I32: r = dev::exec_resident<dev::SrI32, 1>(&smem); break;
+    case TN_TROPICAL_I32:
+      r = dev::exec_resident<dev::SrI32, 1>(&smem);
+      if (r >= 0) r = dev::exec_resident<dev::SrI32, dev::kPackedI16>(&smem);
+      break;
     case TN_COUNTING_TROPICAL: r = dev::exec_resident<dev::SrCnt, 1>(&smem); break;
     case TN_COUNT_MODP: {
       bool small_r = true;
@@ -126,7 +143,9 @@ int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods_v, void* ws,
     case TN_SIZE_MAX_K:
     case TN_COUNTING_MAX_K: return kbest_launch(X, s, &a, st);
     case TN_TROPICAL_F32: return dev::exec_launch_t<dev::SrF32, 1>(X, a, st);
-    case TN_TROPICAL_I32: return dev::exec_launch_t<dev::SrI32, 1>(X, a, st);
+    case TN_TROPICAL_I32:
+      return use_packed(X) ? dev::exec_launch_t<dev::SrI32, dev::kPackedI16>(X, a, st)
+                           : dev::exec_launch_t<dev::SrI32, 1>(X, a, st);
     case TN_COUNTING_TROPICAL: return dev::exec_launch_t<dev::SrCnt, 1>(X, a, st);
     case TN_COUNT_MODP: {
       bool small_r = true;

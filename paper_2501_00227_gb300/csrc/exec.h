@@ -14,6 +14,7 @@
 // aborts the whole launch with TN_ETIMEOUT.
 #pragma once
 
+#include <climits>
 #include <cstdint>
 #include <mutex>
 #include <vector>
@@ -83,6 +84,10 @@ struct ExecPlan {
   bool batched = false;              // built for a batch / served group
   bool keep = false;                 // every intermediate keeps its own arena block (no reuse)
   bool stored_leaves = false;        // leaf operands are arena tensors at leaf_base (weighted networks)
+  // largest |finite value| any tropical tensor of the plan can hold: the
+  // vertex count for unit-weight networks (an independent set's size), else
+  // unbounded (stored leaves carry arbitrary weights)
+  int64_t value_bound = INT64_MAX;
   int64_t leaf_base = 0;             // arena entry offset of the leaf tensors (plan leaf_off within)
   std::vector<int64_t> net_arena_base;  // merged plans: arena entry offset of each network
   int64_t arena_entries = 0;

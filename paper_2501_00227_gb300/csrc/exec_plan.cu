@@ -570,6 +570,7 @@ ExecPlan* exec_plan_get_h(tn_plan_s* p, tn_semiring_t s, int32_t nprimes, int H,
   X->batched = batched;
   X->keep = keep;
   X->stored_leaves = stored_leaves;
+  X->value_bound = stored_leaves ? INT64_MAX : p->n;
   X->tune_gen = tune_generation();
   *rc = build_exec(p, s, nprimes, X.get());
   if (*rc != TN_OK) return nullptr;

@@ -6,6 +6,9 @@
 //   kind 1  mod-p multiply-add: acc += a * b on a 64-bit accumulator, its
 //           high word folded back (acc = hi * (2^32 mod p) + lo) every third
 //           term (the mod-p tile's inner step)
+//   kind 2  (max,+) multiply-add on two int16 lanes: acc = max(acc, a + b)
+//           per 16-bit half, one __viaddmax_s16x2 per two terms (the packed
+//           tropical tile's inner step)
 //
 // Every thread runs 16 independent chains for `iters` terms each, so the
 // pipes, not the latencies, bound the loop; a term is one semiring
@@ -34,6 +37,25 @@ __global__ void __launch_bounds__(256) k_peak_maxplus(int iters, int32_t seed, i
     for (int j = 0; j < kChains; ++j) acc[j] = __viaddmax_s32(ai, b[j], acc[j]);
   }
   int32_t r = 0;
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) r ^= acc[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+__global__ void __launch_bounds__(256) k_peak_maxplus2(int iters, int32_t seed, uint32_t* out) {
+  uint32_t acc[kChains], b[kChains];
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) {
+    acc[j] = static_cast<uint32_t>(seed + j) + threadIdx.x;
+    b[j] = static_cast<uint32_t>(seed) * (j + 1);
+  }
+  const uint32_t a = static_cast<uint32_t>(seed) ^ blockIdx.x;
+  for (int i = 0; i < iters; ++i) {
+    const uint32_t ai = a ^ (static_cast<uint32_t>(i) * 2654435761u);  // shared by 16 instructions
+#pragma unroll
+    for (int j = 0; j < kChains; ++j) acc[j] = __viaddmax_s16x2(ai, b[j], acc[j]);
+  }
+  uint32_t r = 0;
 #pragma unroll
   for (int j = 0; j < kChains; ++j) r ^= acc[j];
   out[blockIdx.x * blockDim.x + threadIdx.x] = r;
@@ -69,7 +91,7 @@ __global__ void __launch_bounds__(256) k_peak_modp(int iters, uint32_t seed, uin
 }  // namespace
 
 extern "C" int tn_alu_peak(int32_t kind, int32_t iters, void* cuda_stream, double* tops_out) {
-  if (!tops_out || (kind != 0 && kind != 1) || iters < 3 || iters > (1 << 24)) return TN_EINVAL;
+  if (!tops_out || kind < 0 || kind > 2 || iters < 3 || iters > (1 << 24)) return TN_EINVAL;
   iters -= iters % 3;
   int dev, sms;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -87,15 +109,17 @@ extern "C" int tn_alu_peak(int32_t kind, int32_t iters, void* cuda_stream, doubl
     cudaEventRecord(e0, st);
     if (kind == 0)
       k_peak_maxplus<<<blocks, threads, 0, st>>>(iters, 12345 + rep, static_cast<int32_t*>(out));
-    else
+    else if (kind == 1)
       k_peak_modp<<<blocks, threads, 0, st>>>(iters, 54321u + rep, 20u, static_cast<uint64_t*>(out));
+    else
+      k_peak_maxplus2<<<blocks, threads, 0, st>>>(iters, 777 + rep, static_cast<uint32_t*>(out));
     cudaEventRecord(e1, st);
     if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
       rc = TN_ECUDA;
   }
   if (rc == TN_OK)
-    *tops_out = double(blocks) * threads * kChains * double(iters) / (double(ms) * 1e-3) / 1e12;
+    *tops_out = double(blocks) * threads * kChains * double(iters) * (kind == 2 ? 2 : 1) / (double(ms) * 1e-3) / 1e12;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(out);

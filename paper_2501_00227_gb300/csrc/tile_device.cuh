@@ -217,10 +217,15 @@ __device__ __forceinline__ uint2 tile_chunk_base(const StepGeom& g, const TileId
 }
 
 // Fragment of T consecutive 4-byte values from shared memory (16-byte
-// vector loads when T is a multiple of 4; the address is 16-byte aligned).
+// vector loads when T is a multiple of 4, the address then 16-byte aligned;
+// one 8-byte load when T = 2, the address 8-byte aligned).
 template <int T, class V>
 __device__ __forceinline__ void load_frag(const V* p, V (&out)[T]) {
-  if constexpr (sizeof(V) == 4 && T % 4 == 0) {
+  if constexpr (sizeof(V) == 4 && T == 2) {
+    const uint2 w = *reinterpret_cast<const uint2*>(p);
+    out[0] = __builtin_bit_cast(V, w.x);
+    out[1] = __builtin_bit_cast(V, w.y);
+  } else if constexpr (sizeof(V) == 4 && T % 4 == 0) {
 #pragma unroll
     for (int i = 0; i < T; i += 4) {
       const uint4 w = *reinterpret_cast<const uint4*>(p + i);
@@ -243,6 +248,51 @@ template <>
 struct Log2<1> {
   static constexpr int v = 0;
 };
+
+// Stages the chunk of k rows starting at k0 into as / bs ([BK][BM] and
+// [BK][BN]): cp.async for stored operands (16-byte runs where the layout
+// allows, see tile_slots4), plain loads for leaves generated on the fly.
+// offA / offB are this thread's element offsets (or its 16-byte slot
+// offsets when va / vb); negative ones are padding and are not written.
+template <class SR, class C, bool CG, int NSA, int NSB>
+__device__ __forceinline__ void tile_stage(const StepGeom& g, const TileIdx<C>& ix, const Operand& A,
+                                           const Operand& B, const int32_t (&offA)[C::EA],
+                                           const int32_t (&offB)[C::EB], bool va, bool vb, typename SR::Val* as,
+                                           typename SR::Val* bs, int64_t k0) {
+  using Val = typename SR::Val;
+  const int tid = threadIdx.x;
+  const uint2 kb = tile_chunk_base<C>(g, ix, k0);
+  if (va) {
+#pragma unroll
+    for (int j = 0; j < NSA; ++j)
+      if (offA[j] >= 0)
+        cp_async16(&as[4 * (tid + kBlock * j)], static_cast<const Val*>(A.p0) + (static_cast<uint32_t>(offA[j]) + kb.x));
+  } else {
+    const bool a_async = A.kind == kOpArena;
+#pragma unroll
+    for (int j = 0; j < C::EA; ++j)
+      if (offA[j] >= 0) {
+        const uint32_t e = static_cast<uint32_t>(offA[j]) + kb.x;
+        if (a_async) SR::copy_async(&as[tid + kBlock * j], A, e);
+        else as[tid + kBlock * j] = SR::template load<CG>(A, e);
+      }
+  }
+  if (vb) {
+#pragma unroll
+    for (int j = 0; j < NSB; ++j)
+      if (offB[j] >= 0)
+        cp_async16(&bs[4 * (tid + kBlock * j)], static_cast<const Val*>(B.p0) + (static_cast<uint32_t>(offB[j]) + kb.y));
+  } else {
+    const bool b_async = B.kind == kOpArena;
+#pragma unroll
+    for (int j = 0; j < C::EB; ++j)
+      if (offB[j] >= 0) {
+        const uint32_t e = static_cast<uint32_t>(offB[j]) + kb.y;
+        if (b_async) SR::copy_async(&bs[tid + kBlock * j], B, e);
+        else bs[tid + kBlock * j] = SR::template load<CG>(B, e);
+      }
+  }
+}
 
 // Accumulates tile (tm, tn) of batch b over k in [kbeg, kend) into acc (of
 // the calling thread's group; the partial tiles of the KG groups are NOT yet
@@ -293,42 +343,8 @@ __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& 
     if (vb) tile_slots4<BN, BK, NSB>(sm.idx.offBn, sm.idx.offBk, static_cast<uint32_t>(tn_) * BN, 1u << g.nn, kvalid, offB);
   }
 
-  // stage the chunk starting at k0 into buffer st: cp.async for stored
-  // operands (16-byte runs where the layout allows), plain loads for leaves
-  // generated on the fly
-  const bool a_async = A.kind == kOpArena, b_async = B.kind == kOpArena;
   auto issue = [&](int st, int64_t k0) {
-    const uint2 kb = tile_chunk_base<C>(g, sm.idx, k0);
-    if (va) {
-#pragma unroll
-      for (int j = 0; j < NSA; ++j)
-        if (offA[j] >= 0)
-          cp_async16(&sm.As[st][4 * (tid + kBlock * j)],
-                     static_cast<const Val*>(A.p0) + (static_cast<uint32_t>(offA[j]) + kb.x));
-    } else {
-#pragma unroll
-      for (int j = 0; j < C::EA; ++j)
-        if (offA[j] >= 0) {
-          const uint32_t e = static_cast<uint32_t>(offA[j]) + kb.x;
-          if (a_async) SR::copy_async(&sm.As[st][tid + kBlock * j], A, e);
-          else sm.As[st][tid + kBlock * j] = SR::template load<CG>(A, e);
-        }
-    }
-    if (vb) {
-#pragma unroll
-      for (int j = 0; j < NSB; ++j)
-        if (offB[j] >= 0)
-          cp_async16(&sm.Bs[st][4 * (tid + kBlock * j)],
-                     static_cast<const Val*>(B.p0) + (static_cast<uint32_t>(offB[j]) + kb.y));
-    } else {
-#pragma unroll
-      for (int j = 0; j < C::EB; ++j)
-        if (offB[j] >= 0) {
-          const uint32_t e = static_cast<uint32_t>(offB[j]) + kb.y;
-          if (b_async) SR::copy_async(&sm.Bs[st][tid + kBlock * j], B, e);
-          else sm.Bs[st][tid + kBlock * j] = SR::template load<CG>(B, e);
-        }
-    }
+    tile_stage<SR, C, CG, NSA, NSB>(g, sm.idx, A, B, offA, offB, va, vb, sm.As[st], sm.Bs[st], k0);
   };
 #pragma unroll
   for (int st = 0; st < kStages - 1; ++st) {
@@ -372,6 +388,188 @@ __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& 
   }
   cp_async_wait<0>();
   __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Packed (max,+) tile for int32 tropical networks with small values.
+// Every finite value of an independent-set network with unit vertex weights
+// is the size of an independent set of a subgraph, an integer in [0, n].
+// When the host proves |finite value| <= kPackedMax for the whole network,
+// two terms run in one __viaddmax_s16x2 (max(a + b, c) on each 16-bit half)
+// and the result is exact:
+//   - a staged value v becomes max(v, kPackedNegInf): finite values are
+//     unchanged, every "-inf" (any int32 below TN_I32_NEG_INF / 2) becomes
+//     -16384;
+//   - finite + finite lies in [-8190, 8190]; a sum with a -inf term lies in
+//     [-32768, -12289], and the accumulator starts at -16384, so no half
+//     ever leaves the int16 range and every accumulated "-inf" stays below
+//     -8192 while every finite maximum stays at or above -8190;
+//   - the epilogue maps halves below -8192 back to TN_I32_NEG_INF.
+// A's staged value a is stored as the pair (a, a) and B's values as pairs
+// (b[n], b[n + 1]), so one instruction updates the two outputs (m, n) and
+// (m, n + 1).  The chunk is staged as int32 by the same cp.async path as the
+// int32 tile; each thread converts the entries it copied itself (its own
+// copies are complete after its cp.async wait), so the chunk still needs a
+// single barrier.  Two packed buffers alternate: the one converted at
+// iteration t + 2 was last read before the barrier of iteration t + 1.
+// ---------------------------------------------------------------------------
+constexpr int32_t kPackedMax = 4095;        // largest |finite value| the packed tile accepts
+constexpr int32_t kPackedNegInf = -16384;   // "-inf" in a 16-bit half
+constexpr int32_t kPackedInfBelow = -8192;  // halves below this are "-inf"
+constexpr int kPackedI16 = 16;              // FOLD argument selecting the packed tile of SrI32
+
+__device__ __forceinline__ uint32_t pk_bcast(int32_t v) {
+  return __byte_perm(static_cast<uint32_t>(max(v, kPackedNegInf)), 0u, 0x1010);
+}
+__device__ __forceinline__ uint32_t pk_pair(int32_t lo, int32_t hi) {
+  return __byte_perm(static_cast<uint32_t>(max(lo, kPackedNegInf)), static_cast<uint32_t>(max(hi, kPackedNegInf)),
+                     0x5410);
+}
+__device__ __forceinline__ int32_t pk_unpack(int32_t h) { return h < kPackedInfBelow ? kNegInf : h; }
+
+template <class C>
+struct TileSmemP {
+  static constexpr int kSt = 3;
+  TileIdx<C> idx;
+  alignas(16) int32_t As[kSt][C::BK * C::BM];        // int32 staging
+  alignas(16) int32_t Bs[kSt][C::BK * C::BN];
+  alignas(16) uint32_t Ap[2][C::BK * C::BM];         // (a, a) pairs
+  alignas(16) uint32_t Bp[2][C::BK * C::BN / 2];     // (b[n], b[n + 1]) pairs
+};
+
+// Converts this thread's staged entries of one chunk (those it copied or
+// generated itself) into the packed buffers ap / bp.
+template <class C, int NSA, int NSB>
+__device__ __forceinline__ void tile_pack(const int32_t* as, const int32_t* bs, uint32_t* ap, uint32_t* bp,
+                                          const int32_t (&offA)[C::EA], const int32_t (&offB)[C::EB], bool va,
+                                          bool vb) {
+  const int tid = threadIdx.x;
+  if (va) {
+#pragma unroll
+    for (int j = 0; j < NSA; ++j)
+      if (offA[j] >= 0) {
+        const int e = 4 * (tid + kBlock * j);
+        const int4 v = *reinterpret_cast<const int4*>(as + e);
+        *reinterpret_cast<uint4*>(ap + e) = make_uint4(pk_bcast(v.x), pk_bcast(v.y), pk_bcast(v.z), pk_bcast(v.w));
+      }
+  } else {
+#pragma unroll
+    for (int j = 0; j < C::EA; ++j)
+      if (offA[j] >= 0) ap[tid + kBlock * j] = pk_bcast(as[tid + kBlock * j]);
+  }
+  if (vb) {
+#pragma unroll
+    for (int j = 0; j < NSB; ++j)
+      if (offB[j] >= 0) {
+        const int e = 4 * (tid + kBlock * j);
+        const int4 v = *reinterpret_cast<const int4*>(bs + e);
+        *reinterpret_cast<uint2*>(bp + e / 2) = make_uint2(pk_pair(v.x, v.y), pk_pair(v.z, v.w));
+      }
+  } else {
+    int16_t* bh = reinterpret_cast<int16_t*>(bp);
+#pragma unroll
+    for (int j = 0; j < C::EB; ++j)
+      if (offB[j] >= 0) bh[tid + kBlock * j] = static_cast<int16_t>(max(bs[tid + kBlock * j], kPackedNegInf));
+  }
+}
+
+// The packed counterpart of tile_mainloop for SrI32 (see above); acc
+// receives int32 values (-inf as TN_I32_NEG_INF) of the calling thread's
+// group, like tile_mainloop's.  All threads of the CTA must call it.
+template <class C, bool CG>
+__device__ __forceinline__ void tile_mainloop_packed(const StepGeom& g, const Operand& A, const Operand& B, int64_t b,
+                                                     int64_t tm, int64_t tn_, int64_t kbeg, int64_t kend,
+                                                     TileSmemP<C>& sm, int32_t (&acc)[C::TM][C::TN],
+                                                     bool ready = false, int vec = 0) {
+  constexpr int kStages = TileSmemP<C>::kSt;
+  constexpr int BM = C::BM, BN = C::BN, BK = C::BK, TM = C::TM, TN = C::TN, TN2 = C::TN / 2;
+  static_assert(TN % 2 == 0 && BN % 2 == 0, "pairs of columns");
+  const int tid = threadIdx.x;
+  const int grp = tid / C::GT, gt = tid % C::GT;
+  const int tx = gt % C::WN, ty = gt / C::WN;
+
+  int32_t offA[C::EA], offB[C::EB];
+  tile_offsets<C>(g, sm.idx, b, tm, tn_, offA, offB, ready);
+  constexpr int NSA = VecSlots<BM, BK * BM>::per_thread, NSB = VecSlots<BN, BK * BN>::per_thread;
+  static_assert(NSA <= C::EA && NSB <= C::EB, "a 16-byte slot covers four staged elements");
+  const bool va = (vec & kVecA) && A.kind == kOpArena;
+  const bool vb = (vec & kVecB) && B.kind == kOpArena;
+
+  // padding entries (outside M / N / K) are -inf in every staging and
+  // packed buffer; nothing writes them afterwards
+#pragma unroll
+  for (int j = 0; j < C::EA; ++j)
+    if (offA[j] < 0) {
+      const int e = tid + kBlock * j;
+      for (int st = 0; st < kStages; ++st) sm.As[st][e] = kNegInf;
+      sm.Ap[0][e] = sm.Ap[1][e] = pk_bcast(kNegInf);
+    }
+#pragma unroll
+  for (int j = 0; j < C::EB; ++j)
+    if (offB[j] < 0) {
+      const int e = tid + kBlock * j;
+      for (int st = 0; st < kStages; ++st) sm.Bs[st][e] = kNegInf;
+      reinterpret_cast<int16_t*>(sm.Bp[0])[e] = static_cast<int16_t>(kPackedNegInf);
+      reinterpret_cast<int16_t*>(sm.Bp[1])[e] = static_cast<int16_t>(kPackedNegInf);
+    }
+  {
+    const uint32_t K = 1u << g.nk, kvalid = K < BK ? K : BK;
+    if (va) tile_slots4<BM, BK, NSA>(sm.idx.offAm, sm.idx.offAk, static_cast<uint32_t>(tm) * BM, 1u << g.nm, kvalid, offA);
+    if (vb) tile_slots4<BN, BK, NSB>(sm.idx.offBn, sm.idx.offBk, static_cast<uint32_t>(tn_) * BN, 1u << g.nn, kvalid, offB);
+  }
+
+  uint32_t acc2[TM][TN2];
+  const uint32_t ninf2 = pk_bcast(kNegInf);
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN2; ++j) acc2[i][j] = ninf2;
+
+  auto issue = [&](int st, int64_t k0) {
+    tile_stage<SrI32, C, CG, NSA, NSB>(g, sm.idx, A, B, offA, offB, va, vb, sm.As[st], sm.Bs[st], k0);
+  };
+#pragma unroll
+  for (int st = 0; st < kStages - 1; ++st) {
+    if (kbeg + st * BK < kend) issue(st, kbeg + st * BK);
+    cp_async_commit();
+  }
+  int cur = 0, pb = 0;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+    cp_async_wait<kStages - 2>();
+    tile_pack<C, NSA, NSB>(sm.As[cur], sm.Bs[cur], sm.Ap[pb], sm.Bp[pb], offA, offB, va, vb);
+    __syncthreads();
+    {
+      // refill the staging buffer this thread converted in the previous
+      // iteration (only its own entries: no other thread reads them)
+      const int64_t kn = k0 + (kStages - 1) * BK;
+      const int nxt = (cur + kStages - 1) % kStages;
+      if (kn < kend) issue(nxt, kn);
+      cp_async_commit();
+    }
+    const uint32_t* Ag = sm.Ap[pb] + grp * C::BKG * BM;
+    const uint32_t* Bg = sm.Bp[pb] + grp * C::BKG * (BN / 2);
+#pragma unroll 2
+    for (int kk = 0; kk < C::BKG; ++kk) {
+      uint32_t a[TM], bv[TN2];
+      load_frag<TM>(Ag + kk * BM + ty * TM, a);
+      load_frag<TN2>(Bg + kk * (BN / 2) + tx * TN2, bv);
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN2; ++j) acc2[i][j] = __viaddmax_s16x2(a[i], bv[j], acc2[i][j]);
+    }
+    cur = (cur + 1) % kStages;
+    pb ^= 1;
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN2; ++j) {
+      acc[i][2 * j] = pk_unpack(static_cast<int32_t>(acc2[i][j] << 16) >> 16);
+      acc[i][2 * j + 1] = pk_unpack(static_cast<int32_t>(acc2[i][j]) >> 16);
+    }
 }
 
 // Merges the KG partial tiles into group 0 (through shared memory `red`,
@@ -424,6 +622,13 @@ constexpr size_t tile_smem_bytes() {
     stage = sizeof(TileSmemCnt<C>) > sizeof(TileSmem<SrI32, C>) ? sizeof(TileSmemCnt<C>) : sizeof(TileSmem<SrI32, C>);
   const size_t merge = tile_merge_off<C>() + sizeof(typename SR::Acc) * (C::KG - 1) * C::BM * C::BN;
   return stage > merge ? stage : merge;
+}
+
+// The same for the packed (max,+) tile.
+template <class C>
+constexpr size_t tile_smem_bytes_packed() {
+  const size_t merge = tile_merge_off<C>() + sizeof(int32_t) * (C::KG - 1) * C::BM * C::BN;
+  return sizeof(TileSmemP<C>) > merge ? sizeof(TileSmemP<C>) : merge;
 }
 
 }  // namespace dev

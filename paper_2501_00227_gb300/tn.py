@@ -701,9 +701,9 @@ def tn_server_completed(server, max_tickets: int = 4096) -> list:
 
 
 def tn_alu_peak(kind: str, iters: int = 1 << 14, stream: int = 0) -> float:
-    """Register-only Tops/s of the "maxplus" or "modp" inner step."""
+    """Register-only Tops/s of the "maxplus", "modp" or "maxplus16x2" inner step."""
     out = ctypes.c_double()
-    _check(lib().tn_alu_peak({"maxplus": 0, "modp": 1}[kind], int(iters), ctypes.c_void_p(stream),
+    _check(lib().tn_alu_peak({"maxplus": 0, "modp": 1, "maxplus16x2": 2}[kind], int(iters), ctypes.c_void_p(stream),
                              ctypes.byref(out)), "tn_alu_peak")
     return float(out.value)
 

@@ -223,6 +223,36 @@ def test_config2_regular_vs_oracle(spec, execu, monkeypatch):
         p.close()
 
 
+@pytest.mark.parametrize("fill", [0x00, 0xFF, 0xA5])
+def test_workspace_contents_do_not_matter(fill):
+    """The executor clears its own counters and header at the start of each
+    launch (no memset before it): a workspace full of any bytes, or left by a
+    different plan, gives the same exact results, launch after launch."""
+    n, e = g.random_regular3(100, 2)
+    p = tn.Plan(n, e, nrepeat=4, seed=1)
+    q = tn.Plan(*g.kings_subgraph(8, 0.8, 1), nrepeat=2, seed=1)
+    pr = tn.PRIMES31[:3]
+    want_size = O.mis_size(n, e, p.order)
+    want_count = O.mis_count(n, e, p.order)
+    want_res = O.count_modp(n, e, p.order, pr)
+    try:
+        need = max(p.workspace_bytes(s, 3) for s in ("tropical_i32", "counting", "modp"))
+        need = max(need, q.workspace_bytes("modp", 3))
+        ws = torch.full((need,), fill, dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            r = tn.tn_contract(p.handle, "tropical_i32", None, ws.data_ptr(), need, _stream())
+            assert r["max"] == want_size
+            r = tn.tn_contract(p.handle, "counting", None, ws.data_ptr(), need, _stream())
+            assert (r["max"], r["count"]) == want_count
+            r = tn.tn_contract(p.handle, "modp", pr, ws.data_ptr(), need, _stream())
+            assert r["residues"] == want_res
+            tn.tn_contract(q.handle, "modp", pr, ws.data_ptr(), need, _stream())
+            ws.fill_(fill)
+    finally:
+        p.close()
+        q.close()
+
+
 def test_square20_count_matches_paper():
     gd = json.load(open(os.path.join(GOLD, "square20.json")))
     n, e = g.square_lattice(20)

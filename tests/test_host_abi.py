@@ -206,7 +206,7 @@ def test_exec_self_check_on_plan_variants(monkeypatch, spec):
         tn.tn_plan_destroy(ps)
 
 
-@pytest.mark.parametrize("kind,iters", [(2, 1024), (-1, 1024), (0, 2), (1, (1 << 24) + 1)])
+@pytest.mark.parametrize("kind,iters", [(3, 1024), (-1, 1024), (0, 2), (1, (1 << 24) + 1)])
 def test_alu_peak_rejects_bad_arguments(kind, iters):
     out = ctypes.c_double()
     assert tn.lib().tn_alu_peak(kind, iters, None, ctypes.byref(out)) == tn.TN_EINVAL
@@ -215,7 +215,8 @@ def test_alu_peak_rejects_bad_arguments(kind, iters):
 @pytest.mark.gpu
 def test_alu_peaks_are_plausible():
     """The register-only rates behind the ALU rooflines: (max,+) near one
-    term per lane per clock (64 per SM), the folded mod-p step slower."""
+    term per lane per clock (64 per SM), the packed 16-bit form near two, the
+    folded mod-p step slower."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -224,6 +225,8 @@ def test_alu_peaks_are_plausible():
     md = tn.tn_alu_peak("modp")
     assert 0.3 * sms * 64 * 1.0e9 / 1e12 < mp < 1.2 * sms * 64 * 2.2e9 / 1e12
     assert 0 < md < mp
+    mp2 = tn.tn_alu_peak("maxplus16x2")
+    assert 1.5 * mp < mp2 < 1.2 * sms * 128 * 2.2e9 / 1e12
 
 
 @pytest.mark.parametrize("ns,ok", [(0, True), (1, True), (2_000_000_000, True), (60_000_000_000, True),
