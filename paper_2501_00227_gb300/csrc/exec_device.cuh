@@ -394,11 +394,9 @@ __device__ __noinline__ void exec_naive_task(const ExecArgs& a, const ExecStep& 
       return;
     }
   }
-  if (task.prime >= 0) {
-    exec_naive_task_q<SR>(a, st, task, task.prime, smem, s_last);
-  } else {
-    for (int q = 0; q < a.nprimes; ++q) exec_naive_task_q<SR>(a, st, task, q, smem, s_last);
-  }
+  // one prime, or every prime in turn (one inlined copy of the body)
+  const int q0 = task.prime >= 0 ? task.prime : 0, q1 = task.prime >= 0 ? task.prime + 1 : a.nprimes;
+  for (int q = q0; q < q1; ++q) exec_naive_task_q<SR>(a, st, task, q, smem, s_last);
 }
 
 template <class SR>
@@ -423,21 +421,23 @@ __device__ __forceinline__ void exec_naive_task_q(const ExecArgs& a, const ExecS
   auto la = [&](uint32_t e) { return SR::template load<true>(A, e); };
   auto lb = [&](uint32_t e) { return SR::template load<true>(B, e); };
   if (a.trace && threadIdx.x == 0) g_trace_mark[0] = global_ns();
+  // k split: partial results to scratch, and the last CTA of the chunk
+  // merges them; else the results go to the output
+  Acc* part = reinterpret_cast<Acc*>(a.scratch + st.scratch_off) +
+              (int64_t(q) * st.nchunks + chunk_id) * ks * st.chunk;
+  auto sink = [&](uint32_t c, const Acc& v) {
+    if (ks == 1) SR::store(C, out_offset(g, sm.gt, c), v, mp);
+    else part[r * chunk + (static_cast<int32_t>(c) - c0)] = v;
+  };
+  if (ks == 1 && st.R == 1 && chunk % (kNaiveWideU * kBlock) == 0)
+    naive_chunk_wide<SR, kNaiveWideU>(g, la, lb, sink, mp, c0, c1, sm);
+  else
+    naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, kh0, kh1, st.R, sm);
   if (ks == 1) {
-    auto sink = [&](uint32_t c, const Acc& v) { SR::store(C, out_offset(g, sm.gt, c), v, mp); };
-    if (st.R == 1 && chunk % (kNaiveWideU * kBlock) == 0)
-      naive_chunk_wide<SR, kNaiveWideU>(g, la, lb, sink, mp, c0, c1, sm);
-    else
-      naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, kh0, kh1, st.R, sm);
     if (a.trace && threadIdx.x == 0) g_trace_mark[1] = global_ns();
     return;
   }
   if constexpr (IsKBest<SR>::value) return;  // planned without k splits
-  // k split: partial results to scratch; the last CTA of the chunk merges
-  Acc* part = reinterpret_cast<Acc*>(a.scratch + st.scratch_off) +
-              (int64_t(q) * st.nchunks + chunk_id) * ks * st.chunk;
-  auto sink = [&](uint32_t c, const Acc& v) { part[r * chunk + (static_cast<int32_t>(c) - c0)] = v; };
-  naive_chunk<SR>(g, la, lb, sink, mp, c0, c1, kh0, kh1, st.R, sm);
   if (!arrive_last(a.arrive + st.arrive_off + int64_t(q) * st.nchunks + chunk_id, ks, s_last)) return;
   if (a.trace && threadIdx.x == 0) g_trace_mark[1] = global_ns();
   if (chunk * ks <= kBlock && ks <= 32) {
