@@ -186,7 +186,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
       if (L.split > 1) L.scratch = static_cast<size_t>(ntiles * npt * L.split * bm * bn) * acc_bytes;
     } else {
       L.kernel = kKernNaive;
-      L.sh = dev::naive_shape(g.rc, g.nk, !is_kbest(s));
+      L.sh = dev::naive_shape(g.rc, g.nk, !is_kbest(s), npt);
       if (L.sh.ks > 1) L.scratch = static_cast<size_t>(L.sh.nchunks * npt * L.sh.ks * L.sh.chunk) * acc_bytes;
     }
   }
@@ -399,7 +399,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
         E.scratch_off = s_off[st] * 256;
       }
     } else {
-      const dev::NaiveShape sh = dev::naive_shape(S.g.rc, S.g.nk, !is_kbest(s));
+      const dev::NaiveShape sh = dev::naive_shape(S.g.rc, S.g.nk, !is_kbest(s), npt);
       E.kernel = kKernNaive;
       E.R = sh.R;
       E.chunk = sh.chunk;

@@ -386,7 +386,7 @@ struct NaiveShape {
   int64_t ntasks;   // nchunks * ks
 };
 
-inline NaiveShape naive_shape(int rc, int nk, bool allow_ksplit) {
+inline NaiveShape naive_shape(int rc, int nk, bool allow_ksplit, int sets = 1) {
   NaiveShape s;
   const int64_t E = int64_t(1) << rc, K = int64_t(1) << nk;
   int R = 1;
@@ -412,6 +412,10 @@ inline NaiveShape naive_shape(int rc, int nk, bool allow_ksplit) {
   int ks = 1;
   while (allow_ksplit && s.nchunks * ks < 304 && ks * 2 <= nkhi && K / (int64_t(R) * ks * 2) >= 8 && ks < 256)
     ks *= 2;
+  // a scalar output (the last step of a network): every task set (one per
+  // prime slot) in one wave of the 304 resident CTAs
+  if (rc == 0)
+    while (ks > 1 && int64_t(ks) * sets > 304) ks /= 2;
   s.ks = ks;
   s.ntasks = s.nchunks * ks;
   return s;
