@@ -110,6 +110,7 @@ int build_batch_plan(tn_plan_s* const* plans, int32_t count, tn_semiring_t semir
     const ExecPlan& x = *xs[i];
     for (size_t s = 0; s < x.steps.size(); ++s) {
       ExecStep e = x.steps[s];
+      e.final_slot = -1;  // final tasks write the results of a batch
       if (e.g.a_kind == kOpArena) e.a_off += arena_base[i];
       if (e.g.b_kind == kOpArena) e.b_off += arena_base[i];
       if (!e.c_shared) e.c_off += arena_base[i];

@@ -39,6 +39,7 @@ struct ExecStep {
   int32_t done_target;           // tasks of this step (its done counter's final value)
   int32_t c_shared;              // 1: the output lives in the group task's shared memory at byte c_off
   int32_t vec;                   // tiles: operands staged in 16-byte runs (kVecA | kVecB of tile_device.cuh)
+  int32_t final_slot;            // >= 0: the task that completes this step writes raw result slot final_slot
 };
 
 // Shared memory of a group task reserved for its internal tensors (bytes),

@@ -742,9 +742,20 @@ __global__ void __launch_bounds__(kBlock, 2) k_exec(const __grid_constant__ Exec
     __syncthreads();
     if (tid == 0) {
       const unsigned long long t_body = a.trace ? global_ns() : 0;
-      // release: the CTA's writes (ordered by the barrier above) become
-      // visible to any CTA that acquires the counter
-      asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(a.done + s_task.step) : "memory");
+      if (s_task.kind != kTaskGroup && s_step.final_slot >= 0) {
+        // the network's last step: the CTA that completes it (acquiring the
+        // other CTAs' writes) also writes the result block
+        int32_t old;
+        asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;"
+                     : "=r"(old)
+                     : "l"(a.done + s_task.step)
+                     : "memory");
+        if (old + 1 == s_step.done_target) exec_final<SR>(a, s_step, s_step.final_slot);
+      } else {
+        // release: the CTA's writes (ordered by the barrier above) become
+        // visible to any CTA that acquires the counter
+        asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(a.done + s_task.step) : "memory");
+      }
       if (a.trace) {
         unsigned smid;
         asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));

@@ -333,6 +333,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
     const Step& S = p->steps[st];
     ExecStep& E = X->steps[x];
     std::memset(&E, 0, sizeof(E));
+    E.final_slot = -1;
     E.g = S.g;
     // a stored leaf (edges first, then vertices, 2^rank entries each) is an
     // arena tensor at leaf_base; a generated leaf needs no offset
@@ -488,7 +489,15 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
       }
     }
   }
-  X->tasks.push_back(ExecTask{X->root_step, 0, 0, kTaskFinal});
+  // the result: written by the CTA that completes the last step (one
+  // dependency hop less), or by a final task after it when that step runs
+  // inside a group task or the plan is merged into a batch (whose final
+  // tasks carry each network's result slot)
+  bool fold = !X->batched;
+  for (const ExecTask& t : X->tasks)
+    if (t.step == X->root_step && t.kind == kTaskGroup) fold = false;
+  if (fold) X->steps[X->root_step].final_slot = 0;
+  else X->tasks.push_back(ExecTask{X->root_step, 0, 0, kTaskFinal});
   X->n_arrive = arrive;
   X->scratch_bytes = scratch;
 

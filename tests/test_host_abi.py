@@ -176,7 +176,7 @@ def test_executor_schedule_self_check(spec, height, monkeypatch):
             info = tn.tn_plan_info(p, sr, 3)
             assert info["exec_tasks"] >= 2
             if height == "1":
-                assert info["exec_tasks"] >= info["nsteps"] + 1
+                assert info["exec_tasks"] >= info["nsteps"]  # a task per step at least; the last one writes the result
             assert info["exec_levels"] >= 1
     finally:
         tn.tn_plan_destroy(p)
@@ -200,7 +200,7 @@ def test_exec_self_check_on_plan_variants(monkeypatch, spec):
             assert tn.tn_sliced_workspace_bytes(ps, sr, 3, 4) > 0
         assert tn.tn_single_config_workspace_bytes(p) > 0
         info = tn.tn_plan_info(ps, tn.TN_COUNTING_TROPICAL, 1)
-        assert info["exec_tasks"] >= info["nsteps"] + 1
+        assert info["exec_tasks"] >= info["nsteps"]  # a task per step at least; the last one writes the result
     finally:
         tn.tn_plan_destroy(p)
         tn.tn_plan_destroy(ps)
