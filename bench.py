@@ -791,7 +791,8 @@ def run_tn(args):
         _current_rows(rows)
     # register-only rates of the kernels' inner steps (the ALU roofline
     # denominators), measured on this GPU before the timed region
-    alu = {"maxplus": tn.tn_alu_peak("maxplus"), "modp": tn.tn_alu_peak("modp")}
+    alu = {"maxplus": tn.tn_alu_peak("maxplus"), "maxplus16x2": tn.tn_alu_peak("maxplus16x2"),
+           "modp": tn.tn_alu_peak("modp")}
     ws_bytes = max(p.workspace_bytes(sr, len(pr) if pr else 1) for p, sr, pr, _, _ in jobs)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     raw = torch.zeros(len(jobs) * tn.TN_RAW_BYTES, dtype=torch.uint8, device=dev)
@@ -904,9 +905,12 @@ def run_tn(args):
                 "per_semiring_tops": per_tops,
                 "per_semiring_frac": {k: per_tops[k] / peak for k in per_tops},
                 "instr_per_op": INSTR_PER_OP,
-                "inner_step_rates": {"unit": "Tops/s", "maxplus": alu["maxplus"], "modp_fold3": alu["modp"],
-                                     "note": "register-only rates of each kernel's inner step (tn_alu_peak); "
-                                             "context, not the denominator"}}
+                "inner_step_rates": {"unit": "Tops/s", "maxplus": alu["maxplus"],
+                                     "maxplus16x2": alu["maxplus16x2"], "modp_fold4": alu["modp"],
+                                     "note": "register-only rates of each kernel's inner step (tn_alu_peak): "
+                                             "int32 add-max, the packed tile's two int16 add-maxes per "
+                                             "instruction, and the mod-p 64-bit multiply-add folded every "
+                                             "fourth term; context, not the denominator"}}
 
     line = {"metric": METRIC, "value": value, "unit": "Gop/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

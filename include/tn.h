@@ -406,10 +406,10 @@ int tn_set_wait_timeout_ns(uint64_t ns);
  * the denominators of their ALU rooflines (no counterpart in the paper):
  * kind 0 = (max,+) int32 multiply-adds (one __viaddmax_s32 each), kind 1 =
  * mod-p multiply-adds (64-bit accumulate of a 32 x 32-bit product, the high
- * word folded back every third term), kind 2 = (max,+) multiply-adds on two
+ * word folded back every fourth term), kind 2 = (max,+) multiply-adds on two
  * int16 lanes (one __viaddmax_s16x2 per two terms).  Runs one warm-up and one timed
  * launch of 8 CTAs per SM, 16 independent chains per thread, `iters` terms
- * each (3 .. 2^24); *tops_out = terms per second / 1e12.  Synchronous;
+ * each (4 .. 2^24); *tops_out = terms per second / 1e12.  Synchronous;
  * allocates and frees a small device buffer. */
 int tn_alu_peak(int32_t kind, int32_t iters, void *cuda_stream, double *tops_out);
 

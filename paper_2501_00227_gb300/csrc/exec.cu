@@ -38,9 +38,10 @@ int exec_prepare_launch(tn_semiring_t s, const void* mods_v) {
       break;
     case TN_COUNTING_TROPICAL: r = dev::exec_resident<dev::SrCnt, 1>(&smem); break;
     case TN_COUNT_MODP: {
-      bool small_r = true;
-      for (int i = 0; i < TN_MAX_PRIMES && mods.q[i].p; ++i) small_r = small_r && mods.q[i].r32 < (1u << 20);
-      r = small_r ? dev::exec_resident<dev::SrMod, 3>(&smem) : dev::exec_resident<dev::SrMod, 1>(&smem);
+      bool fold4 = true;
+      for (int i = 0; i < TN_MAX_PRIMES && mods.q[i].p; ++i)
+        fold4 = fold4 && dev::mod_fold_interval(mods.q[i].p, mods.q[i].r32) == 4;
+      r = fold4 ? dev::exec_resident<dev::SrMod, 4>(&smem) : dev::exec_resident<dev::SrMod, 1>(&smem);
       break;
     }
     default: return TN_EINVAL;
@@ -148,9 +149,9 @@ int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods_v, void* ws,
                            : dev::exec_launch_t<dev::SrI32, 1>(X, a, st);
     case TN_COUNTING_TROPICAL: return dev::exec_launch_t<dev::SrCnt, 1>(X, a, st);
     case TN_COUNT_MODP: {
-      bool small_r = true;
-      for (int i = 0; i < X->nprimes; ++i) small_r = small_r && mods.q[i].r32 < (1u << 20);
-      return small_r ? dev::exec_launch_t<dev::SrMod, 3>(X, a, st) : dev::exec_launch_t<dev::SrMod, 1>(X, a, st);
+      bool fold4 = true;
+      for (int i = 0; i < X->nprimes; ++i) fold4 = fold4 && dev::mod_fold_interval(mods.q[i].p, mods.q[i].r32) == 4;
+      return fold4 ? dev::exec_launch_t<dev::SrMod, 4>(X, a, st) : dev::exec_launch_t<dev::SrMod, 1>(X, a, st);
     }
   }
   return TN_EINVAL;

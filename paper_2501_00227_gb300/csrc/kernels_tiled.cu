@@ -185,9 +185,9 @@ int launch_step_tiled(tn_semiring_t s, const StepGeom& g, const Operand& A, cons
     case TN_COUNTING_TROPICAL:
       return launch_cfg<SrCnt, 1>(a, tile, 1, st);
     case TN_COUNT_MODP: {
-      bool small_r = true;
-      for (int i = 0; i < nprimes; ++i) small_r = small_r && mods.q[i].r32 < (1u << 20);
-      return small_r ? launch_cfg<SrMod, 3>(a, tile, nprimes, st) : launch_cfg<SrMod, 1>(a, tile, nprimes, st);
+      bool fold4 = true;
+      for (int i = 0; i < nprimes; ++i) fold4 = fold4 && mod_fold_interval(mods.q[i].p, mods.q[i].r32) == 4;
+      return fold4 ? launch_cfg<SrMod, 4>(a, tile, nprimes, st) : launch_cfg<SrMod, 1>(a, tile, nprimes, st);
     }
   }
   return TN_EINVAL;

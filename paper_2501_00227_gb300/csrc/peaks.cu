@@ -4,7 +4,7 @@
 //   kind 0  (max,+) multiply-add on int32: acc = max(acc, a + b), one
 //           __viaddmax_s32 per term (the tropical tile's inner step)
 //   kind 1  mod-p multiply-add: acc += a * b on a 64-bit accumulator, its
-//           high word folded back (acc = hi * (2^32 mod p) + lo) every third
+//           high word folded back (acc = hi * (2^32 mod p) + lo) every fourth
 //           term (the mod-p tile's inner step)
 //   kind 2  (max,+) multiply-add on two int16 lanes: acc = max(acc, a + b)
 //           per 16-bit half, one __viaddmax_s16x2 per two terms (the packed
@@ -63,17 +63,17 @@ __global__ void __launch_bounds__(256) k_peak_maxplus2(int iters, int32_t seed, 
 
 __global__ void __launch_bounds__(256) k_peak_modp(int iters, uint32_t seed, uint32_t r32, uint64_t* out) {
   uint64_t acc[kChains];
-  uint32_t b[3][kChains];  // a different factor per term of a fold group: no product can be merged
+  uint32_t b[4][kChains];  // a different factor per term of a fold group: no product can be merged
 #pragma unroll
   for (int j = 0; j < kChains; ++j) {
     acc[j] = seed + j;
 #pragma unroll
-    for (int t = 0; t < 3; ++t) b[t][j] = ((seed * 2654435761u) ^ ((j + 16 * t) * 40503u) ^ threadIdx.x) & 0x7fffffffu;
+    for (int t = 0; t < 4; ++t) b[t][j] = ((seed * 2654435761u) ^ ((j + 16 * t) * 40503u) ^ threadIdx.x) & 0x7fffffffu;
   }
   const uint32_t a = seed ^ blockIdx.x;
-  for (int i = 0; i < iters; i += 3) {
+  for (int i = 0; i < iters; i += 4) {
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
+    for (int t = 0; t < 4; ++t) {
       const uint32_t at = (a + static_cast<uint32_t>(i + t)) & 0x7fffffffu;  // shared by 16 terms
 #pragma unroll
       for (int j = 0; j < kChains; ++j) acc[j] += static_cast<uint64_t>(at) * b[t][j];
@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(256) k_peak_modp(int iters, uint32_t seed, uin
 }  // namespace
 
 extern "C" int tn_alu_peak(int32_t kind, int32_t iters, void* cuda_stream, double* tops_out) {
-  if (!tops_out || kind < 0 || kind > 2 || iters < 3 || iters > (1 << 24)) return TN_EINVAL;
-  iters -= iters % 3;
+  if (!tops_out || kind < 0 || kind > 2 || iters < 4 || iters > (1 << 24)) return TN_EINVAL;
+  iters -= iters % 4;
   int dev, sms;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

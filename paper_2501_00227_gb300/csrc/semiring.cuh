@@ -50,6 +50,17 @@ struct ModParams {
   uint32_t x, pad_;
 };
 
+// Products a mod-p tile may add to its 64-bit accumulator between two folds
+// (acc <- hi * r32 + lo): 4 when the largest folded accumulator,
+// (r32 + 1)(2^32 - 1), plus four products of residues below p stays below
+// 2^64 -- true for every p = 2^31 - c with c < 2^29, e.g. the primes next
+// to 2^31 -- else 1 (exact for every p < 2^31).
+inline int mod_fold_interval(uint32_t p, uint32_t r32) {
+  const unsigned __int128 folded = static_cast<unsigned __int128>(r32 + 1ull) * 0xffffffffull;
+  const unsigned __int128 terms = static_cast<unsigned __int128>(p - 1ull) * (p - 1ull) * 4u;
+  return folded + terms < (static_cast<unsigned __int128>(1) << 64) ? 4 : 1;
+}
+
 // The same operand / output seen at the block of prime slot q (mod p keeps
 // one residue array per slot; the element accessors below read p0 only).
 __device__ __forceinline__ Operand at_prime(Operand o, int q, const ModParams& mp) {

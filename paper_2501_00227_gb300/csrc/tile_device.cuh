@@ -297,7 +297,7 @@ __device__ __forceinline__ void tile_stage(const StepGeom& g, const TileIdx<C>& 
 // Accumulates tile (tm, tn) of batch b over k in [kbeg, kend) into acc (of
 // the calling thread's group; the partial tiles of the KG groups are NOT yet
 // merged -- see tile_merge_groups).  FOLD: mod-p products accumulated between
-// two folds (1 is safe for every p < 2^31; 3 needs 2^32 mod p < 2^20).  All
+// two folds (1 is safe for every p < 2^31; 4 where mod_fold_interval allows it).  All
 // threads of the CTA must call it.
 template <class SR, class C, int FOLD, bool CG>
 __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& A, const Operand& B,

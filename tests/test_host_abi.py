@@ -206,7 +206,7 @@ def test_exec_self_check_on_plan_variants(monkeypatch, spec):
         tn.tn_plan_destroy(ps)
 
 
-@pytest.mark.parametrize("kind,iters", [(3, 1024), (-1, 1024), (0, 2), (1, (1 << 24) + 1)])
+@pytest.mark.parametrize("kind,iters", [(3, 1024), (-1, 1024), (0, 3), (1, (1 << 24) + 1)])
 def test_alu_peak_rejects_bad_arguments(kind, iters):
     out = ctypes.c_double()
     assert tn.lib().tn_alu_peak(kind, iters, None, ctypes.byref(out)) == tn.TN_EINVAL
