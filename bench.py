@@ -339,6 +339,59 @@ def largest_bench(tn, torch, peak_tops: float, autotune: bool = True):
     return out
 
 
+def umma_contraction_bench(tn, torch):
+    """The tensor-core ablation inside a whole contraction (config 4): the
+    King's subgraph 20x20 seed 1, count mod 4 primes, timed three ways on one
+    plan -- the executor (CUDA cores, one launch), one launch per step on the
+    CUDA cores (TN_EXEC=0), and one launch per step with every GEMM-shaped
+    step (M % 128, N % 64, K % 64 == 0) on the tcgen05 limb GEMM (TN_UMMA=1:
+    gather to row-major operands, tn_modp_gemm_umma, scatter of the result)."""
+    import graphgen
+    primes = tuple(tn.PRIMES31[:4])
+    n, e = graphgen.by_name("ksg:20:0.8:1")
+    p = tn.Plan(n, e, nrepeat=10, seed=1)
+    si = tn.tn_plan_step_info(p.handle, "modp", 4)
+    ops = 2.0 ** (si[:, 6] + si[:, 7] + si[:, 8] + si[:, 9])
+    fit = (si[:, 7] >= 7) & (si[:, 8] >= 6) & (si[:, 9] >= 6)
+    ws = torch.empty(p.workspace_bytes("modp", 4), dtype=torch.uint8, device="cuda")
+    raw = torch.zeros(tn.TN_RAW_BYTES, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    total_ops = float(ops.sum()) * 4
+    out = {"workload": "King's subgraph 20x20 p=0.8 seed 1, count mod 4 primes, greedy (nrepeat 10)",
+           "log2_tc": float(np.log2(ops.sum())), "tensor_core_steps": int(fit.sum()),
+           "tensor_core_share_of_tc": float(ops[fit].sum() / ops.sum())}
+    saved = {k: os.environ.get(k) for k in ("TN_EXEC", "TN_UMMA")}
+    try:
+        for name, env in (("executor_cuda_cores", {}), ("per_step_cuda_cores", {"TN_EXEC": "0"}),
+                          ("per_step_tcgen05", {"TN_EXEC": "0", "TN_UMMA": "1"})):
+            for k in ("TN_EXEC", "TN_UMMA"):
+                os.environ.pop(k, None)
+            os.environ.update(env)
+            res = p.contract("modp", primes, workspace=ws)["residues"]
+            times = []
+            for _ in range(3):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                tn.tn_contract_async(p.handle, "modp", primes, ws.data_ptr(), ws.numel(), st, raw.data_ptr())
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = statistics.median(times)
+            out[name] = {"ms": ms, "tops": total_ops / (ms * 1e-3) / 1e12, "residues": res}
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+        p.close()
+    out["equal"] = (out["executor_cuda_cores"]["residues"] == out["per_step_cuda_cores"]["residues"]
+                    == out["per_step_tcgen05"]["residues"])
+    return out
+
+
 def limb_ablation_bench(tn, torch):
     """Tensor-core ablation of the mod-p GEMM (config 4): the largest King's
     subgraph 20x20 step shape, (batch, M, N, K) = (2, 1024, 512, 1024), 4
@@ -928,6 +981,7 @@ def run_tn(args):
     if rank == 0 and not args.no_extras:
         line["largest_tropical"] = largest_bench(tn, torch, peak, autotune=not args.no_autotune)
         line["modp_tensor_core_ablation"] = limb_ablation_bench(tn, torch)
+        line["modp_tensor_core_contraction"] = umma_contraction_bench(tn, torch)
         line["independence_polynomial"] = polynomial_bench(tn, torch, plans, cpu=not args.no_cpu_baseline)
         line["kbest"] = kbest_bench(tn, torch, plans, line["independence_polynomial"])
         line["weighted"] = weighted_bench(tn, torch, plans, cpu=not args.no_cpu_baseline)

@@ -161,7 +161,10 @@ int contract_enqueue(const tn_plan_s* p, tn_semiring_t s, const ModTable& mods, 
     Operand B = operand_of(p, rg, step.b_id);
     Operand Cin = operand_of(p, rg, step.c_id);
     Output C{const_cast<void*>(Cin.p0), const_cast<void*>(Cin.p1), Cin.prime_stride};
-    rc = dev::launch_step(s, step.g, A, B, C, mods, np, st, nullptr);
+    if (s == TN_COUNT_MODP && dev::umma_route_enabled() && dev::umma_step_fits(step.g, A, B))
+      rc = dev::umma_step(step.g, A, B, C, mods, np, st);
+    else
+      rc = dev::launch_step(s, step.g, A, B, C, mods, np, st, nullptr);
     if (rc) return rc;
     if (step_events) {
       rc = cuda_rc(cudaEventRecord(step_events[2 * i + 1], st));

@@ -3,6 +3,7 @@
 // the workspace (counters, split-K scratch, arena) and caches the result per
 // (semiring, number of primes) inside the plan.
 #include <algorithm>
+#include <iterator>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -85,10 +86,12 @@ class LevelArena {
     std::vector<int32_t> rel;
   };
   static void merge(Block* a, const Block& b) {
+    // both releaser lists are sorted and duplicate-free: a linear union
     a->len += b.len;
-    a->rel.insert(a->rel.end(), b.rel.begin(), b.rel.end());
-    std::sort(a->rel.begin(), a->rel.end());
-    a->rel.erase(std::unique(a->rel.begin(), a->rel.end()), a->rel.end());
+    std::vector<int32_t> u;
+    u.reserve(a->rel.size() + b.rel.size());
+    std::set_union(a->rel.begin(), a->rel.end(), b.rel.begin(), b.rel.end(), std::back_inserter(u));
+    a->rel.swap(u);
   }
   std::map<int64_t, Block> free_;
   int64_t top_ = 0;
@@ -301,23 +304,18 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
     auto& d = dep[st];
     std::sort(d.begin(), d.end());
     d.erase(std::unique(d.begin(), d.end()), d.end());
+    // a: the union of the dependencies' (strict) ancestors; a dependency in
+    // it is implied by another one.  Then the dependencies themselves join a.
     uint64_t* a = &anc[static_cast<size_t>(x) * words];
     for (int32_t u : d) {
-      const int pu = pos[u];
-      const uint64_t* au = &anc[static_cast<size_t>(pu) * words];
+      const uint64_t* au = &anc[static_cast<size_t>(pos[u]) * words];
       for (int w = 0; w < words; ++w) a[w] |= au[w];
-      a[pu / 64] |= 1ull << (pu % 64);
     }
     for (int32_t u : d) {
       const int pu = pos[u];
-      bool implied = false;
-      for (int32_t v : d) {
-        if (v == u) continue;
-        const uint64_t* av = &anc[static_cast<size_t>(pos[v]) * words];
-        if ((av[pu / 64] >> (pu % 64)) & 1) { implied = true; break; }
-      }
-      if (!implied) red[st].push_back(pu);
+      if (!((a[pu / 64] >> (pu % 64)) & 1)) red[st].push_back(pu);
     }
+    for (int32_t u : d) a[pos[u] / 64] |= 1ull << (pos[u] % 64);
   }
 
   // steps, tasks, split-K scratch and arrival counters

@@ -33,6 +33,15 @@ void pick_launch(const StepGeom& g, tn_semiring_t s, int nprimes, int* kernel, i
 int launch_step(tn_semiring_t s, const StepGeom& g, const Operand& A, const Operand& B,
                 const Output& C, const ModTable& mods, int nprimes, cudaStream_t st, int* kernel_used);
 
+// Tensor-core ablation inside the one-launch-per-step mode (umma_route.cu):
+// TN_UMMA=1 in the environment routes every mod-p step that fits the
+// tcgen05 limb GEMM (M % 128, N % 64, K % 64 == 0, stored operands) through
+// a gather, tn_modp_gemm_umma and a scatter into the step's stored layout.
+bool umma_route_enabled();
+bool umma_step_fits(const StepGeom& g, const Operand& A, const Operand& B);
+int umma_step(const StepGeom& g, const Operand& A, const Operand& B, const Output& C, const ModTable& mods,
+              int32_t nprimes, cudaStream_t st);
+
 // Copies the root scalar and the status word into a TN_RAW_BYTES block.
 int launch_finalize(tn_semiring_t s, const Operand& root, int nprimes, const uint32_t* d_status,
                     void* d_raw, cudaStream_t st);

@@ -3,6 +3,8 @@ MMAs, tn_modp_gemm_umma on tcgen05): exact against plain integer arithmetic
 on a small case, and bit-identical to the CUDA-core path (tn_contract_pair
 on the same buffers) on larger ones, including k longer than one exact
 8192-term diagonal block."""
+import os
+
 import numpy as np
 import pytest
 
@@ -92,3 +94,36 @@ def test_umma_gemm_matches_integer_mma(batch, m, n, k, nprimes):
     A = _residues(rng, primes, (batch, m, k))
     B = _residues(rng, primes, (batch, n, k))
     assert (_limb(primes, A, B, batch, m, n, k, tn.tn_modp_gemm_umma) == _limb(primes, A, B, batch, m, n, k)).all()
+
+
+def _umma_steps(plan, nprimes):
+    """GEMM-shaped mod-p steps the tensor-core route takes (M % 128, N % 64,
+    K % 64 == 0; the operands of such steps are intermediates)."""
+    si = tn.tn_plan_step_info(plan.handle, "modp", nprimes)
+    return int(((si[:, 7] >= 7) & (si[:, 8] >= 6) & (si[:, 9] >= 6)).sum())
+
+
+@pytest.mark.parametrize("spec,nprimes", [("reg3:140:2", 3), ("ksg:20:0.8:1", 4)])
+def test_contraction_through_tensor_core_route(spec, nprimes, monkeypatch):
+    """A whole contraction with its GEMM-shaped mod-p steps on the tcgen05
+    limb GEMM (one launch per step, TN_UMMA=1) gives the residues of the
+    executor and of the oracle (Sec. 5.1)."""
+    import graphgen as g
+    import oracle as O
+    n, e = g.by_name(spec)
+    primes = tn.PRIMES31[:nprimes]
+    p = tn.Plan(n, e, nrepeat=10, seed=1)
+    try:
+        assert _umma_steps(p, nprimes) >= 2
+        ref = p.contract("modp", primes)["residues"]
+        monkeypatch.setenv("TN_EXEC", "0")
+        monkeypatch.setenv("TN_UMMA", "1")
+        got = p.contract("modp", primes)["residues"]
+        monkeypatch.setenv("TN_UMMA", "0")
+        plain = p.contract("modp", primes)["residues"]
+        assert got == plain == ref
+        if spec.startswith("reg3"):
+            O.set_threads(os.cpu_count() or 1)
+            assert got == O.count_modp(n, e, p.order, primes)
+    finally:
+        p.close()
