@@ -14,15 +14,15 @@
 namespace tn {
 
 namespace {
-// Whether int32 tropical launches of X may use the packed 16-bit tile
-// (TN_PACKED=0 in the environment keeps the int32 tile, for measurement
-// and tests).
+// Whether the int32 tropical or counting launches of X may use the packed
+// 16-bit tiles (TN_PACKED=0 in the environment keeps the 32-bit tiles, for
+// measurement and tests).
 bool use_packed(const ExecPlan* X) {
   static const bool off = [] {
     const char* e = getenv("TN_PACKED");
     return e && e[0] == '0';
   }();
-  return !off && X->value_bound <= dev::kPackedMax;
+  return !off && X->value_bound <= (X->semiring == TN_COUNTING_TROPICAL ? dev::kPackedCntMax : dev::kPackedMax);
 }
 }  // namespace
 
@@ -36,7 +36,10 @@ int exec_prepare_launch(tn_semiring_t s, const void* mods_v) {
       r = dev::exec_resident<dev::SrI32, 1>(&smem);
       if (r >= 0) r = dev::exec_resident<dev::SrI32, dev::kPackedI16>(&smem);
       break;
-    case TN_COUNTING_TROPICAL: r = dev::exec_resident<dev::SrCnt, 1>(&smem); break;
+    case TN_COUNTING_TROPICAL:
+      r = dev::exec_resident<dev::SrCnt, 1>(&smem);
+      if (r >= 0) r = dev::exec_resident<dev::SrCnt, dev::kPackedI16>(&smem);
+      break;
     case TN_COUNT_MODP: {
       bool fold4 = true;
       for (int i = 0; i < TN_MAX_PRIMES && mods.q[i].p; ++i)
@@ -147,7 +150,9 @@ int exec_launch_core(ExecPlan* X, tn_semiring_t s, const void* mods_v, void* ws,
     case TN_TROPICAL_I32:
       return use_packed(X) ? dev::exec_launch_t<dev::SrI32, dev::kPackedI16>(X, a, st)
                            : dev::exec_launch_t<dev::SrI32, 1>(X, a, st);
-    case TN_COUNTING_TROPICAL: return dev::exec_launch_t<dev::SrCnt, 1>(X, a, st);
+    case TN_COUNTING_TROPICAL:
+      return use_packed(X) ? dev::exec_launch_t<dev::SrCnt, dev::kPackedI16>(X, a, st)
+                           : dev::exec_launch_t<dev::SrCnt, 1>(X, a, st);
     case TN_COUNT_MODP: {
       bool fold4 = true;
       for (int i = 0; i < X->nprimes; ++i) fold4 = fold4 && dev::mod_fold_interval(mods.q[i].p, mods.q[i].r32) == 4;

@@ -198,7 +198,8 @@ __device__ __noinline__ void exec_tile_task(const ExecArgs& a, const ExecStep& s
 
   Acc acc[TM][TN];
   if constexpr (std::is_same<SR, SrCnt>::value)
-    tile_mainloop_counting<Cfg, true>(g, A, B, mp, b, tm, tn_, kbeg, kstop, smem, acc, prepared, st.vec);
+    tile_mainloop_counting<Cfg, true, FOLD == kPackedI16>(g, A, B, mp, b, tm, tn_, kbeg, kstop, smem, acc, prepared,
+                                                          st.vec);
   else if constexpr (std::is_same<SR, SrI32>::value && FOLD == kPackedI16)
     tile_mainloop_packed<Cfg, true>(g, A, B, b, tm, tn_, kbeg, kstop, *reinterpret_cast<TileSmemP<Cfg>*>(smem), acc,
                                     prepared, st.vec);
@@ -777,6 +778,12 @@ template <class SR, int FOLD>
 static size_t smem_for() {
   if constexpr (IsKBest<SR>::value) return sizeof(NaiveSmem<SR>);
   size_t t = tile_smem_bytes<SR, TileC1>();
+  if constexpr (std::is_same<SR, SrCnt>::value && FOLD == kPackedI16) {
+    const size_t packed[] = {tile_smem_bytes_cnt_packed<TileC1>(), tile_smem_bytes_cnt_packed<TileC2>(),
+                             tile_smem_bytes_cnt_packed<TileC3>(), tile_smem_bytes_cnt_packed<TileC4>(),
+                             tile_smem_bytes_cnt_packed<TileC5>()};
+    for (size_t c : packed) t = c > t ? c : t;
+  }
   if constexpr (std::is_same<SR, SrI32>::value && FOLD == kPackedI16) {
     const size_t packed[] = {tile_smem_bytes_packed<TileC0>(), tile_smem_bytes_packed<TileC1>(),
                              tile_smem_bytes_packed<TileC2>(), tile_smem_bytes_packed<TileC3>(),

@@ -19,6 +19,8 @@
 // whole tile and only a per-chunk base (the high k bits) changes.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include <type_traits>
 
 #include "semiring.cuh"
@@ -688,7 +690,110 @@ struct TileSmemCnt {
   alignas(16) uint64_t Bc[kSt][C::BK * C::BN];
 };
 
-template <class C, bool CG>
+// ---------------------------------------------------------------------------
+// Packed counting tile: the (max, count) tile of tile_mainloop_counting with
+// the values of two terms in one register, as IEEE half precision.  Integers
+// up to 2048 in magnitude are exact in binary16, so when the host proves
+// |finite value| <= kPackedCntMax for the network (unit-weight networks with
+// n <= 1024), every sum a + b of two finite values is exact and "-inf" is
+// the half -inf (-inf + x = -inf; the counts of -inf entries are 0, so a
+// -inf term that compares equal adds a zero product).  Per pair of terms:
+//   first pass   add.f16x2 and max.f16x2 (the chunk's maxima);
+//   second pass  add.f16x2, one setp.eq.f16x2 that sets a predicate per
+//                half, and a predicated 64-bit multiply-add per term
+// -- 2 instructions per counted term instead of 3, and half the value
+// registers.  Values are staged as int32 exactly as in the unpacked tile;
+// each thread converts the entries it copied itself into (a, a) and
+// (b[n], b[n + 1]) half pairs (two buffers alternate, as in the packed
+// (max,+) tile).  Counts, the slow path and the results are unchanged.
+// ---------------------------------------------------------------------------
+constexpr int32_t kPackedCntMax = 1024;  // largest |finite value| of the packed counting tile
+
+__device__ __forceinline__ uint32_t h16_of(int32_t v) {
+  return v < kNegInf / 2 ? 0xFC00u : static_cast<uint32_t>(__half_as_ushort(__int2half_rn(v)));
+}
+__device__ __forceinline__ int32_t i32_of_h16(uint32_t h) {
+  return (h & 0xFFFFu) == 0xFC00u ? kNegInf : __half2int_rn(__ushort_as_half(static_cast<unsigned short>(h)));
+}
+
+template <class C>
+struct TileSmemCntP {
+  static constexpr int kSt = Stages<SrCnt>::v;
+  TileIdx<C> idx;
+  alignas(16) int32_t Av[kSt][C::BK * C::BM];
+  alignas(16) int32_t Bv[kSt][C::BK * C::BN];
+  alignas(16) uint64_t Ac[kSt][C::BK * C::BM];
+  alignas(16) uint64_t Bc[kSt][C::BK * C::BN];
+  alignas(16) uint32_t Ah[2][C::BK * C::BM];      // (a, a) half pairs
+  alignas(16) uint32_t Bh[2][C::BK * C::BN / 2];  // (b[n], b[n + 1]) half pairs
+};
+
+template <class C>
+constexpr size_t tile_smem_bytes_cnt_packed() {
+  const size_t merge = tile_merge_off<C>() + sizeof(CntVal) * (C::KG - 1) * C::BM * C::BN;
+  return sizeof(TileSmemCntP<C>) > merge ? sizeof(TileSmemCntP<C>) : merge;
+}
+
+// This thread's staged values of one chunk (those it copied or generated) as
+// half pairs.
+template <class C, int NSA, int NSB>
+__device__ __forceinline__ void tile_pack_h16(const int32_t* as, const int32_t* bs, uint32_t* ah, uint32_t* bh,
+                                              const int32_t (&offA)[C::EA], const int32_t (&offB)[C::EB], bool va,
+                                              bool vb) {
+  const int tid = threadIdx.x;
+  if (va) {
+#pragma unroll
+    for (int j = 0; j < NSA; ++j)
+      if (offA[j] >= 0) {
+        const int e = 4 * (tid + kBlock * j);
+        const int4 v = *reinterpret_cast<const int4*>(as + e);
+        *reinterpret_cast<uint4*>(ah + e) =
+            make_uint4(h16_of(v.x) * 0x10001u, h16_of(v.y) * 0x10001u, h16_of(v.z) * 0x10001u, h16_of(v.w) * 0x10001u);
+      }
+  } else {
+#pragma unroll
+    for (int j = 0; j < C::EA; ++j)
+      if (offA[j] >= 0) ah[tid + kBlock * j] = h16_of(as[tid + kBlock * j]) * 0x10001u;
+  }
+  if (vb) {
+#pragma unroll
+    for (int j = 0; j < NSB; ++j)
+      if (offB[j] >= 0) {
+        const int e = 4 * (tid + kBlock * j);
+        const int4 v = *reinterpret_cast<const int4*>(bs + e);
+        *reinterpret_cast<uint2*>(bh + e / 2) =
+            make_uint2(h16_of(v.x) | (h16_of(v.y) << 16), h16_of(v.z) | (h16_of(v.w) << 16));
+      }
+  } else {
+    unsigned short* b16 = reinterpret_cast<unsigned short*>(bh);
+#pragma unroll
+    for (int j = 0; j < C::EB; ++j)
+      if (offB[j] >= 0) b16[tid + kBlock * j] = static_cast<unsigned short>(h16_of(bs[tid + kBlock * j]));
+  }
+}
+
+// mc = max(a + b, mc) on both halves
+__device__ __forceinline__ void h2_addmax(uint32_t& mc, uint32_t a, uint32_t b) {
+  asm("{\n\t.reg .b32 s;\n\tadd.rn.f16x2 s, %1, %2;\n\tmax.f16x2 %0, %0, s;\n\t}" : "+r"(mc) : "r"(a), "r"(b));
+}
+// a larger chunk maximum restarts the entry's count; vmax = max(vmax, mc)
+__device__ __forceinline__ void h2_raise(uint32_t& vmax, uint32_t mc, uint64_t& c0, uint64_t& c1) {
+  asm("{\n\t.reg .pred p, q;\n\tsetp.gt.f16x2 p|q, %3, %2;\n\t@p mov.b64 %0, 0;\n\t@q mov.b64 %1, 0;\n\t}"
+      : "+l"(c0), "+l"(c1)
+      : "r"(vmax), "r"(mc));
+  asm("max.f16x2 %0, %0, %1;" : "+r"(vmax) : "r"(mc));
+}
+// c0 += ac * bc0 where a + b reaches vmax in the low half, c1 += ac * bc1 in
+// the high half (64-bit multiply-adds; the caller guarantees no overflow)
+__device__ __forceinline__ void h2_count(uint64_t& c0, uint64_t& c1, uint32_t a, uint32_t b, uint32_t vmax,
+                                         uint32_t ac, uint32_t bc0, uint32_t bc1) {
+  asm("{\n\t.reg .pred p, q;\n\t.reg .b32 s;\n\tadd.rn.f16x2 s, %2, %3;\n\tsetp.eq.f16x2 p|q, s, %4;\n\t"
+      "@p mad.wide.u32 %0, %5, %6, %0;\n\t@q mad.wide.u32 %1, %5, %7, %1;\n\t}"
+      : "+l"(c0), "+l"(c1)
+      : "r"(a), "r"(b), "r"(vmax), "r"(ac), "r"(bc0), "r"(bc1));
+}
+
+template <class C, bool CG, bool Packed = false>
 __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const Operand& A, const Operand& B,
                                                        const ModParams& mp, int64_t b, int64_t tm, int64_t tn_,
                                                        int64_t kbeg, int64_t kend, unsigned char* smem_raw,
@@ -699,7 +804,8 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
   constexpr int NSA = VecSlots<BM, BK * BM>::per_thread, NSB = VecSlots<BN, BK * BN>::per_thread;
   static_assert(NSA <= C::EA && NSB <= C::EB, "a 16-byte slot covers four staged elements");
   const bool va = (vec & kVecA) && A.kind == kOpArena, vb = (vec & kVecB) && B.kind == kOpArena;
-  auto& sm = *reinterpret_cast<TileSmemCnt<C>*>(smem_raw);
+  // the packed layout extends the unpacked one (same leading members)
+  auto& sm = *reinterpret_cast<TileSmemCntP<C>*>(smem_raw);
   const int tid = threadIdx.x;
   const int grp = tid / C::GT, gt = tid % C::GT;
   const int tx = gt % C::WN, ty = gt / C::WN;
@@ -714,12 +820,21 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
         sm.Ac[st][tid + kBlock * j] = 0ull;
       }
 #pragma unroll
+  for (int j = 0; j < C::EA; ++j)
+    if (Packed && offA[j] < 0) sm.Ah[0][tid + kBlock * j] = sm.Ah[1][tid + kBlock * j] = 0xFC00FC00u;
+#pragma unroll
   for (int j = 0; j < C::EB; ++j)
     if (offB[j] < 0)
       for (int st = 0; st < kSt; ++st) {
         sm.Bv[st][tid + kBlock * j] = kNegInf;
         sm.Bc[st][tid + kBlock * j] = 0ull;
       }
+#pragma unroll
+  for (int j = 0; j < C::EB; ++j)
+    if (Packed && offB[j] < 0) {
+      reinterpret_cast<unsigned short*>(sm.Bh[0])[tid + kBlock * j] = 0xFC00u;
+      reinterpret_cast<unsigned short*>(sm.Bh[1])[tid + kBlock * j] = 0xFC00u;
+    }
   {
     // 16-byte slots (see tile_mainloop): four values, and four counts in two
     // 16-byte halves
@@ -728,15 +843,18 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
     if (vb) tile_slots4<BN, BK, NSB>(sm.idx.offBn, sm.idx.offBk, static_cast<uint32_t>(tn_) * BN, 1u << g.nn, kvalid, offB);
   }
 
-  int32_t vmax[TM][TN];
+  int32_t vmax[TM][TN];           // running maxima (unpacked)
+  uint32_t vmax2[TM][TN / 2];     // running maxima as half pairs (packed)
   uint64_t cnt[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       vmax[i][j] = kNegInf;
+      if (j % 2 == 0) vmax2[i][j / 2] = 0xFC00FC00u;
       cnt[i][j] = 0ull;
     }
+  int pb = 0;  // packed buffer of the current chunk
 
   const bool a_async = A.kind == kOpArena, b_async = B.kind == kOpArena;
   auto issue = [&](int st, int64_t k0) {
@@ -798,6 +916,7 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
   int cur = 0;
   for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
     cp_async_wait<kSt - 2>();
+    if constexpr (Packed) tile_pack_h16<C, NSA, NSB>(sm.Av[cur], sm.Bv[cur], sm.Ah[pb], sm.Bh[pb], offA, offB, va, vb);
     // this thread's own copies of the chunk are complete: the chunk is fast
     // when every staged count is < 2^16 and every accumulator < 2^62 (16
     // products < 2^32 cannot carry out of 64 bits); the barrier publishes the
@@ -823,7 +942,31 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
     const int32_t* Bgv = sm.Bv[cur] + grp * C::BKG * BN;
     const uint64_t* Agc = sm.Ac[cur] + grp * C::BKG * BM;
     const uint64_t* Bgc = sm.Bc[cur] + grp * C::BKG * BN;
-    {
+    const uint32_t* Agh = sm.Ah[pb] + grp * C::BKG * BM;
+    const uint32_t* Bgh = sm.Bh[pb] + grp * C::BKG * (BN / 2);
+    if constexpr (Packed) {
+      // 1: the chunk's maxima on half pairs; a larger maximum restarts the
+      // entry's count
+      uint32_t mc2[TM][TN / 2];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN / 2; ++j) mc2[i][j] = 0xFC00FC00u;
+#pragma unroll 4
+      for (int kk = 0; kk < C::BKG; ++kk) {
+        uint32_t ah[TM], bh[TN / 2];
+        load_frag<TM>(Agh + kk * BM + ty * TM, ah);
+        load_frag<TN / 2>(Bgh + kk * (BN / 2) + tx * (TN / 2), bh);
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN / 2; ++j) h2_addmax(mc2[i][j], ah[i], bh[j]);
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN / 2; ++j) h2_raise(vmax2[i][j], mc2[i][j], cnt[i][2 * j], cnt[i][2 * j + 1]);
+    } else {
       // 1: the chunk's maxima; a larger maximum restarts the entry's count
       int32_t mc[TM][TN];
 #pragma unroll
@@ -850,7 +993,21 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
           }
     }
     // 2: counts of the chunk's terms that reach the running maximum
-    if (!slow) {
+    if (Packed && !slow) {
+#pragma unroll 2
+      for (int kk = 0; kk < C::BKG; ++kk) {
+        uint32_t ah[TM], bh[TN / 2], ac[TM], bc[TN];
+        load_frag<TM>(Agh + kk * BM + ty * TM, ah);
+        load_frag<TN / 2>(Bgh + kk * (BN / 2) + tx * (TN / 2), bh);
+        load_lo_frag<TM>(Agc + kk * BM + ty * TM, ac);
+        load_lo_frag<TN>(Bgc + kk * BN + tx * TN, bc);
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN / 2; ++j)
+            h2_count(cnt[i][2 * j], cnt[i][2 * j + 1], ah[i], bh[j], vmax2[i][j], ac[i], bc[2 * j], bc[2 * j + 1]);
+      }
+    } else if (!slow) {
 #pragma unroll 2
       for (int kk = 0; kk < C::BKG; ++kk) {
         int32_t av[TM], bv[TN];
@@ -872,12 +1029,14 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
           const uint64_t ac = Agc[kk * BM + ty * TM + i];
 #pragma unroll
           for (int j = 0; j < TN; ++j)
-            if (av + Bgv[kk * BN + tx * TN + j] == vmax[i][j])
+            if (av + Bgv[kk * BN + tx * TN + j] ==
+                (Packed ? i32_of_h16(vmax2[i][j / 2] >> (16 * (j % 2))) : vmax[i][j]))
               cnt[i][j] = sat_add_u64(cnt[i][j], sat_mul_u64(ac, Bgc[kk * BN + tx * TN + j]));
         }
       }
     }
     cur = (cur + 1) % kSt;
+    pb ^= 1;
   }
   cp_async_wait<0>();
   __syncthreads();
@@ -885,7 +1044,7 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-      acc[i][j].v = vmax[i][j];
+      acc[i][j].v = Packed ? i32_of_h16(vmax2[i][j / 2] >> (16 * (j % 2))) : vmax[i][j];
       acc[i][j].c = cnt[i][j];
     }
 }

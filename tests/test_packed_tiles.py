@@ -1,14 +1,16 @@
-"""The packed (max,+) tile of int32 tropical contractions (two 16-bit terms
-per __viaddmax_s16x2), against the oracle and against the int32 tile.
+"""The packed tiles: (max,+) on int32 tropical networks (two 16-bit terms per
+__viaddmax_s16x2) and the counting tile on half-precision value pairs,
+against the oracle and against the 32-bit tiles.
 
-The executor takes the packed tile when every finite value of the network is
-at most 4095 in magnitude, i.e. for unit-weight networks with n <= 4095
-vertices.  These tests push tile operands close to that bound (a random
-3-regular core whose vertices carry many pendant vertices: every pendant
-absorbed into its core vertex's tensor adds one to the values the core's
-GEMM-shaped steps see), check one vertex past the bound (the int32 tile
-runs), and compare the two tiles on the same plans (TN_PACKED=0 in a child
-process keeps the int32 tile).
+The executor takes the packed (max,+) tile when every finite value of the
+network is at most 4095 in magnitude (unit-weight networks with n <= 4095
+vertices) and the packed counting tile when it is at most 1024 (n <= 1024).
+These tests push tile operands close to those bounds (a random 3-regular core
+whose vertices carry many pendant vertices: every pendant absorbed into its
+core vertex's tensor adds one to the values the core's GEMM-shaped steps see),
+check one vertex past each bound (the 32-bit tiles run), and compare the two
+kinds of tiles on the same plans (TN_PACKED=0 in a child process keeps the
+32-bit tiles).
 """
 import json
 import os
@@ -109,6 +111,28 @@ def test_values_near_the_packed_bound(total, seed):
         p.close()
 
 
+@pytest.mark.parametrize("total,seed", [(1024, 4), (1025, 5), (700, 6)])
+def test_counting_values_near_the_half_precision_bound(total, seed):
+    """The packed counting tile (values as IEEE half pairs) runs for n <= 1024,
+    where every sum of two finite values is an exact half; one vertex more
+    keeps the 32-bit tile."""
+    core = 100
+    rng = np.random.default_rng(seed)
+    extra = total - core
+    cuts = np.sort(rng.integers(0, extra + 1, size=core - 1))
+    pendants = np.diff(np.concatenate([[0], cuts, [extra]]))
+    n, e, order = _pendant_network(core, seed, pendants)
+    p = tn.Plan(n, e, order)
+    try:
+        assert _tiled_steps(p) > 0
+        want = O.mis_count(n, e, p.order)
+        assert want[0] >= extra
+        r = p.contract("counting")
+        assert (r["max"], r["count"]) == want
+    finally:
+        p.close()
+
+
 _CHILD = r"""
 import json, sys
 sys.path.insert(0, sys.argv[1])
@@ -117,13 +141,14 @@ from paper_2501_00227_gb300 import tn
 out = {}
 for spec in sys.argv[2:]:
     p = tn.Plan(*graphgen.by_name(spec), nrepeat=4, seed=1)
-    out[spec] = p.contract("tropical_i32")["max"]
+    c = p.contract("counting")
+    out[spec] = [p.contract("tropical_i32")["max"], c["max"], c["count"]]
     p.close()
 print(json.dumps(out))
 """
 
 
-def test_packed_and_int32_tiles_agree():
+def test_packed_and_32bit_tiles_agree():
     specs = ["reg3:100:1", "reg3:140:2", "ksg:12:0.8:1", "ksg:14:0.8:2", "er:40:0.15:3", "square:12"]
     env = dict(os.environ)
     env["TN_PACKED"] = "0"
@@ -136,6 +161,9 @@ def test_packed_and_int32_tiles_agree():
         p = tn.Plan(n, e, nrepeat=4, seed=1)
         try:
             got = p.contract("tropical_i32")["max"]
-            assert got == int32_tile[spec] == O.mis_size(n, e, p.order), spec
+            c = p.contract("counting")
+            assert got == int32_tile[spec][0] == O.mis_size(n, e, p.order), spec
+            assert [c["max"], c["count"]] == int32_tile[spec][1:], spec
+            assert (c["max"], c["count"]) == O.mis_count(n, e, p.order), spec
         finally:
             p.close()
