@@ -121,19 +121,20 @@ __device__ __forceinline__ void tile_tables(const StepGeom& g, TileIdx<C>& ix, i
     sync();
   }
   const uint32_t cb = static_cast<uint32_t>(b) << (g.nn + g.nm);
-  #pragma unroll 1
+  // rolled loops: set-up code, kept small for the instruction cache
+#pragma unroll 1
   for (int i = first; i < BM; i += stride)
     ix.offAm[i] = m0 + i < M ? gather(ix.gt.c, ncn, cb | ((m0 + i) << g.nn)).x : 0u;
-  #pragma unroll 1
+#pragma unroll 1
   for (int i = first; i < BN; i += stride) ix.offBn[i] = n0 + i < N ? gather(ix.gt.c, ncn, cb | (n0 + i)).y : 0u;
   if (!g.c_identity) {
-    #pragma unroll 1
+  #pragma unroll 1
     for (int i = first; i < BM; i += stride)
       ix.offCm[i] = m0 + i < M ? out_offset(g, ix.gt, cb | ((m0 + i) << g.nn)) : 0u;
-    #pragma unroll 1
+  #pragma unroll 1
     for (int i = first; i < BN; i += stride) ix.offCn[i] = n0 + i < N ? out_offset(g, ix.gt, n0 + i) : 0u;
   }
-  #pragma unroll 1
+#pragma unroll 1
   for (int i = first; i < BK; i += stride) {
     const uint2 o = gather(ix.gt.k, nkn, static_cast<uint32_t>(i) < K ? static_cast<uint32_t>(i) : 0u);
     ix.offAk[i] = o.x;
