@@ -128,10 +128,10 @@ __device__ __forceinline__ void tile_tables(const StepGeom& g, TileIdx<C>& ix, i
 #pragma unroll 1
   for (int i = first; i < BN; i += stride) ix.offBn[i] = n0 + i < N ? gather(ix.gt.c, ncn, cb | (n0 + i)).y : 0u;
   if (!g.c_identity) {
-  #pragma unroll 1
+#pragma unroll 1
     for (int i = first; i < BM; i += stride)
       ix.offCm[i] = m0 + i < M ? out_offset(g, ix.gt, cb | ((m0 + i) << g.nn)) : 0u;
-  #pragma unroll 1
+#pragma unroll 1
     for (int i = first; i < BN; i += stride) ix.offCn[i] = n0 + i < N ? out_offset(g, ix.gt, n0 + i) : 0u;
   }
 #pragma unroll 1
