@@ -3,12 +3,12 @@
 // the workspace (counters, split-K scratch, arena) and caches the result per
 // (semiring, number of primes) inside the plan.
 #include <algorithm>
-#include <iterator>
 #include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <utility>
 
 #include "exec.h"
 #include "kernels.h"
@@ -50,11 +50,11 @@ class LevelArena {
     size = static_cast<int64_t>(align_up(static_cast<size_t>(size), static_cast<size_t>(align_)));
     for (auto it = free_.begin(); it != free_.end(); ++it) {
       if (it->second.len >= size) {
-        int64_t off = it->first;
-        Block blk = it->second;
+        const int64_t off = it->first;
+        Block blk = std::move(it->second);
         free_.erase(it);
         war->insert(war->end(), blk.rel.begin(), blk.rel.end());
-        if (blk.len > size) free_[off + size] = Block{blk.len - size, blk.rel};
+        if (blk.len > size) free_.emplace(off + size, Block{blk.len - size, std::move(blk.rel)});
         return off;
       }
     }
@@ -86,12 +86,12 @@ class LevelArena {
     std::vector<int32_t> rel;
   };
   static void merge(Block* a, const Block& b) {
-    // both releaser lists are sorted and duplicate-free: a linear union
+    // both releaser lists are sorted and duplicate-free: merged in place
     a->len += b.len;
-    std::vector<int32_t> u;
-    u.reserve(a->rel.size() + b.rel.size());
-    std::set_union(a->rel.begin(), a->rel.end(), b.rel.begin(), b.rel.end(), std::back_inserter(u));
-    a->rel.swap(u);
+    const size_t mid = a->rel.size();
+    a->rel.insert(a->rel.end(), b.rel.begin(), b.rel.end());
+    std::inplace_merge(a->rel.begin(), a->rel.begin() + mid, a->rel.end());
+    a->rel.erase(std::unique(a->rel.begin(), a->rel.end()), a->rel.end());
   }
   std::map<int64_t, Block> free_;
   int64_t top_ = 0;
@@ -210,7 +210,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
       const Step& S = p->steps[st];
       std::vector<int32_t> war;
       c_off[st] = arena.alloc(int64_t(1) << S.g.rc, &war);
-      dep[st] = war;
+      dep[st].swap(war);
       if (ln[st].scratch) {
         war.clear();
         s_off[st] = sarena.alloc(static_cast<int64_t>((ln[st].scratch + 255) / 256), &war);
@@ -354,8 +354,8 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
     E.dep_begin = static_cast<int32_t>(X->deps.size());
     E.dep_count = static_cast<int32_t>(red[st].size());
     X->deps.insert(X->deps.end(), red[st].begin(), red[st].end());
-    int kernel, tile, split;
-    dev::pick_launch(S.g, s, np, &kernel, &tile, &split, X->batched);
+    // the launch shape chosen above (one cost-model call per step)
+    const int kernel = ln[st].kernel, tile = ln[st].tile, split = ln[st].split;
     if (internal(st) || groot[st] == st) {
       // group member: one whole-output chunk, no k split
       const dev::NaiveShape sh = dev::naive_shape(S.g.rc, S.g.nk, false);
@@ -398,7 +398,7 @@ int build_exec(const tn_plan_s* p, tn_semiring_t s, int32_t nprimes, ExecPlan* X
         E.scratch_off = s_off[st] * 256;
       }
     } else {
-      const dev::NaiveShape sh = dev::naive_shape(S.g.rc, S.g.nk, !is_kbest(s), npt);
+      const dev::NaiveShape& sh = ln[st].sh;
       E.kernel = kKernNaive;
       E.R = sh.R;
       E.chunk = sh.chunk;
