@@ -234,7 +234,9 @@ int tn_contract_timed(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *pr
  * phase marks of the body [6], [7] (general chunk: offset tables built,
  * reduction done; GEMM tile: main loop done, final merge or store started;
  * 0 where the task kind has none).  task_step[t], task_kind[t] (0 general
- * chunk, 1 GEMM tile, 2 final copy, 3 group of tiny steps) and step_level[i]
+ * chunk, 1 GEMM tile, 2 final copy -- only when the last step runs inside a
+ * group of tiny steps; otherwise the task that completes the last step
+ * writes the result -- 3 group of tiny steps) and step_level[i]
  * (dependency level of executor step i) describe the schedule; any of the
  * three may be NULL.  Waits for the stream. */
 int tn_contract_trace(tn_plan_t plan, tn_semiring_t semiring, const uint32_t *primes, int32_t nprimes,
