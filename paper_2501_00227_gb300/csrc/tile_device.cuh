@@ -960,7 +960,7 @@ __device__ __forceinline__ void tile_mainloop_counting(const StepGeom& g, const 
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN / 2; ++j) mc2[i][j] = 0xFC00FC00u;
-#pragma unroll 4
+#pragma unroll 8
       for (int kk = 0; kk < C::BKG; ++kk) {
         uint32_t ah[TM], bh[TN / 2];
         load_frag<TM>(Agh + kk * BM + ty * TM, ah);
