@@ -142,7 +142,7 @@ INT32_PER_CLK_SM = 64
 # launch of the small bench command (profiles/launches_bench_reg3_n100_n140.md),
 # averaged per instantiation.  Null once a kernel changes after the capture.
 DRAM_BYTES_PER_LAUNCH = {
-    "tropical_i32": 0.32e6, "counting": 55.86e6, "modp": 28.31e6,
+    "tropical_i32": 0.31e6, "counting": 55.84e6, "modp": 27.33e6,
     "profile": "profiles/launches_bench_reg3_n100_n140.md",
 }
 
@@ -150,9 +150,9 @@ DRAM_BYTES_PER_LAUNCH = {
 # instructions executed x 32 / (tc x primes)), from the ncu captures kept
 # under profiles/ (one launch on random 3-regular n = 140).
 INSTR_PER_OP = {
-    "tropical_i32": {"value": 47.55e6 * 32 / 4.423e8, "profile": "profiles/k_exec_tropical_i32_reg3_n140.md"},
-    "counting": {"value": 187.27e6 * 32 / 4.423e8, "profile": "profiles/k_exec_counting_reg3_n140_s3.md"},
-    "modp": {"value": 214.52e6 * 32 / (3 * 4.423e8), "profile": "profiles/k_exec_modp_reg3_n140.md"},
+    "tropical_i32": {"value": 47.72e6 * 32 / 4.423e8, "profile": "profiles/k_exec_tropical_i32_reg3_n140.md"},
+    "counting": {"value": 187.49e6 * 32 / 4.423e8, "profile": "profiles/k_exec_counting_reg3_n140_s3.md"},
+    "modp": {"value": 215.00e6 * 32 / (3 * 4.423e8), "profile": "profiles/k_exec_modp_reg3_n140.md"},
 }
 
 
